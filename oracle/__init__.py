@@ -1,0 +1,398 @@
+"""Plain CPU FP64 oracle for neural texture compression (ctypes wrapper).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline / reference legs of ``bench.py`` may import this package.  It
+shares no code with the CUDA library: the arithmetic lives in
+``ntc_oracle.c`` (plain C, double precision) and in the few numpy helpers
+below, each citing the paper passage it restates.
+
+Paper: "Random-Access Neural Compression of Material Textures" (2023).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ntc_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+MAX_LEVELS = 8
+
+
+def build(force: bool = False) -> str:
+    """Compile ``liboracle.so`` with gcc (portable flags; no -march)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
+            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "ntc_oracle.h"))):
+        tmp = _LIB + ".tmp.%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC,
+                               "-lm", "-lpthread"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        _declare(_lib)
+    return _lib
+
+
+class _Model(C.Structure):
+    _fields_ = [
+        ("width", C.c_int), ("height", C.c_int), ("channels", C.c_int), ("mips", C.c_int),
+        ("levels", C.c_int), ("c0", C.c_int), ("c1", C.c_int), ("n0", C.c_int), ("n1", C.c_int),
+        ("q0", C.c_double), ("q1", C.c_double),
+        ("g0w", C.c_int * MAX_LEVELS), ("g0h", C.c_int * MAX_LEVELS),
+        ("g1w", C.c_int * MAX_LEVELS), ("g1h", C.c_int * MAX_LEVELS),
+        ("grid0", C.c_void_p * MAX_LEVELS), ("grid1", C.c_void_p * MAX_LEVELS),
+        ("k_in", C.c_int), ("hidden", C.c_int), ("act", C.c_int), ("out_act", C.c_int),
+        ("w1", C.c_void_p), ("b1", C.c_void_p), ("w2", C.c_void_p), ("b2", C.c_void_p),
+        ("w3", C.c_void_p), ("b3", C.c_void_p),
+    ]
+
+
+class _Noise(C.Structure):
+    _fields_ = [("enabled", C.c_int), ("seed", C.c_uint64), ("step", C.c_int64)]
+
+
+class _Grads(C.Structure):
+    _fields_ = [("grid0", C.c_void_p * MAX_LEVELS), ("grid1", C.c_void_p * MAX_LEVELS),
+                ("w1", C.c_void_p), ("b1", C.c_void_p), ("w2", C.c_void_p),
+                ("b2", C.c_void_p), ("w3", C.c_void_p), ("b3", C.c_void_p)]
+
+
+def _declare(L):
+    P, I, I64, U64, D = C.c_void_p, C.c_int, C.c_int64, C.c_uint64, C.c_double
+    sig = {
+        "or_mips": (I, [I, I]),
+        "or_pyramid": (I, [I, I, P, P, P, P]),
+        "or_level_of_mip": (I, [I, I]),
+        "or_quantize": (None, [P, I64, I, D, P]),
+        "or_dequantize": (None, [P, I64, I, D, P]),
+        "or_cell_bytes": (I, [I, I]),
+        "or_pack": (None, [P, I64, I, I, P]),
+        "or_unpack": (None, [P, I64, I, I, P]),
+        "or_splitmix64": (U64, [U64]),
+        "or_rng": (U64, [U64, U64, U64]),
+        "or_noise_value": (D, [U64, I64, I, I, I64, I, I, D]),
+        "or_sample_batch": (None, [U64, I64, I64, I, I, I, P]),
+        "or_positional_encoding": (None, [I, I, P]),
+        "or_activation": (D, [I, D]),
+        "or_activation_grad": (D, [I, D]),
+        "or_features": (None, [P, I, I, I, P, P]),
+        "or_decode_xym": (None, [P, I64, P, P, P, I]),
+        "or_decode_uvl": (None, [P, I64, P, P, P, I]),
+        "or_decode_trilinear": (None, [P, I64, P, P, I]),
+        "or_backward_xym": (None, [P, I64, P, P, P, P, I]),
+        "or_loss_grad_xym": (D, [P, I64, P, P, P, P, I]),
+        "or_cosine_lr": (D, [D, I64, I64]),
+        "or_adam": (None, [P, P, P, P, I64, D, I64, D, D, D, I, D, D]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def default_threads() -> int:
+    return max(1, os.cpu_count() or 1)
+
+
+# ---------------------------------------------------------------------------
+# pyramid / quantisation helpers
+# ---------------------------------------------------------------------------
+def mips(width: int, height: int) -> int:
+    return lib().or_mips(width, height)
+
+
+def pyramid(width: int, height: int):
+    """Feature-level grid sizes (Sec. 4.1, Table 1): list of
+    ``((g0w, g0h), (g1w, g1h))`` per level."""
+    a = [np.zeros(MAX_LEVELS, np.int32) for _ in range(4)]
+    n = lib().or_pyramid(width, height, *[_p(x) for x in a])
+    return [((int(a[0][j]), int(a[1][j])), (int(a[2][j]), int(a[3][j]))) for j in range(n)]
+
+
+def level_of_mip(m: int, levels: int) -> int:
+    return lib().or_level_of_mip(m, levels)
+
+
+def quantize(x: np.ndarray, n_levels: int, q: float) -> np.ndarray:
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.empty(x.shape, np.int32)
+    lib().or_quantize(_p(x), x.size, n_levels, q, _p(out))
+    return out
+
+
+def dequantize(idx: np.ndarray, n_levels: int, q: float) -> np.ndarray:
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    out = np.empty(idx.shape, np.float64)
+    lib().or_dequantize(_p(idx), idx.size, n_levels, q, _p(out))
+    return out
+
+
+def cell_bytes(c: int, bits: int) -> int:
+    return lib().or_cell_bytes(c, bits)
+
+
+def pack(idx: np.ndarray, c: int, bits: int) -> np.ndarray:
+    """Pack ``[cells, c]`` indices into ``[cells, cell_bytes]`` uint8."""
+    idx = np.ascontiguousarray(idx, dtype=np.int32).reshape(-1, c)
+    cb = cell_bytes(c, bits)
+    out = np.empty((idx.shape[0], cb), np.uint8)
+    lib().or_pack(_p(idx), idx.shape[0], c, bits, _p(out))
+    return out
+
+
+def unpack(packed: np.ndarray, c: int, bits: int) -> np.ndarray:
+    packed = np.ascontiguousarray(packed, dtype=np.uint8)
+    cb = cell_bytes(c, bits)
+    cells = packed.size // cb
+    out = np.empty((cells, c), np.int32)
+    lib().or_unpack(_p(packed), cells, c, bits, _p(out))
+    return out
+
+
+def quant_range(n_levels: int, q: float):
+    """Continuous clamp range [-(N-1)/2 Q, N/2 Q] (Sec. 4.2)."""
+    return -(n_levels - 1) / 2.0 * q, n_levels / 2.0 * q
+
+
+# ---------------------------------------------------------------------------
+# random numbers
+# ---------------------------------------------------------------------------
+def splitmix64(x: int) -> int:
+    return int(lib().or_splitmix64(x))
+
+
+def rng(seed: int, stream: int, counter: int) -> int:
+    return int(lib().or_rng(seed, stream, counter))
+
+
+def noise_value(seed, step, level, grid, cell, ch, c, q) -> float:
+    return float(lib().or_noise_value(seed, step, level, grid, cell, ch, c, q))
+
+
+def sample_batch(seed: int, step: int, batch: int, width: int, height: int, n_mips: int):
+    """``[batch, 3]`` int32 rows (x, y, m) of one training batch (Sec. 5.1)."""
+    out = np.empty((batch, 3), np.int32)
+    lib().or_sample_batch(seed, step, batch, width, height, n_mips, _p(out))
+    return out
+
+
+def activation(act: int, z: float) -> float:
+    return float(lib().or_activation(act, z))
+
+
+def activation_grad(act: int, z: float) -> float:
+    return float(lib().or_activation_grad(act, z))
+
+
+def positional_encoding(x: int, y: int) -> np.ndarray:
+    out = np.empty(12, np.float64)
+    lib().or_positional_encoding(x, y, _p(out))
+    return out
+
+
+# ---------------------------------------------------------------------------
+# model
+# ---------------------------------------------------------------------------
+class Model:
+    """One material: latent grids (float64 values) + decoder weights.
+
+    ``grids0[j]`` is ``[g0h, g0w, c0]``, ``grids1[j]`` ``[g1h, g1w, c1]``;
+    ``weights`` is ``[w1, b1, w2, b2, w3, b3]`` with ``w`` stored
+    ``[out][in]``.  ``act`` 0 = ReLU, 1 = hardGELU; ``out_act`` 0 = sigmoid,
+    1 = identity.
+    """
+
+    def __init__(self, width, height, channels, c0, c1, n0, n1, q0, q1, grids0, grids1,
+                 weights, k_in, hidden=64, act=0, out_act=0):
+        self.width, self.height, self.channels = width, height, channels
+        self.mips = mips(width, height)
+        self.levels = len(grids0)
+        self.c0, self.c1, self.n0, self.n1, self.q0, self.q1 = c0, c1, n0, n1, q0, q1
+        self.grids0 = [np.ascontiguousarray(g, np.float64) for g in grids0]
+        self.grids1 = [np.ascontiguousarray(g, np.float64) for g in grids1]
+        self.weights = [np.ascontiguousarray(w, np.float64) for w in weights]
+        self.k_in, self.hidden, self.act, self.out_act = k_in, hidden, act, out_act
+        s = _Model()
+        s.width, s.height, s.channels, s.mips, s.levels = width, height, channels, self.mips, self.levels
+        s.c0, s.c1, s.n0, s.n1, s.q0, s.q1 = c0, c1, n0, n1, q0, q1
+        for j in range(self.levels):
+            s.g0h[j], s.g0w[j] = self.grids0[j].shape[:2]
+            s.g1h[j], s.g1w[j] = self.grids1[j].shape[:2]
+            s.grid0[j] = self.grids0[j].ctypes.data
+            s.grid1[j] = self.grids1[j].ctypes.data
+        s.k_in, s.hidden, s.act, s.out_act = k_in, hidden, act, out_act
+        w = self.weights
+        s.w1, s.b1, s.w2, s.b2, s.w3, s.b3 = [a.ctypes.data for a in w]
+        assert w[0].shape == (hidden, k_in) and w[2].shape == (hidden, hidden)
+        assert w[4].shape == (channels, hidden)
+        self._s = s
+
+    # -- helpers -----------------------------------------------------------
+    @staticmethod
+    def _noise(noise):
+        if noise is None:
+            return None, None
+        n = _Noise(1, noise[0], noise[1])
+        return n, C.byref(n)
+
+    def features(self, x, y, m, noise=None):
+        row = np.empty(self.k_in, np.float64)
+        _, nz = self._noise(noise)
+        lib().or_features(C.byref(self._s), x, y, m, nz, _p(row))
+        return row
+
+    def decode_xym(self, xym, noise=None, threads=None):
+        xym = np.ascontiguousarray(xym, np.int32).reshape(-1, 3)
+        out = np.empty((xym.shape[0], self.channels), np.float64)
+        _, nz = self._noise(noise)
+        lib().or_decode_xym(C.byref(self._s), xym.shape[0], _p(xym), nz, _p(out),
+                            threads or default_threads())
+        return out
+
+    def decode(self, uvl, noise=None, threads=None):
+        """Nearest-texel decode of ``[n, 3]`` float32 (u, v, lod) queries."""
+        uvl = np.ascontiguousarray(uvl, np.float32).reshape(-1, 3)
+        out = np.empty((uvl.shape[0], self.channels), np.float64)
+        _, nz = self._noise(noise)
+        lib().or_decode_uvl(C.byref(self._s), uvl.shape[0], _p(uvl), nz, _p(out),
+                            threads or default_threads())
+        return out
+
+    def decode_trilinear(self, uvl, threads=None):
+        uvl = np.ascontiguousarray(uvl, np.float32).reshape(-1, 3)
+        out = np.empty((uvl.shape[0], self.channels), np.float64)
+        lib().or_decode_trilinear(C.byref(self._s), uvl.shape[0], _p(uvl), _p(out),
+                                  threads or default_threads())
+        return out
+
+    def zero_grads(self):
+        g = {"grid0": [np.zeros_like(a) for a in self.grids0],
+             "grid1": [np.zeros_like(a) for a in self.grids1],
+             "w": [np.zeros_like(a) for a in self.weights]}
+        s = _Grads()
+        for j in range(self.levels):
+            s.grid0[j] = g["grid0"][j].ctypes.data
+            s.grid1[j] = g["grid1"][j].ctypes.data
+        s.w1, s.b1, s.w2, s.b2, s.w3, s.b3 = [a.ctypes.data for a in g["w"]]
+        g["_s"] = s
+        return g
+
+    def backward_xym(self, xym, dout, noise=None, threads=None):
+        """Gradients of sum(dout * y) (exact reverse mode)."""
+        xym = np.ascontiguousarray(xym, np.int32).reshape(-1, 3)
+        dout = np.ascontiguousarray(dout, np.float64).reshape(xym.shape[0], self.channels)
+        g = self.zero_grads()
+        _, nz = self._noise(noise)
+        lib().or_backward_xym(C.byref(self._s), xym.shape[0], _p(xym), _p(dout), nz,
+                              C.byref(g["_s"]), threads or default_threads())
+        return g
+
+    def loss_grad_xym(self, xym, target, noise=None, threads=None):
+        """L2 loss (Sec. 4.5) and its gradients for texels ``xym`` with
+        ``target`` ``[n, c]`` in [0, 1]."""
+        xym = np.ascontiguousarray(xym, np.int32).reshape(-1, 3)
+        target = np.ascontiguousarray(target, np.float64).reshape(xym.shape[0], self.channels)
+        g = self.zero_grads()
+        _, nz = self._noise(noise)
+        loss = lib().or_loss_grad_xym(C.byref(self._s), xym.shape[0], _p(xym), _p(target), nz,
+                                      C.byref(g["_s"]), threads or default_threads())
+        return float(loss), g
+
+
+def uvl_of_xym(xym: np.ndarray, width: int, height: int) -> np.ndarray:
+    """Texel-centre (u, v, lod) query rows for integer texels (x, y, m)."""
+    xym = np.asarray(xym).reshape(-1, 3)
+    m = xym[:, 2].astype(np.int64)
+    wm = np.maximum(1, width >> m)
+    hm = np.maximum(1, height >> m)
+    out = np.empty((xym.shape[0], 3), np.float32)
+    out[:, 0] = (xym[:, 0] + 0.5) / wm
+    out[:, 1] = (xym[:, 1] + 0.5) / hm
+    out[:, 2] = m
+    return out
+
+
+def targets_of_xym(mip_chain_u8, xym) -> np.ndarray:
+    """Reference values t = q/255 of 8-bit mip texels (App. I: 8-bit sources)."""
+    xym = np.asarray(xym).reshape(-1, 3)
+    c = mip_chain_u8[0].shape[2]
+    out = np.empty((xym.shape[0], c), np.float64)
+    for m in np.unique(xym[:, 2]):
+        sel = xym[:, 2] == m
+        lvl = mip_chain_u8[int(m)]
+        out[sel] = lvl[xym[sel, 1], xym[sel, 0]].astype(np.float64) / 255.0
+    return out
+
+
+def cosine_lr(lr0: float, t: int, total: int) -> float:
+    return float(lib().or_cosine_lr(lr0, t, total))
+
+
+def adam(p, m, v, g, lr, t, beta1=0.9, beta2=0.999, eps=1e-8, clamp=None):
+    """In-place FP64 Adam step on contiguous float64 arrays."""
+    lo, hi = clamp if clamp is not None else (0.0, 0.0)
+    lib().or_adam(_p(p), _p(m), _p(v), _p(np.ascontiguousarray(g, np.float64)), p.size, lr, t,
+                  beta1, beta2, eps, 1 if clamp is not None else 0, lo, hi)
+
+
+# ---------------------------------------------------------------------------
+# metrics and storage (numpy)
+# ---------------------------------------------------------------------------
+def texture_set_psnr(ref_levels, test_levels) -> float:
+    """Texture-set PSNR over a mip chain (App. H, Eq. 1): the squared error
+    summed over every mip and channel, divided by c * sum_j w_j h_j, peak 1."""
+    se, count = 0.0, 0
+    for r, t in zip(ref_levels, test_levels):
+        d = np.asarray(r, np.float64) - np.asarray(t, np.float64)
+        se += float(np.sum(d * d))
+        count += d.size
+    mse = se / count
+    return float("inf") if mse == 0.0 else -10.0 * math.log10(mse)
+
+
+def psnr(ref, test) -> float:
+    """PSNR of two equally shaped arrays with values in [0, 1]."""
+    return texture_set_psnr([ref], [test])
+
+
+def grid_storage_bytes(width: int, height: int, c0: int, b0: int, c1: int, b1: int,
+                       all_levels: bool = True, g0_side: int | None = None) -> float:
+    """Bytes of the quantised feature pyramid (App. E, Table 5): c*B bits per
+    cell, densely packed, summed over every feature level's two grids (or
+    over level 0 only).  ``g0_side`` overrides the level-0 G0 side (W/4 in
+    Table 1; profiles 1.0 and 2.25 use W/2); later levels shrink by 4."""
+    if g0_side is None:
+        levels = pyramid(width, height)
+    else:
+        levels = pyramid(4 * g0_side, 4 * g0_side * height // width)
+    if not all_levels:
+        levels = levels[:1]
+    bits = 0
+    for (g0w, g0h), (g1w, g1h) in levels:
+        bits += g0w * g0h * c0 * b0 + g1w * g1h * c1 * b1
+    return bits / 8.0
+
+
+def lod_law_probs(n_mips: int, uniform_frac: float = 0.05) -> np.ndarray:
+    """P(m) of the training LOD sampler (Sec. 5.1): floor(-log4 X) has
+    P(m) = 3 * 4^-(m+1), the tail folded into the last mip, mixed with a
+    uniform choice over all mips at ``uniform_frac``."""
+    p = np.array([3.0 * 4.0 ** -(m + 1) for m in range(n_mips)])
+    p[-1] = 1.0 - p[:-1].sum()
+    return (1.0 - uniform_frac) * p + uniform_frac / n_mips

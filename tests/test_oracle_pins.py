@@ -1,0 +1,389 @@
+"""Pins of the FP64 oracle against what the paper and mathematics fix.
+
+Each test checks the oracle against something other than itself: values the
+paper prints (tests/golden/), closed forms, library routines (scipy, torch)
+on special cases, finite differences and brute force.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from _cases import make_case
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden_rows(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+# ---------------------------------------------------------------- pyramid ---
+def test_table1_pyramid_1024():
+    rows = _golden_rows("table1_pyramid_1024.txt")
+    lv = oracle.pyramid(1024, 1024)
+    assert len(lv) == len(rows)
+    n_mips = oracle.mips(1024, 1024)
+    assert n_mips == 11
+    for j, (level, g0, g1, mips) in enumerate(rows):
+        assert int(level) == j
+        assert lv[j] == ((int(g0), int(g0)), (int(g1), int(g1)))
+        for m in map(int, mips.split(",")):
+            assert oracle.level_of_mip(m, len(lv)) == j
+    # every mip of the chain is served by exactly one level
+    assert sorted(sum([list(map(int, r[3].split(","))) for r in rows], [])) == list(range(n_mips))
+
+
+def test_table5_grid_storage():
+    for prof, side, g0, c0, b0, c1, b1, mb, scope in _golden_rows("table5_grid_storage.txt"):
+        side, g0 = int(side), int(g0)
+        got = oracle.grid_storage_bytes(side, side, int(c0), int(b0), int(c1), int(b1),
+                                        all_levels=(scope == "pyramid"), g0_side=g0) / 2 ** 20
+        tol = 1e-9 if scope == "level0" else 3e-3
+        assert abs(got - float(mb)) <= tol, (prof, side, got, mb)
+
+
+def test_pyramid_last_level_serves_three_mips_at_4k():
+    lv = oracle.pyramid(4096, 4096)
+    assert [a[0] for a, _ in lv] == [1024, 256, 64, 16, 4]
+    assert [b[0] for _, b in lv] == [512, 128, 32, 8, 2]
+    served = [oracle.level_of_mip(m, len(lv)) for m in range(13)]
+    assert served == [0, 0, 0, 0, 1, 1, 2, 2, 3, 3, 4, 4, 4]
+
+
+# ------------------------------------------------------------ random bits ---
+def test_splitmix64_published_vectors():
+    gamma = 0x9E3779B97F4A7C15
+    for n, hx in _golden_rows("splitmix64_vectors.txt"):
+        assert oracle.splitmix64(((int(n) - 1) * gamma) % 2 ** 64) == int(hx, 16)
+
+
+def test_noise_uniform_in_half_bin():
+    q = 1.0 / 16
+    v = np.array([oracle.noise_value(7, 3, 0, 0, cell, ch, 4, q) for cell in range(2000)
+                  for ch in range(4)])
+    assert v.min() >= -q / 2 and v.max() < q / 2
+    assert abs(v.mean()) < 0.02 * q
+    hist, _ = np.histogram(v, bins=8, range=(-q / 2, q / 2))
+    exp = v.size / 8
+    assert ((hist - exp) ** 2 / exp).sum() < 30  # chi^2, 7 dof
+    # a new value for another step, grid or level
+    a = oracle.noise_value(7, 3, 0, 0, 5, 1, 4, q)
+    assert a != oracle.noise_value(7, 4, 0, 0, 5, 1, 4, q)
+    assert a != oracle.noise_value(7, 3, 0, 1, 5, 1, 4, q)
+    assert a != oracle.noise_value(7, 3, 1, 0, 5, 1, 4, q)
+
+
+def test_sampler_lod_law_chi2():
+    """LOD = floor(-log4 X) mixed 95/5 with a uniform LOD (Sec. 5.1)."""
+    n_mips, batch = 12, 200_000
+    xym = oracle.sample_batch(11, 0, batch, 2048, 2048, n_mips)
+    counts = np.bincount(xym[:, 2], minlength=n_mips)
+    p = oracle.lod_law_probs(n_mips)
+    assert abs(p[0] - (0.95 * 0.75 + 0.05 / 12)) < 1e-15
+    exp = p * batch
+    ok = exp >= 5
+    chi2 = (((counts - exp) ** 2 / exp)[ok]).sum()
+    assert chi2 < 40, (counts, exp)  # 11 dof: p < 1e-4
+    # texels are inside their mip and uniform over it
+    w = np.maximum(1, 2048 >> xym[:, 2])
+    assert (xym[:, 0] >= 0).all() and (xym[:, 0] < w).all() and (xym[:, 1] < w).all()
+    sel = xym[:, 2] == 0
+    hx, _ = np.histogram(xym[sel, 0], bins=16, range=(0, 2048))
+    e = sel.sum() / 16
+    assert ((hx - e) ** 2 / e).sum() < 45
+
+
+# ----------------------------------------------------------- quantisation ---
+@pytest.mark.parametrize("bits", [1, 2, 4, 8])
+def test_quantizer_levels_and_roundtrip(bits):
+    n = 1 << bits
+    q = 1.0 / n
+    idx = np.arange(n, dtype=np.int32)
+    x = oracle.dequantize(idx, n, q)
+    # N levels k*Q, k in [-(N/2-1), N/2]; zero is a level (Sec. 4.2)
+    assert np.array_equal(x, (np.arange(n) - (n // 2 - 1)) * q)
+    assert 0.0 in x and x[n // 2 - 1] == 0.0
+    assert np.array_equal(oracle.quantize(x, n, q), idx)
+    lo, hi = oracle.quant_range(n, q)
+    assert oracle.quantize(np.array([lo, hi, -10.0, 10.0]), n, q).tolist() == [0, n - 1, 0, n - 1]
+    # round half to even: (k + 1/2) Q goes to the even neighbour
+    mid = (np.arange(-(n // 2 - 1), n // 2) + 0.5) * q
+    k = oracle.quantize(mid, n, q) - (n // 2 - 1)
+    assert (k % 2 == 0).all()
+
+
+def test_pack_layout_by_hand():
+    # 3 channels x 4 bits -> 12 bits -> 2 bytes per cell; channel 0 in the
+    # low nibble of byte 0
+    packed = oracle.pack(np.array([[1, 2, 3], [15, 0, 9]]), 3, 4)
+    assert packed.tolist() == [[0x21, 0x03], [0x0F, 0x09]]
+    # 12 channels x 4 bits -> 48 bits -> padded to 8 bytes
+    assert oracle.cell_bytes(12, 4) == 8 and oracle.cell_bytes(8, 2) == 2
+    assert oracle.cell_bytes(8, 4) == 4 and oracle.cell_bytes(20, 4) == 16
+
+
+@pytest.mark.parametrize("c,bits", [(8, 4), (12, 4), (16, 4), (8, 2), (12, 2), (5, 8), (7, 1)])
+def test_pack_roundtrip(c, bits):
+    rng = np.random.default_rng(c * 10 + bits)
+    idx = rng.integers(0, 1 << bits, size=(257, c)).astype(np.int32)
+    assert np.array_equal(oracle.unpack(oracle.pack(idx, c, bits), c, bits), idx)
+
+
+# -------------------------------------------------- positional encoding ---
+def test_positional_encoding_closed_form():
+    """Triangle waves equal (2/pi) asin(sin) / (2/pi) asin(cos) of the texel
+    phase, periods 8, 4, 2 (Sec. 4.3.2); last value of each axis constant."""
+    seen = set()
+    for y in range(16):
+        for x in range(16):
+            pe = oracle.positional_encoding(x, y)
+            for a, c in enumerate((x, y)):
+                for h in range(3):
+                    t = (c + 0.5) / (8 >> h)
+                    s_ref = 2 / math.pi * math.asin(math.sin(2 * math.pi * t))
+                    c_ref = 2 / math.pi * math.asin(max(-1.0, min(1.0, math.cos(2 * math.pi * t))))
+                    assert abs(pe[6 * a + 2 * h] - s_ref) < 1e-9
+                    assert abs(pe[6 * a + 2 * h + 1] - c_ref) < 1e-9
+                assert pe[6 * a + 5] == 0.0
+            assert np.array_equal(pe, oracle.positional_encoding(x % 8, y % 8))
+            if x < 8 and y < 8:
+                seen.add(tuple(pe))
+    assert len(seen) == 64  # every texel of the 8x8 tile has its own code
+
+
+# --------------------------------------------------------- interpolation ---
+def test_features_exact_when_grid_matches_mip():
+    """At a mip whose resolution equals the grid's, texel centres land on cell
+    centres and the interpolated features are the grid values exactly."""
+    case = make_case(256, 256, 8, 8, 8, seed=3)
+    md = case.oracle_model()
+    # G0 of level 0 is 64x64 = mip 2; G1 32x32 = mip 3
+    rng = np.random.default_rng(0)
+    for _ in range(50):
+        x, y = rng.integers(0, 64, size=2)
+        row = md.features(int(x), int(y), 2)
+        assert np.array_equal(row[:8], md.grids0[0][y, x])
+        x, y = rng.integers(0, 32, size=2)
+        row = md.features(int(x), int(y), 3)
+        assert np.array_equal(row[8:16], md.grids1[0][y, x])
+
+
+def test_bilinear_matches_scipy_map_coordinates():
+    scipy_nd = pytest.importorskip("scipy.ndimage")
+    case = make_case(64, 32, 4, 3, 2, seed=4)   # non-square, odd channel counts
+    md = case.oracle_model()
+    for m in range(md.mips):
+        j = oracle.level_of_mip(m, md.levels)
+        wm, hm = max(1, 64 >> m), max(1, 32 >> m)
+        for (x, y) in [(0, 0), (wm - 1, hm - 1), (wm // 2, hm // 3), (1 % wm, (hm - 1) // 2)]:
+            row = md.features(x, y, m)
+            for k, (grid, base) in enumerate(((md.grids0[j], 0), (md.grids1[j], md.c0))):
+                gh, gw, c = grid.shape
+                px = (x + 0.5) / wm * gw - 0.5
+                py = (y + 0.5) / hm * gh - 0.5
+                for ch in range(c):
+                    ref = scipy_nd.map_coordinates(grid[:, :, ch], [[py], [px]], order=1,
+                                                   mode="nearest")[0]
+                    assert abs(row[base + ch] - ref) < 1e-12
+
+
+def test_feature_row_layout():
+    case = make_case(128, 128, 4, 8, 8, seed=5)
+    md = case.oracle_model()
+    row = md.features(13, 6, 1)
+    assert row.shape == (32,)
+    assert np.array_equal(row[16:28], oracle.positional_encoding(13, 6))
+    assert row[28] == 1.0 / (md.mips - 1)
+    assert (row[29:] == 0).all()
+
+
+# ------------------------------------------------------------------- MLP ---
+def test_hardgelu_closed_form():
+    a = oracle.activation
+    assert a(1, -2.0) == 0.0 and a(1, 2.0) == 2.0 and a(1, 0.0) == 0.0
+    assert a(1, -0.75) == -0.75 / 3 * 0.75
+    assert a(1, 1.5) == 1.5 and a(1, -1.5) == 0.0          # continuous at the joints
+    assert abs(a(1, 1.5 - 1e-12) - 1.5) < 1e-11 and abs(a(1, -1.5 + 1e-12)) < 1e-11
+    assert a(0, -1.0) == 0.0 and a(0, 0.5) == 0.5
+
+
+def test_decode_matches_torch_mlp_on_oracle_features():
+    torch = pytest.importorskip("torch")
+    F = torch.nn.functional
+    for act, out_act in [(0, 0), (1, 0), (0, 1)]:
+        case = make_case(128, 64, 5, 4, 6, act=act, out_act=out_act, seed=6)
+        md = case.oracle_model()
+        xym = np.array([[3, 2, 0], [17, 9, 1], [0, 0, 6], [5, 1, 3]], np.int32)
+        out = md.decode_xym(xym)
+        w = [torch.tensor(a, dtype=torch.float64) for a in md.weights]
+        for i, (x, y, m) in enumerate(xym):
+            X = torch.tensor(md.features(int(x), int(y), int(m)))
+            h = F.linear(X, w[0], w[1])
+            h = F.relu(h) if act == 0 else torch.where(
+                h < -1.5, torch.zeros_like(h), torch.where(h > 1.5, h, h / 3 * (h + 1.5)))
+            h2 = F.linear(h, w[2], w[3])
+            h2 = F.relu(h2) if act == 0 else torch.where(
+                h2 < -1.5, torch.zeros_like(h2), torch.where(h2 > 1.5, h2, h2 / 3 * (h2 + 1.5)))
+            y_ = F.linear(h2, w[4], w[5])
+            if out_act == 0:
+                y_ = torch.sigmoid(y_)
+            assert np.allclose(out[i], y_.numpy(), rtol=0, atol=1e-13)
+
+
+def test_constant_grids_give_constant_output():
+    case = make_case(64, 64, 6, 4, 4, seed=7)
+    g0 = [np.full_like(v, 0.25, dtype=np.float64) for v in case.val0]
+    g1 = [np.full_like(v, -0.125, dtype=np.float64) for v in case.val1]
+    w = [a.copy() for a in case.weights]
+    w[0][:, 8:] = 0.0                           # PE and LOD columns off
+    md = oracle.Model(64, 64, 6, 4, 4, 16, 16, 1 / 16, 1 / 16, g0, g1, w, case.k_in)
+    xym = np.array([[x, y, m] for m in range(md.mips) for x in range(0, 64 >> m, 3)
+                    for y in range(0, 64 >> m, 5)], np.int32)
+    out = md.decode_xym(xym)
+    X = np.zeros(case.k_in)
+    X[:4], X[4:8] = 0.25, -0.125
+    h1 = np.maximum(w[0] @ X + w[1], 0)
+    h2 = np.maximum(w[2] @ h1 + w[3], 0)
+    ref = 1 / (1 + np.exp(-(w[4] @ h2 + w[5])))
+    assert np.abs(out - ref[None, :]).max() < 1e-14
+
+
+def test_query_mapping_nearest():
+    case = make_case(64, 64, 3, 4, 4, seed=8)
+    md = case.oracle_model()
+    xym = np.array([[5, 7, 0], [31, 0, 1], [0, 15, 2], [0, 0, 6]], np.int32)
+    ref = md.decode_xym(xym)
+    uvl = oracle.uvl_of_xym(xym, 64, 64)
+    assert np.array_equal(md.decode(uvl), ref)
+    # anywhere inside the texel maps to it
+    off = uvl.copy()
+    off[:, 0] += np.float32(0.49) / np.maximum(1, 64 >> xym[:, 2])
+    assert np.array_equal(md.decode(off), ref)
+    # clamps: u = 1 -> last texel, lod beyond the chain -> last mip, NaN -> 0
+    q = np.array([[1.0, 1.0, 0.0], [0.5, 0.5, 99.0], [np.nan, 0.0, np.nan]], np.float32)
+    got = md.decode(q)
+    exp = md.decode_xym(np.array([[63, 63, 0], [0, 0, 6], [0, 0, 0]], np.int32))
+    assert np.array_equal(got, exp)
+
+
+def test_trilinear_reduces_to_nearest_at_texel_centres():
+    case = make_case(64, 64, 3, 4, 4, seed=9)
+    md = case.oracle_model()
+    xym = np.array([[5, 7, 0], [31, 2, 1], [3, 3, 3], [0, 0, 6]], np.int32)
+    uvl = oracle.uvl_of_xym(xym, 64, 64)
+    assert np.abs(md.decode_trilinear(uvl) - md.decode_xym(xym)).max() < 1e-15
+    # half way between two mips: the mean of the two bilinear results
+    u = np.array([[0.3, 0.6, 2.5]], np.float32)
+    lo = md.decode_trilinear(np.array([[0.3, 0.6, 2.0]], np.float32))
+    hi = md.decode_trilinear(np.array([[0.3, 0.6, 3.0]], np.float32))
+    assert np.abs(md.decode_trilinear(u) - 0.5 * (lo + hi)).max() < 1e-12
+
+
+# ------------------------------------------------------------- gradients ---
+def _flat_params(md):
+    return md.grids0 + md.grids1 + md.weights
+
+
+@pytest.mark.parametrize("act", [1, 0])
+def test_gradients_match_central_differences(act):
+    """Reverse-mode gradients vs central differences (h = 1e-6) on a tiny
+    material with the simulated-quantisation noise switched on."""
+    case = make_case(16, 16, 3, 2, 2, k_in=32, hidden=8, act=act, seed=10, wgain=2.0)
+    md = case.oracle_model(quantized=False)
+    rng = np.random.default_rng(1)
+    xym = np.array([[rng.integers(0, 16 >> m), rng.integers(0, 16 >> m), m]
+                    for m in rng.integers(0, md.mips, size=24)], np.int32)
+    target = rng.random((24, 3))
+    noise = (99, 4)
+    loss, g = md.loss_grad_xym(xym, target, noise=noise)
+    grads = g["grid0"] + g["grid1"] + g["w"]
+    params = _flat_params(md)
+    h = 1e-6
+    for p, gp in zip(params, grads):
+        flat, gflat = p.reshape(-1), gp.reshape(-1)
+        num = np.zeros(min(flat.size, 40))
+        picks = rng.choice(flat.size, size=num.size, replace=False)
+        for i, k in enumerate(picks):
+            old = flat[k]
+            flat[k] = old + h
+            lp, _ = md.loss_grad_xym(xym, target, noise=noise)
+            flat[k] = old - h
+            lm, _ = md.loss_grad_xym(xym, target, noise=noise)
+            flat[k] = old
+            num[i] = (lp - lm) / (2 * h)
+        ana = gflat[picks]
+        err = np.linalg.norm(ana - num) / max(np.linalg.norm(num), 1e-30)
+        assert err < 1e-6, (p.shape, err)
+    assert loss > 0
+
+
+def test_backward_is_vector_jacobian_product():
+    """Backward of dout equals the directional derivative <dout, dy/dtheta>."""
+    case = make_case(32, 32, 4, 4, 4, hidden=16, act=1, seed=12)
+    md = case.oracle_model(quantized=False)
+    rng = np.random.default_rng(2)
+    xym = np.array([[rng.integers(0, 32 >> m), rng.integers(0, 32 >> m), m]
+                    for m in rng.integers(0, md.mips, size=10)], np.int32)
+    dout = rng.standard_normal((10, 4))
+    g = md.backward_xym(xym, dout)
+    params = _flat_params(md)
+    grads = g["grid0"] + g["grid1"] + g["w"]
+    direction = [rng.standard_normal(p.shape) for p in params]
+    h = 1e-6
+    for p, d in zip(params, direction):
+        p += h * d
+    yp = md.decode_xym(xym)
+    for p, d in zip(params, direction):
+        p -= 2 * h * d
+    ym = md.decode_xym(xym)
+    for p, d in zip(params, direction):
+        p += h * d
+    num = np.sum(dout * (yp - ym)) / (2 * h)
+    ana = sum(np.sum(gr * d) for gr, d in zip(grads, direction))
+    assert abs(num - ana) <= 1e-6 * abs(num)
+
+
+# ------------------------------------------------------------- optimiser ---
+def test_adam_matches_torch():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(3)
+    p = rng.standard_normal(50)
+    m, v = np.zeros(50), np.zeros(50)
+    tp = torch.tensor(p.copy(), requires_grad=True)
+    opt = torch.optim.Adam([tp], lr=0.01, betas=(0.9, 0.999), eps=1e-8)
+    for t in range(6):
+        g = rng.standard_normal(50)
+        oracle.adam(p, m, v, g, 0.01, t)
+        tp.grad = torch.tensor(g)
+        opt.step()
+        assert np.abs(p - tp.detach().numpy()).max() < 1e-14
+
+
+def test_adam_first_step_is_sign_and_clamps():
+    p = np.array([0.0, 0.0, 0.45, -0.45])
+    g = np.array([3.0, -0.2, -1.0, 1.0])
+    oracle.adam(p, np.zeros(4), np.zeros(4), g, 0.1, 0, clamp=(-7.5 / 16, 0.5))
+    assert np.allclose(p, [-0.1, 0.1, 0.5, -7.5 / 16], atol=1e-7)
+
+
+def test_cosine_lr():
+    assert oracle.cosine_lr(0.01, 0, 100) == 0.01
+    assert abs(oracle.cosine_lr(0.01, 50, 100) - 0.005) < 1e-18
+    assert abs(oracle.cosine_lr(0.01, 100, 100)) < 1e-18
+
+
+# ---------------------------------------------------------------- metric ---
+def test_texture_set_psnr_eq1():
+    ref = [np.zeros((4, 4, 1)), np.zeros((2, 2, 1))]
+    test = [np.full((4, 4, 1), 0.1), np.full((2, 2, 1), 0.2)]
+    # (16 * 0.01 + 4 * 0.04) / 20 = 0.016
+    assert abs(oracle.texture_set_psnr(ref, test) - (-10 * math.log10(0.016))) < 1e-12
