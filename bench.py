@@ -1,0 +1,459 @@
+#!/usr/bin/env python
+"""Benchmark of the NTC hot path on one GB300 (replicas on N GPUs).
+
+One step = one pass of the whole hot path over synthetic inputs shaped like
+the paper's workloads:
+  * random-access decode of a 4096^2 x 16-channel material (13 mips,
+    G0 1024^2 x 12, G1 512^2 x 12 at 4 bits, MLP 48-64-64-16) at 2^24
+    queries with (u, v) uniform in [0,1)^2 and an integer LOD uniform over
+    0..12 -> the headline `value`, decoded texels/s;
+  * one optimisation step (sampler, noise, forward, L2 loss, backward,
+    Adam) of a 2048^2 x 12-channel material (G0 512^2 x 16, G1 256^2 x 16,
+    MLP 48-64-64-12) on 2^18 training texels -> `train_samples_per_s`.
+The decode pass streams 0.74 GB (> L2) between training steps, so every
+training step starts with a cold L2.
+
+Prints ONE JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import ntc_inputs as gen  # noqa: E402
+
+METRIC = "decoded texels/s & train samples/s (fwd+bwd), % tensor peak, vs FP32 path"
+DEC_SIDE, DEC_C, DEC_C0, DEC_K = 4096, 16, 12, 48
+TRN_SIDE, TRN_C, TRN_C0, TRN_K = 2048, 12, 16, 48
+MAX_SM_MHZ = 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "f32", "f16", "f8"])
+    ap.add_argument("--queries", type=int, default=1 << 24)
+    ap.add_argument("--batch", type=int, default=1 << 18)
+    ap.add_argument("--cpu-seconds", type=float, default=8.0,
+                    help="target CPU time of each oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp32-compare", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------
+# distributed plumbing (replicas: no data-path collective)
+# ----------------------------------------------------------------------------
+def dist_init(args):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return rank, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index, self.samples, self.proc = index, [], None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 6:
+                self.samples.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return None
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4)
+                          if s[2 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+# ----------------------------------------------------------------------------
+# workloads
+# ----------------------------------------------------------------------------
+def decode_shapes():
+    import paper_2305_17105_gb300 as ntc
+    return ntc.pyramid(DEC_SIDE, DEC_SIDE)
+
+
+def make_decode_material(precision, device="cuda"):
+    """4096^2 x 16 material: random 4-bit grids (packed on the device by the
+    library's quantiser) and random MLP weights of the requested precision.
+    Returns (Material, host float grid values, host weights)."""
+    import torch
+    import paper_2305_17105_gb300 as ntc
+    rng = np.random.default_rng(1001)
+    n, q = 16, 1.0 / 16
+    lo, hi = -(n - 1) / 2 * q, n / 2 * q
+    g0h, g1h, g0, g1 = [], [], [], []
+    for (w0, h0), (w1, h1) in decode_shapes():
+        a = gen.uniform_grid_values((h0, w0, DEC_C0), lo, hi, rng)
+        b = gen.uniform_grid_values((h1, w1, DEC_C0), lo, hi, rng)
+        g0h.append(a)
+        g1h.append(b)
+        for src, dst in ((a, g0), (b, g1)):
+            t = torch.from_numpy(src).to(device)
+            p = ntc.ntc_quantize_pack(t, DEC_C0, 4, q)
+            dst.append(p.view(src.shape[0], src.shape[1], -1))
+    w = gen.random_mlp(DEC_K, 64, DEC_C, seed=2001, n_used=2 * DEC_C0 + 13)
+    wt = {"f32": torch.float32, "f16": torch.float16}
+    prec = {"f32": ntc.PREC_F32, "f16": ntc.PREC_F16, "f8": ntc.PREC_F8}[precision]
+    scale = None
+    if precision == "f8":
+        ws, dev_w = [], []
+        for l in (0, 2, 4):
+            s = float(np.abs(w[l]).max()) / 448.0
+            ws.append(s)
+            q8 = torch.from_numpy(w[l] / s).to(device).to(torch.float8_e4m3fn)
+            dev_w.append(q8.view(torch.uint8))
+        scale = torch.tensor(ws + [1.0, 1.0, 1.0], dtype=torch.float32, device=device)
+    else:
+        dev_w = [torch.from_numpy(w[l]).to(device).to(wt[precision]) for l in (0, 2, 4)]
+    dev_b = [torch.from_numpy(w[l]).to(device) for l in (1, 3, 5)]
+    k_in = DEC_K if precision != "f8" else 64
+    if k_in != DEC_K:
+        dev_w[0] = torch.nn.functional.pad(dev_w[0], (0, k_in - DEC_K))
+    mat = ntc.Material(DEC_SIDE, DEC_SIDE, DEC_C, DEC_C0, DEC_C0, 4, 4, q, q, g0, g1, dev_w, dev_b,
+                       k_in, prec, scale=scale)
+    return mat, (g0h, g1h), w
+
+
+def make_trainer(precision, total_steps, device="cuda"):
+    import paper_2305_17105_gb300 as ntc
+    tex = gen.synthetic_texture(TRN_SIDE, TRN_SIDE, TRN_C, seed=1002)
+    chain = gen.box_mip_chain_u8(tex)
+    rng = np.random.default_rng(1003)
+    n, q = 16, 1.0 / 16
+    lo, hi = -(n - 1) / 2 * q, n / 2 * q
+    g0, g1 = [], []
+    for (w0, h0), (w1, h1) in ntc.pyramid(TRN_SIDE, TRN_SIDE):
+        g0.append(gen.uniform_grid_values((h0, w0, TRN_C0), lo, hi, rng))
+        g1.append(gen.uniform_grid_values((h1, w1, TRN_C0), lo, hi, rng))
+    w = gen.random_mlp(TRN_K, 64, TRN_C, seed=2002, n_used=2 * TRN_C0 + 13)
+    prec = {"f32": ntc.PREC_F32, "f16": ntc.PREC_F16}[precision]
+    tr = ntc.Trainer(TRN_SIDE, TRN_SIDE, TRN_C, TRN_C0, TRN_C0, 4, 4, q, q, g0, g1,
+                     [w[0], w[2], w[4]], [w[1], w[3], w[5]], TRN_K, prec,
+                     total_steps=total_steps, device=device)
+    return tr, ntc.Target(chain, device=device), chain, (g0, g1), w
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle baseline (bounded samples)
+# ----------------------------------------------------------------------------
+def oracle_decode_rate(grids_host, weights, queries, seconds):
+    """Decoded texels/s of the FP64 oracle on the host cores, on a prefix of
+    the decode workload sized to about `seconds` of work."""
+    import oracle
+    q = 1.0 / 16
+    g0 = [oracle.dequantize(oracle.quantize(a.astype(np.float64), 16, q), 16, q)
+          for a in grids_host[0]]
+    g1 = [oracle.dequantize(oracle.quantize(a.astype(np.float64), 16, q), 16, q)
+          for a in grids_host[1]]
+    md = oracle.Model(DEC_SIDE, DEC_SIDE, DEC_C, DEC_C0, DEC_C0, 16, 16, q, q, g0, g1, weights, DEC_K)
+    threads = oracle.default_threads()
+    n = 4096
+    t0 = time.perf_counter()
+    md.decode(queries[:n], threads=threads)
+    dt = time.perf_counter() - t0
+    n = int(min(len(queries), max(n, n * seconds / max(dt, 1e-6))))
+    t0 = time.perf_counter()
+    md.decode(queries[:n], threads=threads)
+    dt = time.perf_counter() - t0
+    return n / dt, n, threads, dt
+
+
+def oracle_train_rate(chain, grids_host, weights, batch, seconds):
+    import oracle
+    q = 1.0 / 16
+    md = oracle.Model(TRN_SIDE, TRN_SIDE, TRN_C, TRN_C0, TRN_C0, 16, 16, q, q,
+                      [g.astype(np.float64) for g in grids_host[0]],
+                      [g.astype(np.float64) for g in grids_host[1]], weights, TRN_K)
+    threads = min(oracle.default_threads(), 8)  # one private FP64 gradient copy per thread
+    n = 2048
+    xym = oracle.sample_batch(7, 0, batch, TRN_SIDE, TRN_SIDE, md.mips)
+    t = oracle.targets_of_xym(chain, xym)
+    t0 = time.perf_counter()
+    md.loss_grad_xym(xym[:n], t[:n], noise=(7, 0), threads=threads)
+    dt = time.perf_counter() - t0
+    n = int(min(batch, max(n, n * seconds / max(dt, 1e-6))))
+    t0 = time.perf_counter()
+    md.loss_grad_xym(xym[:n], t[:n], noise=(7, 0), threads=threads)
+    dt = time.perf_counter() - t0
+    return n / dt, n, threads, dt
+
+
+# ----------------------------------------------------------------------------
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    # the oracle needs the material only; build it on the host
+    rng = np.random.default_rng(1001)
+    n, q = 16, 1.0 / 16
+    lo, hi = -(n - 1) / 2 * q, n / 2 * q
+    import oracle
+    g0, g1 = [], []
+    for (w0, h0), (w1, h1) in oracle.pyramid(DEC_SIDE, DEC_SIDE):
+        g0.append(gen.uniform_grid_values((h0, w0, DEC_C0), lo, hi, rng))
+        g1.append(gen.uniform_grid_values((h1, w1, DEC_C0), lo, hi, rng))
+    w = gen.random_mlp(DEC_K, 64, DEC_C, seed=2001, n_used=2 * DEC_C0 + 13)
+    queries = gen.random_queries(args.queries, 13, seed=4001)
+    times, rates = [], []
+    for i in range(args.warmup + args.steps):
+        rate, ns, threads, dt = oracle_decode_rate((g0, g1), w, queries, args.cpu_seconds / 4)
+        if i >= args.warmup:
+            rates.append(rate)
+            times.append(dt)
+    value = statistics.median(rates)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "texels/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * statistics.median(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "decode 4096^2x16 material, 2^24 random (u,v,lod) queries "
+                                   "(bounded prefix per step)", "queries_per_step": ns},
+            "cpu_baseline": {"value": value, "unit": "texels/s", "cores": threads, "kind": "oracle",
+                             "sample": f"first {ns} of the 2^24 decode queries per step"},
+            "e2e": {"value": value, "unit": "texels/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import paper_2305_17105_gb300 as ntc
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    rank, world = dist_init(args)
+    ntc.lib()
+    precision = args.precision
+    if precision == "auto":
+        precision = os.environ.get("NTC_BENCH_PRECISION", "f16")
+    train_prec = "f16" if precision in ("f16", "f8") else "f32"
+    dev = "cuda"
+    stream = torch.cuda.current_stream()
+
+    # ---- inputs resident in HBM -------------------------------------------
+    mat, grids_host, w_host = make_decode_material(precision)
+    queries = gen.random_queries(args.queries, 13, seed=4001 + rank)
+    q_host = torch.from_numpy(queries).pin_memory()
+    q_dev = q_host.to(dev)
+    out = torch.empty((args.queries, DEC_C), dtype=torch.float16, device=dev)
+    total = args.warmup + args.steps + 8
+    tr, target, chain, tgrids, tw = make_trainer(train_prec, total)
+    seed = 77 + rank
+
+    def decode():
+        ntc.ntc_decode(mat, q_dev, out=out)
+
+    def train():
+        ntc.ntc_train_step(tr, target, args.batch, seed)
+
+    for _ in range(args.warmup):
+        decode()
+        train()
+    torch.cuda.synchronize()
+
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        t_wall = time.perf_counter()
+        for s in range(args.steps):
+            ev[s][0].record(stream)
+            decode()
+            ev[s][1].record(stream)
+            train()
+            ev[s][2].record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        t_wall = time.perf_counter() - t_wall
+    dec_ms = [a.elapsed_time(b) for a, b, _ in ev]
+    trn_ms = [b.elapsed_time(c) for _, b, c in ev]
+    step_ms = [a.elapsed_time(c) for a, _, c in ev]
+    total_ms = max_over_ranks(sum(step_ms), world)
+    dec_total = max_over_ranks(sum(dec_ms), world)
+    trn_total = max_over_ranks(sum(trn_ms), world)
+    value = world * args.queries * args.steps / (dec_total / 1e3)
+    train_rate = world * args.batch * args.steps / (trn_total / 1e3)
+    loss = float(tr.loss.item())
+
+    # ---- roofline of the decode kernel (one launch per decode call) -------
+    flop_per_q = 2 * (DEC_K * 64 + 64 * 64 + 64 * DEC_C)
+    dec_avg_s = statistics.mean(dec_ms) / 1e3
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    if precision == "f32":
+        sm_mhz = MAX_SM_MHZ
+        peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": flop_per_q * args.queries / dec_avg_s / 1e12,
+                "peak": peak, "unit": "TFLOP/s", "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
+    else:
+        bf16 = peaks.get("bf16_tflops", 1900.0)
+        peak = bf16 * (2.0 if precision == "f8" else 1.0)
+        roof = {"bound": "tensor", "achieved": flop_per_q * args.queries / dec_avg_s / 1e12,
+                "peak": peak, "unit": "TFLOP/s",
+                "peak_source": "measured bf16 burst" + (" x 2 (fp8 nominal ratio)" if precision == "f8" else "")}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    dec_bytes = args.queries * (12 + DEC_C * 2)
+    hbm = peaks.get("hbm_gbs", 6773.2)
+    roof["hbm_gbs_algorithmic"] = dec_bytes / dec_avg_s / 1e9
+    roof["hbm_frac"] = roof["hbm_gbs_algorithmic"] / hbm
+    roof["kernel"] = "decode"
+
+    # ---- end to end through the public API with host buffers --------------
+    e2e = None
+    if not args.no_e2e:
+        out_host = torch.empty((args.queries, DEC_C), dtype=torch.float16).pin_memory()
+        barrier(world)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            qd = q_host.to(dev, non_blocking=True)
+            o = ntc.ntc_decode(mat, qd, out_dtype=torch.float16)
+            out_host.copy_(o, non_blocking=True)
+            ntc.ntc_train_step(tr, target, args.batch, seed)
+            _ = tr.loss.to("cpu", non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = max_over_ranks(e0.elapsed_time(e1), world)
+        e2e = {"value": world * args.queries * args.steps / (e2e_ms / 1e3), "unit": "texels/s",
+               "h2d_bytes_per_step": int(args.queries * 12),
+               "d2h_bytes_per_step": int(args.queries * DEC_C * 2 + 4)}
+
+    # ---- the plain FP32 CUDA-core form on the same inputs ------------------
+    fp32 = None
+    if precision != "f32" and not args.no_fp32_compare:
+        mat32 = mat.with_(weights=[w.float() if w.dtype == torch.float16 else w for w in mat.weights],
+                          precision=ntc.PREC_F32) if precision == "f16" else None
+        if mat32 is not None:
+            for _ in range(2):
+                ntc.ntc_decode(mat32, q_dev, out=out)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(3):
+                ntc.ntc_decode(mat32, q_dev, out=out)
+            b.record(stream)
+            torch.cuda.synchronize()
+            fp32 = {"decode_texels_per_s": 3 * args.queries / (a.elapsed_time(b) / 1e3)}
+            fp32["speedup"] = value / world / fp32["decode_texels_per_s"]
+
+    # ---- CPU oracle baseline (rank 0, N = 1) --------------------------------
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, ns, threads, dt = oracle_decode_rate(grids_host, w_host, queries, args.cpu_seconds)
+        trate, tn, tthreads, tdt = oracle_train_rate(chain, tgrids, tw, args.batch, args.cpu_seconds)
+        cpu = {"value": rate, "unit": "texels/s", "cores": threads, "kind": "oracle",
+               "sample": f"first {ns} of the 2^24 decode queries ({dt:.1f} s)",
+               "train_samples_per_s": trate, "train_cores": tthreads,
+               "train_sample": f"first {tn} of the 2^18 training texels ({tdt:.1f} s)"}
+
+    kernels_per_step = 1 + 3  # decode; train: fused fwd/bwd, Adam, step counter
+    line = {
+        "metric": METRIC, "value": value, "unit": "texels/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"f32": "f32", "f16": "f16", "f8": "e4m3"}[precision], "data": "synthetic",
+        "config": {"workload": "decode 4096^2x16 (13 mips, G0 1024^2x12 + G1 512^2x12 @4b, "
+                               "MLP 48-64-64-16), 2^24 random (u,v,lod) queries + one train step "
+                               "2048^2x12 (G0 512^2x16, G1 256^2x16 FP32, MLP 48-64-64-12), "
+                               "2^18 texels", "queries": args.queries, "train_batch": args.batch,
+                   "decode_precision": precision, "train_precision": train_prec,
+                   "l2": "inputs larger than L2 (0.74 GB streamed per decode pass)",
+                   "parallelism": f"replicas x{world}"},
+        "train_samples_per_s": train_rate, "train_loss": loss,
+        "decode_ms": statistics.median(dec_ms), "train_ms": statistics.median(trn_ms),
+        "roofline": roof, "e2e": e2e, "fp32_path": fp32, "cpu_baseline": cpu,
+        "gpu_launches": kernels_per_step * args.steps,
+        "clocks": clk.summary(), "wall_s": t_wall,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,237 @@
+/*
+ * ntc.h -- C ABI of the GB300 neural-texture-compression library (libntc.so).
+ *
+ * The library implements the data-parallel hot path of "Random-Access Neural
+ * Compression of Material Textures" (Vaidyanathan et al., 2023): the
+ * per-texel random-access decode (Sec. 4.3-4.4, Sec. 5.2) and the per-material
+ * fused forward+backward optimisation that compresses a material (Sec. 4.2,
+ * 4.5, 5.1), as hand-written CUDA for sm_103a.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every array argument is a DEVICE pointer owned by the caller unless the
+ *    parameter says "host".  The library never allocates or frees device
+ *    memory and never synchronises the device; all work is enqueued on the
+ *    caller's `stream` (a cudaStream_t passed as void*; NULL = legacy default
+ *    stream) in launch order.
+ *  - Structs (ntc_material, ntc_grads, ntc_trainer, ntc_target) are passed by
+ *    HOST pointer; their fields point to device memory.  They are read during
+ *    the call only; the call does not keep them.
+ *  - Every call returns an ntc_status.  On failure nothing was enqueued
+ *    (argument errors) or the CUDA launch error is reported (NTC_ERR_CUDA);
+ *    ntc_last_error() returns a thread-local human-readable message.  No C++
+ *    exception crosses this boundary.
+ *  - Device arrays must be 16-byte aligned (NTC_ERR_ALIGN otherwise).
+ *  - Calls on one stream are ordered; calls that write the same memory from
+ *    different streams race.
+ */
+#ifndef NTC_H
+#define NTC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NTC_MAX_LEVELS 8    /* feature levels F^j (Sec. 4.1) */
+#define NTC_MAX_MIPS 16     /* mip levels: textures up to 32768^2 */
+#define NTC_MAX_CHANNELS 16 /* texture-set channels c (Sec. 4) */
+#define NTC_MAX_FEATURES 32 /* c0 + c1 latent features per query */
+#define NTC_MAX_K 128       /* padded MLP input width */
+#define NTC_HIDDEN 64       /* hidden width of the decoder MLP (Sec. 4.4) */
+
+typedef enum {
+  NTC_OK = 0,
+  NTC_ERR_ARG = 1,         /* null pointer, negative size, bad enum value */
+  NTC_ERR_SHAPE = 2,       /* sizes violate the pyramid / MLP shape rules */
+  NTC_ERR_ALIGN = 3,       /* a device pointer is not 16-byte aligned */
+  NTC_ERR_UNSUPPORTED = 4, /* a valid combination this build does not implement */
+  NTC_ERR_CUDA = 5,        /* a CUDA launch or API call failed */
+  NTC_ERR_TIMEOUT = 6      /* a bounded device-side wait gave up (status word) */
+} ntc_status;
+
+/* Latent grid storage. */
+enum {
+  NTC_GRID_PACKED = 0, /* B-bit quantisation indices, one power-of-two-sized cell
+                          per grid position (see ntc_cell_bytes) */
+  NTC_GRID_F32 = 1     /* float32 values [g_h][g_w][c] (training form) */
+};
+/* Arithmetic of the decoder MLP. */
+enum {
+  NTC_PREC_F32 = 0, /* FP32 CUDA-core form: weights float32 */
+  NTC_PREC_F16 = 1, /* tcgen05 tensor-core form: weights float16, FP32 accumulation */
+  NTC_PREC_F8 = 2   /* tcgen05 tensor-core form: weights FP8-E4M3 with per-layer scales */
+};
+enum { NTC_ACT_RELU = 0, NTC_ACT_HARDGELU = 1 };   /* hidden activation (Sec. 4.4) */
+enum { NTC_OUT_SIGMOID = 0, NTC_OUT_IDENTITY = 1 }; /* output activation */
+enum { NTC_FILTER_NEAREST = 0, NTC_FILTER_TRILINEAR = 1 }; /* Sec. 5.3 */
+enum { NTC_DTYPE_F32 = 0, NTC_DTYPE_F16 = 1 };              /* output element type */
+
+/* Flags of ntc_decode / ntc_backward / ntc_train_step. */
+#define NTC_FLAG_NOISE 0x1        /* add simulated-quantisation noise (Sec. 4.2); F32 grids */
+#define NTC_FLAG_FREEZE_GRIDS 0x2 /* train_step: grids fixed (Sec. 4.2 final phase) */
+#define NTC_FLAG_NO_NOISE 0x4     /* train_step: no noise while grids still train */
+#define NTC_FLAG_SIMT 0x8         /* force the FP32 CUDA-core kernels (any precision
+                                     is converted to FP32 on load) */
+
+/* One feature level F^j = (G^j_0, G^j_1) (Sec. 4.1, Table 1). */
+typedef struct {
+  int32_t g0_w, g0_h; /* G0 resolution */
+  int32_t g1_w, g1_h; /* G1 resolution */
+  const void* grid0;  /* PACKED: [g0_h][g0_w] cells of ntc_cell_bytes(c0,bits0) bytes;
+                         F32: float [g0_h][g0_w][c0] */
+  const void* grid1;  /* likewise with c1, bits1 */
+} ntc_level;
+
+/* A compressed material: feature pyramid + decoder (Sec. 4). */
+typedef struct {
+  int32_t width, height; /* mip-0 texture-set resolution w x h, powers of two */
+  int32_t channels;      /* c, decoder outputs, 1..NTC_MAX_CHANNELS */
+  int32_t mips;          /* M = log2(max(w, h)) + 1 */
+  int32_t levels;        /* feature levels L, 1..NTC_MAX_LEVELS */
+  int32_t c0, c1;        /* features per cell of G0 / G1; c0 + c1 <= NTC_MAX_FEATURES */
+  int32_t bits0, bits1;  /* quantisation bits B_k in {1,2,4,8}: N_k = 2^B_k levels */
+  float q0, q1;          /* bin width Q_k: level values (k - (N/2-1)) * Q (Sec. 4.2) */
+  int32_t encoding;      /* NTC_GRID_PACKED | NTC_GRID_F32 */
+  int32_t k_in;          /* MLP input width: >= c0 + c1 + 13, multiple of 16
+                            (of 32 for NTC_PREC_F8), <= NTC_MAX_K */
+  int32_t hidden;        /* must be NTC_HIDDEN */
+  int32_t act;           /* NTC_ACT_* */
+  int32_t out_act;       /* NTC_OUT_* */
+  int32_t precision;     /* NTC_PREC_* */
+  ntc_level lv[NTC_MAX_LEVELS];
+  const void* w[3];      /* layer weights [out][in]: W1 [hidden][k_in], W2 [hidden][hidden],
+                            W3 [channels][hidden]; float / half / e4m3 by precision */
+  const float* b[3];     /* biases, float32 [out] */
+  const float* scale;    /* NTC_PREC_F8 only: 6 device floats, weight scales s_w[3]
+                            then input-activation scales s_a[3]; layer l computes
+                            (s_w[l]*s_a[l]) * (W8 . q8(x / s_a[l])) + b.  NULL otherwise */
+} ntc_material;
+
+/* Gradient outputs of ntc_backward, ACCUMULATED (+=) in float32, same
+ * layouts as the F32 grids and the weights. */
+typedef struct {
+  float* grid0[NTC_MAX_LEVELS];
+  float* grid1[NTC_MAX_LEVELS];
+  float* w[3];
+  float* b[3];
+} ntc_grads;
+
+/* Optimiser state of ntc_train_step (Sec. 5.1: Adam, two learning rates,
+ * cosine annealing).  `params` is one float32 array holding every trainable
+ * tensor; the material passed to ntc_train_step must point its F32 grids and
+ * its biases into it, and w_master[l] gives the FP32 master of W_l inside it
+ * (for NTC_PREC_F32 the material's w[l] must equal w_master[l]; for F16 the
+ * step rewrites the material's half copies from the masters after each
+ * update).  adam_m, adam_v and grad have params' length; grad is scratch that
+ * every step leaves zeroed (initialise it to zero once). */
+typedef struct {
+  float* params;
+  float* adam_m;
+  float* adam_v;
+  float* grad;
+  int64_t n_params;
+  float* w_master[3];
+  int64_t* step;        /* device int64: 0-based index of the next step; the step
+                           reads it and increments it on the device */
+  int64_t total_steps;  /* T of the cosine schedule lr_t = lr0 (1 + cos(pi t / T)) / 2 */
+  float lr_grid;        /* 0.01 in the paper */
+  float lr_mlp;         /* 0.005 in the paper */
+  float beta1, beta2, eps;
+} ntc_trainer;
+
+/* Reference texture set: the 8-bit mip chain, texel values q/255. */
+typedef struct {
+  const uint8_t* texels;           /* device */
+  int64_t offset[NTC_MAX_MIPS];    /* byte offset of mip m: [h_m][w_m][channels] u8 */
+} ntc_target;
+
+/* Library version string (static storage). */
+const char* ntc_version(void);
+
+/* Message of the last failing call on this thread (static, thread-local). */
+const char* ntc_last_error(void);
+
+/* Bytes of one packed grid cell for c features of `bits` bits: c*bits bits
+ * rounded up to a power-of-two number of bytes.  Channel ch occupies bits
+ * [ch*bits, (ch+1)*bits) counting from bit 0 of byte 0.  0 on bad input. */
+int32_t ntc_cell_bytes(int32_t c, int32_t bits);
+
+/* Feature pyramid of a w x h texture set (Sec. 4.1, Table 1): G0 of level j
+ * is (w >> (2j+2), h >> (2j+2)) (each at least 1), G1 half of G0; levels
+ * continue while G0's longer side is at least 4.  Writes up to
+ * NTC_MAX_LEVELS entries into the HOST arrays and returns the level count
+ * (0 on bad input).  Mip m is served by level min(L-1, m < 4 ? 0 : (m-2)/2). */
+int32_t ntc_pyramid(int32_t width, int32_t height, int32_t* g0_w, int32_t* g0_h,
+                    int32_t* g1_w, int32_t* g1_h);
+
+/* Random-access decode (Sec. 4.3-4.4; filtering Sec. 5.3).
+ *  uvl  [n][3] float: u, v in [0,1) and the level of detail.  NEAREST: mip
+ *       m = floor(lod) clamped to [0, M-1], texel x = floor(u w_m) clamped to
+ *       [0, w_m - 1] (NaN -> 0).  TRILINEAR: lod is continuous; 2x2 texels
+ *       around (u, v) on mips floor(lod) and floor(lod)+1 (clamped), texel
+ *       taps wrap around, 8 decodes blended.
+ *  out  [n][channels] float32 or float16 (out_dtype), row-major.
+ *  flags NTC_FLAG_NOISE (F32 grids only: decode the noisy training grids of
+ *       (noise_seed, noise_step)), NTC_FLAG_SIMT.
+ * Decodes each query from the level of its mip: bilinear G0 and G1 features,
+ * 12 positional-encoding values, normalised LOD m/(M-1), zero padding, then
+ * the 3-layer MLP.  n == 0 is a no-op. */
+int ntc_decode(const ntc_material* m, const float* uvl, int64_t n, void* out,
+               int32_t out_dtype, int32_t filter, int32_t flags, uint64_t noise_seed,
+               int64_t noise_step, void* stream);
+
+/* Gradient of sum_i sum_c dout[i][c] * y[i][c] for nearest decodes y of the
+ * queries uvl (Sec. 4.5, reverse mode of ntc_decode), ACCUMULATED into g.
+ * Requires NTC_GRID_F32 grids.  With NTC_FLAG_NOISE the forward uses the
+ * noisy grids of (noise_seed, noise_step), whose noise passes gradients
+ * unchanged.  Activations are recomputed, never stored.  g fields may be
+ * NULL to skip that tensor (grid entries: per level). */
+int ntc_backward(const ntc_material* m, const float* uvl, int64_t n, const float* dout,
+                 const ntc_grads* g, int32_t flags, uint64_t noise_seed, int64_t noise_step,
+                 void* stream);
+
+/* One optimisation step of a material (Sec. 4.2, 4.5, 5.1), fully on the
+ * device: draw `batch` training texels (or use uvl_or_null [batch][3] texel
+ * queries), decode them with simulated-quantisation noise, L2 loss against the
+ * 8-bit reference t (mean over batch*channels, written to *loss_out, a device
+ * float), backward into tr->grad, then Adam with cosine-annealed learning
+ * rates lr_grid / lr_mlp, clamping of every grid to its quantisation range
+ * [-(N-1)/2 Q, N/2 Q], refresh of half-precision weight copies, and
+ * *tr->step += 1.  Sampling and noise are counter-based from (seed, *step),
+ * so the call is CUDA-graph capturable and replays identically.
+ * flags: NTC_FLAG_FREEZE_GRIDS (no noise, grids neither differentiated nor
+ * updated), NTC_FLAG_NO_NOISE, NTC_FLAG_SIMT. */
+int ntc_train_step(const ntc_material* m, const ntc_trainer* tr, const ntc_target* t,
+                   int64_t batch, uint64_t seed, const float* uvl_or_null, float* loss_out,
+                   int32_t flags, void* stream);
+
+/* Final quantisation (Sec. 4.2): for `cells` cells of c float32 values,
+ * index q = clamp(rint(x / Q) + N/2 - 1, 0, N-1) (ties to even), packed into
+ * packed_out ([cells][ntc_cell_bytes(c, bits)], may be NULL) and, if
+ * snapped_out is not NULL, the level value (q - (N/2-1)) Q written back as
+ * float32 (may alias `values`). */
+int ntc_quantize_pack(const float* values, int64_t cells, int32_t c, int32_t bits, float q,
+                      uint8_t* packed_out, float* snapped_out, void* stream);
+
+/* Inverse of the packing: indices (int32 [cells][c], may be NULL) and/or
+ * level values (float32 [cells][c], may be NULL). */
+int ntc_unpack(const uint8_t* packed, int64_t cells, int32_t c, int32_t bits, float q,
+               int32_t* idx_out, float* values_out, void* stream);
+
+/* The training-texel sampler of ntc_train_step (Sec. 5.1), exposed for
+ * testing: [batch][3] int32 rows (x, y, m) of step `step`. */
+int ntc_sample_batch(uint64_t seed, int64_t step, int64_t batch, int32_t width,
+                     int32_t height, int32_t mips, int32_t* xym_out, void* stream);
+
+/* The MLP input rows of nearest decodes (Sec. 4.3), exposed for testing:
+ * float32 [n][k_in]. */
+int ntc_sample_features(const ntc_material* m, const float* uvl, int64_t n, float* rows_out,
+                        int32_t flags, uint64_t noise_seed, int64_t noise_step, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NTC_H */

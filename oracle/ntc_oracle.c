@@ -128,14 +128,19 @@ uint64_t or_rng(uint64_t seed, uint64_t stream, uint64_t counter) {
   return splitmix64(key ^ counter);
 }
 
-/* Uniform noise in [-Q/2, Q/2) for one latent value (Sec. 4.2): one draw per
- * (step, feature level, grid, cell, channel); the stream of step s is 2s+1. */
+/* Uniform noise in [-Q/2, Q/2) for one latent value (Sec. 4.2).  Reading:
+ * one value per (step, feature level, grid, cell, channel).  One 64-bit draw
+ * serves a channel pair: counter = (2*level + grid) << 40 | (cell *
+ * ceil(c/2) + ch/2) on stream 2*step + 1; even channels take draw bits
+ * 40..63, odd channels bits 16..39, as a 24-bit fraction u; noise (u-1/2) Q. */
 double or_noise_value(uint64_t seed, int64_t step, int level, int grid, int64_t cell,
                       int ch, int c, double q) {
   uint64_t stream = ((uint64_t)step << 1) | 1u;
-  uint64_t counter = ((uint64_t)(2 * level + grid) << 40) | (uint64_t)(cell * c + ch);
+  uint64_t pairs = (uint64_t)((c + 1) / 2);
+  uint64_t counter = ((uint64_t)(2 * level + grid) << 40) | ((uint64_t)cell * pairs + (uint64_t)(ch / 2));
   uint64_t h = or_rng(seed, stream, counter);
-  double u = (double)(h >> 40) * (1.0 / 16777216.0);
+  uint64_t bits24 = (ch & 1) ? ((h >> 16) & 0xFFFFFFULL) : (h >> 40);
+  double u = (double)bits24 * (1.0 / 16777216.0);
   return (u - 0.5) * q;
 }
 

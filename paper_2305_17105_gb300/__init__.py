@@ -1,0 +1,433 @@
+"""GB300 neural texture compression: Python binding of libntc.so.
+
+Thin argument marshalling over the C ABI declared in ``include/ntc.h`` (same
+function names).  PyTorch supplies device memory and streams; every step of
+the decode and of the optimisation runs in the library's CUDA kernels.  There
+is no CPU path: without the compiled library or a CUDA device the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libntc.so")
+
+MAX_LEVELS = 8
+MAX_MIPS = 16
+MAX_CHANNELS = 16
+MAX_K = 128
+HIDDEN = 64
+
+OK, ERR_ARG, ERR_SHAPE, ERR_ALIGN, ERR_UNSUPPORTED, ERR_CUDA, ERR_TIMEOUT = range(7)
+GRID_PACKED, GRID_F32 = 0, 1
+PREC_F32, PREC_F16, PREC_F8 = 0, 1, 2
+ACT_RELU, ACT_HARDGELU = 0, 1
+OUT_SIGMOID, OUT_IDENTITY = 0, 1
+FILTER_NEAREST, FILTER_TRILINEAR = 0, 1
+DTYPE_F32, DTYPE_F16 = 0, 1
+FLAG_NOISE, FLAG_FREEZE_GRIDS, FLAG_NO_NOISE, FLAG_SIMT = 0x1, 0x2, 0x4, 0x8
+
+
+class NTCError(RuntimeError):
+    def __init__(self, name, code, msg):
+        super().__init__(f"{name} failed with status {code}: {msg}")
+        self.code = code
+
+
+# ----------------------------------------------------------------------------
+# ctypes mirrors of include/ntc.h
+# ----------------------------------------------------------------------------
+class ntc_level(C.Structure):
+    _fields_ = [("g0_w", C.c_int32), ("g0_h", C.c_int32), ("g1_w", C.c_int32), ("g1_h", C.c_int32),
+                ("grid0", C.c_void_p), ("grid1", C.c_void_p)]
+
+
+class ntc_material(C.Structure):
+    _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("channels", C.c_int32),
+                ("mips", C.c_int32), ("levels", C.c_int32), ("c0", C.c_int32), ("c1", C.c_int32),
+                ("bits0", C.c_int32), ("bits1", C.c_int32), ("q0", C.c_float), ("q1", C.c_float),
+                ("encoding", C.c_int32), ("k_in", C.c_int32), ("hidden", C.c_int32),
+                ("act", C.c_int32), ("out_act", C.c_int32), ("precision", C.c_int32),
+                ("lv", ntc_level * MAX_LEVELS), ("w", C.c_void_p * 3), ("b", C.c_void_p * 3),
+                ("scale", C.c_void_p)]
+
+
+class ntc_grads(C.Structure):
+    _fields_ = [("grid0", C.c_void_p * MAX_LEVELS), ("grid1", C.c_void_p * MAX_LEVELS),
+                ("w", C.c_void_p * 3), ("b", C.c_void_p * 3)]
+
+
+class ntc_trainer(C.Structure):
+    _fields_ = [("params", C.c_void_p), ("adam_m", C.c_void_p), ("adam_v", C.c_void_p),
+                ("grad", C.c_void_p), ("n_params", C.c_int64), ("w_master", C.c_void_p * 3),
+                ("step", C.c_void_p), ("total_steps", C.c_int64), ("lr_grid", C.c_float),
+                ("lr_mlp", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float),
+                ("eps", C.c_float)]
+
+
+class ntc_target(C.Structure):
+    _fields_ = [("texels", C.c_void_p), ("offset", C.c_int64 * MAX_MIPS)]
+
+
+# name -> (restype, argtypes); every entry point of include/ntc.h
+_P, _I32, _I64, _U64, _F = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_float
+SIGNATURES = {
+    "ntc_version": (C.c_char_p, []),
+    "ntc_last_error": (C.c_char_p, []),
+    "ntc_cell_bytes": (_I32, [_I32, _I32]),
+    "ntc_pyramid": (_I32, [_I32, _I32, _P, _P, _P, _P]),
+    "ntc_decode": (C.c_int, [_P, _P, _I64, _P, _I32, _I32, _I32, _U64, _I64, _P]),
+    "ntc_backward": (C.c_int, [_P, _P, _I64, _P, _P, _I32, _U64, _I64, _P]),
+    "ntc_train_step": (C.c_int, [_P, _P, _P, _I64, _U64, _P, _P, _I32, _P]),
+    "ntc_quantize_pack": (C.c_int, [_P, _I64, _I32, _I32, _F, _P, _P, _P]),
+    "ntc_unpack": (C.c_int, [_P, _I64, _I32, _I32, _F, _P, _P, _P]),
+    "ntc_sample_batch": (C.c_int, [_U64, _I64, _I64, _I32, _I32, _I32, _P, _P]),
+    "ntc_sample_features": (C.c_int, [_P, _P, _I64, _P, _I32, _U64, _I64, _P]),
+}
+
+_lib = None
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile libntc.so for sm_103a (nvcc) next to this file."""
+    from . import build as _b
+    return _b.build(force=force, verbose=verbose)
+
+
+def lib():
+    """The loaded libntc.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "paper_2305_17105_gb300.build() (there is no fallback)")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _call(name, *args):
+    rc = getattr(lib(), name)(*args)
+    if rc != OK:
+        raise NTCError(name, rc, lib().ntc_last_error().decode())
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def _dev(t: torch.Tensor, name: str):
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+# ----------------------------------------------------------------------------
+# small host helpers
+# ----------------------------------------------------------------------------
+def version() -> str:
+    return lib().ntc_version().decode()
+
+
+def cell_bytes(c: int, bits: int) -> int:
+    return int(lib().ntc_cell_bytes(c, bits))
+
+
+def mips_of(width: int, height: int) -> int:
+    return max(width, height).bit_length()
+
+
+def ntc_pyramid(width: int, height: int):
+    """Feature-level grid sizes ``[((g0w, g0h), (g1w, g1h)), ...]`` (Table 1)."""
+    a = [(C.c_int32 * MAX_LEVELS)() for _ in range(4)]
+    n = lib().ntc_pyramid(width, height, *[C.cast(x, C.c_void_p) for x in a])
+    if n == 0:
+        raise ValueError("bad texture size")
+    return [((a[0][j], a[1][j]), (a[2][j], a[3][j])) for j in range(n)]
+
+
+pyramid = ntc_pyramid
+
+
+# ----------------------------------------------------------------------------
+# materials
+# ----------------------------------------------------------------------------
+class Material:
+    """A compressed material on the device, as the C ABI sees it.
+
+    ``grids0[j]`` / ``grids1[j]``: uint8 ``[g_h, g_w, cell_bytes]`` (packed) or
+    float32 ``[g_h, g_w, c]`` (F32) CUDA tensors.  ``weights``: ``[w1, w2, w3]``
+    ``[out][in]`` tensors of the precision's dtype (float32, float16, or
+    uint8 holding E4M3 bytes); ``biases`` float32; ``scale`` (F8 only) float32
+    ``[6]``: weight scales then activation scales.
+    """
+
+    def __init__(self, width, height, channels, c0, c1, bits0, bits1, q0, q1, grids0, grids1,
+                 weights, biases, k_in, precision=PREC_F32, act=ACT_RELU, out_act=OUT_SIGMOID,
+                 scale=None):
+        self.width, self.height, self.channels = width, height, channels
+        self.mips = mips_of(width, height)
+        self.c0, self.c1, self.bits0, self.bits1 = c0, c1, bits0, bits1
+        self.q0, self.q1 = float(q0), float(q1)
+        self.grids0, self.grids1 = list(grids0), list(grids1)
+        self.weights, self.biases = list(weights), list(biases)
+        self.k_in, self.precision, self.act, self.out_act = k_in, precision, act, out_act
+        self.scale = scale
+        self.encoding = GRID_PACKED if self.grids0[0].dtype == torch.uint8 else GRID_F32
+        self.levels = len(self.grids0)
+
+    @property
+    def struct(self) -> ntc_material:
+        s = ntc_material()
+        s.width, s.height, s.channels, s.mips, s.levels = (self.width, self.height, self.channels,
+                                                           self.mips, self.levels)
+        s.c0, s.c1, s.bits0, s.bits1 = self.c0, self.c1, self.bits0, self.bits1
+        s.q0, s.q1 = self.q0, self.q1
+        s.encoding, s.k_in, s.hidden = self.encoding, self.k_in, HIDDEN
+        s.act, s.out_act, s.precision = self.act, self.out_act, self.precision
+        for j in range(self.levels):
+            g0, g1 = self.grids0[j], self.grids1[j]
+            s.lv[j].g0_h, s.lv[j].g0_w = g0.shape[0], g0.shape[1]
+            s.lv[j].g1_h, s.lv[j].g1_w = g1.shape[0], g1.shape[1]
+            s.lv[j].grid0, s.lv[j].grid1 = g0.data_ptr(), g1.data_ptr()
+        for l in range(3):
+            s.w[l] = self.weights[l].data_ptr()
+            s.b[l] = self.biases[l].data_ptr()
+        s.scale = self.scale.data_ptr() if self.scale is not None else None
+        return s
+
+    def with_(self, **kw) -> "Material":
+        m = Material.__new__(Material)
+        m.__dict__.update(self.__dict__)
+        m.__dict__.update(kw)
+        if "grids0" in kw:
+            m.encoding = GRID_PACKED if m.grids0[0].dtype == torch.uint8 else GRID_F32
+        return m
+
+
+# ----------------------------------------------------------------------------
+# entry points (same names as the C ABI)
+# ----------------------------------------------------------------------------
+def ntc_decode(mat: Material, uvl: torch.Tensor, out_dtype=torch.float32,
+               filter=FILTER_NEAREST, flags=0, noise_seed=0, noise_step=0, out=None, stream=None):
+    """Decode ``uvl`` ``[n, 3]`` float32 queries -> ``[n, channels]``."""
+    _dev(uvl, "uvl")
+    n = uvl.shape[0]
+    if out is None:
+        out = torch.empty((n, mat.channels), dtype=out_dtype, device=uvl.device)
+    dt = DTYPE_F16 if out.dtype == torch.float16 else DTYPE_F32
+    s = mat.struct
+    _call("ntc_decode", C.byref(s), _ptr(uvl), n, _ptr(out), dt, filter, flags, noise_seed,
+          noise_step, _stream(stream))
+    return out
+
+
+def grads_struct(mat: Material, grid0=None, grid1=None, w=None, b=None) -> ntc_grads:
+    g = ntc_grads()
+    for j in range(mat.levels):
+        g.grid0[j] = grid0[j].data_ptr() if grid0 is not None and grid0[j] is not None else None
+        g.grid1[j] = grid1[j].data_ptr() if grid1 is not None and grid1[j] is not None else None
+    for l in range(3):
+        g.w[l] = w[l].data_ptr() if w is not None and w[l] is not None else None
+        g.b[l] = b[l].data_ptr() if b is not None and b[l] is not None else None
+    return g
+
+
+def ntc_backward(mat: Material, uvl, dout, grads: ntc_grads, flags=0, noise_seed=0, noise_step=0,
+                 stream=None):
+    """Accumulate d(sum dout*y)/d(grids, weights) into ``grads``."""
+    _dev(uvl, "uvl")
+    _dev(dout, "dout")
+    s = mat.struct
+    _call("ntc_backward", C.byref(s), _ptr(uvl), uvl.shape[0], _ptr(dout), C.byref(grads), flags,
+          noise_seed, noise_step, _stream(stream))
+
+
+def ntc_quantize_pack(values: torch.Tensor, c: int, bits: int, q: float, packed=None, snapped=None,
+                      want_packed=True, stream=None):
+    _dev(values, "values")
+    cells = values.numel() // c
+    if packed is None and want_packed:
+        packed = torch.empty((cells, cell_bytes(c, bits)), dtype=torch.uint8, device=values.device)
+    _call("ntc_quantize_pack", _ptr(values), cells, c, bits, q, _ptr(packed), _ptr(snapped),
+          _stream(stream))
+    return packed
+
+
+def ntc_unpack(packed: torch.Tensor, c: int, bits: int, q: float, want_idx=True, want_values=True,
+               stream=None):
+    _dev(packed, "packed")
+    cells = packed.numel() // cell_bytes(c, bits)
+    idx = torch.empty((cells, c), dtype=torch.int32, device=packed.device) if want_idx else None
+    val = torch.empty((cells, c), dtype=torch.float32, device=packed.device) if want_values else None
+    _call("ntc_unpack", _ptr(packed), cells, c, bits, q, _ptr(idx), _ptr(val), _stream(stream))
+    return idx, val
+
+
+def ntc_sample_batch(seed: int, step: int, batch: int, width: int, height: int, n_mips: int,
+                     device="cuda", stream=None):
+    out = torch.empty((batch, 3), dtype=torch.int32, device=device)
+    _call("ntc_sample_batch", seed, step, batch, width, height, n_mips, _ptr(out), _stream(stream))
+    return out
+
+
+def ntc_sample_features(mat: Material, uvl, flags=0, noise_seed=0, noise_step=0, stream=None):
+    _dev(uvl, "uvl")
+    rows = torch.empty((uvl.shape[0], mat.k_in), dtype=torch.float32, device=uvl.device)
+    s = mat.struct
+    _call("ntc_sample_features", C.byref(s), _ptr(uvl), uvl.shape[0], _ptr(rows), flags,
+          noise_seed, noise_step, _stream(stream))
+    return rows
+
+
+# ----------------------------------------------------------------------------
+# training state
+# ----------------------------------------------------------------------------
+def _align4(n: int) -> int:
+    return (n + 3) // 4 * 4
+
+
+class Trainer:
+    """FP32 master parameters + Adam state of one material in one flat
+    device array (grids level by level, then W1, b1, W2, b2, W3, b3; every
+    tensor 16-byte aligned), driven by ``ntc_train_step``."""
+
+    def __init__(self, width, height, channels, c0, c1, bits0, bits1, q0, q1, grids0, grids1,
+                 weights, biases, k_in, precision=PREC_F32, act=ACT_RELU, out_act=OUT_SIGMOID,
+                 total_steps=1000, lr_grid=0.01, lr_mlp=0.005, betas=(0.9, 0.999), eps=1e-8,
+                 device="cuda"):
+        tensors = [np.asarray(g, np.float32) for g in grids0] + \
+                  [np.asarray(g, np.float32) for g in grids1]
+        mlp = []
+        for w, b in zip(weights, biases):
+            mlp += [np.asarray(w, np.float32), np.asarray(b, np.float32)]
+        tensors += mlp
+        offs, n = [], 0
+        for t in tensors:
+            offs.append(n)
+            n += _align4(t.size)
+        flat = np.zeros(n, np.float32)
+        for o, t in zip(offs, tensors):
+            flat[o:o + t.size] = t.reshape(-1)
+        self.params = torch.from_numpy(flat).to(device)
+        self.adam_m = torch.zeros_like(self.params)
+        self.adam_v = torch.zeros_like(self.params)
+        self.grad = torch.zeros_like(self.params)
+        self.step_t = torch.zeros(1, dtype=torch.int64, device=device)
+        self.loss = torch.zeros(1, dtype=torch.float32, device=device)
+        views = [self.params[o:o + t.size].view(t.shape) for o, t in zip(offs, tensors)]
+        L = len(grids0)
+        g0, g1, rest = views[:L], views[L:2 * L], views[2 * L:]
+        self.w_master = [rest[0], rest[2], rest[4]]
+        self.b = [rest[1], rest[3], rest[5]]
+        self.grad_views = [self.grad[o:o + t.size].view(t.shape) for o, t in zip(offs, tensors)]
+        if precision == PREC_F16:
+            self.w_compute = [w.half().contiguous() for w in self.w_master]
+        elif precision == PREC_F32:
+            self.w_compute = self.w_master
+        else:
+            raise ValueError("training supports FP32 and FP16 weights")
+        self.material = Material(width, height, channels, c0, c1, bits0, bits1, q0, q1, g0, g1,
+                                 self.w_compute, self.b, k_in, precision, act, out_act)
+        self.total_steps, self.lr_grid, self.lr_mlp = total_steps, lr_grid, lr_mlp
+        self.betas, self.eps = betas, eps
+
+    @property
+    def struct(self) -> ntc_trainer:
+        t = ntc_trainer()
+        t.params, t.adam_m = self.params.data_ptr(), self.adam_m.data_ptr()
+        t.adam_v, t.grad = self.adam_v.data_ptr(), self.grad.data_ptr()
+        t.n_params = self.params.numel()
+        for l in range(3):
+            t.w_master[l] = self.w_master[l].data_ptr()
+        t.step = self.step_t.data_ptr()
+        t.total_steps = self.total_steps
+        t.lr_grid, t.lr_mlp = self.lr_grid, self.lr_mlp
+        t.beta1, t.beta2 = self.betas
+        t.eps = self.eps
+        return t
+
+
+class Target:
+    """The 8-bit reference mip chain on the device."""
+
+    def __init__(self, mip_chain_u8, device="cuda"):
+        offs, n = [], 0
+        for lvl in mip_chain_u8:
+            offs.append(n)
+            n += (lvl.size + 15) // 16 * 16
+        buf = np.zeros(n, np.uint8)
+        for o, lvl in zip(offs, mip_chain_u8):
+            buf[o:o + lvl.size] = np.asarray(lvl, np.uint8).reshape(-1)
+        self.texels = torch.from_numpy(buf).to(device)
+        self.offsets = offs
+
+    @property
+    def struct(self) -> ntc_target:
+        t = ntc_target()
+        t.texels = self.texels.data_ptr()
+        for m, o in enumerate(self.offsets):
+            t.offset[m] = o
+        return t
+
+
+def ntc_train_step(trainer: Trainer, target: Target, batch: int, seed: int, uvl=None, flags=0,
+                   stream=None):
+    """One fused optimisation step; returns the device loss tensor."""
+    m, t, tg = trainer.material.struct, trainer.struct, target.struct
+    _call("ntc_train_step", C.byref(m), C.byref(t), C.byref(tg), batch, seed, _ptr(uvl),
+          _ptr(trainer.loss), flags, _stream(stream))
+    return trainer.loss
+
+
+# ----------------------------------------------------------------------------
+# autograd
+# ----------------------------------------------------------------------------
+class NTCDecodeFunction(torch.autograd.Function):
+    """Nearest decode with a hand-written adjoint: ``ntc_decode`` forward,
+    ``ntc_backward`` backward (recomputes activations; scatter-adds into the
+    latent grids; the simulated-quantisation noise passes gradients)."""
+
+    @staticmethod
+    def forward(ctx, uvl, mat_proto, noise, *tensors):
+        L = mat_proto.levels
+        g0, g1 = list(tensors[:L]), list(tensors[L:2 * L])
+        w, b = list(tensors[2 * L:2 * L + 3]), list(tensors[2 * L + 3:2 * L + 6])
+        wc = [x.half().contiguous() for x in w] if mat_proto.precision == PREC_F16 else w
+        mat = mat_proto.with_(grids0=g0, grids1=g1, weights=wc, biases=b)
+        flags = FLAG_NOISE if noise is not None else 0
+        seed, step = noise if noise is not None else (0, 0)
+        y = ntc_decode(mat, uvl, flags=flags, noise_seed=seed, noise_step=step)
+        ctx.save_for_backward(uvl, *tensors)
+        ctx.mat, ctx.flags, ctx.seed, ctx.step, ctx.L = mat, flags, seed, step, L
+        return y
+
+    @staticmethod
+    def backward(ctx, dy):
+        uvl, *tensors = ctx.saved_tensors
+        L = ctx.L
+        grads = [torch.zeros_like(t) for t in tensors]
+        gs = grads_struct(ctx.mat, grads[:L], grads[L:2 * L], grads[2 * L:2 * L + 3],
+                          grads[2 * L + 3:2 * L + 6])
+        ntc_backward(ctx.mat, uvl, dy.contiguous().float(), gs, flags=ctx.flags,
+                     noise_seed=ctx.seed, noise_step=ctx.step)
+        return (None, None, None, *grads)
+
+
+def decode_autograd(mat_proto: Material, uvl, grids0, grids1, weights, biases, noise=None):
+    return NTCDecodeFunction.apply(uvl, mat_proto, noise, *grids0, *grids1, *weights, *biases)

@@ -1,0 +1,184 @@
+// Element-wise kernels around the fused passes: Adam with cosine-annealed
+// learning rates and quantisation-range clamping (Sec. 4.2, 5.1), the final
+// quantisation and packing of the grids (Sec. 4.2), and test entry points for
+// the sampler and the MLP input rows.
+#include <math.h>
+
+#include "ntc_device.cuh"
+#include "ntc_internal.h"
+
+namespace ntc {
+
+int sm_count() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
+  return n > 0 ? n : 1;
+}
+
+namespace {
+
+// One Adam step (Kingma & Ba, bias-corrected) at the device step counter t,
+// learning rate lr0 (1 + cos(pi t / T)) / 2 per group, then the grid clamp
+// to [-(N-1)/2 Q, N/2 Q] (Sec. 4.2: clamp after the update).  The gradient is
+// zeroed for the next step; half-precision weight copies are refreshed.
+__global__ void __launch_bounds__(kAdamBlock) adam_kernel(const AdamArgs A) {
+  __shared__ float s_lr, s_c1, s_c2;
+  const int64_t b = blockIdx.x;
+  int s = 0;
+  while (s + 1 < A.nseg && b >= A.block_start[s + 1]) ++s;
+  const AdamSeg& S = A.seg[s];
+  if (threadIdx.x == 0) {
+    const int64_t t = *A.step;
+    const double pi = 3.14159265358979323846;
+    const double lr = (double)A.lr[S.group] * 0.5 * (1.0 + cos(pi * (double)t / (double)A.total));
+    s_lr = (float)lr;
+    s_c1 = (float)(1.0 - pow((double)A.beta1, (double)(t + 1)));
+    s_c2 = (float)(1.0 - pow((double)A.beta2, (double)(t + 1)));
+  }
+  __syncthreads();
+  if (A.freeze_grids && S.group == 0) return;
+  const float lr = s_lr, inv_c1 = 1.f / s_c1, inv_c2 = 1.f / s_c2;
+  const float b1 = A.beta1, b2 = A.beta2, eps = A.eps;
+  const int64_t first = (b - A.block_start[s]) * (int64_t)(kAdamBlock * kAdamPerThread) + threadIdx.x;
+#pragma unroll
+  for (int k = 0; k < kAdamPerThread; ++k) {
+    const int64_t idx = first + (int64_t)k * kAdamBlock;
+    if (idx >= S.len) break;
+    const int64_t e = S.off + idx;
+    const float g = A.g[e];
+    const float m = fmaf(b1, A.m[e], (1.f - b1) * g);
+    const float v = fmaf(b2, A.v[e], (1.f - b2) * g * g);
+    float p = A.p[e] - lr * (m * inv_c1) / (sqrtf(v * inv_c2) + eps);
+    if (S.clamp) p = fminf(fmaxf(p, S.lo), S.hi);
+    A.m[e] = m;
+    A.v[e] = v;
+    A.p[e] = p;
+    A.g[e] = 0.f;
+    if (S.half_copy) S.half_copy[idx] = __float2half_rn(p);
+  }
+}
+
+__global__ void advance_step_kernel(int64_t* step) { *step += 1; }
+
+// q = clamp(rint(x / Q) + N/2 - 1, 0, N - 1), ties to even, evaluated in
+// double so that the index never depends on the rounding of x / Q.
+__global__ void quantize_pack_kernel(const float* __restrict__ x, int64_t cells, int c, int bits,
+                                     float q, uint8_t* __restrict__ packed,
+                                     float* __restrict__ snapped) {
+  const int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= cells) return;
+  const int n = 1 << bits, off = n / 2 - 1;
+  uint64_t lo = 0, hi = 0;
+  for (int ch = 0; ch < c; ++ch) {
+    const float v = x[cell * c + ch];
+    double k = rint((double)v / (double)q) + (double)off;
+    k = fmin(fmax(k, 0.0), (double)(n - 1));
+    const uint64_t qi = (uint64_t)k;
+    const int bit = ch * bits;
+    if (bit < 64) lo |= qi << bit;
+    else hi |= qi << (bit - 64);
+    if (snapped) snapped[cell * c + ch] = (float)((int)qi - off) * q;
+  }
+  if (!packed) return;
+  const int cb = cell_bytes(c, bits);
+  uint8_t* p = packed + cell * cb;
+  switch (cb) {
+    case 1: *p = (uint8_t)lo; break;
+    case 2: *reinterpret_cast<uint16_t*>(p) = (uint16_t)lo; break;
+    case 4: *reinterpret_cast<uint32_t*>(p) = (uint32_t)lo; break;
+    case 8: *reinterpret_cast<unsigned long long*>(p) = lo; break;
+    default:
+      *reinterpret_cast<uint4*>(p) =
+          make_uint4((uint32_t)lo, (uint32_t)(lo >> 32), (uint32_t)hi, (uint32_t)(hi >> 32));
+  }
+}
+
+__global__ void unpack_kernel(const uint8_t* __restrict__ packed, int64_t cells, int c, int bits,
+                              float q, int32_t* __restrict__ idx, float* __restrict__ values) {
+  const int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= cells) return;
+  const int off = (1 << (bits - 1)) - 1;
+  const int cb = cell_bytes(c, bits);
+  const Cell cc = load_cell(packed + cell * cb, 0, cb);
+  for (int ch = 0; ch < c; ++ch) {
+    const int v = (int)cell_index(cc, ch, bits);
+    if (idx) idx[cell * c + ch] = v;
+    if (values) values[cell * c + ch] = (float)(v - off) * q;
+  }
+}
+
+__global__ void sample_batch_kernel(uint64_t skey, int64_t batch, int w, int h, int mips,
+                                    int32_t* __restrict__ xym) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= batch) return;
+  int x, y, m;
+  sample_texel(skey, i, w, h, mips, x, y, m);
+  xym[3 * i] = x;
+  xym[3 * i + 1] = y;
+  xym[3 * i + 2] = m;
+}
+
+struct GlobalRowSink {
+  float* row;
+  __device__ __forceinline__ void operator()(int i, float v) const { row[i] = v; }
+};
+
+__global__ void sample_features_kernel(const ntc_material M, const float* __restrict__ uvl,
+                                       int64_t n, float* __restrict__ rows, int noise,
+                                       uint64_t nkey) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int x, y, m;
+  query_texel(M, uvl[3 * i], uvl[3 * i + 1], uvl[3 * i + 2], x, y, m);
+  GlobalRowSink sink{rows + i * M.k_in};
+  featurize(M, x, y, m, noise != 0, nkey, sink);
+}
+
+inline int blocks_for(int64_t n, int per) { return (int)((n + per - 1) / per); }
+
+}  // namespace
+
+cudaError_t launch_adam(const AdamArgs& a, int64_t blocks, cudaStream_t s) {
+  if (blocks == 0) return cudaSuccess;
+  adam_kernel<<<(unsigned)blocks, kAdamBlock, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_advance_step(int64_t* step, cudaStream_t s) {
+  advance_step_kernel<<<1, 1, 0, s>>>(step);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_quantize_pack(const float* values, int64_t cells, int c, int bits, float q,
+                                 uint8_t* packed, float* snapped, cudaStream_t s) {
+  if (cells == 0) return cudaSuccess;
+  quantize_pack_kernel<<<blocks_for(cells, 256), 256, 0, s>>>(values, cells, c, bits, q, packed,
+                                                               snapped);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpack(const uint8_t* packed, int64_t cells, int c, int bits, float q,
+                          int32_t* idx, float* values, cudaStream_t s) {
+  if (cells == 0) return cudaSuccess;
+  unpack_kernel<<<blocks_for(cells, 256), 256, 0, s>>>(packed, cells, c, bits, q, idx, values);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sample_batch(uint64_t seed, int64_t step, int64_t batch, int w, int h, int mips,
+                                int32_t* xym, cudaStream_t s) {
+  if (batch == 0) return cudaSuccess;
+  sample_batch_kernel<<<blocks_for(batch, 256), 256, 0, s>>>(rng_key(seed, sampler_stream(step)),
+                                                             batch, w, h, mips, xym);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sample_features(const ntc_material& m, const float* uvl, int64_t n, float* rows,
+                                   int noise, uint64_t seed, int64_t step, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  sample_features_kernel<<<blocks_for(n, 128), 128, 0, s>>>(m, uvl, n, rows, noise,
+                                                            rng_key(seed, noise_stream(step)));
+  return cudaGetLastError();
+}
+
+}  // namespace ntc

@@ -1,0 +1,353 @@
+// C-ABI entry points of libntc.so (declared in include/ntc.h): argument
+// validation, error reporting and dispatch to the kernels.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "ntc_device.cuh"
+#include "ntc_internal.h"
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+int cuda_status(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return NTC_OK;
+  if (e == cudaErrorNotSupported) return fail(NTC_ERR_UNSUPPORTED, "%s: not supported", what);
+  return fail(NTC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+bool aligned(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+int log2i(int v) {
+  int r = 0;
+  while ((1 << r) < v) ++r;
+  return r;
+}
+
+#define CHECK_PTR(p, name)                                                        \
+  do {                                                                            \
+    if (!(p)) return fail(NTC_ERR_ARG, "%s is NULL", name);                       \
+    if (!aligned(p)) return fail(NTC_ERR_ALIGN, "%s is not 16-byte aligned", name); \
+  } while (0)
+
+// Shape and pointer rules shared by every call that takes a material.
+int check_material(const ntc_material* m, bool need_f32_grids) {
+  if (!m) return fail(NTC_ERR_ARG, "material is NULL");
+  if (!pow2(m->width) || !pow2(m->height) || m->width > 32768 || m->height > 32768)
+    return fail(NTC_ERR_SHAPE, "texture %dx%d: sides must be powers of two <= 32768", m->width,
+                m->height);
+  const int mips = log2i(m->width > m->height ? m->width : m->height) + 1;
+  if (m->mips != mips) return fail(NTC_ERR_SHAPE, "mips = %d, expected %d", m->mips, mips);
+  if (m->channels < 1 || m->channels > NTC_MAX_CHANNELS)
+    return fail(NTC_ERR_SHAPE, "channels = %d outside 1..%d", m->channels, NTC_MAX_CHANNELS);
+  if (m->levels < 1 || m->levels > NTC_MAX_LEVELS)
+    return fail(NTC_ERR_SHAPE, "levels = %d outside 1..%d", m->levels, NTC_MAX_LEVELS);
+  if (m->c0 < 1 || m->c1 < 1 || m->c0 > ntc::kMaxGridCh || m->c1 > ntc::kMaxGridCh)
+    return fail(NTC_ERR_SHAPE, "c0 = %d, c1 = %d outside 1..%d", m->c0, m->c1, ntc::kMaxGridCh);
+  for (int b : {m->bits0, m->bits1})
+    if (b != 1 && b != 2 && b != 4 && b != 8) return fail(NTC_ERR_ARG, "bits %d not in {1,2,4,8}", b);
+  if (!(m->q0 > 0.f) || !(m->q1 > 0.f)) return fail(NTC_ERR_ARG, "bin widths must be positive");
+  if (m->encoding != NTC_GRID_PACKED && m->encoding != NTC_GRID_F32)
+    return fail(NTC_ERR_ARG, "encoding %d", m->encoding);
+  if (need_f32_grids && m->encoding != NTC_GRID_F32)
+    return fail(NTC_ERR_ARG, "this call needs NTC_GRID_F32 grids");
+  if (m->hidden != NTC_HIDDEN) return fail(NTC_ERR_UNSUPPORTED, "hidden = %d (only %d)", m->hidden, NTC_HIDDEN);
+  if (m->precision < NTC_PREC_F32 || m->precision > NTC_PREC_F8)
+    return fail(NTC_ERR_ARG, "precision %d", m->precision);
+  const int kmul = m->precision == NTC_PREC_F8 ? 32 : 16;
+  if (m->k_in % kmul != 0 || m->k_in < m->c0 + m->c1 + 13 || m->k_in > NTC_MAX_K)
+    return fail(NTC_ERR_SHAPE, "k_in = %d: need a multiple of %d in [c0+c1+13, %d]", m->k_in, kmul,
+                NTC_MAX_K);
+  if (m->act != NTC_ACT_RELU && m->act != NTC_ACT_HARDGELU) return fail(NTC_ERR_ARG, "act %d", m->act);
+  if (m->out_act != NTC_OUT_SIGMOID && m->out_act != NTC_OUT_IDENTITY)
+    return fail(NTC_ERR_ARG, "out_act %d", m->out_act);
+  for (int j = 0; j < m->levels; ++j) {
+    const ntc_level& L = m->lv[j];
+    if (L.g0_w < 1 || L.g0_h < 1 || L.g1_w < 1 || L.g1_h < 1 || L.g0_w > 32768 || L.g0_h > 32768 ||
+        L.g1_w > 32768 || L.g1_h > 32768)
+      return fail(NTC_ERR_SHAPE, "level %d grid sizes must be in 1..32768", j);
+    if ((int64_t)L.g0_w * L.g0_h * (m->encoding == NTC_GRID_F32 ? m->c0 : 1) >= (1LL << 31) ||
+        (int64_t)L.g1_w * L.g1_h * (m->encoding == NTC_GRID_F32 ? m->c1 : 1) >= (1LL << 31))
+      return fail(NTC_ERR_SHAPE, "level %d grid too large", j);
+    CHECK_PTR(L.grid0, "grid0");
+    CHECK_PTR(L.grid1, "grid1");
+  }
+  for (int l = 0; l < 3; ++l) {
+    CHECK_PTR(m->w[l], "weight");
+    CHECK_PTR(m->b[l], "bias");
+  }
+  if (m->precision == NTC_PREC_F8) CHECK_PTR(m->scale, "scale");
+  return NTC_OK;
+}
+
+bool use_simt(const ntc_material* m, int flags) {
+  return (flags & NTC_FLAG_SIMT) || m->precision == NTC_PREC_F32;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ntc_version(void) { return "ntc-gb300 0.1 (sm_103a)"; }
+
+const char* ntc_last_error(void) { return g_err; }
+
+int32_t ntc_cell_bytes(int32_t c, int32_t bits) {
+  if (c < 1 || c > 64 || (bits != 1 && bits != 2 && bits != 4 && bits != 8) || c * bits > 128)
+    return 0;
+  return ntc::cell_bytes(c, bits);
+}
+
+int32_t ntc_pyramid(int32_t width, int32_t height, int32_t* g0_w, int32_t* g0_h, int32_t* g1_w,
+                    int32_t* g1_h) {
+  if (!pow2(width) || !pow2(height) || !g0_w || !g0_h || !g1_w || !g1_h) return 0;
+  int levels = 0;
+  for (int j = 0; j < NTC_MAX_LEVELS; ++j) {
+    const int sh = 2 * j + 2;
+    const int w0 = (width >> sh) > 0 ? (width >> sh) : 1;
+    const int h0 = (height >> sh) > 0 ? (height >> sh) : 1;
+    if (j > 0 && (w0 > h0 ? w0 : h0) < 4) break;
+    g0_w[j] = w0;
+    g0_h[j] = h0;
+    g1_w[j] = (w0 >> 1) > 0 ? (w0 >> 1) : 1;
+    g1_h[j] = (h0 >> 1) > 0 ? (h0 >> 1) : 1;
+    ++levels;
+  }
+  return levels;
+}
+
+int ntc_decode(const ntc_material* m, const float* uvl, int64_t n, void* out, int32_t out_dtype,
+               int32_t filter, int32_t flags, uint64_t noise_seed, int64_t noise_step,
+               void* stream) {
+  int st = check_material(m, (flags & NTC_FLAG_NOISE) != 0);
+  if (st) return st;
+  if (n < 0) return fail(NTC_ERR_ARG, "n < 0");
+  if (out_dtype != NTC_DTYPE_F32 && out_dtype != NTC_DTYPE_F16) return fail(NTC_ERR_ARG, "out_dtype");
+  if (filter != NTC_FILTER_NEAREST && filter != NTC_FILTER_TRILINEAR) return fail(NTC_ERR_ARG, "filter");
+  if ((flags & NTC_FLAG_NOISE) && filter != NTC_FILTER_NEAREST)
+    return fail(NTC_ERR_ARG, "noise needs nearest filtering");
+  if (n == 0) return NTC_OK;
+  CHECK_PTR(uvl, "uvl");
+  CHECK_PTR(out, "out");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (use_simt(m, flags) || (flags & NTC_FLAG_NOISE))
+    return cuda_status(ntc::launch_decode_simt(*m, uvl, n, out, out_dtype, filter,
+                                               (flags & NTC_FLAG_NOISE) != 0, noise_seed,
+                                               noise_step, s),
+                       "decode (FP32 CUDA cores)");
+  return cuda_status(ntc::launch_decode_tc(*m, uvl, n, out, out_dtype, filter, s, 0),
+                     "decode (tcgen05)");
+}
+
+int ntc_backward(const ntc_material* m, const float* uvl, int64_t n, const float* dout,
+                 const ntc_grads* g, int32_t flags, uint64_t noise_seed, int64_t noise_step,
+                 void* stream) {
+  int st = check_material(m, true);
+  if (st) return st;
+  if (n < 0) return fail(NTC_ERR_ARG, "n < 0");
+  if (!g) return fail(NTC_ERR_ARG, "grads is NULL");
+  if (n == 0) return NTC_OK;
+  CHECK_PTR(uvl, "uvl");
+  CHECK_PTR(dout, "dout");
+  ntc::BwdArgs a{};
+  a.uvl = uvl;
+  a.dout = dout;
+  a.n = n;
+  a.g = *g;
+  for (int j = 0; j < m->levels; ++j) {
+    if (a.g.grid0[j] && !aligned(a.g.grid0[j])) return fail(NTC_ERR_ALIGN, "grad grid0");
+    if (a.g.grid1[j] && !aligned(a.g.grid1[j])) return fail(NTC_ERR_ALIGN, "grad grid1");
+  }
+  for (int j = m->levels; j < NTC_MAX_LEVELS; ++j) a.g.grid0[j] = a.g.grid1[j] = nullptr;
+  a.grad_scale = 1.f;
+  a.noise = (flags & NTC_FLAG_NOISE) != 0;
+  a.noise_seed = noise_seed;
+  a.noise_step = noise_step;
+  a.train = 0;
+  a.grids = 1;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (use_simt(m, flags)) {
+    if (m->k_in > 64) return fail(NTC_ERR_UNSUPPORTED, "FP32 backward supports k_in <= 64");
+    return cuda_status(ntc::launch_backward_simt(*m, a, s), "backward (FP32 CUDA cores)");
+  }
+  return cuda_status(ntc::launch_backward_tc(*m, a, s), "backward (tcgen05)");
+}
+
+int ntc_train_step(const ntc_material* m, const ntc_trainer* tr, const ntc_target* t,
+                   int64_t batch, uint64_t seed, const float* uvl_or_null, float* loss_out,
+                   int32_t flags, void* stream) {
+  int st = check_material(m, true);
+  if (st) return st;
+  if (!tr || !t) return fail(NTC_ERR_ARG, "trainer / target is NULL");
+  if (batch <= 0) return fail(NTC_ERR_ARG, "batch must be positive");
+  if (m->precision == NTC_PREC_F8) return fail(NTC_ERR_UNSUPPORTED, "FP8 training");
+  CHECK_PTR(tr->params, "params");
+  CHECK_PTR(tr->adam_m, "adam_m");
+  CHECK_PTR(tr->adam_v, "adam_v");
+  CHECK_PTR(tr->grad, "grad");
+  CHECK_PTR(tr->step, "step");
+  CHECK_PTR(t->texels, "target texels");
+  CHECK_PTR(loss_out, "loss_out");
+  if (uvl_or_null && !aligned(uvl_or_null)) return fail(NTC_ERR_ALIGN, "uvl");
+  if (tr->total_steps <= 0) return fail(NTC_ERR_ARG, "total_steps must be positive");
+  for (int l = 0; l < 3; ++l) CHECK_PTR(tr->w_master[l], "w_master");
+  if (m->precision == NTC_PREC_F32)
+    for (int l = 0; l < 3; ++l)
+      if (m->w[l] != tr->w_master[l]) return fail(NTC_ERR_ARG, "F32 weights must be the masters");
+
+  // Segments of the parameter array: grids (group 0, clamped), MLP (group 1).
+  ntc::AdamArgs a{};
+  const float* P = tr->params;
+  auto offset_of = [&](const void* ptr, int64_t len, int64_t* off) -> bool {
+    const float* f = static_cast<const float*>(ptr);
+    if (f < P || f + len > P + tr->n_params) return false;
+    *off = f - P;
+    return true;
+  };
+  auto add_seg = [&](const void* ptr, int64_t len, int group, bool clamp, float lo, float hi,
+                     __half* half_copy) -> bool {
+    ntc::AdamSeg& sg = a.seg[a.nseg++];
+    if (!offset_of(ptr, len, &sg.off)) return false;
+    sg.len = len;
+    sg.group = group;
+    sg.clamp = clamp;
+    sg.lo = lo;
+    sg.hi = hi;
+    sg.half_copy = half_copy;
+    return true;
+  };
+  const int n0 = 1 << m->bits0, n1 = 1 << m->bits1;
+  const float lo0 = -(float)(n0 - 1) / 2.f * m->q0, hi0 = (float)n0 / 2.f * m->q0;
+  const float lo1 = -(float)(n1 - 1) / 2.f * m->q1, hi1 = (float)n1 / 2.f * m->q1;
+  for (int j = 0; j < m->levels; ++j) {
+    const ntc_level& L = m->lv[j];
+    if (!add_seg(L.grid0, (int64_t)L.g0_w * L.g0_h * m->c0, 0, true, lo0, hi0, nullptr) ||
+        !add_seg(L.grid1, (int64_t)L.g1_w * L.g1_h * m->c1, 0, true, lo1, hi1, nullptr))
+      return fail(NTC_ERR_ARG, "grid %d is not inside params", j);
+  }
+  const int64_t wlen[3] = {(int64_t)NTC_HIDDEN * m->k_in, (int64_t)NTC_HIDDEN * NTC_HIDDEN,
+                           (int64_t)m->channels * NTC_HIDDEN};
+  const int64_t blen[3] = {NTC_HIDDEN, NTC_HIDDEN, m->channels};
+  for (int l = 0; l < 3; ++l) {
+    __half* hc = m->precision == NTC_PREC_F16 ? (__half*)m->w[l] : nullptr;
+    if (!add_seg(tr->w_master[l], wlen[l], 1, false, 0, 0, hc) ||
+        !add_seg(m->b[l], blen[l], 1, false, 0, 0, nullptr))
+      return fail(NTC_ERR_ARG, "MLP tensor %d is not inside params", l);
+  }
+  const int64_t per_block = ntc::kAdamBlock * ntc::kAdamPerThread;
+  a.block_start[0] = 0;
+  for (int i = 0; i < a.nseg; ++i)
+    a.block_start[i + 1] = a.block_start[i] + (a.seg[i].len + per_block - 1) / per_block;
+  a.p = tr->params;
+  a.m = tr->adam_m;
+  a.v = tr->adam_v;
+  a.g = tr->grad;
+  a.step = tr->step;
+  a.total = tr->total_steps;
+  a.lr[0] = tr->lr_grid;
+  a.lr[1] = tr->lr_mlp;
+  a.beta1 = tr->beta1;
+  a.beta2 = tr->beta2;
+  a.eps = tr->eps;
+  const bool freeze = (flags & NTC_FLAG_FREEZE_GRIDS) != 0;
+  a.freeze_grids = freeze;
+
+  // Fused forward + loss + backward into tr->grad.
+  ntc::BwdArgs b{};
+  b.uvl = uvl_or_null;
+  b.target = t->texels;
+  for (int i = 0; i < NTC_MAX_MIPS; ++i) b.tgt_off[i] = t->offset[i];
+  b.n = batch;
+  float* G = tr->grad;
+  for (int j = 0; j < m->levels; ++j) {
+    b.g.grid0[j] = freeze ? nullptr : G + a.seg[2 * j].off;
+    b.g.grid1[j] = freeze ? nullptr : G + a.seg[2 * j + 1].off;
+  }
+  for (int l = 0; l < 3; ++l) {
+    b.g.w[l] = G + a.seg[2 * m->levels + 2 * l].off;
+    b.g.b[l] = G + a.seg[2 * m->levels + 2 * l + 1].off;
+  }
+  b.grad_scale = (float)(1.0 / ((double)batch * (double)m->channels));
+  b.loss = loss_out;
+  b.loss_scale = b.grad_scale;
+  b.noise = !(freeze || (flags & NTC_FLAG_NO_NOISE));
+  b.noise_seed = seed;
+  b.sample_seed = seed;
+  b.step_dev = tr->step;
+  b.train = 1;
+  b.grids = !freeze;
+
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemsetAsync(loss_out, 0, sizeof(float), s);
+  if (e != cudaSuccess) return cuda_status(e, "train_step memset");
+  if (use_simt(m, flags)) {
+    if (m->k_in > 64) return fail(NTC_ERR_UNSUPPORTED, "FP32 training supports k_in <= 64");
+    e = ntc::launch_backward_simt(*m, b, s);
+  } else {
+    e = ntc::launch_backward_tc(*m, b, s);
+  }
+  if (e != cudaSuccess) return cuda_status(e, "train_step forward/backward");
+  e = ntc::launch_adam(a, a.block_start[a.nseg], s);
+  if (e != cudaSuccess) return cuda_status(e, "train_step adam");
+  return cuda_status(ntc::launch_advance_step(tr->step, s), "train_step step counter");
+}
+
+int ntc_quantize_pack(const float* values, int64_t cells, int32_t c, int32_t bits, float q,
+                      uint8_t* packed_out, float* snapped_out, void* stream) {
+  if (cells < 0 || ntc_cell_bytes(c, bits) == 0 || !(q > 0.f)) return fail(NTC_ERR_ARG, "quantize args");
+  if (cells == 0) return NTC_OK;
+  CHECK_PTR(values, "values");
+  if (packed_out && !aligned(packed_out)) return fail(NTC_ERR_ALIGN, "packed_out");
+  if (snapped_out && !aligned(snapped_out)) return fail(NTC_ERR_ALIGN, "snapped_out");
+  return cuda_status(ntc::launch_quantize_pack(values, cells, c, bits, q, packed_out, snapped_out,
+                                               static_cast<cudaStream_t>(stream)),
+                     "quantize_pack");
+}
+
+int ntc_unpack(const uint8_t* packed, int64_t cells, int32_t c, int32_t bits, float q,
+               int32_t* idx_out, float* values_out, void* stream) {
+  if (cells < 0 || ntc_cell_bytes(c, bits) == 0 || !(q > 0.f)) return fail(NTC_ERR_ARG, "unpack args");
+  if (cells == 0) return NTC_OK;
+  CHECK_PTR(packed, "packed");
+  if (idx_out && !aligned(idx_out)) return fail(NTC_ERR_ALIGN, "idx_out");
+  if (values_out && !aligned(values_out)) return fail(NTC_ERR_ALIGN, "values_out");
+  return cuda_status(ntc::launch_unpack(packed, cells, c, bits, q, idx_out, values_out,
+                                        static_cast<cudaStream_t>(stream)),
+                     "unpack");
+}
+
+int ntc_sample_batch(uint64_t seed, int64_t step, int64_t batch, int32_t width, int32_t height,
+                     int32_t mips, int32_t* xym_out, void* stream) {
+  if (batch < 0 || step < 0 || !pow2(width) || !pow2(height) || mips < 1 || mips > NTC_MAX_MIPS)
+    return fail(NTC_ERR_ARG, "sample_batch args");
+  if (batch == 0) return NTC_OK;
+  CHECK_PTR(xym_out, "xym_out");
+  return cuda_status(ntc::launch_sample_batch(seed, step, batch, width, height, mips, xym_out,
+                                              static_cast<cudaStream_t>(stream)),
+                     "sample_batch");
+}
+
+int ntc_sample_features(const ntc_material* m, const float* uvl, int64_t n, float* rows_out,
+                        int32_t flags, uint64_t noise_seed, int64_t noise_step, void* stream) {
+  int st = check_material(m, (flags & NTC_FLAG_NOISE) != 0);
+  if (st) return st;
+  if (n < 0) return fail(NTC_ERR_ARG, "n < 0");
+  if (n == 0) return NTC_OK;
+  CHECK_PTR(uvl, "uvl");
+  CHECK_PTR(rows_out, "rows_out");
+  return cuda_status(ntc::launch_sample_features(*m, uvl, n, rows_out, (flags & NTC_FLAG_NOISE) != 0,
+                                                 noise_seed, noise_step,
+                                                 static_cast<cudaStream_t>(stream)),
+                     "sample_features");
+}
+
+}  // extern "C"

@@ -1,0 +1,82 @@
+// Internal launch interface between the C-ABI layer (ntc_api.cu) and the
+// kernel translation units.  Every launcher returns a cudaError_t from the
+// launch; arguments are validated by the caller.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ntc.h"
+
+namespace ntc {
+
+// What the fused forward+backward kernel differentiates.
+struct BwdArgs {
+  const float* uvl;        // queries (nullable in training mode: sampler instead)
+  const float* dout;       // [n][C] upstream gradient (backward mode) or nullptr
+  const uint8_t* target;   // training mode: u8 mip chain
+  int64_t tgt_off[NTC_MAX_MIPS];
+  int64_t n;
+  ntc_grads g;             // gradient destinations (accumulated)
+  float grad_scale;        // multiplies every accumulated gradient
+  float* loss;             // training mode: += mean squared error
+  float loss_scale;        // 1 / (n * C)
+  int noise;               // simulated-quantisation noise on
+  uint64_t noise_seed;
+  int64_t noise_step;      // used when step_dev == nullptr
+  uint64_t sample_seed;
+  const int64_t* step_dev; // training mode: device step counter (noise + sampler)
+  int train;               // 1: loss mode (dout = 2 (y - t)), 0: dout given
+  int grids;               // 0: skip grid gradients (frozen grids)
+};
+
+cudaError_t launch_decode_simt(const ntc_material& m, const float* uvl, int64_t n, void* out,
+                               int out_dtype, int filter, int noise, uint64_t noise_seed,
+                               int64_t noise_step, cudaStream_t s);
+cudaError_t launch_backward_simt(const ntc_material& m, const BwdArgs& a, cudaStream_t s);
+
+cudaError_t launch_decode_tc(const ntc_material& m, const float* uvl, int64_t n, void* out,
+                             int out_dtype, int filter, cudaStream_t s, int ctas_per_sm);
+cudaError_t launch_backward_tc(const ntc_material& m, const BwdArgs& a, cudaStream_t s);
+
+// Adam over the segments of the trainer's parameter array.
+constexpr int kMaxSegs = 2 * NTC_MAX_LEVELS + 6;
+struct AdamSeg {
+  int64_t off, len;   // float offset into params and element count
+  float lo, hi;       // clamp range (grids)
+  int group;          // 0 grids, 1 MLP
+  int clamp;
+  __half* half_copy;  // refresh target (F16 weights) or nullptr
+};
+struct AdamArgs {
+  AdamSeg seg[kMaxSegs];
+  int64_t block_start[kMaxSegs + 1];  // prefix sums of blocks per segment
+  int nseg;
+  float* p;
+  float* m;
+  float* v;
+  float* g;
+  const int64_t* step;
+  int64_t total;
+  float lr[2];
+  float beta1, beta2, eps;
+  int freeze_grids;
+};
+constexpr int kAdamBlock = 256;
+constexpr int kAdamPerThread = 4;
+cudaError_t launch_adam(const AdamArgs& a, int64_t blocks, cudaStream_t s);
+cudaError_t launch_advance_step(int64_t* step, cudaStream_t s);
+
+cudaError_t launch_quantize_pack(const float* values, int64_t cells, int c, int bits, float q,
+                                 uint8_t* packed, float* snapped, cudaStream_t s);
+cudaError_t launch_unpack(const uint8_t* packed, int64_t cells, int c, int bits, float q,
+                          int32_t* idx, float* values, cudaStream_t s);
+cudaError_t launch_sample_batch(uint64_t seed, int64_t step, int64_t batch, int w, int h, int mips,
+                                int32_t* xym, cudaStream_t s);
+cudaError_t launch_sample_features(const ntc_material& m, const float* uvl, int64_t n, float* rows,
+                                   int noise, uint64_t seed, int64_t step, cudaStream_t s);
+
+int sm_count();
+
+}  // namespace ntc

@@ -1,0 +1,64 @@
+"""Device-side construction of the seeded cases for the GPU parity tests.
+
+Packed grids are produced by the oracle's packer from the case's indices (an
+input encoding, identical for both sides); the library's own packer is
+checked bit-exactly against it separately.
+"""
+import numpy as np
+import torch
+
+import oracle
+import paper_2305_17105_gb300 as ntc
+
+DEV = "cuda"
+
+
+def _t(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.to(DEV)
+
+
+def stored_weights(case, precision):
+    """The weights as the library stores them and the exactly converted
+    float64 values the oracle then sees (stored-weight parity)."""
+    w = case.weights
+    if precision == ntc.PREC_F16:
+        ws = [w[0].astype(np.float16), w[2].astype(np.float16), w[4].astype(np.float16)]
+        oracle_w = [ws[0].astype(np.float64), w[1], ws[1].astype(np.float64), w[3],
+                    ws[2].astype(np.float64), w[5]]
+        dev = [_t(x) for x in ws]
+    else:
+        oracle_w = list(w)
+        dev = [_t(w[0]), _t(w[2]), _t(w[4])]
+    return dev, [np.asarray(x, np.float64) for x in oracle_w]
+
+
+def device_material(case, precision=ntc.PREC_F32, packed=True):
+    """(ntc.Material, oracle.Model) for one case."""
+    wdev, wor = stored_weights(case, precision)
+    if packed:
+        g0 = [_t(oracle.pack(i.reshape(-1, case.c0), case.c0, case.bits0).reshape(
+            i.shape[0], i.shape[1], -1)) for i in case.idx0]
+        g1 = [_t(oracle.pack(i.reshape(-1, case.c1), case.c1, case.bits1).reshape(
+            i.shape[0], i.shape[1], -1)) for i in case.idx1]
+    else:
+        g0 = [_t(v) for v in case.val0]
+        g1 = [_t(v) for v in case.val1]
+    b = [_t(case.weights[1]), _t(case.weights[3]), _t(case.weights[5])]
+    mat = ntc.Material(case.width, case.height, case.channels, case.c0, case.c1, case.bits0,
+                       case.bits1, case.q0, case.q1, g0, g1, wdev, b, case.k_in, precision,
+                       case.act, case.out_act)
+    md = case.oracle_model(weights=wor, quantized=packed)
+    return mat, md
+
+
+def to_np(t):
+    return t.detach().float().cpu().numpy().astype(np.float64)
+
+
+def rel_err(got, ref):
+    got, ref = np.asarray(got, np.float64), np.asarray(ref, np.float64)
+    den = np.linalg.norm(ref)
+    return np.linalg.norm(got - ref) / (den if den > 0 else 1.0)

@@ -1,0 +1,165 @@
+"""Host-side checks of the C ABI: the library builds and loads, exports every
+entry point that include/ntc.h declares, and its host logic (pyramid rule,
+cell sizes, argument validation) behaves -- no GPU needed: every call here
+returns before any CUDA work is enqueued."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+import oracle
+import paper_2305_17105_gb300 as ntc
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not os.path.exists(ntc.LIB_PATH):
+        ntc.build()
+    return ntc.lib()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "ntc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ntc_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(L):
+    names = _declared()
+    assert "ntc_decode" in names and "ntc_train_step" in names and "ntc_backward" in names
+    for n in names:
+        assert hasattr(L, n), n
+    # and the binding wraps each of them
+    assert set(names) <= set(ntc.SIGNATURES)
+
+
+def test_version(L):
+    assert "sm_103a" in ntc.version()
+
+
+@pytest.mark.parametrize("c,bits", [(8, 4), (12, 4), (16, 4), (8, 2), (12, 2), (20, 4), (3, 4),
+                                    (5, 8), (7, 1), (16, 8)])
+def test_cell_bytes_matches_oracle(L, c, bits):
+    assert ntc.cell_bytes(c, bits) == oracle.cell_bytes(c, bits)
+
+
+def test_cell_bytes_rejects(L):
+    assert ntc.cell_bytes(0, 4) == 0 and ntc.cell_bytes(8, 3) == 0 and ntc.cell_bytes(17, 8) == 0
+
+
+@pytest.mark.parametrize("w,h", [(1, 1), (2, 2), (8, 8), (16, 16), (64, 32), (256, 256),
+                                 (1024, 1024), (2048, 2048), (4096, 4096), (8192, 8192),
+                                 (512, 4096), (32768, 32768)])
+def test_pyramid_matches_oracle(L, w, h):
+    assert ntc.pyramid(w, h) == oracle.pyramid(w, h)
+
+
+def _fake_material(**kw):
+    """A well-formed material struct whose device pointers are fake but
+    aligned: only argument validation may look at it."""
+    m = ntc.ntc_material()
+    m.width = m.height = 64
+    m.channels, m.mips, m.levels = 4, 7, 2
+    m.c0 = m.c1 = 8
+    m.bits0 = m.bits1 = 4
+    m.q0 = m.q1 = 1 / 16
+    m.encoding, m.k_in, m.hidden = ntc.GRID_PACKED, 32, 64
+    m.act, m.out_act, m.precision = 0, 0, ntc.PREC_F32
+    for j in range(2):
+        m.lv[j].g0_w = m.lv[j].g0_h = 16 >> (2 * j)
+        m.lv[j].g1_w = m.lv[j].g1_h = 8 >> (2 * j)
+        m.lv[j].grid0 = m.lv[j].grid1 = 0x10000
+    for l in range(3):
+        m.w[l] = m.b[l] = 0x20000
+    for k, v in kw.items():
+        setattr(m, k, v)
+    return m
+
+
+def _decode_rc(L, m, n=0, uvl=0x30000, out=0x40000, out_dtype=0, filt=0, flags=0):
+    return L.ntc_decode(C.byref(m) if m is not None else None, uvl, n, out, out_dtype, filt, flags,
+                        0, 0, None)
+
+
+def test_valid_material_with_zero_queries_is_a_noop(L):
+    assert _decode_rc(L, _fake_material(), n=0) == ntc.OK
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(width=63), ntc.ERR_SHAPE),
+    (dict(mips=6), ntc.ERR_SHAPE),
+    (dict(channels=17), ntc.ERR_SHAPE),
+    (dict(channels=0), ntc.ERR_SHAPE),
+    (dict(levels=0), ntc.ERR_SHAPE),
+    (dict(levels=9), ntc.ERR_SHAPE),
+    (dict(c0=17), ntc.ERR_SHAPE),
+    (dict(bits0=3), ntc.ERR_ARG),
+    (dict(q1=0.0), ntc.ERR_ARG),
+    (dict(k_in=24), ntc.ERR_SHAPE),       # not a multiple of 16
+    (dict(k_in=16), ntc.ERR_SHAPE),       # < c0 + c1 + 13
+    (dict(k_in=144), ntc.ERR_SHAPE),
+    (dict(hidden=32), ntc.ERR_UNSUPPORTED),
+    (dict(act=5), ntc.ERR_ARG),
+    (dict(out_act=3), ntc.ERR_ARG),
+    (dict(precision=7), ntc.ERR_ARG),
+    (dict(encoding=4), ntc.ERR_ARG),
+])
+def test_material_validation(L, kw, code):
+    assert _decode_rc(L, _fake_material(**kw), n=5) == code
+    assert L.ntc_last_error().decode()
+
+
+def test_pointer_validation(L):
+    assert _decode_rc(L, None, n=5) == ntc.ERR_ARG
+    assert _decode_rc(L, _fake_material(), n=5, uvl=0x30004) == ntc.ERR_ALIGN
+    assert _decode_rc(L, _fake_material(), n=5, out=0) == ntc.ERR_ARG
+    m = _fake_material()
+    m.lv[1].grid1 = 0x10008
+    assert _decode_rc(L, m, n=5) == ntc.ERR_ALIGN
+    assert _decode_rc(L, _fake_material(), n=-1) == ntc.ERR_ARG
+    assert _decode_rc(L, _fake_material(), n=5, out_dtype=9) == ntc.ERR_ARG
+    assert _decode_rc(L, _fake_material(), n=5, filt=9) == ntc.ERR_ARG
+    # noise needs F32 grids
+    assert _decode_rc(L, _fake_material(), n=5, flags=ntc.FLAG_NOISE) == ntc.ERR_ARG
+    # FP8 needs 32-aligned K and a scale pointer
+    assert _decode_rc(L, _fake_material(precision=ntc.PREC_F8, k_in=48), n=5) == ntc.ERR_SHAPE
+    assert _decode_rc(L, _fake_material(precision=ntc.PREC_F8, k_in=64), n=5) == ntc.ERR_ARG
+
+
+def test_train_step_validation(L):
+    m = _fake_material(encoding=ntc.GRID_F32)
+    tr = ntc.ntc_trainer()
+    tg = ntc.ntc_target()
+    loss = C.c_void_p(0x50000)
+    # packed grids are not trainable
+    rc = L.ntc_train_step(C.byref(_fake_material()), C.byref(tr), C.byref(tg), 16, 1, None, loss, 0, None)
+    assert rc == ntc.ERR_ARG
+    # missing trainer buffers
+    rc = L.ntc_train_step(C.byref(m), C.byref(tr), C.byref(tg), 16, 1, None, loss, 0, None)
+    assert rc == ntc.ERR_ARG
+    tr.params = tr.adam_m = tr.adam_v = tr.grad = 0x100000
+    tr.step = 0x200000
+    tg.texels = 0x300000
+    tr.total_steps = 10
+    for l in range(3):
+        tr.w_master[l] = 0x20000
+    tr.n_params = 16
+    # grids do not lie inside params
+    rc = L.ntc_train_step(C.byref(m), C.byref(tr), C.byref(tg), 16, 1, None, loss, 0, None)
+    assert rc == ntc.ERR_ARG and "params" in L.ntc_last_error().decode()
+    rc = L.ntc_train_step(C.byref(m), C.byref(tr), C.byref(tg), 0, 1, None, loss, 0, None)
+    assert rc == ntc.ERR_ARG
+
+
+def test_quantize_and_sampler_validation(L):
+    assert L.ntc_quantize_pack(0x1000, 10, 8, 3, 0.0625, 0x2000, None, None) == ntc.ERR_ARG
+    assert L.ntc_quantize_pack(0x1000, 10, 8, 4, 0.0, 0x2000, None, None) == ntc.ERR_ARG
+    assert L.ntc_quantize_pack(0x1004, 10, 8, 4, 0.0625, 0x2000, None, None) == ntc.ERR_ALIGN
+    assert L.ntc_quantize_pack(0x1000, 0, 8, 4, 0.0625, 0x2000, None, None) == ntc.OK
+    assert L.ntc_unpack(0x1000, 10, 8, 4, 0.0625, 0x2004, None, None) == ntc.ERR_ALIGN
+    assert L.ntc_sample_batch(1, 0, 10, 48, 64, 7, 0x1000, None) == ntc.ERR_ARG
+    assert L.ntc_sample_batch(1, 0, 10, 64, 64, 17, 0x1000, None) == ntc.ERR_ARG
+    assert L.ntc_sample_batch(1, 0, 0, 64, 64, 7, 0x1000, None) == ntc.OK
