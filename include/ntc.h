@@ -154,6 +154,13 @@ const char* ntc_version(void);
 /* Message of the last failing call on this thread (static, thread-local). */
 const char* ntc_last_error(void);
 
+/* Synchronises the current device, then returns NTC_OK or the error that a
+ * kernel recorded in the library's device status word since the last reset:
+ * NTC_ERR_TIMEOUT when a bounded wait of a tensor-core kernel (TMEM
+ * allocation, MMA completion) gave up -- that launch's outputs are then
+ * incomplete.  reset != 0 clears the word.  The only call that synchronises. */
+int ntc_device_status(int32_t reset);
+
 /* Bytes of one packed grid cell for c features of `bits` bits: c*bits bits
  * rounded up to a power-of-two number of bytes.  Channel ch occupies bits
  * [ch*bits, (ch+1)*bits) counting from bit 0 of byte 0.  0 on bad input. */

@@ -87,6 +87,7 @@ SIGNATURES = {
     "ntc_unpack": (C.c_int, [_P, _I64, _I32, _I32, _F, _P, _P, _P]),
     "ntc_sample_batch": (C.c_int, [_U64, _I64, _I64, _I32, _I32, _I32, _P, _P]),
     "ntc_sample_features": (C.c_int, [_P, _P, _I64, _P, _I32, _U64, _I64, _P]),
+    "ntc_device_status": (C.c_int, [_I32]),
 }
 
 _lib = None
@@ -94,8 +95,8 @@ _lib = None
 
 def build(force: bool = False, verbose: bool = False) -> str:
     """Compile libntc.so for sm_103a (nvcc) next to this file."""
-    from . import build as _b
-    return _b.build(force=force, verbose=verbose)
+    from . import build_ext
+    return build_ext.build(force=force, verbose=verbose)
 
 
 def lib():
@@ -140,6 +141,12 @@ def _dev(t: torch.Tensor, name: str):
 # ----------------------------------------------------------------------------
 # small host helpers
 # ----------------------------------------------------------------------------
+def ntc_device_status(reset: bool = True) -> int:
+    """Synchronise the device and return (and clear) the status word that
+    bounded device-side waits set on timeout (OK or ERR_TIMEOUT)."""
+    return int(lib().ntc_device_status(1 if reset else 0))
+
+
 def version() -> str:
     return lib().ntc_version().decode()
 

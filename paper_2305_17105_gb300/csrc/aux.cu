@@ -17,6 +17,35 @@ int sm_count() {
 }
 
 namespace {
+__device__ int g_status_word;
+}  // namespace
+
+int* status_word() {
+  static int* ptr[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  if (!ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_status_word) != cudaSuccess) return nullptr;
+    ptr[dev] = static_cast<int*>(p);
+  }
+  return ptr[dev];
+}
+
+int read_status_word(int reset) {
+  int* p = status_word();
+  if (!p) return -1;
+  int v = 0;
+  if (cudaDeviceSynchronize() != cudaSuccess) return -1;
+  if (cudaMemcpy(&v, p, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+  if (reset && v != 0) {
+    const int z = 0;
+    if (cudaMemcpy(p, &z, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) return -1;
+  }
+  return v;
+}
+
+namespace {
 
 // One Adam step (Kingma & Ba, bias-corrected) at the device step counter t,
 // learning rate lr0 (1 + cos(pi t / T)) / 2 per group, then the grid clamp

@@ -101,6 +101,13 @@ const char* ntc_version(void) { return "ntc-gb300 0.1 (sm_103a)"; }
 
 const char* ntc_last_error(void) { return g_err; }
 
+int ntc_device_status(int32_t reset) {
+  const int v = ntc::read_status_word(reset);
+  if (v < 0) return fail(NTC_ERR_CUDA, "device status: %s", cudaGetErrorString(cudaGetLastError()));
+  if (v == NTC_ERR_TIMEOUT) return fail(NTC_ERR_TIMEOUT, "a device-side wait timed out");
+  return v == 0 ? NTC_OK : fail(v, "device status %d", v);
+}
+
 int32_t ntc_cell_bytes(int32_t c, int32_t bits) {
   if (c < 1 || c > 64 || (bits != 1 && bits != 2 && bits != 4 && bits != 8) || c * bits > 128)
     return 0;

@@ -79,4 +79,9 @@ cudaError_t launch_sample_features(const ntc_material& m, const float* uvl, int6
 
 int sm_count();
 
+// Device status word of the current device (bounded waits write
+// NTC_ERR_TIMEOUT there); read and cleared by ntc_device_status.
+int* status_word();
+int read_status_word(int reset);  // synchronises the device; -1 on CUDA error
+
 }  // namespace ntc
