@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="auto", choices=["auto", "f32", "f16", "f8"])
+    ap.add_argument("--train-precision", default="f32", choices=["f32", "f16"])
     ap.add_argument("--queries", type=int, default=1 << 24)
     ap.add_argument("--batch", type=int, default=1 << 18)
     ap.add_argument("--cpu-seconds", type=float, default=8.0,
@@ -304,7 +305,7 @@ def main():
     precision = args.precision
     if precision == "auto":
         precision = os.environ.get("NTC_BENCH_PRECISION", "f16")
-    train_prec = "f16" if precision in ("f16", "f8") else "f32"
+    train_prec = args.train_precision
     dev = "cuda"
     stream = torch.cuda.current_stream()
 
@@ -324,6 +325,10 @@ def main():
     def train():
         ntc.ntc_train_step(tr, target, args.batch, seed)
 
+    tuning = None
+    if precision != "f32":
+        best, ms = ntc.ntc_autotune_decode(mat, q_dev, out)
+        tuning = {"decode_warpgroups": best, "ms_per_shape": ms}
     for _ in range(args.warmup):
         decode()
         train()
@@ -444,7 +449,7 @@ def main():
                    "parallelism": f"replicas x{world}"},
         "train_samples_per_s": train_rate, "train_loss": loss,
         "decode_ms": statistics.median(dec_ms), "train_ms": statistics.median(trn_ms),
-        "roofline": roof, "e2e": e2e, "fp32_path": fp32, "cpu_baseline": cpu,
+        "roofline": roof, "tuning": tuning, "e2e": e2e, "fp32_path": fp32, "cpu_baseline": cpu,
         "gpu_launches": kernels_per_step * args.steps,
         "clocks": clk.summary(), "wall_s": t_wall,
     }

@@ -190,6 +190,20 @@ int ntc_decode(const ntc_material* m, const float* uvl, int64_t n, void* out,
                int32_t out_dtype, int32_t filter, int32_t flags, uint64_t noise_seed,
                int64_t noise_step, void* stream);
 
+/* Launch shape of the tensor-core decode: warpgroup tile pipelines per CTA
+ * (one CTA per SM), 4, 6 or 8; 0 restores the default.  Process-wide; takes
+ * effect for later ntc_decode calls. */
+int ntc_set_decode_warpgroups(int32_t nwg);
+
+/* Autotuner of the tensor-core decode: times every launch shape (1 warm-up
+ * + 3 timed launches each, CUDA events on `stream`) on the caller's queries
+ * (writing `out`), selects the fastest as ntc_set_decode_warpgroups would,
+ * and returns it in *best (host).  ms_out (host, nullable) receives the
+ * mean time per launch of the shapes 4, 6, 8.  Synchronises the stream. */
+int ntc_autotune_decode(const ntc_material* m, const float* uvl, int64_t n, void* out,
+                        int32_t out_dtype, int32_t filter, int32_t* best, float* ms_out,
+                        void* stream);
+
 /* Gradient of sum_i sum_c dout[i][c] * y[i][c] for nearest decodes y of the
  * queries uvl (Sec. 4.5, reverse mode of ntc_decode), ACCUMULATED into g.
  * Requires NTC_GRID_F32 grids.  With NTC_FLAG_NOISE the forward uses the

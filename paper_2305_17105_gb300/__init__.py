@@ -88,6 +88,8 @@ SIGNATURES = {
     "ntc_sample_batch": (C.c_int, [_U64, _I64, _I64, _I32, _I32, _I32, _P, _P]),
     "ntc_sample_features": (C.c_int, [_P, _P, _I64, _P, _I32, _U64, _I64, _P]),
     "ntc_device_status": (C.c_int, [_I32]),
+    "ntc_set_decode_warpgroups": (C.c_int, [_I32]),
+    "ntc_autotune_decode": (C.c_int, [_P, _P, _I64, _P, _I32, _I32, _P, _P, _P]),
 }
 
 _lib = None
@@ -242,6 +244,22 @@ def ntc_decode(mat: Material, uvl: torch.Tensor, out_dtype=torch.float32,
     _call("ntc_decode", C.byref(s), _ptr(uvl), n, _ptr(out), dt, filter, flags, noise_seed,
           noise_step, _stream(stream))
     return out
+
+
+def ntc_set_decode_warpgroups(nwg: int) -> None:
+    _call("ntc_set_decode_warpgroups", nwg)
+
+
+def ntc_autotune_decode(mat: Material, uvl, out, filter=FILTER_NEAREST, stream=None):
+    """Pick the fastest tensor-core launch shape on these queries; returns
+    (best warpgroups, {shape: ms per launch})."""
+    best = C.c_int32(0)
+    ms = (C.c_float * 3)()
+    dt = DTYPE_F16 if out.dtype == torch.float16 else DTYPE_F32
+    s = mat.struct
+    _call("ntc_autotune_decode", C.byref(s), _ptr(uvl), uvl.shape[0], _ptr(out), dt, filter,
+          C.byref(best), C.cast(ms, C.c_void_p), _stream(stream))
+    return best.value, {4: ms[0], 6: ms[1], 8: ms[2]}
 
 
 def grads_struct(mat: Material, grid0=None, grid1=None, w=None, b=None) -> ntc_grads:

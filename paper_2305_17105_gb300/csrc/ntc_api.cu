@@ -1,5 +1,6 @@
 // C-ABI entry points of libntc.so (declared in include/ntc.h): argument
 // validation, error reporting and dispatch to the kernels.
+#include <atomic>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -89,6 +90,8 @@ int check_material(const ntc_material* m, bool need_f32_grids) {
   return NTC_OK;
 }
 
+std::atomic<int> g_decode_nwg{0};  // tensor-core decode warpgroups per CTA (0 = default)
+
 bool use_simt(const ntc_material* m, int flags) {
   return (flags & NTC_FLAG_SIMT) || m->precision == NTC_PREC_F32;
 }
@@ -151,8 +154,52 @@ int ntc_decode(const ntc_material* m, const float* uvl, int64_t n, void* out, in
                                                (flags & NTC_FLAG_NOISE) != 0, noise_seed,
                                                noise_step, s),
                        "decode (FP32 CUDA cores)");
-  return cuda_status(ntc::launch_decode_tc(*m, uvl, n, out, out_dtype, filter, s, 0),
+  return cuda_status(ntc::launch_decode_tc(*m, uvl, n, out, out_dtype, filter, s, g_decode_nwg.load()),
                      "decode (tcgen05)");
+}
+
+int ntc_set_decode_warpgroups(int32_t nwg) {
+  if (nwg != 0 && nwg != 4 && nwg != 6 && nwg != 8) return fail(NTC_ERR_ARG, "warpgroups %d", nwg);
+  g_decode_nwg.store(nwg);
+  return NTC_OK;
+}
+
+int ntc_autotune_decode(const ntc_material* m, const float* uvl, int64_t n, void* out,
+                        int32_t out_dtype, int32_t filter, int32_t* best, float* ms_out,
+                        void* stream) {
+  if (!best) return fail(NTC_ERR_ARG, "best is NULL");
+  int st = check_material(m, false);
+  if (st) return st;
+  if (m->precision == NTC_PREC_F32) return fail(NTC_ERR_ARG, "the FP32 form has no launch shapes");
+  if (n <= 0) return fail(NTC_ERR_ARG, "n must be positive");
+  CHECK_PTR(uvl, "uvl");
+  CHECK_PTR(out, "out");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int shapes[3] = {4, 6, 8};
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return cuda_status(cudaGetLastError(), "autotune events");
+  float best_ms = 1e30f;
+  int best_nwg = 0, rc = NTC_OK;
+  for (int i = 0; i < 3 && rc == NTC_OK; ++i) {
+    cudaError_t e = ntc::launch_decode_tc(*m, uvl, n, out, out_dtype, filter, s, shapes[i]);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+    for (int r = 0; r < 3 && e == cudaSuccess; ++r)
+      e = ntc::launch_decode_tc(*m, uvl, n, out, out_dtype, filter, s, shapes[i]);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) rc = cuda_status(e, "autotune");
+    if (ms_out) ms_out[i] = ms / 3.f;
+    if (ms < best_ms) { best_ms = ms; best_nwg = shapes[i]; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != NTC_OK) return rc;
+  g_decode_nwg.store(best_nwg);
+  *best = best_nwg;
+  return NTC_OK;
 }
 
 int ntc_backward(const ntc_material* m, const float* uvl, int64_t n, const float* dout,

@@ -1,26 +1,35 @@
 // Tensor-core (tcgen05) random-access decode, FP16 or FP8-E4M3 operands with
 // FP32 accumulation in TMEM (Sec. 4.3-4.4, 5.2-5.3).
 //
-// Persistent CTAs of 128 threads; a tile is 128 MLP rows (one query per row,
-// or for trilinear filtering 16 queries x 8 texel taps).  Per tile:
-//   1. every thread gathers and dequantises its row's latent features, adds
-//      the positional encoding and LOD, and writes the row into the A tile
-//      (canonical K-major layout in shared memory);
-//   2. one thread issues layer 1 (M=128, N=64) into TMEM and commits to an
-//      mbarrier; every thread waits, loads its accumulator row with
-//      tcgen05.ld, applies the activation and writes the hidden row back as
-//      the next A tile;
+// One persistent CTA per SM runs NWG independent warpgroup pipelines that
+// share one copy of the weights.  A warpgroup owns a stream of tiles of 128
+// MLP rows (one query per row, or for trilinear filtering 16 queries x 8
+// texel taps), one activation tile in shared memory, one mbarrier and 64
+// TMEM columns.  Per tile:
+//   1. every thread gathers the 8 cells of its texel (4 bilinear taps x 2
+//      grids), dequantises, interpolates, appends the positional encoding
+//      and the LOD, and writes the row into the activation tile (canonical
+//      K-major layout);
+//   2. one thread issues layer 1 (M=128, N=64) into TMEM and commits to the
+//      mbarrier; the warpgroup waits, loads its accumulator rows with
+//      tcgen05.ld, applies the activation and writes the hidden rows back
+//      into the same tile (the MMA that read it has completed);
 //   3. likewise layer 2 (N=64) and layer 3 (N=16), whose epilogue applies the
 //      output activation and stores the texel.
-// Several CTAs per SM overlap one CTA's gathers with another's MMAs.
+// While one warpgroup waits on its MMAs the others gather and convert, so the
+// tensor pipe and the CUDA cores overlap.
 //
-// The MLP input row is stored in an internal slot order that keeps every
-// 8-slot group register-resident: [G0 | pad][G1 | pad][12 PE, LOD, 0, 1, 1]
-// [0 ...]; W1's columns are permuted to match when staged.  For FP16 the
-// biases ride on the tensor core: layer 1 through two constant-one slots
-// (bias split into an FP16 head and tail), layers 2 and 3 through one extra
-// K=16 block of a constant tile.  For FP8 each layer's epilogue applies
-// (s_w * s_a) * acc + b in FP32.
+// Internal input-slot order (W1's columns are permuted to match when
+// staged): [G0 groups][G1 groups][12 PE, LOD, 0, 1, 1][0 ...], 8 slots per
+// group.  With 4-bit packed grids and FP16 operands each 32-bit word of a
+// cell holds 8 channels; one LOP3 per channel pair turns nibbles i and i+4
+// into the half2 (1024 + q_i, 1024 + q_{i+4}), so a group stores channels
+// in the order 0,4,1,5,2,6,3,7.  For FP16 the biases ride on the tensor
+// core: layer 1 through two constant-one slots (bias split into an FP16 head
+// and tail), layers 2 and 3 through one extra K=16 block of a constant tile.
+// For FP8 each layer's epilogue applies (s_w * s_a) * acc + b in FP32.
+#include <cuda_fp16.h>
+
 #include "ntc_device.cuh"
 #include "ntc_internal.h"
 #include "tc_ptx.cuh"
@@ -39,43 +48,77 @@ struct Cfg {
   static constexpr int KSTEP = F8 ? 32 : 16;  // K per MMA instruction
 };
 
-// Shared memory plan (bytes from a 1024-aligned base).
+// Per-mip constants of a material (shared memory).
+struct MipInfo {
+  int wm, hm, level, pad;
+  float sx0, sy0, sx1, sy1;  // grid / mip resolution ratios (exact for powers of two)
+  float lodn;                // m / (M - 1)
+  float pad2[3];
+};
+
+// Shared memory plan (byte offsets).
 struct Plan {
-  int k_int;                     // internal MLP input width
-  int ng0, ng1;                  // 8-slot groups of G0 / G1
-  uint32_t x, h, cst, w1, w2, w3, wb2, wb3, bias, total;
-  __host__ __device__ Plan(int c0, int c1, bool f8) {
+  int k_int;                 // internal MLP input width
+  int ng0, ng1;              // 8-slot groups of G0 / G1
+  uint32_t w1, w2, w3, wb2, wb3, cst, bias, mip, pe_a, pe_b, act, act_bytes, total;
+  __host__ __device__ Plan(int c0, int c1, bool f8, int nwg) {
     const int eb = f8 ? 1 : 2, kstep = f8 ? 32 : 16;
     ng0 = (c0 + 7) / 8;
     ng1 = (c1 + 7) / 8;
     const int slots = 8 * (ng0 + ng1 + 2);
     k_int = (slots + kstep - 1) / kstep * kstep;
     uint32_t o = 0;
-    x = o;   o += kRows * k_int * eb;      // A: input rows
-    h = o;   o += kRows * kHidden * eb;    // A: hidden rows
-    cst = o; o += f8 ? 0 : kRows * 16 * 2; // A: constant-one block (FP16)
-    w1 = o;  o += kHidden * k_int * eb;    // B: W1 (internal slot order)
-    w2 = o;  o += kHidden * kHidden * eb;  // B: W2
-    w3 = o;  o += kN3 * kHidden * eb;      // B: W3 (rows >= C zero)
-    wb2 = o; o += f8 ? 0 : kHidden * 16 * 2;  // B: bias block of layer 2 (FP16)
-    wb3 = o; o += f8 ? 0 : kN3 * 16 * 2;      // B: bias block of layer 3 (FP16)
-    bias = o; o += (2 * kHidden + kN3) * 4;   // FP32 biases (FP8 epilogues)
+    w1 = o;   o += kHidden * k_int * eb;          // B: W1 (internal slot order)
+    w2 = o;   o += kHidden * kHidden * eb;        // B: W2
+    w3 = o;   o += kN3 * kHidden * eb;            // B: W3 (rows >= C zero)
+    wb2 = o;  o += f8 ? 0 : kHidden * 16 * 2;     // B: bias block of layer 2 (FP16)
+    wb3 = o;  o += f8 ? 0 : kN3 * 16 * 2;         // B: bias block of layer 3 (FP16)
+    cst = o;  o += f8 ? 0 : kRows * 16 * 2;       // A: constant-one block (FP16)
+    bias = o; o += (2 * kHidden + kN3) * 4;       // FP32 biases (FP8 epilogues)
+    mip = o;  o += NTC_MAX_MIPS * sizeof(MipInfo);
+    pe_a = o; o += 64 * 16;                       // PE group 0 per (x&7, y&7), FP16
+    pe_b = o; o += 8 * 8;                         // PE y-values 2..5 per y&7, FP16
+    o = (o + 127) / 128 * 128;
+    act = o;
+    act_bytes = kRows * (k_int > kHidden ? k_int : kHidden) * eb;  // X, H1, H2 alias
+    o += act_bytes * nwg;
     total = o;
   }
 };
 
-struct Smem {
-  uint64_t mbar;
-  uint32_t tmem;
-  int abort;
-};
+__device__ __forceinline__ uint32_t h2u(__half2 h) {
+  union { __half2 h; uint32_t u; } c;
+  c.h = h;
+  return c.u;
+}
+__device__ __forceinline__ __half2 u2h(uint32_t u) {
+  union { __half2 h; uint32_t u; } c;
+  c.u = u;
+  return c.h;
+}
+
+// Packed 4-bit cells feed the half2 fast path (FP16 operands only).
+__device__ __forceinline__ bool fast_grid(const ntc_material& M, int k, bool f8) {
+  return !f8 && M.encoding == NTC_GRID_PACKED && (k ? M.bits1 : M.bits0) == 4;
+}
+
+// Channel held by slot e (0..7) of a grid's group g.
+__device__ __forceinline__ int slot_channel(bool fast, int g, int e) {
+  return fast ? 8 * g + (e & 1) * 4 + (e >> 1) : 8 * g + e;
+}
 
 // User column of internal input slot s: >= 0 a W1 column, -1 zero padding,
 // -2 / -3 the constant-one slots carrying the FP16 bias head / tail.
 __device__ __forceinline__ int w1_column(const ntc_material& M, const Plan& P, int s, bool f8) {
   const int g0 = 8 * P.ng0, g1 = 8 * P.ng1;
-  if (s < g0) return s < M.c0 ? s : -1;
-  if (s < g0 + g1) return (s - g0) < M.c1 ? M.c0 + (s - g0) : -1;
+  if (s < g0) {
+    const int ch = slot_channel(fast_grid(M, 0, f8), s >> 3, s & 7);
+    return ch < M.c0 ? ch : -1;
+  }
+  if (s < g0 + g1) {
+    const int ch = slot_channel(fast_grid(M, 1, f8), (s - g0) >> 3, (s - g0) & 7);
+    return ch < M.c1 ? M.c0 + ch : -1;
+  }
   const int e = s - g0 - g1;
   if (e < 13) return M.c0 + M.c1 + e;
   if (!f8 && e == 14) return -2;
@@ -90,10 +133,9 @@ __device__ __forceinline__ void split_bias(float b, __half& hd, __half& tl) {
 }
 
 template <bool F8>
-__device__ void stage_weights_tc(const ntc_material& M, const Plan& P, uint8_t* sm) {
+__device__ void stage_shared(const ntc_material& M, const Plan& P, uint8_t* sm) {
   const int tid = threadIdx.x, nt = blockDim.x;
   constexpr int EB = Cfg<F8>::EB;
-  // W1 [64][k_int] in internal slot order
   for (int i = tid; i < kHidden * P.k_int; i += nt) {
     const int n = i / P.k_int, s = i - n * P.k_int;
     const int col = w1_column(M, P, s, F8);
@@ -112,7 +154,6 @@ __device__ void stage_weights_tc(const ntc_material& M, const Plan& P, uint8_t* 
       *reinterpret_cast<__half*>(sm + off) = hv;
     }
   }
-  // W2 [64][64], W3 [16][64]
   for (int i = tid; i < kHidden * kHidden; i += nt) {
     const int n = i / kHidden, k = i - n * kHidden;
     const uint32_t off = P.w2 + tc::canon_offset(n, k, kHidden, EB);
@@ -134,7 +175,6 @@ __device__ void stage_weights_tc(const ntc_material& M, const Plan& P, uint8_t* 
   }
   for (int i = tid; i < kN3; i += nt) bias[2 * kHidden + i] = i < M.channels ? M.b[2][i] : 0.f;
   if (!F8) {
-    // constant-one A block [128][16]: columns 0 and 1 = 1; bias B blocks
     for (int i = tid; i < kRows * 16; i += nt) {
       const int r = i / 16, k = i - r * 16;
       *reinterpret_cast<__half*>(sm + P.cst + tc::canon_offset(r, k, kRows, 2)) =
@@ -154,6 +194,41 @@ __device__ void stage_weights_tc(const ntc_material& M, const Plan& P, uint8_t* 
       *reinterpret_cast<__half*>(sm + P.wb3 + tc::canon_offset(n, k, kN3, 2)) =
           k == 0 ? hd : (k == 1 ? tl : __float2half_rn(0.f));
     }
+  }
+  // per-mip table
+  MipInfo* mi = reinterpret_cast<MipInfo*>(sm + P.mip);
+  for (int m = tid; m < M.mips; m += nt) {
+    MipInfo t;
+    t.wm = mip_dim(M.width, m);
+    t.hm = mip_dim(M.height, m);
+    t.level = level_of_mip(m, M.levels);
+    t.pad = 0;
+    const ntc_level& L = M.lv[t.level];
+    t.sx0 = (float)L.g0_w / (float)t.wm;
+    t.sy0 = (float)L.g0_h / (float)t.hm;
+    t.sx1 = (float)L.g1_w / (float)t.wm;
+    t.sy1 = (float)L.g1_h / (float)t.hm;
+    t.lodn = M.mips > 1 ? (float)m / (float)(M.mips - 1) : 0.f;
+    t.pad2[0] = t.pad2[1] = t.pad2[2] = 0.f;
+    mi[m] = t;
+  }
+  // positional-encoding tables (values are dyadic: exact in FP16)
+  struct Pe {
+    float v[16];
+    __device__ void operator()(int i, float x) { v[i] = x; }
+  };
+  for (int i = tid; i < 64; i += nt) {
+    Pe pe;
+    positional_encoding(i & 7, i >> 3, 0, pe);
+    uint4 w;
+    w.x = tc::pack_f16x2(pe.v[0], pe.v[1]);
+    w.y = tc::pack_f16x2(pe.v[2], pe.v[3]);
+    w.z = tc::pack_f16x2(pe.v[4], pe.v[5]);
+    w.w = tc::pack_f16x2(pe.v[6], pe.v[7]);
+    reinterpret_cast<uint4*>(sm + P.pe_a)[i] = w;
+    if ((i & 7) == 0)
+      reinterpret_cast<uint2*>(sm + P.pe_b)[i >> 3] =
+          make_uint2(tc::pack_f16x2(pe.v[8], pe.v[9]), tc::pack_f16x2(pe.v[10], pe.v[11]));
   }
 }
 
@@ -179,56 +254,153 @@ __device__ __forceinline__ void put_group(uint8_t* tile, int row, int g, const f
   }
 }
 
-struct PeSink {
-  float v[16];
-  __device__ __forceinline__ void operator()(int i, float x) { v[i] = x; }
-};
+__device__ __forceinline__ void taps_of(int x, int y, float sx, float sy, int gw, int gh, Taps& t) {
+  const float px = ((float)x + 0.5f) * sx - 0.5f;
+  const float py = ((float)y + 0.5f) * sy - 0.5f;
+  const float fx0 = floorf(px), fy0 = floorf(py);
+  const float fx = px - fx0, fy = py - fy0;
+  int ix0 = (int)fx0, iy0 = (int)fy0;
+  const int ix1 = min(max(ix0 + 1, 0), gw - 1), iy1 = min(max(iy0 + 1, 0), gh - 1);
+  ix0 = min(max(ix0, 0), gw - 1);
+  iy0 = min(max(iy0, 0), gh - 1);
+  t.cell[0] = iy0 * gw + ix0; t.w[0] = (1.f - fx) * (1.f - fy);
+  t.cell[1] = iy0 * gw + ix1; t.w[1] = fx * (1.f - fy);
+  t.cell[2] = iy1 * gw + ix0; t.w[2] = (1.f - fx) * fy;
+  t.cell[3] = iy1 * gw + ix1; t.w[3] = fx * fy;
+}
 
-// Gather, dequantise and encode one texel into the A tile (internal order).
+// Half2 dequantise + bilinear of 4-bit cells: group g of the grid from the
+// 32-bit words g of the four tap cells.
+__device__ __forceinline__ void fast_group(const Cell (&cl)[4], const Taps& t, int g, float q,
+                                           int off, uint8_t* tile, int row, int kg) {
+  const __half2 bias1024 = __float2half2_rn(1024.f);
+  __half2 acc[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) acc[i] = __float2half2_rn(0.f);
+#pragma unroll
+  for (int tp = 0; tp < 4; ++tp) {
+    const uint32_t w = g == 0 ? (uint32_t)cl[tp].lo : (uint32_t)(cl[tp].lo >> 32);
+    const __half2 wt = __float2half2_rn(t.w[tp]);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const uint32_t h = tc::lop3_and_or(w >> (4 * i), 0x000F000Fu, 0x64006400u);
+      acc[i] = __hfma2(wt, __hsub2(u2h(h), bias1024), acc[i]);
+    }
+  }
+  const __half2 q2 = __float2half2_rn(q), o2 = __float2half2_rn(-(float)off * q);
+  uint4 out;
+  out.x = h2u(__hfma2(acc[0], q2, o2));
+  out.y = h2u(__hfma2(acc[1], q2, o2));
+  out.z = h2u(__hfma2(acc[2], q2, o2));
+  out.w = h2u(__hfma2(acc[3], q2, o2));
+  *reinterpret_cast<uint4*>(tile + tc::canon_chunk(row, kg, kRows)) = out;
+}
+
+// Float path of one grid (other bit widths, F32 grids, FP8 operands).
 template <bool F8>
-__device__ __forceinline__ void feature_row(const ntc_material& M, const Plan& P, uint8_t* tile,
-                                            int row, int x, int y, int m, bool valid,
-                                            float inv_sa) {
+__device__ __forceinline__ void float_grid(const ntc_material& M, int j, int k, const Taps& t,
+                                           const Cell (&cl)[4], int ng, uint8_t* tile, int row,
+                                           int kg0, float inv_sa) {
+  const int c = k ? M.c1 : M.c0;
+  const float q = k ? M.q1 : M.q0;
+  float acc[kMaxGridCh];
+#pragma unroll
+  for (int ch = 0; ch < kMaxGridCh; ++ch) acc[ch] = 0.f;
+  if (M.encoding == NTC_GRID_PACKED) {
+    const int bits = k ? M.bits1 : M.bits0;
+    const int off = (1 << (bits - 1)) - 1;
+#pragma unroll
+    for (int tp = 0; tp < 4; ++tp)
+#pragma unroll
+      for (int ch = 0; ch < kMaxGridCh; ++ch)
+        if (ch < c)
+          acc[ch] = fmaf(t.w[tp], (float)((int)cell_index(cl[tp], ch, bits) - off) * q, acc[ch]);
+  } else {
+    const float* base = static_cast<const float*>(k ? M.lv[j].grid1 : M.lv[j].grid0);
+#pragma unroll
+    for (int tp = 0; tp < 4; ++tp) {
+      const float* g = base + (size_t)t.cell[tp] * c;
+#pragma unroll
+      for (int ch = 0; ch < kMaxGridCh; ++ch)
+        if (ch < c) acc[ch] = fmaf(t.w[tp], __ldg(g + ch), acc[ch]);
+    }
+  }
+#pragma unroll
+  for (int g = 0; g < 2; ++g)
+    if (g < ng) {
+      float v[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) v[e] = acc[8 * g + e];
+      put_group<F8>(tile, row, kg0 + g, v, inv_sa);
+    }
+}
+
+// Gather, dequantise, interpolate and encode one texel into row `row`.
+template <bool F8>
+__device__ __forceinline__ void feature_row(const ntc_material& M, const Plan& P,
+                                            const uint8_t* sm, uint8_t* tile, int row, int x,
+                                            int y, int m, bool valid, float inv_sa) {
   const int groups = P.k_int / 8;
   if (!valid) {
     const float z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int g = 0; g < groups; ++g) put_group<F8>(tile, row, g, z, 1.f);
     return;
   }
-  const int j = level_of_mip(m, M.levels);
-  const int wm = mip_dim(M.width, m), hm = mip_dim(M.height, m);
-  GridSample gs;
+  const MipInfo mi = reinterpret_cast<const MipInfo*>(sm + P.mip)[m];
+  const int j = mi.level;
+  const ntc_level& L = M.lv[j];
+  Taps t0, t1;
+  taps_of(x, y, mi.sx0, mi.sy0, L.g0_w, L.g0_h, t0);
+  taps_of(x, y, mi.sx1, mi.sy1, L.g1_w, L.g1_h, t1);
+  // issue all eight cell loads before using any
+  Cell c0[4], c1[4];
+  if (M.encoding == NTC_GRID_PACKED) {
+    const int cb0 = cell_bytes(M.c0, M.bits0), cb1 = cell_bytes(M.c1, M.bits1);
+    const uint8_t* b0 = static_cast<const uint8_t*>(L.grid0);
+    const uint8_t* b1 = static_cast<const uint8_t*>(L.grid1);
 #pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    sample_grid(M, j, k, x, y, wm, hm, false, 0, gs);
-    const int base = k ? P.ng0 : 0, ng = k ? P.ng1 : P.ng0;
-#pragma unroll
-    for (int g = 0; g < 2; ++g)
-      if (g < ng) {
-        float v[8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) v[e] = gs.acc[8 * g + e];
-        put_group<F8>(tile, row, base + g, v, inv_sa);
-      }
-  }
-  PeSink pe;
-  positional_encoding(x, y, 0, pe);
-  pe.v[12] = M.mips > 1 ? (float)m / (float)(M.mips - 1) : 0.f;
-  pe.v[13] = 0.f;
-  pe.v[14] = F8 ? 0.f : 1.f;
-  pe.v[15] = F8 ? 0.f : 1.f;
-  const int gp = P.ng0 + P.ng1;
-  float v[8];
-#pragma unroll
-  for (int e = 0; e < 8; ++e) v[e] = pe.v[e];
-  put_group<F8>(tile, row, gp, v, inv_sa);
-#pragma unroll
-  for (int e = 0; e < 8; ++e) v[e] = pe.v[8 + e];
-  if (F8) {
-    // the constant-one slots are FP16-only; scale the LOD group like the rest
-    put_group<F8>(tile, row, gp + 1, v, inv_sa);
+    for (int tp = 0; tp < 4; ++tp) {
+      c0[tp] = load_cell(b0, t0.cell[tp], cb0);
+      c1[tp] = load_cell(b1, t1.cell[tp], cb1);
+    }
   } else {
-    put_group<F8>(tile, row, gp + 1, v, 1.f);
+#pragma unroll
+    for (int tp = 0; tp < 4; ++tp) c0[tp] = c1[tp] = Cell{0, 0};
+  }
+  if (fast_grid(M, 0, F8)) {
+    fast_group(c0, t0, 0, M.q0, 7, tile, row, 0);
+    if (P.ng0 > 1) fast_group(c0, t0, 1, M.q0, 7, tile, row, 1);
+  } else {
+    float_grid<F8>(M, j, 0, t0, c0, P.ng0, tile, row, 0, inv_sa);
+  }
+  if (fast_grid(M, 1, F8)) {
+    fast_group(c1, t1, 0, M.q1, 7, tile, row, P.ng0);
+    if (P.ng1 > 1) fast_group(c1, t1, 1, M.q1, 7, tile, row, P.ng0 + 1);
+  } else {
+    float_grid<F8>(M, j, 1, t1, c1, P.ng1, tile, row, P.ng0, inv_sa);
+  }
+  const int gp = P.ng0 + P.ng1;
+  if (!F8) {
+    const uint4 a = reinterpret_cast<const uint4*>(sm + P.pe_a)[(x & 7) | ((y & 7) << 3)];
+    const uint2 b = reinterpret_cast<const uint2*>(sm + P.pe_b)[y & 7];
+    *reinterpret_cast<uint4*>(tile + tc::canon_chunk(row, gp, kRows)) = a;
+    *reinterpret_cast<uint4*>(tile + tc::canon_chunk(row, gp + 1, kRows)) =
+        make_uint4(b.x, b.y, tc::pack_f16x2(mi.lodn, 0.f), tc::pack_f16x2(1.f, 1.f));
+  } else {
+    struct Pe {
+      float v[16];
+      __device__ void operator()(int i, float x) { v[i] = x; }
+    } pe;
+    positional_encoding(x, y, 0, pe);
+    float v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = pe.v[e];
+    put_group<F8>(tile, row, gp, v, inv_sa);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) v[e] = pe.v[8 + e];
+    v[4] = mi.lodn;
+    v[5] = v[6] = v[7] = 0.f;
+    put_group<F8>(tile, row, gp + 1, v, inv_sa);
   }
   const float z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   for (int g = gp + 2; g < groups; ++g) put_group<F8>(tile, row, g, z, 1.f);
@@ -274,36 +446,39 @@ __device__ __forceinline__ void hidden_epilogue(uint32_t tmem_row, uint8_t* htil
   }
 }
 
-template <bool F8>
-__global__ void __launch_bounds__(kRows) decode_tc_kernel(const ntc_material M,
-                                                          const float* __restrict__ uvl, int64_t n,
-                                                          void* __restrict__ out, int out_dtype,
-                                                          int filter, int* status) {
+template <bool F8, int NWG>
+__global__ void __launch_bounds__(kRows* NWG, 1) decode_tc_kernel(
+    const ntc_material M, const float* __restrict__ uvl, int64_t n, void* __restrict__ out,
+    int out_dtype, int filter, int* status) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
-  __shared__ Smem ctl;
-  const Plan P(M.c0, M.c1, F8);
+  __shared__ uint64_t mbar[NWG];
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_any;
+  constexpr int KSTEP = Cfg<F8>::KSTEP;
+  constexpr uint32_t kCols = NWG * 64 <= 256 ? (NWG * 64 <= 128 ? 128 : 256) : 512;
+  const Plan P(M.c0, M.c1, F8, NWG);
   uint8_t* sm = smem_raw;
   const int tid = threadIdx.x, warp = tid >> 5;
-  constexpr int KSTEP = Cfg<F8>::KSTEP;
+  const int wg = tid / kRows, row = tid % kRows;
+  const int bar_id = 1 + wg;
 
-  stage_weights_tc<F8>(M, P, sm);
+  stage_shared<F8>(M, P, sm);
   if (warp == 0) {
-    tc::tmem_alloc(&ctl.tmem, 64);
+    tc::tmem_alloc(&tmem_base, kCols);
     tc::tmem_relinquish();
   }
-  if (tid == 0) {
-    tc::mbar_init(&ctl.mbar, 1);
-    tc::fence_mbar_init();
-    ctl.abort = 0;
-  }
+  if (tid < NWG) tc::mbar_init(&mbar[tid], 1);
+  if (tid == 0) abort_any = 0;
+  tc::fence_mbar_init();
   tc::fence_proxy_async();
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  const uint32_t tmem = ctl.tmem;
-  const uint32_t tmem_row = tmem + ((uint32_t)(warp * 32) << 16);
+  const uint32_t tmem = tmem_base + 64u * wg;
+  const uint32_t tmem_row = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+  uint8_t* tile = sm + P.act + P.act_bytes * wg;
+  uint64_t* bar = &mbar[wg];
 
-  // per-layer scales (FP8): acc * s_w * s_a + b; inputs scaled by 1 / s_a
   float sc[3] = {1.f, 1.f, 1.f}, inv_sa[3] = {1.f, 1.f, 1.f};
   if (F8) {
 #pragma unroll
@@ -313,8 +488,10 @@ __global__ void __launch_bounds__(kRows) decode_tc_kernel(const ntc_material M,
     }
   }
   const float* bias = reinterpret_cast<const float*>(sm + P.bias);
+  const MipInfo* mip = reinterpret_cast<const MipInfo*>(sm + P.mip);
   const uint32_t sbase = tc::smem_u32(sm);
-  const uint32_t lbo_a = (kRows / 8) * 128, lbo_w = (kHidden / 8) * 128, lbo_w3 = (kN3 / 8) * 128;
+  const uint32_t tbase = tc::smem_u32(tile);
+  constexpr uint32_t lbo_a = (kRows / 8) * 128, lbo_w = (kHidden / 8) * 128, lbo_w3 = (kN3 / 8) * 128;
   constexpr uint32_t id64 = tc::idesc(kRows, kHidden), id16 = tc::idesc(kRows, kN3);
 
   const bool tri = filter == NTC_FILTER_TRILINEAR;
@@ -322,26 +499,31 @@ __global__ void __launch_bounds__(kRows) decode_tc_kernel(const ntc_material M,
   const int64_t ntiles = (n + per_tile - 1) / per_tile;
   uint32_t phase = 0;
   const int C = M.channels;
+  bool aborted = false;
 
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  for (int64_t tl = (int64_t)blockIdx.x * NWG + wg; tl < ntiles; tl += (int64_t)gridDim.x * NWG) {
     // ---- 1. features ---------------------------------------------------------
-    const int64_t q = tri ? tile * per_tile + (tid >> 3) : tile * per_tile + tid;
+    const int64_t q = tri ? tl * per_tile + (row >> 3) : tl * per_tile + row;
     const bool valid = q < n;
     float wtap = 0.f;
     int x = 0, yy = 0, m = 0;
     if (valid) {
       const float u = uvl[3 * q], v = uvl[3 * q + 1], l = uvl[3 * q + 2];
       if (!tri) {
-        query_texel(M, u, v, l, x, yy, m);
+        m = !(l >= 0.f) ? 0 : (l >= (float)(M.mips - 1) ? M.mips - 1 : (int)floorf(l));
+        const int wm = mip[m].wm, hm = mip[m].hm;
+        const float tu = u * (float)wm, tv = v * (float)hm;
+        x = !(tu >= 0.f) ? 0 : (tu >= (float)wm ? wm - 1 : (int)floorf(tu));
+        yy = !(tv >= 0.f) ? 0 : (tv >= (float)hm ? hm - 1 : (int)floorf(tv));
       } else {
-        const int tap = tid & 7, s = tap >> 2, dx = tap & 1, dy = (tap >> 1) & 1;
+        const int tap = row & 7, s = tap >> 2, dx = tap & 1, dy = (tap >> 1) & 1;
         const float lam = !(l >= 0.f) ? 0.f : fminf(l, (float)(M.mips - 1));
         const int m0 = min((int)floorf(lam), M.mips - 1);
         const int m1 = min(m0 + 1, M.mips - 1);
         const float t = lam - (float)m0;
         m = s ? m1 : m0;
         const float wl = s ? t : 1.f - t;
-        const int wm = mip_dim(M.width, m), hm = mip_dim(M.height, m);
+        const int wm = mip[m].wm, hm = mip[m].hm;
         const float px = u * (float)wm - 0.5f, py = v * (float)hm - 0.5f;
         const float fx0 = floorf(px), fy0 = floorf(py);
         const float fx = px - fx0, fy = py - fy0;
@@ -350,36 +532,37 @@ __global__ void __launch_bounds__(kRows) decode_tc_kernel(const ntc_material M,
         wtap = wl * (dx ? fx : 1.f - fx) * (dy ? fy : 1.f - fy);
       }
     }
-    feature_row<F8>(M, P, sm + P.x, tid, x, yy, m, valid, inv_sa[0]);
+    feature_row<F8>(M, P, sm, tile, row, x, yy, m, valid, inv_sa[0]);
     tc::fence_proxy_async();
-    __syncthreads();
+    tc::bar_sync(bar_id, kRows);
 
     // ---- 2. layer 1 ----------------------------------------------------------
-    if (tid == 0) {
+    if (row == 0) {
       tc::fence_after_sync();
       const int ksteps = P.k_int / KSTEP;
       for (int s = 0; s < ksteps; ++s) {
-        const uint64_t a = tc::smem_desc(sbase + P.x + 2 * s * lbo_a, lbo_a, 128);
+        const uint64_t a = tc::smem_desc(tbase + 2 * s * lbo_a, lbo_a, 128);
         const uint64_t b = tc::smem_desc(sbase + P.w1 + 2 * s * lbo_w, lbo_w, 128);
         if (F8) tc::mma_f8(tmem, a, b, id64, s > 0);
         else tc::mma_f16(tmem, a, b, id64, s > 0);
       }
-      tc::mma_commit(&ctl.mbar);
+      tc::mma_commit(bar);
     }
-    bool ok = tc::mbar_wait(&ctl.mbar, phase, kWaitLimit);
+    bool ok = tc::mbar_wait(bar, phase, kWaitLimit);
     phase ^= 1;
-    if (__syncthreads_or(!ok)) { ctl.abort = 1; break; }
+    if (tc::bar_or(bar_id, kRows, !ok)) { aborted = true; break; }
     tc::fence_after_sync();
-    hidden_epilogue<F8>(tmem_row, sm + P.h, tid, M.act, bias, sc[0], inv_sa[1]);
+    hidden_epilogue<F8>(tmem_row, tile, row, M.act, bias, sc[0], inv_sa[1]);
     tc::fence_before_sync();
     tc::fence_proxy_async();
-    __syncthreads();
+    tc::bar_sync(bar_id, kRows);
 
     // ---- 3. layer 2 ----------------------------------------------------------
-    if (tid == 0) {
+    if (row == 0) {
       tc::fence_after_sync();
+#pragma unroll
       for (int s = 0; s < kHidden / KSTEP; ++s) {
-        const uint64_t a = tc::smem_desc(sbase + P.h + 2 * s * lbo_a, lbo_a, 128);
+        const uint64_t a = tc::smem_desc(tbase + 2 * s * lbo_a, lbo_a, 128);
         const uint64_t b = tc::smem_desc(sbase + P.w2 + 2 * s * lbo_w, lbo_w, 128);
         if (F8) tc::mma_f8(tmem, a, b, id64, s > 0);
         else tc::mma_f16(tmem, a, b, id64, s > 0);
@@ -389,22 +572,23 @@ __global__ void __launch_bounds__(kRows) decode_tc_kernel(const ntc_material M,
         const uint64_t b = tc::smem_desc(sbase + P.wb2, lbo_w, 128);
         tc::mma_f16(tmem, a, b, id64, 1);
       }
-      tc::mma_commit(&ctl.mbar);
+      tc::mma_commit(bar);
     }
-    ok = tc::mbar_wait(&ctl.mbar, phase, kWaitLimit);
+    ok = tc::mbar_wait(bar, phase, kWaitLimit);
     phase ^= 1;
-    if (__syncthreads_or(!ok)) { ctl.abort = 1; break; }
+    if (tc::bar_or(bar_id, kRows, !ok)) { aborted = true; break; }
     tc::fence_after_sync();
-    hidden_epilogue<F8>(tmem_row, sm + P.h, tid, M.act, bias + kHidden, sc[1], inv_sa[2]);
+    hidden_epilogue<F8>(tmem_row, tile, row, M.act, bias + kHidden, sc[1], inv_sa[2]);
     tc::fence_before_sync();
     tc::fence_proxy_async();
-    __syncthreads();
+    tc::bar_sync(bar_id, kRows);
 
     // ---- 4. layer 3 + output ----------------------------------------------
-    if (tid == 0) {
+    if (row == 0) {
       tc::fence_after_sync();
+#pragma unroll
       for (int s = 0; s < kHidden / KSTEP; ++s) {
-        const uint64_t a = tc::smem_desc(sbase + P.h + 2 * s * lbo_a, lbo_a, 128);
+        const uint64_t a = tc::smem_desc(tbase + 2 * s * lbo_a, lbo_a, 128);
         const uint64_t b = tc::smem_desc(sbase + P.w3 + 2 * s * lbo_w3, lbo_w3, 128);
         if (F8) tc::mma_f8(tmem, a, b, id16, s > 0);
         else tc::mma_f16(tmem, a, b, id16, s > 0);
@@ -414,11 +598,11 @@ __global__ void __launch_bounds__(kRows) decode_tc_kernel(const ntc_material M,
         const uint64_t b = tc::smem_desc(sbase + P.wb3, lbo_w3, 128);
         tc::mma_f16(tmem, a, b, id16, 1);
       }
-      tc::mma_commit(&ctl.mbar);
+      tc::mma_commit(bar);
     }
-    ok = tc::mbar_wait(&ctl.mbar, phase, kWaitLimit);
+    ok = tc::mbar_wait(bar, phase, kWaitLimit);
     phase ^= 1;
-    if (__syncthreads_or(!ok)) { ctl.abort = 1; break; }
+    if (tc::bar_or(bar_id, kRows, !ok)) { aborted = true; break; }
     tc::fence_after_sync();
     float yv[16];
     tc::tmem_ld16(tmem_row, yv);
@@ -440,7 +624,7 @@ __global__ void __launch_bounds__(kRows) decode_tc_kernel(const ntc_material M,
         yv[c] = s;
       }
     }
-    const bool writer = valid && (!tri || (tid & 7) == 0);
+    const bool writer = valid && (!tri || (row & 7) == 0);
     if (writer) {
       if (out_dtype == NTC_DTYPE_F16) {
         __half* o = static_cast<__half*>(out) + q * C;
@@ -468,7 +652,8 @@ __global__ void __launch_bounds__(kRows) decode_tc_kernel(const ntc_material M,
         if ((C & 3) == 0) {
 #pragma unroll
           for (int c = 0; c < 16; c += 4)
-            if (c < C) *reinterpret_cast<float4*>(o + c) = make_float4(yv[c], yv[c + 1], yv[c + 2], yv[c + 3]);
+            if (c < C)
+              *reinterpret_cast<float4*>(o + c) = make_float4(yv[c], yv[c + 1], yv[c + 2], yv[c + 3]);
         } else {
 #pragma unroll
           for (int c = 0; c < 16; ++c)
@@ -478,48 +663,51 @@ __global__ void __launch_bounds__(kRows) decode_tc_kernel(const ntc_material M,
     }
   }
 
+  if (aborted && row == 0) abort_any = 1;
   tc::fence_before_sync();
   __syncthreads();
-  if (tid == 0 && ctl.abort) atomicExch(status, NTC_ERR_TIMEOUT);
+  if (tid == 0 && abort_any) atomicExch(status, NTC_ERR_TIMEOUT);
   if (warp == 0) {
     tc::fence_after_sync();
-    tc::tmem_dealloc(tmem, 64);
+    tc::tmem_dealloc(tmem_base, kCols);
   }
 }
 
-template <bool F8>
+template <bool F8, int NWG>
 cudaError_t launch_k(const ntc_material& m, const float* uvl, int64_t n, void* out, int out_dtype,
-                     int filter, cudaStream_t s, int ctas_per_sm) {
-  const Plan P(m.c0, m.c1, F8);
+                     int filter, cudaStream_t s) {
+  const Plan P(m.c0, m.c1, F8, NWG);
   const size_t smem = P.total;
-  cudaError_t e = cudaFuncSetAttribute(decode_tc_kernel<F8>,
+  cudaError_t e = cudaFuncSetAttribute(decode_tc_kernel<F8, NWG>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, decode_tc_kernel<F8>, kRows, smem);
-  if (e != cudaSuccess) return e;
-  // TMEM: 64 columns per CTA, 512 per SM
-  per_sm = per_sm > 8 ? 8 : per_sm;
-  if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
-  if (per_sm < 1) per_sm = 1;
   const int per_tile = filter == NTC_FILTER_TRILINEAR ? kRows / 8 : kRows;
   const int64_t tiles = (n + per_tile - 1) / per_tile;
-  const int64_t cap = (int64_t)sm_count() * per_sm;
-  const int grid = (int)(tiles < cap ? tiles : cap);
-  decode_tc_kernel<F8><<<grid, kRows, smem, s>>>(m, uvl, n, out, out_dtype, filter, status_word());
+  const int64_t ctas = (tiles + NWG - 1) / NWG;
+  const int64_t cap = sm_count();
+  const int grid = (int)(ctas < cap ? ctas : cap);
+  decode_tc_kernel<F8, NWG><<<grid, kRows * NWG, smem, s>>>(m, uvl, n, out, out_dtype, filter,
+                                                             status_word());
   return cudaGetLastError();
 }
 
 }  // namespace
 
+// Warpgroups per CTA (one CTA per SM): 4, 6 or 8; 0 = default.
 cudaError_t launch_decode_tc(const ntc_material& m, const float* uvl, int64_t n, void* out,
-                             int out_dtype, int filter, cudaStream_t s, int ctas_per_sm) {
+                             int out_dtype, int filter, cudaStream_t s, int nwg) {
   if (n == 0) return cudaSuccess;
-  if (m.precision == NTC_PREC_F16)
-    return launch_k<false>(m, uvl, n, out, out_dtype, filter, s, ctas_per_sm);
-  if (m.precision == NTC_PREC_F8)
-    return launch_k<true>(m, uvl, n, out, out_dtype, filter, s, ctas_per_sm);
-  return cudaErrorInvalidValue;
+  if (nwg <= 0) nwg = 6;
+  const bool f8 = m.precision == NTC_PREC_F8;
+  if (m.precision != NTC_PREC_F16 && !f8) return cudaErrorInvalidValue;
+  switch (nwg) {
+    case 4: return f8 ? launch_k<true, 4>(m, uvl, n, out, out_dtype, filter, s)
+                      : launch_k<false, 4>(m, uvl, n, out, out_dtype, filter, s);
+    case 6: return f8 ? launch_k<true, 6>(m, uvl, n, out, out_dtype, filter, s)
+                      : launch_k<false, 6>(m, uvl, n, out, out_dtype, filter, s);
+    default: return f8 ? launch_k<true, 8>(m, uvl, n, out, out_dtype, filter, s)
+                       : launch_k<false, 8>(m, uvl, n, out, out_dtype, filter, s);
+  }
 }
 
 cudaError_t launch_backward_tc(const ntc_material&, const BwdArgs&, cudaStream_t) {

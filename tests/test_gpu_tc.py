@@ -134,3 +134,32 @@ def test_decode_f8_close_to_oracle():
     assert np.isfinite(got).all()
     assert err.mean() < 1e-2, err.mean()
     assert oracle.psnr(ref, got) > 35.0
+
+
+@pytest.mark.parametrize("nwg", [4, 6, 8])
+def test_decode_every_launch_shape(nwg):
+    case = make_case(512, 512, 16, 12, 12, k_in=48, seed=57)
+    mat, md = device_material(case, precision=ntc.PREC_F16)
+    q = gen.random_queries(100 * 128 + 3, md.mips, seed=4057)
+    ref = md.decode(q)
+    ntc.ntc_set_decode_warpgroups(nwg)
+    try:
+        assert np.abs(_decode(mat, q) - ref).max() <= OUT_TOL
+        tri = _decode(mat, q[:999], filter=ntc.FILTER_TRILINEAR)
+        assert np.abs(tri - md.decode_trilinear(q[:999])).max() <= OUT_TOL
+    finally:
+        ntc.ntc_set_decode_warpgroups(0)
+
+
+def test_autotune_picks_a_shape_and_stays_correct():
+    case = make_case(512, 512, 16, 12, 12, k_in=48, seed=58)
+    mat, md = device_material(case, precision=ntc.PREC_F16)
+    q = gen.random_queries(50000, md.mips, seed=4058)
+    uvl = _uvl(q)
+    out = torch.empty((q.shape[0], 16), dtype=torch.float16, device=DEV)
+    best, ms = ntc.ntc_autotune_decode(mat, uvl, out)
+    try:
+        assert best in (4, 6, 8) and all(v > 0 for v in ms.values())
+        assert np.abs(_decode(mat, q) - md.decode(q)).max() <= OUT_TOL
+    finally:
+        ntc.ntc_set_decode_warpgroups(0)
