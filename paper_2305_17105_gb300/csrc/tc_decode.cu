@@ -48,25 +48,57 @@ struct Cfg {
   static constexpr int KSTEP = F8 ? 32 : 16;  // K per MMA instruction
 };
 
-// Per-mip constants of a material (shared memory).
+// Per-mip constants of a material, staged in shared memory so that the hot
+// loop reads grid pointers and sizes with LDS instead of indexed
+// kernel-parameter loads.
 struct MipInfo {
-  int wm, hm, level, pad;
+  const uint8_t* grid0;
+  const uint8_t* grid1;
+  int wm, hm;
+  int g0w, g0h, g1w, g1h;
   float sx0, sy0, sx1, sy1;  // grid / mip resolution ratios (exact for powers of two)
   float lodn;                // m / (M - 1)
-  float pad2[3];
+  int level;
 };
+static_assert(sizeof(MipInfo) == 64, "MipInfo layout");
 
-// Shared memory plan (byte offsets).
+// Input-row layout and shared memory plan (byte offsets).
+//
+// Fast layout (4-bit packed grids, FP16 operands): f0 / f1 full groups of 8
+// channels per grid, each from one 32-bit cell word with slots holding the
+// channels 0,4,1,5,2,6,3,7 of that word; then the tails (c mod 8 channels):
+// when both tails have at most 4 channels they share one "merged" group whose
+// half2 lanes hold (G0 channel, G1 channel) pairs, otherwise each tail takes a
+// group of its own.  Generic layout: ceil(c/8) groups per grid, channels in
+// order.  Both end with two PE groups [PE0..7][PE8..11, LOD, 0, 1, 1].
 struct Plan {
-  int k_int;                 // internal MLP input width
-  int ng0, ng1;              // 8-slot groups of G0 / G1
+  int fast, merged, f0, f1, t0, t1, gpe, k_int, cb0, cb1;
   uint32_t w1, w2, w3, wb2, wb3, cst, bias, mip, pe_a, pe_b, act, act_bytes, total;
-  __host__ __device__ Plan(int c0, int c1, bool f8, int nwg) {
+  __host__ __device__ Plan(int c0, int c1, int bits0, int bits1, bool packed, bool f8, int nwg) {
     const int eb = f8 ? 1 : 2, kstep = f8 ? 32 : 16;
-    ng0 = (c0 + 7) / 8;
-    ng1 = (c1 + 7) / 8;
-    const int slots = 8 * (ng0 + ng1 + 2);
-    k_int = (slots + kstep - 1) / kstep * kstep;
+    cb0 = cb1 = 0;
+    if (packed) {
+      cb0 = cell_bytes(c0, bits0);
+      cb1 = cell_bytes(c1, bits1);
+    }
+    // the fast layout reads whole 32-bit cell words: 4-bit cells of 4 or 8 bytes
+    fast = !f8 && packed && bits0 == 4 && bits1 == 4 && (cb0 == 4 || cb0 == 8) &&
+           (cb1 == 4 || cb1 == 8);
+    if (fast) {
+      f0 = c0 / 8;
+      f1 = c1 / 8;
+      const int r0 = c0 % 8, r1 = c1 % 8;
+      merged = r0 && r1 && r0 <= 4 && r1 <= 4;
+      t0 = (!merged && r0) ? 1 : 0;
+      t1 = (!merged && r1) ? 1 : 0;
+      gpe = f0 + f1 + (merged ? 1 : t0 + t1);
+    } else {
+      f0 = (c0 + 7) / 8;
+      f1 = (c1 + 7) / 8;
+      merged = t0 = t1 = 0;
+      gpe = f0 + f1;
+    }
+    k_int = (8 * (gpe + 2) + kstep - 1) / kstep * kstep;
     uint32_t o = 0;
     w1 = o;   o += kHidden * k_int * eb;          // B: W1 (internal slot order)
     w2 = o;   o += kHidden * kHidden * eb;        // B: W2
@@ -75,9 +107,10 @@ struct Plan {
     wb3 = o;  o += f8 ? 0 : kN3 * 16 * 2;         // B: bias block of layer 3 (FP16)
     cst = o;  o += f8 ? 0 : kRows * 16 * 2;       // A: constant-one block (FP16)
     bias = o; o += (2 * kHidden + kN3) * 4;       // FP32 biases (FP8 epilogues)
+    o = (o + 63) / 64 * 64;
     mip = o;  o += NTC_MAX_MIPS * sizeof(MipInfo);
     pe_a = o; o += 64 * 16;                       // PE group 0 per (x&7, y&7), FP16
-    pe_b = o; o += 8 * 8;                         // PE y-values 2..5 per y&7, FP16
+    pe_b = o; o += 8 * 8;                         // PE values 8..11 per y&7, FP16
     o = (o + 127) / 128 * 128;
     act = o;
     act_bytes = kRows * (k_int > kHidden ? k_int : kHidden) * eb;  // X, H1, H2 alias
@@ -97,32 +130,48 @@ __device__ __forceinline__ __half2 u2h(uint32_t u) {
   return c.h;
 }
 
-// Packed 4-bit cells feed the half2 fast path (FP16 operands only).
-__device__ __forceinline__ bool fast_grid(const ntc_material& M, int k, bool f8) {
-  return !f8 && M.encoding == NTC_GRID_PACKED && (k ? M.bits1 : M.bits0) == 4;
-}
-
-// Channel held by slot e (0..7) of a grid's group g.
-__device__ __forceinline__ int slot_channel(bool fast, int g, int e) {
-  return fast ? 8 * g + (e & 1) * 4 + (e >> 1) : 8 * g + e;
-}
-
 // User column of internal input slot s: >= 0 a W1 column, -1 zero padding,
 // -2 / -3 the constant-one slots carrying the FP16 bias head / tail.
 __device__ __forceinline__ int w1_column(const ntc_material& M, const Plan& P, int s, bool f8) {
-  const int g0 = 8 * P.ng0, g1 = 8 * P.ng1;
-  if (s < g0) {
-    const int ch = slot_channel(fast_grid(M, 0, f8), s >> 3, s & 7);
-    return ch < M.c0 ? ch : -1;
+  int g = s >> 3;
+  const int e = s & 7;
+  const int pair = (e & 1) * 4 + (e >> 1);  // fast-layout channel of slot e within a word
+  if (P.fast) {
+    if (g < P.f0) return 8 * g + pair;
+    g -= P.f0;
+    if (g < P.f1) return M.c0 + 8 * g + pair;
+    g -= P.f1;
+    if (P.merged) {
+      if (g == 0) {
+        const int i = e >> 1;
+        if (e & 1) return 8 * P.f1 + i < M.c1 ? M.c0 + 8 * P.f1 + i : -1;
+        return 8 * P.f0 + i < M.c0 ? 8 * P.f0 + i : -1;
+      }
+      g -= 1;
+    } else {
+      if (P.t0) {
+        if (g == 0) return 8 * P.f0 + pair < M.c0 ? 8 * P.f0 + pair : -1;
+        g -= 1;
+      }
+      if (P.t1) {
+        if (g == 0) return 8 * P.f1 + pair < M.c1 ? M.c0 + 8 * P.f1 + pair : -1;
+        g -= 1;
+      }
+    }
+  } else {
+    if (g < P.f0) return 8 * g + e < M.c0 ? 8 * g + e : -1;
+    g -= P.f0;
+    if (g < P.f1) return 8 * g + e < M.c1 ? M.c0 + 8 * g + e : -1;
+    g -= P.f1;
   }
-  if (s < g0 + g1) {
-    const int ch = slot_channel(fast_grid(M, 1, f8), (s - g0) >> 3, (s - g0) & 7);
-    return ch < M.c1 ? M.c0 + ch : -1;
+  const int pe = M.c0 + M.c1;
+  if (g == 0) return pe + e;
+  if (g == 1) {
+    if (e < 4) return pe + 8 + e;
+    if (e == 4) return pe + 12;
+    if (!f8 && e == 6) return -2;
+    if (!f8 && e == 7) return -3;
   }
-  const int e = s - g0 - g1;
-  if (e < 13) return M.c0 + M.c1 + e;
-  if (!f8 && e == 14) return -2;
-  if (!f8 && e == 15) return -3;
   return -1;
 }
 
@@ -202,14 +251,15 @@ __device__ void stage_shared(const ntc_material& M, const Plan& P, uint8_t* sm) 
     t.wm = mip_dim(M.width, m);
     t.hm = mip_dim(M.height, m);
     t.level = level_of_mip(m, M.levels);
-    t.pad = 0;
     const ntc_level& L = M.lv[t.level];
+    t.grid0 = static_cast<const uint8_t*>(L.grid0);
+    t.grid1 = static_cast<const uint8_t*>(L.grid1);
+    t.g0w = L.g0_w; t.g0h = L.g0_h; t.g1w = L.g1_w; t.g1h = L.g1_h;
     t.sx0 = (float)L.g0_w / (float)t.wm;
     t.sy0 = (float)L.g0_h / (float)t.hm;
     t.sx1 = (float)L.g1_w / (float)t.wm;
     t.sy1 = (float)L.g1_h / (float)t.hm;
     t.lodn = M.mips > 1 ? (float)m / (float)(M.mips - 1) : 0.f;
-    t.pad2[0] = t.pad2[1] = t.pad2[2] = 0.f;
     mi[m] = t;
   }
   // positional-encoding tables (values are dyadic: exact in FP16)
@@ -269,25 +319,97 @@ __device__ __forceinline__ void taps_of(int x, int y, float sx, float sy, int gw
   t.cell[3] = iy1 * gw + ix1; t.w[3] = fx * fy;
 }
 
-// Half2 dequantise + bilinear of 4-bit cells: group g of the grid from the
-// 32-bit words g of the four tap cells.
-__device__ __forceinline__ void fast_group(const Cell (&cl)[4], const Taps& t, int g, float q,
-                                           int off, uint8_t* tile, int row, int kg) {
+// One row's texel, its tap weights and (fast layout) its gathered cells.
+// Filled ahead of use so the gathers overlap the previous tile's MMAs.
+struct Row {
+  uint2 c0[4], c1[4];  // cells of the 4 taps of G0 / G1 (at most 8 bytes each)
+  float w0[4], w1[4];  // bilinear tap weights
+  float wtap;          // trilinear blend weight of this row
+  int x, y, m;
+  int valid;
+};
+
+// Query -> texel of this row (nearest: one per query; trilinear: tap `row & 7`
+// of query `row / 8`), then its bilinear taps.
+__device__ __forceinline__ void locate(const ntc_material& M, const MipInfo* mip,
+                                       const float* __restrict__ uvl, int64_t q, bool valid,
+                                       bool tri, int row, Row& r) {
+  r.valid = valid;
+  r.wtap = 0.f;
+  r.x = r.y = r.m = 0;
+  if (!valid) return;
+  const float u = __ldg(uvl + 3 * q), v = __ldg(uvl + 3 * q + 1), l = __ldg(uvl + 3 * q + 2);
+  if (!tri) {
+    const int m = !(l >= 0.f) ? 0 : (l >= (float)(M.mips - 1) ? M.mips - 1 : (int)floorf(l));
+    const int wm = mip[m].wm, hm = mip[m].hm;
+    const float tu = u * (float)wm, tv = v * (float)hm;
+    r.x = !(tu >= 0.f) ? 0 : (tu >= (float)wm ? wm - 1 : (int)floorf(tu));
+    r.y = !(tv >= 0.f) ? 0 : (tv >= (float)hm ? hm - 1 : (int)floorf(tv));
+    r.m = m;
+  } else {
+    const int tap = row & 7, s = tap >> 2, dx = tap & 1, dy = (tap >> 1) & 1;
+    const float lam = !(l >= 0.f) ? 0.f : fminf(l, (float)(M.mips - 1));
+    const int m0 = min((int)floorf(lam), M.mips - 1);
+    const int m1 = min(m0 + 1, M.mips - 1);
+    const float t = lam - (float)m0;
+    const int m = s ? m1 : m0;
+    const float wl = s ? t : 1.f - t;
+    const int wm = mip[m].wm, hm = mip[m].hm;
+    const float px = u * (float)wm - 0.5f, py = v * (float)hm - 0.5f;
+    const float fx0 = floorf(px), fy0 = floorf(py);
+    const float fx = px - fx0, fy = py - fy0;
+    r.x = (((int)fx0 + dx) % wm + wm) % wm;
+    r.y = (((int)fy0 + dy) % hm + hm) % hm;
+    r.m = m;
+    r.wtap = wl * (dx ? fx : 1.f - fx) * (dy ? fy : 1.f - fy);
+  }
+}
+
+// Issue the eight cell loads of a fast-layout row.
+__device__ __forceinline__ void gather_fast(const MipInfo* mip, const Plan& P, Row& r) {
+  if (!r.valid) {
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      r.c0[t] = r.c1[t] = make_uint2(0, 0);
+      r.w0[t] = r.w1[t] = 0.f;
+    }
+    return;
+  }
+  const MipInfo& mi = mip[r.m];
+  Taps t0, t1;
+  taps_of(r.x, r.y, mi.sx0, mi.sy0, mi.g0w, mi.g0h, t0);
+  taps_of(r.x, r.y, mi.sx1, mi.sy1, mi.g1w, mi.g1h, t1);
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    r.w0[t] = t0.w[t];
+    r.w1[t] = t1.w[t];
+    if (P.cb0 == 8) r.c0[t] = __ldg(reinterpret_cast<const uint2*>(mi.grid0) + t0.cell[t]);
+    else r.c0[t] = make_uint2(__ldg(reinterpret_cast<const uint32_t*>(mi.grid0) + t0.cell[t]), 0u);
+    if (P.cb1 == 8) r.c1[t] = __ldg(reinterpret_cast<const uint2*>(mi.grid1) + t1.cell[t]);
+    else r.c1[t] = make_uint2(__ldg(reinterpret_cast<const uint32_t*>(mi.grid1) + t1.cell[t]), 0u);
+  }
+}
+
+__device__ __forceinline__ uint32_t word_of(const uint2& c, int f) { return f ? c.y : c.x; }
+
+// Half2 dequantisation + bilinear interpolation of one group: 32-bit cell
+// words w[t] of the four taps, per-lane tap weights wt[t], bin widths q2 and
+// offsets (N/2-1) per lane.  Writes the 16-byte chunk `kg` of the row.
+__device__ __forceinline__ void half2_group(const uint32_t (&w)[4], const __half2 (&wt)[4],
+                                            __half2 q2, __half2 o2, uint8_t* tile, int row,
+                                            int kg) {
   const __half2 bias1024 = __float2half2_rn(1024.f);
   __half2 acc[4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) acc[i] = __float2half2_rn(0.f);
 #pragma unroll
   for (int tp = 0; tp < 4; ++tp) {
-    const uint32_t w = g == 0 ? (uint32_t)cl[tp].lo : (uint32_t)(cl[tp].lo >> 32);
-    const __half2 wt = __float2half2_rn(t.w[tp]);
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      const uint32_t h = tc::lop3_and_or(w >> (4 * i), 0x000F000Fu, 0x64006400u);
-      acc[i] = __hfma2(wt, __hsub2(u2h(h), bias1024), acc[i]);
+      const uint32_t h = tc::lop3_and_or(w[tp] >> (4 * i), 0x000F000Fu, 0x64006400u);
+      acc[i] = __hfma2(wt[tp], __hsub2(u2h(h), bias1024), acc[i]);
     }
   }
-  const __half2 q2 = __float2half2_rn(q), o2 = __float2half2_rn(-(float)off * q);
   uint4 out;
   out.x = h2u(__hfma2(acc[0], q2, o2));
   out.y = h2u(__hfma2(acc[1], q2, o2));
@@ -296,19 +418,94 @@ __device__ __forceinline__ void fast_group(const Cell (&cl)[4], const Taps& t, i
   *reinterpret_cast<uint4*>(tile + tc::canon_chunk(row, kg, kRows)) = out;
 }
 
-// Float path of one grid (other bit widths, F32 grids, FP8 operands).
+__device__ __forceinline__ void pe_groups(const Plan& P, const uint8_t* sm, float lodn, int x,
+                                          int y, uint8_t* tile, int row) {
+  const uint4 a = reinterpret_cast<const uint4*>(sm + P.pe_a)[(x & 7) | ((y & 7) << 3)];
+  const uint2 b = reinterpret_cast<const uint2*>(sm + P.pe_b)[y & 7];
+  *reinterpret_cast<uint4*>(tile + tc::canon_chunk(row, P.gpe, kRows)) = a;
+  *reinterpret_cast<uint4*>(tile + tc::canon_chunk(row, P.gpe + 1, kRows)) =
+      make_uint4(b.x, b.y, tc::pack_f16x2(lodn, 0.f), tc::pack_f16x2(1.f, 1.f));
+}
+
+// Fast layout: every group of the row from the prefetched cells.
+__device__ __forceinline__ void build_fast(const ntc_material& M, const Plan& P, const uint8_t* sm,
+                                           const Row& r, uint8_t* tile, int row) {
+  const int groups = P.k_int / 8;
+  if (!r.valid) {
+    for (int g = 0; g < groups; ++g)
+      *reinterpret_cast<uint4*>(tile + tc::canon_chunk(row, g, kRows)) = make_uint4(0, 0, 0, 0);
+    return;
+  }
+  __half2 w0[4], w1[4], wm[4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    w0[t] = __float2half2_rn(r.w0[t]);
+    w1[t] = __float2half2_rn(r.w1[t]);
+    wm[t] = __floats2half2_rn(r.w0[t], r.w1[t]);
+  }
+  const __half2 q0 = __float2half2_rn(M.q0), q1 = __float2half2_rn(M.q1);
+  const __half2 o0 = __float2half2_rn(-7.f * M.q0), o1 = __float2half2_rn(-7.f * M.q1);
+  int kg = 0;
+#pragma unroll
+  for (int f = 0; f < 2; ++f)
+    if (f < P.f0) {
+      const uint32_t w[4] = {word_of(r.c0[0], f), word_of(r.c0[1], f), word_of(r.c0[2], f),
+                             word_of(r.c0[3], f)};
+      half2_group(w, w0, q0, o0, tile, row, kg++);
+    }
+#pragma unroll
+  for (int f = 0; f < 2; ++f)
+    if (f < P.f1) {
+      const uint32_t w[4] = {word_of(r.c1[0], f), word_of(r.c1[1], f), word_of(r.c1[2], f),
+                             word_of(r.c1[3], f)};
+      half2_group(w, w1, q1, o1, tile, row, kg++);
+    }
+  if (P.merged) {
+    uint32_t w[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+      w[t] = (word_of(r.c0[t], P.f0) & 0xFFFFu) | (word_of(r.c1[t], P.f1) << 16);
+    half2_group(w, wm, __lows2half2(q0, q1), __lows2half2(o0, o1), tile, row, kg++);
+  } else {
+    if (P.t0) {
+      const uint32_t w[4] = {word_of(r.c0[0], P.f0), word_of(r.c0[1], P.f0),
+                             word_of(r.c0[2], P.f0), word_of(r.c0[3], P.f0)};
+      half2_group(w, w0, q0, o0, tile, row, kg++);
+    }
+    if (P.t1) {
+      const uint32_t w[4] = {word_of(r.c1[0], P.f1), word_of(r.c1[1], P.f1),
+                             word_of(r.c1[2], P.f1), word_of(r.c1[3], P.f1)};
+      half2_group(w, w1, q1, o1, tile, row, kg++);
+    }
+  }
+  const MipInfo* mip = reinterpret_cast<const MipInfo*>(sm + P.mip);
+  pe_groups(P, sm, mip[r.m].lodn, r.x, r.y, tile, row);
+  for (int g = P.gpe + 2; g < groups; ++g)
+    *reinterpret_cast<uint4*>(tile + tc::canon_chunk(row, g, kRows)) = make_uint4(0, 0, 0, 0);
+}
+
+// Generic layout (other bit widths, F32 grids, FP8 operands): float
+// dequantisation and interpolation, channels in order.
 template <bool F8>
-__device__ __forceinline__ void float_grid(const ntc_material& M, int j, int k, const Taps& t,
-                                           const Cell (&cl)[4], int ng, uint8_t* tile, int row,
-                                           int kg0, float inv_sa) {
+__device__ __forceinline__ void generic_grid(const ntc_material& M, const MipInfo& mi, int k,
+                                             const Plan& P, int x, int y, uint8_t* tile, int row,
+                                             int kg0, float inv_sa) {
   const int c = k ? M.c1 : M.c0;
   const float q = k ? M.q1 : M.q0;
+  Taps t;
+  if (k) taps_of(x, y, mi.sx1, mi.sy1, mi.g1w, mi.g1h, t);
+  else taps_of(x, y, mi.sx0, mi.sy0, mi.g0w, mi.g0h, t);
+  const uint8_t* base = k ? mi.grid1 : mi.grid0;
   float acc[kMaxGridCh];
 #pragma unroll
   for (int ch = 0; ch < kMaxGridCh; ++ch) acc[ch] = 0.f;
   if (M.encoding == NTC_GRID_PACKED) {
     const int bits = k ? M.bits1 : M.bits0;
     const int off = (1 << (bits - 1)) - 1;
+    const int cb = k ? P.cb1 : P.cb0;
+    Cell cl[4];
+#pragma unroll
+    for (int tp = 0; tp < 4; ++tp) cl[tp] = load_cell(base, t.cell[tp], cb);
 #pragma unroll
     for (int tp = 0; tp < 4; ++tp)
 #pragma unroll
@@ -316,15 +513,16 @@ __device__ __forceinline__ void float_grid(const ntc_material& M, int j, int k, 
         if (ch < c)
           acc[ch] = fmaf(t.w[tp], (float)((int)cell_index(cl[tp], ch, bits) - off) * q, acc[ch]);
   } else {
-    const float* base = static_cast<const float*>(k ? M.lv[j].grid1 : M.lv[j].grid0);
+    const float* fb = reinterpret_cast<const float*>(base);
 #pragma unroll
     for (int tp = 0; tp < 4; ++tp) {
-      const float* g = base + (size_t)t.cell[tp] * c;
+      const float* g = fb + (size_t)t.cell[tp] * c;
 #pragma unroll
       for (int ch = 0; ch < kMaxGridCh; ++ch)
         if (ch < c) acc[ch] = fmaf(t.w[tp], __ldg(g + ch), acc[ch]);
     }
   }
+  const int ng = k ? P.f1 : P.f0;
 #pragma unroll
   for (int g = 0; g < 2; ++g)
     if (g < ng) {
@@ -335,75 +533,38 @@ __device__ __forceinline__ void float_grid(const ntc_material& M, int j, int k, 
     }
 }
 
-// Gather, dequantise, interpolate and encode one texel into row `row`.
 template <bool F8>
-__device__ __forceinline__ void feature_row(const ntc_material& M, const Plan& P,
-                                            const uint8_t* sm, uint8_t* tile, int row, int x,
-                                            int y, int m, bool valid, float inv_sa) {
+__device__ __forceinline__ void build_generic(const ntc_material& M, const Plan& P,
+                                              const uint8_t* sm, const Row& r, uint8_t* tile,
+                                              int row, float inv_sa) {
   const int groups = P.k_int / 8;
-  if (!valid) {
-    const float z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  const float z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  if (!r.valid) {
     for (int g = 0; g < groups; ++g) put_group<F8>(tile, row, g, z, 1.f);
     return;
   }
-  const MipInfo mi = reinterpret_cast<const MipInfo*>(sm + P.mip)[m];
-  const int j = mi.level;
-  const ntc_level& L = M.lv[j];
-  Taps t0, t1;
-  taps_of(x, y, mi.sx0, mi.sy0, L.g0_w, L.g0_h, t0);
-  taps_of(x, y, mi.sx1, mi.sy1, L.g1_w, L.g1_h, t1);
-  // issue all eight cell loads before using any
-  Cell c0[4], c1[4];
-  if (M.encoding == NTC_GRID_PACKED) {
-    const int cb0 = cell_bytes(M.c0, M.bits0), cb1 = cell_bytes(M.c1, M.bits1);
-    const uint8_t* b0 = static_cast<const uint8_t*>(L.grid0);
-    const uint8_t* b1 = static_cast<const uint8_t*>(L.grid1);
-#pragma unroll
-    for (int tp = 0; tp < 4; ++tp) {
-      c0[tp] = load_cell(b0, t0.cell[tp], cb0);
-      c1[tp] = load_cell(b1, t1.cell[tp], cb1);
-    }
-  } else {
-#pragma unroll
-    for (int tp = 0; tp < 4; ++tp) c0[tp] = c1[tp] = Cell{0, 0};
-  }
-  if (fast_grid(M, 0, F8)) {
-    fast_group(c0, t0, 0, M.q0, 7, tile, row, 0);
-    if (P.ng0 > 1) fast_group(c0, t0, 1, M.q0, 7, tile, row, 1);
-  } else {
-    float_grid<F8>(M, j, 0, t0, c0, P.ng0, tile, row, 0, inv_sa);
-  }
-  if (fast_grid(M, 1, F8)) {
-    fast_group(c1, t1, 0, M.q1, 7, tile, row, P.ng0);
-    if (P.ng1 > 1) fast_group(c1, t1, 1, M.q1, 7, tile, row, P.ng0 + 1);
-  } else {
-    float_grid<F8>(M, j, 1, t1, c1, P.ng1, tile, row, P.ng0, inv_sa);
-  }
-  const int gp = P.ng0 + P.ng1;
+  const MipInfo& mi = reinterpret_cast<const MipInfo*>(sm + P.mip)[r.m];
+  generic_grid<F8>(M, mi, 0, P, r.x, r.y, tile, row, 0, inv_sa);
+  generic_grid<F8>(M, mi, 1, P, r.x, r.y, tile, row, P.f0, inv_sa);
   if (!F8) {
-    const uint4 a = reinterpret_cast<const uint4*>(sm + P.pe_a)[(x & 7) | ((y & 7) << 3)];
-    const uint2 b = reinterpret_cast<const uint2*>(sm + P.pe_b)[y & 7];
-    *reinterpret_cast<uint4*>(tile + tc::canon_chunk(row, gp, kRows)) = a;
-    *reinterpret_cast<uint4*>(tile + tc::canon_chunk(row, gp + 1, kRows)) =
-        make_uint4(b.x, b.y, tc::pack_f16x2(mi.lodn, 0.f), tc::pack_f16x2(1.f, 1.f));
+    pe_groups(P, sm, mi.lodn, r.x, r.y, tile, row);
   } else {
     struct Pe {
       float v[16];
       __device__ void operator()(int i, float x) { v[i] = x; }
     } pe;
-    positional_encoding(x, y, 0, pe);
+    positional_encoding(r.x, r.y, 0, pe);
     float v[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) v[e] = pe.v[e];
-    put_group<F8>(tile, row, gp, v, inv_sa);
+    put_group<F8>(tile, row, P.gpe, v, inv_sa);
 #pragma unroll
     for (int e = 0; e < 4; ++e) v[e] = pe.v[8 + e];
     v[4] = mi.lodn;
     v[5] = v[6] = v[7] = 0.f;
-    put_group<F8>(tile, row, gp + 1, v, inv_sa);
+    put_group<F8>(tile, row, P.gpe + 1, v, inv_sa);
   }
-  const float z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  for (int g = gp + 2; g < groups; ++g) put_group<F8>(tile, row, g, z, 1.f);
+  for (int g = P.gpe + 2; g < groups; ++g) put_group<F8>(tile, row, g, z, 1.f);
 }
 
 // Layer epilogue for a 64-wide hidden layer: TMEM row -> activation -> next
@@ -446,7 +607,7 @@ __device__ __forceinline__ void hidden_epilogue(uint32_t tmem_row, uint8_t* htil
   }
 }
 
-template <bool F8, int NWG>
+template <bool F8, bool FAST, int NWG>
 __global__ void __launch_bounds__(kRows* NWG, 1) decode_tc_kernel(
     const ntc_material M, const float* __restrict__ uvl, int64_t n, void* __restrict__ out,
     int out_dtype, int filter, int* status) {
@@ -456,7 +617,7 @@ __global__ void __launch_bounds__(kRows* NWG, 1) decode_tc_kernel(
   __shared__ int abort_any;
   constexpr int KSTEP = Cfg<F8>::KSTEP;
   constexpr uint32_t kCols = NWG * 64 <= 256 ? (NWG * 64 <= 128 ? 128 : 256) : 512;
-  const Plan P(M.c0, M.c1, F8, NWG);
+  const Plan P(M.c0, M.c1, M.bits0, M.bits1, M.encoding == NTC_GRID_PACKED, F8, NWG);
   uint8_t* sm = smem_raw;
   const int tid = threadIdx.x, warp = tid >> 5;
   const int wg = tid / kRows, row = tid % kRows;
@@ -497,46 +658,31 @@ __global__ void __launch_bounds__(kRows* NWG, 1) decode_tc_kernel(
   const bool tri = filter == NTC_FILTER_TRILINEAR;
   const int per_tile = tri ? kRows / 8 : kRows;
   const int64_t ntiles = (n + per_tile - 1) / per_tile;
+  const int64_t stride = (int64_t)gridDim.x * NWG;
   uint32_t phase = 0;
   const int C = M.channels;
   bool aborted = false;
 
-  for (int64_t tl = (int64_t)blockIdx.x * NWG + wg; tl < ntiles; tl += (int64_t)gridDim.x * NWG) {
-    // ---- 1. features ---------------------------------------------------------
+  // the row of the first tile (later rows are fetched one tile ahead)
+  Row cur;
+  int64_t tl = (int64_t)blockIdx.x * NWG + wg;
+  {
     const int64_t q = tri ? tl * per_tile + (row >> 3) : tl * per_tile + row;
-    const bool valid = q < n;
-    float wtap = 0.f;
-    int x = 0, yy = 0, m = 0;
-    if (valid) {
-      const float u = uvl[3 * q], v = uvl[3 * q + 1], l = uvl[3 * q + 2];
-      if (!tri) {
-        m = !(l >= 0.f) ? 0 : (l >= (float)(M.mips - 1) ? M.mips - 1 : (int)floorf(l));
-        const int wm = mip[m].wm, hm = mip[m].hm;
-        const float tu = u * (float)wm, tv = v * (float)hm;
-        x = !(tu >= 0.f) ? 0 : (tu >= (float)wm ? wm - 1 : (int)floorf(tu));
-        yy = !(tv >= 0.f) ? 0 : (tv >= (float)hm ? hm - 1 : (int)floorf(tv));
-      } else {
-        const int tap = row & 7, s = tap >> 2, dx = tap & 1, dy = (tap >> 1) & 1;
-        const float lam = !(l >= 0.f) ? 0.f : fminf(l, (float)(M.mips - 1));
-        const int m0 = min((int)floorf(lam), M.mips - 1);
-        const int m1 = min(m0 + 1, M.mips - 1);
-        const float t = lam - (float)m0;
-        m = s ? m1 : m0;
-        const float wl = s ? t : 1.f - t;
-        const int wm = mip[m].wm, hm = mip[m].hm;
-        const float px = u * (float)wm - 0.5f, py = v * (float)hm - 0.5f;
-        const float fx0 = floorf(px), fy0 = floorf(py);
-        const float fx = px - fx0, fy = py - fy0;
-        x = (((int)fx0 + dx) % wm + wm) % wm;
-        yy = (((int)fy0 + dy) % hm + hm) % hm;
-        wtap = wl * (dx ? fx : 1.f - fx) * (dy ? fy : 1.f - fy);
-      }
-    }
-    feature_row<F8>(M, P, sm, tile, row, x, yy, m, valid, inv_sa[0]);
+    locate(M, mip, uvl, q, tl < ntiles && q < n, tri, row, cur);
+    if (FAST) gather_fast(mip, P, cur);
+  }
+
+  for (; tl < ntiles; tl += stride) {
+    const int64_t q = tri ? tl * per_tile + (row >> 3) : tl * per_tile + row;
+    const bool valid = cur.valid != 0;
+    const float wtap = cur.wtap;
+    // ---- 1. features ---------------------------------------------------------
+    if (FAST) build_fast(M, P, sm, cur, tile, row);
+    else build_generic<F8>(M, P, sm, cur, tile, row, inv_sa[0]);
     tc::fence_proxy_async();
     tc::bar_sync(bar_id, kRows);
 
-    // ---- 2. layer 1 ----------------------------------------------------------
+    // ---- 2. layer 1, then fetch the next tile's row while the MMAs run -------
     if (row == 0) {
       tc::fence_after_sync();
       const int ksteps = P.k_int / KSTEP;
@@ -547,6 +693,12 @@ __global__ void __launch_bounds__(kRows* NWG, 1) decode_tc_kernel(
         else tc::mma_f16(tmem, a, b, id64, s > 0);
       }
       tc::mma_commit(bar);
+    }
+    {
+      const int64_t nt = tl + stride;
+      const int64_t nq = tri ? nt * per_tile + (row >> 3) : nt * per_tile + row;
+      locate(M, mip, uvl, nq, nt < ntiles && nq < n, tri, row, cur);
+      if (FAST) gather_fast(mip, P, cur);
     }
     bool ok = tc::mbar_wait(bar, phase, kWaitLimit);
     phase ^= 1;
@@ -612,7 +764,7 @@ __global__ void __launch_bounds__(kRows* NWG, 1) decode_tc_kernel(
     for (int c = 0; c < 16; ++c) {
       float z = yv[c];
       if (F8) z = fmaf(z, sc[2], bias[2 * kHidden + c]);
-      yv[c] = out_fwd(M.out_act, z);
+      yv[c] = M.out_act == NTC_OUT_IDENTITY ? z : tc::sigmoid_fast(z);
     }
     if (tri) {
 #pragma unroll
@@ -673,12 +825,12 @@ __global__ void __launch_bounds__(kRows* NWG, 1) decode_tc_kernel(
   }
 }
 
-template <bool F8, int NWG>
+template <bool F8, bool FAST, int NWG>
 cudaError_t launch_k(const ntc_material& m, const float* uvl, int64_t n, void* out, int out_dtype,
                      int filter, cudaStream_t s) {
-  const Plan P(m.c0, m.c1, F8, NWG);
+  const Plan P(m.c0, m.c1, m.bits0, m.bits1, m.encoding == NTC_GRID_PACKED, F8, NWG);
   const size_t smem = P.total;
-  cudaError_t e = cudaFuncSetAttribute(decode_tc_kernel<F8, NWG>,
+  cudaError_t e = cudaFuncSetAttribute(decode_tc_kernel<F8, FAST, NWG>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int per_tile = filter == NTC_FILTER_TRILINEAR ? kRows / 8 : kRows;
@@ -686,9 +838,19 @@ cudaError_t launch_k(const ntc_material& m, const float* uvl, int64_t n, void* o
   const int64_t ctas = (tiles + NWG - 1) / NWG;
   const int64_t cap = sm_count();
   const int grid = (int)(ctas < cap ? ctas : cap);
-  decode_tc_kernel<F8, NWG><<<grid, kRows * NWG, smem, s>>>(m, uvl, n, out, out_dtype, filter,
-                                                             status_word());
+  decode_tc_kernel<F8, FAST, NWG><<<grid, kRows * NWG, smem, s>>>(m, uvl, n, out, out_dtype,
+                                                                   filter, status_word());
   return cudaGetLastError();
+}
+
+template <bool F8, bool FAST>
+cudaError_t launch_shape(const ntc_material& m, const float* uvl, int64_t n, void* out,
+                         int out_dtype, int filter, cudaStream_t s, int nwg) {
+  switch (nwg) {
+    case 4: return launch_k<F8, FAST, 4>(m, uvl, n, out, out_dtype, filter, s);
+    case 6: return launch_k<F8, FAST, 6>(m, uvl, n, out, out_dtype, filter, s);
+    default: return launch_k<F8, FAST, 8>(m, uvl, n, out, out_dtype, filter, s);
+  }
 }
 
 }  // namespace
@@ -698,16 +860,11 @@ cudaError_t launch_decode_tc(const ntc_material& m, const float* uvl, int64_t n,
                              int out_dtype, int filter, cudaStream_t s, int nwg) {
   if (n == 0) return cudaSuccess;
   if (nwg <= 0) nwg = 6;
-  const bool f8 = m.precision == NTC_PREC_F8;
-  if (m.precision != NTC_PREC_F16 && !f8) return cudaErrorInvalidValue;
-  switch (nwg) {
-    case 4: return f8 ? launch_k<true, 4>(m, uvl, n, out, out_dtype, filter, s)
-                      : launch_k<false, 4>(m, uvl, n, out, out_dtype, filter, s);
-    case 6: return f8 ? launch_k<true, 6>(m, uvl, n, out, out_dtype, filter, s)
-                      : launch_k<false, 6>(m, uvl, n, out, out_dtype, filter, s);
-    default: return f8 ? launch_k<true, 8>(m, uvl, n, out, out_dtype, filter, s)
-                       : launch_k<false, 8>(m, uvl, n, out, out_dtype, filter, s);
-  }
+  if (m.precision == NTC_PREC_F8) return launch_shape<true, false>(m, uvl, n, out, out_dtype, filter, s, nwg);
+  if (m.precision != NTC_PREC_F16) return cudaErrorInvalidValue;
+  const Plan P(m.c0, m.c1, m.bits0, m.bits1, m.encoding == NTC_GRID_PACKED, false, 1);
+  if (P.fast) return launch_shape<false, true>(m, uvl, n, out, out_dtype, filter, s, nwg);
+  return launch_shape<false, false>(m, uvl, n, out, out_dtype, filter, s, nwg);
 }
 
 cudaError_t launch_backward_tc(const ntc_material&, const BwdArgs&, cudaStream_t) {

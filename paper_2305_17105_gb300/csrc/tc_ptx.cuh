@@ -164,6 +164,15 @@ __device__ __forceinline__ uint32_t pack_e4m3x2(float a, float b) {
   return (uint32_t)d;
 }
 
+// Logistic sigmoid through the hardware tanh approximation:
+// 1/(1+e^-z) = (1 + tanh(z/2)) / 2, one MUFU operation (max relative error of
+// tanh.approx about 2^-11, i.e. < 2.5e-4 absolute on the sigmoid).
+__device__ __forceinline__ float sigmoid_fast(float z) {
+  float t;
+  asm("tanh.approx.f32 %0, %1;\n" : "=f"(t) : "f"(0.5f * z));
+  return fmaf(0.5f, t, 0.5f);
+}
+
 // Named barrier over `count` threads (a warpgroup), and its OR-reduction form.
 __device__ __forceinline__ void bar_sync(int id, int count) {
   asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(count) : "memory");
