@@ -45,6 +45,8 @@ def _decode(mat, q, **kw):
     dict(width=128, height=64, channels=5, c0=3, c1=6, bits0=2, bits1=8, k_in=32, act=1),
     dict(width=64, height=64, channels=16, c0=12, c1=12, k_in=64, out_act=1),
     dict(width=1, height=1, channels=3, c0=4, c1=4, k_in=32),
+    dict(width=256, height=512, channels=7, c0=10, c1=14, k_in=48),   # unmerged tails
+    dict(width=128, height=128, channels=9, c0=16, c1=4, k_in=48, act=1),
 ])
 def test_decode_f16_matches_oracle(shape):
     case = make_case(seed=51, **shape)
