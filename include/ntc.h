@@ -191,15 +191,15 @@ int ntc_decode(const ntc_material* m, const float* uvl, int64_t n, void* out,
                int64_t noise_step, void* stream);
 
 /* Launch shape of the tensor-core decode: warpgroup tile pipelines per CTA
- * (one CTA per SM), 4, 6 or 8; 0 restores the default.  Process-wide; takes
- * effect for later ntc_decode calls. */
+ * (one CTA per SM, 128 TMEM columns per pipeline), 2, 3 or 4; 0 restores the
+ * default (4).  Process-wide; takes effect for later ntc_decode calls. */
 int ntc_set_decode_warpgroups(int32_t nwg);
 
 /* Autotuner of the tensor-core decode: times every launch shape (1 warm-up
  * + 3 timed launches each, CUDA events on `stream`) on the caller's queries
  * (writing `out`), selects the fastest as ntc_set_decode_warpgroups would,
  * and returns it in *best (host).  ms_out (host, nullable) receives the
- * mean time per launch of the shapes 4, 6, 8.  Synchronises the stream. */
+ * mean time per launch of the shapes 2, 3, 4.  Synchronises the stream. */
 int ntc_autotune_decode(const ntc_material* m, const float* uvl, int64_t n, void* out,
                         int32_t out_dtype, int32_t filter, int32_t* best, float* ms_out,
                         void* stream);

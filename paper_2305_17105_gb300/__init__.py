@@ -259,7 +259,7 @@ def ntc_autotune_decode(mat: Material, uvl, out, filter=FILTER_NEAREST, stream=N
     s = mat.struct
     _call("ntc_autotune_decode", C.byref(s), _ptr(uvl), uvl.shape[0], _ptr(out), dt, filter,
           C.byref(best), C.cast(ms, C.c_void_p), _stream(stream))
-    return best.value, {4: ms[0], 6: ms[1], 8: ms[2]}
+    return best.value, {2: ms[0], 3: ms[1], 4: ms[2]}
 
 
 def grads_struct(mat: Material, grid0=None, grid1=None, w=None, b=None) -> ntc_grads:

@@ -159,7 +159,7 @@ int ntc_decode(const ntc_material* m, const float* uvl, int64_t n, void* out, in
 }
 
 int ntc_set_decode_warpgroups(int32_t nwg) {
-  if (nwg != 0 && nwg != 4 && nwg != 6 && nwg != 8) return fail(NTC_ERR_ARG, "warpgroups %d", nwg);
+  if (nwg != 0 && (nwg < 2 || nwg > 4)) return fail(NTC_ERR_ARG, "warpgroups %d", nwg);
   g_decode_nwg.store(nwg);
   return NTC_OK;
 }
@@ -175,7 +175,7 @@ int ntc_autotune_decode(const ntc_material* m, const float* uvl, int64_t n, void
   CHECK_PTR(uvl, "uvl");
   CHECK_PTR(out, "out");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const int shapes[3] = {4, 6, 8};
+  const int shapes[3] = {2, 3, 4};
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     return cuda_status(cudaGetLastError(), "autotune events");

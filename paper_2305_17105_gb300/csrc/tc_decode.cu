@@ -1,33 +1,34 @@
 // Tensor-core (tcgen05) random-access decode, FP16 or FP8-E4M3 operands with
-// FP32 accumulation in TMEM (Sec. 4.3-4.4, 5.2-5.3).
+// FP32 accumulation (Sec. 4.3-4.4, 5.2-5.3).
 //
-// One persistent CTA per SM runs NWG independent warpgroup pipelines that
-// share one copy of the weights.  A warpgroup owns a stream of tiles of 128
-// MLP rows (one query per row, or for trilinear filtering 16 queries x 8
-// texel taps), one activation tile in shared memory, one mbarrier and 64
-// TMEM columns.  Per tile:
+// One persistent CTA per SM runs 2-4 independent warpgroup pipelines that
+// share one copy of the weights (the B operands, in shared memory).  A
+// warpgroup owns a stream of tiles of 128 MLP rows (one query per row, or
+// for trilinear filtering 16 queries x 8 texel taps), one mbarrier and 128
+// TMEM columns: 64 for the FP32 accumulator D and the rest for the A operand.
+// Activations never touch shared memory: thread r owns row r = TMEM lane r,
+// writes its input row and its hidden rows into the A columns with
+// tcgen05.st, and tcgen05.mma reads A from TMEM.  Per tile:
 //   1. every thread gathers the 8 cells of its texel (4 bilinear taps x 2
-//      grids), dequantises, interpolates, appends the positional encoding
-//      and the LOD, and writes the row into the activation tile (canonical
-//      K-major layout);
-//   2. one thread issues layer 1 (M=128, N=64) into TMEM and commits to the
-//      mbarrier; the warpgroup waits, loads its accumulator rows with
-//      tcgen05.ld, applies the activation and writes the hidden rows back
-//      into the same tile (the MMA that read it has completed);
+//      grids; fetched one tile ahead), dequantises, interpolates, appends the
+//      positional encoding and the LOD and stores the row into A;
+//   2. one thread issues layer 1 (M=128, N=64) and commits to the mbarrier;
+//      the warpgroup fetches the next tile's cells, waits, loads D with
+//      tcgen05.ld, applies the activation and stores the hidden row into A;
 //   3. likewise layer 2 (N=64) and layer 3 (N=16), whose epilogue applies the
-//      output activation and stores the texel.
-// While one warpgroup waits on its MMAs the others gather and convert, so the
-// tensor pipe and the CUDA cores overlap.
+//      output activation and stores the texel to global memory.
 //
-// Internal input-slot order (W1's columns are permuted to match when
-// staged): [G0 groups][G1 groups][12 PE, LOD, 0, 1, 1][0 ...], 8 slots per
-// group.  With 4-bit packed grids and FP16 operands each 32-bit word of a
-// cell holds 8 channels; one LOP3 per channel pair turns nibbles i and i+4
-// into the half2 (1024 + q_i, 1024 + q_{i+4}), so a group stores channels
-// in the order 0,4,1,5,2,6,3,7.  For FP16 the biases ride on the tensor
-// core: layer 1 through two constant-one slots (bias split into an FP16 head
-// and tail), layers 2 and 3 through one extra K=16 block of a constant tile.
-// For FP8 each layer's epilogue applies (s_w * s_a) * acc + b in FP32.
+// Input-slot order (W1's columns permuted to match when staged), 8 slots per
+// group: fast layout (4-bit packed grids, FP16): full groups of 8 channels
+// from one 32-bit cell word each, slots holding channels 0,4,1,5,2,6,3,7 (one
+// LOP3 per channel pair turns nibbles i and i+4 into the half2
+// (1024 + q_i, 1024 + q_{i+4})); the <= 4-channel tails of G0 and G1 share a
+// merged group of (G0, G1) lane pairs.  Generic layout: channels in order.
+// Then [PE0..7][PE8..11, LOD, 0, 1, 1].  For FP16 the biases ride on the
+// tensor core: layer 1 through the two constant-one slots (bias split into
+// an FP16 head and tail), layers 2 and 3 through one extra K=16 step against
+// a constant-one A block kept in TMEM.  FP8: each epilogue applies
+// (s_w * s_a) * acc + b in FP32.
 #include <cuda_fp16.h>
 
 #include "ntc_device.cuh"
@@ -40,41 +41,32 @@ namespace {
 
 constexpr int kRows = 128;
 constexpr int kN3 = 16;
+constexpr int kColA = 64;              // A operand columns follow D's 64
+constexpr int kColCst = kColA + 32;    // FP16: constant-one block after H (32 columns)
 constexpr uint32_t kWaitLimit = 1u << 22;
 
 template <bool F8>
 struct Cfg {
   static constexpr int EB = F8 ? 1 : 2;       // operand bytes
-  static constexpr int KSTEP = F8 ? 32 : 16;  // K per MMA instruction
+  static constexpr int KSTEP = F8 ? 32 : 16;  // K per MMA instruction (= 8 TMEM columns)
 };
 
-// Per-mip constants of a material, staged in shared memory so that the hot
-// loop reads grid pointers and sizes with LDS instead of indexed
-// kernel-parameter loads.
-struct MipInfo {
-  const uint8_t* grid0;
-  const uint8_t* grid1;
-  int wm, hm;
-  int g0w, g0h, g1w, g1h;
-  float sx0, sy0, sx1, sy1;  // grid / mip resolution ratios (exact for powers of two)
-  float lodn;                // m / (M - 1)
-  int level;
+// Per-mip constants (structure of arrays: lanes that look up different mips
+// read different banks).
+struct MipTab {
+  const uint8_t* grid0[NTC_MAX_MIPS];
+  const uint8_t* grid1[NTC_MAX_MIPS];
+  int wm[NTC_MAX_MIPS], hm[NTC_MAX_MIPS];
+  int g0w[NTC_MAX_MIPS], g0h[NTC_MAX_MIPS], g1w[NTC_MAX_MIPS], g1h[NTC_MAX_MIPS];
+  float sx0[NTC_MAX_MIPS], sy0[NTC_MAX_MIPS], sx1[NTC_MAX_MIPS], sy1[NTC_MAX_MIPS];
+  float lodn[NTC_MAX_MIPS];
 };
-static_assert(sizeof(MipInfo) == 64, "MipInfo layout");
 
 // Input-row layout and shared memory plan (byte offsets).
-//
-// Fast layout (4-bit packed grids, FP16 operands): f0 / f1 full groups of 8
-// channels per grid, each from one 32-bit cell word with slots holding the
-// channels 0,4,1,5,2,6,3,7 of that word; then the tails (c mod 8 channels):
-// when both tails have at most 4 channels they share one "merged" group whose
-// half2 lanes hold (G0 channel, G1 channel) pairs, otherwise each tail takes a
-// group of its own.  Generic layout: ceil(c/8) groups per grid, channels in
-// order.  Both end with two PE groups [PE0..7][PE8..11, LOD, 0, 1, 1].
 struct Plan {
   int fast, merged, f0, f1, t0, t1, gpe, k_int, cb0, cb1;
-  uint32_t w1, w2, w3, wb2, wb3, cst, bias, mip, pe_a, pe_b, act, act_bytes, total;
-  __host__ __device__ Plan(int c0, int c1, int bits0, int bits1, bool packed, bool f8, int nwg) {
+  uint32_t w1, w2, w3, wb2, wb3, bias, tab, pe, total;
+  __host__ __device__ Plan(int c0, int c1, int bits0, int bits1, bool packed, bool f8) {
     const int eb = f8 ? 1 : 2, kstep = f8 ? 32 : 16;
     cb0 = cb1 = 0;
     if (packed) {
@@ -105,16 +97,10 @@ struct Plan {
     w3 = o;   o += kN3 * kHidden * eb;            // B: W3 (rows >= C zero)
     wb2 = o;  o += f8 ? 0 : kHidden * 16 * 2;     // B: bias block of layer 2 (FP16)
     wb3 = o;  o += f8 ? 0 : kN3 * 16 * 2;         // B: bias block of layer 3 (FP16)
-    cst = o;  o += f8 ? 0 : kRows * 16 * 2;       // A: constant-one block (FP16)
     bias = o; o += (2 * kHidden + kN3) * 4;       // FP32 biases (FP8 epilogues)
-    o = (o + 63) / 64 * 64;
-    mip = o;  o += NTC_MAX_MIPS * sizeof(MipInfo);
-    pe_a = o; o += 64 * 16;                       // PE group 0 per (x&7, y&7), FP16
-    pe_b = o; o += 8 * 8;                         // PE values 8..11 per y&7, FP16
-    o = (o + 127) / 128 * 128;
-    act = o;
-    act_bytes = kRows * (k_int > kHidden ? k_int : kHidden) * eb;  // X, H1, H2 alias
-    o += act_bytes * nwg;
+    o = (o + 15) / 16 * 16;
+    tab = o;  o += sizeof(MipTab);
+    pe = o;   o += 3 * 8 * 4;                     // half2 (sin, cos) per octave and x & 7
     total = o;
   }
 };
@@ -224,11 +210,6 @@ __device__ void stage_shared(const ntc_material& M, const Plan& P, uint8_t* sm) 
   }
   for (int i = tid; i < kN3; i += nt) bias[2 * kHidden + i] = i < M.channels ? M.b[2][i] : 0.f;
   if (!F8) {
-    for (int i = tid; i < kRows * 16; i += nt) {
-      const int r = i / 16, k = i - r * 16;
-      *reinterpret_cast<__half*>(sm + P.cst + tc::canon_offset(r, k, kRows, 2)) =
-          __float2half_rn(k < 2 ? 1.f : 0.f);
-    }
     for (int i = tid; i < kHidden * 16; i += nt) {
       const int n = i / 16, k = i - n * 16;
       __half hd, tl;
@@ -244,63 +225,52 @@ __device__ void stage_shared(const ntc_material& M, const Plan& P, uint8_t* sm) 
           k == 0 ? hd : (k == 1 ? tl : __float2half_rn(0.f));
     }
   }
-  // per-mip table
-  MipInfo* mi = reinterpret_cast<MipInfo*>(sm + P.mip);
+  MipTab* tb = reinterpret_cast<MipTab*>(sm + P.tab);
   for (int m = tid; m < M.mips; m += nt) {
-    MipInfo t;
-    t.wm = mip_dim(M.width, m);
-    t.hm = mip_dim(M.height, m);
-    t.level = level_of_mip(m, M.levels);
-    const ntc_level& L = M.lv[t.level];
-    t.grid0 = static_cast<const uint8_t*>(L.grid0);
-    t.grid1 = static_cast<const uint8_t*>(L.grid1);
-    t.g0w = L.g0_w; t.g0h = L.g0_h; t.g1w = L.g1_w; t.g1h = L.g1_h;
-    t.sx0 = (float)L.g0_w / (float)t.wm;
-    t.sy0 = (float)L.g0_h / (float)t.hm;
-    t.sx1 = (float)L.g1_w / (float)t.wm;
-    t.sy1 = (float)L.g1_h / (float)t.hm;
-    t.lodn = M.mips > 1 ? (float)m / (float)(M.mips - 1) : 0.f;
-    mi[m] = t;
+    const int wm = mip_dim(M.width, m), hm = mip_dim(M.height, m);
+    const ntc_level& L = M.lv[level_of_mip(m, M.levels)];
+    tb->grid0[m] = static_cast<const uint8_t*>(L.grid0);
+    tb->grid1[m] = static_cast<const uint8_t*>(L.grid1);
+    tb->wm[m] = wm;
+    tb->hm[m] = hm;
+    tb->g0w[m] = L.g0_w; tb->g0h[m] = L.g0_h; tb->g1w[m] = L.g1_w; tb->g1h[m] = L.g1_h;
+    tb->sx0[m] = (float)L.g0_w / (float)wm;
+    tb->sy0[m] = (float)L.g0_h / (float)hm;
+    tb->sx1[m] = (float)L.g1_w / (float)wm;
+    tb->sy1[m] = (float)L.g1_h / (float)hm;
+    tb->lodn[m] = M.mips > 1 ? (float)m / (float)(M.mips - 1) : 0.f;
   }
-  // positional-encoding tables (values are dyadic: exact in FP16)
+  // positional encoding: per octave h and coordinate c & 7 the (sin, cos)
+  // pair, exact in FP16
   struct Pe {
     float v[16];
     __device__ void operator()(int i, float x) { v[i] = x; }
   };
-  for (int i = tid; i < 64; i += nt) {
+  for (int c = tid; c < 8; c += nt) {
     Pe pe;
-    positional_encoding(i & 7, i >> 3, 0, pe);
-    uint4 w;
-    w.x = tc::pack_f16x2(pe.v[0], pe.v[1]);
-    w.y = tc::pack_f16x2(pe.v[2], pe.v[3]);
-    w.z = tc::pack_f16x2(pe.v[4], pe.v[5]);
-    w.w = tc::pack_f16x2(pe.v[6], pe.v[7]);
-    reinterpret_cast<uint4*>(sm + P.pe_a)[i] = w;
-    if ((i & 7) == 0)
-      reinterpret_cast<uint2*>(sm + P.pe_b)[i >> 3] =
-          make_uint2(tc::pack_f16x2(pe.v[8], pe.v[9]), tc::pack_f16x2(pe.v[10], pe.v[11]));
+    positional_encoding(c, 0, 0, pe);
+    for (int h = 0; h < 3; ++h)
+      reinterpret_cast<uint32_t*>(sm + P.pe)[h * 8 + c] = tc::pack_f16x2(pe.v[2 * h], pe.v[2 * h + 1]);
   }
 }
 
-// Write one 8-slot group of a row: FP16 -> one 16-byte chunk; FP8 -> 8 bytes
-// (scaled by `inv_scale` before rounding to E4M3).
+// One 8-slot group into the TMEM A columns of this thread's row:
+// FP16 -> 4 columns; FP8 -> 2 columns (scaled by `inv_scale` first).
 template <bool F8>
-__device__ __forceinline__ void put_group(uint8_t* tile, int row, int g, const float (&v)[8],
-                                          float inv_scale) {
+__device__ __forceinline__ void put_group(uint32_t ta, int g, const float (&v)[8], float inv_scale) {
   if (F8) {
-    uint2 w;
-    w.x = tc::pack_e4m3x2(v[0] * inv_scale, v[1] * inv_scale) |
-          (tc::pack_e4m3x2(v[2] * inv_scale, v[3] * inv_scale) << 16);
-    w.y = tc::pack_e4m3x2(v[4] * inv_scale, v[5] * inv_scale) |
-          (tc::pack_e4m3x2(v[6] * inv_scale, v[7] * inv_scale) << 16);
-    *reinterpret_cast<uint2*>(tile + tc::canon_offset(row, 8 * g, kRows, 1)) = w;
+    const uint32_t a = tc::pack_e4m3x2(v[0] * inv_scale, v[1] * inv_scale) |
+                       (tc::pack_e4m3x2(v[2] * inv_scale, v[3] * inv_scale) << 16);
+    const uint32_t b = tc::pack_e4m3x2(v[4] * inv_scale, v[5] * inv_scale) |
+                       (tc::pack_e4m3x2(v[6] * inv_scale, v[7] * inv_scale) << 16);
+    tc::tmem_st2(ta + 2 * g, a, b);
   } else {
     uint4 w;
     w.x = tc::pack_f16x2(v[0], v[1]);
     w.y = tc::pack_f16x2(v[2], v[3]);
     w.z = tc::pack_f16x2(v[4], v[5]);
     w.w = tc::pack_f16x2(v[6], v[7]);
-    *reinterpret_cast<uint4*>(tile + tc::canon_chunk(row, g, kRows)) = w;
+    tc::tmem_st4(ta + 4 * g, w);
   }
 }
 
@@ -320,7 +290,7 @@ __device__ __forceinline__ void taps_of(int x, int y, float sx, float sy, int gw
 }
 
 // One row's texel, its tap weights and (fast layout) its gathered cells.
-// Filled ahead of use so the gathers overlap the previous tile's MMAs.
+// Filled one tile ahead so the gathers overlap the previous tile's MMAs.
 struct Row {
   uint2 c0[4], c1[4];  // cells of the 4 taps of G0 / G1 (at most 8 bytes each)
   float w0[4], w1[4];  // bilinear tap weights
@@ -330,8 +300,8 @@ struct Row {
 };
 
 // Query -> texel of this row (nearest: one per query; trilinear: tap `row & 7`
-// of query `row / 8`), then its bilinear taps.
-__device__ __forceinline__ void locate(const ntc_material& M, const MipInfo* mip,
+// of query `row / 8`).
+__device__ __forceinline__ void locate(const ntc_material& M, const MipTab* tb,
                                        const float* __restrict__ uvl, int64_t q, bool valid,
                                        bool tri, int row, Row& r) {
   r.valid = valid;
@@ -341,7 +311,7 @@ __device__ __forceinline__ void locate(const ntc_material& M, const MipInfo* mip
   const float u = __ldg(uvl + 3 * q), v = __ldg(uvl + 3 * q + 1), l = __ldg(uvl + 3 * q + 2);
   if (!tri) {
     const int m = !(l >= 0.f) ? 0 : (l >= (float)(M.mips - 1) ? M.mips - 1 : (int)floorf(l));
-    const int wm = mip[m].wm, hm = mip[m].hm;
+    const int wm = tb->wm[m], hm = tb->hm[m];
     const float tu = u * (float)wm, tv = v * (float)hm;
     r.x = !(tu >= 0.f) ? 0 : (tu >= (float)wm ? wm - 1 : (int)floorf(tu));
     r.y = !(tv >= 0.f) ? 0 : (tv >= (float)hm ? hm - 1 : (int)floorf(tv));
@@ -354,7 +324,7 @@ __device__ __forceinline__ void locate(const ntc_material& M, const MipInfo* mip
     const float t = lam - (float)m0;
     const int m = s ? m1 : m0;
     const float wl = s ? t : 1.f - t;
-    const int wm = mip[m].wm, hm = mip[m].hm;
+    const int wm = tb->wm[m], hm = tb->hm[m];
     const float px = u * (float)wm - 0.5f, py = v * (float)hm - 0.5f;
     const float fx0 = floorf(px), fy0 = floorf(py);
     const float fx = px - fx0, fy = py - fy0;
@@ -365,39 +335,38 @@ __device__ __forceinline__ void locate(const ntc_material& M, const MipInfo* mip
   }
 }
 
-// Issue the eight cell loads of a fast-layout row.
-__device__ __forceinline__ void gather_fast(const MipInfo* mip, const Plan& P, Row& r) {
-  if (!r.valid) {
+// Issue the eight cell loads of a fast-layout row (invalid rows load nothing).
+__device__ __forceinline__ void gather_fast(const MipTab* tb, const Plan& P, Row& r) {
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      r.c0[t] = r.c1[t] = make_uint2(0, 0);
-      r.w0[t] = r.w1[t] = 0.f;
-    }
-    return;
+  for (int t = 0; t < 4; ++t) {
+    r.c0[t] = r.c1[t] = make_uint2(0, 0);
+    r.w0[t] = r.w1[t] = 0.f;
   }
-  const MipInfo& mi = mip[r.m];
+  if (!r.valid) return;
+  const int m = r.m;
   Taps t0, t1;
-  taps_of(r.x, r.y, mi.sx0, mi.sy0, mi.g0w, mi.g0h, t0);
-  taps_of(r.x, r.y, mi.sx1, mi.sy1, mi.g1w, mi.g1h, t1);
+  taps_of(r.x, r.y, tb->sx0[m], tb->sy0[m], tb->g0w[m], tb->g0h[m], t0);
+  taps_of(r.x, r.y, tb->sx1[m], tb->sy1[m], tb->g1w[m], tb->g1h[m], t1);
+  const uint8_t* g0 = tb->grid0[m];
+  const uint8_t* g1 = tb->grid1[m];
 #pragma unroll
   for (int t = 0; t < 4; ++t) {
     r.w0[t] = t0.w[t];
     r.w1[t] = t1.w[t];
-    if (P.cb0 == 8) r.c0[t] = __ldg(reinterpret_cast<const uint2*>(mi.grid0) + t0.cell[t]);
-    else r.c0[t] = make_uint2(__ldg(reinterpret_cast<const uint32_t*>(mi.grid0) + t0.cell[t]), 0u);
-    if (P.cb1 == 8) r.c1[t] = __ldg(reinterpret_cast<const uint2*>(mi.grid1) + t1.cell[t]);
-    else r.c1[t] = make_uint2(__ldg(reinterpret_cast<const uint32_t*>(mi.grid1) + t1.cell[t]), 0u);
+    if (P.cb0 == 8) r.c0[t] = __ldg(reinterpret_cast<const uint2*>(g0) + t0.cell[t]);
+    else r.c0[t].x = __ldg(reinterpret_cast<const uint32_t*>(g0) + t0.cell[t]);
+    if (P.cb1 == 8) r.c1[t] = __ldg(reinterpret_cast<const uint2*>(g1) + t1.cell[t]);
+    else r.c1[t].x = __ldg(reinterpret_cast<const uint32_t*>(g1) + t1.cell[t]);
   }
 }
 
 __device__ __forceinline__ uint32_t word_of(const uint2& c, int f) { return f ? c.y : c.x; }
 
-// Half2 dequantisation + bilinear interpolation of one group: 32-bit cell
-// words w[t] of the four taps, per-lane tap weights wt[t], bin widths q2 and
-// offsets (N/2-1) per lane.  Writes the 16-byte chunk `kg` of the row.
-__device__ __forceinline__ void half2_group(const uint32_t (&w)[4], const __half2 (&wt)[4],
-                                            __half2 q2, __half2 o2, uint8_t* tile, int row,
-                                            int kg) {
+// Half2 dequantisation + bilinear interpolation of one group from the 32-bit
+// cell words w[t] of the four taps, per-lane tap weights wt[t], bin widths
+// q2 and offsets -(N/2-1) Q per lane.
+__device__ __forceinline__ uint4 half2_group(const uint32_t (&w)[4], const __half2 (&wt)[4],
+                                             __half2 q2, __half2 o2) {
   const __half2 bias1024 = __float2half2_rn(1024.f);
   __half2 acc[4];
 #pragma unroll
@@ -410,32 +379,24 @@ __device__ __forceinline__ void half2_group(const uint32_t (&w)[4], const __half
       acc[i] = __hfma2(wt[tp], __hsub2(u2h(h), bias1024), acc[i]);
     }
   }
-  uint4 out;
-  out.x = h2u(__hfma2(acc[0], q2, o2));
-  out.y = h2u(__hfma2(acc[1], q2, o2));
-  out.z = h2u(__hfma2(acc[2], q2, o2));
-  out.w = h2u(__hfma2(acc[3], q2, o2));
-  *reinterpret_cast<uint4*>(tile + tc::canon_chunk(row, kg, kRows)) = out;
+  return make_uint4(h2u(__hfma2(acc[0], q2, o2)), h2u(__hfma2(acc[1], q2, o2)),
+                    h2u(__hfma2(acc[2], q2, o2)), h2u(__hfma2(acc[3], q2, o2)));
 }
 
+// The two PE groups (FP16): (sin, cos) pairs of the 3 octaves of x, then of
+// y, then (LOD, 0) and the constant-one bias slots.
 __device__ __forceinline__ void pe_groups(const Plan& P, const uint8_t* sm, float lodn, int x,
-                                          int y, uint8_t* tile, int row) {
-  const uint4 a = reinterpret_cast<const uint4*>(sm + P.pe_a)[(x & 7) | ((y & 7) << 3)];
-  const uint2 b = reinterpret_cast<const uint2*>(sm + P.pe_b)[y & 7];
-  *reinterpret_cast<uint4*>(tile + tc::canon_chunk(row, P.gpe, kRows)) = a;
-  *reinterpret_cast<uint4*>(tile + tc::canon_chunk(row, P.gpe + 1, kRows)) =
-      make_uint4(b.x, b.y, tc::pack_f16x2(lodn, 0.f), tc::pack_f16x2(1.f, 1.f));
+                                          int y, uint32_t ta) {
+  const uint32_t* pe = reinterpret_cast<const uint32_t*>(sm + P.pe);
+  const int cx = x & 7, cy = y & 7;
+  tc::tmem_st4(ta + 4 * P.gpe, make_uint4(pe[cx], pe[8 + cx], pe[16 + cx], pe[cy]));
+  tc::tmem_st4(ta + 4 * (P.gpe + 1), make_uint4(pe[8 + cy], pe[16 + cy], tc::pack_f16x2(lodn, 0.f),
+                                                tc::pack_f16x2(1.f, 1.f)));
 }
 
 // Fast layout: every group of the row from the prefetched cells.
 __device__ __forceinline__ void build_fast(const ntc_material& M, const Plan& P, const uint8_t* sm,
-                                           const Row& r, uint8_t* tile, int row) {
-  const int groups = P.k_int / 8;
-  if (!r.valid) {
-    for (int g = 0; g < groups; ++g)
-      *reinterpret_cast<uint4*>(tile + tc::canon_chunk(row, g, kRows)) = make_uint4(0, 0, 0, 0);
-    return;
-  }
+                                           const Row& r, uint32_t ta) {
   __half2 w0[4], w1[4], wm[4];
 #pragma unroll
   for (int t = 0; t < 4; ++t) {
@@ -451,75 +412,77 @@ __device__ __forceinline__ void build_fast(const ntc_material& M, const Plan& P,
     if (f < P.f0) {
       const uint32_t w[4] = {word_of(r.c0[0], f), word_of(r.c0[1], f), word_of(r.c0[2], f),
                              word_of(r.c0[3], f)};
-      half2_group(w, w0, q0, o0, tile, row, kg++);
+      tc::tmem_st4(ta + 4 * kg++, half2_group(w, w0, q0, o0));
     }
 #pragma unroll
   for (int f = 0; f < 2; ++f)
     if (f < P.f1) {
       const uint32_t w[4] = {word_of(r.c1[0], f), word_of(r.c1[1], f), word_of(r.c1[2], f),
                              word_of(r.c1[3], f)};
-      half2_group(w, w1, q1, o1, tile, row, kg++);
+      tc::tmem_st4(ta + 4 * kg++, half2_group(w, w1, q1, o1));
     }
   if (P.merged) {
     uint32_t w[4];
 #pragma unroll
     for (int t = 0; t < 4; ++t)
       w[t] = (word_of(r.c0[t], P.f0) & 0xFFFFu) | (word_of(r.c1[t], P.f1) << 16);
-    half2_group(w, wm, __lows2half2(q0, q1), __lows2half2(o0, o1), tile, row, kg++);
+    tc::tmem_st4(ta + 4 * kg++, half2_group(w, wm, __lows2half2(q0, q1), __lows2half2(o0, o1)));
   } else {
     if (P.t0) {
       const uint32_t w[4] = {word_of(r.c0[0], P.f0), word_of(r.c0[1], P.f0),
                              word_of(r.c0[2], P.f0), word_of(r.c0[3], P.f0)};
-      half2_group(w, w0, q0, o0, tile, row, kg++);
+      tc::tmem_st4(ta + 4 * kg++, half2_group(w, w0, q0, o0));
     }
     if (P.t1) {
       const uint32_t w[4] = {word_of(r.c1[0], P.f1), word_of(r.c1[1], P.f1),
                              word_of(r.c1[2], P.f1), word_of(r.c1[3], P.f1)};
-      half2_group(w, w1, q1, o1, tile, row, kg++);
+      tc::tmem_st4(ta + 4 * kg++, half2_group(w, w1, q1, o1));
     }
   }
-  const MipInfo* mip = reinterpret_cast<const MipInfo*>(sm + P.mip);
-  pe_groups(P, sm, mip[r.m].lodn, r.x, r.y, tile, row);
-  for (int g = P.gpe + 2; g < groups; ++g)
-    *reinterpret_cast<uint4*>(tile + tc::canon_chunk(row, g, kRows)) = make_uint4(0, 0, 0, 0);
+  const MipTab* tb = reinterpret_cast<const MipTab*>(sm + P.tab);
+  pe_groups(P, sm, tb->lodn[r.m], r.x, r.y, ta);
+  for (int g = P.gpe + 2; g < P.k_int / 8; ++g) tc::tmem_st4(ta + 4 * g, make_uint4(0, 0, 0, 0));
 }
 
 // Generic layout (other bit widths, F32 grids, FP8 operands): float
 // dequantisation and interpolation, channels in order.
 template <bool F8>
-__device__ __forceinline__ void generic_grid(const ntc_material& M, const MipInfo& mi, int k,
-                                             const Plan& P, int x, int y, uint8_t* tile, int row,
-                                             int kg0, float inv_sa) {
+__device__ __forceinline__ void generic_grid(const ntc_material& M, const MipTab* tb, int k,
+                                             const Plan& P, const Row& r, uint32_t ta, int kg0,
+                                             float inv_sa) {
   const int c = k ? M.c1 : M.c0;
   const float q = k ? M.q1 : M.q0;
-  Taps t;
-  if (k) taps_of(x, y, mi.sx1, mi.sy1, mi.g1w, mi.g1h, t);
-  else taps_of(x, y, mi.sx0, mi.sy0, mi.g0w, mi.g0h, t);
-  const uint8_t* base = k ? mi.grid1 : mi.grid0;
+  const int m = r.m;
   float acc[kMaxGridCh];
 #pragma unroll
   for (int ch = 0; ch < kMaxGridCh; ++ch) acc[ch] = 0.f;
-  if (M.encoding == NTC_GRID_PACKED) {
-    const int bits = k ? M.bits1 : M.bits0;
-    const int off = (1 << (bits - 1)) - 1;
-    const int cb = k ? P.cb1 : P.cb0;
-    Cell cl[4];
+  if (r.valid) {
+    Taps t;
+    if (k) taps_of(r.x, r.y, tb->sx1[m], tb->sy1[m], tb->g1w[m], tb->g1h[m], t);
+    else taps_of(r.x, r.y, tb->sx0[m], tb->sy0[m], tb->g0w[m], tb->g0h[m], t);
+    const uint8_t* base = k ? tb->grid1[m] : tb->grid0[m];
+    if (M.encoding == NTC_GRID_PACKED) {
+      const int bits = k ? M.bits1 : M.bits0;
+      const int off = (1 << (bits - 1)) - 1;
+      const int cb = k ? P.cb1 : P.cb0;
+      Cell cl[4];
 #pragma unroll
-    for (int tp = 0; tp < 4; ++tp) cl[tp] = load_cell(base, t.cell[tp], cb);
+      for (int tp = 0; tp < 4; ++tp) cl[tp] = load_cell(base, t.cell[tp], cb);
 #pragma unroll
-    for (int tp = 0; tp < 4; ++tp)
+      for (int tp = 0; tp < 4; ++tp)
 #pragma unroll
-      for (int ch = 0; ch < kMaxGridCh; ++ch)
-        if (ch < c)
-          acc[ch] = fmaf(t.w[tp], (float)((int)cell_index(cl[tp], ch, bits) - off) * q, acc[ch]);
-  } else {
-    const float* fb = reinterpret_cast<const float*>(base);
+        for (int ch = 0; ch < kMaxGridCh; ++ch)
+          if (ch < c)
+            acc[ch] = fmaf(t.w[tp], (float)((int)cell_index(cl[tp], ch, bits) - off) * q, acc[ch]);
+    } else {
+      const float* fb = reinterpret_cast<const float*>(base);
 #pragma unroll
-    for (int tp = 0; tp < 4; ++tp) {
-      const float* g = fb + (size_t)t.cell[tp] * c;
+      for (int tp = 0; tp < 4; ++tp) {
+        const float* g = fb + (size_t)t.cell[tp] * c;
 #pragma unroll
-      for (int ch = 0; ch < kMaxGridCh; ++ch)
-        if (ch < c) acc[ch] = fmaf(t.w[tp], __ldg(g + ch), acc[ch]);
+        for (int ch = 0; ch < kMaxGridCh; ++ch)
+          if (ch < c) acc[ch] = fmaf(t.w[tp], __ldg(g + ch), acc[ch]);
+      }
     }
   }
   const int ng = k ? P.f1 : P.f0;
@@ -529,25 +492,19 @@ __device__ __forceinline__ void generic_grid(const ntc_material& M, const MipInf
       float v[8];
 #pragma unroll
       for (int e = 0; e < 8; ++e) v[e] = acc[8 * g + e];
-      put_group<F8>(tile, row, kg0 + g, v, inv_sa);
+      put_group<F8>(ta, kg0 + g, v, inv_sa);
     }
 }
 
 template <bool F8>
 __device__ __forceinline__ void build_generic(const ntc_material& M, const Plan& P,
-                                              const uint8_t* sm, const Row& r, uint8_t* tile,
-                                              int row, float inv_sa) {
-  const int groups = P.k_int / 8;
-  const float z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  if (!r.valid) {
-    for (int g = 0; g < groups; ++g) put_group<F8>(tile, row, g, z, 1.f);
-    return;
-  }
-  const MipInfo& mi = reinterpret_cast<const MipInfo*>(sm + P.mip)[r.m];
-  generic_grid<F8>(M, mi, 0, P, r.x, r.y, tile, row, 0, inv_sa);
-  generic_grid<F8>(M, mi, 1, P, r.x, r.y, tile, row, P.f0, inv_sa);
+                                              const uint8_t* sm, const Row& r, uint32_t ta,
+                                              float inv_sa) {
+  const MipTab* tb = reinterpret_cast<const MipTab*>(sm + P.tab);
+  generic_grid<F8>(M, tb, 0, P, r, ta, 0, inv_sa);
+  generic_grid<F8>(M, tb, 1, P, r, ta, P.f0, inv_sa);
   if (!F8) {
-    pe_groups(P, sm, mi.lodn, r.x, r.y, tile, row);
+    pe_groups(P, sm, tb->lodn[r.m], r.x, r.y, ta);
   } else {
     struct Pe {
       float v[16];
@@ -557,67 +514,88 @@ __device__ __forceinline__ void build_generic(const ntc_material& M, const Plan&
     float v[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) v[e] = pe.v[e];
-    put_group<F8>(tile, row, P.gpe, v, inv_sa);
+    put_group<F8>(ta, P.gpe, v, inv_sa);
 #pragma unroll
     for (int e = 0; e < 4; ++e) v[e] = pe.v[8 + e];
-    v[4] = mi.lodn;
+    v[4] = tb->lodn[r.m];
     v[5] = v[6] = v[7] = 0.f;
-    put_group<F8>(tile, row, P.gpe + 1, v, inv_sa);
+    put_group<F8>(ta, P.gpe + 1, v, inv_sa);
   }
-  for (int g = P.gpe + 2; g < groups; ++g) put_group<F8>(tile, row, g, z, 1.f);
+  const float z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int g = P.gpe + 2; g < P.k_int / 8; ++g) put_group<F8>(ta, g, z, 1.f);
 }
 
-// Layer epilogue for a 64-wide hidden layer: TMEM row -> activation -> next
-// A tile.  FP8: (s_w s_a) acc + b, activation, scale by 1/s_a(next), E4M3.
+// Hidden-layer epilogue: D row (TMEM) -> activation -> A row (TMEM).
+// FP8: (s_w s_a) acc + b, activation, scale by 1/s_a(next), E4M3.
 template <bool F8>
-__device__ __forceinline__ void hidden_epilogue(uint32_t tmem_row, uint8_t* htile, int row, int act,
+__device__ __forceinline__ void hidden_epilogue(uint32_t td, uint32_t ta, int act,
                                                 const float* bias, float scale, float inv_next) {
 #pragma unroll
   for (int half = 0; half < 2; ++half) {
     float a[16], b[16];
-    tc::tmem_ld16(tmem_row + 32 * half, a);
-    tc::tmem_ld16(tmem_row + 32 * half + 16, b);
+    tc::tmem_ld16(td + 32 * half, a);
+    tc::tmem_ld16(td + 32 * half + 16, b);
     tc::tmem_ld_wait();
     float v[32];
 #pragma unroll
     for (int i = 0; i < 16; ++i) { v[i] = a[i]; v[16 + i] = b[i]; }
     if (F8) {
+      uint32_t w[8];
 #pragma unroll
-      for (int i = 0; i < 32; ++i) v[i] = fmaf(v[i], scale, bias[32 * half + i]);
-    }
-    if (!F8 && act == NTC_ACT_RELU) {
+      for (int i = 0; i < 8; ++i) {
+        float e[4];
 #pragma unroll
-      for (int g = 0; g < 4; ++g) {
-        uint4 w;
-        w.x = tc::pack_f16x2_relu(v[8 * g + 0], v[8 * g + 1]);
-        w.y = tc::pack_f16x2_relu(v[8 * g + 2], v[8 * g + 3]);
-        w.z = tc::pack_f16x2_relu(v[8 * g + 4], v[8 * g + 5]);
-        w.w = tc::pack_f16x2_relu(v[8 * g + 6], v[8 * g + 7]);
-        *reinterpret_cast<uint4*>(htile + tc::canon_chunk(row, 4 * half + g, kRows)) = w;
+        for (int j = 0; j < 4; ++j)
+          e[j] = act_fwd(act, fmaf(v[4 * i + j], scale, bias[32 * half + 4 * i + j])) * inv_next;
+        w[i] = tc::pack_e4m3x2(e[0], e[1]) | (tc::pack_e4m3x2(e[2], e[3]) << 16);
       }
+      tc::tmem_st4(ta + 8 * half, make_uint4(w[0], w[1], w[2], w[3]));
+      tc::tmem_st4(ta + 8 * half + 4, make_uint4(w[4], w[5], w[6], w[7]));
     } else {
+      uint32_t w[16];
+      if (act == NTC_ACT_RELU) {
 #pragma unroll
-      for (int g = 0; g < 4; ++g) {
-        float e[8];
+        for (int i = 0; i < 16; ++i) w[i] = tc::pack_f16x2_relu(v[2 * i], v[2 * i + 1]);
+      } else {
 #pragma unroll
-        for (int i = 0; i < 8; ++i) e[i] = act_fwd(act, v[8 * g + i]);
-        put_group<F8>(htile, row, 4 * half + g, e, inv_next);
+        for (int i = 0; i < 16; ++i)
+          w[i] = tc::pack_f16x2(act_fwd(act, v[2 * i]), act_fwd(act, v[2 * i + 1]));
       }
+      tc::tmem_st16(ta + 16 * half, w);
     }
   }
 }
 
-template <bool F8, bool FAST, int NWG>
-__global__ void __launch_bounds__(kRows* NWG, 1) decode_tc_kernel(
+// Issue one layer: D (+)= A[tmem] B[smem]^T over `ksteps` K-steps of W, then
+// (FP16) the bias step against the constant-one A block, then commit.
+template <bool F8>
+__device__ __forceinline__ void issue_layer(uint32_t tmem_d, uint32_t tmem_a, uint32_t b_addr,
+                                            uint32_t lbo, int ksteps, uint32_t id,
+                                            uint32_t bias_b_addr, uint64_t* bar) {
+  tc::fence_after_sync();
+  for (int s = 0; s < ksteps; ++s) {
+    const uint64_t b = tc::smem_desc(b_addr + 2 * s * lbo, lbo, 128);
+    if (F8) tc::mma_f8_ta(tmem_d, tmem_a + 8 * s, b, id, s > 0);
+    else tc::mma_f16_ta(tmem_d, tmem_a + 8 * s, b, id, s > 0);
+  }
+  if (!F8 && bias_b_addr) {
+    const uint64_t b = tc::smem_desc(bias_b_addr, lbo, 128);
+    tc::mma_f16_ta(tmem_d, tmem_a + (kColCst - kColA), b, id, 1);
+  }
+  tc::mma_commit(bar);
+}
+
+template <bool F8, bool FAST, int kNWG>
+__global__ void __launch_bounds__(kRows* kNWG, 1) decode_tc_kernel(
     const ntc_material M, const float* __restrict__ uvl, int64_t n, void* __restrict__ out,
     int out_dtype, int filter, int* status) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
-  __shared__ uint64_t mbar[NWG];
+  __shared__ uint64_t mbar[kNWG];
   __shared__ uint32_t tmem_base;
   __shared__ int abort_any;
   constexpr int KSTEP = Cfg<F8>::KSTEP;
-  constexpr uint32_t kCols = NWG * 64 <= 256 ? (NWG * 64 <= 128 ? 128 : 256) : 512;
-  const Plan P(M.c0, M.c1, M.bits0, M.bits1, M.encoding == NTC_GRID_PACKED, F8, NWG);
+  constexpr uint32_t kCols = kNWG <= 2 ? 256 : 512;  // 128 columns per warpgroup
+  const Plan P(M.c0, M.c1, M.bits0, M.bits1, M.encoding == NTC_GRID_PACKED, F8);
   uint8_t* sm = smem_raw;
   const int tid = threadIdx.x, warp = tid >> 5;
   const int wg = tid / kRows, row = tid % kRows;
@@ -628,17 +606,24 @@ __global__ void __launch_bounds__(kRows* NWG, 1) decode_tc_kernel(
     tc::tmem_alloc(&tmem_base, kCols);
     tc::tmem_relinquish();
   }
-  if (tid < NWG) tc::mbar_init(&mbar[tid], 1);
+  if (tid < kNWG) tc::mbar_init(&mbar[tid], 1);
   if (tid == 0) abort_any = 0;
   tc::fence_mbar_init();
   tc::fence_proxy_async();
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  const uint32_t tmem = tmem_base + 64u * wg;
-  const uint32_t tmem_row = tmem + ((uint32_t)((warp & 3) * 32) << 16);
-  uint8_t* tile = sm + P.act + P.act_bytes * wg;
+  // this warpgroup's 128 columns; per-thread addresses carry the warp's lane quarter
+  const uint32_t tw = tmem_base + 128u * wg;
+  const uint32_t lane = (uint32_t)((warp & 3) * 32) << 16;
+  const uint32_t td = tw + lane;            // D row of this thread
+  const uint32_t ta = tw + kColA + lane;    // A row of this thread
   uint64_t* bar = &mbar[wg];
+  if (!F8) {
+    // constant-one A block (bias steps of layers 2 and 3): k = 0, 1 are one
+    tc::tmem_st4(ta + (kColCst - kColA), make_uint4(tc::pack_f16x2(1.f, 1.f), 0, 0, 0));
+    tc::tmem_st4(ta + (kColCst - kColA) + 4, make_uint4(0, 0, 0, 0));
+  }
 
   float sc[3] = {1.f, 1.f, 1.f}, inv_sa[3] = {1.f, 1.f, 1.f};
   if (F8) {
@@ -649,115 +634,81 @@ __global__ void __launch_bounds__(kRows* NWG, 1) decode_tc_kernel(
     }
   }
   const float* bias = reinterpret_cast<const float*>(sm + P.bias);
-  const MipInfo* mip = reinterpret_cast<const MipInfo*>(sm + P.mip);
+  const MipTab* tb = reinterpret_cast<const MipTab*>(sm + P.tab);
   const uint32_t sbase = tc::smem_u32(sm);
-  const uint32_t tbase = tc::smem_u32(tile);
-  constexpr uint32_t lbo_a = (kRows / 8) * 128, lbo_w = (kHidden / 8) * 128, lbo_w3 = (kN3 / 8) * 128;
+  constexpr uint32_t lbo_w = (kHidden / 8) * 128, lbo_w3 = (kN3 / 8) * 128;
   constexpr uint32_t id64 = tc::idesc(kRows, kHidden), id16 = tc::idesc(kRows, kN3);
+  const uint32_t tmem_d = tw, tmem_a = tw + kColA;
 
   const bool tri = filter == NTC_FILTER_TRILINEAR;
   const int per_tile = tri ? kRows / 8 : kRows;
   const int64_t ntiles = (n + per_tile - 1) / per_tile;
-  const int64_t stride = (int64_t)gridDim.x * NWG;
+  const int64_t stride = (int64_t)gridDim.x * kNWG;
   uint32_t phase = 0;
   const int C = M.channels;
   bool aborted = false;
 
   // the row of the first tile (later rows are fetched one tile ahead)
   Row cur;
-  int64_t tl = (int64_t)blockIdx.x * NWG + wg;
+  int64_t tl = (int64_t)blockIdx.x * kNWG + wg;
   {
     const int64_t q = tri ? tl * per_tile + (row >> 3) : tl * per_tile + row;
-    locate(M, mip, uvl, q, tl < ntiles && q < n, tri, row, cur);
-    if (FAST) gather_fast(mip, P, cur);
+    locate(M, tb, uvl, q, tl < ntiles && q < n, tri, row, cur);
+    if (FAST) gather_fast(tb, P, cur);
   }
 
   for (; tl < ntiles; tl += stride) {
     const int64_t q = tri ? tl * per_tile + (row >> 3) : tl * per_tile + row;
     const bool valid = cur.valid != 0;
     const float wtap = cur.wtap;
-    // ---- 1. features ---------------------------------------------------------
-    if (FAST) build_fast(M, P, sm, cur, tile, row);
-    else build_generic<F8>(M, P, sm, cur, tile, row, inv_sa[0]);
-    tc::fence_proxy_async();
+    // ---- 1. features -> A ----------------------------------------------------
+    if (FAST) build_fast(M, P, sm, cur, ta);
+    else build_generic<F8>(M, P, sm, cur, ta, inv_sa[0]);
+    tc::tmem_st_wait();
+    tc::fence_before_sync();
     tc::bar_sync(bar_id, kRows);
 
-    // ---- 2. layer 1, then fetch the next tile's row while the MMAs run -------
-    if (row == 0) {
-      tc::fence_after_sync();
-      const int ksteps = P.k_int / KSTEP;
-      for (int s = 0; s < ksteps; ++s) {
-        const uint64_t a = tc::smem_desc(tbase + 2 * s * lbo_a, lbo_a, 128);
-        const uint64_t b = tc::smem_desc(sbase + P.w1 + 2 * s * lbo_w, lbo_w, 128);
-        if (F8) tc::mma_f8(tmem, a, b, id64, s > 0);
-        else tc::mma_f16(tmem, a, b, id64, s > 0);
-      }
-      tc::mma_commit(bar);
-    }
+    // ---- 2. layer 1; fetch the next tile's row while the MMAs run -------------
+    if (row == 0)
+      issue_layer<F8>(tmem_d, tmem_a, sbase + P.w1, lbo_w, P.k_int / KSTEP, id64, 0, bar);
     {
       const int64_t nt = tl + stride;
       const int64_t nq = tri ? nt * per_tile + (row >> 3) : nt * per_tile + row;
-      locate(M, mip, uvl, nq, nt < ntiles && nq < n, tri, row, cur);
-      if (FAST) gather_fast(mip, P, cur);
+      locate(M, tb, uvl, nq, nt < ntiles && nq < n, tri, row, cur);
+      if (FAST) gather_fast(tb, P, cur);
     }
     bool ok = tc::mbar_wait(bar, phase, kWaitLimit);
     phase ^= 1;
     if (tc::bar_or(bar_id, kRows, !ok)) { aborted = true; break; }
     tc::fence_after_sync();
-    hidden_epilogue<F8>(tmem_row, tile, row, M.act, bias, sc[0], inv_sa[1]);
+    hidden_epilogue<F8>(td, ta, M.act, bias, sc[0], inv_sa[1]);
+    tc::tmem_st_wait();
     tc::fence_before_sync();
-    tc::fence_proxy_async();
     tc::bar_sync(bar_id, kRows);
 
     // ---- 3. layer 2 ----------------------------------------------------------
-    if (row == 0) {
-      tc::fence_after_sync();
-#pragma unroll
-      for (int s = 0; s < kHidden / KSTEP; ++s) {
-        const uint64_t a = tc::smem_desc(tbase + 2 * s * lbo_a, lbo_a, 128);
-        const uint64_t b = tc::smem_desc(sbase + P.w2 + 2 * s * lbo_w, lbo_w, 128);
-        if (F8) tc::mma_f8(tmem, a, b, id64, s > 0);
-        else tc::mma_f16(tmem, a, b, id64, s > 0);
-      }
-      if (!F8) {
-        const uint64_t a = tc::smem_desc(sbase + P.cst, lbo_a, 128);
-        const uint64_t b = tc::smem_desc(sbase + P.wb2, lbo_w, 128);
-        tc::mma_f16(tmem, a, b, id64, 1);
-      }
-      tc::mma_commit(bar);
-    }
+    if (row == 0)
+      issue_layer<F8>(tmem_d, tmem_a, sbase + P.w2, lbo_w, kHidden / KSTEP, id64,
+                      F8 ? 0 : sbase + P.wb2, bar);
     ok = tc::mbar_wait(bar, phase, kWaitLimit);
     phase ^= 1;
     if (tc::bar_or(bar_id, kRows, !ok)) { aborted = true; break; }
     tc::fence_after_sync();
-    hidden_epilogue<F8>(tmem_row, tile, row, M.act, bias + kHidden, sc[1], inv_sa[2]);
+    hidden_epilogue<F8>(td, ta, M.act, bias + kHidden, sc[1], inv_sa[2]);
+    tc::tmem_st_wait();
     tc::fence_before_sync();
-    tc::fence_proxy_async();
     tc::bar_sync(bar_id, kRows);
 
     // ---- 4. layer 3 + output ----------------------------------------------
-    if (row == 0) {
-      tc::fence_after_sync();
-#pragma unroll
-      for (int s = 0; s < kHidden / KSTEP; ++s) {
-        const uint64_t a = tc::smem_desc(tbase + 2 * s * lbo_a, lbo_a, 128);
-        const uint64_t b = tc::smem_desc(sbase + P.w3 + 2 * s * lbo_w3, lbo_w3, 128);
-        if (F8) tc::mma_f8(tmem, a, b, id16, s > 0);
-        else tc::mma_f16(tmem, a, b, id16, s > 0);
-      }
-      if (!F8) {
-        const uint64_t a = tc::smem_desc(sbase + P.cst, lbo_a, 128);
-        const uint64_t b = tc::smem_desc(sbase + P.wb3, lbo_w3, 128);
-        tc::mma_f16(tmem, a, b, id16, 1);
-      }
-      tc::mma_commit(bar);
-    }
+    if (row == 0)
+      issue_layer<F8>(tmem_d, tmem_a, sbase + P.w3, lbo_w3, kHidden / KSTEP, id16,
+                      F8 ? 0 : sbase + P.wb3, bar);
     ok = tc::mbar_wait(bar, phase, kWaitLimit);
     phase ^= 1;
     if (tc::bar_or(bar_id, kRows, !ok)) { aborted = true; break; }
     tc::fence_after_sync();
     float yv[16];
-    tc::tmem_ld16(tmem_row, yv);
+    tc::tmem_ld16(td, yv);
     tc::tmem_ld_wait();
     tc::fence_before_sync();
 #pragma unroll
@@ -825,21 +776,21 @@ __global__ void __launch_bounds__(kRows* NWG, 1) decode_tc_kernel(
   }
 }
 
-template <bool F8, bool FAST, int NWG>
+template <bool F8, bool FAST, int kNWG>
 cudaError_t launch_k(const ntc_material& m, const float* uvl, int64_t n, void* out, int out_dtype,
                      int filter, cudaStream_t s) {
-  const Plan P(m.c0, m.c1, m.bits0, m.bits1, m.encoding == NTC_GRID_PACKED, F8, NWG);
+  const Plan P(m.c0, m.c1, m.bits0, m.bits1, m.encoding == NTC_GRID_PACKED, F8);
   const size_t smem = P.total;
-  cudaError_t e = cudaFuncSetAttribute(decode_tc_kernel<F8, FAST, NWG>,
+  cudaError_t e = cudaFuncSetAttribute(decode_tc_kernel<F8, FAST, kNWG>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int per_tile = filter == NTC_FILTER_TRILINEAR ? kRows / 8 : kRows;
   const int64_t tiles = (n + per_tile - 1) / per_tile;
-  const int64_t ctas = (tiles + NWG - 1) / NWG;
+  const int64_t ctas = (tiles + kNWG - 1) / kNWG;
   const int64_t cap = sm_count();
   const int grid = (int)(ctas < cap ? ctas : cap);
-  decode_tc_kernel<F8, FAST, NWG><<<grid, kRows * NWG, smem, s>>>(m, uvl, n, out, out_dtype,
-                                                                   filter, status_word());
+  decode_tc_kernel<F8, FAST, kNWG><<<grid, kRows * kNWG, smem, s>>>(m, uvl, n, out, out_dtype,
+                                                                    filter, status_word());
   return cudaGetLastError();
 }
 
@@ -847,22 +798,25 @@ template <bool F8, bool FAST>
 cudaError_t launch_shape(const ntc_material& m, const float* uvl, int64_t n, void* out,
                          int out_dtype, int filter, cudaStream_t s, int nwg) {
   switch (nwg) {
-    case 4: return launch_k<F8, FAST, 4>(m, uvl, n, out, out_dtype, filter, s);
-    case 6: return launch_k<F8, FAST, 6>(m, uvl, n, out, out_dtype, filter, s);
-    default: return launch_k<F8, FAST, 8>(m, uvl, n, out, out_dtype, filter, s);
+    case 2: return launch_k<F8, FAST, 2>(m, uvl, n, out, out_dtype, filter, s);
+    case 3: return launch_k<F8, FAST, 3>(m, uvl, n, out, out_dtype, filter, s);
+    default: return launch_k<F8, FAST, 4>(m, uvl, n, out, out_dtype, filter, s);
   }
 }
 
 }  // namespace
 
-// Warpgroups per CTA (one CTA per SM): 4, 6 or 8; 0 = default.
+// Launch shape: one CTA per SM with `nwg` warpgroup pipelines (2, 3 or 4;
+// 0 = 4), each holding 128 of the SM's 512 TMEM columns.
 cudaError_t launch_decode_tc(const ntc_material& m, const float* uvl, int64_t n, void* out,
                              int out_dtype, int filter, cudaStream_t s, int nwg) {
   if (n == 0) return cudaSuccess;
-  if (nwg <= 0) nwg = 6;
-  if (m.precision == NTC_PREC_F8) return launch_shape<true, false>(m, uvl, n, out, out_dtype, filter, s, nwg);
+  if (nwg == 0) nwg = 4;
+  if (nwg < 2 || nwg > 4) return cudaErrorInvalidValue;
+  if (m.precision == NTC_PREC_F8)
+    return launch_shape<true, false>(m, uvl, n, out, out_dtype, filter, s, nwg);
   if (m.precision != NTC_PREC_F16) return cudaErrorInvalidValue;
-  const Plan P(m.c0, m.c1, m.bits0, m.bits1, m.encoding == NTC_GRID_PACKED, false, 1);
+  const Plan P(m.c0, m.c1, m.bits0, m.bits1, m.encoding == NTC_GRID_PACKED, false);
   if (P.fast) return launch_shape<false, true>(m, uvl, n, out, out_dtype, filter, s, nwg);
   return launch_shape<false, false>(m, uvl, n, out, out_dtype, filter, s, nwg);
 }

@@ -138,7 +138,7 @@ def test_decode_f8_close_to_oracle():
     assert oracle.psnr(ref, got) > 35.0
 
 
-@pytest.mark.parametrize("nwg", [4, 6, 8])
+@pytest.mark.parametrize("nwg", [2, 3, 4])
 def test_decode_every_launch_shape(nwg):
     case = make_case(512, 512, 16, 12, 12, k_in=48, seed=57)
     mat, md = device_material(case, precision=ntc.PREC_F16)
@@ -161,7 +161,7 @@ def test_autotune_picks_a_shape_and_stays_correct():
     out = torch.empty((q.shape[0], 16), dtype=torch.float16, device=DEV)
     best, ms = ntc.ntc_autotune_decode(mat, uvl, out)
     try:
-        assert best in (4, 6, 8) and all(v > 0 for v in ms.values())
+        assert best in (2, 3, 4) and all(v > 0 for v in ms.values())
         assert np.abs(_decode(mat, q) - md.decode(q)).max() <= OUT_TOL
     finally:
         ntc.ntc_set_decode_warpgroups(0)
