@@ -229,6 +229,29 @@ int ntc_train_step(const ntc_material* m, const ntc_trainer* tr, const ntc_targe
                    int64_t batch, uint64_t seed, const float* uvl_or_null, float* loss_out,
                    int32_t flags, void* stream);
 
+/* ntc_train_step for callers that cannot allocate device memory: code that
+ * runs inside an engine's frame loop or a real-time thread (cudaMalloc may
+ * synchronise the device and stall it), code that enqueues into a stream that
+ * is being captured into a CUDA graph (allocation is not a capturable
+ * operation), and plugins that only receive device buffers from their host.
+ * The paper has no counterpart: this is a deployment variant of the same step.
+ *
+ * Identical to ntc_train_step except that tr->grad is ignored (may be NULL):
+ * the scratch gradient is a fixed array of NTC_NOALLOC_MAX_PARAMS floats
+ * (8 MiB) compiled into the library, which every GPU that loads the library
+ * holds until the process exits.  tr->n_params above NTC_NOALLOC_MAX_PARAMS
+ * is rejected with NTC_ERR_SHAPE.  Each call clears the first n_params floats
+ * of the array on `stream` before using it; nothing else is allocated.  The
+ * first call on a device looks up the array's device address (with that
+ * device current); make that first call before capturing a stream.  All
+ * calls on a device share the one array: calls that overlap on the GPU
+ * (different streams, or different materials in flight) race and corrupt
+ * each other's gradients. */
+#define NTC_NOALLOC_MAX_PARAMS (1 << 21)
+int ntc_train_step_noalloc(const ntc_material* m, const ntc_trainer* tr, const ntc_target* t,
+                           int64_t batch, uint64_t seed, const float* uvl_or_null,
+                           float* loss_out, int32_t flags, void* stream);
+
 /* Final quantisation (Sec. 4.2): for `cells` cells of c float32 values,
  * index q = clamp(rint(x / Q) + N/2 - 1, 0, N-1) (ties to even), packed into
  * packed_out ([cells][ntc_cell_bytes(c, bits)], may be NULL) and, if

@@ -83,6 +83,7 @@ SIGNATURES = {
     "ntc_decode": (C.c_int, [_P, _P, _I64, _P, _I32, _I32, _I32, _U64, _I64, _P]),
     "ntc_backward": (C.c_int, [_P, _P, _I64, _P, _P, _I32, _U64, _I64, _P]),
     "ntc_train_step": (C.c_int, [_P, _P, _P, _I64, _U64, _P, _P, _I32, _P]),
+    "ntc_train_step_noalloc": (C.c_int, [_P, _P, _P, _I64, _U64, _P, _P, _I32, _P]),
     "ntc_quantize_pack": (C.c_int, [_P, _I64, _I32, _I32, _F, _P, _P, _P]),
     "ntc_unpack": (C.c_int, [_P, _I64, _I32, _I32, _F, _P, _P, _P]),
     "ntc_sample_batch": (C.c_int, [_U64, _I64, _I64, _I32, _I32, _I32, _P, _P]),
@@ -416,6 +417,17 @@ def ntc_train_step(trainer: Trainer, target: Target, batch: int, seed: int, uvl=
     """One fused optimisation step; returns the device loss tensor."""
     m, t, tg = trainer.material.struct, trainer.struct, target.struct
     _call("ntc_train_step", C.byref(m), C.byref(t), C.byref(tg), batch, seed, _ptr(uvl),
+          _ptr(trainer.loss), flags, _stream(stream))
+    return trainer.loss
+
+
+def ntc_train_step_noalloc(trainer: Trainer, target: Target, batch: int, seed: int, uvl=None,
+                           flags=0, stream=None):
+    """ntc_train_step with the scratch gradient in the library's static
+    device array (no caller-provided gradient buffer; see include/ntc.h)."""
+    m, t, tg = trainer.material.struct, trainer.struct, target.struct
+    t.grad = None
+    _call("ntc_train_step_noalloc", C.byref(m), C.byref(t), C.byref(tg), batch, seed, _ptr(uvl),
           _ptr(trainer.loss), flags, _stream(stream))
     return trainer.loss
 

@@ -98,6 +98,16 @@ bool use_simt(const ntc_material* m, int flags) {
 
 }  // namespace
 
+namespace ntc {
+int report_error(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+}  // namespace ntc
+
 extern "C" {
 
 const char* ntc_version(void) { return "ntc-gb300 0.1 (sm_103a)"; }

@@ -79,6 +79,9 @@ cudaError_t launch_sample_features(const ntc_material& m, const float* uvl, int6
 
 int sm_count();
 
+// Record a thread-local error message (ntc_last_error) and return `code`.
+int report_error(int code, const char* fmt, ...);
+
 // Device status word of the current device (bounded waits write
 // NTC_ERR_TIMEOUT there); read and cleared by ntc_device_status.
 int* status_word();
