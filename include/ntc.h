@@ -75,6 +75,9 @@ enum { NTC_DTYPE_F32 = 0, NTC_DTYPE_F16 = 1 };              /* output element ty
 #define NTC_FLAG_NO_NOISE 0x4     /* train_step: no noise while grids still train */
 #define NTC_FLAG_SIMT 0x8         /* force the FP32 CUDA-core kernels (any precision
                                      is converted to FP32 on load) */
+#define NTC_FLAG_GRAD_ONLY 0x10   /* train_step: accumulate the batch's gradient into
+                                     tr->grad and stop (no Adam update, step counter
+                                     unchanged); the next regular step applies the sum */
 
 /* One feature level F^j = (G^j_0, G^j_1) (Sec. 4.1, Table 1). */
 typedef struct {
@@ -224,7 +227,9 @@ int ntc_backward(const ntc_material* m, const float* uvl, int64_t n, const float
  * *tr->step += 1.  Sampling and noise are counter-based from (seed, *step),
  * so the call is CUDA-graph capturable and replays identically.
  * flags: NTC_FLAG_FREEZE_GRIDS (no noise, grids neither differentiated nor
- * updated), NTC_FLAG_NO_NOISE, NTC_FLAG_SIMT. */
+ * updated), NTC_FLAG_NO_NOISE, NTC_FLAG_SIMT, NTC_FLAG_GRAD_ONLY.  FP16
+ * weights train on the tensor cores (tcgen05, ReLU only); FP32 weights or
+ * NTC_FLAG_SIMT on the FP32 CUDA cores. */
 int ntc_train_step(const ntc_material* m, const ntc_trainer* tr, const ntc_target* t,
                    int64_t batch, uint64_t seed, const float* uvl_or_null, float* loss_out,
                    int32_t flags, void* stream);

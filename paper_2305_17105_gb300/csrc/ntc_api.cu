@@ -238,12 +238,11 @@ int ntc_backward(const ntc_material* m, const float* uvl, int64_t n, const float
   a.noise_step = noise_step;
   a.train = 0;
   a.grids = 1;
+  // An arbitrary upstream gradient has no known scale for FP16 operands: the
+  // adjoint always runs in FP32 (FP16 / FP8 weights are widened on load).
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (use_simt(m, flags)) {
-    if (m->k_in > 64) return fail(NTC_ERR_UNSUPPORTED, "FP32 backward supports k_in <= 64");
-    return cuda_status(ntc::launch_backward_simt(*m, a, s), "backward (FP32 CUDA cores)");
-  }
-  return cuda_status(ntc::launch_backward_tc(*m, a, s), "backward (tcgen05)");
+  if (m->k_in > 64) return fail(NTC_ERR_UNSUPPORTED, "backward supports k_in <= 64");
+  return cuda_status(ntc::launch_backward_simt(*m, a, s), "backward (FP32 CUDA cores)");
 }
 
 int ntc_train_step(const ntc_material* m, const ntc_trainer* tr, const ntc_target* t,
@@ -357,9 +356,12 @@ int ntc_train_step(const ntc_material* m, const ntc_trainer* tr, const ntc_targe
     if (m->k_in > 64) return fail(NTC_ERR_UNSUPPORTED, "FP32 training supports k_in <= 64");
     e = ntc::launch_backward_simt(*m, b, s);
   } else {
-    e = ntc::launch_backward_tc(*m, b, s);
+    if (m->act != NTC_ACT_RELU)
+      return fail(NTC_ERR_UNSUPPORTED, "tensor-core training supports ReLU (use NTC_FLAG_SIMT)");
+    e = ntc::launch_train_tc(*m, b, s);
   }
   if (e != cudaSuccess) return cuda_status(e, "train_step forward/backward");
+  if (flags & NTC_FLAG_GRAD_ONLY) return NTC_OK;
   e = ntc::launch_adam(a, a.block_start[a.nseg], s);
   if (e != cudaSuccess) return cuda_status(e, "train_step adam");
   return cuda_status(ntc::launch_advance_step(tr->step, s), "train_step step counter");

@@ -38,7 +38,7 @@ cudaError_t launch_backward_simt(const ntc_material& m, const BwdArgs& a, cudaSt
 
 cudaError_t launch_decode_tc(const ntc_material& m, const float* uvl, int64_t n, void* out,
                              int out_dtype, int filter, cudaStream_t s, int ctas_per_sm);
-cudaError_t launch_backward_tc(const ntc_material& m, const BwdArgs& a, cudaStream_t s);
+cudaError_t launch_train_tc(const ntc_material& m, const BwdArgs& a, cudaStream_t s);
 
 // Adam over the segments of the trainer's parameter array.
 constexpr int kMaxSegs = 2 * NTC_MAX_LEVELS + 6;

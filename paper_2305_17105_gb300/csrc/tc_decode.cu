@@ -821,8 +821,4 @@ cudaError_t launch_decode_tc(const ntc_material& m, const float* uvl, int64_t n,
   return launch_shape<false, false>(m, uvl, n, out, out_dtype, filter, s, nwg);
 }
 
-cudaError_t launch_backward_tc(const ntc_material&, const BwdArgs&, cudaStream_t) {
-  return cudaErrorNotSupported;
-}
-
 }  // namespace ntc

@@ -1,0 +1,109 @@
+"""GPU parity of the training step's gradients (FP32 CUDA-core form and the
+tcgen05 FP16 form) against the FP64 oracle, through ntc_train_step with
+NTC_FLAG_GRAD_ONLY (sampler, noise, forward, loss, backward; no update).
+
+The oracle sees the weights as the step's forward sees them (FP16 copies of
+the masters for the tensor-core form).  Bar: 1e-2 relative error per tensor
+(L2 norm); the loss within 2e-3 relative (FP16 activations).
+"""
+import numpy as np
+import pytest
+import torch
+
+import ntc_inputs as gen
+import oracle
+import paper_2305_17105_gb300 as ntc
+from _cases import make_case
+from _gpu import rel_err, to_np
+
+pytestmark = pytest.mark.gpu
+GRAD_TOL = 1e-2
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ntc.lib()
+
+
+def _trainer(case, precision, total=100):
+    w = case.weights
+    return ntc.Trainer(case.width, case.height, case.channels, case.c0, case.c1, case.bits0,
+                       case.bits1, case.q0, case.q1, case.val0, case.val1, [w[0], w[2], w[4]],
+                       [w[1], w[3], w[5]], case.k_in, precision, case.act, case.out_act,
+                       total_steps=total)
+
+
+def _oracle_weights(case, precision):
+    w = [np.asarray(a, np.float64) for a in case.weights]
+    if precision == ntc.PREC_F16:
+        for i in (0, 2, 4):
+            w[i] = case.weights[i].astype(np.float16).astype(np.float64)
+    return w
+
+
+@pytest.mark.parametrize("precision", [ntc.PREC_F32, ntc.PREC_F16])
+@pytest.mark.parametrize("shape", [
+    dict(width=64, height=64, channels=6, c0=8, c1=8, k_in=32),
+    dict(width=128, height=128, channels=12, c0=16, c1=16, k_in=48),
+    dict(width=256, height=128, channels=16, c0=12, c1=12, k_in=48),
+    dict(width=32, height=32, channels=3, c0=3, c1=5, k_in=32),
+])
+def test_train_gradients_match_oracle(shape, precision):
+    case = make_case(seed=71, **shape)
+    chain = gen.box_mip_chain_u8(gen.synthetic_texture(case.width, case.height, case.channels,
+                                                       seed=1071))
+    tr = _trainer(case, precision)
+    target = ntc.Target(chain)
+    batch, seed, step = 5 * 256 + 77, 4242, 3
+    tr.step_t.fill_(step)
+    loss = ntc.ntc_train_step(tr, target, batch, seed, flags=ntc.FLAG_GRAD_ONLY).item()
+    assert ntc.ntc_device_status() == ntc.OK
+    assert int(tr.step_t.item()) == step  # no update, no advance
+    md = case.oracle_model(weights=_oracle_weights(case, precision), quantized=False)
+    xym = oracle.sample_batch(seed, step, batch, case.width, case.height, md.mips)
+    lref, gref = md.loss_grad_xym(xym, oracle.targets_of_xym(chain, xym), noise=(seed, step))
+    assert abs(loss - lref) <= 2e-3 * lref, (loss, lref)
+    L = len(case.val0)
+    refs = gref["grid0"] + gref["grid1"] + gref["w"]
+    for k, (v, r) in enumerate(zip(tr.grad_views, refs)):
+        err = rel_err(to_np(v), r.reshape(v.shape))
+        assert err <= GRAD_TOL, (k, err)
+
+
+def test_train_f16_full_step_and_accumulation():
+    """GRAD_ONLY twice then a regular step equals the sum of three batches'
+    gradients applied once (gradient accumulation); the scratch gradient is
+    left zeroed."""
+    case = make_case(128, 128, 12, 16, 16, k_in=48, seed=72)
+    chain = gen.box_mip_chain_u8(gen.synthetic_texture(128, 128, 12, seed=1072))
+    target = ntc.Target(chain)
+    tr = _trainer(case, ntc.PREC_F16)
+    ntc.ntc_train_step(tr, target, 1000, 5, flags=ntc.FLAG_GRAD_ONLY)
+    g1 = tr.grad.clone()
+    ntc.ntc_train_step(tr, target, 1000, 5, flags=ntc.FLAG_GRAD_ONLY)
+    assert rel_err(to_np(tr.grad), 2 * to_np(g1)) < 1e-3
+    p0 = tr.params.clone()
+    ntc.ntc_train_step(tr, target, 1000, 5)
+    assert ntc.ntc_device_status() == ntc.OK
+    assert int(tr.step_t.item()) == 1
+    assert float(tr.grad.abs().max()) == 0.0
+    assert float((tr.params - p0).abs().max()) > 0
+    # the FP16 weight copies follow the masters
+    for wc, wm in zip(tr.material.weights, tr.w_master):
+        assert torch.equal(wc, wm.half())
+
+
+def test_train_f16_reduces_loss_like_fp32():
+    """Both forms lower the loss on the same material at a similar rate."""
+    case = make_case(128, 128, 8, 8, 8, k_in=32, seed=73)
+    chain = gen.box_mip_chain_u8(gen.synthetic_texture(128, 128, 8, seed=1073))
+    target = ntc.Target(chain)
+    curves = {}
+    for prec in (ntc.PREC_F32, ntc.PREC_F16):
+        tr = _trainer(case, prec, total=300)
+        curves[prec] = [ntc.ntc_train_step(tr, target, 4096, 9).item() for _ in range(300)]
+    a, b = np.mean(curves[ntc.PREC_F32][-20:]), np.mean(curves[ntc.PREC_F16][-20:])
+    assert a < 0.5 * np.mean(curves[ntc.PREC_F32][:5])
+    assert abs(a - b) <= 0.1 * a, (a, b)
