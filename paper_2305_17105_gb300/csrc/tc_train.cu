@@ -238,12 +238,14 @@ __device__ __forceinline__ void issue_kmajor(uint32_t d, uint32_t a, uint32_t a_
 }
 
 // MN-major operands with K = the 128 texels of the tile: 8 K-steps of 16
-// texels (2 row groups = 256 bytes); LBO = the 8-unit group stride (2048),
-// SBO = the 8-texel group stride (128).
+// texels (2 row groups = 256 bytes).  Without swizzling the descriptor's
+// stride-dimension offset steps between core matrices along M/N (the 8-unit
+// groups, 2048 bytes apart) and the leading-dimension offset along K (the
+// 8-texel groups, 128 bytes apart), as in the K-major case.
 __device__ __forceinline__ void issue_mnmajor(uint32_t d, uint32_t a, uint32_t b, uint32_t id,
                                               uint32_t acc0) {
   for (int s = 0; s < kRows / 16; ++s)
-    tc::mma_f16(d, tc::smem_desc(a + 256 * s, kGroup, 128), tc::smem_desc(b + 256 * s, kGroup, 128),
+    tc::mma_f16(d, tc::smem_desc(a + 256 * s, 128, kGroup), tc::smem_desc(b + 256 * s, 128, kGroup),
                 id, (s > 0) | acc0);
 }
 
