@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="auto", choices=["auto", "f32", "f16", "f8"])
-    ap.add_argument("--train-precision", default="f32", choices=["f32", "f16"])
+    ap.add_argument("--train-precision", default="auto", choices=["auto", "f32", "f16"])
     ap.add_argument("--queries", type=int, default=1 << 24)
     ap.add_argument("--batch", type=int, default=1 << 18)
     ap.add_argument("--cpu-seconds", type=float, default=8.0,
@@ -306,6 +306,8 @@ def main():
     if precision == "auto":
         precision = os.environ.get("NTC_BENCH_PRECISION", "f16")
     train_prec = args.train_precision
+    if train_prec == "auto":
+        train_prec = "f32" if precision == "f32" else "f16"
     dev = "cuda"
     stream = torch.cuda.current_stream()
 
@@ -409,9 +411,9 @@ def main():
     # ---- the plain FP32 CUDA-core form on the same inputs ------------------
     fp32 = None
     if precision != "f32" and not args.no_fp32_compare:
-        mat32 = mat.with_(weights=[w.float() if w.dtype == torch.float16 else w for w in mat.weights],
-                          precision=ntc.PREC_F32) if precision == "f16" else None
-        if mat32 is not None:
+        fp32 = {}
+        if precision == "f16":
+            mat32 = mat.with_(weights=[w.float() for w in mat.weights], precision=ntc.PREC_F32)
             for _ in range(2):
                 ntc.ntc_decode(mat32, q_dev, out=out)
             torch.cuda.synchronize()
@@ -421,8 +423,22 @@ def main():
                 ntc.ntc_decode(mat32, q_dev, out=out)
             b.record(stream)
             torch.cuda.synchronize()
-            fp32 = {"decode_texels_per_s": 3 * args.queries / (a.elapsed_time(b) / 1e3)}
-            fp32["speedup"] = value / world / fp32["decode_texels_per_s"]
+            fp32["decode_texels_per_s"] = 3 * args.queries / (a.elapsed_time(b) / 1e3)
+            fp32["decode_speedup"] = value / world / fp32["decode_texels_per_s"]
+        if train_prec != "f32":
+            tr32, _, _, _, _ = make_trainer("f32", 16)
+            for _ in range(2):
+                ntc.ntc_train_step(tr32, target, args.batch, seed)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(3):
+                ntc.ntc_train_step(tr32, target, args.batch, seed)
+            b.record(stream)
+            torch.cuda.synchronize()
+            fp32["train_samples_per_s"] = 3 * args.batch / (a.elapsed_time(b) / 1e3)
+            fp32["train_speedup"] = train_rate / world / fp32["train_samples_per_s"]
+            del tr32
 
     # ---- CPU oracle baseline (rank 0, N = 1) --------------------------------
     cpu = None
