@@ -41,8 +41,13 @@ namespace {
 
 constexpr int kRows = 128;
 constexpr int kN3 = 16;
-constexpr int kColA = 64;              // A operand columns follow D's 64
-constexpr int kColCst = kColA + 32;    // FP16: constant-one block after H (32 columns)
+// TMEM columns of a warpgroup (128): the FP32 accumulator D, the hidden
+// rows H (A operand of layers 2 and 3), the input rows X (A operand of layer
+// 1; separate from H so the next tile's X is built while layer 2 runs) and the
+// constant-one block of the FP16 bias steps.
+constexpr int kColH = 64;              // FP16: 32 columns (64 halves); FP8: 16
+constexpr int kColX = 96;              // FP16: up to 24 columns (48 halves); FP8: 16
+constexpr int kColCst = 120;           // FP16: 8 columns
 constexpr uint32_t kWaitLimit = 1u << 22;
 
 template <bool F8>
@@ -299,16 +304,30 @@ struct Row {
   int valid;
 };
 
+// A query's (u, v, lod), loaded ahead of use.
+struct Query {
+  float u, v, l;
+  int valid;
+};
+__device__ __forceinline__ Query load_query(const float* __restrict__ uvl, int64_t q, bool valid) {
+  Query r{0.f, 0.f, 0.f, valid};
+  if (valid) {
+    r.u = __ldg(uvl + 3 * q);
+    r.v = __ldg(uvl + 3 * q + 1);
+    r.l = __ldg(uvl + 3 * q + 2);
+  }
+  return r;
+}
+
 // Query -> texel of this row (nearest: one per query; trilinear: tap `row & 7`
 // of query `row / 8`).
-__device__ __forceinline__ void locate(const ntc_material& M, const MipTab* tb,
-                                       const float* __restrict__ uvl, int64_t q, bool valid,
+__device__ __forceinline__ void locate(const ntc_material& M, const MipTab* tb, const Query& qu,
                                        bool tri, int row, Row& r) {
-  r.valid = valid;
+  r.valid = qu.valid;
   r.wtap = 0.f;
   r.x = r.y = r.m = 0;
-  if (!valid) return;
-  const float u = __ldg(uvl + 3 * q), v = __ldg(uvl + 3 * q + 1), l = __ldg(uvl + 3 * q + 2);
+  if (!qu.valid) return;
+  const float u = qu.u, v = qu.v, l = qu.l;
   if (!tri) {
     const int m = !(l >= 0.f) ? 0 : (l >= (float)(M.mips - 1) ? M.mips - 1 : (int)floorf(l));
     const int wm = tb->wm[m], hm = tb->hm[m];
@@ -571,7 +590,8 @@ __device__ __forceinline__ void hidden_epilogue(uint32_t td, uint32_t ta, int ac
 template <bool F8>
 __device__ __forceinline__ void issue_layer(uint32_t tmem_d, uint32_t tmem_a, uint32_t b_addr,
                                             uint32_t lbo, int ksteps, uint32_t id,
-                                            uint32_t bias_b_addr, uint64_t* bar) {
+                                            uint32_t bias_b_addr, uint32_t tmem_cst,
+                                            uint64_t* bar) {
   tc::fence_after_sync();
   for (int s = 0; s < ksteps; ++s) {
     const uint64_t b = tc::smem_desc(b_addr + 2 * s * lbo, lbo, 128);
@@ -580,7 +600,7 @@ __device__ __forceinline__ void issue_layer(uint32_t tmem_d, uint32_t tmem_a, ui
   }
   if (!F8 && bias_b_addr) {
     const uint64_t b = tc::smem_desc(bias_b_addr, lbo, 128);
-    tc::mma_f16_ta(tmem_d, tmem_a + (kColCst - kColA), b, id, 1);
+    tc::mma_f16_ta(tmem_d, tmem_cst, b, id, 1);
   }
   tc::mma_commit(bar);
 }
@@ -592,7 +612,7 @@ __global__ void __launch_bounds__(kRows* kNWG, 1) decode_tc_kernel(
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   __shared__ uint64_t mbar[kNWG];
   __shared__ uint32_t tmem_base;
-  __shared__ int abort_any;
+  __shared__ int wg_abort[kNWG];
   constexpr int KSTEP = Cfg<F8>::KSTEP;
   constexpr uint32_t kCols = kNWG <= 2 ? 256 : 512;  // 128 columns per warpgroup
   const Plan P(M.c0, M.c1, M.bits0, M.bits1, M.encoding == NTC_GRID_PACKED, F8);
@@ -606,8 +626,10 @@ __global__ void __launch_bounds__(kRows* kNWG, 1) decode_tc_kernel(
     tc::tmem_alloc(&tmem_base, kCols);
     tc::tmem_relinquish();
   }
-  if (tid < kNWG) tc::mbar_init(&mbar[tid], 1);
-  if (tid == 0) abort_any = 0;
+  if (tid < kNWG) {
+    tc::mbar_init(&mbar[tid], 1);
+    wg_abort[tid] = 0;
+  }
   tc::fence_mbar_init();
   tc::fence_proxy_async();
   tc::fence_before_sync();
@@ -616,13 +638,13 @@ __global__ void __launch_bounds__(kRows* kNWG, 1) decode_tc_kernel(
   // this warpgroup's 128 columns; per-thread addresses carry the warp's lane quarter
   const uint32_t tw = tmem_base + 128u * wg;
   const uint32_t lane = (uint32_t)((warp & 3) * 32) << 16;
-  const uint32_t td = tw + lane;            // D row of this thread
-  const uint32_t ta = tw + kColA + lane;    // A row of this thread
+  const uint32_t td = tw + lane, th = tw + kColH + lane, tx = tw + kColX + lane;
   uint64_t* bar = &mbar[wg];
+  volatile int* abort_flag = &wg_abort[wg];
   if (!F8) {
     // constant-one A block (bias steps of layers 2 and 3): k = 0, 1 are one
-    tc::tmem_st4(ta + (kColCst - kColA), make_uint4(tc::pack_f16x2(1.f, 1.f), 0, 0, 0));
-    tc::tmem_st4(ta + (kColCst - kColA) + 4, make_uint4(0, 0, 0, 0));
+    tc::tmem_st4(tw + kColCst + lane, make_uint4(tc::pack_f16x2(1.f, 1.f), 0, 0, 0));
+    tc::tmem_st4(tw + kColCst + 4 + lane, make_uint4(0, 0, 0, 0));
   }
 
   float sc[3] = {1.f, 1.f, 1.f}, inv_sa[3] = {1.f, 1.f, 1.f};
@@ -638,74 +660,88 @@ __global__ void __launch_bounds__(kRows* kNWG, 1) decode_tc_kernel(
   const uint32_t sbase = tc::smem_u32(sm);
   constexpr uint32_t lbo_w = (kHidden / 8) * 128, lbo_w3 = (kN3 / 8) * 128;
   constexpr uint32_t id64 = tc::idesc(kRows, kHidden), id16 = tc::idesc(kRows, kN3);
-  const uint32_t tmem_d = tw, tmem_a = tw + kColA;
 
   const bool tri = filter == NTC_FILTER_TRILINEAR;
   const int per_tile = tri ? kRows / 8 : kRows;
   const int64_t ntiles = (n + per_tile - 1) / per_tile;
   const int64_t stride = (int64_t)gridDim.x * kNWG;
+  auto qindex = [&](int64_t t) { return tri ? t * per_tile + (row >> 3) : t * per_tile + row; };
   uint32_t phase = 0;
   const int C = M.channels;
   bool aborted = false;
 
-  // the row of the first tile (later rows are fetched one tile ahead)
-  Row cur;
+  // Prologue: the first tile's input rows, and the next tile's query.
   int64_t tl = (int64_t)blockIdx.x * kNWG + wg;
+  int cur_valid;
+  float cur_wtap;
+  Query nq;
   {
-    const int64_t q = tri ? tl * per_tile + (row >> 3) : tl * per_tile + row;
-    locate(M, tb, uvl, q, tl < ntiles && q < n, tri, row, cur);
-    if (FAST) gather_fast(tb, P, cur);
+    const int64_t q0 = qindex(tl);
+    Row r;
+    locate(M, tb, load_query(uvl, q0, tl < ntiles && q0 < n), tri, row, r);
+    if (FAST) {
+      gather_fast(tb, P, r);
+      build_fast(M, P, sm, r, tx);
+    } else {
+      build_generic<F8>(M, P, sm, r, tx, inv_sa[0]);
+    }
+    cur_valid = r.valid;
+    cur_wtap = r.wtap;
+    const int64_t q1 = qindex(tl + stride);
+    nq = load_query(uvl, q1, tl + stride < ntiles && q1 < n);
+    tc::tmem_st_wait();
+    tc::fence_before_sync();
+    tc::bar_sync(bar_id, kRows);
   }
 
   for (; tl < ntiles; tl += stride) {
-    const int64_t q = tri ? tl * per_tile + (row >> 3) : tl * per_tile + row;
-    const bool valid = cur.valid != 0;
-    const float wtap = cur.wtap;
-    // ---- 1. features -> A ----------------------------------------------------
-    if (FAST) build_fast(M, P, sm, cur, ta);
-    else build_generic<F8>(M, P, sm, cur, ta, inv_sa[0]);
-    tc::tmem_st_wait();
-    tc::fence_before_sync();
-    tc::bar_sync(bar_id, kRows);
+    const int64_t q = qindex(tl);
+    const bool valid = cur_valid != 0;
+    const float wtap = cur_wtap;
 
-    // ---- 2. layer 1; fetch the next tile's row while the MMAs run -------------
+    // ---- layer 1 (X of this tile is in TMEM) ---------------------------------
     if (row == 0)
-      issue_layer<F8>(tmem_d, tmem_a, sbase + P.w1, lbo_w, P.k_int / KSTEP, id64, 0, bar);
+      issue_layer<F8>(tw, tw + kColX, sbase + P.w1, lbo_w, P.k_int / KSTEP, id64, 0, 0, bar);
+    // next tile: texel and cell gathers now, its query two tiles ahead
+    Row nxt;
+    locate(M, tb, nq, tri, row, nxt);
+    if (FAST) gather_fast(tb, P, nxt);
     {
-      const int64_t nt = tl + stride;
-      const int64_t nq = tri ? nt * per_tile + (row >> 3) : nt * per_tile + row;
-      locate(M, tb, uvl, nq, nt < ntiles && nq < n, tri, row, cur);
-      if (FAST) gather_fast(tb, P, cur);
+      const int64_t t2 = tl + 2 * stride;
+      const int64_t q2 = qindex(t2);
+      nq = load_query(uvl, q2, t2 < ntiles && q2 < n);
     }
-    bool ok = tc::mbar_wait(bar, phase, kWaitLimit);
+    if (!tc::mbar_wait(bar, phase, kWaitLimit)) *abort_flag = 1;
     phase ^= 1;
-    if (tc::bar_or(bar_id, kRows, !ok)) { aborted = true; break; }
     tc::fence_after_sync();
-    hidden_epilogue<F8>(td, ta, M.act, bias, sc[0], inv_sa[1]);
+    hidden_epilogue<F8>(td, th, M.act, bias, sc[0], inv_sa[1]);
     tc::tmem_st_wait();
     tc::fence_before_sync();
     tc::bar_sync(bar_id, kRows);
 
-    // ---- 3. layer 2 ----------------------------------------------------------
+    // ---- layer 2; meanwhile the next tile's X (layer 1 is done with X) -------
     if (row == 0)
-      issue_layer<F8>(tmem_d, tmem_a, sbase + P.w2, lbo_w, kHidden / KSTEP, id64,
-                      F8 ? 0 : sbase + P.wb2, bar);
-    ok = tc::mbar_wait(bar, phase, kWaitLimit);
+      issue_layer<F8>(tw, tw + kColH, sbase + P.w2, lbo_w, kHidden / KSTEP, id64,
+                      F8 ? 0 : sbase + P.wb2, tw + kColCst, bar);
+    if (FAST) build_fast(M, P, sm, nxt, tx);
+    else build_generic<F8>(M, P, sm, nxt, tx, inv_sa[0]);
+    cur_valid = nxt.valid;
+    cur_wtap = nxt.wtap;
+    if (!tc::mbar_wait(bar, phase, kWaitLimit)) *abort_flag = 1;
     phase ^= 1;
-    if (tc::bar_or(bar_id, kRows, !ok)) { aborted = true; break; }
     tc::fence_after_sync();
-    hidden_epilogue<F8>(td, ta, M.act, bias + kHidden, sc[1], inv_sa[2]);
+    hidden_epilogue<F8>(td, th, M.act, bias + kHidden, sc[1], inv_sa[2]);
     tc::tmem_st_wait();
     tc::fence_before_sync();
     tc::bar_sync(bar_id, kRows);
+    if (*abort_flag) { aborted = true; break; }
 
-    // ---- 4. layer 3 + output ----------------------------------------------
+    // ---- layer 3 + output ----------------------------------------------
     if (row == 0)
-      issue_layer<F8>(tmem_d, tmem_a, sbase + P.w3, lbo_w3, kHidden / KSTEP, id16,
-                      F8 ? 0 : sbase + P.wb3, bar);
-    ok = tc::mbar_wait(bar, phase, kWaitLimit);
+      issue_layer<F8>(tw, tw + kColH, sbase + P.w3, lbo_w3, kHidden / KSTEP, id16,
+                      F8 ? 0 : sbase + P.wb3, tw + kColCst, bar);
+    if (!tc::mbar_wait(bar, phase, kWaitLimit)) *abort_flag = 1;
     phase ^= 1;
-    if (tc::bar_or(bar_id, kRows, !ok)) { aborted = true; break; }
     tc::fence_after_sync();
     float yv[16];
     tc::tmem_ld16(td, yv);
@@ -764,12 +800,18 @@ __global__ void __launch_bounds__(kRows* kNWG, 1) decode_tc_kernel(
         }
       }
     }
+    // the next tile's layer 1 overwrites D: every row must have read it
+    tc::bar_sync(bar_id, kRows);
+    if (*abort_flag) { aborted = true; break; }
   }
 
-  if (aborted && row == 0) abort_any = 1;
   tc::fence_before_sync();
   __syncthreads();
-  if (tid == 0 && abort_any) atomicExch(status, NTC_ERR_TIMEOUT);
+  if (tid == 0) {
+    int any = 0;
+    for (int w = 0; w < kNWG; ++w) any |= wg_abort[w];
+    if (any || aborted) atomicExch(status, NTC_ERR_TIMEOUT);
+  }
   if (warp == 0) {
     tc::fence_after_sync();
     tc::tmem_dealloc(tmem_base, kCols);
