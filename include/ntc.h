@@ -234,6 +234,45 @@ int ntc_train_step(const ntc_material* m, const ntc_trainer* tr, const ntc_targe
                    int64_t batch, uint64_t seed, const float* uvl_or_null, float* loss_out,
                    int32_t flags, void* stream);
 
+/* ---- many materials in one launch -------------------------------------- */
+
+/* A prepared batch of materials (filled by ntc_batch_prepare, host memory). */
+typedef struct {
+  const void* workspace;   /* device descriptor block, ntc_batch_workspace_bytes() bytes */
+  int32_t n_materials;
+  int32_t filter;          /* NTC_FILTER_* the batch was prepared for */
+  int64_t total_queries;   /* rows of the concatenated uvl array */
+  int64_t total_outputs;   /* elements of the concatenated output: sum of n_i * channels_i */
+  int64_t total_tiles;
+  int32_t wg_smem;         /* internal launch parameters */
+  int32_t fast;
+} ntc_batch;
+
+#define NTC_MAX_BATCH 1024
+
+/* Bytes of the device workspace a batch descriptor needs (about 0.4 MB). */
+size_t ntc_batch_workspace_bytes(void);
+
+/* Prepare a batch decode of n_materials materials (HOST array `mats`, all
+ * NTC_PREC_F16, of one grid layout class) with n_queries[i] (HOST) queries
+ * each: validates every material, lays the materials' queries out back to
+ * back (material i's rows start at sum_{j<i} n_queries[j] of the uvl array
+ * and its outputs at sum_{j<i} n_queries[j] * channels_j of the output
+ * array), splits them into tiles ordered by material and copies the
+ * descriptor into `workspace` (device, caller-owned) on `stream` with a
+ * host-to-device copy from pageable memory: call it outside graph capture.
+ * The workspace must stay untouched while batch decodes that use it run. */
+int ntc_batch_prepare(const ntc_material* mats, const int64_t* n_queries, int32_t n_materials,
+                      int32_t filter, void* workspace, size_t workspace_bytes, ntc_batch* batch_out,
+                      void* stream);
+
+/* Decode every material of a prepared batch in one persistent launch (the
+ * multi-material case of Sec. 5.2 / App. A, done by sorting work by material
+ * instead of per-SIMD-group loops): uvl [total_queries][3], out (f16 or f32)
+ * [total_outputs].  Only launches a kernel: capturable in a CUDA graph. */
+int ntc_decode_batched(const ntc_batch* batch, const float* uvl, void* out, int32_t out_dtype,
+                       void* stream);
+
 /* ntc_train_step for callers that cannot allocate device memory: code that
  * runs inside an engine's frame loop or a real-time thread (cudaMalloc may
  * synchronise the device and stall it), code that enqueues into a stream that

@@ -69,6 +69,12 @@ class ntc_trainer(C.Structure):
                 ("eps", C.c_float)]
 
 
+class ntc_batch(C.Structure):
+    _fields_ = [("workspace", C.c_void_p), ("n_materials", C.c_int32), ("filter", C.c_int32),
+                ("total_queries", C.c_int64), ("total_outputs", C.c_int64),
+                ("total_tiles", C.c_int64), ("wg_smem", C.c_int32), ("fast", C.c_int32)]
+
+
 class ntc_target(C.Structure):
     _fields_ = [("texels", C.c_void_p), ("offset", C.c_int64 * MAX_MIPS)]
 
@@ -89,6 +95,9 @@ SIGNATURES = {
     "ntc_sample_batch": (C.c_int, [_U64, _I64, _I64, _I32, _I32, _I32, _P, _P]),
     "ntc_sample_features": (C.c_int, [_P, _P, _I64, _P, _I32, _U64, _I64, _P]),
     "ntc_device_status": (C.c_int, [_I32]),
+    "ntc_batch_workspace_bytes": (C.c_size_t, []),
+    "ntc_batch_prepare": (C.c_int, [_P, _P, _I32, _I32, _P, C.c_size_t, _P, _P]),
+    "ntc_decode_batched": (C.c_int, [_P, _P, _P, _I32, _P]),
     "ntc_set_decode_warpgroups": (C.c_int, [_I32]),
     "ntc_autotune_decode": (C.c_int, [_P, _P, _I64, _P, _I32, _I32, _P, _P, _P]),
 }
@@ -319,6 +328,38 @@ def ntc_sample_features(mat: Material, uvl, flags=0, noise_seed=0, noise_step=0,
     _call("ntc_sample_features", C.byref(s), _ptr(uvl), uvl.shape[0], _ptr(rows), flags,
           noise_seed, noise_step, _stream(stream))
     return rows
+
+
+class Batch:
+    """Materials decoded together by one persistent launch.  Keeps the
+    device workspace and the prepared descriptor alive; `offsets` gives each
+    material's first query row and first output element."""
+
+    def __init__(self, materials, n_queries, filter=FILTER_NEAREST, device="cuda", stream=None):
+        n = len(materials)
+        self.materials = list(materials)
+        arr = (ntc_material * n)()
+        for i, m in enumerate(materials):
+            arr[i] = m.struct
+        nq = (C.c_int64 * n)(*[int(x) for x in n_queries])
+        ws_bytes = lib().ntc_batch_workspace_bytes()
+        self.workspace = torch.empty(ws_bytes, dtype=torch.uint8, device=device)
+        self.desc = ntc_batch()
+        _call("ntc_batch_prepare", C.cast(arr, C.c_void_p), C.cast(nq, C.c_void_p), n, filter,
+              _ptr(self.workspace), ws_bytes, C.byref(self.desc), _stream(stream))
+        self.n_queries = [int(x) for x in n_queries]
+        self.q_offsets = np.concatenate([[0], np.cumsum(self.n_queries)]).astype(np.int64)
+        self.o_offsets = np.concatenate(
+            [[0], np.cumsum([q * m.channels for q, m in zip(self.n_queries, materials)])]).astype(np.int64)
+
+
+def ntc_decode_batched(batch: Batch, uvl, out_dtype=torch.float32, out=None, stream=None):
+    _dev(uvl, "uvl")
+    if out is None:
+        out = torch.empty(int(batch.desc.total_outputs), dtype=out_dtype, device=uvl.device)
+    dt = DTYPE_F16 if out.dtype == torch.float16 else DTYPE_F32
+    _call("ntc_decode_batched", C.byref(batch.desc), _ptr(uvl), _ptr(out), dt, _stream(stream))
+    return out
 
 
 # ----------------------------------------------------------------------------

@@ -50,41 +50,67 @@ namespace {
 // One Adam step (Kingma & Ba, bias-corrected) at the device step counter t,
 // learning rate lr0 (1 + cos(pi t / T)) / 2 per group, then the grid clamp
 // to [-(N-1)/2 Q, N/2 Q] (Sec. 4.2: clamp after the update).  The gradient is
-// zeroed for the next step; half-precision weight copies are refreshed.
+// zeroed for the next step; half-precision weight copies are refreshed.  Each
+// thread owns kAdamPerThread consecutive elements (float4 accesses); the
+// schedule factors are computed once per block in FP32.
 __global__ void __launch_bounds__(kAdamBlock) adam_kernel(const AdamArgs A) {
-  __shared__ float s_lr, s_c1, s_c2;
+  __shared__ float s_lr, s_ic1, s_ic2;
   const int64_t b = blockIdx.x;
   int s = 0;
   while (s + 1 < A.nseg && b >= A.block_start[s + 1]) ++s;
   const AdamSeg& S = A.seg[s];
   if (threadIdx.x == 0) {
     const int64_t t = *A.step;
-    const double pi = 3.14159265358979323846;
-    const double lr = (double)A.lr[S.group] * 0.5 * (1.0 + cos(pi * (double)t / (double)A.total));
-    s_lr = (float)lr;
-    s_c1 = (float)(1.0 - pow((double)A.beta1, (double)(t + 1)));
-    s_c2 = (float)(1.0 - pow((double)A.beta2, (double)(t + 1)));
+    const float x = (float)((double)t / (double)A.total);
+    s_lr = A.lr[S.group] * 0.5f * (1.f + cospif(x));
+    s_ic1 = 1.f / (1.f - powf(A.beta1, (float)(t + 1)));
+    s_ic2 = 1.f / (1.f - powf(A.beta2, (float)(t + 1)));
   }
   __syncthreads();
   if (A.freeze_grids && S.group == 0) return;
-  const float lr = s_lr, inv_c1 = 1.f / s_c1, inv_c2 = 1.f / s_c2;
+  const float lr = s_lr, inv_c1 = s_ic1, inv_c2 = s_ic2;
   const float b1 = A.beta1, b2 = A.beta2, eps = A.eps;
-  const int64_t first = (b - A.block_start[s]) * (int64_t)(kAdamBlock * kAdamPerThread) + threadIdx.x;
-#pragma unroll
-  for (int k = 0; k < kAdamPerThread; ++k) {
-    const int64_t idx = first + (int64_t)k * kAdamBlock;
-    if (idx >= S.len) break;
-    const int64_t e = S.off + idx;
-    const float g = A.g[e];
-    const float m = fmaf(b1, A.m[e], (1.f - b1) * g);
-    const float v = fmaf(b2, A.v[e], (1.f - b2) * g * g);
-    float p = A.p[e] - lr * (m * inv_c1) / (sqrtf(v * inv_c2) + eps);
-    if (S.clamp) p = fminf(fmaxf(p, S.lo), S.hi);
-    A.m[e] = m;
-    A.v[e] = v;
-    A.p[e] = p;
-    A.g[e] = 0.f;
-    if (S.half_copy) S.half_copy[idx] = __float2half_rn(p);
+  const int64_t first =
+      ((b - A.block_start[s]) * (int64_t)kAdamBlock + threadIdx.x) * kAdamPerThread;
+  if (first >= S.len) return;
+  const int64_t e0 = S.off + first;
+  auto upd = [&](float p, float m, float v, float g, float& po, float& mo, float& vo) {
+    mo = fmaf(b1, m, (1.f - b1) * g);
+    vo = fmaf(b2, v, (1.f - b2) * g * g);
+    po = p - lr * (mo * inv_c1) / (sqrtf(vo * inv_c2) + eps);
+    if (S.clamp) po = fminf(fmaxf(po, S.lo), S.hi);
+  };
+  if (first + kAdamPerThread <= S.len) {
+    // segments start 16-byte aligned: whole float4 groups
+    const float4 p = *reinterpret_cast<const float4*>(A.p + e0);
+    const float4 m = *reinterpret_cast<const float4*>(A.m + e0);
+    const float4 v = *reinterpret_cast<const float4*>(A.v + e0);
+    const float4 g = *reinterpret_cast<const float4*>(A.g + e0);
+    float4 po, mo, vo;
+    upd(p.x, m.x, v.x, g.x, po.x, mo.x, vo.x);
+    upd(p.y, m.y, v.y, g.y, po.y, mo.y, vo.y);
+    upd(p.z, m.z, v.z, g.z, po.z, mo.z, vo.z);
+    upd(p.w, m.w, v.w, g.w, po.w, mo.w, vo.w);
+    *reinterpret_cast<float4*>(A.p + e0) = po;
+    *reinterpret_cast<float4*>(A.m + e0) = mo;
+    *reinterpret_cast<float4*>(A.v + e0) = vo;
+    *reinterpret_cast<float4*>(A.g + e0) = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (S.half_copy) {
+      __half2* h = reinterpret_cast<__half2*>(S.half_copy + first);
+      h[0] = __floats2half2_rn(po.x, po.y);
+      h[1] = __floats2half2_rn(po.z, po.w);
+    }
+  } else {
+    for (int64_t k = first; k < S.len; ++k) {
+      const int64_t e = S.off + k;
+      float po, mo, vo;
+      upd(A.p[e], A.m[e], A.v[e], A.g[e], po, mo, vo);
+      A.p[e] = po;
+      A.m[e] = mo;
+      A.v[e] = vo;
+      A.g[e] = 0.f;
+      if (S.half_copy) S.half_copy[k] = __float2half_rn(po);
+    }
   }
 }
 

@@ -1,6 +1,7 @@
 // C-ABI entry points of libntc.so (declared in include/ntc.h): argument
 // validation, error reporting and dispatch to the kernels.
 #include <atomic>
+#include <vector>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -365,6 +366,79 @@ int ntc_train_step(const ntc_material* m, const ntc_trainer* tr, const ntc_targe
   e = ntc::launch_adam(a, a.block_start[a.nseg], s);
   if (e != cudaSuccess) return cuda_status(e, "train_step adam");
   return cuda_status(ntc::launch_advance_step(tr->step, s), "train_step step counter");
+}
+
+size_t ntc_batch_workspace_bytes(void) { return sizeof(ntc::BatchHeader); }
+
+int ntc_batch_prepare(const ntc_material* mats, const int64_t* n_queries, int32_t n_materials,
+                      int32_t filter, void* workspace, size_t workspace_bytes, ntc_batch* batch_out,
+                      void* stream) {
+  if (!mats || !n_queries || !batch_out) return fail(NTC_ERR_ARG, "batch: NULL argument");
+  if (n_materials < 1 || n_materials > NTC_MAX_BATCH)
+    return fail(NTC_ERR_ARG, "batch: n_materials = %d outside 1..%d", n_materials, NTC_MAX_BATCH);
+  if (filter != NTC_FILTER_NEAREST && filter != NTC_FILTER_TRILINEAR) return fail(NTC_ERR_ARG, "filter");
+  CHECK_PTR(workspace, "workspace");
+  if (workspace_bytes < sizeof(ntc::BatchHeader))
+    return fail(NTC_ERR_ARG, "batch: workspace of %zu bytes, need %zu", workspace_bytes,
+                sizeof(ntc::BatchHeader));
+  std::vector<ntc::BatchHeader> host(1);
+  ntc::BatchHeader& B = host[0];
+  memset(&B, 0, sizeof(B));
+  const int per_tile = filter == NTC_FILTER_TRILINEAR ? 16 : 128;
+  uint32_t wg_smem = 0;
+  int fast = -1;
+  for (int i = 0; i < n_materials; ++i) {
+    const ntc_material* m = &mats[i];
+    int st = check_material(m, false);
+    if (st) {
+      char why[sizeof(g_err)];
+      memcpy(why, g_err, sizeof(why));
+      return fail(st, "batch material %d: %s", i, why);
+    }
+    if (m->precision != NTC_PREC_F16)
+      return fail(NTC_ERR_UNSUPPORTED, "batch material %d: batches decode FP16 materials", i);
+    if (n_queries[i] < 0) return fail(NTC_ERR_ARG, "batch material %d: negative query count", i);
+    const bool packed = m->encoding == NTC_GRID_PACKED;
+    const int f = ntc::batched_fast(m->c0, m->c1, m->bits0, m->bits1, packed) ? 1 : 0;
+    if (fast >= 0 && f != fast)
+      return fail(NTC_ERR_UNSUPPORTED, "batch: materials mix 4-bit packed and other grid layouts");
+    fast = f;
+    const uint32_t need = ntc::batched_wg_smem(m->c0, m->c1, m->bits0, m->bits1, packed);
+    wg_smem = need > wg_smem ? need : wg_smem;
+    B.mats[i] = *m;
+    B.tile_start[i + 1] = B.tile_start[i] + (n_queries[i] + per_tile - 1) / per_tile;
+    B.q_off[i + 1] = B.q_off[i] + n_queries[i];
+    B.o_off[i + 1] = B.o_off[i] + n_queries[i] * m->channels;
+  }
+  if ((size_t)wg_smem * 4 > 227 * 1024) return fail(NTC_ERR_UNSUPPORTED, "batch: shared memory");
+  B.n_materials = n_materials;
+  B.total_tiles = B.tile_start[n_materials];
+  cudaError_t e = cudaMemcpyAsync(workspace, &B, sizeof(B), cudaMemcpyHostToDevice,
+                                  static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_status(e, "batch: descriptor upload");
+  batch_out->workspace = workspace;
+  batch_out->n_materials = n_materials;
+  batch_out->filter = filter;
+  batch_out->total_queries = B.q_off[n_materials];
+  batch_out->total_outputs = B.o_off[n_materials];
+  batch_out->total_tiles = B.total_tiles;
+  batch_out->wg_smem = (int32_t)wg_smem;
+  batch_out->fast = fast;
+  return NTC_OK;
+}
+
+int ntc_decode_batched(const ntc_batch* batch, const float* uvl, void* out, int32_t out_dtype,
+                       void* stream) {
+  if (!batch || !batch->workspace) return fail(NTC_ERR_ARG, "batch is not prepared");
+  if (out_dtype != NTC_DTYPE_F32 && out_dtype != NTC_DTYPE_F16) return fail(NTC_ERR_ARG, "out_dtype");
+  if (batch->total_queries == 0) return NTC_OK;
+  CHECK_PTR(uvl, "uvl");
+  CHECK_PTR(out, "out");
+  return cuda_status(ntc::launch_decode_batched(static_cast<const ntc::BatchHeader*>(batch->workspace),
+                                                batch->total_tiles, (uint32_t)batch->wg_smem,
+                                                batch->fast != 0, uvl, out, out_dtype, batch->filter,
+                                                static_cast<cudaStream_t>(stream)),
+                     "decode_batched");
 }
 
 int ntc_quantize_pack(const float* values, int64_t cells, int32_t c, int32_t bits, float q,

@@ -64,7 +64,7 @@ struct AdamArgs {
   int freeze_grids;
 };
 constexpr int kAdamBlock = 256;
-constexpr int kAdamPerThread = 4;
+constexpr int kAdamPerThread = 4;  // one float4 per thread
 cudaError_t launch_adam(const AdamArgs& a, int64_t blocks, cudaStream_t s);
 cudaError_t launch_advance_step(int64_t* step, cudaStream_t s);
 
@@ -76,6 +76,23 @@ cudaError_t launch_sample_batch(uint64_t seed, int64_t step, int64_t batch, int 
                                 int32_t* xym, cudaStream_t s);
 cudaError_t launch_sample_features(const ntc_material& m, const float* uvl, int64_t n, float* rows,
                                    int noise, uint64_t seed, int64_t step, cudaStream_t s);
+
+// Device-side descriptor of a batch of materials (ntc_batch_prepare).
+constexpr int kMaxBatch = 1024;
+struct BatchHeader {
+  int32_t n_materials;
+  int32_t pad;
+  int64_t total_tiles;
+  int64_t tile_start[kMaxBatch + 1];  // prefix sums of tiles, ordered by material
+  int64_t q_off[kMaxBatch + 1];       // query row offsets
+  int64_t o_off[kMaxBatch + 1];       // output element offsets
+  ntc_material mats[kMaxBatch];
+};
+uint32_t batched_wg_smem(int c0, int c1, int bits0, int bits1, bool packed);
+bool batched_fast(int c0, int c1, int bits0, int bits1, bool packed);
+cudaError_t launch_decode_batched(const BatchHeader* dev, int64_t total_tiles, uint32_t wg_smem,
+                                  bool fast, const float* uvl, void* out, int out_dtype, int filter,
+                                  cudaStream_t s);
 
 int sm_count();
 
