@@ -386,7 +386,7 @@ int ntc_batch_prepare(const ntc_material* mats, const int64_t* n_queries, int32_
   memset(&B, 0, sizeof(B));
   const int per_tile = filter == NTC_FILTER_TRILINEAR ? 16 : 128;
   uint32_t wg_smem = 0;
-  int fast = -1;
+  int fast = 1;  // the fast input layout when every material allows it, else the generic one
   for (int i = 0; i < n_materials; ++i) {
     const ntc_material* m = &mats[i];
     int st = check_material(m, false);
@@ -398,17 +398,15 @@ int ntc_batch_prepare(const ntc_material* mats, const int64_t* n_queries, int32_
     if (m->precision != NTC_PREC_F16)
       return fail(NTC_ERR_UNSUPPORTED, "batch material %d: batches decode FP16 materials", i);
     if (n_queries[i] < 0) return fail(NTC_ERR_ARG, "batch material %d: negative query count", i);
-    const bool packed = m->encoding == NTC_GRID_PACKED;
-    const int f = ntc::batched_fast(m->c0, m->c1, m->bits0, m->bits1, packed) ? 1 : 0;
-    if (fast >= 0 && f != fast)
-      return fail(NTC_ERR_UNSUPPORTED, "batch: materials mix 4-bit packed and other grid layouts");
-    fast = f;
-    const uint32_t need = ntc::batched_wg_smem(m->c0, m->c1, m->bits0, m->bits1, packed);
-    wg_smem = need > wg_smem ? need : wg_smem;
+    if (!ntc::batched_fast(*m)) fast = 0;
     B.mats[i] = *m;
     B.tile_start[i + 1] = B.tile_start[i] + (n_queries[i] + per_tile - 1) / per_tile;
     B.q_off[i + 1] = B.q_off[i] + n_queries[i];
     B.o_off[i + 1] = B.o_off[i] + n_queries[i] * m->channels;
+  }
+  for (int i = 0; i < n_materials; ++i) {
+    const uint32_t need = ntc::batched_wg_smem(mats[i], fast != 0);
+    wg_smem = need > wg_smem ? need : wg_smem;
   }
   if ((size_t)wg_smem * 4 > 227 * 1024) return fail(NTC_ERR_UNSUPPORTED, "batch: shared memory");
   B.n_materials = n_materials;

@@ -88,8 +88,9 @@ struct BatchHeader {
   int64_t o_off[kMaxBatch + 1];       // output element offsets
   ntc_material mats[kMaxBatch];
 };
-uint32_t batched_wg_smem(int c0, int c1, int bits0, int bits1, bool packed);
-bool batched_fast(int c0, int c1, int bits0, int bits1, bool packed);
+uint32_t batched_wg_smem(const ntc_material& m, bool fast);
+bool batched_fast(const ntc_material& m);
+bool fast_layout_ok(const ntc_material& m);
 cudaError_t launch_decode_batched(const BatchHeader* dev, int64_t total_tiles, uint32_t wg_smem,
                                   bool fast, const float* uvl, void* out, int out_dtype, int filter,
                                   cudaStream_t s);

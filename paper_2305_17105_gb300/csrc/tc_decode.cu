@@ -19,17 +19,23 @@
 //      output activation and stores the texel to global memory.
 //
 // Input-slot order (W1's columns permuted to match when staged), 8 slots per
-// group: fast layout (4-bit packed grids, FP16): full groups of 8 channels
-// from one 32-bit cell word each, slots holding channels 0,4,1,5,2,6,3,7 (one
-// LOP3 per channel pair turns nibbles i and i+4 into the half2
-// (1024 + q_i, 1024 + q_{i+4})); the <= 4-channel tails of G0 and G1 share a
-// merged group of (G0, G1) lane pairs.  Generic layout: channels in order.
+// group.  Fast layout (4-bit packed grids, FP16, tap fractions on a 1/16
+// lattice): a cell word of 5-8 channels is split into its even and odd
+// nibbles (4 byte lanes each), both rows of taps are interpolated along x in
+// integer byte-lane arithmetic (16 q_0 + f (q_1 - q_0) <= 240, exact), and
+// each pair of lanes is put into the mantissa of the half 1024 + lane and
+// interpolated along y with two half FMAs: slots hold channels
+// 0,4,2,6,1,5,3,7.  Words of 1-4 channels (the tail of a 9-12 channel cell)
+// hold channels 0,1,2,3 in half a group; the tails of G0 and G1 share one
+// group.  Generic layout: channels in order.
 // Then [PE0..7][PE8..11, LOD, 0, 1, 1].  For FP16 the biases ride on the
 // tensor core: layer 1 through the two constant-one slots (bias split into
 // an FP16 head and tail), layers 2 and 3 through one extra K=16 step against
 // a constant-one A block kept in TMEM.  FP8: each epilogue applies
 // (s_w * s_a) * acc + b in FP32.
 #include <cuda_fp16.h>
+
+#include <cmath>
 
 #include "ntc_device.cuh"
 #include "ntc_internal.h"
@@ -48,7 +54,7 @@ constexpr int kN3 = 16;
 constexpr int kColH = 64;              // FP16: 32 columns (64 halves); FP8: 16
 constexpr int kColX = 96;              // FP16: up to 24 columns (48 halves); FP8: 16
 constexpr int kColCst = 120;           // FP16: 8 columns
-constexpr uint32_t kWaitLimit = 1u << 22;
+constexpr uint32_t kWaitLimit = 1u << 18;  // suspended tries: ms to seconds
 
 template <bool F8>
 struct Cfg {
@@ -59,6 +65,11 @@ struct Cfg {
 // Per-mip constants (structure of arrays: lanes that look up different mips
 // read different banks).
 struct MipTab {
+  // fast layout: per grid {8 G_x / w_m, 8 G_y / h_m, G_x, G_y}: the texel
+  // centre 2x+1 times the first entry, minus 8, is the tap position in 1/16
+  // cell units
+  int4 tk0[NTC_MAX_MIPS], tk1[NTC_MAX_MIPS];
+  uint32_t lodh[NTC_MAX_MIPS];  // half2 (LOD input, 0)
   const uint8_t* grid0[NTC_MAX_MIPS];
   const uint8_t* grid1[NTC_MAX_MIPS];
   int wm[NTC_MAX_MIPS], hm[NTC_MAX_MIPS];
@@ -69,9 +80,12 @@ struct MipTab {
 
 // Input-row layout and shared memory plan (byte offsets).
 struct Plan {
-  int fast, merged, f0, f1, t0, t1, gpe, k_int, cb0, cb1;
-  uint32_t w1, w2, w3, wb2, wb3, bias, tab, pe, total;
-  __host__ __device__ Plan(int c0, int c1, int bits0, int bits1, bool packed, bool f8) {
+  int fast, eo0, eo1, t0, t1, f0, f1, gpe, k_int, cb0, cb1;
+  uint32_t w1, w2, w3, wb2, wb3, bias, tab, pe, desc, total;
+  // `taps_ok`: every grid/mip size ratio puts the taps on the 1/16 lattice and
+  // the bin widths are powers of two (fast_layout_ok).
+  __host__ __device__ Plan(int c0, int c1, int bits0, int bits1, bool packed, bool f8,
+                           bool taps_ok) {
     const int eb = f8 ? 1 : 2, kstep = f8 ? 32 : 16;
     cb0 = cb1 = 0;
     if (packed) {
@@ -79,20 +93,20 @@ struct Plan {
       cb1 = cell_bytes(c1, bits1);
     }
     // the fast layout reads whole 32-bit cell words: 4-bit cells of 4 or 8 bytes
-    fast = !f8 && packed && bits0 == 4 && bits1 == 4 && (cb0 == 4 || cb0 == 8) &&
+    fast = taps_ok && !f8 && packed && bits0 == 4 && bits1 == 4 && (cb0 == 4 || cb0 == 8) &&
            (cb1 == 4 || cb1 == 8);
+    eo0 = eo1 = t0 = t1 = 0;
     if (fast) {
-      f0 = c0 / 8;
-      f1 = c1 / 8;
-      const int r0 = c0 % 8, r1 = c1 % 8;
-      merged = r0 && r1 && r0 <= 4 && r1 <= 4;
-      t0 = (!merged && r0) ? 1 : 0;
-      t1 = (!merged && r1) ? 1 : 0;
-      gpe = f0 + f1 + (merged ? 1 : t0 + t1);
+      // word 0 holds 5-8 channels; word 1 (8-byte cells) the other c - 8
+      eo0 = (cb0 == 8 && c0 > 12) ? 2 : 1;
+      eo1 = (cb1 == 8 && c1 > 12) ? 2 : 1;
+      t0 = (cb0 == 8 && c0 <= 12) ? 1 : 0;
+      t1 = (cb1 == 8 && c1 <= 12) ? 1 : 0;
+      f0 = f1 = 0;
+      gpe = eo0 + eo1 + ((t0 | t1) ? 1 : 0);
     } else {
       f0 = (c0 + 7) / 8;
       f1 = (c1 + 7) / 8;
-      merged = t0 = t1 = 0;
       gpe = f0 + f1;
     }
     k_int = (8 * (gpe + 2) + kstep - 1) / kstep * kstep;
@@ -105,7 +119,8 @@ struct Plan {
     bias = o; o += (2 * kHidden + kN3) * 4;       // FP32 biases (FP8 epilogues)
     o = (o + 15) / 16 * 16;
     tab = o;  o += sizeof(MipTab);
-    pe = o;   o += 3 * 8 * 4;                     // half2 (sin, cos) per octave and x & 7
+    pe = o;   o += 8 * 16;                        // per x & 7: half2 (sin, cos) of 3 octaves, 0
+    desc = o; o += 16 * 8;                        // B descriptors: W1 0-3, W2 4-7, b2 8, W3 9-12, b3 13
     total = o;
   }
 };
@@ -126,28 +141,25 @@ __device__ __forceinline__ __half2 u2h(uint32_t u) {
 __device__ __forceinline__ int w1_column(const ntc_material& M, const Plan& P, int s, bool f8) {
   int g = s >> 3;
   const int e = s & 7;
-  const int pair = (e & 1) * 4 + (e >> 1);  // fast-layout channel of slot e within a word
+  const int j = e >> 1, l = e & 1;  // half2 j of the group, lane l
   if (P.fast) {
-    if (g < P.f0) return 8 * g + pair;
-    g -= P.f0;
-    if (g < P.f1) return M.c0 + 8 * g + pair;
-    g -= P.f1;
-    if (P.merged) {
+    // 5-8 channel word: half2 (lo E, hi E, lo O, hi O) = channels (0,4) (2,6) (1,5) (3,7)
+    const int eo = 2 * (j & 1) + (j >> 1) + 4 * l;
+    if (g < P.eo0) return 8 * g + eo < M.c0 ? 8 * g + eo : -1;
+    g -= P.eo0;
+    if (g < P.eo1) return 8 * g + eo < M.c1 ? M.c0 + 8 * g + eo : -1;
+    g -= P.eo1;
+    if (P.t0 | P.t1) {
       if (g == 0) {
-        const int i = e >> 1;
-        if (e & 1) return 8 * P.f1 + i < M.c1 ? M.c0 + 8 * P.f1 + i : -1;
-        return 8 * P.f0 + i < M.c0 ? 8 * P.f0 + i : -1;
+        // tail words: half2 (lo T, hi T) = channels (8,9) (10,11) of G0, then of G1
+        const bool both = P.t0 && P.t1;
+        if (!both && j >= 2) return -1;
+        const int k = both ? (j >> 1) : (P.t0 ? 0 : 1);
+        const int ch = 8 + 2 * (j & 1) + l;
+        if (k == 0) return ch < M.c0 ? ch : -1;
+        return ch < M.c1 ? M.c0 + ch : -1;
       }
       g -= 1;
-    } else {
-      if (P.t0) {
-        if (g == 0) return 8 * P.f0 + pair < M.c0 ? 8 * P.f0 + pair : -1;
-        g -= 1;
-      }
-      if (P.t1) {
-        if (g == 0) return 8 * P.f1 + pair < M.c1 ? M.c0 + 8 * P.f1 + pair : -1;
-        g -= 1;
-      }
     }
   } else {
     if (g < P.f0) return 8 * g + e < M.c0 ? 8 * g + e : -1;
@@ -199,20 +211,23 @@ __device__ void stage_shared(const ntc_material& M, const Plan& P, uint8_t* sm, 
     if (F8) sm[off] = static_cast<const uint8_t*>(M.w[1])[i];
     else *reinterpret_cast<__half*>(sm + off) = static_cast<const __half*>(M.w[1])[i];
   }
+  // sigmoid(z) = (1 + tanh(z / 2)) / 2: layer 3 is staged pre-halved (exact
+  // but for FP16 subnormals) so the output epilogue is one tanh and one FMA
+  const float h3 = M.out_act == NTC_OUT_IDENTITY ? 1.f : 0.5f;
   for (int i = tid; i < kN3 * kHidden; i += nt) {
     const int n = i / kHidden, k = i - n * kHidden;
     const uint32_t off = P.w3 + tc::canon_offset(n, k, kN3, EB);
     const bool live = n < M.channels;
     if (F8) sm[off] = live ? static_cast<const uint8_t*>(M.w[2])[i] : 0;
-    else *reinterpret_cast<__half*>(sm + off) =
-        live ? static_cast<const __half*>(M.w[2])[i] : __float2half_rn(0.f);
+    else *reinterpret_cast<__half*>(sm + off) = __float2half_rn(
+        live ? h3 * __half2float(static_cast<const __half*>(M.w[2])[i]) : 0.f);
   }
   float* bias = reinterpret_cast<float*>(sm + P.bias);
   for (int i = tid; i < kHidden; i += nt) {
     bias[i] = M.b[0][i];
     bias[kHidden + i] = M.b[1][i];
   }
-  for (int i = tid; i < kN3; i += nt) bias[2 * kHidden + i] = i < M.channels ? M.b[2][i] : 0.f;
+  for (int i = tid; i < kN3; i += nt) bias[2 * kHidden + i] = i < M.channels ? h3 * M.b[2][i] : 0.f;
   if (!F8) {
     for (int i = tid; i < kHidden * 16; i += nt) {
       const int n = i / 16, k = i - n * 16;
@@ -224,7 +239,7 @@ __device__ void stage_shared(const ntc_material& M, const Plan& P, uint8_t* sm, 
     for (int i = tid; i < kN3 * 16; i += nt) {
       const int n = i / 16, k = i - n * 16;
       __half hd = __float2half_rn(0.f), tl = __float2half_rn(0.f);
-      if (n < M.channels) split_bias(M.b[2][n], hd, tl);
+      if (n < M.channels) split_bias(h3 * M.b[2][n], hd, tl);
       *reinterpret_cast<__half*>(sm + P.wb3 + tc::canon_offset(n, k, kN3, 2)) =
           k == 0 ? hd : (k == 1 ? tl : __float2half_rn(0.f));
     }
@@ -243,6 +258,9 @@ __device__ void stage_shared(const ntc_material& M, const Plan& P, uint8_t* sm, 
     tb->sx1[m] = (float)L.g1_w / (float)wm;
     tb->sy1[m] = (float)L.g1_h / (float)hm;
     tb->lodn[m] = M.mips > 1 ? (float)m / (float)(M.mips - 1) : 0.f;
+    tb->lodh[m] = tc::pack_f16x2(tb->lodn[m], 0.f);
+    tb->tk0[m] = make_int4(8 * L.g0_w / wm, 8 * L.g0_h / hm, L.g0_w, L.g0_h);
+    tb->tk1[m] = make_int4(8 * L.g1_w / wm, 8 * L.g1_h / hm, L.g1_w, L.g1_h);
   }
   // positional encoding: per octave h and coordinate c & 7 the (sin, cos)
   // pair, exact in FP16
@@ -253,8 +271,24 @@ __device__ void stage_shared(const ntc_material& M, const Plan& P, uint8_t* sm, 
   for (int c = tid; c < 8; c += nt) {
     Pe pe;
     positional_encoding(c, 0, 0, pe);
-    for (int h = 0; h < 3; ++h)
-      reinterpret_cast<uint32_t*>(sm + P.pe)[h * 8 + c] = tc::pack_f16x2(pe.v[2 * h], pe.v[2 * h + 1]);
+    reinterpret_cast<uint4*>(sm + P.pe)[c] =
+        make_uint4(tc::pack_f16x2(pe.v[0], pe.v[1]), tc::pack_f16x2(pe.v[2], pe.v[3]),
+                   tc::pack_f16x2(pe.v[4], pe.v[5]), 0u);
+  }
+  // shared-memory descriptors of every B operand K-step (K-major, no swizzle:
+  // LBO = K-direction core-matrix stride, SBO = 128 between 8-row groups)
+  if (tid == 0) {
+    constexpr int KS = Cfg<F8>::KSTEP;
+    constexpr uint32_t lbo = (kHidden / 8) * 128, lbo3 = (kN3 / 8) * 128;
+    uint64_t* d = reinterpret_cast<uint64_t*>(sm + P.desc);
+    const uint32_t sb = tc::smem_u32(sm);
+    for (int k = 0; k < P.k_int / KS; ++k) d[k] = tc::smem_desc(sb + P.w1 + 2 * k * lbo, lbo, 128);
+    for (int k = 0; k < kHidden / KS; ++k) {
+      d[4 + k] = tc::smem_desc(sb + P.w2 + 2 * k * lbo, lbo, 128);
+      d[9 + k] = tc::smem_desc(sb + P.w3 + 2 * k * lbo3, lbo3, 128);
+    }
+    d[8] = tc::smem_desc(sb + P.wb2, lbo, 128);
+    d[13] = tc::smem_desc(sb + P.wb3, lbo3, 128);
   }
 }
 
@@ -297,7 +331,7 @@ __device__ __forceinline__ void taps_of(int x, int y, float sx, float sy, int gw
 // Filled one tile ahead so the gathers overlap the previous tile's MMAs.
 struct Row {
   uint2 c0[4], c1[4];  // cells of the 4 taps of G0 / G1 (at most 8 bytes each)
-  float w0[4], w1[4];  // bilinear tap weights
+  int frac;            // tap fractions in 1/16: fx0 | fy0 << 4 | fx1 << 8 | fy1 << 12
   float wtap;          // trilinear blend weight of this row
   int x, y, m;
   int valid;
@@ -353,113 +387,168 @@ __device__ __forceinline__ void locate(const ntc_material& M, const MipTab* tb, 
   }
 }
 
+// Fast-layout taps of one grid: with the grid/mip ratio r = G / w_m a
+// multiple of 1/8, the tap position p = (x + 1/2) r - 1/2 is exactly
+// ((2x+1) 8r - 8) / 16, so its integer part and its fraction (in 1/16) come
+// from a shift and a mask.  p lies in [-1/2, G - 1/2): only the lower tap can
+// fall below 0 and only the upper one beyond G - 1.
+__device__ __forceinline__ void taps16(int x2, int y2, int4 k, int (&cell)[4], int& frac) {
+  const int px = x2 * k.x - 8, py = y2 * k.y - 8;
+  const int ix = px >> 4, iy = py >> 4;
+  frac = (px & 15) | ((py & 15) << 4);
+  const int ix0 = max(ix, 0), ix1 = min(ix + 1, k.z - 1);
+  const int r0 = max(iy, 0) * k.z, r1 = min(iy + 1, k.w - 1) * k.z;
+  cell[0] = r0 + ix0;
+  cell[1] = r0 + ix1;
+  cell[2] = r1 + ix0;
+  cell[3] = r1 + ix1;
+}
+
 // Issue the eight cell loads of a fast-layout row (invalid rows load nothing).
 __device__ __forceinline__ void gather_fast(const MipTab* tb, const Plan& P, Row& r) {
 #pragma unroll
-  for (int t = 0; t < 4; ++t) {
-    r.c0[t] = r.c1[t] = make_uint2(0, 0);
-    r.w0[t] = r.w1[t] = 0.f;
-  }
+  for (int t = 0; t < 4; ++t) r.c0[t] = r.c1[t] = make_uint2(0, 0);
+  r.frac = 0;
   if (!r.valid) return;
   const int m = r.m;
-  Taps t0, t1;
-  taps_of(r.x, r.y, tb->sx0[m], tb->sy0[m], tb->g0w[m], tb->g0h[m], t0);
-  taps_of(r.x, r.y, tb->sx1[m], tb->sy1[m], tb->g1w[m], tb->g1h[m], t1);
+  const int x2 = 2 * r.x + 1, y2 = 2 * r.y + 1;
+  int cell0[4], cell1[4], f0, f1;
+  taps16(x2, y2, tb->tk0[m], cell0, f0);
+  taps16(x2, y2, tb->tk1[m], cell1, f1);
+  r.frac = f0 | (f1 << 8);
   const uint8_t* g0 = tb->grid0[m];
   const uint8_t* g1 = tb->grid1[m];
 #pragma unroll
   for (int t = 0; t < 4; ++t) {
-    r.w0[t] = t0.w[t];
-    r.w1[t] = t1.w[t];
-    if (P.cb0 == 8) r.c0[t] = __ldg(reinterpret_cast<const uint2*>(g0) + t0.cell[t]);
-    else r.c0[t].x = __ldg(reinterpret_cast<const uint32_t*>(g0) + t0.cell[t]);
-    if (P.cb1 == 8) r.c1[t] = __ldg(reinterpret_cast<const uint2*>(g1) + t1.cell[t]);
-    else r.c1[t].x = __ldg(reinterpret_cast<const uint32_t*>(g1) + t1.cell[t]);
+    if (P.cb0 == 8) r.c0[t] = __ldg(reinterpret_cast<const uint2*>(g0) + cell0[t]);
+    else r.c0[t].x = __ldg(reinterpret_cast<const uint32_t*>(g0) + cell0[t]);
+    if (P.cb1 == 8) r.c1[t] = __ldg(reinterpret_cast<const uint2*>(g1) + cell1[t]);
+    else r.c1[t].x = __ldg(reinterpret_cast<const uint32_t*>(g1) + cell1[t]);
   }
 }
 
 __device__ __forceinline__ uint32_t word_of(const uint2& c, int f) { return f ? c.y : c.x; }
 
-// Half2 dequantisation + bilinear interpolation of one group from the 32-bit
-// cell words w[t] of the four taps, per-lane tap weights wt[t], bin widths
-// q2 and offsets -(N/2-1) Q per lane.
-__device__ __forceinline__ uint4 half2_group(const uint32_t (&w)[4], const __half2 (&wt)[4],
-                                             __half2 q2, __half2 o2) {
-  const __half2 bias1024 = __float2half2_rn(1024.f);
-  __half2 acc[4];
+// y-interpolation constants of one grid: with wy0 = 16 - fy, wy1 = fy and
+// s = Q / 256, c0 = wy0 s, c1 = wy1 s and o = -7 Q - 1024 c0 (all exact in
+// FP16 for power-of-two Q in [2^-6, 2^6]).
+struct YLerp {
+  __half2 c0, c1, o;
+};
+__device__ __forceinline__ YLerp ylerp_of(int fy, __half2 s, __half2 s16, __half2 m7q) {
+  YLerp y;
+  const __half2 k = u2h((uint32_t)(16 - fy) * 0x10001u + 0x64006400u);  // 1024 + wy0
+  y.c0 = __hfma2(k, s, __hmul2(s, __float2half2_rn(-1024.f)));
+  y.c1 = __hsub2(s16, y.c0);
+  y.o = __hfma2(y.c0, __float2half2_rn(-1024.f), m7q);
+  return y;
+}
+
+// Lanes (0, 2) / (1, 3) of the x-interpolated rows A0, A1 (16 x the
+// x-lerp of q, <= 240) -> dequantised bilinear value (lerp/16 - 7) Q.  The
+// byte goes into the mantissa of 1024 + lane; the first FMA cancels the 1024
+// exactly, so each output is rounded twice.
+__device__ __forceinline__ uint32_t ylerp(uint32_t A0, uint32_t A1, uint32_t sel, const YLerp& y) {
+  const uint32_t k = 0x64646464u;
+  const __half2 a0 = u2h(__byte_perm(A0, k, sel));
+  const __half2 a1 = __hsub2(u2h(__byte_perm(A1, k, sel)), __float2half2_rn(1024.f));
+  return h2u(__hfma2(a1, y.c1, __hfma2(a0, y.c0, y.o)));
+}
+
+// A 5-8 channel word of the four taps -> one group (channels 0,4,2,6,1,5,3,7).
+__device__ __forceinline__ uint4 eo_group(const uint32_t (&w)[4], uint32_t wx0, uint32_t wx1,
+                                          const YLerp& y) {
+  uint32_t e[4], o[4];
 #pragma unroll
-  for (int i = 0; i < 4; ++i) acc[i] = __float2half2_rn(0.f);
-#pragma unroll
-  for (int tp = 0; tp < 4; ++tp) {
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const uint32_t h = tc::lop3_and_or(w[tp] >> (4 * i), 0x000F000Fu, 0x64006400u);
-      acc[i] = __hfma2(wt[tp], __hsub2(u2h(h), bias1024), acc[i]);
-    }
+  for (int t = 0; t < 4; ++t) {
+    e[t] = w[t] & 0x0F0F0F0Fu;
+    o[t] = (w[t] >> 4) & 0x0F0F0F0Fu;
   }
-  return make_uint4(h2u(__hfma2(acc[0], q2, o2)), h2u(__hfma2(acc[1], q2, o2)),
-                    h2u(__hfma2(acc[2], q2, o2)), h2u(__hfma2(acc[3], q2, o2)));
+  const uint32_t e0 = e[0] * wx0 + e[1] * wx1, e1 = e[2] * wx0 + e[3] * wx1;
+  const uint32_t o0 = o[0] * wx0 + o[1] * wx1, o1 = o[2] * wx0 + o[3] * wx1;
+  return make_uint4(ylerp(e0, e1, 0x4240u, y), ylerp(e0, e1, 0x4341u, y), ylerp(o0, o1, 0x4240u, y),
+                    ylerp(o0, o1, 0x4341u, y));
+}
+
+// A 1-4 channel word (low 16 bits) of the four taps -> half a group
+// (channels 0,1 and 2,3).
+__device__ __forceinline__ uint2 t_half(const uint32_t (&w)[4], uint32_t wx0, uint32_t wx1,
+                                        const YLerp& y) {
+  uint32_t t4[4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) t4[t] = __byte_perm(w[t], w[t] << 12, 0x7610u) & 0x0F0F0F0Fu;
+  const uint32_t a0 = t4[0] * wx0 + t4[1] * wx1, a1 = t4[2] * wx0 + t4[3] * wx1;
+  return make_uint2(ylerp(a0, a1, 0x4240u, y), ylerp(a0, a1, 0x4341u, y));
 }
 
 // The two PE groups (FP16): (sin, cos) pairs of the 3 octaves of x, then of
 // y, then (LOD, 0) and the constant-one bias slots.
-__device__ __forceinline__ void pe_groups(const Plan& P, const uint8_t* sm, float lodn, int x,
+__device__ __forceinline__ void pe_groups(const Plan& P, const uint8_t* sm, uint32_t lodh, int x,
                                           int y, uint32_t ta) {
-  const uint32_t* pe = reinterpret_cast<const uint32_t*>(sm + P.pe);
-  const int cx = x & 7, cy = y & 7;
-  tc::tmem_st4(ta + 4 * P.gpe, make_uint4(pe[cx], pe[8 + cx], pe[16 + cx], pe[cy]));
-  tc::tmem_st4(ta + 4 * (P.gpe + 1), make_uint4(pe[8 + cy], pe[16 + cy], tc::pack_f16x2(lodn, 0.f),
-                                                tc::pack_f16x2(1.f, 1.f)));
+  const uint4* pe = reinterpret_cast<const uint4*>(sm + P.pe);
+  const uint4 px = pe[x & 7], py = pe[y & 7];
+  tc::tmem_st4(ta + 4 * P.gpe, make_uint4(px.x, px.y, px.z, py.x));
+  tc::tmem_st4(ta + 4 * (P.gpe + 1), make_uint4(py.y, py.z, lodh, tc::pack_f16x2(1.f, 1.f)));
 }
 
-// Fast layout: every group of the row from the prefetched cells.
-__device__ __forceinline__ void build_fast(const ntc_material& M, const Plan& P, const uint8_t* sm,
-                                           const Row& r, uint32_t ta) {
-  __half2 w0[4], w1[4], wm[4];
+// Per-grid FP16 constants of the fast layout.
+struct FastK {
+  __half2 s[2], s16[2], m7q[2];
+  __device__ FastK(const ntc_material& M) {
+    const float q[2] = {M.q0, M.q1};
 #pragma unroll
-  for (int t = 0; t < 4; ++t) {
-    w0[t] = __float2half2_rn(r.w0[t]);
-    w1[t] = __float2half2_rn(r.w1[t]);
-    wm[t] = __floats2half2_rn(r.w0[t], r.w1[t]);
+    for (int k = 0; k < 2; ++k) {
+      s[k] = __float2half2_rn(q[k] * (1.f / 256.f));
+      s16[k] = __float2half2_rn(q[k] * (16.f / 256.f));
+      m7q[k] = __float2half2_rn(-7.f * q[k]);
+    }
   }
-  const __half2 q0 = __float2half2_rn(M.q0), q1 = __float2half2_rn(M.q1);
-  const __half2 o0 = __float2half2_rn(-7.f * M.q0), o1 = __float2half2_rn(-7.f * M.q1);
+};
+
+// Fast layout: every group of the row from the prefetched cells.
+__device__ __forceinline__ void build_fast(const Plan& P, const FastK& K, const uint8_t* sm,
+                                           const Row& r, uint32_t ta) {
+  const uint32_t fx0 = r.frac & 15, fx1 = (r.frac >> 8) & 15;
+  const YLerp y0 = ylerp_of((r.frac >> 4) & 15, K.s[0], K.s16[0], K.m7q[0]);
+  const YLerp y1 = ylerp_of((r.frac >> 12) & 15, K.s[1], K.s16[1], K.m7q[1]);
   int kg = 0;
 #pragma unroll
   for (int f = 0; f < 2; ++f)
-    if (f < P.f0) {
+    if (f < P.eo0) {
       const uint32_t w[4] = {word_of(r.c0[0], f), word_of(r.c0[1], f), word_of(r.c0[2], f),
                              word_of(r.c0[3], f)};
-      tc::tmem_st4(ta + 4 * kg++, half2_group(w, w0, q0, o0));
+      tc::tmem_st4(ta + 4 * kg++, eo_group(w, 16 - fx0, fx0, y0));
     }
 #pragma unroll
   for (int f = 0; f < 2; ++f)
-    if (f < P.f1) {
+    if (f < P.eo1) {
       const uint32_t w[4] = {word_of(r.c1[0], f), word_of(r.c1[1], f), word_of(r.c1[2], f),
                              word_of(r.c1[3], f)};
-      tc::tmem_st4(ta + 4 * kg++, half2_group(w, w1, q1, o1));
+      tc::tmem_st4(ta + 4 * kg++, eo_group(w, 16 - fx1, fx1, y1));
     }
-  if (P.merged) {
-    uint32_t w[4];
-#pragma unroll
-    for (int t = 0; t < 4; ++t)
-      w[t] = (word_of(r.c0[t], P.f0) & 0xFFFFu) | (word_of(r.c1[t], P.f1) << 16);
-    tc::tmem_st4(ta + 4 * kg++, half2_group(w, wm, __lows2half2(q0, q1), __lows2half2(o0, o1)));
-  } else {
+  if (P.t0 | P.t1) {
+    uint2 a = make_uint2(0, 0), b = make_uint2(0, 0);
     if (P.t0) {
-      const uint32_t w[4] = {word_of(r.c0[0], P.f0), word_of(r.c0[1], P.f0),
-                             word_of(r.c0[2], P.f0), word_of(r.c0[3], P.f0)};
-      tc::tmem_st4(ta + 4 * kg++, half2_group(w, w0, q0, o0));
+      const uint32_t w[4] = {r.c0[0].y, r.c0[1].y, r.c0[2].y, r.c0[3].y};
+      a = t_half(w, 16 - fx0, fx0, y0);
     }
     if (P.t1) {
-      const uint32_t w[4] = {word_of(r.c1[0], P.f1), word_of(r.c1[1], P.f1),
-                             word_of(r.c1[2], P.f1), word_of(r.c1[3], P.f1)};
-      tc::tmem_st4(ta + 4 * kg++, half2_group(w, w1, q1, o1));
+      const uint32_t w[4] = {r.c1[0].y, r.c1[1].y, r.c1[2].y, r.c1[3].y};
+      b = t_half(w, 16 - fx1, fx1, y1);
     }
+    if (!P.t0) { a = b; b = make_uint2(0, 0); }
+    tc::tmem_st4(ta + 4 * kg++, make_uint4(a.x, a.y, b.x, b.y));
   }
   const MipTab* tb = reinterpret_cast<const MipTab*>(sm + P.tab);
-  pe_groups(P, sm, tb->lodn[r.m], r.x, r.y, ta);
-  for (int g = P.gpe + 2; g < P.k_int / 8; ++g) tc::tmem_st4(ta + 4 * g, make_uint4(0, 0, 0, 0));
+  pe_groups(P, sm, tb->lodh[r.m], r.x, r.y, ta);
+}
+
+// Zero groups between the PE groups and K (written once per material: the
+// per-tile builds never touch them).
+template <bool F8>
+__device__ __forceinline__ void zero_tail_groups(const Plan& P, uint32_t ta) {
+  const float z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int g = P.gpe + 2; g < P.k_int / 8; ++g) put_group<F8>(ta, g, z, 1.f);
 }
 
 // Generic layout (other bit widths, F32 grids, FP8 operands): float
@@ -522,7 +611,7 @@ __device__ __forceinline__ void build_generic(const ntc_material& M, const Plan&
   generic_grid<F8>(M, tb, 0, P, r, ta, 0, inv_sa);
   generic_grid<F8>(M, tb, 1, P, r, ta, P.f0, inv_sa);
   if (!F8) {
-    pe_groups(P, sm, tb->lodn[r.m], r.x, r.y, ta);
+    pe_groups(P, sm, tb->lodh[r.m], r.x, r.y, ta);
   } else {
     struct Pe {
       float v[16];
@@ -539,8 +628,6 @@ __device__ __forceinline__ void build_generic(const ntc_material& M, const Plan&
     v[5] = v[6] = v[7] = 0.f;
     put_group<F8>(ta, P.gpe + 1, v, inv_sa);
   }
-  const float z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  for (int g = P.gpe + 2; g < P.k_int / 8; ++g) put_group<F8>(ta, g, z, 1.f);
 }
 
 // Hidden-layer epilogue: D row (TMEM) -> activation -> A row (TMEM).
@@ -584,23 +671,20 @@ __device__ __forceinline__ void hidden_epilogue(uint32_t td, uint32_t ta, int ac
   }
 }
 
-// Issue one layer: D (+)= A[tmem] B[smem]^T over `ksteps` K-steps of W, then
-// (FP16) the bias step against the constant-one A block, then commit.
+// Issue one layer: D (+)= A[tmem] B[smem]^T over `ksteps` K-steps of W
+// (descriptors desc[0..ksteps)), then (FP16, `bias`) the bias step desc[ksteps]
+// against the constant-one A block, then commit.  Layers are issued by lane 0
+// of warps 0, 1, 2 of the warpgroup, spreading the issue work.
 template <bool F8>
-__device__ __forceinline__ void issue_layer(uint32_t tmem_d, uint32_t tmem_a, uint32_t b_addr,
-                                            uint32_t lbo, int ksteps, uint32_t id,
-                                            uint32_t bias_b_addr, uint32_t tmem_cst,
+__device__ __forceinline__ void issue_layer(uint32_t tmem_d, uint32_t tmem_a, const uint64_t* desc,
+                                            int ksteps, uint32_t id, bool bias, uint32_t tmem_cst,
                                             uint64_t* bar) {
   tc::fence_after_sync();
   for (int s = 0; s < ksteps; ++s) {
-    const uint64_t b = tc::smem_desc(b_addr + 2 * s * lbo, lbo, 128);
-    if (F8) tc::mma_f8_ta(tmem_d, tmem_a + 8 * s, b, id, s > 0);
-    else tc::mma_f16_ta(tmem_d, tmem_a + 8 * s, b, id, s > 0);
+    if (F8) tc::mma_f8_ta(tmem_d, tmem_a + 8 * s, desc[s], id, s > 0);
+    else tc::mma_f16_ta(tmem_d, tmem_a + 8 * s, desc[s], id, s > 0);
   }
-  if (!F8 && bias_b_addr) {
-    const uint64_t b = tc::smem_desc(bias_b_addr, lbo, 128);
-    tc::mma_f16_ta(tmem_d, tmem_cst, b, id, 1);
-  }
+  if (!F8 && bias) tc::mma_f16_ta(tmem_d, tmem_cst, desc[ksteps], id, 1);
   tc::mma_commit(bar);
 }
 
@@ -614,7 +698,7 @@ __global__ void __launch_bounds__(kRows* kNWG, 1) decode_tc_kernel(
   __shared__ int wg_abort[kNWG];
   constexpr int KSTEP = Cfg<F8>::KSTEP;
   constexpr uint32_t kCols = kNWG <= 2 ? 256 : 512;  // 128 columns per warpgroup
-  const Plan P(M.c0, M.c1, M.bits0, M.bits1, M.encoding == NTC_GRID_PACKED, F8);
+  const Plan P(M.c0, M.c1, M.bits0, M.bits1, M.encoding == NTC_GRID_PACKED, F8, FAST);
   uint8_t* sm = smem_raw;
   const int tid = threadIdx.x, warp = tid >> 5;
   const int wg = tid / kRows, row = tid % kRows;
@@ -645,6 +729,7 @@ __global__ void __launch_bounds__(kRows* kNWG, 1) decode_tc_kernel(
     tc::tmem_st4(tw + kColCst + lane, make_uint4(tc::pack_f16x2(1.f, 1.f), 0, 0, 0));
     tc::tmem_st4(tw + kColCst + 4 + lane, make_uint4(0, 0, 0, 0));
   }
+  zero_tail_groups<F8>(P, tx);
 
   float sc[3] = {1.f, 1.f, 1.f}, inv_sa[3] = {1.f, 1.f, 1.f};
   if (F8) {
@@ -653,11 +738,12 @@ __global__ void __launch_bounds__(kRows* kNWG, 1) decode_tc_kernel(
       sc[l] = M.scale[l] * M.scale[3 + l];
       inv_sa[l] = 1.f / M.scale[3 + l];
     }
+    if (M.out_act != NTC_OUT_IDENTITY) sc[2] *= 0.5f;  // layer 3 pre-halved (tanh form)
   }
+  const FastK K(M);
   const float* bias = reinterpret_cast<const float*>(sm + P.bias);
   const MipTab* tb = reinterpret_cast<const MipTab*>(sm + P.tab);
-  const uint32_t sbase = tc::smem_u32(sm);
-  constexpr uint32_t lbo_w = (kHidden / 8) * 128, lbo_w3 = (kN3 / 8) * 128;
+  const uint64_t* dsc = reinterpret_cast<const uint64_t*>(sm + P.desc);
   constexpr uint32_t id64 = tc::idesc(kRows, kHidden), id16 = tc::idesc(kRows, kN3);
 
   const bool tri = filter == NTC_FILTER_TRILINEAR;
@@ -680,7 +766,7 @@ __global__ void __launch_bounds__(kRows* kNWG, 1) decode_tc_kernel(
     locate(M, tb, load_query(uvl, q0, tl < ntiles && q0 < n), tri, row, r);
     if (FAST) {
       gather_fast(tb, P, r);
-      build_fast(M, P, sm, r, tx);
+      build_fast(P, K, sm, r, tx);
     } else {
       build_generic<F8>(M, P, sm, r, tx, inv_sa[0]);
     }
@@ -699,8 +785,7 @@ __global__ void __launch_bounds__(kRows* kNWG, 1) decode_tc_kernel(
     const float wtap = cur_wtap;
 
     // ---- layer 1 (X of this tile is in TMEM) ---------------------------------
-    if (row == 0)
-      issue_layer<F8>(tw, tw + kColX, sbase + P.w1, lbo_w, P.k_int / KSTEP, id64, 0, 0, bar);
+    if (row == 0) issue_layer<F8>(tw, tw + kColX, dsc, P.k_int / KSTEP, id64, false, 0, bar);
     // next tile: texel and cell gathers now, its query two tiles ahead
     Row nxt;
     locate(M, tb, nq, tri, row, nxt);
@@ -719,10 +804,8 @@ __global__ void __launch_bounds__(kRows* kNWG, 1) decode_tc_kernel(
     tc::bar_sync(bar_id, kRows);
 
     // ---- layer 2; meanwhile the next tile's X (layer 1 is done with X) -------
-    if (row == 0)
-      issue_layer<F8>(tw, tw + kColH, sbase + P.w2, lbo_w, kHidden / KSTEP, id64,
-                      F8 ? 0 : sbase + P.wb2, tw + kColCst, bar);
-    if (FAST) build_fast(M, P, sm, nxt, tx);
+    if (row == 32) issue_layer<F8>(tw, tw + kColH, dsc + 4, kHidden / KSTEP, id64, !F8, tw + kColCst, bar);
+    if (FAST) build_fast(P, K, sm, nxt, tx);
     else build_generic<F8>(M, P, sm, nxt, tx, inv_sa[0]);
     cur_valid = nxt.valid;
     cur_wtap = nxt.wtap;
@@ -736,9 +819,7 @@ __global__ void __launch_bounds__(kRows* kNWG, 1) decode_tc_kernel(
     if (*abort_flag) { aborted = true; break; }
 
     // ---- layer 3 + output ----------------------------------------------
-    if (row == 0)
-      issue_layer<F8>(tw, tw + kColH, sbase + P.w3, lbo_w3, kHidden / KSTEP, id16,
-                      F8 ? 0 : sbase + P.wb3, tw + kColCst, bar);
+    if (row == 64) issue_layer<F8>(tw, tw + kColH, dsc + 9, kHidden / KSTEP, id16, !F8, tw + kColCst, bar);
     if (!tc::mbar_wait(bar, phase, kWaitLimit)) *abort_flag = 1;
     phase ^= 1;
     tc::fence_after_sync();
@@ -750,7 +831,7 @@ __global__ void __launch_bounds__(kRows* kNWG, 1) decode_tc_kernel(
     for (int c = 0; c < 16; ++c) {
       float z = yv[c];
       if (F8) z = fmaf(z, sc[2], bias[2 * kHidden + c]);
-      yv[c] = M.out_act == NTC_OUT_IDENTITY ? z : tc::sigmoid_fast(z);
+      yv[c] = M.out_act == NTC_OUT_IDENTITY ? z : fmaf(0.5f, tc::tanh_fast(z), 0.5f);
     }
     if (tri) {
 #pragma unroll
@@ -820,7 +901,7 @@ __global__ void __launch_bounds__(kRows* kNWG, 1) decode_tc_kernel(
 template <bool F8, bool FAST, int kNWG>
 cudaError_t launch_k(const ntc_material& m, const float* uvl, int64_t n, void* out, int out_dtype,
                      int filter, cudaStream_t s) {
-  const Plan P(m.c0, m.c1, m.bits0, m.bits1, m.encoding == NTC_GRID_PACKED, F8);
+  const Plan P(m.c0, m.c1, m.bits0, m.bits1, m.encoding == NTC_GRID_PACKED, F8, FAST);
   const size_t smem = P.total;
   cudaError_t e = cudaFuncSetAttribute(decode_tc_kernel<F8, FAST, kNWG>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -886,8 +967,6 @@ __global__ void __launch_bounds__(kRows * 4, 1) decode_batched_kernel(
   tc::tmem_st4(tw + kColCst + lane, make_uint4(tc::pack_f16x2(1.f, 1.f), 0, 0, 0));
   tc::tmem_st4(tw + kColCst + 4 + lane, make_uint4(0, 0, 0, 0));
   uint8_t* sm = smem_raw + (size_t)wg * wg_smem;
-  const uint32_t sbase = tc::smem_u32(sm);
-  constexpr uint32_t lbo_w = (kHidden / 8) * 128, lbo_w3 = (kN3 / 8) * 128;
   constexpr uint32_t id64 = tc::idesc(kRows, kHidden), id16 = tc::idesc(kRows, kN3);
   const bool tri = filter == NTC_FILTER_TRILINEAR;
   const int per_tile = tri ? kRows / 8 : kRows;
@@ -910,15 +989,18 @@ __global__ void __launch_bounds__(kRows * 4, 1) decode_batched_kernel(
       if (row == 0) mat_s[wg] = B->mats[mid];
       tc::bar_sync(bar_id, kRows);
       const ntc_material& Mn = mat_s[wg];
-      const Plan Pn(Mn.c0, Mn.c1, Mn.bits0, Mn.bits1, Mn.encoding == NTC_GRID_PACKED, false);
+      const Plan Pn(Mn.c0, Mn.c1, Mn.bits0, Mn.bits1, Mn.encoding == NTC_GRID_PACKED, false, FAST);
       stage_shared<false>(Mn, Pn, sm, row, kRows);
+      zero_tail_groups<false>(Pn, tx);
+      tc::tmem_st_wait();
       tc::fence_proxy_async();
       tc::bar_sync(bar_id, kRows);
       cur = mid;
     }
     const ntc_material& M = mat_s[wg];
-    const Plan P(M.c0, M.c1, M.bits0, M.bits1, M.encoding == NTC_GRID_PACKED, false);
+    const Plan P(M.c0, M.c1, M.bits0, M.bits1, M.encoding == NTC_GRID_PACKED, false, FAST);
     const MipTab* tb = reinterpret_cast<const MipTab*>(sm + P.tab);
+    const uint64_t* dsc = reinterpret_cast<const uint64_t*>(sm + P.desc);
     const int64_t local = tl - B->tile_start[mid];
     const int64_t nq = B->q_off[mid + 1] - B->q_off[mid];
     const int64_t ql = tri ? local * per_tile + (row >> 3) : local * per_tile + row;
@@ -928,7 +1010,7 @@ __global__ void __launch_bounds__(kRows * 4, 1) decode_batched_kernel(
     locate(M, tb, load_query(uvl, qg, valid), tri, row, r);
     if (FAST) {
       gather_fast(tb, P, r);
-      build_fast(M, P, sm, r, tx);
+      build_fast(P, FastK(M), sm, r, tx);
     } else {
       build_generic<false>(M, P, sm, r, tx, 1.f);
     }
@@ -937,7 +1019,7 @@ __global__ void __launch_bounds__(kRows * 4, 1) decode_batched_kernel(
     tc::bar_sync(bar_id, kRows);
 
     if (row == 0)
-      issue_layer<false>(tw, tw + kColX, sbase + P.w1, lbo_w, P.k_int / 16, id64, 0, 0, bar);
+      issue_layer<false>(tw, tw + kColX, dsc, P.k_int / 16, id64, false, 0, bar);
     if (!tc::mbar_wait(bar, phase, kWaitLimit)) *abort_flag = 1;
     phase ^= 1;
     tc::fence_after_sync();
@@ -945,8 +1027,8 @@ __global__ void __launch_bounds__(kRows * 4, 1) decode_batched_kernel(
     tc::tmem_st_wait();
     tc::fence_before_sync();
     tc::bar_sync(bar_id, kRows);
-    if (row == 0)
-      issue_layer<false>(tw, tw + kColH, sbase + P.w2, lbo_w, 4, id64, sbase + P.wb2, tw + kColCst, bar);
+    if (row == 32)
+      issue_layer<false>(tw, tw + kColH, dsc + 4, 4, id64, true, tw + kColCst, bar);
     if (!tc::mbar_wait(bar, phase, kWaitLimit)) *abort_flag = 1;
     phase ^= 1;
     tc::fence_after_sync();
@@ -955,8 +1037,8 @@ __global__ void __launch_bounds__(kRows * 4, 1) decode_batched_kernel(
     tc::fence_before_sync();
     tc::bar_sync(bar_id, kRows);
     if (*abort_flag) { aborted = true; break; }
-    if (row == 0)
-      issue_layer<false>(tw, tw + kColH, sbase + P.w3, lbo_w3, 4, id16, sbase + P.wb3, tw + kColCst, bar);
+    if (row == 64)
+      issue_layer<false>(tw, tw + kColH, dsc + 9, 4, id16, true, tw + kColCst, bar);
     if (!tc::mbar_wait(bar, phase, kWaitLimit)) *abort_flag = 1;
     phase ^= 1;
     tc::fence_after_sync();
@@ -966,7 +1048,7 @@ __global__ void __launch_bounds__(kRows * 4, 1) decode_batched_kernel(
     tc::fence_before_sync();
 #pragma unroll
     for (int c = 0; c < 16; ++c)
-      yv[c] = M.out_act == NTC_OUT_IDENTITY ? yv[c] : tc::sigmoid_fast(yv[c]);
+      yv[c] = M.out_act == NTC_OUT_IDENTITY ? yv[c] : fmaf(0.5f, tc::tanh_fast(yv[c]), 0.5f);
     if (tri) {
 #pragma unroll
       for (int c = 0; c < 16; ++c) {
@@ -1011,6 +1093,23 @@ __global__ void __launch_bounds__(kRows * 4, 1) decode_batched_kernel(
 
 }  // namespace
 
+// The fast layout's exactness conditions: every grid/mip size ratio of every
+// mip is a multiple of 1/8 (taps on the 1/16 lattice) and the bin widths are
+// powers of two in [2^-6, 2^6] (the half constants of ylerp_of exact).
+bool fast_layout_ok(const ntc_material& m) {
+  for (int mi = 0; mi < m.mips; ++mi) {
+    const int wm = mip_dim(m.width, mi), hm = mip_dim(m.height, mi);
+    const ntc_level& L = m.lv[level_of_mip(mi, m.levels)];
+    if ((8 * L.g0_w) % wm || (8 * L.g0_h) % hm || (8 * L.g1_w) % wm || (8 * L.g1_h) % hm)
+      return false;
+  }
+  for (float q : {m.q0, m.q1}) {
+    int e = 0;
+    if (!(q > 0.f) || std::frexp(q, &e) != 0.5f || e < -5 || e > 7) return false;
+  }
+  return true;
+}
+
 // Launch shape: one CTA per SM with `nwg` warpgroup pipelines (2, 3 or 4;
 // 0 = 4), each holding 128 of the SM's 512 TMEM columns.
 cudaError_t launch_decode_tc(const ntc_material& m, const float* uvl, int64_t n, void* out,
@@ -1021,17 +1120,19 @@ cudaError_t launch_decode_tc(const ntc_material& m, const float* uvl, int64_t n,
   if (m.precision == NTC_PREC_F8)
     return launch_shape<true, false>(m, uvl, n, out, out_dtype, filter, s, nwg);
   if (m.precision != NTC_PREC_F16) return cudaErrorInvalidValue;
-  const Plan P(m.c0, m.c1, m.bits0, m.bits1, m.encoding == NTC_GRID_PACKED, false);
+  const Plan P(m.c0, m.c1, m.bits0, m.bits1, m.encoding == NTC_GRID_PACKED, false,
+               fast_layout_ok(m));
   if (P.fast) return launch_shape<false, true>(m, uvl, n, out, out_dtype, filter, s, nwg);
   return launch_shape<false, false>(m, uvl, n, out, out_dtype, filter, s, nwg);
 }
 
-uint32_t batched_wg_smem(int c0, int c1, int bits0, int bits1, bool packed) {
-  const Plan P(c0, c1, bits0, bits1, packed, false);
+uint32_t batched_wg_smem(const ntc_material& m, bool fast) {
+  const Plan P(m.c0, m.c1, m.bits0, m.bits1, m.encoding == NTC_GRID_PACKED, false, fast);
   return (P.total + 127) / 128 * 128;
 }
-bool batched_fast(int c0, int c1, int bits0, int bits1, bool packed) {
-  return Plan(c0, c1, bits0, bits1, packed, false).fast != 0;
+bool batched_fast(const ntc_material& m) {
+  return Plan(m.c0, m.c1, m.bits0, m.bits1, m.encoding == NTC_GRID_PACKED, false,
+              fast_layout_ok(m)).fast != 0;
 }
 
 cudaError_t launch_decode_batched(const BatchHeader* dev, int64_t total_tiles, uint32_t wg_smem,

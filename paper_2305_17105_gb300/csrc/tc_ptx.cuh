@@ -163,13 +163,25 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* mbar, uint32_t phase) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait for the phase with parity `phase` to complete; false when the
-// limit ran out (the caller reports NTC_ERR_TIMEOUT and leaves).
+// try_wait with a suspend-time hint: the thread sleeps (issuing nothing)
+// until the phase completes or `ns` nanoseconds pass.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* mbar, uint32_t phase, uint32_t ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(mbar)), "r"(phase), "r"(ns)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase with parity `phase` to complete: at most `limit`
+// suspended tries of up to 10 us each; false when the limit ran out (the
+// caller reports NTC_ERR_TIMEOUT and leaves).  Waiting warps sleep instead of
+// polling, leaving the issue slots to the other warpgroups.
 __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t phase, uint32_t limit) {
-  for (uint32_t i = 0; i < limit; ++i) {
-    if (mbar_try_wait(mbar, phase)) return true;
-    if (i > 64) __nanosleep(32);
-  }
+  for (uint32_t i = 0; i < limit; ++i)
+    if (mbar_try_wait_sleep(mbar, phase, 10000u)) return true;
   return false;
 }
 
@@ -211,6 +223,11 @@ __device__ __forceinline__ uint32_t pack_e4m3x2(float a, float b) {
 // Logistic sigmoid through the hardware tanh approximation:
 // 1/(1+e^-z) = (1 + tanh(z/2)) / 2, one MUFU operation (max relative error of
 // tanh.approx about 2^-11, i.e. < 2.5e-4 absolute on the sigmoid).
+__device__ __forceinline__ float tanh_fast(float z) {
+  float t;
+  asm("tanh.approx.f32 %0, %1;\n" : "=f"(t) : "f"(z));
+  return t;
+}
 __device__ __forceinline__ float sigmoid_fast(float z) {
   float t;
   asm("tanh.approx.f32 %0, %1;\n" : "=f"(t) : "f"(0.5f * z));

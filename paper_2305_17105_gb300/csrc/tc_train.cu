@@ -38,7 +38,7 @@ constexpr int kColD = 0;                // per warpgroup: layer accumulator (64)
 constexpr int kColW12 = 64;             // [dW1 db1; dW2 db2] accumulator (128)
 constexpr int kColW3 = 192;             // [dW3^T; db3] accumulator (16)
 constexpr uint32_t kGroup = 2048;       // bytes per 8-unit group of a 128-row tile
-constexpr uint32_t kWaitLimit = 1u << 22;
+constexpr uint32_t kWaitLimit = 1u << 18;  // suspended tries: ms to seconds
 
 // Shared-memory plan.  Input slots (generic layout): G0 groups, G1 groups,
 // [PE0..7][PE8..11, LOD, 0, 1, 1], zero groups up to k_int.

@@ -47,6 +47,10 @@ def _decode(mat, q, **kw):
     dict(width=1, height=1, channels=3, c0=4, c1=4, k_in=32),
     dict(width=256, height=512, channels=7, c0=10, c1=14, k_in=48),   # unmerged tails
     dict(width=128, height=128, channels=9, c0=16, c1=4, k_in=48, act=1),
+    dict(width=256, height=256, channels=8, c0=8, c1=12, k_in=48),    # tail word of G1 only
+    dict(width=128, height=128, channels=6, c0=9, c1=9, k_in=32),     # 1-channel tails
+    dict(width=256, height=128, channels=10, c0=13, c1=16, k_in=48),  # two 5-8 channel words
+    dict(width=256, height=256, channels=12, c0=12, c1=12, q0=0.1, q1=0.05, k_in=48),  # generic
 ])
 def test_decode_f16_matches_oracle(shape):
     case = make_case(seed=51, **shape)
