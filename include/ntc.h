@@ -194,15 +194,18 @@ int ntc_decode(const ntc_material* m, const float* uvl, int64_t n, void* out,
                int64_t noise_step, void* stream);
 
 /* Launch shape of the tensor-core decode: warpgroup tile pipelines per CTA
- * (one CTA per SM, 128 TMEM columns per pipeline), 2, 3 or 4; 0 restores the
+ * (one CTA per SM, 128 TMEM columns per pipeline), 2, 3 or 4, or 5 for the
+ * warp-specialised form (4 compute warpgroups whose MMA chains a fifth
+ * warpgroup issues; FP16, FP8 materials run 4 pipelines); 0 restores the
  * default (4).  Process-wide; takes effect for later ntc_decode calls. */
 int ntc_set_decode_warpgroups(int32_t nwg);
 
 /* Autotuner of the tensor-core decode: times every launch shape (1 warm-up
  * + 3 timed launches each, CUDA events on `stream`) on the caller's queries
  * (writing `out`), selects the fastest as ntc_set_decode_warpgroups would,
- * and returns it in *best (host).  ms_out (host, nullable) receives the
- * mean time per launch of the shapes 2, 3, 4.  Synchronises the stream. */
+ * and returns it in *best (host).  ms_out (host, nullable, 4 floats)
+ * receives the mean time per launch of the shapes 2, 3, 4, 5.  Synchronises
+ * the stream. */
 int ntc_autotune_decode(const ntc_material* m, const float* uvl, int64_t n, void* out,
                         int32_t out_dtype, int32_t filter, int32_t* best, float* ms_out,
                         void* stream);

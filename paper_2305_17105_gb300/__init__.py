@@ -264,12 +264,12 @@ def ntc_autotune_decode(mat: Material, uvl, out, filter=FILTER_NEAREST, stream=N
     """Pick the fastest tensor-core launch shape on these queries; returns
     (best warpgroups, {shape: ms per launch})."""
     best = C.c_int32(0)
-    ms = (C.c_float * 3)()
+    ms = (C.c_float * 4)()
     dt = DTYPE_F16 if out.dtype == torch.float16 else DTYPE_F32
     s = mat.struct
     _call("ntc_autotune_decode", C.byref(s), _ptr(uvl), uvl.shape[0], _ptr(out), dt, filter,
           C.byref(best), C.cast(ms, C.c_void_p), _stream(stream))
-    return best.value, {2: ms[0], 3: ms[1], 4: ms[2]}
+    return best.value, {2: ms[0], 3: ms[1], 4: ms[2], 5: ms[3]}
 
 
 def grads_struct(mat: Material, grid0=None, grid1=None, w=None, b=None) -> ntc_grads:

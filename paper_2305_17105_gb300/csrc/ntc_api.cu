@@ -170,7 +170,7 @@ int ntc_decode(const ntc_material* m, const float* uvl, int64_t n, void* out, in
 }
 
 int ntc_set_decode_warpgroups(int32_t nwg) {
-  if (nwg != 0 && (nwg < 2 || nwg > 4)) return fail(NTC_ERR_ARG, "warpgroups %d", nwg);
+  if (nwg != 0 && (nwg < 2 || nwg > 5)) return fail(NTC_ERR_ARG, "warpgroups %d", nwg);
   g_decode_nwg.store(nwg);
   return NTC_OK;
 }
@@ -186,13 +186,13 @@ int ntc_autotune_decode(const ntc_material* m, const float* uvl, int64_t n, void
   CHECK_PTR(uvl, "uvl");
   CHECK_PTR(out, "out");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const int shapes[3] = {2, 3, 4};
+  const int shapes[4] = {2, 3, 4, 5};
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     return cuda_status(cudaGetLastError(), "autotune events");
   float best_ms = 1e30f;
   int best_nwg = 0, rc = NTC_OK;
-  for (int i = 0; i < 3 && rc == NTC_OK; ++i) {
+  for (int i = 0; i < 4 && rc == NTC_OK; ++i) {
     cudaError_t e = ntc::launch_decode_tc(*m, uvl, n, out, out_dtype, filter, s, shapes[i]);
     if (e == cudaSuccess) e = cudaEventRecord(e0, s);
     for (int r = 0; r < 3 && e == cudaSuccess; ++r)

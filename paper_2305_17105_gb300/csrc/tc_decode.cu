@@ -292,23 +292,47 @@ __device__ void stage_shared(const ntc_material& M, const Plan& P, uint8_t* sm, 
   }
 }
 
-// One 8-slot group into the TMEM A columns of this thread's row:
-// FP16 -> 4 columns; FP8 -> 2 columns (scaled by `inv_scale` first).
-template <bool F8>
-__device__ __forceinline__ void put_group(uint32_t ta, int g, const float (&v)[8], float inv_scale) {
+// Where a thread's input row goes: its TMEM lane (A operand read from TMEM;
+// an 8-slot group is 4 FP16 / 2 FP8 columns) or its 16-byte chunks of a
+// 128-row canonical K-major tile in shared memory (A read through a
+// descriptor; chunk stride 16 row groups x 128 bytes along K).
+struct TmemRow {
+  uint32_t ta;
+  __device__ __forceinline__ void put4(int g, uint4 w) const { tc::tmem_st4(ta + 4 * g, w); }
+  __device__ __forceinline__ void put2(int g, uint32_t a, uint32_t b) const {
+    tc::tmem_st2(ta + 2 * g, a, b);
+  }
+};
+struct SmemRow {
+  uint8_t* p;  // this row's chunk of K group 0
+  __device__ __forceinline__ void put4(int g, uint4 w) const {
+    *reinterpret_cast<uint4*>(p + g * 2048) = w;
+  }
+  __device__ __forceinline__ void put2(int g, uint32_t a, uint32_t b) const {
+    *reinterpret_cast<uint2*>(p + (g >> 1) * 2048 + (g & 1) * 8) = make_uint2(a, b);
+  }
+};
+__device__ __forceinline__ uint8_t* smem_row(uint8_t* tile, int row) {
+  return tile + (row >> 3) * 128 + (row & 7) * 16;
+}
+
+// One 8-slot group of this thread's row: FP16, or FP8 (scaled by
+// `inv_scale` first).
+template <bool F8, class S>
+__device__ __forceinline__ void put_group(const S& dst, int g, const float (&v)[8], float inv_scale) {
   if (F8) {
     const uint32_t a = tc::pack_e4m3x2(v[0] * inv_scale, v[1] * inv_scale) |
                        (tc::pack_e4m3x2(v[2] * inv_scale, v[3] * inv_scale) << 16);
     const uint32_t b = tc::pack_e4m3x2(v[4] * inv_scale, v[5] * inv_scale) |
                        (tc::pack_e4m3x2(v[6] * inv_scale, v[7] * inv_scale) << 16);
-    tc::tmem_st2(ta + 2 * g, a, b);
+    dst.put2(g, a, b);
   } else {
     uint4 w;
     w.x = tc::pack_f16x2(v[0], v[1]);
     w.y = tc::pack_f16x2(v[2], v[3]);
     w.z = tc::pack_f16x2(v[4], v[5]);
     w.w = tc::pack_f16x2(v[6], v[7]);
-    tc::tmem_st4(ta + 4 * g, w);
+    dst.put4(g, w);
   }
 }
 
@@ -483,12 +507,13 @@ __device__ __forceinline__ uint2 t_half(const uint32_t (&w)[4], uint32_t wx0, ui
 
 // The two PE groups (FP16): (sin, cos) pairs of the 3 octaves of x, then of
 // y, then (LOD, 0) and the constant-one bias slots.
+template <class S>
 __device__ __forceinline__ void pe_groups(const Plan& P, const uint8_t* sm, uint32_t lodh, int x,
-                                          int y, uint32_t ta) {
+                                          int y, const S& dst) {
   const uint4* pe = reinterpret_cast<const uint4*>(sm + P.pe);
   const uint4 px = pe[x & 7], py = pe[y & 7];
-  tc::tmem_st4(ta + 4 * P.gpe, make_uint4(px.x, px.y, px.z, py.x));
-  tc::tmem_st4(ta + 4 * (P.gpe + 1), make_uint4(py.y, py.z, lodh, tc::pack_f16x2(1.f, 1.f)));
+  dst.put4(P.gpe, make_uint4(px.x, px.y, px.z, py.x));
+  dst.put4(P.gpe + 1, make_uint4(py.y, py.z, lodh, tc::pack_f16x2(1.f, 1.f)));
 }
 
 // Per-grid FP16 constants of the fast layout.
@@ -506,8 +531,9 @@ struct FastK {
 };
 
 // Fast layout: every group of the row from the prefetched cells.
+template <class S>
 __device__ __forceinline__ void build_fast(const Plan& P, const FastK& K, const uint8_t* sm,
-                                           const Row& r, uint32_t ta) {
+                                           const Row& r, const S& dst) {
   const uint32_t fx0 = r.frac & 15, fx1 = (r.frac >> 8) & 15;
   const YLerp y0 = ylerp_of((r.frac >> 4) & 15, K.s[0], K.s16[0], K.m7q[0]);
   const YLerp y1 = ylerp_of((r.frac >> 12) & 15, K.s[1], K.s16[1], K.m7q[1]);
@@ -517,14 +543,14 @@ __device__ __forceinline__ void build_fast(const Plan& P, const FastK& K, const 
     if (f < P.eo0) {
       const uint32_t w[4] = {word_of(r.c0[0], f), word_of(r.c0[1], f), word_of(r.c0[2], f),
                              word_of(r.c0[3], f)};
-      tc::tmem_st4(ta + 4 * kg++, eo_group(w, 16 - fx0, fx0, y0));
+      dst.put4(kg++, eo_group(w, 16 - fx0, fx0, y0));
     }
 #pragma unroll
   for (int f = 0; f < 2; ++f)
     if (f < P.eo1) {
       const uint32_t w[4] = {word_of(r.c1[0], f), word_of(r.c1[1], f), word_of(r.c1[2], f),
                              word_of(r.c1[3], f)};
-      tc::tmem_st4(ta + 4 * kg++, eo_group(w, 16 - fx1, fx1, y1));
+      dst.put4(kg++, eo_group(w, 16 - fx1, fx1, y1));
     }
   if (P.t0 | P.t1) {
     uint2 a = make_uint2(0, 0), b = make_uint2(0, 0);
@@ -537,25 +563,25 @@ __device__ __forceinline__ void build_fast(const Plan& P, const FastK& K, const 
       b = t_half(w, 16 - fx1, fx1, y1);
     }
     if (!P.t0) { a = b; b = make_uint2(0, 0); }
-    tc::tmem_st4(ta + 4 * kg++, make_uint4(a.x, a.y, b.x, b.y));
+    dst.put4(kg++, make_uint4(a.x, a.y, b.x, b.y));
   }
   const MipTab* tb = reinterpret_cast<const MipTab*>(sm + P.tab);
-  pe_groups(P, sm, tb->lodh[r.m], r.x, r.y, ta);
+  pe_groups(P, sm, tb->lodh[r.m], r.x, r.y, dst);
 }
 
 // Zero groups between the PE groups and K (written once per material: the
 // per-tile builds never touch them).
-template <bool F8>
-__device__ __forceinline__ void zero_tail_groups(const Plan& P, uint32_t ta) {
+template <bool F8, class S>
+__device__ __forceinline__ void zero_tail_groups(const Plan& P, const S& dst) {
   const float z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  for (int g = P.gpe + 2; g < P.k_int / 8; ++g) put_group<F8>(ta, g, z, 1.f);
+  for (int g = P.gpe + 2; g < P.k_int / 8; ++g) put_group<F8>(dst, g, z, 1.f);
 }
 
 // Generic layout (other bit widths, F32 grids, FP8 operands): float
 // dequantisation and interpolation, channels in order.
-template <bool F8>
+template <bool F8, class S>
 __device__ __forceinline__ void generic_grid(const ntc_material& M, const MipTab* tb, int k,
-                                             const Plan& P, const Row& r, uint32_t ta, int kg0,
+                                             const Plan& P, const Row& r, const S& dst, int kg0,
                                              float inv_sa) {
   const int c = k ? M.c1 : M.c0;
   const float q = k ? M.q1 : M.q0;
@@ -599,19 +625,19 @@ __device__ __forceinline__ void generic_grid(const ntc_material& M, const MipTab
       float v[8];
 #pragma unroll
       for (int e = 0; e < 8; ++e) v[e] = acc[8 * g + e];
-      put_group<F8>(ta, kg0 + g, v, inv_sa);
+      put_group<F8>(dst, kg0 + g, v, inv_sa);
     }
 }
 
-template <bool F8>
+template <bool F8, class S>
 __device__ __forceinline__ void build_generic(const ntc_material& M, const Plan& P,
-                                              const uint8_t* sm, const Row& r, uint32_t ta,
+                                              const uint8_t* sm, const Row& r, const S& dst,
                                               float inv_sa) {
   const MipTab* tb = reinterpret_cast<const MipTab*>(sm + P.tab);
-  generic_grid<F8>(M, tb, 0, P, r, ta, 0, inv_sa);
-  generic_grid<F8>(M, tb, 1, P, r, ta, P.f0, inv_sa);
+  generic_grid<F8>(M, tb, 0, P, r, dst, 0, inv_sa);
+  generic_grid<F8>(M, tb, 1, P, r, dst, P.f0, inv_sa);
   if (!F8) {
-    pe_groups(P, sm, tb->lodh[r.m], r.x, r.y, ta);
+    pe_groups(P, sm, tb->lodh[r.m], r.x, r.y, dst);
   } else {
     struct Pe {
       float v[16];
@@ -621,12 +647,70 @@ __device__ __forceinline__ void build_generic(const ntc_material& M, const Plan&
     float v[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) v[e] = pe.v[e];
-    put_group<F8>(ta, P.gpe, v, inv_sa);
+    put_group<F8>(dst, P.gpe, v, inv_sa);
 #pragma unroll
     for (int e = 0; e < 4; ++e) v[e] = pe.v[8 + e];
     v[4] = tb->lodn[r.m];
     v[5] = v[6] = v[7] = 0.f;
-    put_group<F8>(ta, P.gpe + 1, v, inv_sa);
+    put_group<F8>(dst, P.gpe + 1, v, inv_sa);
+  }
+}
+
+// One texel's C outputs (FP16 or FP32) at output row q.
+__device__ __forceinline__ void store_texel(void* out, int out_dtype, int64_t q, int C,
+                                            const float (&yv)[16]) {
+  if (out_dtype == NTC_DTYPE_F16) {
+    __half* o = static_cast<__half*>(out) + q * C;
+    if (C == 16) {
+      uint4 a, b;
+      a.x = tc::pack_f16x2(yv[0], yv[1]); a.y = tc::pack_f16x2(yv[2], yv[3]);
+      a.z = tc::pack_f16x2(yv[4], yv[5]); a.w = tc::pack_f16x2(yv[6], yv[7]);
+      b.x = tc::pack_f16x2(yv[8], yv[9]); b.y = tc::pack_f16x2(yv[10], yv[11]);
+      b.z = tc::pack_f16x2(yv[12], yv[13]); b.w = tc::pack_f16x2(yv[14], yv[15]);
+      reinterpret_cast<uint4*>(o)[0] = a;
+      reinterpret_cast<uint4*>(o)[1] = b;
+    } else if ((C & 3) == 0) {
+#pragma unroll
+      for (int c = 0; c < 16; c += 4)
+        if (c < C)
+          *reinterpret_cast<uint2*>(o + c) =
+              make_uint2(tc::pack_f16x2(yv[c], yv[c + 1]), tc::pack_f16x2(yv[c + 2], yv[c + 3]));
+    } else {
+#pragma unroll
+      for (int c = 0; c < 16; ++c)
+        if (c < C) o[c] = __float2half_rn(yv[c]);
+    }
+  } else {
+    float* o = static_cast<float*>(out) + q * C;
+    if ((C & 3) == 0) {
+#pragma unroll
+      for (int c = 0; c < 16; c += 4)
+        if (c < C) *reinterpret_cast<float4*>(o + c) = make_float4(yv[c], yv[c + 1], yv[c + 2], yv[c + 3]);
+    } else {
+#pragma unroll
+      for (int c = 0; c < 16; ++c)
+        if (c < C) o[c] = yv[c];
+    }
+  }
+}
+
+// FP16 hidden-layer epilogue in quarters of 16 accumulators (a smaller
+// register footprint, for the warp-specialised kernel's compute warps).
+__device__ __forceinline__ void hidden_epilogue_q(uint32_t td, uint32_t ta, int act) {
+#pragma unroll
+  for (int qtr = 0; qtr < 4; ++qtr) {
+    float a[16];
+    tc::tmem_ld16(td + 16 * qtr, a);
+    tc::tmem_ld_wait();
+    uint32_t w[8];
+    if (act == NTC_ACT_RELU) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) w[i] = tc::pack_f16x2_relu(a[2 * i], a[2 * i + 1]);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) w[i] = tc::pack_f16x2(act_fwd(act, a[2 * i]), act_fwd(act, a[2 * i + 1]));
+    }
+    tc::tmem_st8(ta + 8 * qtr, w);
   }
 }
 
@@ -729,7 +813,7 @@ __global__ void __launch_bounds__(kRows* kNWG, 1) decode_tc_kernel(
     tc::tmem_st4(tw + kColCst + lane, make_uint4(tc::pack_f16x2(1.f, 1.f), 0, 0, 0));
     tc::tmem_st4(tw + kColCst + 4 + lane, make_uint4(0, 0, 0, 0));
   }
-  zero_tail_groups<F8>(P, tx);
+  zero_tail_groups<F8>(P, TmemRow{tx});
 
   float sc[3] = {1.f, 1.f, 1.f}, inv_sa[3] = {1.f, 1.f, 1.f};
   if (F8) {
@@ -766,9 +850,9 @@ __global__ void __launch_bounds__(kRows* kNWG, 1) decode_tc_kernel(
     locate(M, tb, load_query(uvl, q0, tl < ntiles && q0 < n), tri, row, r);
     if (FAST) {
       gather_fast(tb, P, r);
-      build_fast(P, K, sm, r, tx);
+      build_fast(P, K, sm, r, TmemRow{tx});
     } else {
-      build_generic<F8>(M, P, sm, r, tx, inv_sa[0]);
+      build_generic<F8>(M, P, sm, r, TmemRow{tx}, inv_sa[0]);
     }
     cur_valid = r.valid;
     cur_wtap = r.wtap;
@@ -805,8 +889,8 @@ __global__ void __launch_bounds__(kRows* kNWG, 1) decode_tc_kernel(
 
     // ---- layer 2; meanwhile the next tile's X (layer 1 is done with X) -------
     if (row == 32) issue_layer<F8>(tw, tw + kColH, dsc + 4, kHidden / KSTEP, id64, !F8, tw + kColCst, bar);
-    if (FAST) build_fast(P, K, sm, nxt, tx);
-    else build_generic<F8>(M, P, sm, nxt, tx, inv_sa[0]);
+    if (FAST) build_fast(P, K, sm, nxt, TmemRow{tx});
+    else build_generic<F8>(M, P, sm, nxt, TmemRow{tx}, inv_sa[0]);
     cur_valid = nxt.valid;
     cur_wtap = nxt.wtap;
     if (!tc::mbar_wait(bar, phase, kWaitLimit)) *abort_flag = 1;
@@ -843,43 +927,7 @@ __global__ void __launch_bounds__(kRows* kNWG, 1) decode_tc_kernel(
         yv[c] = s;
       }
     }
-    const bool writer = valid && (!tri || (row & 7) == 0);
-    if (writer) {
-      if (out_dtype == NTC_DTYPE_F16) {
-        __half* o = static_cast<__half*>(out) + q * C;
-        if (C == 16) {
-          uint4 a, b;
-          a.x = tc::pack_f16x2(yv[0], yv[1]); a.y = tc::pack_f16x2(yv[2], yv[3]);
-          a.z = tc::pack_f16x2(yv[4], yv[5]); a.w = tc::pack_f16x2(yv[6], yv[7]);
-          b.x = tc::pack_f16x2(yv[8], yv[9]); b.y = tc::pack_f16x2(yv[10], yv[11]);
-          b.z = tc::pack_f16x2(yv[12], yv[13]); b.w = tc::pack_f16x2(yv[14], yv[15]);
-          reinterpret_cast<uint4*>(o)[0] = a;
-          reinterpret_cast<uint4*>(o)[1] = b;
-        } else if ((C & 3) == 0) {
-#pragma unroll
-          for (int c = 0; c < 16; c += 4)
-            if (c < C)
-              *reinterpret_cast<uint2*>(o + c) =
-                  make_uint2(tc::pack_f16x2(yv[c], yv[c + 1]), tc::pack_f16x2(yv[c + 2], yv[c + 3]));
-        } else {
-#pragma unroll
-          for (int c = 0; c < 16; ++c)
-            if (c < C) o[c] = __float2half_rn(yv[c]);
-        }
-      } else {
-        float* o = static_cast<float*>(out) + q * C;
-        if ((C & 3) == 0) {
-#pragma unroll
-          for (int c = 0; c < 16; c += 4)
-            if (c < C)
-              *reinterpret_cast<float4*>(o + c) = make_float4(yv[c], yv[c + 1], yv[c + 2], yv[c + 3]);
-        } else {
-#pragma unroll
-          for (int c = 0; c < 16; ++c)
-            if (c < C) o[c] = yv[c];
-        }
-      }
-    }
+    if (valid && (!tri || (row & 7) == 0)) store_texel(out, out_dtype, q, C, yv);
     // the next tile's layer 1 overwrites D: every row must have read it
     tc::bar_sync(bar_id, kRows);
     if (*abort_flag) { aborted = true; break; }
@@ -896,6 +944,253 @@ __global__ void __launch_bounds__(kRows* kNWG, 1) decode_tc_kernel(
     tc::fence_after_sync();
     tc::tmem_dealloc(tmem_base, kCols);
   }
+}
+
+// ---------------------------------------------------------------------------
+// Warp-specialised form (FP16): four compute warpgroups, each running its own
+// stream of tiles, and one issuer warpgroup whose warp w issues every
+// tcgen05.mma chain of compute warpgroup w.  A chain of dependent MMAs holds
+// its issuing thread until it drains, so issuing from the compute warps
+// stalls them; here they only hand over through mbarriers and keep working:
+//   X(i) in shared memory --x--> L1 --d--> epilogue 1 -> H --h--> L2 --d-->
+//   epilogue 2 -> H --h--> L3 (own accumulator D3) --o--> output,
+// and while L2(i) runs the compute warps build X(i+1), while L3(i) runs they
+// gather the cells of tile i+2, while L1(i+1) runs they write tile i.  L1
+// reads its A operand from shared memory, the bias steps a constant-one A
+// block in shared memory; L2 and L3 read H from TMEM.
+// TMEM per compute warpgroup (128 columns): D [0, 64), H [64, 96),
+// D3 [96, 112).
+// ---------------------------------------------------------------------------
+constexpr int kWsCompute = 4;
+constexpr int kWsThreads = kRows * (kWsCompute + 1);
+constexpr int kColD3 = 96;
+
+struct WsPlan {
+  uint32_t cst, x, xbytes, total;
+  __host__ __device__ explicit WsPlan(const Plan& P) {
+    uint32_t o = (P.total + 1023) / 1024 * 1024;
+    cst = o;  o += kRows * 16 * 2;                 // constant-one A block (K = 16)
+    xbytes = kRows * P.k_int * 2;
+    x = o;    o += kWsCompute * xbytes;            // one X tile per compute warpgroup
+    total = o;
+  }
+};
+
+template <bool FAST>
+__global__ void __launch_bounds__(kWsThreads, 1) decode_ws_kernel(
+    const ntc_material M, const float* __restrict__ uvl, int64_t n, void* __restrict__ out,
+    int out_dtype, int filter, int* status) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  __shared__ uint64_t bar_x[kWsCompute], bar_h[kWsCompute], bar_d[kWsCompute],
+      bar_o[kWsCompute], bar_fin[kWsCompute];
+  __shared__ uint32_t tmem_base;
+  __shared__ int wg_abort[kWsCompute];
+  const Plan P(M.c0, M.c1, M.bits0, M.bits1, M.encoding == NTC_GRID_PACKED, false, FAST);
+  const WsPlan W(P);
+  uint8_t* sm = smem_raw;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int wg = warp >> 2, row = tid & (kRows - 1);
+
+  stage_shared<false>(M, P, sm, tid, blockDim.x);
+  // constant-one A block: every row (1, 1, 0, ..., 0)
+  for (int i = tid; i < kRows * 16 / 2; i += blockDim.x) {
+    const int chunk = i >> 2, e = i & 3;
+    reinterpret_cast<uint32_t*>(sm + W.cst)[i] =
+        (chunk < kRows && e == 0) ? tc::pack_f16x2(1.f, 1.f) : 0u;
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(&tmem_base, 512);
+    tc::tmem_relinquish();
+  }
+  if (tid < kWsCompute) {
+    tc::mbar_init(&bar_x[tid], 4);
+    tc::mbar_init(&bar_h[tid], 4);
+    tc::mbar_init(&bar_d[tid], 1);
+    tc::mbar_init(&bar_o[tid], 1);
+    tc::mbar_init(&bar_fin[tid], 1);
+    wg_abort[tid] = 0;
+  }
+  if (wg < kWsCompute) zero_tail_groups<false>(P, SmemRow{smem_row(sm + W.x + wg * W.xbytes, row)});
+  tc::fence_mbar_init();
+  tc::fence_proxy_async();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+
+  const bool tri = filter == NTC_FILTER_TRILINEAR;
+  const int per_tile = tri ? kRows / 8 : kRows;
+  const int64_t ntiles = (n + per_tile - 1) / per_tile;
+  const int64_t stride = (int64_t)gridDim.x * kWsCompute;
+  constexpr uint32_t id64 = tc::idesc(kRows, kHidden), id16 = tc::idesc(kRows, kN3);
+  const int w = wg < kWsCompute ? wg : (warp & 3);  // the compute warpgroup served
+  const int64_t first = (int64_t)blockIdx.x * kWsCompute + w;
+  const uint32_t tw = tmem_base + 128u * w;
+
+  if (wg == kWsCompute) {
+    // ---- issuer warp w ------------------------------------------------------
+    if (lane == 0) {
+      const uint64_t* d = reinterpret_cast<const uint64_t*>(sm + P.desc);
+      const uint32_t xa = tc::smem_u32(sm + W.x + w * W.xbytes);
+      const uint64_t cst = tc::smem_desc(tc::smem_u32(sm + W.cst), 2048, 128);
+      const int k1 = P.k_int / 16;
+      uint32_t px = 0, ph = 0;
+      bool ok = true;
+      for (int64_t tl = first; tl < ntiles; tl += stride) {
+        if (!(ok = tc::mbar_wait(&bar_x[w], px, kWaitLimit))) break;
+        px ^= 1;
+        tc::fence_after_sync();
+        for (int s = 0; s < k1; ++s)
+          tc::mma_f16(tw, tc::smem_desc(xa + s * 4096, 2048, 128), d[s], id64, s > 0);
+        tc::mma_commit(&bar_d[w]);
+        if (!(ok = tc::mbar_wait(&bar_h[w], ph, kWaitLimit))) break;
+        ph ^= 1;
+        tc::fence_after_sync();
+        for (int s = 0; s < kHidden / 16; ++s)
+          tc::mma_f16_ta(tw, tw + kColH + 8 * s, d[4 + s], id64, s > 0);
+        tc::mma_f16(tw, cst, d[8], id64, 1);
+        tc::mma_commit(&bar_d[w]);
+        if (!(ok = tc::mbar_wait(&bar_h[w], ph, kWaitLimit))) break;
+        ph ^= 1;
+        tc::fence_after_sync();
+        for (int s = 0; s < kHidden / 16; ++s)
+          tc::mma_f16_ta(tw + kColD3, tw + kColH + 8 * s, d[9 + s], id16, s > 0);
+        tc::mma_f16(tw + kColD3, cst, d[13], id16, 1);
+        tc::mma_commit(&bar_o[w]);
+      }
+      if (!ok) *reinterpret_cast<volatile int*>(&wg_abort[w]) = 1;
+      // every MMA of this thread completes before TMEM is released
+      tc::mma_commit(&bar_fin[w]);
+      if (!tc::mbar_wait(&bar_fin[w], 0, kWaitLimit)) *reinterpret_cast<volatile int*>(&wg_abort[w]) = 1;
+    }
+  } else {
+    // ---- compute warpgroup w -------------------------------------------------
+    const uint32_t lq = (uint32_t)((warp & 3) * 32) << 16;
+    const uint32_t td = tw + lq, th = tw + kColH + lq, td3 = tw + kColD3 + lq;
+    const SmemRow xs{smem_row(sm + W.x + w * W.xbytes, row)};
+    const MipTab* tb = reinterpret_cast<const MipTab*>(sm + P.tab);
+    const FastK K(M);
+    volatile int* abort_flag = &wg_abort[w];
+    auto qindex = [&](int64_t t) { return tri ? t * per_tile + (row >> 3) : t * per_tile + row; };
+    auto build = [&](const Row& r) {
+      if (FAST) build_fast(P, K, sm, r, xs);
+      else build_generic<false>(M, P, sm, r, xs, 1.f);
+      tc::fence_proxy_async();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&bar_x[w]);
+    };
+    const int C = M.channels;
+    uint32_t pd = 0, po = 0;
+    int64_t tl = first;
+    int cur_valid = 0;
+    float cur_wtap = 0.f;
+    Row nxt;
+    Query nq;
+    if (tl < ntiles) {
+      Row r;
+      const int64_t q0 = qindex(tl);
+      locate(M, tb, load_query(uvl, q0, q0 < n), tri, row, r);
+      if (FAST) gather_fast(tb, P, r);
+      build(r);
+      cur_valid = r.valid;
+      cur_wtap = r.wtap;
+      const int64_t q1 = qindex(tl + stride);
+      locate(M, tb, load_query(uvl, q1, tl + stride < ntiles && q1 < n), tri, row, nxt);
+      if (FAST) gather_fast(tb, P, nxt);
+      const int64_t q2 = qindex(tl + 2 * stride);
+      nq = load_query(uvl, q2, tl + 2 * stride < ntiles && q2 < n);
+    }
+    for (; tl < ntiles; tl += stride) {
+      const int64_t q = qindex(tl);
+      const bool valid = cur_valid != 0;
+      const float wtap = cur_wtap;
+      // layer 1 -> H1
+      if (!tc::mbar_wait(&bar_d[w], pd, kWaitLimit)) *abort_flag = 1;
+      pd ^= 1;
+      tc::fence_after_sync();
+      hidden_epilogue_q(td, th, M.act);
+      tc::tmem_st_wait();
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&bar_h[w]);
+      // the next tile's input rows (layer 1 is done with X)
+      if (tl + stride < ntiles) {
+        build(nxt);
+        cur_valid = nxt.valid;
+        cur_wtap = nxt.wtap;
+      }
+      // layer 2 -> H2
+      if (!tc::mbar_wait(&bar_d[w], pd, kWaitLimit)) *abort_flag = 1;
+      pd ^= 1;
+      tc::fence_after_sync();
+      hidden_epilogue_q(td, th, M.act);
+      tc::tmem_st_wait();
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&bar_h[w]);
+      if (*abort_flag) break;
+      // the tile after next: texel and cells; its successor's query
+      locate(M, tb, nq, tri, row, nxt);
+      if (FAST) gather_fast(tb, P, nxt);
+      {
+        const int64_t t3 = tl + 3 * stride;
+        const int64_t q3 = qindex(t3);
+        nq = load_query(uvl, q3, t3 < ntiles && q3 < n);
+      }
+      // layer 3 -> output
+      if (!tc::mbar_wait(&bar_o[w], po, kWaitLimit)) *abort_flag = 1;
+      po ^= 1;
+      tc::fence_after_sync();
+      float yv[16];
+      tc::tmem_ld16(td3, yv);
+      tc::tmem_ld_wait();
+      tc::fence_before_sync();
+#pragma unroll
+      for (int c = 0; c < 16; ++c)
+        yv[c] = M.out_act == NTC_OUT_IDENTITY ? yv[c] : fmaf(0.5f, tc::tanh_fast(yv[c]), 0.5f);
+      if (tri) {
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          float s = yv[c] * wtap;
+          s += __shfl_xor_sync(0xffffffffu, s, 1);
+          s += __shfl_xor_sync(0xffffffffu, s, 2);
+          s += __shfl_xor_sync(0xffffffffu, s, 4);
+          yv[c] = s;
+        }
+      }
+      if (valid && (!tri || (row & 7) == 0)) store_texel(out, out_dtype, q, C, yv);
+      if (*abort_flag) break;
+    }
+  }
+
+  tc::fence_before_sync();
+  __syncthreads();
+  if (tid == 0) {
+    int any = 0;
+    for (int i = 0; i < kWsCompute; ++i) any |= wg_abort[i];
+    if (any) atomicExch(status, NTC_ERR_TIMEOUT);
+  }
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem_base, 512);
+  }
+}
+
+template <bool FAST>
+cudaError_t launch_ws(const ntc_material& m, const float* uvl, int64_t n, void* out, int out_dtype,
+                      int filter, cudaStream_t s) {
+  const Plan P(m.c0, m.c1, m.bits0, m.bits1, m.encoding == NTC_GRID_PACKED, false, FAST);
+  const WsPlan W(P);
+  cudaError_t e = cudaFuncSetAttribute(decode_ws_kernel<FAST>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)W.total);
+  if (e != cudaSuccess) return e;
+  const int per_tile = filter == NTC_FILTER_TRILINEAR ? kRows / 8 : kRows;
+  const int64_t tiles = (n + per_tile - 1) / per_tile;
+  const int64_t ctas = (tiles + kWsCompute - 1) / kWsCompute;
+  const int64_t cap = sm_count();
+  const int grid = (int)(ctas < cap ? ctas : cap);
+  decode_ws_kernel<FAST><<<grid, kWsThreads, W.total, s>>>(m, uvl, n, out, out_dtype, filter,
+                                                           status_word());
+  return cudaGetLastError();
 }
 
 template <bool F8, bool FAST, int kNWG>
@@ -991,7 +1286,7 @@ __global__ void __launch_bounds__(kRows * 4, 1) decode_batched_kernel(
       const ntc_material& Mn = mat_s[wg];
       const Plan Pn(Mn.c0, Mn.c1, Mn.bits0, Mn.bits1, Mn.encoding == NTC_GRID_PACKED, false, FAST);
       stage_shared<false>(Mn, Pn, sm, row, kRows);
-      zero_tail_groups<false>(Pn, tx);
+      zero_tail_groups<false>(Pn, TmemRow{tx});
       tc::tmem_st_wait();
       tc::fence_proxy_async();
       tc::bar_sync(bar_id, kRows);
@@ -1010,9 +1305,9 @@ __global__ void __launch_bounds__(kRows * 4, 1) decode_batched_kernel(
     locate(M, tb, load_query(uvl, qg, valid), tri, row, r);
     if (FAST) {
       gather_fast(tb, P, r);
-      build_fast(P, FastK(M), sm, r, tx);
+      build_fast(P, FastK(M), sm, r, TmemRow{tx});
     } else {
-      build_generic<false>(M, P, sm, r, tx, 1.f);
+      build_generic<false>(M, P, sm, r, TmemRow{tx}, 1.f);
     }
     tc::tmem_st_wait();
     tc::fence_before_sync();
@@ -1111,17 +1406,22 @@ bool fast_layout_ok(const ntc_material& m) {
 }
 
 // Launch shape: one CTA per SM with `nwg` warpgroup pipelines (2, 3 or 4;
-// 0 = 4), each holding 128 of the SM's 512 TMEM columns.
+// 0 = 4), each holding 128 of the SM's 512 TMEM columns, or (5) the
+// warp-specialised form: 4 compute warpgroups plus their MMA issuers (FP16;
+// FP8 runs 4 pipelines).
 cudaError_t launch_decode_tc(const ntc_material& m, const float* uvl, int64_t n, void* out,
                              int out_dtype, int filter, cudaStream_t s, int nwg) {
   if (n == 0) return cudaSuccess;
   if (nwg == 0) nwg = 4;
-  if (nwg < 2 || nwg > 4) return cudaErrorInvalidValue;
+  if (nwg < 2 || nwg > 5) return cudaErrorInvalidValue;
   if (m.precision == NTC_PREC_F8)
-    return launch_shape<true, false>(m, uvl, n, out, out_dtype, filter, s, nwg);
+    return launch_shape<true, false>(m, uvl, n, out, out_dtype, filter, s, nwg == 5 ? 4 : nwg);
   if (m.precision != NTC_PREC_F16) return cudaErrorInvalidValue;
   const Plan P(m.c0, m.c1, m.bits0, m.bits1, m.encoding == NTC_GRID_PACKED, false,
                fast_layout_ok(m));
+  if (nwg == 5)
+    return P.fast ? launch_ws<true>(m, uvl, n, out, out_dtype, filter, s)
+                  : launch_ws<false>(m, uvl, n, out, out_dtype, filter, s);
   if (P.fast) return launch_shape<false, true>(m, uvl, n, out, out_dtype, filter, s, nwg);
   return launch_shape<false, false>(m, uvl, n, out, out_dtype, filter, s, nwg);
 }

@@ -38,7 +38,7 @@ def _decode(mat, q, **kw):
     return to_np(out)
 
 
-@pytest.mark.parametrize("shape", [
+SHAPES = [
     dict(width=256, height=256, channels=8, c0=8, c1=8, q0=0.125, q1=0.125, k_in=32),
     dict(width=512, height=512, channels=16, c0=12, c1=12, k_in=48),
     dict(width=256, height=256, channels=12, c0=16, c1=16, k_in=48),
@@ -51,7 +51,10 @@ def _decode(mat, q, **kw):
     dict(width=128, height=128, channels=6, c0=9, c1=9, k_in=32),     # 1-channel tails
     dict(width=256, height=128, channels=10, c0=13, c1=16, k_in=48),  # two 5-8 channel words
     dict(width=256, height=256, channels=12, c0=12, c1=12, q0=0.1, q1=0.05, k_in=48),  # generic
-])
+]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
 def test_decode_f16_matches_oracle(shape):
     case = make_case(seed=51, **shape)
     mat, md = device_material(case, precision=ntc.PREC_F16)
@@ -63,6 +66,25 @@ def test_decode_f16_matches_oracle(shape):
         got = _decode(mat, q, out_dtype=dt)
         err = np.abs(got - ref).max()
         assert err <= OUT_TOL, (dt, err)
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_decode_warp_specialised_matches_oracle(shape):
+    """Launch shape 5 (compute warpgroups + MMA issuer warpgroup), nearest
+    and trilinear, FP16 and FP32 outputs."""
+    case = make_case(seed=59, **shape)
+    mat, md = device_material(case, precision=ntc.PREC_F16)
+    q = gen.random_queries(9 * 128 + 77, md.mips, seed=4059)
+    q[:2] = [[0.0, 0.0, 0.0], [0.999999, 0.999999, md.mips - 1]]
+    ref = md.decode(q)
+    ntc.ntc_set_decode_warpgroups(5)
+    try:
+        for dt in (torch.float32, torch.float16):
+            assert np.abs(_decode(mat, q, out_dtype=dt) - ref).max() <= OUT_TOL
+        tri = _decode(mat, q[:333], filter=ntc.FILTER_TRILINEAR)
+        assert np.abs(tri - md.decode_trilinear(q[:333])).max() <= OUT_TOL
+    finally:
+        ntc.ntc_set_decode_warpgroups(0)
 
 
 @pytest.mark.parametrize("n", [1, 127, 128, 129, 3000])
@@ -142,7 +164,7 @@ def test_decode_f8_close_to_oracle():
     assert oracle.psnr(ref, got) > 35.0
 
 
-@pytest.mark.parametrize("nwg", [2, 3, 4])
+@pytest.mark.parametrize("nwg", [2, 3, 4, 5])
 def test_decode_every_launch_shape(nwg):
     case = make_case(512, 512, 16, 12, 12, k_in=48, seed=57)
     mat, md = device_material(case, precision=ntc.PREC_F16)
@@ -165,7 +187,7 @@ def test_autotune_picks_a_shape_and_stays_correct():
     out = torch.empty((q.shape[0], 16), dtype=torch.float16, device=DEV)
     best, ms = ntc.ntc_autotune_decode(mat, uvl, out)
     try:
-        assert best in (2, 3, 4) and all(v > 0 for v in ms.values())
+        assert best in (2, 3, 4, 5) and all(v > 0 for v in ms.values())
         assert np.abs(_decode(mat, q) - md.decode(q)).max() <= OUT_TOL
     finally:
         ntc.ntc_set_decode_warpgroups(0)
