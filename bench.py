@@ -44,7 +44,7 @@ MAX_SM_MHZ = 2070.0
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="auto", choices=["auto", "f32", "f16", "f8"])
@@ -56,6 +56,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp32-compare", action="store_true")
+    ap.add_argument("--no-render", action="store_true",
+                    help="skip the camera-frame decode of the trained model")
+    ap.add_argument("--render-steps", type=int, default=1000,
+                    help="training steps added before the camera-frame decode")
     return ap.parse_args()
 
 
@@ -107,7 +111,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -209,6 +213,73 @@ def make_trainer(precision, total_steps, device="cuda"):
                      [w[0], w[2], w[4]], [w[1], w[3], w[5]], TRN_K, prec,
                      total_steps=total_steps, device=device)
     return tr, ntc.Target(chain, device=device), chain, (g0, g1), w
+
+
+# ----------------------------------------------------------------------------
+# Render-like decode of a trained model (camera frame, trilinear filtering)
+# ----------------------------------------------------------------------------
+def f8_of(ntc, mat16, w32, device="cuda"):
+    """E4M3 copy of a material: per-layer weight scales max|w|/448 and
+    activation scales that keep each layer's inputs inside the E4M3 range."""
+    import torch
+    ws, q8 = [], []
+    for l in range(3):
+        s = float(np.abs(w32[l]).max()) / 448.0
+        ws.append(s)
+        q8.append(torch.from_numpy(w32[l] / s).to(device).to(torch.float8_e4m3fn).view(torch.uint8))
+    scale = torch.tensor(ws + [1.0 / 256, 16.0 / 256, 16.0 / 256], dtype=torch.float32, device=device)
+    # FP8 operands take K in steps of 32: W1 padded with zero columns
+    k8 = (mat16.k_in + 31) // 32 * 32
+    q8[0] = torch.nn.functional.pad(q8[0], (0, k8 - mat16.k_in))
+    return mat16.with_(weights=q8, precision=ntc.PREC_F8, scale=scale, k_in=k8)
+
+
+def render_eval(ntc, tr, target, chain, batch, seed, extra_steps, stream):
+    """The camera workload: the training material's model after `extra_steps`
+    more steps, exported with 4-bit grids, decoded for a 3840x2160 frame with
+    trilinear filtering (8 decodes per pixel) in FP16, FP8 and FP32.  Reports
+    frame times, the PSNR of each reduced-precision frame against the FP32
+    form's frame, and the texture PSNR of mip 0 against the 8-bit reference."""
+    import torch
+    for _ in range(extra_steps):
+        ntc.ntc_train_step(tr, target, batch, seed)
+    m16 = tr.export(ntc.PREC_F16)
+    m32 = tr.export(ntc.PREC_F32)
+    m8 = f8_of(ntc, m16, [x.cpu().numpy() for x in tr.w_master])
+    q = gen.camera_queries(3840, 2160, TRN_SIDE, ntc.mips_of(TRN_SIDE, TRN_SIDE))
+    uvl = torch.from_numpy(q).cuda()
+    res = {"workload": f"3840x2160 camera frame over the trained {TRN_SIDE}^2x{TRN_C} material "
+                       "(plane pitched 60 deg, 90 deg FoV), trilinear: 8 decodes per pixel",
+           "pixels": int(q.shape[0]), "train_steps": int(tr.step_t.item())}
+    frames = {}
+    for name, m in (("f16", m16), ("f8", m8), ("f32", m32)):
+        o = torch.empty((q.shape[0], TRN_C), dtype=torch.float32, device="cuda")
+        ntc.ntc_decode(m, uvl, out=o, filter=ntc.FILTER_TRILINEAR)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(3):
+            ntc.ntc_decode(m, uvl, out=o, filter=ntc.FILTER_TRILINEAR)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / 3
+        res[f"frame_ms_{name}"] = ms
+        res[f"decodes_per_s_{name}"] = 8 * q.shape[0] / (ms / 1e3)
+        frames[name] = o
+
+    def psnr(a, b):
+        mse = float(((a - b) ** 2).mean())
+        return float("inf") if mse == 0 else 10 * math.log10(1.0 / mse)
+
+    res["psnr_vs_f32_form_db"] = {k: psnr(frames[k], frames["f32"]) for k in ("f16", "f8")}
+    # texture quality: every texel of mip 0 against the 8-bit reference
+    ys, xs = np.meshgrid(np.arange(TRN_SIDE), np.arange(TRN_SIDE), indexing="ij")
+    t0 = np.stack([(xs + 0.5) / TRN_SIDE, (ys + 0.5) / TRN_SIDE, np.zeros_like(xs, float)],
+                  -1).reshape(-1, 3).astype(np.float32)
+    dec = ntc.ntc_decode(m16, torch.from_numpy(t0).cuda())
+    refm = torch.from_numpy(chain[0].reshape(-1, TRN_C).astype(np.float32) / 255.0).cuda()
+    res["texture_psnr_mip0_db"] = psnr(dec, refm)
+    return res
 
 
 # ----------------------------------------------------------------------------
@@ -317,7 +388,7 @@ def main():
     q_host = torch.from_numpy(queries).pin_memory()
     q_dev = q_host.to(dev)
     out = torch.empty((args.queries, DEC_C), dtype=torch.float16, device=dev)
-    total = args.warmup + args.steps + 8
+    total = args.warmup + args.steps + 40 + args.render_steps  # + e2e and render passes
     tr, target, chain, tgrids, tw = make_trainer(train_prec, total)
     seed = 77 + rank
 
@@ -395,7 +466,8 @@ def main():
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(args.steps):
+        e2e_steps = min(args.steps, 20)
+        for _ in range(e2e_steps):
             qd = q_host.to(dev, non_blocking=True)
             o = ntc.ntc_decode(mat, qd, out_dtype=torch.float16)
             out_host.copy_(o, non_blocking=True)
@@ -404,7 +476,7 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         e2e_ms = max_over_ranks(e0.elapsed_time(e1), world)
-        e2e = {"value": world * args.queries * args.steps / (e2e_ms / 1e3), "unit": "texels/s",
+        e2e = {"value": world * args.queries * e2e_steps / (e2e_ms / 1e3), "unit": "texels/s",
                "h2d_bytes_per_step": int(args.queries * 12),
                "d2h_bytes_per_step": int(args.queries * DEC_C * 2 + 4)}
 
@@ -450,6 +522,13 @@ def main():
                "train_samples_per_s": trate, "train_cores": tthreads,
                "train_sample": f"first {tn} of the 2^18 training texels ({tdt:.1f} s)"}
 
+    render = None
+    if not args.no_render:
+        try:
+            render = render_eval(ntc, tr, target, chain, args.batch, seed, args.render_steps, stream)
+        except Exception as e:  # reported, never fatal to the headline line
+            render = {"error": f"{type(e).__name__}: {e}"[:300]}
+
     kernels_per_step = 1 + 3  # decode; train: fused fwd/bwd, Adam, step counter
     line = {
         "metric": METRIC, "value": value, "unit": "texels/s", "n_gpus": world,
@@ -466,6 +545,7 @@ def main():
         "train_samples_per_s": train_rate, "train_loss": loss,
         "decode_ms": statistics.median(dec_ms), "train_ms": statistics.median(trn_ms),
         "roofline": roof, "tuning": tuning, "e2e": e2e, "fp32_path": fp32, "cpu_baseline": cpu,
+        "render": render,
         "gpu_launches": kernels_per_step * args.steps,
         "clocks": clk.summary(), "wall_s": t_wall,
     }

@@ -197,7 +197,7 @@ int ntc_decode(const ntc_material* m, const float* uvl, int64_t n, void* out,
  * (one CTA per SM, 128 TMEM columns per pipeline), 2, 3 or 4, or 5 for the
  * warp-specialised form (4 compute warpgroups whose MMA chains a fifth
  * warpgroup issues; FP16, FP8 materials run 4 pipelines); 0 restores the
- * default (4).  Process-wide; takes effect for later ntc_decode calls. */
+ * default (5).  Process-wide; takes effect for later ntc_decode calls. */
 int ntc_set_decode_warpgroups(int32_t nwg);
 
 /* Autotuner of the tensor-core decode: times every launch shape (1 warm-up

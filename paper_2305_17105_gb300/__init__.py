@@ -414,6 +414,26 @@ class Trainer:
         self.total_steps, self.lr_grid, self.lr_mlp = total_steps, lr_grid, lr_mlp
         self.betas, self.eps = betas, eps
 
+    def export(self, precision=PREC_F16, stream=None) -> Material:
+        """The compressed material of the current parameters (Sec. 4.2):
+        every grid value quantised to its B-bit index (bit-exact rounding)
+        and packed by ``ntc_quantize_pack``; weights in the requested
+        precision (FP16 or FP32) from the FP32 masters; biases copied."""
+        m = self.material
+        g0 = [ntc_quantize_pack(g.contiguous(), m.c0, m.bits0, m.q0, stream=stream).view(
+            g.shape[0], g.shape[1], -1) for g in m.grids0]
+        g1 = [ntc_quantize_pack(g.contiguous(), m.c1, m.bits1, m.q1, stream=stream).view(
+            g.shape[0], g.shape[1], -1) for g in m.grids1]
+        if precision == PREC_F16:
+            w = [x.half().contiguous() for x in self.w_master]
+        elif precision == PREC_F32:
+            w = [x.clone() for x in self.w_master]
+        else:
+            raise ValueError("export writes FP16 or FP32 weights")
+        return Material(m.width, m.height, m.channels, m.c0, m.c1, m.bits0, m.bits1, m.q0, m.q1,
+                        g0, g1, w, [b.clone() for b in self.b], m.k_in, precision, m.act,
+                        m.out_act)
+
     @property
     def struct(self) -> ntc_trainer:
         t = ntc_trainer()

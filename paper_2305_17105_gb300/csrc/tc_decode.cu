@@ -1405,14 +1405,14 @@ bool fast_layout_ok(const ntc_material& m) {
   return true;
 }
 
-// Launch shape: one CTA per SM with `nwg` warpgroup pipelines (2, 3 or 4;
-// 0 = 4), each holding 128 of the SM's 512 TMEM columns, or (5) the
-// warp-specialised form: 4 compute warpgroups plus their MMA issuers (FP16;
-// FP8 runs 4 pipelines).
+// Launch shape: one CTA per SM with `nwg` warpgroup pipelines (2, 3 or 4),
+// each holding 128 of the SM's 512 TMEM columns, or (5, the default for 0)
+// the warp-specialised form: 4 compute warpgroups plus their MMA issuers
+// (FP16; FP8 runs 4 pipelines).
 cudaError_t launch_decode_tc(const ntc_material& m, const float* uvl, int64_t n, void* out,
                              int out_dtype, int filter, cudaStream_t s, int nwg) {
   if (n == 0) return cudaSuccess;
-  if (nwg == 0) nwg = 4;
+  if (nwg == 0) nwg = 5;
   if (nwg < 2 || nwg > 5) return cudaErrorInvalidValue;
   if (m.precision == NTC_PREC_F8)
     return launch_shape<true, false>(m, uvl, n, out, out_dtype, filter, s, nwg == 5 ? 4 : nwg);
