@@ -91,6 +91,9 @@ struct BatchHeader {
 uint32_t batched_wg_smem(const ntc_material& m, bool fast);
 bool batched_fast(const ntc_material& m);
 bool fast_layout_ok(const ntc_material& m);
+// Warp-specialised tensor-core decode (FP16), fast 4-bit layout or generic.
+cudaError_t launch_decode_ws(const ntc_material& m, const float* uvl, int64_t n, void* out,
+                             int out_dtype, int filter, cudaStream_t s, bool fast);
 cudaError_t launch_decode_batched(const BatchHeader* dev, int64_t total_tiles, uint32_t wg_smem,
                                   bool fast, const float* uvl, void* out, int out_dtype, int filter,
                                   cudaStream_t s);

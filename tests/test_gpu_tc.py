@@ -51,6 +51,10 @@ SHAPES = [
     dict(width=128, height=128, channels=6, c0=9, c1=9, k_in=32),     # 1-channel tails
     dict(width=256, height=128, channels=10, c0=13, c1=16, k_in=48),  # two 5-8 channel words
     dict(width=256, height=256, channels=12, c0=12, c1=12, q0=0.1, q1=0.05, k_in=48),  # generic
+    dict(width=128, height=128, channels=4, c0=8, c1=16, k_in=48),    # fast classes (0, 2),
+    dict(width=128, height=256, channels=11, c0=12, c1=8, k_in=48),   # (1, 0),
+    dict(width=256, height=128, channels=16, c0=16, c1=8, k_in=48),   # (2, 0),
+    dict(width=128, height=128, channels=3, c0=14, c1=10, k_in=48),   # (2, 1)
 ]
 
 
