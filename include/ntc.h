@@ -129,7 +129,12 @@ typedef struct {
  * (for NTC_PREC_F32 the material's w[l] must equal w_master[l]; for F16 the
  * step rewrites the material's half copies from the masters after each
  * update).  adam_m, adam_v and grad have params' length; grad is scratch that
- * every step leaves zeroed (initialise it to zero once). */
+ * every step leaves zeroed (initialise it to zero once).  `noisy` (nullable)
+ * is scratch of params' length: with it a noisy step first writes the grids
+ * plus this step's quantisation noise (Sec. 4.2) into it in one dense pass
+ * and the fused step gathers from there (each grid value is hashed once per
+ * step instead of once per tap that reads it); without it the fused step
+ * adds the noise per tap.  Both give the same noisy values. */
 typedef struct {
   float* params;
   float* adam_m;
@@ -143,6 +148,7 @@ typedef struct {
   float lr_grid;        /* 0.01 in the paper */
   float lr_mlp;         /* 0.005 in the paper */
   float beta1, beta2, eps;
+  float* noisy;         /* optional scratch, params' length (see above) */
 } ntc_trainer;
 
 /* Reference texture set: the 8-bit mip chain, texel values q/255. */

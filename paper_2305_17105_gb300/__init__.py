@@ -66,7 +66,7 @@ class ntc_trainer(C.Structure):
                 ("grad", C.c_void_p), ("n_params", C.c_int64), ("w_master", C.c_void_p * 3),
                 ("step", C.c_void_p), ("total_steps", C.c_int64), ("lr_grid", C.c_float),
                 ("lr_mlp", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float),
-                ("eps", C.c_float)]
+                ("eps", C.c_float), ("noisy", C.c_void_p)]
 
 
 class ntc_batch(C.Structure):
@@ -377,7 +377,7 @@ class Trainer:
     def __init__(self, width, height, channels, c0, c1, bits0, bits1, q0, q1, grids0, grids1,
                  weights, biases, k_in, precision=PREC_F32, act=ACT_RELU, out_act=OUT_SIGMOID,
                  total_steps=1000, lr_grid=0.01, lr_mlp=0.005, betas=(0.9, 0.999), eps=1e-8,
-                 device="cuda"):
+                 device="cuda", noisy_scratch=True):
         tensors = [np.asarray(g, np.float32) for g in grids0] + \
                   [np.asarray(g, np.float32) for g in grids1]
         mlp = []
@@ -395,6 +395,8 @@ class Trainer:
         self.adam_m = torch.zeros_like(self.params)
         self.adam_v = torch.zeros_like(self.params)
         self.grad = torch.zeros_like(self.params)
+        # scratch for the dense noise pass of each step (None: noise per tap)
+        self.noisy = torch.empty_like(self.params) if noisy_scratch else None
         self.step_t = torch.zeros(1, dtype=torch.int64, device=device)
         self.loss = torch.zeros(1, dtype=torch.float32, device=device)
         views = [self.params[o:o + t.size].view(t.shape) for o, t in zip(offs, tensors)]
@@ -447,6 +449,7 @@ class Trainer:
         t.lr_grid, t.lr_mlp = self.lr_grid, self.lr_mlp
         t.beta1, t.beta2 = self.betas
         t.eps = self.eps
+        t.noisy = self.noisy.data_ptr() if self.noisy is not None else None
         return t
 
 

@@ -116,6 +116,30 @@ __global__ void __launch_bounds__(kAdamBlock) adam_kernel(const AdamArgs A) {
 
 __global__ void advance_step_kernel(int64_t* step) { *step += 1; }
 
+// One thread per channel pair of a grid cell: both channels' noise comes
+// from the same 64-bit draw (noise_of), added in FP32 exactly as the fused
+// step adds it per tap.
+__global__ void __launch_bounds__(kNoiseBlock) noise_grids_kernel(const NoiseArgs a) {
+  int s = 0;
+  while (s + 1 < a.nseg && (int64_t)blockIdx.x >= a.block_start[s + 1]) ++s;
+  const NoiseSeg& g = a.seg[s];
+  const int64_t p = ((int64_t)blockIdx.x - a.block_start[s]) * kNoiseBlock + threadIdx.x;
+  if (p >= g.pairs) return;
+  const int pc = (g.c + 1) >> 1;
+  const int64_t cell = p / pc;
+  const int ch = 2 * (int)(p - cell * pc);
+  const uint64_t key = rng_key(a.seed, noise_stream(*a.step));
+  const int64_t i = g.off + cell * g.c + ch;
+  float v = a.src[i];
+  v += noise_of(key, g.level, g.grid, (int)cell, ch, g.c, g.q);
+  a.dst[i] = v;
+  if (ch + 1 < g.c) {
+    float w = a.src[i + 1];
+    w += noise_of(key, g.level, g.grid, (int)cell, ch + 1, g.c, g.q);
+    a.dst[i + 1] = w;
+  }
+}
+
 // q = clamp(rint(x / Q) + N/2 - 1, 0, N - 1), ties to even, evaluated in
 // double so that the index never depends on the rounding of x / Q.
 __global__ void quantize_pack_kernel(const float* __restrict__ x, int64_t cells, int c, int bits,
@@ -197,6 +221,13 @@ inline int blocks_for(int64_t n, int per) { return (int)((n + per - 1) / per); }
 cudaError_t launch_adam(const AdamArgs& a, int64_t blocks, cudaStream_t s) {
   if (blocks == 0) return cudaSuccess;
   adam_kernel<<<(unsigned)blocks, kAdamBlock, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_noise_grids(const NoiseArgs& a, cudaStream_t s) {
+  const int64_t blocks = a.block_start[a.nseg];
+  if (blocks == 0) return cudaSuccess;
+  noise_grids_kernel<<<(unsigned)blocks, kNoiseBlock, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -353,13 +353,44 @@ int ntc_train_step(const ntc_material* m, const ntc_trainer* tr, const ntc_targe
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaMemsetAsync(loss_out, 0, sizeof(float), s);
   if (e != cudaSuccess) return cuda_status(e, "train_step memset");
+  // With the noisy scratch: one dense noise pass, and the fused step reads
+  // the noisy grids at the same offsets of the scratch.
+  ntc_material mt = *m;
+  if (b.noise && tr->noisy) {
+    CHECK_PTR(tr->noisy, "trainer noisy scratch");
+    ntc::NoiseArgs na{};
+    na.src = tr->params;
+    na.dst = tr->noisy;
+    na.seed = seed;
+    na.step = tr->step;
+    na.block_start[0] = 0;
+    for (int j = 0; j < m->levels; ++j)
+      for (int k = 0; k < 2; ++k) {
+        const ntc::AdamSeg& sg = a.seg[2 * j + k];
+        const int c = k ? m->c1 : m->c0;
+        ntc::NoiseSeg& g = na.seg[na.nseg];
+        g.off = sg.off;
+        g.c = c;
+        g.pairs = sg.len / c * ((c + 1) / 2);
+        g.level = j;
+        g.grid = k;
+        g.q = k ? m->q1 : m->q0;
+        na.block_start[na.nseg + 1] =
+            na.block_start[na.nseg] + (g.pairs + ntc::kNoiseBlock - 1) / ntc::kNoiseBlock;
+        ++na.nseg;
+        (k ? mt.lv[j].grid1 : mt.lv[j].grid0) = tr->noisy + sg.off;
+      }
+    e = ntc::launch_noise_grids(na, s);
+    if (e != cudaSuccess) return cuda_status(e, "train_step noise pass");
+    b.noise = 0;
+  }
   if (use_simt(m, flags)) {
     if (m->k_in > 64) return fail(NTC_ERR_UNSUPPORTED, "FP32 training supports k_in <= 64");
-    e = ntc::launch_backward_simt(*m, b, s);
+    e = ntc::launch_backward_simt(mt, b, s);
   } else {
     if (m->act != NTC_ACT_RELU)
       return fail(NTC_ERR_UNSUPPORTED, "tensor-core training supports ReLU (use NTC_FLAG_SIMT)");
-    e = ntc::launch_train_tc(*m, b, s);
+    e = ntc::launch_train_tc(mt, b, s);
   }
   if (e != cudaSuccess) return cuda_status(e, "train_step forward/backward");
   if (flags & NTC_FLAG_GRAD_ONLY) return NTC_OK;

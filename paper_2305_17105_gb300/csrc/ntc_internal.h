@@ -66,6 +66,25 @@ struct AdamArgs {
 constexpr int kAdamBlock = 256;
 constexpr int kAdamPerThread = 4;  // one float4 per thread
 cudaError_t launch_adam(const AdamArgs& a, int64_t blocks, cudaStream_t s);
+
+// Dense quantisation-noise pass of one step: dst = src + noise for every
+// value of every grid segment (offsets into params / the noisy scratch).
+struct NoiseSeg {
+  int64_t off, pairs;  // first value; channel pairs (cells * ceil(c / 2))
+  int c, level, grid;
+  float q;
+};
+struct NoiseArgs {
+  const float* src;
+  float* dst;
+  NoiseSeg seg[2 * NTC_MAX_LEVELS];
+  int64_t block_start[2 * NTC_MAX_LEVELS + 1];
+  int nseg;
+  uint64_t seed;
+  const int64_t* step;
+};
+constexpr int kNoiseBlock = 256;
+cudaError_t launch_noise_grids(const NoiseArgs& a, cudaStream_t s);
 cudaError_t launch_advance_step(int64_t* step, cudaStream_t s);
 
 cudaError_t launch_quantize_pack(const float* values, int64_t cells, int c, int bits, float q,

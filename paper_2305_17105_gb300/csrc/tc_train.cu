@@ -249,6 +249,35 @@ __device__ __forceinline__ void issue_mnmajor(uint32_t d, uint32_t a, uint32_t b
                 id, (s > 0) | acc0);
 }
 
+// Bilinear sample of one FP32 grid of 4k channels with 16-byte loads, all
+// taps' loads issued before the interpolation (same FMA order as
+// sample_grid, so the same values).
+__device__ __forceinline__ void sample_grid_f32x4(const ntc_material& M, int j, int k, int x, int y,
+                                                  int wm, int hm, GridSample& gs) {
+  const ntc_level& L = M.lv[j];
+  const int gw = k ? L.g1_w : L.g0_w, gh = k ? L.g1_h : L.g0_h;
+  const int c4 = (k ? M.c1 : M.c0) >> 2;
+  const Taps t = bilinear_taps(x, y, wm, hm, gw, gh);
+  const float4* g = static_cast<const float4*>(k ? L.grid1 : L.grid0);
+  float4 v[4][kMaxGridCh / 4];
+#pragma unroll
+  for (int tp = 0; tp < 4; ++tp)
+#pragma unroll
+    for (int q = 0; q < kMaxGridCh / 4; ++q)
+      v[tp][q] = q < c4 ? __ldg(g + (size_t)t.cell[tp] * c4 + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+  for (int ch = 0; ch < kMaxGridCh; ++ch) gs.acc[ch] = 0.f;
+#pragma unroll
+  for (int tp = 0; tp < 4; ++tp)
+#pragma unroll
+    for (int q = 0; q < kMaxGridCh / 4; ++q) {
+      gs.acc[4 * q] = fmaf(t.w[tp], v[tp][q].x, gs.acc[4 * q]);
+      gs.acc[4 * q + 1] = fmaf(t.w[tp], v[tp][q].y, gs.acc[4 * q + 1]);
+      gs.acc[4 * q + 2] = fmaf(t.w[tp], v[tp][q].z, gs.acc[4 * q + 2]);
+      gs.acc[4 * q + 3] = fmaf(t.w[tp], v[tp][q].w, gs.acc[4 * q + 3]);
+    }
+}
+
 __device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t& phase, int bar_id) {
   const bool ok = tc::mbar_wait(bar, phase, kWaitLimit);
   phase ^= 1;
@@ -316,8 +345,18 @@ __global__ void __launch_bounds__(kRows* kNWG, 1) train_tc_kernel(const ntc_mate
     float tgt[kN3];
     {
       const uint8_t* trow = A.target + A.tgt_off[m] + ((int64_t)y * tb->wm[m] + x) * C;
+      if ((C & 3) == 0) {
+        // whole 4-byte words of the u8 row (row offsets are multiples of 4)
 #pragma unroll
-      for (int c = 0; c < kN3; ++c) tgt[c] = (valid && c < C) ? (float)trow[c] * (1.f / 255.f) : 0.f;
+        for (int c4 = 0; c4 < kN3 / 4; ++c4) {
+          const uint32_t wv = (valid && 4 * c4 < C) ? __ldg(reinterpret_cast<const uint32_t*>(trow) + c4) : 0u;
+#pragma unroll
+          for (int b = 0; b < 4; ++b) tgt[4 * c4 + b] = (float)((wv >> (8 * b)) & 0xFFu) * (1.f / 255.f);
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < kN3; ++c) tgt[c] = (valid && c < C) ? (float)trow[c] * (1.f / 255.f) : 0.f;
+      }
     }
     uint8_t* X = W + P.X;
     {
@@ -326,7 +365,9 @@ __global__ void __launch_bounds__(kRows* kNWG, 1) train_tc_kernel(const ntc_mate
       GridSample gs;
 #pragma unroll
       for (int k = 0; k < 2; ++k) {
-        sample_grid(M, j, k, x, y, wm, hm, A.noise != 0 && valid, nkey, gs);
+        const int ck = k ? M.c1 : M.c0;
+        if (!A.noise && (ck & 3) == 0) sample_grid_f32x4(M, j, k, x, y, wm, hm, gs);
+        else sample_grid(M, j, k, x, y, wm, hm, A.noise != 0 && valid, nkey, gs);
         const int g0 = k ? P.f0 : 0, ng = k ? P.f1 : P.f0;
 #pragma unroll
         for (int g = 0; g < 2; ++g)

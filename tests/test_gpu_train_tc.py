@@ -107,3 +107,29 @@ def test_train_f16_reduces_loss_like_fp32():
     a, b = np.mean(curves[ntc.PREC_F32][-20:]), np.mean(curves[ntc.PREC_F16][-20:])
     assert a < 0.5 * np.mean(curves[ntc.PREC_F32][:5])
     assert abs(a - b) <= 0.1 * a, (a, b)
+
+
+@pytest.mark.parametrize("precision", [ntc.PREC_F32, ntc.PREC_F16])
+def test_dense_noise_pass_equals_noise_per_tap(precision):
+    """The step with the trainer's noisy scratch (one dense noise pass, then
+    gathers of noisy values) and without it (noise added per tap) see the
+    same noisy grids: equal loss and gradients up to the order of the
+    atomic sums."""
+    case = make_case(256, 128, 12, 12, 12, k_in=48, seed=73)
+    chain = gen.box_mip_chain_u8(gen.synthetic_texture(256, 128, 12, seed=1073))
+    target = ntc.Target(chain)
+    w = case.weights
+    grads, losses = [], []
+    for scratch in (True, False):
+        tr = ntc.Trainer(case.width, case.height, case.channels, case.c0, case.c1, case.bits0,
+                         case.bits1, case.q0, case.q1, case.val0, case.val1, [w[0], w[2], w[4]],
+                         [w[1], w[3], w[5]], case.k_in, precision, total_steps=50,
+                         noisy_scratch=scratch)
+        tr.step_t.fill_(5)
+        ntc.ntc_train_step(tr, target, 3 * 1024 + 5, 99, flags=ntc.FLAG_GRAD_ONLY)
+        torch.cuda.synchronize()
+        assert ntc.ntc_device_status() == ntc.OK
+        grads.append(to_np(tr.grad))
+        losses.append(tr.loss.item())
+    assert abs(losses[0] - losses[1]) <= 1e-6 * abs(losses[1])
+    assert rel_err(grads[0], grads[1]) < 1e-5
