@@ -66,15 +66,21 @@ def parse():
 # ----------------------------------------------------------------------------
 # distributed plumbing (replicas: no data-path collective)
 # ----------------------------------------------------------------------------
-def dist_init(args):
+def dist_init(args=None):
+    """One process per GPU (torchrun environment): NCCL with GPUs, gloo on a
+    CPU-only host.  Replicas only: the process group carries the barrier and
+    the max-over-ranks timing, never data-path traffic."""
     import torch
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl")
+        else:
+            dist.init_process_group("gloo")
     elif torch.cuda.is_available():
         torch.cuda.set_device(0)
     return rank, world
@@ -91,7 +97,8 @@ def max_over_ranks(x, world):
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -285,16 +292,23 @@ def render_eval(ntc, tr, target, chain, batch, seed, extra_steps, stream):
 # ----------------------------------------------------------------------------
 # CPU oracle baseline (bounded samples)
 # ----------------------------------------------------------------------------
-def oracle_decode_rate(grids_host, weights, queries, seconds):
-    """Decoded texels/s of the FP64 oracle on the host cores, on a prefix of
-    the decode workload sized to about `seconds` of work."""
+def oracle_decoder(grids_host, weights):
+    """The FP64 oracle's model of the decode material (4-bit grids)."""
     import oracle
     q = 1.0 / 16
     g0 = [oracle.dequantize(oracle.quantize(a.astype(np.float64), 16, q), 16, q)
           for a in grids_host[0]]
     g1 = [oracle.dequantize(oracle.quantize(a.astype(np.float64), 16, q), 16, q)
           for a in grids_host[1]]
-    md = oracle.Model(DEC_SIDE, DEC_SIDE, DEC_C, DEC_C0, DEC_C0, 16, 16, q, q, g0, g1, weights, DEC_K)
+    return oracle.Model(DEC_SIDE, DEC_SIDE, DEC_C, DEC_C0, DEC_C0, 16, 16, q, q, g0, g1, weights,
+                        DEC_K)
+
+
+def oracle_decode_rate(grids_host, weights, queries, seconds):
+    """Decoded texels/s of the FP64 oracle on the host cores, on a prefix of
+    the decode workload sized to about `seconds` of work."""
+    import oracle
+    md = oracle_decoder(grids_host, weights)
     threads = oracle.default_threads()
     n = 4096
     t0 = time.perf_counter()
@@ -343,11 +357,23 @@ def run_reference(args):
         g1.append(gen.uniform_grid_values((h1, w1, DEC_C0), lo, hi, rng))
     w = gen.random_mlp(DEC_K, 64, DEC_C, seed=2001, n_used=2 * DEC_C0 + 13)
     queries = gen.random_queries(args.queries, 13, seed=4001)
+    md = oracle_decoder((g0, g1), w)
+    threads = oracle.default_threads()
+    # one step = a bounded slice of the workload, sized so that the whole run
+    # takes about `budget` seconds of host time
+    budget = max(10.0, min(120.0, 15.0 * args.cpu_seconds))
+    t0 = time.perf_counter()
+    md.decode(queries[:4096], threads=threads)
+    rate0 = 4096 / max(time.perf_counter() - t0, 1e-6)
+    ns = int(min(len(queries), max(1024, rate0 * budget / (args.warmup + args.steps))))
     times, rates = [], []
     for i in range(args.warmup + args.steps):
-        rate, ns, threads, dt = oracle_decode_rate((g0, g1), w, queries, args.cpu_seconds / 4)
+        off = (i * ns) % max(1, len(queries) - ns + 1)
+        t0 = time.perf_counter()
+        md.decode(queries[off:off + ns], threads=threads)
+        dt = time.perf_counter() - t0
         if i >= args.warmup:
-            rates.append(rate)
+            rates.append(ns / dt)
             times.append(dt)
     value = statistics.median(rates)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "texels/s",
