@@ -477,7 +477,12 @@ def main():
                 "peak": peak, "unit": "TFLOP/s",
                 "peak_source": "measured bf16 burst" + (" x 2 (fp8 nominal ratio)" if precision == "f8" else "")}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    # DRAM bytes per launch of decode_ws_kernel from the committed ncu capture
+    # (profiles/decode_ws_f16_4096x16.md: 141.3 MB at 2^22 queries, scaled by
+    # the query count); null for another precision or query count
+    roof["traffic"] = (141.32e6 * args.queries / (1 << 22)
+                       if precision == "f16" and tuning and tuning["decode_warpgroups"] == 5 else None)
+    roof["traffic_unit"] = "bytes"
     dec_bytes = args.queries * (12 + DEC_C * 2)
     hbm = peaks.get("hbm_gbs", 6773.2)
     roof["hbm_gbs_algorithmic"] = dec_bytes / dec_avg_s / 1e9
@@ -555,7 +560,7 @@ def main():
         except Exception as e:  # reported, never fatal to the headline line
             render = {"error": f"{type(e).__name__}: {e}"[:300]}
 
-    kernels_per_step = 1 + 3  # decode; train: fused fwd/bwd, Adam, step counter
+    kernels_per_step = 1 + 4  # decode; train: noise pass, fused fwd/bwd, Adam, step counter
     line = {
         "metric": METRIC, "value": value, "unit": "texels/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
