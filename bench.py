@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--no-fp32-compare", action="store_true")
     ap.add_argument("--no-render", action="store_true",
                     help="skip the camera-frame decode of the trained model")
+    ap.add_argument("--no-multi", action="store_true",
+                    help="skip the 64-material batched decode and training graph")
     ap.add_argument("--render-steps", type=int, default=1000,
                     help="training steps added before the camera-frame decode")
     return ap.parse_args()
@@ -286,6 +288,111 @@ def render_eval(ntc, tr, target, chain, batch, seed, extra_steps, stream):
     dec = ntc.ntc_decode(m16, torch.from_numpy(t0).cuda())
     refm = torch.from_numpy(chain[0].reshape(-1, TRN_C).astype(np.float32) / 255.0).cuda()
     res["texture_psnr_mip0_db"] = psnr(dec, refm)
+    return res
+
+
+# ----------------------------------------------------------------------------
+# Many materials: batched decode launch, graph-captured training of all of them
+# ----------------------------------------------------------------------------
+def multi_material_eval(ntc, n_mat, q_per, train_batch, stream):
+    """The multi-material workload: n_mat square materials (side 2^k, k
+    uniform over 8..12; C uniform over {8, 12, 16}; G0 = side/4 and G1 =
+    side/8 with 12 channels each at 4 bits; random grids and MLPs), q_per
+    random queries each.  Decode: one persistent batched launch against one
+    launch per material.  Training: one step of train_batch texels for every
+    material (FP32 state, FP16 tensor-core step), captured once as a CUDA
+    graph and replayed."""
+    import torch
+    g = torch.Generator(device="cuda")
+    g.manual_seed(5005)
+    shapes = gen.material_set_shapes(n_mat, seed=5000)
+    q = 1.0 / 16
+    cb = ntc.cell_bytes(12, 4)
+    mats, uvls = [], []
+    for i, (side, c) in enumerate(shapes):
+        levels = ntc.ntc_pyramid(side, side)
+        g0 = [torch.randint(0, 256, (h0, w0, cb), dtype=torch.uint8, device="cuda", generator=g)
+              for (w0, h0), _ in levels]
+        g1 = [torch.randint(0, 256, (h1, w1, cb), dtype=torch.uint8, device="cuda", generator=g)
+              for _, (w1, h1) in levels]
+        w = gen.random_mlp(48, 64, c, seed=6000 + i, n_used=2 * 12 + 13)
+        wd = [torch.from_numpy(w[l]).cuda().half() for l in (0, 2, 4)]
+        bd = [torch.from_numpy(w[l]).cuda() for l in (1, 3, 5)]
+        mats.append(ntc.Material(side, side, c, 12, 12, 4, 4, q, q, g0, g1, wd, bd, 48, ntc.PREC_F16))
+        mips = ntc.mips_of(side, side)
+        uv = torch.rand((q_per, 2), generator=g, device="cuda")
+        lod = torch.randint(0, mips, (q_per, 1), generator=g, device="cuda").float()
+        uvls.append(torch.cat([uv, lod], 1).contiguous())
+    uvl = torch.cat(uvls)
+    res = {"workload": f"{n_mat} materials (sides 256-4096, C in {{8,12,16}}, G0 side/4 and G1 side/8 "
+                       f"x 12 ch at 4 bits), {q_per} random queries each; one training step of "
+                       f"{train_batch} texels per material",
+           "sides": [s for s, _ in shapes], "channels": [c for _, c in shapes]}
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    batch = ntc.Batch(mats, [q_per] * n_mat)
+    out = torch.empty(int(batch.desc.total_outputs), dtype=torch.float16, device="cuda")
+    ms_b = timed(lambda: ntc.ntc_decode_batched(batch, uvl, out=out))
+    outs = [torch.empty((q_per, m.channels), dtype=torch.float16, device="cuda") for m in mats]
+
+    def separate():
+        for m, u, o in zip(mats, uvls, outs):
+            ntc.ntc_decode(m, u, out=o)
+    ms_s = timed(separate)
+    res["decode_batched_ms"] = ms_b
+    res["decode_batched_texels_per_s"] = n_mat * q_per / (ms_b / 1e3)
+    res["decode_per_material_launches_ms"] = ms_s
+    res["decode_per_material_texels_per_s"] = n_mat * q_per / (ms_s / 1e3)
+    del out, outs, uvl, uvls, batch
+
+    trainers, targets = [], []
+    lo, hi = -(16 - 1) / 2 * q, 16 / 2 * q
+    for i, (side, c) in enumerate(shapes):
+        levels = ntc.ntc_pyramid(side, side)
+        z0 = [np.zeros((h0, w0, 12), np.float32) for (w0, h0), _ in levels]
+        z1 = [np.zeros((h1, w1, 12), np.float32) for _, (w1, h1) in levels]
+        w = gen.random_mlp(48, 64, c, seed=6000 + i, n_used=2 * 12 + 13)
+        tr = ntc.Trainer(side, side, c, 12, 12, 4, 4, q, q, z0, z1, [w[0], w[2], w[4]],
+                         [w[1], w[3], w[5]], 48, ntc.PREC_F16, total_steps=1000)
+        for t in tr.material.grids0 + tr.material.grids1:
+            t.uniform_(lo, hi, generator=g)
+        tg = ntc.Target.__new__(ntc.Target)
+        offs, n = [], 0
+        for m in range(ntc.mips_of(side, side)):
+            offs.append(n)
+            n += (max(1, side >> m) ** 2 * c + 15) // 16 * 16
+        tg.texels = torch.randint(0, 256, (n,), dtype=torch.uint8, device="cuda", generator=g)
+        tg.offsets = offs
+        trainers.append(tr)
+        targets.append(tg)
+
+    def step_all():
+        for tr, tg in zip(trainers, targets):
+            ntc.ntc_train_step(tr, tg, train_batch, 55)
+    step_all()  # warm-up outside the capture
+    torch.cuda.synchronize()
+    side_stream = torch.cuda.Stream()
+    side_stream.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side_stream):
+        with torch.cuda.graph(graph, stream=side_stream):
+            step_all()
+    torch.cuda.current_stream().wait_stream(side_stream)
+    ms_t = timed(graph.replay, reps=5)
+    res["train_graph_step_ms"] = ms_t
+    res["train_samples_per_s"] = n_mat * train_batch / (ms_t / 1e3)
+    res["train_kernels_per_graph"] = 5 * n_mat
+    res["status"] = ntc.ntc_device_status()
     return res
 
 
@@ -560,6 +667,13 @@ def main():
         except Exception as e:  # reported, never fatal to the headline line
             render = {"error": f"{type(e).__name__}: {e}"[:300]}
 
+    multi = None
+    if not args.no_multi:
+        try:
+            multi = multi_material_eval(ntc, 64, 1 << 20, 1 << 16, stream)
+        except Exception as e:  # reported, never fatal to the headline line
+            multi = {"error": f"{type(e).__name__}: {e}"[:300]}
+
     kernels_per_step = 1 + 4  # decode; train: noise pass, fused fwd/bwd, Adam, step counter
     line = {
         "metric": METRIC, "value": value, "unit": "texels/s", "n_gpus": world,
@@ -576,7 +690,7 @@ def main():
         "train_samples_per_s": train_rate, "train_loss": loss,
         "decode_ms": statistics.median(dec_ms), "train_ms": statistics.median(trn_ms),
         "roofline": roof, "tuning": tuning, "e2e": e2e, "fp32_path": fp32, "cpu_baseline": cpu,
-        "render": render,
+        "render": render, "multi_material": multi,
         "gpu_launches": kernels_per_step * args.steps,
         "clocks": clk.summary(), "wall_s": t_wall,
     }

@@ -253,8 +253,8 @@ typedef struct {
   int64_t total_queries;   /* rows of the concatenated uvl array */
   int64_t total_outputs;   /* elements of the concatenated output: sum of n_i * channels_i */
   int64_t total_tiles;
-  int32_t wg_smem;         /* internal launch parameters */
-  int32_t fast;
+  int32_t wg_smem;         /* internal: shared-memory bytes of one material's plan */
+  int32_t fast;            /* internal: input-layout class of the batch */
 } ntc_batch;
 
 #define NTC_MAX_BATCH 1024
@@ -263,7 +263,7 @@ typedef struct {
 size_t ntc_batch_workspace_bytes(void);
 
 /* Prepare a batch decode of n_materials materials (HOST array `mats`, all
- * NTC_PREC_F16, of one grid layout class) with n_queries[i] (HOST) queries
+ * NTC_PREC_F16) with n_queries[i] (HOST) queries
  * each: validates every material, lays the materials' queries out back to
  * back (material i's rows start at sum_{j<i} n_queries[j] of the uvl array
  * and its outputs at sum_{j<i} n_queries[j] * channels_j of the output

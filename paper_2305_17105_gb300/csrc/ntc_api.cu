@@ -416,8 +416,9 @@ int ntc_batch_prepare(const ntc_material* mats, const int64_t* n_queries, int32_
   ntc::BatchHeader& B = host[0];
   memset(&B, 0, sizeof(B));
   const int per_tile = filter == NTC_FILTER_TRILINEAR ? 16 : 128;
-  uint32_t wg_smem = 0;
-  int fast = 1;  // the fast input layout when every material allows it, else the generic one
+  uint32_t plan_bytes = 0;
+  // input-layout class: one fast class for all, -1 fast with mixed classes, 0 generic
+  int cls = -2;
   for (int i = 0; i < n_materials; ++i) {
     const ntc_material* m = &mats[i];
     int st = check_material(m, false);
@@ -429,17 +430,19 @@ int ntc_batch_prepare(const ntc_material* mats, const int64_t* n_queries, int32_
     if (m->precision != NTC_PREC_F16)
       return fail(NTC_ERR_UNSUPPORTED, "batch material %d: batches decode FP16 materials", i);
     if (n_queries[i] < 0) return fail(NTC_ERR_ARG, "batch material %d: negative query count", i);
-    if (!ntc::batched_fast(*m)) fast = 0;
+    const int c = ntc::fast_class(*m);
+    cls = cls == -2 ? c : (cls == c ? cls : (cls != 0 && c != 0 ? -1 : 0));
     B.mats[i] = *m;
     B.tile_start[i + 1] = B.tile_start[i] + (n_queries[i] + per_tile - 1) / per_tile;
     B.q_off[i + 1] = B.q_off[i] + n_queries[i];
     B.o_off[i + 1] = B.o_off[i] + n_queries[i] * m->channels;
   }
   for (int i = 0; i < n_materials; ++i) {
-    const uint32_t need = ntc::batched_wg_smem(mats[i], fast != 0);
-    wg_smem = need > wg_smem ? need : wg_smem;
+    const uint32_t need = ntc::ws_plan_bytes(mats[i], cls != 0);
+    plan_bytes = need > plan_bytes ? need : plan_bytes;
   }
-  if ((size_t)wg_smem * 4 > 227 * 1024) return fail(NTC_ERR_UNSUPPORTED, "batch: shared memory");
+  if (ntc::ws_batched_smem(plan_bytes) > 227 * 1024)
+    return fail(NTC_ERR_UNSUPPORTED, "batch: shared memory");
   B.n_materials = n_materials;
   B.total_tiles = B.tile_start[n_materials];
   cudaError_t e = cudaMemcpyAsync(workspace, &B, sizeof(B), cudaMemcpyHostToDevice,
@@ -451,8 +454,8 @@ int ntc_batch_prepare(const ntc_material* mats, const int64_t* n_queries, int32_
   batch_out->total_queries = B.q_off[n_materials];
   batch_out->total_outputs = B.o_off[n_materials];
   batch_out->total_tiles = B.total_tiles;
-  batch_out->wg_smem = (int32_t)wg_smem;
-  batch_out->fast = fast;
+  batch_out->wg_smem = (int32_t)plan_bytes;
+  batch_out->fast = cls;
   return NTC_OK;
 }
 
@@ -463,11 +466,11 @@ int ntc_decode_batched(const ntc_batch* batch, const float* uvl, void* out, int3
   if (batch->total_queries == 0) return NTC_OK;
   CHECK_PTR(uvl, "uvl");
   CHECK_PTR(out, "out");
-  return cuda_status(ntc::launch_decode_batched(static_cast<const ntc::BatchHeader*>(batch->workspace),
-                                                batch->total_tiles, (uint32_t)batch->wg_smem,
-                                                batch->fast != 0, uvl, out, out_dtype, batch->filter,
-                                                static_cast<cudaStream_t>(stream)),
-                     "decode_batched");
+  return cuda_status(
+      ntc::launch_decode_ws_batched(static_cast<const ntc::BatchHeader*>(batch->workspace),
+                                    batch->total_tiles, (uint32_t)batch->wg_smem, batch->fast, uvl,
+                                    out, out_dtype, batch->filter, static_cast<cudaStream_t>(stream)),
+      "decode_batched");
 }
 
 int ntc_quantize_pack(const float* values, int64_t cells, int32_t c, int32_t bits, float q,

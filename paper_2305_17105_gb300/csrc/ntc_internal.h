@@ -107,15 +107,22 @@ struct BatchHeader {
   int64_t o_off[kMaxBatch + 1];       // output element offsets
   ntc_material mats[kMaxBatch];
 };
-uint32_t batched_wg_smem(const ntc_material& m, bool fast);
-bool batched_fast(const ntc_material& m);
+// Input-layout class of a material for the warp-specialised kernels: 0
+// generic, 1..9 fast 4-bit layout (1 + 3 k0 + k1 by grid class).
+int fast_class(const ntc_material& m);
+// Shared-memory plan bytes of one material, and the batched kernel's total.
+uint32_t ws_plan_bytes(const ntc_material& m, bool fast);
+uint32_t ws_batched_smem(uint32_t plan_bytes);
+// Many materials in one warp-specialised launch; cls: 0 generic, 1..9 one
+// fast class for every material, -1 fast with per-material classes.
+cudaError_t launch_decode_ws_batched(const BatchHeader* dev, int64_t total_tiles,
+                                     uint32_t plan_bytes, int cls, const float* uvl, void* out,
+                                     int out_dtype, int filter, cudaStream_t s);
 bool fast_layout_ok(const ntc_material& m);
 // Warp-specialised tensor-core decode (FP16), fast 4-bit layout or generic.
 cudaError_t launch_decode_ws(const ntc_material& m, const float* uvl, int64_t n, void* out,
                              int out_dtype, int filter, cudaStream_t s, bool fast);
-cudaError_t launch_decode_batched(const BatchHeader* dev, int64_t total_tiles, uint32_t wg_smem,
-                                  bool fast, const float* uvl, void* out, int out_dtype, int filter,
-                                  cudaStream_t s);
+
 
 int sm_count();
 

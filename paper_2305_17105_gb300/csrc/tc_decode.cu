@@ -241,171 +241,6 @@ cudaError_t launch_shape(const ntc_material& m, const float* uvl, int64_t n, voi
   }
 }
 
-// ---------------------------------------------------------------------------
-// Many materials in one persistent launch (FP16).  The batch descriptor in
-// device memory lists the materials, the prefix sums of their tiles and the
-// offsets of their queries and outputs; tiles are ordered by material.  Each
-// warpgroup takes a contiguous range of tiles and keeps a private copy of the
-// current material's weights and tables in shared memory, restaged when its
-// range crosses into the next material.
-// ---------------------------------------------------------------------------
-template <bool FAST>
-__global__ void __launch_bounds__(kRows * 4, 1) decode_batched_kernel(
-    const BatchHeader* __restrict__ B, const float* __restrict__ uvl, void* __restrict__ out,
-    int out_dtype, int filter, uint32_t wg_smem, int* status) {
-  constexpr int kNWG = 4;
-  extern __shared__ __align__(1024) uint8_t smem_raw[];
-  __shared__ uint64_t mbar[kNWG];
-  __shared__ uint32_t tmem_base;
-  __shared__ int wg_abort[kNWG];
-  __shared__ ntc_material mat_s[kNWG];
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const int wg = tid / kRows, row = tid % kRows;
-  const int bar_id = 1 + wg;
-  if (warp == 0) {
-    tc::tmem_alloc(&tmem_base, 512);
-    tc::tmem_relinquish();
-  }
-  if (tid < kNWG) {
-    tc::mbar_init(&mbar[tid], 1);
-    wg_abort[tid] = 0;
-  }
-  tc::fence_mbar_init();
-  tc::fence_before_sync();
-  __syncthreads();
-  tc::fence_after_sync();
-  const uint32_t tw = tmem_base + 128u * wg;
-  const uint32_t lane = (uint32_t)((warp & 3) * 32) << 16;
-  const uint32_t td = tw + lane, th = tw + kColH + lane, tx = tw + kColX + lane;
-  uint64_t* bar = &mbar[wg];
-  volatile int* abort_flag = &wg_abort[wg];
-  tc::tmem_st4(tw + kColCst + lane, make_uint4(tc::pack_f16x2(1.f, 1.f), 0, 0, 0));
-  tc::tmem_st4(tw + kColCst + 4 + lane, make_uint4(0, 0, 0, 0));
-  uint8_t* sm = smem_raw + (size_t)wg * wg_smem;
-  constexpr uint32_t id64 = tc::idesc(kRows, kHidden), id16 = tc::idesc(kRows, kN3);
-  const bool tri = filter == NTC_FILTER_TRILINEAR;
-  const int per_tile = tri ? kRows / 8 : kRows;
-  const int nm = B->n_materials;
-  const int64_t total = B->total_tiles;
-  const int64_t nwgs = (int64_t)gridDim.x * kNWG, gwg = (int64_t)blockIdx.x * kNWG + wg;
-  const int64_t t_begin = total * gwg / nwgs, t_end = total * (gwg + 1) / nwgs;
-  uint32_t phase = 0;
-  int cur = -1;
-  bool aborted = false;
-  const float dummy_scale[3] = {1.f, 1.f, 1.f};
-  (void)dummy_scale;
-
-  for (int64_t tl = t_begin; tl < t_end; ++tl) {
-    // material of this tile (tiles are ordered by material)
-    int mid = cur < 0 ? 0 : cur;
-    while (mid + 1 < nm && tl >= B->tile_start[mid + 1]) ++mid;
-    if (mid != cur) {
-      tc::bar_sync(bar_id, kRows);  // every row is done with the previous material
-      if (row == 0) mat_s[wg] = B->mats[mid];
-      tc::bar_sync(bar_id, kRows);
-      const ntc_material& Mn = mat_s[wg];
-      const Plan Pn(Mn.c0, Mn.c1, Mn.bits0, Mn.bits1, Mn.encoding == NTC_GRID_PACKED, false, FAST);
-      stage_shared<false>(Mn, Pn, sm, row, kRows);
-      zero_tail_groups<false>(Pn, TmemRow{tx});
-      tc::tmem_st_wait();
-      tc::fence_proxy_async();
-      tc::bar_sync(bar_id, kRows);
-      cur = mid;
-    }
-    const ntc_material& M = mat_s[wg];
-    const Plan P(M.c0, M.c1, M.bits0, M.bits1, M.encoding == NTC_GRID_PACKED, false, FAST);
-    const MipTab* tb = reinterpret_cast<const MipTab*>(sm + P.tab);
-    const uint64_t* dsc = reinterpret_cast<const uint64_t*>(sm + P.desc);
-    const int64_t local = tl - B->tile_start[mid];
-    const int64_t nq = B->q_off[mid + 1] - B->q_off[mid];
-    const int64_t ql = tri ? local * per_tile + (row >> 3) : local * per_tile + row;
-    const bool valid = ql < nq;
-    const int64_t qg = B->q_off[mid] + ql;
-    Row r;
-    locate(M, tb, load_query(uvl, qg, valid), tri, row, r);
-    if (FAST) {
-      gather_fast(P, tb, r);
-      build_fast(P, P, FastK(M), sm, r, TmemRow{tx});
-    } else {
-      build_generic<false>(M, P, sm, r, TmemRow{tx}, 1.f);
-    }
-    tc::tmem_st_wait();
-    tc::fence_before_sync();
-    tc::bar_sync(bar_id, kRows);
-
-    if (row == 0)
-      issue_layer<false>(tw, tw + kColX, dsc, P.k_int / 16, id64, false, 0, bar);
-    if (!tc::mbar_wait(bar, phase, kWaitLimit)) *abort_flag = 1;
-    phase ^= 1;
-    tc::fence_after_sync();
-    hidden_epilogue<false>(td, th, M.act, nullptr, 1.f, 1.f);
-    tc::tmem_st_wait();
-    tc::fence_before_sync();
-    tc::bar_sync(bar_id, kRows);
-    if (row == 32)
-      issue_layer<false>(tw, tw + kColH, dsc + 4, 4, id64, true, tw + kColCst, bar);
-    if (!tc::mbar_wait(bar, phase, kWaitLimit)) *abort_flag = 1;
-    phase ^= 1;
-    tc::fence_after_sync();
-    hidden_epilogue<false>(td, th, M.act, nullptr, 1.f, 1.f);
-    tc::tmem_st_wait();
-    tc::fence_before_sync();
-    tc::bar_sync(bar_id, kRows);
-    if (*abort_flag) { aborted = true; break; }
-    if (row == 64)
-      issue_layer<false>(tw, tw + kColH, dsc + 9, 4, id16, true, tw + kColCst, bar);
-    if (!tc::mbar_wait(bar, phase, kWaitLimit)) *abort_flag = 1;
-    phase ^= 1;
-    tc::fence_after_sync();
-    float yv[16];
-    tc::tmem_ld16(td, yv);
-    tc::tmem_ld_wait();
-    tc::fence_before_sync();
-#pragma unroll
-    for (int c = 0; c < 16; ++c)
-      yv[c] = M.out_act == NTC_OUT_IDENTITY ? yv[c] : fmaf(0.5f, tc::tanh_fast(yv[c]), 0.5f);
-    if (tri) {
-#pragma unroll
-      for (int c = 0; c < 16; ++c) {
-        float s = yv[c] * r.wtap;
-        s += __shfl_xor_sync(0xffffffffu, s, 1);
-        s += __shfl_xor_sync(0xffffffffu, s, 2);
-        s += __shfl_xor_sync(0xffffffffu, s, 4);
-        yv[c] = s;
-      }
-    }
-    const int C = M.channels;
-    if (valid && (!tri || (row & 7) == 0)) {
-      const int64_t o = B->o_off[mid] + ql * C;
-      if (out_dtype == NTC_DTYPE_F16) {
-        __half* op = static_cast<__half*>(out) + o;
-#pragma unroll
-        for (int c = 0; c < 16; ++c)
-          if (c < C) op[c] = __float2half_rn(yv[c]);
-      } else {
-        float* op = static_cast<float*>(out) + o;
-#pragma unroll
-        for (int c = 0; c < 16; ++c)
-          if (c < C) op[c] = yv[c];
-      }
-    }
-    tc::bar_sync(bar_id, kRows);
-    if (*abort_flag) { aborted = true; break; }
-  }
-
-  tc::fence_before_sync();
-  __syncthreads();
-  if (tid == 0) {
-    int any = aborted ? 1 : 0;
-    for (int w = 0; w < kNWG; ++w) any |= wg_abort[w];
-    if (any) atomicExch(status, NTC_ERR_TIMEOUT);
-  }
-  if (warp == 0) {
-    tc::fence_after_sync();
-    tc::tmem_dealloc(tmem_base, 512);
-  }
-}
-
 }  // namespace
 
 // The fast layout's exactness conditions: every grid/mip size ratio of every
@@ -442,35 +277,6 @@ cudaError_t launch_decode_tc(const ntc_material& m, const float* uvl, int64_t n,
   if (nwg == 5) return launch_decode_ws(m, uvl, n, out, out_dtype, filter, s, P.fast != 0);
   if (P.fast) return launch_shape<false, true>(m, uvl, n, out, out_dtype, filter, s, nwg);
   return launch_shape<false, false>(m, uvl, n, out, out_dtype, filter, s, nwg);
-}
-
-uint32_t batched_wg_smem(const ntc_material& m, bool fast) {
-  const Plan P(m.c0, m.c1, m.bits0, m.bits1, m.encoding == NTC_GRID_PACKED, false, fast);
-  return (P.total + 127) / 128 * 128;
-}
-bool batched_fast(const ntc_material& m) {
-  return Plan(m.c0, m.c1, m.bits0, m.bits1, m.encoding == NTC_GRID_PACKED, false,
-              fast_layout_ok(m)).fast != 0;
-}
-
-cudaError_t launch_decode_batched(const BatchHeader* dev, int64_t total_tiles, uint32_t wg_smem,
-                                  bool fast, const float* uvl, void* out, int out_dtype, int filter,
-                                  cudaStream_t s) {
-  if (total_tiles == 0) return cudaSuccess;
-  const size_t smem = (size_t)wg_smem * 4;
-  const void* fn = fast ? (const void*)decode_batched_kernel<true> : (const void*)decode_batched_kernel<false>;
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  const int64_t cap = sm_count();
-  const int64_t ctas = (total_tiles + 3) / 4;
-  const int grid = (int)(ctas < cap ? ctas : cap);
-  if (fast)
-    decode_batched_kernel<true><<<grid, kRows * 4, smem, s>>>(dev, uvl, out, out_dtype, filter, wg_smem,
-                                                              status_word());
-  else
-    decode_batched_kernel<false><<<grid, kRows * 4, smem, s>>>(dev, uvl, out, out_dtype, filter, wg_smem,
-                                                               status_word());
-  return cudaGetLastError();
 }
 
 }  // namespace ntc

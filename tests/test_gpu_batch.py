@@ -140,3 +140,25 @@ def test_multi_material_training_loop_in_cuda_graph():
         assert int(a.step_t.item()) == int(b.step_t.item()) == 4
         assert abs(a.loss.item() - b.loss.item()) <= 1e-4 * a.loss.item()
         assert rel_err(to_np(b.params), to_np(a.params)) < 1e-3
+
+
+def test_batched_decode_mixed_fast_classes_and_channels():
+    """Materials whose 4-bit cell layouts differ (fast classes decided per
+    material inside the launch), odd channel counts and output blocks that
+    are not 8-element aligned."""
+    specs = [(128, 3, 8, 8), (256, 16, 12, 12), (64, 5, 16, 16), (128, 7, 8, 16), (256, 12, 13, 10)]
+    mats, qs = [], []
+    for i, (side, c, c0, c1) in enumerate(specs):
+        case = make_case(side, side, c, c0, c1, k_in=48, seed=200 + i)
+        mats.append(device_material(case, precision=ntc.PREC_F16))
+        qs.append(gen.random_queries(131 * (i + 1) + 3, oracle.mips(side, side), seed=4200 + i))
+    batch = ntc.Batch([m for m, _ in mats], [len(q) for q in qs])
+    for filt in (ntc.FILTER_NEAREST, ntc.FILTER_TRILINEAR):
+        if filt == ntc.FILTER_TRILINEAR:
+            batch = ntc.Batch([m for m, _ in mats], [len(q) for q in qs], filter=filt)
+        out = to_np(ntc.ntc_decode_batched(batch, _uvl(np.concatenate(qs))))
+        assert ntc.ntc_device_status() == ntc.OK
+        for i, ((m, md), q) in enumerate(zip(mats, qs)):
+            got = out[batch.o_offsets[i]:batch.o_offsets[i + 1]].reshape(len(q), m.channels)
+            ref = md.decode_trilinear(q) if filt == ntc.FILTER_TRILINEAR else md.decode(q)
+            assert np.abs(got - ref).max() <= OUT_TOL, (filt, i)
