@@ -365,14 +365,14 @@ def ntc_decode_batched(batch: Batch, uvl, out_dtype=torch.float32, out=None, str
 # ----------------------------------------------------------------------------
 # training state
 # ----------------------------------------------------------------------------
-def _align4(n: int) -> int:
-    return (n + 3) // 4 * 4
+def _align8(n: int) -> int:
+    return (n + 7) // 8 * 8
 
 
 class Trainer:
     """FP32 master parameters + Adam state of one material in one flat
     device array (grids level by level, then W1, b1, W2, b2, W3, b3; every
-    tensor 16-byte aligned), driven by ``ntc_train_step``."""
+    tensor 32-byte aligned), driven by ``ntc_train_step``."""
 
     def __init__(self, width, height, channels, c0, c1, bits0, bits1, q0, q1, grids0, grids1,
                  weights, biases, k_in, precision=PREC_F32, act=ACT_RELU, out_act=OUT_SIGMOID,
@@ -387,7 +387,7 @@ class Trainer:
         offs, n = [], 0
         for t in tensors:
             offs.append(n)
-            n += _align4(t.size)
+            n += _align8(t.size)
         flat = np.zeros(n, np.float32)
         for o, t in zip(offs, tensors):
             flat[o:o + t.size] = t.reshape(-1)

@@ -249,6 +249,13 @@ __device__ __forceinline__ void issue_mnmajor(uint32_t d, uint32_t a, uint32_t b
                 id, (s > 0) | acc0);
 }
 
+// 32-byte read-only global load (sm_100+), 32-byte aligned address.
+__device__ __forceinline__ void ld_nc_v8(const float* p, float4& a, float4& b) {
+  asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
+      : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+      : "l"(p));
+}
+
 // Bilinear sample of one FP32 grid of 4k channels with 16-byte loads, all
 // taps' loads issued before the interpolation (same FMA order as
 // sample_grid, so the same values).
@@ -260,11 +267,23 @@ __device__ __forceinline__ void sample_grid_f32x4(const ntc_material& M, int j, 
   const Taps t = bilinear_taps(x, y, wm, hm, gw, gh);
   const float4* g = static_cast<const float4*>(k ? L.grid1 : L.grid0);
   float4 v[4][kMaxGridCh / 4];
+  if ((c4 == 2 || c4 == 4) && (reinterpret_cast<uintptr_t>(g) & 31) == 0) {
+    // 32-byte loads: one L1 wavefront brings 8 channels
 #pragma unroll
-  for (int tp = 0; tp < 4; ++tp)
+    for (int tp = 0; tp < 4; ++tp)
 #pragma unroll
-    for (int q = 0; q < kMaxGridCh / 4; ++q)
-      v[tp][q] = q < c4 ? __ldg(g + (size_t)t.cell[tp] * c4 + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int h = 0; h < 2; ++h) {
+        if (2 * h < c4) ld_nc_v8(reinterpret_cast<const float*>(g + (size_t)t.cell[tp] * c4 + 2 * h),
+                                 v[tp][2 * h], v[tp][2 * h + 1]);
+        else v[tp][2 * h] = v[tp][2 * h + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+  } else {
+#pragma unroll
+    for (int tp = 0; tp < 4; ++tp)
+#pragma unroll
+      for (int q = 0; q < kMaxGridCh / 4; ++q)
+        v[tp][q] = q < c4 ? __ldg(g + (size_t)t.cell[tp] * c4 + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
 #pragma unroll
   for (int ch = 0; ch < kMaxGridCh; ++ch) gs.acc[ch] = 0.f;
 #pragma unroll
