@@ -281,6 +281,24 @@ def render_eval(ntc, tr, target, chain, batch, seed, extra_steps, stream):
         return float("inf") if mse == 0 else 10 * math.log10(1.0 / mse)
 
     res["psnr_vs_f32_form_db"] = {k: psnr(frames[k], frames["f32"]) for k in ("f16", "f8")}
+    # stochastic filtering (Sec. 5.3): one jittered nearest decode per pixel
+    o = torch.empty((q.shape[0], TRN_C), dtype=torch.float32, device="cuda")
+    ms = {"s": 0.0}
+
+    def stoch(frame=[0]):
+        frame[0] += 1
+        ntc.ntc_decode(m16, uvl, out=o, filter=ntc.FILTER_STOCHASTIC, noise_seed=9,
+                       noise_step=frame[0])
+    stoch()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(5):
+        stoch()
+    b.record(stream)
+    torch.cuda.synchronize()
+    res["frame_ms_stochastic_f16"] = a.elapsed_time(b) / 5
+    res["psnr_stochastic_frame_vs_trilinear_db"] = psnr(o, frames["f16"])
     # texture quality: every texel of mip 0 against the 8-bit reference
     ys, xs = np.meshgrid(np.arange(TRN_SIDE), np.arange(TRN_SIDE), indexing="ij")
     t0 = np.stack([(xs + 0.5) / TRN_SIDE, (ys + 0.5) / TRN_SIDE, np.zeros_like(xs, float)],

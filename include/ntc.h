@@ -66,7 +66,12 @@ enum {
 };
 enum { NTC_ACT_RELU = 0, NTC_ACT_HARDGELU = 1 };   /* hidden activation (Sec. 4.4) */
 enum { NTC_OUT_SIGMOID = 0, NTC_OUT_IDENTITY = 1 }; /* output activation */
-enum { NTC_FILTER_NEAREST = 0, NTC_FILTER_TRILINEAR = 1 }; /* Sec. 5.3 */
+/* Sec. 5.3: nearest texel of (u, v) at mip floor(lod); trilinear (8 texels
+ * decoded and blended); stochastic: one decode at the nearest texel of the
+ * jittered position u w_m - 1/2 + xi_x (same for v) on mip floor(lod + xi_l),
+ * xi uniform in [0, 1) from a counter hash of (noise_seed, noise_step, query
+ * index), which equals trilinear filtering in expectation. */
+enum { NTC_FILTER_NEAREST = 0, NTC_FILTER_TRILINEAR = 1, NTC_FILTER_STOCHASTIC = 2 };
 enum { NTC_DTYPE_F32 = 0, NTC_DTYPE_F16 = 1 };              /* output element type */
 
 /* Flags of ntc_decode / ntc_backward / ntc_train_step. */

@@ -28,8 +28,10 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
             os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "ntc_oracle.h"))):
         tmp = _LIB + ".tmp.%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC,
-                               "-lm", "-lpthread"])
+        # no FMA contraction: FP32 decisions (stochastic texel choice) are
+        # evaluated one operation at a time, as written
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
+                               "-o", tmp, _SRC, "-lm", "-lpthread"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -91,6 +93,7 @@ def _declare(L):
         "or_decode_xym": (None, [P, I64, P, P, P, I]),
         "or_decode_uvl": (None, [P, I64, P, P, P, I]),
         "or_decode_trilinear": (None, [P, I64, P, P, I]),
+        "or_decode_stochastic": (None, [P, I64, P, C.c_uint64, I64, P, I]),
         "or_backward_xym": (None, [P, I64, P, P, P, P, I]),
         "or_loss_grad_xym": (D, [P, I64, P, P, P, P, I]),
         "or_cosine_lr": (D, [D, I64, I64]),
@@ -279,6 +282,15 @@ class Model:
         out = np.empty((uvl.shape[0], self.channels), np.float64)
         lib().or_decode_trilinear(C.byref(self._s), uvl.shape[0], _p(uvl), _p(out),
                                   threads or default_threads())
+        return out
+
+    def decode_stochastic(self, uvl, seed, step, threads=None):
+        """Stochastic filtering (Sec. 5.3) of frame `step`: one jittered nearest
+        decode per query."""
+        uvl = np.ascontiguousarray(uvl, np.float32).reshape(-1, 3)
+        out = np.empty((uvl.shape[0], self.channels), np.float64)
+        lib().or_decode_stochastic(C.byref(self._s), uvl.shape[0], _p(uvl), seed, step, _p(out),
+                                   threads or default_threads())
         return out
 
     def zero_grads(self):

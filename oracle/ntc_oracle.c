@@ -345,6 +345,8 @@ typedef struct job_s {
   double* out;
   or_grads g;       /* this thread's private accumulators */
   double loss;
+  uint64_t seed;    /* stochastic filtering: seed and frame of the jitter */
+  int64_t step;
   int64_t lo, hi;
 } job;
 
@@ -473,6 +475,70 @@ void or_decode_trilinear(const or_model* md, int64_t n, const float* uvl, double
   job* jobs = calloc((size_t)nthreads, sizeof(job));
   for (int t = 0; t < nthreads; ++t) {
     jobs[t].fn = decode_tri_job; jobs[t].md = md; jobs[t].uvl = uvl; jobs[t].out = out;
+  }
+  run_jobs(jobs, nthreads, n);
+  free(jobs);
+}
+
+
+/* Stochastic filtering (Sec. 5.3): add noise to the texel position and the
+ * LOD, then take the nearest texel -- one decode per query, equal to the
+ * trilinear filter above in expectation.  Reading of the noise: per query q
+ * of frame `step` one 64-bit draw h on stream 4*step + 2 (counter q); xi_x
+ * = h bits 40..63, xi_y = bits 16..39 as 24-bit fractions, xi_l = bits 0..15
+ * as a 16-bit fraction, all uniform in [0, 1).  The texel is the nearest one
+ * of the jittered position u*w_m - 1/2 + xi_x (x0 with probability 1 - f,
+ * x0 + 1 with probability f: the bilinear weights), wrapped like the
+ * trilinear taps; the mip floor(lod + xi_l) (the linear weights across
+ * mips).  The texel choice is an integer decided in FP32, the kernels'
+ * precision: each step below is one FP32 operation (this file is compiled
+ * without FMA contraction); u is taken as 0 when NaN and clamped to
+ * [-16384, 16384]. */
+static int stoch_mip(float lod, int mips, uint64_t h) {
+  float xl = (float)(uint32_t)(h & 0xFFFFu) * (1.0f / 65536.0f);
+  float l = !(lod >= 0.0f) ? 0.0f : (lod > (float)(mips - 1) ? (float)(mips - 1) : lod);
+  float s = l + xl;
+  int m = (int)floorf(s);
+  return m < mips - 1 ? m : mips - 1;
+}
+
+static int stoch_coord(float u, int w, uint32_t b24) {
+  float xi = (float)b24 * (1.0f / 16777216.0f);
+  float uc = (u == u) ? u : 0.0f;
+  if (uc < -16384.0f) uc = -16384.0f;
+  if (uc > 16384.0f) uc = 16384.0f;
+  float p = uc * (float)w;
+  p = p - 0.5f;
+  p = p + xi;
+  int i = (int)floorf(p);
+  return ((i % w) + w) % w;
+}
+
+static void decode_stoch_job(job* jb, int64_t lo, int64_t hi) {
+  const or_model* md = jb->md;
+  mlp_buf b;
+  mlp_alloc(md, &b);
+  int C = md->channels;
+  for (int64_t i = lo; i < hi; ++i) {
+    float u = jb->uvl[3 * i], v = jb->uvl[3 * i + 1], lod = jb->uvl[3 * i + 2];
+    uint64_t h = or_rng(jb->seed, ((uint64_t)jb->step << 2) | 2u, (uint64_t)i);
+    int m = stoch_mip(lod, md->mips, h);
+    int x = stoch_coord(u, mip_w(md, m), (uint32_t)(h >> 40));
+    int y = stoch_coord(v, mip_h(md, m), (uint32_t)((h >> 16) & 0xFFFFFFu));
+    or_features(md, x, y, m, NULL, b.x);
+    mlp_forward(md, &b);
+    for (int c = 0; c < C; ++c) jb->out[i * C + c] = b.y[c];
+  }
+  mlp_free(&b);
+}
+
+void or_decode_stochastic(const or_model* md, int64_t n, const float* uvl, uint64_t seed,
+                          int64_t step, double* out, int nthreads) {
+  nthreads = clamp_threads(nthreads, n);
+  job* jobs = calloc((size_t)nthreads, sizeof(job));
+  for (int t = 0; t < nthreads; ++t) {
+    jobs[t].fn = decode_stoch_job; jobs[t].md = md; jobs[t].uvl = uvl; jobs[t].out = out;
+    jobs[t].seed = seed; jobs[t].step = step;
   }
   run_jobs(jobs, nthreads, n);
   free(jobs);

@@ -82,6 +82,10 @@ void or_decode_uvl(const or_model* md, int64_t n, const float* uvl, const or_noi
                    double* out, int nthreads);
 void or_decode_trilinear(const or_model* md, int64_t n, const float* uvl, double* out,
                          int nthreads);
+/* Stochastic filtering (Sec. 5.3): one nearest decode per query at the
+ * jittered texel and mip of frame `step` (see ntc_oracle.c). */
+void or_decode_stochastic(const or_model* md, int64_t n, const float* uvl, uint64_t seed,
+                          int64_t step, double* out, int nthreads);
 
 /* --- backward and loss (Sec. 4.5, 5.1) --- */
 void or_backward_xym(const or_model* md, int64_t n, const int32_t* xym, const double* dout,

@@ -27,7 +27,7 @@ GRID_PACKED, GRID_F32 = 0, 1
 PREC_F32, PREC_F16, PREC_F8 = 0, 1, 2
 ACT_RELU, ACT_HARDGELU = 0, 1
 OUT_SIGMOID, OUT_IDENTITY = 0, 1
-FILTER_NEAREST, FILTER_TRILINEAR = 0, 1
+FILTER_NEAREST, FILTER_TRILINEAR, FILTER_STOCHASTIC = 0, 1, 2
 DTYPE_F32, DTYPE_F16 = 0, 1
 FLAG_NOISE, FLAG_FREEZE_GRIDS, FLAG_NO_NOISE, FLAG_SIMT, FLAG_GRAD_ONLY = 0x1, 0x2, 0x4, 0x8, 0x10
 

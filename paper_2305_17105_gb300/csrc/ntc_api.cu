@@ -153,7 +153,9 @@ int ntc_decode(const ntc_material* m, const float* uvl, int64_t n, void* out, in
   if (st) return st;
   if (n < 0) return fail(NTC_ERR_ARG, "n < 0");
   if (out_dtype != NTC_DTYPE_F32 && out_dtype != NTC_DTYPE_F16) return fail(NTC_ERR_ARG, "out_dtype");
-  if (filter != NTC_FILTER_NEAREST && filter != NTC_FILTER_TRILINEAR) return fail(NTC_ERR_ARG, "filter");
+  if (filter != NTC_FILTER_NEAREST && filter != NTC_FILTER_TRILINEAR &&
+      filter != NTC_FILTER_STOCHASTIC)
+    return fail(NTC_ERR_ARG, "filter");
   if ((flags & NTC_FLAG_NOISE) && filter != NTC_FILTER_NEAREST)
     return fail(NTC_ERR_ARG, "noise needs nearest filtering");
   if (n == 0) return NTC_OK;
@@ -165,7 +167,9 @@ int ntc_decode(const ntc_material* m, const float* uvl, int64_t n, void* out, in
                                                (flags & NTC_FLAG_NOISE) != 0, noise_seed,
                                                noise_step, s),
                        "decode (FP32 CUDA cores)");
-  return cuda_status(ntc::launch_decode_tc(*m, uvl, n, out, out_dtype, filter, s, g_decode_nwg.load()),
+  return cuda_status(ntc::launch_decode_tc(*m, uvl, n, out, out_dtype, filter,
+                                           ntc::jitter_key(noise_seed, noise_step), s,
+                                           g_decode_nwg.load()),
                      "decode (tcgen05)");
 }
 
@@ -187,16 +191,17 @@ int ntc_autotune_decode(const ntc_material* m, const float* uvl, int64_t n, void
   CHECK_PTR(out, "out");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int shapes[4] = {2, 3, 4, 5};
+  const uint64_t jk = ntc::jitter_key(0, 0);  // stochastic filtering: frame 0 of seed 0
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     return cuda_status(cudaGetLastError(), "autotune events");
   float best_ms = 1e30f;
   int best_nwg = 0, rc = NTC_OK;
   for (int i = 0; i < 4 && rc == NTC_OK; ++i) {
-    cudaError_t e = ntc::launch_decode_tc(*m, uvl, n, out, out_dtype, filter, s, shapes[i]);
+    cudaError_t e = ntc::launch_decode_tc(*m, uvl, n, out, out_dtype, filter, jk, s, shapes[i]);
     if (e == cudaSuccess) e = cudaEventRecord(e0, s);
     for (int r = 0; r < 3 && e == cudaSuccess; ++r)
-      e = ntc::launch_decode_tc(*m, uvl, n, out, out_dtype, filter, s, shapes[i]);
+      e = ntc::launch_decode_tc(*m, uvl, n, out, out_dtype, filter, jk, s, shapes[i]);
     if (e == cudaSuccess) e = cudaEventRecord(e1, s);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
     float ms = 0.f;

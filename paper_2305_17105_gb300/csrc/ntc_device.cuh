@@ -70,6 +70,31 @@ __device__ __forceinline__ void query_texel(const ntc_material& M, float u, floa
   m = mm;
 }
 
+// Stochastic filtering (Sec. 5.3).  Query q of frame `step` takes one
+// SplitMix64 draw h = splitmix64(jitter_key ^ q): xi_x = h[40,64) 2^-24,
+// xi_y = h[16,40) 2^-24, xi_l = h[0,16) 2^-16.  The texel is the nearest one
+// of the jittered position u w_m - 1/2 + xi_x (x0 or x0 + 1 with the
+// bilinear weights; taps wrap like the trilinear filter's), the mip
+// floor(lod + xi_l) (floor(lod) or floor(lod) + 1 with the linear weights).
+// Every step is an FP32 operation without contraction, so the texel choice
+// is reproducible bit for bit; u is taken as 0 when NaN and clamped to
+// +-16384 (textures repeat).
+__host__ __device__ __forceinline__ uint64_t jitter_key(uint64_t seed, int64_t step) {
+  return rng_key(seed, ((uint64_t)step << 2) | 2u);
+}
+__device__ __forceinline__ int stochastic_mip(float lod, int mips, uint64_t h) {
+  const float xl = (float)(uint32_t)(h & 0xFFFFu) * (1.f / 65536.f);
+  const float l = !(lod >= 0.f) ? 0.f : fminf(lod, (float)(mips - 1));
+  return min((int)floorf(__fadd_rn(l, xl)), mips - 1);
+}
+__device__ __forceinline__ int stochastic_coord(float u, int w, uint32_t b24) {
+  const float xi = (float)b24 * (1.f / 16777216.f);
+  const float uc = fminf(fmaxf(u == u ? u : 0.f, -16384.f), 16384.f);
+  const float p = __fadd_rn(__fadd_rn(__fmul_rn(uc, (float)w), -0.5f), xi);
+  const int i = (int)floorf(p);
+  return (i % w + w) % w;
+}
+
 // Bilinear taps of a gw x gh grid for texel (x, y) of a wm x hm mip
 // (Sec. 4.3.1): texel centre (x + 1/2)/wm maps to p = centre * gw - 1/2 in
 // cell-centre coordinates; taps clamp to the grid edge.  With power-of-two

@@ -36,8 +36,9 @@ cudaError_t launch_decode_simt(const ntc_material& m, const float* uvl, int64_t 
                                int64_t noise_step, cudaStream_t s);
 cudaError_t launch_backward_simt(const ntc_material& m, const BwdArgs& a, cudaStream_t s);
 
+// jkey: jitter_key(seed, frame) of the stochastic filter (unused otherwise).
 cudaError_t launch_decode_tc(const ntc_material& m, const float* uvl, int64_t n, void* out,
-                             int out_dtype, int filter, cudaStream_t s, int ctas_per_sm);
+                             int out_dtype, int filter, uint64_t jkey, cudaStream_t s, int nwg);
 cudaError_t launch_train_tc(const ntc_material& m, const BwdArgs& a, cudaStream_t s);
 
 // Adam over the segments of the trainer's parameter array.
@@ -121,7 +122,7 @@ cudaError_t launch_decode_ws_batched(const BatchHeader* dev, int64_t total_tiles
 bool fast_layout_ok(const ntc_material& m);
 // Warp-specialised tensor-core decode (FP16), fast 4-bit layout or generic.
 cudaError_t launch_decode_ws(const ntc_material& m, const float* uvl, int64_t n, void* out,
-                             int out_dtype, int filter, cudaStream_t s, bool fast);
+                             int out_dtype, int filter, uint64_t jkey, cudaStream_t s, bool fast);
 
 
 int sm_count();

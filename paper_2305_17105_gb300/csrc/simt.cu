@@ -145,7 +145,7 @@ __host__ __device__ __forceinline__ int row_stride(int K) { return K + 4; }
 
 __global__ void __launch_bounds__(kThreads) decode_simt_kernel(
     const ntc_material M, const float* __restrict__ uvl, int64_t n, void* __restrict__ out,
-    int out_dtype, int filter, int noise, uint64_t nkey) {
+    int out_dtype, int filter, int noise, uint64_t nkey, uint64_t jkey) {
   extern __shared__ __align__(16) float smem[];
   const int K = M.k_in, C = M.channels;
   const SW L(K);
@@ -161,6 +161,13 @@ __global__ void __launch_bounds__(kThreads) decode_simt_kernel(
       int x, yy, m;
       query_texel(M, u, v, l, x, yy, m);
       featurize(M, x, yy, m, noise != 0, nkey, sink);
+      mlp_forward(sw, L, sink.row, K, M.act, M.out_act, y);
+    } else if (filter == NTC_FILTER_STOCHASTIC) {
+      const uint64_t h = splitmix64(jkey ^ (uint64_t)q);
+      const int m = stochastic_mip(l, M.mips, h);
+      const int x = stochastic_coord(u, mip_dim(M.width, m), (uint32_t)(h >> 40));
+      const int yy = stochastic_coord(v, mip_dim(M.height, m), (uint32_t)(h >> 16) & 0xFFFFFFu);
+      featurize(M, x, yy, m, false, 0, sink);
       mlp_forward(sw, L, sink.row, K, M.act, M.out_act, y);
     } else {
       // software trilinear filtering (Sec. 5.3): 2x2 texels on two mips
@@ -473,6 +480,7 @@ cudaError_t launch_decode_simt(const ntc_material& m, const float* uvl, int64_t 
                                int64_t noise_step, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   const uint64_t nkey = rng_key(noise_seed, noise_stream(noise_step));
+  const uint64_t jkey = jitter_key(noise_seed, noise_step);
   const SW L(m.k_in);
   const size_t smem = (size_t)(L.size + kThreads * row_stride(m.k_in)) * sizeof(float);
   cudaError_t e = cudaFuncSetAttribute(decode_simt_kernel,
@@ -484,7 +492,8 @@ cudaError_t launch_decode_simt(const ntc_material& m, const float* uvl, int64_t 
   const int64_t tiles = (n + kThreads - 1) / kThreads;
   const int64_t cap = (int64_t)sm_count() * (per_sm > 0 ? per_sm : 1);
   const int grid = (int)(tiles < cap ? tiles : cap);
-  decode_simt_kernel<<<grid, kThreads, smem, s>>>(m, uvl, n, out, out_dtype, filter, noise, nkey);
+  decode_simt_kernel<<<grid, kThreads, smem, s>>>(m, uvl, n, out, out_dtype, filter, noise, nkey,
+                                                  jkey);
   return cudaGetLastError();
 }
 

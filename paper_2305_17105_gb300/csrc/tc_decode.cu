@@ -42,7 +42,7 @@ namespace {
 template <bool F8, bool FAST, int kNWG>
 __global__ void __launch_bounds__(kRows* kNWG, 1) decode_tc_kernel(
     const ntc_material M, const float* __restrict__ uvl, int64_t n, void* __restrict__ out,
-    int out_dtype, int filter, int* status) {
+    int out_dtype, int filter, uint64_t jkey, int* status) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   __shared__ uint64_t mbar[kNWG];
   __shared__ uint32_t tmem_base;
@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(kRows* kNWG, 1) decode_tc_kernel(
   {
     const int64_t q0 = qindex(tl);
     Row r;
-    locate(M, tb, load_query(uvl, q0, tl < ntiles && q0 < n), tri, row, r);
+    locate(M, tb, load_query(uvl, q0, tl < ntiles && q0 < n), filter, row, r, q0, jkey);
     if (FAST) {
       gather_fast(P, tb, r);
       build_fast(P, P, K, sm, r, TmemRow{tx});
@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(kRows* kNWG, 1) decode_tc_kernel(
     if (row == 0) issue_layer<F8>(tw, tw + kColX, dsc, P.k_int / KSTEP, id64, false, 0, bar);
     // next tile: texel and cell gathers now, its query two tiles ahead
     Row nxt;
-    locate(M, tb, nq, tri, row, nxt);
+    locate(M, tb, nq, filter, row, nxt, qindex(tl + stride), jkey);
     if (FAST) gather_fast(P, tb, nxt);
     {
       const int64_t t2 = tl + 2 * stride;
@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(kRows* kNWG, 1) decode_tc_kernel(
 
 template <bool F8, bool FAST, int kNWG>
 cudaError_t launch_k(const ntc_material& m, const float* uvl, int64_t n, void* out, int out_dtype,
-                     int filter, cudaStream_t s) {
+                     int filter, uint64_t jkey, cudaStream_t s) {
   const Plan P(m.c0, m.c1, m.bits0, m.bits1, m.encoding == NTC_GRID_PACKED, F8, FAST);
   const size_t smem = P.total;
   cudaError_t e = cudaFuncSetAttribute(decode_tc_kernel<F8, FAST, kNWG>,
@@ -227,17 +227,17 @@ cudaError_t launch_k(const ntc_material& m, const float* uvl, int64_t n, void* o
   const int64_t cap = sm_count();
   const int grid = (int)(ctas < cap ? ctas : cap);
   decode_tc_kernel<F8, FAST, kNWG><<<grid, kRows * kNWG, smem, s>>>(m, uvl, n, out, out_dtype,
-                                                                    filter, status_word());
+                                                                    filter, jkey, status_word());
   return cudaGetLastError();
 }
 
 template <bool F8, bool FAST>
 cudaError_t launch_shape(const ntc_material& m, const float* uvl, int64_t n, void* out,
-                         int out_dtype, int filter, cudaStream_t s, int nwg) {
+                         int out_dtype, int filter, uint64_t jkey, cudaStream_t s, int nwg) {
   switch (nwg) {
-    case 2: return launch_k<F8, FAST, 2>(m, uvl, n, out, out_dtype, filter, s);
-    case 3: return launch_k<F8, FAST, 3>(m, uvl, n, out, out_dtype, filter, s);
-    default: return launch_k<F8, FAST, 4>(m, uvl, n, out, out_dtype, filter, s);
+    case 2: return launch_k<F8, FAST, 2>(m, uvl, n, out, out_dtype, filter, jkey, s);
+    case 3: return launch_k<F8, FAST, 3>(m, uvl, n, out, out_dtype, filter, jkey, s);
+    default: return launch_k<F8, FAST, 4>(m, uvl, n, out, out_dtype, filter, jkey, s);
   }
 }
 
@@ -265,18 +265,18 @@ bool fast_layout_ok(const ntc_material& m) {
 // the warp-specialised form: 4 compute warpgroups plus their MMA issuers
 // (FP16; FP8 runs 4 pipelines).
 cudaError_t launch_decode_tc(const ntc_material& m, const float* uvl, int64_t n, void* out,
-                             int out_dtype, int filter, cudaStream_t s, int nwg) {
+                             int out_dtype, int filter, uint64_t jkey, cudaStream_t s, int nwg) {
   if (n == 0) return cudaSuccess;
   if (nwg == 0) nwg = 5;
   if (nwg < 2 || nwg > 5) return cudaErrorInvalidValue;
   if (m.precision == NTC_PREC_F8)
-    return launch_shape<true, false>(m, uvl, n, out, out_dtype, filter, s, nwg == 5 ? 4 : nwg);
+    return launch_shape<true, false>(m, uvl, n, out, out_dtype, filter, jkey, s, nwg == 5 ? 4 : nwg);
   if (m.precision != NTC_PREC_F16) return cudaErrorInvalidValue;
   const Plan P(m.c0, m.c1, m.bits0, m.bits1, m.encoding == NTC_GRID_PACKED, false,
                fast_layout_ok(m));
-  if (nwg == 5) return launch_decode_ws(m, uvl, n, out, out_dtype, filter, s, P.fast != 0);
-  if (P.fast) return launch_shape<false, true>(m, uvl, n, out, out_dtype, filter, s, nwg);
-  return launch_shape<false, false>(m, uvl, n, out, out_dtype, filter, s, nwg);
+  if (nwg == 5) return launch_decode_ws(m, uvl, n, out, out_dtype, filter, jkey, s, P.fast != 0);
+  if (P.fast) return launch_shape<false, true>(m, uvl, n, out, out_dtype, filter, jkey, s, nwg);
+  return launch_shape<false, false>(m, uvl, n, out, out_dtype, filter, jkey, s, nwg);
 }
 
 }  // namespace ntc

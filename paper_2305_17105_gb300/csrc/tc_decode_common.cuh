@@ -348,23 +348,25 @@ __device__ __forceinline__ Query load_query(const float* __restrict__ uvl, int64
   return r;
 }
 
-// Query -> texel of this row (nearest: one per query; trilinear: tap `row & 7`
-// of query `row / 8`).
+// Query -> texel of this row (nearest and stochastic: one per query;
+// trilinear: tap `row & 7` of query `row / 8`).  q: the query's index (the
+// stochastic filter's counter), jkey: jitter_key of the frame.
 __device__ __forceinline__ void locate(const ntc_material& M, const MipTab* tb, const Query& qu,
-                                       bool tri, int row, Row& r) {
+                                       int filter, int row, Row& r, int64_t q = 0,
+                                       uint64_t jkey = 0) {
   r.valid = qu.valid;
   r.wtap = 0.f;
   r.x = r.y = r.m = 0;
   if (!qu.valid) return;
   const float u = qu.u, v = qu.v, l = qu.l;
-  if (!tri) {
+  if (filter == NTC_FILTER_NEAREST) {
     const int m = !(l >= 0.f) ? 0 : (l >= (float)(M.mips - 1) ? M.mips - 1 : (int)floorf(l));
     const int wm = tb->wm[m], hm = tb->hm[m];
     const float tu = u * (float)wm, tv = v * (float)hm;
     r.x = !(tu >= 0.f) ? 0 : (tu >= (float)wm ? wm - 1 : (int)floorf(tu));
     r.y = !(tv >= 0.f) ? 0 : (tv >= (float)hm ? hm - 1 : (int)floorf(tv));
     r.m = m;
-  } else {
+  } else if (filter == NTC_FILTER_TRILINEAR) {
     const int tap = row & 7, s = tap >> 2, dx = tap & 1, dy = (tap >> 1) & 1;
     const float lam = !(l >= 0.f) ? 0.f : fminf(l, (float)(M.mips - 1));
     const int m0 = min((int)floorf(lam), M.mips - 1);
@@ -380,6 +382,12 @@ __device__ __forceinline__ void locate(const ntc_material& M, const MipTab* tb, 
     r.y = (((int)fy0 + dy) % hm + hm) % hm;
     r.m = m;
     r.wtap = wl * (dx ? fx : 1.f - fx) * (dy ? fy : 1.f - fy);
+  } else {
+    const uint64_t h = splitmix64(jkey ^ (uint64_t)q);
+    const int m = stochastic_mip(l, M.mips, h);
+    r.x = stochastic_coord(u, tb->wm[m], (uint32_t)(h >> 40));
+    r.y = stochastic_coord(v, tb->hm[m], (uint32_t)(h >> 16) & 0xFFFFFFu);
+    r.m = m;
   }
 }
 

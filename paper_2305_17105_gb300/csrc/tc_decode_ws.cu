@@ -39,7 +39,7 @@ struct WsPlan {
 template <int CLS>
 __global__ void __launch_bounds__(kWsThreads, 1) decode_ws_kernel(
     const ntc_material M, const float* __restrict__ uvl, int64_t n, void* __restrict__ out,
-    int out_dtype, int filter, int* status) {
+    int out_dtype, int filter, uint64_t jkey, int* status) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   __shared__ uint64_t bar_x[kWsCompute], bar_h[kWsCompute], bar_d[kWsCompute],
       bar_o[kWsCompute], bar_fin[kWsCompute];
@@ -150,13 +150,13 @@ __global__ void __launch_bounds__(kWsThreads, 1) decode_ws_kernel(
     if (tl < ntiles) {
       Row r;
       const int64_t q0 = qindex(tl);
-      locate(M, tb, load_query(uvl, q0, q0 < n), tri, row, r);
+      locate(M, tb, load_query(uvl, q0, q0 < n), filter, row, r, q0, jkey);
       if (FAST) gather_fast(lay, tb, r);
       build(r);
       cur_valid = r.valid;
       cur_wtap = r.wtap;
       const int64_t q1 = qindex(tl + stride);
-      locate(M, tb, load_query(uvl, q1, tl + stride < ntiles && q1 < n), tri, row, nxt);
+      locate(M, tb, load_query(uvl, q1, tl + stride < ntiles && q1 < n), filter, row, nxt, q1, jkey);
       if (FAST) gather_fast(lay, tb, nxt);
       const int64_t q2 = qindex(tl + 2 * stride);
       nq = load_query(uvl, q2, tl + 2 * stride < ntiles && q2 < n);
@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) decode_ws_kernel(
       if (lane == 0) tc::mbar_arrive(&bar_h[w]);
       if (*abort_flag) break;
       // the tile after next: texel and cells; its successor's query
-      locate(M, tb, nq, tri, row, nxt);
+      locate(M, tb, nq, filter, row, nxt, qindex(tl + 2 * stride), jkey);
       if (FAST) gather_fast(lay, tb, nxt);
       {
         const int64_t t3 = tl + 3 * stride;
@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) decode_ws_kernel(
 
 template <int CLS>
 cudaError_t launch_ws(const ntc_material& m, const float* uvl, int64_t n, void* out, int out_dtype,
-                      int filter, cudaStream_t s) {
+                      int filter, uint64_t jkey, cudaStream_t s) {
   const Plan P(m.c0, m.c1, m.bits0, m.bits1, m.encoding == NTC_GRID_PACKED, false, CLS > 0);
   const WsPlan W(P);
   cudaError_t e = cudaFuncSetAttribute(decode_ws_kernel<CLS>,
@@ -248,7 +248,7 @@ cudaError_t launch_ws(const ntc_material& m, const float* uvl, int64_t n, void* 
   const int64_t ctas = (tiles + kWsCompute - 1) / kWsCompute;
   const int64_t cap = sm_count();
   const int grid = (int)(ctas < cap ? ctas : cap);
-  decode_ws_kernel<CLS><<<grid, kWsThreads, W.total, s>>>(m, uvl, n, out, out_dtype, filter,
+  decode_ws_kernel<CLS><<<grid, kWsThreads, W.total, s>>>(m, uvl, n, out, out_dtype, filter, jkey,
                                                           status_word());
   return cudaGetLastError();
 }
@@ -410,7 +410,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) decode_ws_batched_kernel(
     auto locate_tile = [&](int64_t t, Row& r) {
       const int64_t ql = tri ? (t - m_t0) * per_tile + (row >> 3) : (t - m_t0) * per_tile + row;
       const bool valid = ql < m_nq;
-      locate(M, tb, load_query(uvl, m_q0 + ql, valid), tri, row, r);
+      locate(M, tb, load_query(uvl, m_q0 + ql, valid), filter, row, r);
       if (CLS > 0) gather_fast(Lay(), tb, r);
       else if (CLS < 0) gather_fast(P, tb, r);
     };
@@ -581,19 +581,19 @@ cudaError_t launch_decode_ws_batched(const BatchHeader* dev, int64_t total_tiles
 }
 
 cudaError_t launch_decode_ws(const ntc_material& m, const float* uvl, int64_t n, void* out,
-                             int out_dtype, int filter, cudaStream_t s, bool fast) {
-  if (!fast) return launch_ws<0>(m, uvl, n, out, out_dtype, filter, s);
+                             int out_dtype, int filter, uint64_t jkey, cudaStream_t s, bool fast) {
+  if (!fast) return launch_ws<0>(m, uvl, n, out, out_dtype, filter, jkey, s);
   const Plan P(m.c0, m.c1, m.bits0, m.bits1, true, false, true);
   switch (1 + 3 * grid_class(m.c0, P.cb0) + grid_class(m.c1, P.cb1)) {
-    case 1: return launch_ws<1>(m, uvl, n, out, out_dtype, filter, s);
-    case 2: return launch_ws<2>(m, uvl, n, out, out_dtype, filter, s);
-    case 3: return launch_ws<3>(m, uvl, n, out, out_dtype, filter, s);
-    case 4: return launch_ws<4>(m, uvl, n, out, out_dtype, filter, s);
-    case 5: return launch_ws<5>(m, uvl, n, out, out_dtype, filter, s);
-    case 6: return launch_ws<6>(m, uvl, n, out, out_dtype, filter, s);
-    case 7: return launch_ws<7>(m, uvl, n, out, out_dtype, filter, s);
-    case 8: return launch_ws<8>(m, uvl, n, out, out_dtype, filter, s);
-    default: return launch_ws<9>(m, uvl, n, out, out_dtype, filter, s);
+    case 1: return launch_ws<1>(m, uvl, n, out, out_dtype, filter, jkey, s);
+    case 2: return launch_ws<2>(m, uvl, n, out, out_dtype, filter, jkey, s);
+    case 3: return launch_ws<3>(m, uvl, n, out, out_dtype, filter, jkey, s);
+    case 4: return launch_ws<4>(m, uvl, n, out, out_dtype, filter, jkey, s);
+    case 5: return launch_ws<5>(m, uvl, n, out, out_dtype, filter, jkey, s);
+    case 6: return launch_ws<6>(m, uvl, n, out, out_dtype, filter, jkey, s);
+    case 7: return launch_ws<7>(m, uvl, n, out, out_dtype, filter, jkey, s);
+    case 8: return launch_ws<8>(m, uvl, n, out, out_dtype, filter, jkey, s);
+    default: return launch_ws<9>(m, uvl, n, out, out_dtype, filter, jkey, s);
   }
 }
 

@@ -287,3 +287,18 @@ def test_train_loop_reduces_loss():
     lo, hi = oracle.quant_range(16, 1 / 16)
     g = tr.material.grids0[0]
     assert float(g.min()) >= lo - 1e-7 and float(g.max()) <= hi + 1e-7
+
+
+def test_stochastic_filter_fp32_matches_oracle():
+    """FP32 form of the stochastic filter: same texel choice as the oracle,
+    outputs within FP32 rounding."""
+    case = make_case(128, 64, 5, 6, 10, bits0=2, bits1=8, k_in=32, seed=62)
+    mat, md = device_material(case)
+    rng = np.random.default_rng(62)
+    q = np.empty((2000, 3), np.float32)
+    q[:, :2] = rng.uniform(-2.0, 3.0, (2000, 2))
+    q[:, 2] = rng.uniform(-1.0, md.mips + 1.0, 2000)
+    for seed, step in ((3, 0), (3, 5)):
+        got = to_np(ntc.ntc_decode(mat, torch.from_numpy(q).cuda(), filter=ntc.FILTER_STOCHASTIC,
+                                   noise_seed=seed, noise_step=step))
+        assert np.abs(got - md.decode_stochastic(q, seed, step)).max() < 1e-5

@@ -195,3 +195,25 @@ def test_autotune_picks_a_shape_and_stays_correct():
         assert np.abs(_decode(mat, q) - md.decode(q)).max() <= OUT_TOL
     finally:
         ntc.ntc_set_decode_warpgroups(0)
+
+
+@pytest.mark.parametrize("nwg", [4, 5])
+@pytest.mark.parametrize("shape", [SHAPES[1], SHAPES[3], SHAPES[6]])
+def test_stochastic_filter_matches_oracle(shape, nwg):
+    """Stochastic filtering (Sec. 5.3): the jittered texel and mip chosen in
+    FP32 on both sides (bit-identical choice), then the FP16 decode."""
+    case = make_case(seed=61, **shape)
+    mat, md = device_material(case, precision=ntc.PREC_F16)
+    rng = np.random.default_rng(61)
+    n = 5 * 128 + 19
+    q = np.empty((n, 3), np.float32)
+    q[:, :2] = rng.uniform(-1.0, 2.0, (n, 2))
+    q[:, 2] = rng.uniform(-0.5, md.mips + 0.5, n)
+    q[:3] = [[np.nan, 0.5, 1.0], [0.25, 0.75, np.nan], [1e9, -1e9, 2.0]]
+    ntc.ntc_set_decode_warpgroups(nwg)
+    try:
+        for seed, step in ((7, 0), (7, 1), (123456789, 99)):
+            got = _decode(mat, q, filter=ntc.FILTER_STOCHASTIC, noise_seed=seed, noise_step=step)
+            assert np.abs(got - md.decode_stochastic(q, seed, step)).max() <= OUT_TOL
+    finally:
+        ntc.ntc_set_decode_warpgroups(0)

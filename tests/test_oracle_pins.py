@@ -288,6 +288,39 @@ def test_trilinear_reduces_to_nearest_at_texel_centres():
     assert np.abs(md.decode_trilinear(u) - 0.5 * (lo + hi)).max() < 1e-12
 
 
+def test_stochastic_filter_is_nearest_at_texel_centres():
+    """Stochastic filtering (Sec. 5.3) at texel centres with integer LODs: the
+    jitter xi in [0, 1) never leaves the texel or the mip, for any frame."""
+    case = make_case(64, 32, 3, 4, 4, seed=11)
+    md = case.oracle_model()
+    xym = np.array([[5, 7, 0], [31, 2, 1], [3, 3, 3], [0, 0, 5], [63, 31, 0]], np.int32)
+    uvl = oracle.uvl_of_xym(xym, 64, 32)
+    ref = md.decode_xym(xym)
+    for step in (0, 1, 77):
+        assert np.abs(md.decode_stochastic(uvl, 5, step) - ref).max() == 0.0
+
+
+def test_stochastic_filter_converges_to_trilinear():
+    """Averaged over frames the stochastic decode is the trilinear filter (the
+    jitter picks each of the 8 texels with its trilinear weight): the mean of
+    400 frames lies within 5 standard errors of the trilinear decode, while
+    single frames do not equal it."""
+    case = make_case(64, 64, 3, 4, 4, seed=12)
+    md = case.oracle_model()
+    rng = np.random.default_rng(13)
+    q = np.empty((40, 3), np.float32)
+    q[:, :2] = rng.random((40, 2))
+    q[:, 2] = rng.uniform(0.0, md.mips - 1.0, 40)
+    frames = np.stack([md.decode_stochastic(q, 21, s) for s in range(400)])
+    mean, se = frames.mean(0), frames.std(0) / np.sqrt(len(frames))
+    tri = md.decode_trilinear(q)
+    assert np.all(np.abs(mean - tri) <= 5 * se + 1e-12)
+    assert np.abs(frames[0] - tri).max() > 1e-3
+    # frames are reproducible and differ from one another
+    assert np.array_equal(md.decode_stochastic(q, 21, 3), frames[3])
+    assert not np.array_equal(frames[3], frames[4])
+
+
 # ------------------------------------------------------------- gradients ---
 def _flat_params(md):
     return md.grids0 + md.grids1 + md.weights
