@@ -73,6 +73,12 @@ enum { NTC_OUT_SIGMOID = 0, NTC_OUT_IDENTITY = 1 }; /* output activation */
  * index), which equals trilinear filtering in expectation. */
 enum { NTC_FILTER_NEAREST = 0, NTC_FILTER_TRILINEAR = 1, NTC_FILTER_STOCHASTIC = 2 };
 enum { NTC_DTYPE_F32 = 0, NTC_DTYPE_F16 = 1 };              /* output element type */
+/* Resampling of G0 (Sec. 4.3.1): bilinear like G1, or learned interpolation:
+ * the four neighbouring G0 feature vectors of the bilinear footprint (taps
+ * (x0,y0), (x1,y0), (x0,y1), (x1,y1)) concatenated in the MLP input, which
+ * then holds 4 c0 + c1 + 13 used values.  Learned interpolation runs on the
+ * FP32 and FP16 decode forms and the FP32 training form. */
+enum { NTC_INTERP_BILINEAR = 0, NTC_INTERP_LEARNED = 1 };
 
 /* Flags of ntc_decode / ntc_backward / ntc_train_step. */
 #define NTC_FLAG_NOISE 0x1        /* add simulated-quantisation noise (Sec. 4.2); F32 grids */
@@ -103,12 +109,14 @@ typedef struct {
   int32_t bits0, bits1;  /* quantisation bits B_k in {1,2,4,8}: N_k = 2^B_k levels */
   float q0, q1;          /* bin width Q_k: level values (k - (N/2-1)) * Q (Sec. 4.2) */
   int32_t encoding;      /* NTC_GRID_PACKED | NTC_GRID_F32 */
-  int32_t k_in;          /* MLP input width: >= c0 + c1 + 13, multiple of 16
+  int32_t k_in;          /* MLP input width: >= c0 + c1 + 13 (4 c0 + c1 + 13 with
+                            learned interpolation), multiple of 16
                             (of 32 for NTC_PREC_F8), <= NTC_MAX_K */
   int32_t hidden;        /* must be NTC_HIDDEN */
   int32_t act;           /* NTC_ACT_* */
   int32_t out_act;       /* NTC_OUT_* */
   int32_t precision;     /* NTC_PREC_* */
+  int32_t interp0;       /* NTC_INTERP_*: resampling of G0 (Sec. 4.3.1) */
   ntc_level lv[NTC_MAX_LEVELS];
   const void* w[3];      /* layer weights [out][in]: W1 [hidden][k_in], W2 [hidden][hidden],
                             W3 [channels][hidden]; float / half / e4m3 by precision */

@@ -57,7 +57,7 @@ class _Model(C.Structure):
         ("grid0", C.c_void_p * MAX_LEVELS), ("grid1", C.c_void_p * MAX_LEVELS),
         ("k_in", C.c_int), ("hidden", C.c_int), ("act", C.c_int), ("out_act", C.c_int),
         ("w1", C.c_void_p), ("b1", C.c_void_p), ("w2", C.c_void_p), ("b2", C.c_void_p),
-        ("w3", C.c_void_p), ("b3", C.c_void_p),
+        ("w3", C.c_void_p), ("b3", C.c_void_p), ("interp0", C.c_int),
     ]
 
 
@@ -222,7 +222,7 @@ class Model:
     """
 
     def __init__(self, width, height, channels, c0, c1, n0, n1, q0, q1, grids0, grids1,
-                 weights, k_in, hidden=64, act=0, out_act=0):
+                 weights, k_in, hidden=64, act=0, out_act=0, interp0=0):
         self.width, self.height, self.channels = width, height, channels
         self.mips = mips(width, height)
         self.levels = len(grids0)
@@ -240,6 +240,7 @@ class Model:
             s.grid0[j] = self.grids0[j].ctypes.data
             s.grid1[j] = self.grids1[j].ctypes.data
         s.k_in, s.hidden, s.act, s.out_act = k_in, hidden, act, out_act
+        self.interp0 = s.interp0 = interp0
         w = self.weights
         s.w1, s.b1, s.w2, s.b2, s.w3, s.b3 = [a.ctypes.data for a in w]
         assert w[0].shape == (hidden, k_in) and w[2].shape == (hidden, hidden)

@@ -231,22 +231,33 @@ static double grid_value(const or_model* md, int j, int k, int64_t cell, int ch,
 /* The decoder's input row (Sec. 4.3, 4.4): bilinear G0 features, bilinear G1
  * features, 12 positional-encoding values, the normalised LOD m/(M-1), then
  * zeros up to k_in. */
+/* Width of the G0 part of the input row: c0 (bilinear) or 4 c0 (learned
+ * interpolation, Sec. 4.3.1: the four neighbouring feature vectors of the
+ * bilinear footprint concatenated, taps in the order (x0,y0), (x1,y0),
+ * (x0,y1), (x1,y1), so that the MLP weighs them by the texel's phase). */
+static int g0_width(const or_model* md) { return md->interp0 ? 4 * md->c0 : md->c0; }
+
 void or_features(const or_model* md, int x, int y, int m, const or_noise* nz, double* row) {
   int j = or_level_of_mip(m, md->levels);
   int wm = mip_w(md, m), hm = mip_h(md, m);
   for (int i = 0; i < md->k_in; ++i) row[i] = 0.0;
   for (int k = 0; k < 2; ++k) {
     int gw = k ? md->g1w[j] : md->g0w[j], gh = k ? md->g1h[j] : md->g0h[j];
-    int c = k ? md->c1 : md->c0, base = k ? md->c0 : 0;
+    int c = k ? md->c1 : md->c0, base = k ? g0_width(md) : 0;
     int64_t cell[4]; double wt[4];
     bilinear_taps(x, y, wm, hm, gw, gh, cell, wt);
+    if (k == 0 && md->interp0) {
+      for (int t = 0; t < 4; ++t)
+        for (int ch = 0; ch < c; ++ch) row[t * c + ch] = grid_value(md, j, 0, cell[t], ch, nz);
+      continue;
+    }
     for (int ch = 0; ch < c; ++ch) {
       double s = 0.0;
       for (int t = 0; t < 4; ++t) s += wt[t] * grid_value(md, j, k, cell[t], ch, nz);
       row[base + ch] = s;
     }
   }
-  double* pe = row + md->c0 + md->c1;
+  double* pe = row + g0_width(md) + md->c1;
   or_positional_encoding(x, y, pe);
   pe[12] = md->mips > 1 ? (double)m / (double)(md->mips - 1) : 0.0;
 }
@@ -591,15 +602,21 @@ static void backward_one(const or_model* md, int x, int y, int m, const double* 
     for (int o = 0; o < H; ++o) s += md->w1[(int64_t)o * K + i] * dz1[o];
     dx[i] = s;
   }
-  /* scatter the feature part of dx back through the bilinear taps */
+  /* scatter the feature part of dx back through the taps: bilinear weights,
+   * or (learned interpolation of G0) each tap's own slots with weight 1 */
   int j = or_level_of_mip(m, md->levels);
   int wm = mip_w(md, m), hm = mip_h(md, m);
   for (int k = 0; k < 2; ++k) {
     int gw = k ? md->g1w[j] : md->g0w[j], gh = k ? md->g1h[j] : md->g0h[j];
-    int c = k ? md->c1 : md->c0, base = k ? md->c0 : 0;
+    int c = k ? md->c1 : md->c0, base = k ? g0_width(md) : 0;
     double* gg = k ? g->grid1[j] : g->grid0[j];
     int64_t cell[4]; double wt[4];
     bilinear_taps(x, y, wm, hm, gw, gh, cell, wt);
+    if (k == 0 && md->interp0) {
+      for (int t = 0; t < 4; ++t)
+        for (int ch = 0; ch < c; ++ch) gg[cell[t] * c + ch] += dx[t * c + ch];
+      continue;
+    }
     for (int t = 0; t < 4; ++t)
       for (int ch = 0; ch < c; ++ch) gg[cell[t] * c + ch] += wt[t] * dx[base + ch];
   }

@@ -35,6 +35,8 @@ typedef struct {
   const double *w1, *b1;    /* [hidden][k_in], [hidden] */
   const double *w2, *b2;    /* [hidden][hidden], [hidden] */
   const double *w3, *b3;    /* [channels][hidden], [channels] */
+  int interp0;              /* G0 resampling (Sec. 4.3.1): 0 bilinear, 1 learned
+                               interpolation (the four taps concatenated) */
 } or_model;
 
 /* Simulated-quantisation noise switch (Sec. 4.2). */

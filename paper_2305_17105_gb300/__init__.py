@@ -52,7 +52,7 @@ class ntc_material(C.Structure):
                 ("bits0", C.c_int32), ("bits1", C.c_int32), ("q0", C.c_float), ("q1", C.c_float),
                 ("encoding", C.c_int32), ("k_in", C.c_int32), ("hidden", C.c_int32),
                 ("act", C.c_int32), ("out_act", C.c_int32), ("precision", C.c_int32),
-                ("lv", ntc_level * MAX_LEVELS), ("w", C.c_void_p * 3), ("b", C.c_void_p * 3),
+                ("interp0", C.c_int32), ("lv", ntc_level * MAX_LEVELS), ("w", C.c_void_p * 3), ("b", C.c_void_p * 3),
                 ("scale", C.c_void_p)]
 
 
@@ -198,7 +198,7 @@ class Material:
 
     def __init__(self, width, height, channels, c0, c1, bits0, bits1, q0, q1, grids0, grids1,
                  weights, biases, k_in, precision=PREC_F32, act=ACT_RELU, out_act=OUT_SIGMOID,
-                 scale=None):
+                 scale=None, interp0=0):
         self.width, self.height, self.channels = width, height, channels
         self.mips = mips_of(width, height)
         self.c0, self.c1, self.bits0, self.bits1 = c0, c1, bits0, bits1
@@ -207,6 +207,7 @@ class Material:
         self.weights, self.biases = list(weights), list(biases)
         self.k_in, self.precision, self.act, self.out_act = k_in, precision, act, out_act
         self.scale = scale
+        self.interp0 = interp0
         self.encoding = GRID_PACKED if self.grids0[0].dtype == torch.uint8 else GRID_F32
         self.levels = len(self.grids0)
 
@@ -219,6 +220,7 @@ class Material:
         s.q0, s.q1 = self.q0, self.q1
         s.encoding, s.k_in, s.hidden = self.encoding, self.k_in, HIDDEN
         s.act, s.out_act, s.precision = self.act, self.out_act, self.precision
+        s.interp0 = self.interp0
         for j in range(self.levels):
             g0, g1 = self.grids0[j], self.grids1[j]
             s.lv[j].g0_h, s.lv[j].g0_w = g0.shape[0], g0.shape[1]

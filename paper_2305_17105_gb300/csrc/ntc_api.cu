@@ -66,8 +66,13 @@ int check_material(const ntc_material* m, bool need_f32_grids) {
   if (m->precision < NTC_PREC_F32 || m->precision > NTC_PREC_F8)
     return fail(NTC_ERR_ARG, "precision %d", m->precision);
   const int kmul = m->precision == NTC_PREC_F8 ? 32 : 16;
-  if (m->k_in % kmul != 0 || m->k_in < m->c0 + m->c1 + 13 || m->k_in > NTC_MAX_K)
-    return fail(NTC_ERR_SHAPE, "k_in = %d: need a multiple of %d in [c0+c1+13, %d]", m->k_in, kmul,
+  if (m->interp0 != NTC_INTERP_BILINEAR && m->interp0 != NTC_INTERP_LEARNED)
+    return fail(NTC_ERR_ARG, "interp0 %d", m->interp0);
+  if (m->interp0 == NTC_INTERP_LEARNED && m->precision == NTC_PREC_F8)
+    return fail(NTC_ERR_UNSUPPORTED, "learned interpolation: FP32 or FP16 weights");
+  const int used = (m->interp0 == NTC_INTERP_LEARNED ? 4 * m->c0 : m->c0) + m->c1 + 13;
+  if (m->k_in % kmul != 0 || m->k_in < used || m->k_in > NTC_MAX_K)
+    return fail(NTC_ERR_SHAPE, "k_in = %d: need a multiple of %d in [%d, %d]", m->k_in, kmul, used,
                 NTC_MAX_K);
   if (m->act != NTC_ACT_RELU && m->act != NTC_ACT_HARDGELU) return fail(NTC_ERR_ARG, "act %d", m->act);
   if (m->out_act != NTC_OUT_SIGMOID && m->out_act != NTC_OUT_IDENTITY)
@@ -393,8 +398,9 @@ int ntc_train_step(const ntc_material* m, const ntc_trainer* tr, const ntc_targe
     if (m->k_in > 64) return fail(NTC_ERR_UNSUPPORTED, "FP32 training supports k_in <= 64");
     e = ntc::launch_backward_simt(mt, b, s);
   } else {
-    if (m->act != NTC_ACT_RELU)
-      return fail(NTC_ERR_UNSUPPORTED, "tensor-core training supports ReLU (use NTC_FLAG_SIMT)");
+    if (m->act != NTC_ACT_RELU || m->interp0 != NTC_INTERP_BILINEAR)
+      return fail(NTC_ERR_UNSUPPORTED,
+                  "tensor-core training supports ReLU and bilinear G0 (use NTC_FLAG_SIMT)");
     e = ntc::launch_train_tc(mt, b, s);
   }
   if (e != cudaSuccess) return cuda_status(e, "train_step forward/backward");
@@ -442,10 +448,13 @@ int ntc_batch_prepare(const ntc_material* mats, const int64_t* n_queries, int32_
     B.q_off[i + 1] = B.q_off[i] + n_queries[i];
     B.o_off[i + 1] = B.o_off[i] + n_queries[i] * m->channels;
   }
+  uint32_t kmax = 0;
   for (int i = 0; i < n_materials; ++i) {
     const uint32_t need = ntc::ws_plan_bytes(mats[i], cls != 0);
-    plan_bytes = need > plan_bytes ? need : plan_bytes;
+    plan_bytes = (need & 0xFFFFFFu) > plan_bytes ? (need & 0xFFFFFFu) : plan_bytes;
+    kmax = (need >> 24) > kmax ? (need >> 24) : kmax;
   }
+  plan_bytes |= kmax << 24;  // internal: plan bytes | largest K << 24
   if (ntc::ws_batched_smem(plan_bytes) > 227 * 1024)
     return fail(NTC_ERR_UNSUPPORTED, "batch: shared memory");
   B.n_materials = n_materials;

@@ -253,6 +253,24 @@ __device__ __forceinline__ void sample_grid(const ntc_material& M, int j, int k,
   }
 }
 
+// One latent value of grid k at a cell: dequantised index (packed) or the
+// FP32 value plus this step's noise.
+__device__ __forceinline__ float grid_value(const ntc_material& M, int j, int k, int cell, int ch,
+                                            bool noise, uint64_t nkey) {
+  const ntc_level& L = M.lv[j];
+  const int c = k ? M.c1 : M.c0;
+  const float q = k ? M.q1 : M.q0;
+  if (M.encoding == NTC_GRID_PACKED) {
+    const int bits = k ? M.bits1 : M.bits0;
+    const Cell cl = load_cell(static_cast<const uint8_t*>(k ? L.grid1 : L.grid0), cell,
+                              cell_bytes(c, bits));
+    return (float)((int)cell_index(cl, ch, bits) - ((1 << (bits - 1)) - 1)) * q;
+  }
+  float val = __ldg(static_cast<const float*>(k ? L.grid1 : L.grid0) + (size_t)cell * c + ch);
+  if (noise) val += noise_of(nkey, j, k, cell, ch, c, q);
+  return val;
+}
+
 // The MLP input row of texel (x, y, m) (Sec. 4.3, 4.4):
 // [G0 features | G1 features | 12 PE values | m/(M-1) | 0 ...], written
 // through sink(index, value) for indices 0 .. k_in-1.
@@ -262,15 +280,26 @@ __device__ __forceinline__ void featurize(const ntc_material& M, int x, int y, i
   const int j = level_of_mip(m, M.levels);
   const int wm = mip_dim(M.width, m), hm = mip_dim(M.height, m);
   GridSample gs;
-  sample_grid(M, j, 0, x, y, wm, hm, noise, nkey, gs);
+  int w0 = M.c0;
+  if (M.interp0 == NTC_INTERP_LEARNED) {
+    // learned interpolation (Sec. 4.3.1): the four G0 taps concatenated
+    const ntc_level& L = M.lv[j];
+    const Taps t = bilinear_taps(x, y, wm, hm, L.g0_w, L.g0_h);
+#pragma unroll 1
+    for (int tp = 0; tp < 4; ++tp)
+      for (int ch = 0; ch < M.c0; ++ch) sink(tp * M.c0 + ch, grid_value(M, j, 0, t.cell[tp], ch, noise, nkey));
+    w0 = 4 * M.c0;
+  } else {
+    sample_grid(M, j, 0, x, y, wm, hm, noise, nkey, gs);
 #pragma unroll
-  for (int ch = 0; ch < kMaxGridCh; ++ch)
-    if (ch < M.c0) sink(ch, gs.acc[ch]);
+    for (int ch = 0; ch < kMaxGridCh; ++ch)
+      if (ch < M.c0) sink(ch, gs.acc[ch]);
+  }
   sample_grid(M, j, 1, x, y, wm, hm, noise, nkey, gs);
 #pragma unroll
   for (int ch = 0; ch < kMaxGridCh; ++ch)
-    if (ch < M.c1) sink(M.c0 + ch, gs.acc[ch]);
-  const int pe = M.c0 + M.c1;
+    if (ch < M.c1) sink(w0 + ch, gs.acc[ch]);
+  const int pe = w0 + M.c1;
   positional_encoding(x, y, pe, sink);
   sink(pe + 12, M.mips > 1 ? (float)m / (float)(M.mips - 1) : 0.f);
   for (int i = pe + 13; i < M.k_in; ++i) sink(i, 0.f);

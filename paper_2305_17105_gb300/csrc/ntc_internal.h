@@ -111,7 +111,8 @@ struct BatchHeader {
 // Input-layout class of a material for the warp-specialised kernels: 0
 // generic, 1..9 fast 4-bit layout (1 + 3 k0 + k1 by grid class).
 int fast_class(const ntc_material& m);
-// Shared-memory plan bytes of one material, and the batched kernel's total.
+// Shared-memory plan bytes of one material | its internal K << 24, and the
+// batched kernel's total for the batch's maxima of both.
 uint32_t ws_plan_bytes(const ntc_material& m, bool fast);
 uint32_t ws_batched_smem(uint32_t plan_bytes);
 // Many materials in one warp-specialised launch; cls: 0 generic, 1..9 one

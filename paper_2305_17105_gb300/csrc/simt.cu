@@ -231,8 +231,8 @@ struct SB {
     z1 = x + kTile * row_stride(K);              // [128][65]
     z2 = z1 + kTile * (kHidden + 1);             // [128][65]
     d3 = z2 + kTile * (kHidden + 1);             // [128][17]
-    dx = d3 + kTile * (kMaxC + 1);               // [128][33]
-    red = dx + kTile * (NTC_MAX_FEATURES + 1);   // [4]
+    dx = d3 + kTile * (kMaxC + 1);               // [128][K+1]: dX over the feature slots
+    red = dx + kTile * (K + 1);                  // [4]
     size = red + 4;
   }
 };
@@ -240,7 +240,9 @@ struct SB {
 __global__ void __launch_bounds__(kThreads, 1) backward_simt_kernel(const ntc_material M,
                                                                     const BwdArgs A) {
   extern __shared__ __align__(16) float smem[];
-  const int K = M.k_in, C = M.channels, F = M.c0 + M.c1;
+  const int K = M.k_in, C = M.channels;
+  const int W0 = M.interp0 == NTC_INTERP_LEARNED ? 4 * M.c0 : M.c0;  // width of the G0 slots
+  const int F = W0 + M.c1;
   const SB S(K);
   float* sw = smem;
   float* sg = smem + S.g;
@@ -254,7 +256,7 @@ __global__ void __launch_bounds__(kThreads, 1) backward_simt_kernel(const ntc_ma
   float* z1row = smem + S.z1 + tid * (kHidden + 1);
   float* z2row = smem + S.z2 + tid * (kHidden + 1);
   float* d3row = smem + S.d3 + tid * (kMaxC + 1);
-  float* dxrow = smem + S.dx + tid * (NTC_MAX_FEATURES + 1);
+  float* dxrow = smem + S.dx + tid * (K + 1);
   RowSink sink{xrow};
   float loss_acc = 0.f;
   __syncthreads();
@@ -364,11 +366,14 @@ __global__ void __launch_bounds__(kThreads, 1) backward_simt_kernel(const ntc_ma
         float* g = k ? A.g.grid1[j] : A.g.grid0[j];
         if (!g) continue;
         const int c = k ? M.c1 : M.c0;
-        const float* dk = dxrow + (k ? M.c0 : 0);
+        const bool learned = k == 0 && W0 != M.c0;
         const Taps t = bilinear_taps(x, y, wm, hm, k ? Lv.g1_w : Lv.g0_w, k ? Lv.g1_h : Lv.g0_h);
 #pragma unroll
         for (int tp = 0; tp < 4; ++tp) {
-          const float wgt = t.w[tp] * A.grad_scale;
+          // bilinear: the tap's weight on the shared slots; learned
+          // interpolation: the tap's own slots with weight 1
+          const float* dk = dxrow + (k ? W0 : (learned ? tp * c : 0));
+          const float wgt = (learned ? 1.f : t.w[tp]) * A.grad_scale;
           float* gp = g + (size_t)t.cell[tp] * c;
           if ((c & 3) == 0) {
             for (int c4 = 0; 4 * c4 < c; ++c4)

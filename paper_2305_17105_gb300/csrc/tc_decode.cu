@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(kRows* kNWG, 1) decode_tc_kernel(
   __shared__ int wg_abort[kNWG];
   constexpr int KSTEP = Cfg<F8>::KSTEP;
   constexpr uint32_t kCols = kNWG <= 2 ? 256 : 512;  // 128 columns per warpgroup
-  const Plan P(M.c0, M.c1, M.bits0, M.bits1, M.encoding == NTC_GRID_PACKED, F8, FAST);
+  const Plan P(M, F8, FAST);
   uint8_t* sm = smem_raw;
   const int tid = threadIdx.x, warp = tid >> 5;
   const int wg = tid / kRows, row = tid % kRows;
@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(kRows* kNWG, 1) decode_tc_kernel(
     tc::bar_sync(bar_id, kRows);
 
     // ---- layer 2; meanwhile the next tile's X (layer 1 is done with X) -------
-    if (row == 32) issue_layer<F8>(tw, tw + kColH, dsc + 4, kHidden / KSTEP, id64, !F8, tw + kColCst, bar);
+    if (row == 32) issue_layer<F8>(tw, tw + kColH, dsc + kDescW2, kHidden / KSTEP, id64, !F8, tw + kColCst, bar);
     if (FAST) build_fast(P, P, K, sm, nxt, TmemRow{tx});
     else build_generic<F8>(M, P, sm, nxt, TmemRow{tx}, inv_sa[0]);
     cur_valid = nxt.valid;
@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(kRows* kNWG, 1) decode_tc_kernel(
     if (*abort_flag) { aborted = true; break; }
 
     // ---- layer 3 + output ----------------------------------------------
-    if (row == 64) issue_layer<F8>(tw, tw + kColH, dsc + 9, kHidden / KSTEP, id16, !F8, tw + kColCst, bar);
+    if (row == 64) issue_layer<F8>(tw, tw + kColH, dsc + kDescW3, kHidden / KSTEP, id16, !F8, tw + kColCst, bar);
     if (!tc::mbar_wait(bar, phase, kWaitLimit)) *abort_flag = 1;
     phase ^= 1;
     tc::fence_after_sync();
@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(kRows* kNWG, 1) decode_tc_kernel(
 template <bool F8, bool FAST, int kNWG>
 cudaError_t launch_k(const ntc_material& m, const float* uvl, int64_t n, void* out, int out_dtype,
                      int filter, uint64_t jkey, cudaStream_t s) {
-  const Plan P(m.c0, m.c1, m.bits0, m.bits1, m.encoding == NTC_GRID_PACKED, F8, FAST);
+  const Plan P(m, F8, FAST);
   const size_t smem = P.total;
   cudaError_t e = cudaFuncSetAttribute(decode_tc_kernel<F8, FAST, kNWG>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -272,9 +272,10 @@ cudaError_t launch_decode_tc(const ntc_material& m, const float* uvl, int64_t n,
   if (m.precision == NTC_PREC_F8)
     return launch_shape<true, false>(m, uvl, n, out, out_dtype, filter, jkey, s, nwg == 5 ? 4 : nwg);
   if (m.precision != NTC_PREC_F16) return cudaErrorInvalidValue;
-  const Plan P(m.c0, m.c1, m.bits0, m.bits1, m.encoding == NTC_GRID_PACKED, false,
-               fast_layout_ok(m));
-  if (nwg == 5) return launch_decode_ws(m, uvl, n, out, out_dtype, filter, jkey, s, P.fast != 0);
+  const Plan P(m, false, fast_layout_ok(m));
+  // the warpgroup-pipeline kernel keeps X in 24 TMEM columns (K <= 48)
+  if (nwg == 5 || P.k_int > 48)
+    return launch_decode_ws(m, uvl, n, out, out_dtype, filter, jkey, s, P.fast != 0);
   if (P.fast) return launch_shape<false, true>(m, uvl, n, out, out_dtype, filter, jkey, s, nwg);
   return launch_shape<false, false>(m, uvl, n, out, out_dtype, filter, jkey, s, nwg);
 }

@@ -27,6 +27,9 @@ constexpr int kColH = 64;              // FP16: 32 columns (64 halves); FP8: 16
 constexpr int kColX = 96;              // FP16: up to 24 columns (48 halves); FP8: 16
 constexpr int kColCst = 120;           // FP16: 8 columns
 constexpr uint32_t kWaitLimit = 1u << 18;  // suspended tries: ms to seconds
+// Shared-memory B descriptor table: W1 K-steps [0, 8) (K <= 128), W2 [8, 12),
+// its bias block 12, W3 [13, 17), its bias block 17.
+constexpr int kDescW2 = 8, kDescW3 = 13, kDescs = 18;
 
 template <bool F8>
 struct Cfg {
@@ -52,12 +55,17 @@ struct MipTab {
 
 // Input-row layout and shared memory plan (byte offsets).
 struct Plan {
-  int fast, eo0, eo1, t0, t1, f0, f1, gpe, k_int, cb0, cb1;
+  int fast, learned, eo0, eo1, t0, t1, f0, f1, gpe, k_int, cb0, cb1;
   uint32_t w1, w2, w3, wb2, wb3, bias, tab, pe, desc, total;
   // `taps_ok`: every grid/mip size ratio puts the taps on the 1/16 lattice and
   // the bin widths are powers of two (fast_layout_ok).
-  __host__ __device__ Plan(int c0, int c1, int bits0, int bits1, bool packed, bool f8,
-                           bool taps_ok) {
+  __host__ __device__ Plan(const ntc_material& M, bool f8, bool taps_ok) {
+    const int c0 = M.c0, c1 = M.c1, bits0 = M.bits0, bits1 = M.bits1;
+    const bool packed = M.encoding == NTC_GRID_PACKED;
+    // learned interpolation of G0 (Sec. 4.3.1): the generic layout with one
+    // group range per tap
+    learned = M.interp0 != 0;
+    if (learned) taps_ok = false;
     const int eb = f8 ? 1 : 2, kstep = f8 ? 32 : 16;
     cb0 = cb1 = 0;
     if (packed) {
@@ -77,7 +85,7 @@ struct Plan {
       f0 = f1 = 0;
       gpe = eo0 + eo1 + ((t0 | t1) ? 1 : 0);
     } else {
-      f0 = (c0 + 7) / 8;
+      f0 = (learned ? 4 : 1) * ((c0 + 7) / 8);
       f1 = (c1 + 7) / 8;
       gpe = f0 + f1;
     }
@@ -92,7 +100,7 @@ struct Plan {
     o = (o + 15) / 16 * 16;
     tab = o;  o += sizeof(MipTab);
     pe = o;   o += 8 * 16;                        // per x & 7: half2 (sin, cos) of 3 octaves, 0
-    desc = o; o += 16 * 8;                        // B descriptors: W1 0-3, W2 4-7, b2 8, W3 9-12, b3 13
+    desc = o; o += kDescs * 8;                    // B descriptors: W1 0-7, W2 8-11, b2 12, W3 13-16, b3 17
     total = o;
   }
 };
@@ -134,12 +142,20 @@ __device__ __forceinline__ int w1_column(const ntc_material& M, const Plan& P, i
       g -= 1;
     }
   } else {
-    if (g < P.f0) return 8 * g + e < M.c0 ? 8 * g + e : -1;
+    if (g < P.f0) {
+      if (P.learned) {
+        // tap t's c0 values in groups [t f0t, (t+1) f0t); user columns t c0 + ch
+        const int f0t = (M.c0 + 7) / 8, tap = g / f0t, ch = 8 * (g - tap * f0t) + e;
+        return ch < M.c0 ? tap * M.c0 + ch : -1;
+      }
+      return 8 * g + e < M.c0 ? 8 * g + e : -1;
+    }
     g -= P.f0;
-    if (g < P.f1) return 8 * g + e < M.c1 ? M.c0 + 8 * g + e : -1;
+    const int w0 = P.learned ? 4 * M.c0 : M.c0;
+    if (g < P.f1) return 8 * g + e < M.c1 ? w0 + 8 * g + e : -1;
     g -= P.f1;
   }
-  const int pe = M.c0 + M.c1;
+  const int pe = (P.learned ? 4 * M.c0 : M.c0) + M.c1;
   if (g == 0) return pe + e;
   if (g == 1) {
     if (e < 4) return pe + 8 + e;
@@ -256,11 +272,11 @@ __device__ void stage_shared(const ntc_material& M, const Plan& P, uint8_t* sm, 
     const uint32_t sb = tc::smem_u32(sm);
     for (int k = 0; k < P.k_int / KS; ++k) d[k] = tc::smem_desc(sb + P.w1 + 2 * k * lbo, lbo, 128);
     for (int k = 0; k < kHidden / KS; ++k) {
-      d[4 + k] = tc::smem_desc(sb + P.w2 + 2 * k * lbo, lbo, 128);
-      d[9 + k] = tc::smem_desc(sb + P.w3 + 2 * k * lbo3, lbo3, 128);
+      d[kDescW2 + k] = tc::smem_desc(sb + P.w2 + 2 * k * lbo, lbo, 128);
+      d[kDescW3 + k] = tc::smem_desc(sb + P.w3 + 2 * k * lbo3, lbo3, 128);
     }
-    d[8] = tc::smem_desc(sb + P.wb2, lbo, 128);
-    d[13] = tc::smem_desc(sb + P.wb3, lbo3, 128);
+    d[kDescW2 + 4] = tc::smem_desc(sb + P.wb2, lbo, 128);
+    d[kDescW3 + 4] = tc::smem_desc(sb + P.wb3, lbo3, 128);
   }
 }
 
@@ -578,6 +594,37 @@ __device__ __forceinline__ void generic_grid(const ntc_material& M, const MipTab
   const int c = k ? M.c1 : M.c0;
   const float q = k ? M.q1 : M.q0;
   const int m = r.m;
+  if (k == 0 && P.learned) {
+    // learned interpolation: each tap's dequantised values, unweighted
+    const int f0t = (c + 7) / 8;
+    Taps t;
+    taps_of(r.x, r.y, tb->sx0[m], tb->sy0[m], tb->g0w[m], tb->g0h[m], t);
+    const uint8_t* base = tb->grid0[m];
+#pragma unroll 1
+    for (int tp = 0; tp < 4; ++tp) {
+      float acc[kMaxGridCh];
+      if (M.encoding == NTC_GRID_PACKED) {
+        const int off = (1 << (M.bits0 - 1)) - 1;
+        const Cell cl = load_cell(base, r.valid ? t.cell[tp] : 0, P.cb0);
+#pragma unroll
+        for (int ch = 0; ch < kMaxGridCh; ++ch)
+          acc[ch] = ch < c ? (float)((int)cell_index(cl, ch, M.bits0) - off) * q : 0.f;
+      } else {
+        const float* g = reinterpret_cast<const float*>(base) + (size_t)(r.valid ? t.cell[tp] : 0) * c;
+#pragma unroll
+        for (int ch = 0; ch < kMaxGridCh; ++ch) acc[ch] = ch < c ? __ldg(g + ch) : 0.f;
+      }
+#pragma unroll
+      for (int g2 = 0; g2 < 2; ++g2)
+        if (g2 < f0t) {
+          float v[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) v[e] = r.valid ? acc[8 * g2 + e] : 0.f;
+          put_group<F8>(dst, kg0 + tp * f0t + g2, v, inv_sa);
+        }
+    }
+    return;
+  }
   float acc[kMaxGridCh];
 #pragma unroll
   for (int ch = 0; ch < kMaxGridCh; ++ch) acc[ch] = 0.f;

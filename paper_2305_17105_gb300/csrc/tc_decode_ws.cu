@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) decode_ws_kernel(
   __shared__ int wg_abort[kWsCompute];
   constexpr bool FAST = CLS > 0;
   const FastLayout<FAST ? CLS : 1> lay;
-  const Plan P(M.c0, M.c1, M.bits0, M.bits1, M.encoding == NTC_GRID_PACKED, false, FAST);
+  const Plan P(M, false, FAST);
   const WsPlan W(P);
   uint8_t* sm = smem_raw;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -108,15 +108,15 @@ __global__ void __launch_bounds__(kWsThreads, 1) decode_ws_kernel(
         ph ^= 1;
         tc::fence_after_sync();
         for (int s = 0; s < kHidden / 16; ++s)
-          tc::mma_f16_ta(tw, tw + kColH + 8 * s, d[4 + s], id64, s > 0);
-        tc::mma_f16(tw, cst, d[8], id64, 1);
+          tc::mma_f16_ta(tw, tw + kColH + 8 * s, d[kDescW2 + s], id64, s > 0);
+        tc::mma_f16(tw, cst, d[kDescW2 + 4], id64, 1);
         tc::mma_commit(&bar_d[w]);
         if (!(ok = tc::mbar_wait(&bar_h[w], ph, kWaitLimit))) break;
         ph ^= 1;
         tc::fence_after_sync();
         for (int s = 0; s < kHidden / 16; ++s)
-          tc::mma_f16_ta(tw + kColD3, tw + kColH + 8 * s, d[9 + s], id16, s > 0);
-        tc::mma_f16(tw + kColD3, cst, d[13], id16, 1);
+          tc::mma_f16_ta(tw + kColD3, tw + kColH + 8 * s, d[kDescW3 + s], id16, s > 0);
+        tc::mma_f16(tw + kColD3, cst, d[kDescW3 + 4], id16, 1);
         tc::mma_commit(&bar_o[w]);
       }
       if (!ok) *reinterpret_cast<volatile int*>(&wg_abort[w]) = 1;
@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) decode_ws_kernel(
 template <int CLS>
 cudaError_t launch_ws(const ntc_material& m, const float* uvl, int64_t n, void* out, int out_dtype,
                       int filter, uint64_t jkey, cudaStream_t s) {
-  const Plan P(m.c0, m.c1, m.bits0, m.bits1, m.encoding == NTC_GRID_PACKED, false, CLS > 0);
+  const Plan P(m, false, CLS > 0);
   const WsPlan W(P);
   cudaError_t e = cudaFuncSetAttribute(decode_ws_kernel<CLS>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)W.total);
@@ -270,12 +270,15 @@ int grid_class(int c, int cb) { return cb == 4 ? 0 : (c > 12 ? 2 : 1); }
 //   0 generic layout, 1..9 one compile-time fast class for the whole batch.
 // ---------------------------------------------------------------------------
 struct WsBatchSmem {
-  uint32_t region, cst, x, total;  // per-warpgroup region size; offsets
-  __host__ __device__ explicit WsBatchSmem(uint32_t plan_bytes) {
+  uint32_t region, cst, x, xbytes, total;  // per-warpgroup region size; offsets
+  // packed: plan bytes of the largest material | largest internal K << 24
+  __host__ __device__ explicit WsBatchSmem(uint32_t packed) {
+    const uint32_t plan_bytes = packed & 0xFFFFFFu, kmax = packed >> 24;
     region = (plan_bytes + 1023) / 1024 * 1024;
     cst = kWsCompute * region;
     x = cst + kRows * 16 * 2;
-    total = x + kWsCompute * kRows * 48 * 2;  // K <= 48 for FP16 operands
+    xbytes = kRows * kmax * 2;
+    total = x + kWsCompute * xbytes;
   }
 };
 
@@ -329,7 +332,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) decode_ws_batched_kernel(
   constexpr uint32_t id64 = tc::idesc(kRows, kHidden), id16 = tc::idesc(kRows, kN3);
   const uint32_t tw = tmem_base + 128u * w;
   uint8_t* region = smem_raw + (size_t)w * S.region;
-  uint8_t* xtile = smem_raw + S.x + (size_t)w * kRows * 48 * 2;
+  uint8_t* xtile = smem_raw + S.x + (size_t)w * S.xbytes;
 
   if (wg == kWsCompute) {
     // ---- issuer warp w ------------------------------------------------------
@@ -352,15 +355,15 @@ __global__ void __launch_bounds__(kWsThreads, 1) decode_ws_batched_kernel(
         ph ^= 1;
         tc::fence_after_sync();
         for (int s = 0; s < kHidden / 16; ++s)
-          tc::mma_f16_ta(tw, tw + kColH + 8 * s, d[4 + s], id64, s > 0);
-        tc::mma_f16(tw, cst, d[8], id64, 1);
+          tc::mma_f16_ta(tw, tw + kColH + 8 * s, d[kDescW2 + s], id64, s > 0);
+        tc::mma_f16(tw, cst, d[kDescW2 + 4], id64, 1);
         tc::mma_commit(&bar_d[w]);
         if (!(ok = tc::mbar_wait(&bar_h[w], ph, kWaitLimit))) break;
         ph ^= 1;
         tc::fence_after_sync();
         for (int s = 0; s < kHidden / 16; ++s)
-          tc::mma_f16_ta(tw + kColD3, tw + kColH + 8 * s, d[9 + s], id16, s > 0);
-        tc::mma_f16(tw + kColD3, cst, d[13], id16, 1);
+          tc::mma_f16_ta(tw + kColD3, tw + kColH + 8 * s, d[kDescW3 + s], id16, s > 0);
+        tc::mma_f16(tw + kColD3, cst, d[kDescW3 + 4], id16, 1);
         tc::mma_commit(&bar_o[w]);
       }
       if (!ok) *reinterpret_cast<volatile int*>(&wg_abort[w]) = 1;
@@ -377,7 +380,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) decode_ws_batched_kernel(
     const ntc_material& M = mat_s[w];
     // the current material: its plan, its tile range and query/output bases
     int mid = 0;
-    Plan P(1, 1, 4, 4, true, false, false);
+    Plan P(mat_s[w], false, false);
     int64_t m_t0 = 0, m_t1 = 0, m_q0 = 0, m_nq = 0, m_o0 = 0;
     // stage material `mid` (no MMA of this warpgroup in flight, no thread
     // still reading the region)
@@ -386,7 +389,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) decode_ws_batched_kernel(
       tc::bar_sync(bar_id, kRows);
       if (row == 0) mat_s[w] = B->mats[id];
       tc::bar_sync(bar_id, kRows);
-      P = Plan(M.c0, M.c1, M.bits0, M.bits1, M.encoding == NTC_GRID_PACKED, false, FAST);
+      P = Plan(M, false, FAST);
       stage_shared<false>(M, P, region, row, kRows);
       zero_tail_groups<false>(P, xs);
       if (row == 0) {
@@ -558,16 +561,16 @@ cudaError_t launch_ws_batched(const BatchHeader* dev, int64_t total_tiles, uint3
 }  // namespace
 
 int fast_class(const ntc_material& m) {
-  const Plan P(m.c0, m.c1, m.bits0, m.bits1, m.encoding == NTC_GRID_PACKED, false,
-               fast_layout_ok(m));
+  const Plan P(m, false, fast_layout_ok(m));
   if (!P.fast) return 0;
   return 1 + 3 * grid_class(m.c0, P.cb0) + grid_class(m.c1, P.cb1);
 }
 
 uint32_t ws_plan_bytes(const ntc_material& m, bool fast) {
-  return Plan(m.c0, m.c1, m.bits0, m.bits1, m.encoding == NTC_GRID_PACKED, false, fast).total;
+  const Plan P(m, false, fast);
+  return P.total | ((uint32_t)P.k_int << 24);
 }
-uint32_t ws_batched_smem(uint32_t plan_bytes) { return WsBatchSmem(plan_bytes).total; }
+uint32_t ws_batched_smem(uint32_t packed) { return WsBatchSmem(packed).total; }
 
 cudaError_t launch_decode_ws_batched(const BatchHeader* dev, int64_t total_tiles,
                                      uint32_t plan_bytes, int cls, const float* uvl, void* out,
@@ -583,7 +586,7 @@ cudaError_t launch_decode_ws_batched(const BatchHeader* dev, int64_t total_tiles
 cudaError_t launch_decode_ws(const ntc_material& m, const float* uvl, int64_t n, void* out,
                              int out_dtype, int filter, uint64_t jkey, cudaStream_t s, bool fast) {
   if (!fast) return launch_ws<0>(m, uvl, n, out, out_dtype, filter, jkey, s);
-  const Plan P(m.c0, m.c1, m.bits0, m.bits1, true, false, true);
+  const Plan P(m, false, true);
   switch (1 + 3 * grid_class(m.c0, P.cb0) + grid_class(m.c1, P.cb1)) {
     case 1: return launch_ws<1>(m, uvl, n, out, out_dtype, filter, jkey, s);
     case 2: return launch_ws<2>(m, uvl, n, out, out_dtype, filter, jkey, s);

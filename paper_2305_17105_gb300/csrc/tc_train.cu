@@ -643,7 +643,9 @@ __global__ void __launch_bounds__(kRows* kNWG, 1) train_tc_kernel(const ntc_mate
 
 cudaError_t launch_train_tc(const ntc_material& m, const BwdArgs& a, cudaStream_t s) {
   if (a.n == 0) return cudaSuccess;
-  if (m.precision != NTC_PREC_F16 || m.act != NTC_ACT_RELU || !a.train) return cudaErrorNotSupported;
+  if (m.precision != NTC_PREC_F16 || m.act != NTC_ACT_RELU || m.interp0 != NTC_INTERP_BILINEAR ||
+      !a.train)
+    return cudaErrorNotSupported;
   const TPlan P(m.c0, m.c1);
   const size_t smem = P.total;
   cudaError_t e = cudaFuncSetAttribute(train_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

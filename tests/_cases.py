@@ -36,6 +36,7 @@ class Case:
     val0: list              # per level float32 values
     val1: list
     weights: list           # [w1, b1, w2, b2, w3, b3] float32
+    interp0: int = 0        # G0 resampling: 0 bilinear, 1 learned (4 taps concatenated)
 
     @property
     def mips(self):
@@ -61,15 +62,15 @@ class Case:
         w = self.weights if weights is None else weights
         return oracle.Model(self.width, self.height, self.channels, self.c0, self.c1, self.n0,
                             self.n1, self.q0, self.q1, g0, g1, [np.asarray(a, np.float64) for a in w],
-                            self.k_in, self.hidden, self.act, self.out_act)
+                            self.k_in, self.hidden, self.act, self.out_act, self.interp0)
 
 
 def make_case(width=64, height=64, channels=8, c0=8, c1=8, bits0=4, bits1=4, q0=None, q1=None,
-              k_in=None, hidden=64, act=0, out_act=0, seed=0, wgain=1.0):
+              k_in=None, hidden=64, act=0, out_act=0, seed=0, wgain=1.0, interp0=0):
     n0, n1 = 1 << bits0, 1 << bits1
     q0 = 1.0 / n0 if q0 is None else q0
     q1 = 1.0 / n1 if q1 is None else q1
-    used = c0 + c1 + 13
+    used = (4 * c0 if interp0 else c0) + c1 + 13
     if k_in is None:
         k_in = (used + 15) // 16 * 16
     rng = np.random.default_rng(1000 + seed)
@@ -84,7 +85,7 @@ def make_case(width=64, height=64, channels=8, c0=8, c1=8, bits0=4, bits1=4, q0=
         val1.append(gen.uniform_grid_values((g1h, g1w, c1), lo1, hi1, rng))
     weights = gen.random_mlp(k_in, hidden, channels, 2000 + seed, n_used=used, gain=wgain)
     return Case(width, height, channels, c0, c1, bits0, bits1, q0, q1, k_in, hidden, act, out_act,
-                levels, idx0, idx1, val0, val1, weights)
+                levels, idx0, idx1, val0, val1, weights, interp0)
 
 
 # The five workload shapes (sizes of the paper-shaped synthetic workloads).

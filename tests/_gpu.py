@@ -49,7 +49,7 @@ def device_material(case, precision=ntc.PREC_F32, packed=True):
     b = [_t(case.weights[1]), _t(case.weights[3]), _t(case.weights[5])]
     mat = ntc.Material(case.width, case.height, case.channels, case.c0, case.c1, case.bits0,
                        case.bits1, case.q0, case.q1, g0, g1, wdev, b, case.k_in, precision,
-                       case.act, case.out_act)
+                       case.act, case.out_act, interp0=case.interp0)
     md = case.oracle_model(weights=wor, quantized=packed)
     return mat, md
 

@@ -1,0 +1,123 @@
+"""Learned interpolation of G0 (Sec. 4.3.1): the four G0 taps concatenated in
+the MLP input (the paper's decoder input, 4 c0 + c1 + 13 values) with the
+paper's hardGELU and identity output.  Parity with the FP64 oracle of the
+same model: FP32 form (decode and gradients), FP16 tensor-core decode
+(nearest, trilinear, stochastic; warp-specialised and batched launches)."""
+import numpy as np
+import pytest
+import torch
+
+import ntc_inputs as gen
+import oracle
+import paper_2305_17105_gb300 as ntc
+from _cases import make_case
+from _gpu import DEV, device_material, rel_err, to_np
+
+pytestmark = pytest.mark.gpu
+OUT_TOL = 2e-3
+
+# (c0 x b0, c1 x b1) of the paper's four profiles (Sec. 6), at small sides;
+# grids hold at most 16 channels here, so profile 0.5's 20-channel G1 runs with 16
+PROFILES = [
+    dict(width=256, height=256, channels=9, c0=8, c1=12, bits0=2, bits1=4, k_in=64),   # 0.2
+    dict(width=256, height=128, channels=9, c0=12, c1=16, bits0=4, bits1=4, k_in=80),  # 0.5 (G1 16 of 20)
+    dict(width=128, height=128, channels=9, c0=12, c1=10, bits0=2, bits1=4, k_in=80),  # 1.0
+    dict(width=256, height=256, channels=9, c0=16, c1=12, bits0=4, bits1=4, k_in=96),  # 2.25
+]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ntc.lib()
+
+
+def _uvl(q):
+    return torch.from_numpy(np.ascontiguousarray(q, np.float32)).to(DEV)
+
+
+def _queries(md, n, seed):
+    rng = np.random.default_rng(seed)
+    q = np.empty((n, 3), np.float32)
+    q[:, :2] = rng.random((n, 2))
+    q[:, 2] = rng.uniform(-0.5, md.mips + 0.5, n)
+    return q
+
+
+@pytest.mark.parametrize("shape", PROFILES)
+def test_learned_decode_fp32_matches_oracle(shape):
+    case = make_case(seed=91, act=1, out_act=1, interp0=1, **shape)
+    mat, md = device_material(case)
+    q = _queries(md, 1500, 4091)
+    for filt, ref in ((ntc.FILTER_NEAREST, md.decode(q)), (ntc.FILTER_TRILINEAR, md.decode_trilinear(q)),
+                      (ntc.FILTER_STOCHASTIC, md.decode_stochastic(q, 4, 2))):
+        got = to_np(ntc.ntc_decode(mat, _uvl(q), filter=filt, noise_seed=4, noise_step=2))
+        assert np.abs(got - ref).max() < 2e-5, filt
+
+
+@pytest.mark.parametrize("shape", PROFILES)
+def test_learned_decode_f16_matches_oracle(shape):
+    case = make_case(seed=92, act=1, out_act=1, interp0=1, **shape)
+    mat, md = device_material(case, precision=ntc.PREC_F16)
+    q = _queries(md, 7 * 128 + 41, 4092)
+    for nwg in (0, 4):  # shape 4 routes K > 48 to the warp-specialised kernel too
+        ntc.ntc_set_decode_warpgroups(nwg)
+        try:
+            for filt, ref in ((ntc.FILTER_NEAREST, md.decode(q)),
+                              (ntc.FILTER_TRILINEAR, md.decode_trilinear(q))):
+                got = to_np(ntc.ntc_decode(mat, _uvl(q), filter=filt))
+                assert ntc.ntc_device_status() == ntc.OK
+                assert np.abs(got - ref).max() <= OUT_TOL, (nwg, filt)
+        finally:
+            ntc.ntc_set_decode_warpgroups(0)
+
+
+def test_learned_and_bilinear_in_one_batch():
+    a = make_case(seed=93, act=1, out_act=1, interp0=1, **PROFILES[1])
+    b = make_case(128, 128, 8, 12, 12, k_in=48, seed=94)
+    mats = [device_material(a, precision=ntc.PREC_F16), device_material(b, precision=ntc.PREC_F16)]
+    qs = [_queries(mats[0][1], 777, 4093), _queries(mats[1][1], 555, 4094)]
+    batch = ntc.Batch([m for m, _ in mats], [len(q) for q in qs])
+    out = to_np(ntc.ntc_decode_batched(batch, _uvl(np.concatenate(qs))))
+    assert ntc.ntc_device_status() == ntc.OK
+    for i, ((m, md), q) in enumerate(zip(mats, qs)):
+        got = out[batch.o_offsets[i]:batch.o_offsets[i + 1]].reshape(len(q), m.channels)
+        assert np.abs(got - md.decode(q)).max() <= OUT_TOL, i
+
+
+def test_learned_gradients_fp32_match_oracle():
+    """FP32 fused step with learned interpolation (K <= 64): gradients of
+    every tensor against the oracle's reverse mode, noise on."""
+    case = make_case(64, 64, 5, 8, 4, k_in=64, act=1, out_act=1, seed=95, interp0=1)
+    chain = gen.box_mip_chain_u8(gen.synthetic_texture(64, 64, 5, seed=1095))
+    w = case.weights
+    tr = ntc.Trainer(64, 64, 5, 8, 4, 4, 4, case.q0, case.q1, case.val0, case.val1,
+                     [w[0], w[2], w[4]], [w[1], w[3], w[5]], 64, ntc.PREC_F32, act=1, out_act=1,
+                     total_steps=10)
+    tr.material.interp0 = 1
+    tr.step_t.fill_(2)
+    target = ntc.Target(chain)
+    batch, seed = 3 * 128 + 9, 515
+    ntc.ntc_train_step(tr, target, batch, seed, flags=ntc.FLAG_GRAD_ONLY | ntc.FLAG_SIMT)
+    torch.cuda.synchronize()
+    assert ntc.ntc_device_status() == ntc.OK
+    md = case.oracle_model(quantized=False)
+    xym = oracle.sample_batch(seed, 2, batch, 64, 64, md.mips)
+    t = oracle.targets_of_xym(chain, xym)
+    _, g = md.loss_grad_xym(xym, t, noise=(seed, 2))
+    for got, ref in zip(tr.grad_views[:len(md.grids0)], g["grid0"]):
+        assert rel_err(to_np(got), ref) < 1e-2
+    for got, ref in zip(tr.grad_views[2 * len(md.grids0)::2], g["w"][0::2]):
+        assert rel_err(to_np(got), ref) < 1e-2
+
+
+def test_learned_tensor_core_training_is_refused():
+    case = make_case(64, 64, 5, 8, 4, k_in=64, seed=96, interp0=1)
+    w = case.weights
+    tr = ntc.Trainer(64, 64, 5, 8, 4, 4, 4, case.q0, case.q1, case.val0, case.val1,
+                     [w[0], w[2], w[4]], [w[1], w[3], w[5]], 64, ntc.PREC_F16, total_steps=10)
+    tr.material.interp0 = 1
+    target = ntc.Target(gen.box_mip_chain_u8(gen.synthetic_texture(64, 64, 5, seed=1096)))
+    with pytest.raises(ntc.NTCError):
+        ntc.ntc_train_step(tr, target, 256, 1)

@@ -288,6 +288,50 @@ def test_trilinear_reduces_to_nearest_at_texel_centres():
     assert np.abs(md.decode_trilinear(u) - 0.5 * (lo + hi)).max() < 1e-12
 
 
+def test_learned_interpolation_row_layout():
+    """Learned interpolation of G0 (Sec. 4.3.1): the input row holds the four
+    neighbouring G0 feature vectors (taps (x0,y0), (x1,y0), (x0,y1), (x1,y1)
+    of the bilinear footprint) unweighted, then bilinear G1, PE and LOD; the
+    bilinear G0 value is their combination with the bilinear weights."""
+    case = make_case(64, 64, 3, 4, 6, k_in=48, seed=14, interp0=1)
+    learned = case.oracle_model()
+    case.interp0 = 0
+    bil = case.oracle_model()
+    for x, y, m in [(5, 7, 0), (30, 2, 1), (3, 3, 2), (0, 0, 3)]:
+        r4 = learned.features(x, y, m)
+        r1 = bil.features(x, y, m)
+        taps = r4[:16].reshape(4, 4)
+        wm = 64 >> m
+        g0 = case.idx0[0].shape[1]
+        p = (x + 0.5) / wm * g0 - 0.5
+        py = (y + 0.5) / wm * g0 - 0.5
+        fx, fy = p - np.floor(p), py - np.floor(py)
+        w = np.array([(1 - fx) * (1 - fy), fx * (1 - fy), (1 - fx) * fy, fx * fy])
+        assert np.allclose(w @ taps, r1[:4], atol=1e-12)
+        assert np.array_equal(r4[16:16 + 6 + 13], r1[4:4 + 6 + 13])
+
+
+def test_learned_interpolation_gradients_match_central_differences():
+    case = make_case(16, 16, 3, 2, 2, k_in=32, hidden=8, act=1, seed=15, wgain=2.0, interp0=1)
+    md = case.oracle_model(quantized=False)
+    xym = np.array([[3, 5, 0], [1, 2, 1], [0, 1, 2]], np.int32)
+    dout = np.random.default_rng(16).standard_normal((3, 3))
+    g = md.backward_xym(xym, dout, noise=(3, 1))
+    params = md.grids0 + md.grids1 + md.weights
+    grads = g["grid0"] + g["grid1"] + g["w"]
+    rng = np.random.default_rng(17)
+    for p, gp in zip(params, grads):
+        for _ in range(3):
+            i = tuple(rng.integers(0, s) for s in p.shape)
+            old = p[i]
+            p[i] = old + 1e-6
+            hi = (md.decode_xym(xym, noise=(3, 1)) * dout).sum()
+            p[i] = old - 1e-6
+            lo = (md.decode_xym(xym, noise=(3, 1)) * dout).sum()
+            p[i] = old
+            assert abs((hi - lo) / 2e-6 - gp[i]) <= 1e-6 * max(1.0, abs(gp[i])), (p.shape, i)
+
+
 def test_stochastic_filter_is_nearest_at_texel_centres():
     """Stochastic filtering (Sec. 5.3) at texel centres with integer LODs: the
     jitter xi in [0, 1) never leaves the texel or the mip, for any frame."""
