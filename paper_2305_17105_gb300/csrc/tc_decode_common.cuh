@@ -65,7 +65,6 @@ struct Plan {
     // learned interpolation of G0 (Sec. 4.3.1): the generic layout with one
     // group range per tap
     learned = M.interp0 != 0;
-    if (learned) taps_ok = false;
     const int eb = f8 ? 1 : 2, kstep = f8 ? 32 : 16;
     cb0 = cb1 = 0;
     if (packed) {
@@ -83,7 +82,9 @@ struct Plan {
       t0 = (cb0 == 8 && c0 <= 12) ? 1 : 0;
       t1 = (cb1 == 8 && c1 <= 12) ? 1 : 0;
       f0 = f1 = 0;
-      gpe = eo0 + eo1 + ((t0 | t1) ? 1 : 0);
+      // learned interpolation: each G0 tap's words, the tail halves of taps
+      // (0,1) and (2,3) sharing a group, G1's tail half alone
+      gpe = learned ? 4 * eo0 + 2 * t0 + eo1 + t1 : eo0 + eo1 + ((t0 | t1) ? 1 : 0);
     } else {
       f0 = (learned ? 4 : 1) * ((c0 + 7) / 8);
       f1 = (c1 + 7) / 8;
@@ -122,7 +123,31 @@ __device__ __forceinline__ int w1_column(const ntc_material& M, const Plan& P, i
   int g = s >> 3;
   const int e = s & 7;
   const int j = e >> 1, l = e & 1;  // half2 j of the group, lane l
-  if (P.fast) {
+  if (P.fast && P.learned) {
+    const int eo = 2 * (j & 1) + (j >> 1) + 4 * l;
+    if (g < 4 * P.eo0) {  // tap g / eo0, word g % eo0
+      const int tap = g / P.eo0, ch = 8 * (g - tap * P.eo0) + eo;
+      return ch < M.c0 ? tap * M.c0 + ch : -1;
+    }
+    g -= 4 * P.eo0;
+    if (P.t0) {
+      if (g < 2) {  // tail halves (lo T, hi T) = channels (8,9) (10,11) of taps 2g, 2g+1
+        const int tap = 2 * g + (j >> 1), ch = 8 + 2 * (j & 1) + l;
+        return ch < M.c0 ? tap * M.c0 + ch : -1;
+      }
+      g -= 2;
+    }
+    const int w0 = 4 * M.c0;
+    if (g < P.eo1) return 8 * g + eo < M.c1 ? w0 + 8 * g + eo : -1;
+    g -= P.eo1;
+    if (P.t1) {
+      if (g == 0) {
+        const int ch = 8 + 2 * (j & 1) + l;
+        return j < 2 && ch < M.c1 ? w0 + ch : -1;
+      }
+      g -= 1;
+    }
+  } else if (P.fast) {
     // 5-8 channel word: half2 (lo E, hi E, lo O, hi O) = channels (0,4) (2,6) (1,5) (3,7)
     const int eo = 2 * (j & 1) + (j >> 1) + 4 * l;
     if (g < P.eo0) return 8 * g + eo < M.c0 ? 8 * g + eo : -1;
@@ -433,6 +458,7 @@ struct FastLayout {
   static constexpr int k0 = (CLS - 1) / 3, k1 = (CLS - 1) % 3;
   static constexpr int eo0 = k0 == 2 ? 2 : 1, t0 = k0 == 1 ? 1 : 0, cb0 = k0 == 0 ? 4 : 8;
   static constexpr int eo1 = k1 == 2 ? 2 : 1, t1 = k1 == 1 ? 1 : 0, cb1 = k1 == 0 ? 4 : 8;
+  static constexpr int learned = 0;
 };
 
 // Issue the eight cell loads of a fast-layout row (invalid rows load nothing).
@@ -526,14 +552,16 @@ __device__ __forceinline__ void pe_groups(const Plan& P, const uint8_t* sm, uint
 
 // Per-grid FP16 constants of the fast layout.
 struct FastK {
-  __half2 s[2], s16[2], m7q[2];
+  __half2 s[2], s16[2], m7q[2], q[2], o1031[2];
   __device__ FastK(const ntc_material& M) {
-    const float q[2] = {M.q0, M.q1};
+    const float qq[2] = {M.q0, M.q1};
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
-      s[k] = __float2half2_rn(q[k] * (1.f / 256.f));
-      s16[k] = __float2half2_rn(q[k] * (16.f / 256.f));
-      m7q[k] = __float2half2_rn(-7.f * q[k]);
+      s[k] = __float2half2_rn(qq[k] * (1.f / 256.f));
+      s16[k] = __float2half2_rn(qq[k] * (16.f / 256.f));
+      m7q[k] = __float2half2_rn(-7.f * qq[k]);
+      q[k] = __float2half2_rn(qq[k]);
+      o1031[k] = __float2half2_rn(-1031.f * qq[k]);
     }
   }
 };
@@ -543,9 +571,51 @@ template <class L, class S>
 __device__ __forceinline__ void build_fast(const L& lay, const Plan& P, const FastK& K,
                                            const uint8_t* sm, const Row& r, const S& dst) {
   const uint32_t fx0 = r.frac & 15, fx1 = (r.frac >> 8) & 15;
-  const YLerp y0 = ylerp_of((r.frac >> 4) & 15, K.s[0], K.s16[0], K.m7q[0]);
   const YLerp y1 = ylerp_of((r.frac >> 12) & 15, K.s[1], K.s16[1], K.m7q[1]);
   int kg = 0;
+  if (lay.learned) {
+    // learned interpolation of G0: every tap's channels, dequantised as
+    // (1024 + q) Q - 1031 Q = (q - 7) Q in one FMA (exact for power-of-two Q)
+    const __half2 q2 = K.q[0], o2 = K.o1031[0];
+    const uint32_t kk = 0x64646464u;
+    auto dq = [&](uint32_t a, uint32_t sel) { return h2u(__hfma2(u2h(__byte_perm(a, kk, sel)), q2, o2)); };
+    uint32_t tl[4][2];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+#pragma unroll
+      for (int f = 0; f < 2; ++f)
+        if (f < lay.eo0) {
+          const uint32_t w = word_of(r.c0[t], f);
+          const uint32_t e = w & 0x0F0F0F0Fu, o = (w >> 4) & 0x0F0F0F0Fu;
+          dst.put4(kg++, make_uint4(dq(e, 0x4240u), dq(e, 0x4341u), dq(o, 0x4240u), dq(o, 0x4341u)));
+        }
+      if (lay.t0) {
+        const uint32_t tw = __byte_perm(r.c0[t].y, r.c0[t].y << 12, 0x7610u) & 0x0F0F0F0Fu;
+        tl[t][0] = dq(tw, 0x4240u);
+        tl[t][1] = dq(tw, 0x4341u);
+      }
+    }
+    if (lay.t0) {
+      dst.put4(kg++, make_uint4(tl[0][0], tl[0][1], tl[1][0], tl[1][1]));
+      dst.put4(kg++, make_uint4(tl[2][0], tl[2][1], tl[3][0], tl[3][1]));
+    }
+#pragma unroll
+    for (int f = 0; f < 2; ++f)
+      if (f < lay.eo1) {
+        const uint32_t w[4] = {word_of(r.c1[0], f), word_of(r.c1[1], f), word_of(r.c1[2], f),
+                               word_of(r.c1[3], f)};
+        dst.put4(kg++, eo_group(w, 16 - fx1, fx1, y1));
+      }
+    if (lay.t1) {
+      const uint32_t w[4] = {r.c1[0].y, r.c1[1].y, r.c1[2].y, r.c1[3].y};
+      const uint2 b = t_half(w, 16 - fx1, fx1, y1);
+      dst.put4(kg++, make_uint4(b.x, b.y, 0u, 0u));
+    }
+    const MipTab* tb = reinterpret_cast<const MipTab*>(sm + P.tab);
+    pe_groups(P, sm, tb->lodh[r.m], r.x, r.y, dst);
+    return;
+  }
+  const YLerp y0 = ylerp_of((r.frac >> 4) & 15, K.s[0], K.s16[0], K.m7q[0]);
 #pragma unroll
   for (int f = 0; f < 2; ++f)
     if (f < lay.eo0) {
@@ -746,6 +816,12 @@ __device__ __forceinline__ void store_texel(void* out, int out_dtype, int64_t q,
   }
 }
 
+// hardGELU (Sec. 4.4) as z * clamp(z/3 + 1/2, 0, 1): one saturating FMA and
+// one multiply, the same function as its three-piece definition.
+__device__ __forceinline__ float hardgelu_sat(float z) {
+  return z * __saturatef(fmaf(z, 1.f / 3.f, 0.5f));
+}
+
 // FP16 hidden-layer epilogue in quarters of 16 accumulators (a smaller
 // register footprint, for the warp-specialised kernel's compute warps).
 __device__ __forceinline__ void hidden_epilogue_q(uint32_t td, uint32_t ta, int act) {
@@ -760,7 +836,7 @@ __device__ __forceinline__ void hidden_epilogue_q(uint32_t td, uint32_t ta, int 
       for (int i = 0; i < 8; ++i) w[i] = tc::pack_f16x2_relu(a[2 * i], a[2 * i + 1]);
     } else {
 #pragma unroll
-      for (int i = 0; i < 8; ++i) w[i] = tc::pack_f16x2(act_fwd(act, a[2 * i]), act_fwd(act, a[2 * i + 1]));
+      for (int i = 0; i < 8; ++i) w[i] = tc::pack_f16x2(hardgelu_sat(a[2 * i]), hardgelu_sat(a[2 * i + 1]));
     }
     tc::tmem_st8(ta + 8 * qtr, w);
   }
@@ -800,7 +876,7 @@ __device__ __forceinline__ void hidden_epilogue(uint32_t td, uint32_t ta, int ac
       } else {
 #pragma unroll
         for (int i = 0; i < 16; ++i)
-          w[i] = tc::pack_f16x2(act_fwd(act, v[2 * i]), act_fwd(act, v[2 * i + 1]));
+          w[i] = tc::pack_f16x2(hardgelu_sat(v[2 * i]), hardgelu_sat(v[2 * i + 1]));
       }
       tc::tmem_st16(ta + 16 * half, w);
     }

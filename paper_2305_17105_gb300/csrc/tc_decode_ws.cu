@@ -45,8 +45,9 @@ __global__ void __launch_bounds__(kWsThreads, 1) decode_ws_kernel(
       bar_o[kWsCompute], bar_fin[kWsCompute];
   __shared__ uint32_t tmem_base;
   __shared__ int wg_abort[kWsCompute];
-  constexpr bool FAST = CLS > 0;
-  const FastLayout<FAST ? CLS : 1> lay;
+  // CLS > 0: compile-time fast class; -1: fast layout with the class read
+  // from the plan (learned interpolation); 0: generic layout
+  constexpr bool FAST = CLS != 0;
   const Plan P(M, false, FAST);
   const WsPlan W(P);
   uint8_t* sm = smem_raw;
@@ -134,7 +135,8 @@ __global__ void __launch_bounds__(kWsThreads, 1) decode_ws_kernel(
     volatile int* abort_flag = &wg_abort[w];
     auto qindex = [&](int64_t t) { return tri ? t * per_tile + (row >> 3) : t * per_tile + row; };
     auto build = [&](const Row& r) {
-      if (FAST) build_fast(lay, P, K, sm, r, xs);
+      if (CLS > 0) build_fast(FastLayout<(CLS > 0 ? CLS : 1)>(), P, K, sm, r, xs);
+      else if (CLS < 0) build_fast(P, P, K, sm, r, xs);
       else build_generic<false>(M, P, sm, r, xs, 1.f);
       tc::fence_proxy_async();
       __syncwarp();
@@ -151,13 +153,15 @@ __global__ void __launch_bounds__(kWsThreads, 1) decode_ws_kernel(
       Row r;
       const int64_t q0 = qindex(tl);
       locate(M, tb, load_query(uvl, q0, q0 < n), filter, row, r, q0, jkey);
-      if (FAST) gather_fast(lay, tb, r);
+      if (CLS > 0) gather_fast(FastLayout<(CLS > 0 ? CLS : 1)>(), tb, r);
+      else if (CLS < 0) gather_fast(P, tb, r);
       build(r);
       cur_valid = r.valid;
       cur_wtap = r.wtap;
       const int64_t q1 = qindex(tl + stride);
       locate(M, tb, load_query(uvl, q1, tl + stride < ntiles && q1 < n), filter, row, nxt, q1, jkey);
-      if (FAST) gather_fast(lay, tb, nxt);
+      if (CLS > 0) gather_fast(FastLayout<(CLS > 0 ? CLS : 1)>(), tb, nxt);
+      else if (CLS < 0) gather_fast(P, tb, nxt);
       const int64_t q2 = qindex(tl + 2 * stride);
       nq = load_query(uvl, q2, tl + 2 * stride < ntiles && q2 < n);
     }
@@ -192,7 +196,8 @@ __global__ void __launch_bounds__(kWsThreads, 1) decode_ws_kernel(
       if (*abort_flag) break;
       // the tile after next: texel and cells; its successor's query
       locate(M, tb, nq, filter, row, nxt, qindex(tl + 2 * stride), jkey);
-      if (FAST) gather_fast(lay, tb, nxt);
+      if (CLS > 0) gather_fast(FastLayout<(CLS > 0 ? CLS : 1)>(), tb, nxt);
+      else if (CLS < 0) gather_fast(P, tb, nxt);
       {
         const int64_t t3 = tl + 3 * stride;
         const int64_t q3 = qindex(t3);
@@ -238,7 +243,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) decode_ws_kernel(
 template <int CLS>
 cudaError_t launch_ws(const ntc_material& m, const float* uvl, int64_t n, void* out, int out_dtype,
                       int filter, uint64_t jkey, cudaStream_t s) {
-  const Plan P(m, false, CLS > 0);
+  const Plan P(m, false, CLS != 0);
   const WsPlan W(P);
   cudaError_t e = cudaFuncSetAttribute(decode_ws_kernel<CLS>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)W.total);
@@ -563,6 +568,7 @@ cudaError_t launch_ws_batched(const BatchHeader* dev, int64_t total_tiles, uint3
 int fast_class(const ntc_material& m) {
   const Plan P(m, false, fast_layout_ok(m));
   if (!P.fast) return 0;
+  if (P.learned) return -1;
   return 1 + 3 * grid_class(m.c0, P.cb0) + grid_class(m.c1, P.cb1);
 }
 
@@ -587,6 +593,7 @@ cudaError_t launch_decode_ws(const ntc_material& m, const float* uvl, int64_t n,
                              int out_dtype, int filter, uint64_t jkey, cudaStream_t s, bool fast) {
   if (!fast) return launch_ws<0>(m, uvl, n, out, out_dtype, filter, jkey, s);
   const Plan P(m, false, true);
+  if (P.learned) return launch_ws<-1>(m, uvl, n, out, out_dtype, filter, jkey, s);
   switch (1 + 3 * grid_class(m.c0, P.cb0) + grid_class(m.c1, P.cb1)) {
     case 1: return launch_ws<1>(m, uvl, n, out, out_dtype, filter, jkey, s);
     case 2: return launch_ws<2>(m, uvl, n, out, out_dtype, filter, jkey, s);
