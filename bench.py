@@ -312,12 +312,13 @@ def render_eval(ntc, tr, target, chain, batch, seed, extra_steps, stream):
 # ----------------------------------------------------------------------------
 # The paper's decoder form: learned interpolation of G0, hardGELU, identity
 # ----------------------------------------------------------------------------
-def paper_form_eval(ntc, q_dev, stream):
+def paper_form_eval(ntc, q_dev, batch, stream):
     """Decode of the 2^24 queries with the paper's own decoder input (Sec.
     4.3.1, 4.4: the four G0 taps concatenated, 4 c0 + c1 + 13 inputs,
     hardGELU, no output activation) on a 4096^2 x 16 material with the NTC
     2.25 profile's grids (G0 1024^2 x 16 at 4 bits, G1 512^2 x 12 at 4 bits),
-    random weights, FP16 tensor cores."""
+    random weights, FP16 tensor cores; then the training step of the same
+    decoder form (paper_form_train)."""
     import torch
     g = torch.Generator(device="cuda")
     g.manual_seed(7007)
@@ -344,10 +345,50 @@ def paper_form_eval(ntc, q_dev, stream):
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / 5
     flop = 2 * (k * 64 + 64 * 64 + 64 * DEC_C)
-    return {"workload": "4096^2x16, G0 1024^2x16 (learned interpolation: 4 taps concatenated) + "
-                        "G1 512^2x12 at 4 bits, MLP 96-64-64-16 hardGELU/identity, 2^24 random queries",
-            "decode_ms": ms, "texels_per_s": q_dev.shape[0] / (ms / 1e3),
-            "tflops": flop * q_dev.shape[0] / (ms / 1e3) / 1e12, "status": ntc.ntc_device_status()}
+    res = {"workload": "4096^2x16, G0 1024^2x16 (learned interpolation: 4 taps concatenated) + "
+                       "G1 512^2x12 at 4 bits, MLP 96-64-64-16 hardGELU/identity, 2^24 random queries",
+           "decode_ms": ms, "texels_per_s": q_dev.shape[0] / (ms / 1e3),
+           "tflops": flop * q_dev.shape[0] / (ms / 1e3) / 1e12, "status": ntc.ntc_device_status()}
+    res["train"] = paper_form_train(ntc, batch, stream)
+    return res
+
+
+def paper_form_train(ntc, batch, stream, steps=20):
+    """Training step of the paper-form decoder (learned G0 interpolation,
+    hardGELU, identity output) on a 2048^2 x 12 material with the NTC 2.25
+    profile's grids (G0 512^2 x 16, G1 256^2 x 12, FP32 values in the 4-bit
+    range), MLP 96-64-64-12, FP16 tensor-core step with noise, `batch`
+    sampled texels per step."""
+    import torch
+    side, c, c0, c1, k = TRN_SIDE, TRN_C, 16, 12, 96
+    tex = gen.synthetic_texture(side, side, c, seed=1102)
+    chain = gen.box_mip_chain_u8(tex)
+    rng = np.random.default_rng(1103)
+    n, q = 16, 1.0 / 16
+    lo, hi = -(n - 1) / 2 * q, n / 2 * q
+    g0, g1 = [], []
+    for (w0, h0), (w1, h1) in ntc.pyramid(side, side):
+        g0.append(gen.uniform_grid_values((h0, w0, c0), lo, hi, rng))
+        g1.append(gen.uniform_grid_values((h1, w1, c1), lo, hi, rng))
+    w = gen.random_mlp(k, 64, c, seed=1104, n_used=4 * c0 + c1 + 13)
+    tr = ntc.Trainer(side, side, c, c0, c1, 4, 4, q, q, g0, g1, [w[0], w[2], w[4]],
+                     [w[1], w[3], w[5]], k, ntc.PREC_F16, act=ntc.ACT_HARDGELU,
+                     out_act=ntc.OUT_IDENTITY, total_steps=steps + 3, interp0=ntc.INTERP_LEARNED)
+    target = ntc.Target(chain)
+    for _ in range(3):
+        ntc.ntc_train_step(tr, target, batch, 5)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        ntc.ntc_train_step(tr, target, batch, 5)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps
+    return {"workload": f"2048^2x12, G0 512^2x16 (learned interpolation) + G1 256^2x12, "
+                        f"MLP 96-64-64-12 hardGELU/identity, {batch} texels per step",
+            "train_ms": ms, "samples_per_s": batch / (ms / 1e3), "loss": float(tr.loss.item()),
+            "status": ntc.ntc_device_status()}
 
 
 # ----------------------------------------------------------------------------
@@ -728,7 +769,7 @@ def main():
 
     paper_form = None
     try:
-        paper_form = paper_form_eval(ntc, q_dev, stream)
+        paper_form = paper_form_eval(ntc, q_dev, args.batch, stream)
     except Exception as e:  # reported, never fatal to the headline line
         paper_form = {"error": f"{type(e).__name__}: {e}"[:300]}
 

@@ -77,7 +77,7 @@ enum { NTC_DTYPE_F32 = 0, NTC_DTYPE_F16 = 1 };              /* output element ty
  * the four neighbouring G0 feature vectors of the bilinear footprint (taps
  * (x0,y0), (x1,y0), (x0,y1), (x1,y1)) concatenated in the MLP input, which
  * then holds 4 c0 + c1 + 13 used values.  Learned interpolation runs on the
- * FP32 and FP16 decode forms and the FP32 training form. */
+ * FP32 and FP16 decode forms and both training forms. */
 enum { NTC_INTERP_BILINEAR = 0, NTC_INTERP_LEARNED = 1 };
 
 /* Flags of ntc_decode / ntc_backward / ntc_train_step. */
@@ -250,8 +250,9 @@ int ntc_backward(const ntc_material* m, const float* uvl, int64_t n, const float
  * so the call is CUDA-graph capturable and replays identically.
  * flags: NTC_FLAG_FREEZE_GRIDS (no noise, grids neither differentiated nor
  * updated), NTC_FLAG_NO_NOISE, NTC_FLAG_SIMT, NTC_FLAG_GRAD_ONLY.  FP16
- * weights train on the tensor cores (tcgen05, ReLU only); FP32 weights or
- * NTC_FLAG_SIMT on the FP32 CUDA cores. */
+ * weights train on the tensor cores (tcgen05; ReLU or hardGELU, sigmoid or
+ * identity output, bilinear or learned G0); FP32 weights or NTC_FLAG_SIMT on
+ * the FP32 CUDA cores (k_in <= 64). */
 int ntc_train_step(const ntc_material* m, const ntc_trainer* tr, const ntc_target* t,
                    int64_t batch, uint64_t seed, const float* uvl_or_null, float* loss_out,
                    int32_t flags, void* stream);

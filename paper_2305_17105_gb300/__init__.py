@@ -28,6 +28,7 @@ PREC_F32, PREC_F16, PREC_F8 = 0, 1, 2
 ACT_RELU, ACT_HARDGELU = 0, 1
 OUT_SIGMOID, OUT_IDENTITY = 0, 1
 FILTER_NEAREST, FILTER_TRILINEAR, FILTER_STOCHASTIC = 0, 1, 2
+INTERP_BILINEAR, INTERP_LEARNED = 0, 1
 DTYPE_F32, DTYPE_F16 = 0, 1
 FLAG_NOISE, FLAG_FREEZE_GRIDS, FLAG_NO_NOISE, FLAG_SIMT, FLAG_GRAD_ONLY = 0x1, 0x2, 0x4, 0x8, 0x10
 
@@ -379,7 +380,7 @@ class Trainer:
     def __init__(self, width, height, channels, c0, c1, bits0, bits1, q0, q1, grids0, grids1,
                  weights, biases, k_in, precision=PREC_F32, act=ACT_RELU, out_act=OUT_SIGMOID,
                  total_steps=1000, lr_grid=0.01, lr_mlp=0.005, betas=(0.9, 0.999), eps=1e-8,
-                 device="cuda", noisy_scratch=True):
+                 device="cuda", noisy_scratch=True, interp0=INTERP_BILINEAR):
         tensors = [np.asarray(g, np.float32) for g in grids0] + \
                   [np.asarray(g, np.float32) for g in grids1]
         mlp = []
@@ -414,7 +415,8 @@ class Trainer:
         else:
             raise ValueError("training supports FP32 and FP16 weights")
         self.material = Material(width, height, channels, c0, c1, bits0, bits1, q0, q1, g0, g1,
-                                 self.w_compute, self.b, k_in, precision, act, out_act)
+                                 self.w_compute, self.b, k_in, precision, act, out_act,
+                                 interp0=interp0)
         self.total_steps, self.lr_grid, self.lr_mlp = total_steps, lr_grid, lr_mlp
         self.betas, self.eps = betas, eps
 
@@ -436,7 +438,7 @@ class Trainer:
             raise ValueError("export writes FP16 or FP32 weights")
         return Material(m.width, m.height, m.channels, m.c0, m.c1, m.bits0, m.bits1, m.q0, m.q1,
                         g0, g1, w, [b.clone() for b in self.b], m.k_in, precision, m.act,
-                        m.out_act)
+                        m.out_act, interp0=m.interp0)
 
     @property
     def struct(self) -> ntc_trainer:

@@ -264,6 +264,13 @@ int ntc_train_step(const ntc_material* m, const ntc_trainer* tr, const ntc_targe
   if (!tr || !t) return fail(NTC_ERR_ARG, "trainer / target is NULL");
   if (batch <= 0) return fail(NTC_ERR_ARG, "batch must be positive");
   if (m->precision == NTC_PREC_F8) return fail(NTC_ERR_UNSUPPORTED, "FP8 training");
+  if (use_simt(m, flags)) {
+    if (m->k_in > 64) return fail(NTC_ERR_UNSUPPORTED, "FP32 training supports k_in <= 64");
+  } else if (!ntc::train_tc_supported(*m)) {
+    return fail(NTC_ERR_UNSUPPORTED,
+                "tensor-core training: activation or feature layout not supported "
+                "(use NTC_FLAG_SIMT)");
+  }
   CHECK_PTR(tr->params, "params");
   CHECK_PTR(tr->adam_m, "adam_m");
   CHECK_PTR(tr->adam_v, "adam_v");
@@ -394,15 +401,7 @@ int ntc_train_step(const ntc_material* m, const ntc_trainer* tr, const ntc_targe
     if (e != cudaSuccess) return cuda_status(e, "train_step noise pass");
     b.noise = 0;
   }
-  if (use_simt(m, flags)) {
-    if (m->k_in > 64) return fail(NTC_ERR_UNSUPPORTED, "FP32 training supports k_in <= 64");
-    e = ntc::launch_backward_simt(mt, b, s);
-  } else {
-    if (m->act != NTC_ACT_RELU || m->interp0 != NTC_INTERP_BILINEAR)
-      return fail(NTC_ERR_UNSUPPORTED,
-                  "tensor-core training supports ReLU and bilinear G0 (use NTC_FLAG_SIMT)");
-    e = ntc::launch_train_tc(mt, b, s);
-  }
+  e = use_simt(m, flags) ? ntc::launch_backward_simt(mt, b, s) : ntc::launch_train_tc(mt, b, s);
   if (e != cudaSuccess) return cuda_status(e, "train_step forward/backward");
   if (flags & NTC_FLAG_GRAD_ONLY) return NTC_OK;
   e = ntc::launch_adam(a, a.block_start[a.nseg], s);

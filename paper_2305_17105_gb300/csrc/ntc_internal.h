@@ -39,6 +39,9 @@ cudaError_t launch_backward_simt(const ntc_material& m, const BwdArgs& a, cudaSt
 // jkey: jitter_key(seed, frame) of the stochastic filter (unused otherwise).
 cudaError_t launch_decode_tc(const ntc_material& m, const float* uvl, int64_t n, void* out,
                              int out_dtype, int filter, uint64_t jkey, cudaStream_t s, int nwg);
+// FP16 fused training step: ReLU or hardGELU, bilinear or learned G0, while
+// the operand tiles of two pipelines fit one CTA (k_int <= 96).
+bool train_tc_supported(const ntc_material& m);
 cudaError_t launch_train_tc(const ntc_material& m, const BwdArgs& a, cudaStream_t s);
 
 // Adam over the segments of the trainer's parameter array.

@@ -4,22 +4,30 @@
 // One persistent CTA per SM runs two warpgroup pipelines; a warpgroup owns a
 // stream of tiles of 128 training texels (one per thread = one row = one
 // TMEM lane).  Per tile, with every activation kept on chip:
-//   forward   X -> Z1 = X W1^T (+b1) -> H1 = relu -> Z2 (+b2) -> H2 -> Z3 (+b3)
-//             -> y = sigmoid, loss, dZ3 = 2 (y - t) y (1 - y)
-//   backward  dH2 = dZ3 W3, dZ2 = dH2 * [H2 > 0], dH1 = dZ2 W2,
-//             dZ1 = dH1 * [H1 > 0], dX = dZ1 W1 -> scatter-add into the grid
-//             gradients through the bilinear taps (FP32 atomics)
-//   weights   [dW1 db1; dW2 db2] += [dZ1^T; dZ2^T] [X | H1 | 1] and
+//   forward   X -> Z1 = X W1^T (+b1) -> H1 = act(Z1) -> Z2 (+b2) -> H2 -> Z3 (+b3)
+//             -> y = out(Z3), loss, dZ3 = 2 (y - t) out'(Z3)
+//   backward  dH2 = dZ3 W3, dZ2 = dH2 * act'(Z2), dH1 = dZ2 W2,
+//             dZ1 = dH1 * act'(Z1), dX = dZ1 W1 -> scatter-add into the grid
+//             gradients through the taps (FP32 atomics): bilinear weights for
+//             a bilinear grid, weight 1 per tap slot for learned
+//             interpolation of G0 (Sec. 4.3.1)
+//   weights   [dW1 db1; dW2 db2] += [dZ1^T; dZ2^T] [X | H1] and
 //             [dW3^T; db3] += [H2^T; 1] dZ3, accumulated in TMEM over all of
 //             the CTA's tiles and added to global memory once at the end.
 // X, H1, H2, dZ1, dZ2, dZ3 are FP16 tiles in shared memory, stored one row
 // per texel in the canonical K-major layout (8 x 16-byte core matrices, row
 // group fastest).  The same bytes serve as K-major A operands of the forward
 // and backward layers and, read with the MN-major descriptor mode (K = the
-// 128 texels), as the operands of the weight-gradient MMAs.  dZ3 carries the
-// loss scale B*C (2 (y - t) instead of 2 (y - t) / (B C)) so it stays well
-// inside FP16's range; every gradient is multiplied by 1 / (B C) in FP32 when
-// it leaves the chip.
+// 128 texels), as the operands of the weight-gradient MMAs.  The backward
+// layers read the forward weight tiles as MN-major B operands (no transposed
+// copies).  The biases of layer 1 ride in X's two constant-one slots, so the
+// same X columns of the [dW1; dW2] accumulator give db1 and db2.  ReLU's
+// derivative is read back from the sign of H; hardGELU's act'(Z) is written
+// in FP16 into the dZ tile of its layer by the forward epilogue and
+// multiplied in place by the backward one.  dZ3 carries the loss scale B*C
+// (2 (y - t) instead of 2 (y - t) / (B C)) so it stays well inside FP16's
+// range; every gradient is multiplied by 1 / (B C) in FP32 when it leaves the
+// chip.
 #include <cuda_fp16.h>
 
 #include "ntc_device.cuh"
@@ -34,52 +42,59 @@ constexpr int kRows = 128;
 constexpr int kN3 = 16;
 constexpr int kNWG = 2;                 // warpgroup pipelines per CTA
 constexpr uint32_t kCols = 512;         // 2 x 256 TMEM columns
-constexpr int kColD = 0;                // per warpgroup: layer accumulator (64)
-constexpr int kColW12 = 64;             // [dW1 db1; dW2 db2] accumulator (128)
-constexpr int kColW3 = 192;             // [dW3^T; db3] accumulator (16)
 constexpr uint32_t kGroup = 2048;       // bytes per 8-unit group of a 128-row tile
 constexpr uint32_t kWaitLimit = 1u << 18;  // suspended tries: ms to seconds
+constexpr int kDxStride = 84;           // floats per row of the dX staging rows
 
-// Shared-memory plan.  Input slots (generic layout): G0 groups, G1 groups,
+// Shared-memory and TMEM plan.  Input slots: G0 groups (c0 values, or the
+// four taps' 4 c0 values with learned interpolation), G1 groups,
 // [PE0..7][PE8..11, LOD, 0, 1, 1], zero groups up to k_int.
 struct TPlan {
-  int f0, f1, gpe, k_int;
-  uint32_t w1, w2, w3, w1t, w2t, w3t, wb2, wb3, tab, wg0, wg_bytes, total;
+  int w0, f0, f1, gpe, k_int, dx_n;
+  uint32_t w1, w2, w3, wb2, wb3, tab, wg0, wg_bytes, total;
+  uint32_t colD, colW12, colW3, cols;  // TMEM columns of one warpgroup
   // offsets inside one warpgroup's region
-  uint32_t P, X, H1, ONE, R, H2, ONE2, Q, DZ1, DZ2, DZ3;
-  __host__ __device__ TPlan(int c0, int c1) {
-    f0 = (c0 + 7) / 8;
+  uint32_t P, X, H1, R, H2, ONE, Q, DZ1, DZ2, DZ3;
+  __host__ __device__ TPlan(int c0, int c1, bool learned) {
+    w0 = learned ? 4 * c0 : c0;
+    f0 = (w0 + 7) / 8;
     f1 = (c1 + 7) / 8;
     gpe = f0 + f1;
     k_int = (8 * (gpe + 2) + 15) / 16 * 16;
+    dx_n = (8 * gpe + 15) / 16 * 16;     // dX columns: the grid slots
     uint32_t o = 0;
-    w1 = o;  o += kHidden * k_int * 2;   // B of layer 1: W1 [64][k_int]
-    w2 = o;  o += kHidden * kHidden * 2; // B of layer 2
-    w3 = o;  o += kN3 * kHidden * 2;     // B of layer 3: W3 [16][64]
-    w1t = o; o += k_int * kHidden * 2;   // B of dX: W1^T [k_int][64]
-    w2t = o; o += kHidden * kHidden * 2; // B of dH1: W2^T
-    w3t = o; o += kHidden * kN3 * 2;     // B of dH2: W3^T [64][16]
+    w1 = o;  o += kHidden * k_int * 2;   // W1 [64][k_int]: B of layer 1, MN-major B of dX
+    w2 = o;  o += kHidden * kHidden * 2; // W2: B of layer 2, MN-major B of dH1
+    w3 = o;  o += kN3 * kHidden * 2;     // W3 [16][64]: B of layer 3, MN-major B of dH2
     wb2 = o; o += kHidden * 16 * 2;      // bias blocks (head, tail)
     wb3 = o; o += kN3 * 16 * 2;
     o = (o + 15) / 16 * 16;
     tab = o; o += 16 * 16 * 4;           // per-mip table (MipTabT)
     o = (o + 1023) / 1024 * 1024;
     wg0 = o;
-    // per warpgroup: P = [X | H1 | ONE], R = [H2 | ONE2], Q = [dZ1 | dZ2], DZ3;
+    // per warpgroup: P = [X | H1], R = [H2 | ONE], Q = [dZ1 | dZ2], DZ3;
     // R must be followed by Q: the dW3 operand reads 16 groups from R's start
     P = 0;
     X = P;
     H1 = X + (k_int / 8) * kGroup;
-    ONE = H1 + 8 * kGroup;
-    R = ONE + 2 * kGroup;
+    R = H1 + 8 * kGroup;
     H2 = R;
-    ONE2 = H2 + 8 * kGroup;
-    Q = ONE2 + 2 * kGroup;
+    ONE = H2 + 8 * kGroup;
+    Q = ONE + 2 * kGroup;
     DZ1 = Q;
     DZ2 = DZ1 + 8 * kGroup;
     DZ3 = DZ2 + 8 * kGroup;
     wg_bytes = DZ3 + 2 * kGroup;
     total = wg0 + kNWG * wg_bytes;
+    colD = 0;
+    colW12 = dx_n > kHidden ? dx_n : kHidden;
+    colW3 = colW12 + k_int + kHidden;
+    cols = colW3 + kN3;
+  }
+  // fits one CTA: shared memory, 256 TMEM columns per warpgroup, the dX rows
+  __host__ __device__ bool fits() const {
+    return total + 2048u <= 232448u && cols <= 256u && (uint32_t)kRows * kDxStride * 4 <= wg_bytes &&
+           dx_n <= kDxStride;
   }
 };
 
@@ -88,16 +103,16 @@ struct MipTabT {
   float lodn[16];
 };
 
-// User column of internal input slot s (generic layout): >= 0 a W1 column,
-// -1 zero padding, -2 / -3 the constant-one slots (bias head / tail).
+// User column of internal input slot s: >= 0 a W1 column, -1 zero padding,
+// -2 / -3 the constant-one slots (bias head / tail).
 __device__ __forceinline__ int slot_column(const ntc_material& M, const TPlan& P, int s) {
   int g = s >> 3;
   const int e = s & 7;
-  if (g < P.f0) return 8 * g + e < M.c0 ? 8 * g + e : -1;
+  if (g < P.f0) return 8 * g + e < P.w0 ? 8 * g + e : -1;
   g -= P.f0;
-  if (g < P.f1) return 8 * g + e < M.c1 ? M.c0 + 8 * g + e : -1;
+  if (g < P.f1) return 8 * g + e < M.c1 ? P.w0 + 8 * g + e : -1;
   g -= P.f1;
-  const int pe = M.c0 + M.c1;
+  const int pe = P.w0 + M.c1;
   if (g == 0) return pe + e;
   if (g == 1) {
     if (e < 4) return pe + 8 + e;
@@ -132,20 +147,15 @@ __device__ void stage_train(const ntc_material& M, const TPlan& P, uint8_t* sm) 
       v = col == -2 ? hd : tl;
     }
     *reinterpret_cast<__half*>(sm + P.w1 + tc::canon_offset(o, s, kHidden, 2)) = v;
-    // the bias slots carry no gradient path back into the grids
-    *reinterpret_cast<__half*>(sm + P.w1t + tc::canon_offset(s, o, P.k_int, 2)) = col >= 0 ? v : z;
   }
   for (int i = tid; i < kHidden * kHidden; i += nt) {
     const int o = i / kHidden, k = i - o * kHidden;
-    const __half v = w_at(M, 1, i);
-    *reinterpret_cast<__half*>(sm + P.w2 + tc::canon_offset(o, k, kHidden, 2)) = v;
-    *reinterpret_cast<__half*>(sm + P.w2t + tc::canon_offset(k, o, kHidden, 2)) = v;
+    *reinterpret_cast<__half*>(sm + P.w2 + tc::canon_offset(o, k, kHidden, 2)) = w_at(M, 1, i);
   }
   for (int i = tid; i < kN3 * kHidden; i += nt) {
     const int c = i / kHidden, k = i - c * kHidden;
-    const __half v = c < M.channels ? w_at(M, 2, i) : z;
-    *reinterpret_cast<__half*>(sm + P.w3 + tc::canon_offset(c, k, kN3, 2)) = v;
-    *reinterpret_cast<__half*>(sm + P.w3t + tc::canon_offset(k, c, kHidden, 2)) = v;
+    *reinterpret_cast<__half*>(sm + P.w3 + tc::canon_offset(c, k, kN3, 2)) =
+        c < M.channels ? w_at(M, 2, i) : z;
   }
   for (int i = tid; i < kHidden * 16; i += nt) {
     const int n = i / 16, k = i - n * 16;
@@ -168,13 +178,13 @@ __device__ void stage_train(const ntc_material& M, const TPlan& P, uint8_t* sm) 
     tb->level[m] = level_of_mip(m, M.levels);
     tb->lodn[m] = M.mips > 1 ? (float)m / (float)(M.mips - 1) : 0.f;
   }
-  // constant-one groups of every warpgroup (columns 0 and 1 of ONE and ONE2)
+  // constant-one group of every warpgroup (columns 0 and 1 of ONE)
   for (int i = tid; i < kNWG * kRows * 2; i += nt) {
     const int w = i / (kRows * 2), r = (i / 2) % kRows, which = i & 1;
-    uint8_t* base = sm + P.wg0 + w * P.wg_bytes + (which ? P.ONE2 : P.ONE);
+    uint8_t* base = sm + P.wg0 + w * P.wg_bytes + P.ONE;
     const uint4 one = make_uint4(tc::pack_f16x2(1.f, 1.f), 0u, 0u, 0u);
-    *reinterpret_cast<uint4*>(base + tc::canon_chunk(r, 0, kRows)) = one;
-    *reinterpret_cast<uint4*>(base + tc::canon_chunk(r, 1, kRows)) = make_uint4(0, 0, 0, 0);
+    *reinterpret_cast<uint4*>(base + tc::canon_chunk(r, which, kRows)) =
+        which ? make_uint4(0, 0, 0, 0) : one;
   }
 }
 
@@ -297,12 +307,128 @@ __device__ __forceinline__ void sample_grid_f32x4(const ntc_material& M, int j, 
     }
 }
 
+// K-major A, MN-major B: a forward weight tile [out][in] (K-major, `R` rows
+// of outputs) read as B[n = in][k = out]; its core matrices step 128 bytes
+// along K (8 outputs) and (R / 8) * 128 bytes along N.
+__device__ __forceinline__ void issue_kmn(uint32_t d, uint32_t a, uint32_t a_lbo, uint32_t b,
+                                          uint32_t b_sbo, int ksteps, uint32_t id) {
+  for (int s = 0; s < ksteps; ++s)
+    tc::mma_f16(d, tc::smem_desc(a + 2 * s * a_lbo, a_lbo, 128),
+                tc::smem_desc(b + 256 * s, 128, b_sbo), id, s > 0);
+}
+
+// Forward epilogue of a hidden layer: H = act(Z) into `htile`; hardGELU
+// also writes act'(Z) into `gtile` (the layer's dZ tile).
+template <int ACT>
+__device__ __forceinline__ void hidden_forward(uint32_t taddr, uint8_t* htile, uint8_t* gtile,
+                                               int row) {
+#pragma unroll
+  for (int half = 0; half < 2; ++half) {
+    float a[16], b[16];
+    tc::tmem_ld16(taddr + 32 * half, a);
+    tc::tmem_ld16(taddr + 32 * half + 16, b);
+    tc::tmem_ld_wait();
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      float v[8], dv[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int i = 8 * g + e;
+        const float z = i < 16 ? a[i] : b[i - 16];
+        v[e] = act_fwd(ACT, z);
+        dv[e] = act_grad(ACT, z);
+      }
+      put_chunk(htile, row, 4 * half + g, v);
+      if (ACT == NTC_ACT_HARDGELU) put_chunk(gtile, row, 4 * half + g, dv);
+    }
+  }
+}
+
+// Backward epilogue: dZ = dH * act'(Z) into `dztile` (ReLU: the sign of H;
+// hardGELU: the act'(Z) the forward left in `dztile`, replaced in place).
+template <int ACT>
+__device__ __forceinline__ void hidden_backward(uint32_t taddr, const uint8_t* htile,
+                                                uint8_t* dztile, int row) {
+  __half2 h[32];
+  tile_row64(ACT == NTC_ACT_HARDGELU ? dztile : htile, row, h);
+  row64_to_tile(taddr, dztile, row, [&](int q, float g) {
+    return ACT == NTC_ACT_HARDGELU ? g * half_of(h, q) : (half_of(h, q) > 0.f ? g : 0.f);
+  });
+}
+
+__device__ __forceinline__ void put_half(uint8_t* tile, int row, int s, float v) {
+  *reinterpret_cast<__half*>(tile + tc::canon_chunk(row, s >> 3, kRows) + (s & 7) * 2) =
+      __float2half_rn(v);
+}
+// four values at slots s .. s+3, s a multiple of 4
+__device__ __forceinline__ void put_half4(uint8_t* tile, int row, int s, float4 v) {
+  *reinterpret_cast<uint2*>(tile + tc::canon_chunk(row, s >> 3, kRows) + (s & 7) * 2) =
+      make_uint2(tc::pack_f16x2(v.x, v.y), tc::pack_f16x2(v.z, v.w));
+}
+
+// Learned interpolation of G0 (Sec. 4.3.1): the c0 values of the four
+// bilinear-footprint cells at slots tap * c0 + ch, zeros up to the group
+// boundary.  FP32 grid values (plus this step's noise when asked).
+__device__ __forceinline__ void learned_g0(const ntc_material& M, const TPlan& P, int j, int x,
+                                           int y, int wm, int hm, bool valid, bool noise,
+                                           uint64_t nkey, uint8_t* X, int row) {
+  const ntc_level& L = M.lv[j];
+  const Taps t = bilinear_taps(x, y, wm, hm, L.g0_w, L.g0_h);
+  const int c = M.c0;
+  if ((c & 3) == 0 && !noise) {
+    const float* g = static_cast<const float*>(L.grid0);
+    float4 v[4][kMaxGridCh / 4];
+#pragma unroll
+    for (int tp = 0; tp < 4; ++tp)
+#pragma unroll
+      for (int q = 0; q < kMaxGridCh / 4; ++q)
+        v[tp][q] = (valid && 4 * q < c)
+                       ? __ldg(reinterpret_cast<const float4*>(g + (size_t)t.cell[tp] * c) + q)
+                       : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int tp = 0; tp < 4; ++tp)
+#pragma unroll
+      for (int q = 0; q < kMaxGridCh / 4; ++q)
+        if (4 * q < c) put_half4(X, row, tp * c + 4 * q, v[tp][q]);
+  } else {
+#pragma unroll
+    for (int tp = 0; tp < 4; ++tp)
+      for (int ch = 0; ch < c; ++ch)
+        put_half(X, row, tp * c + ch, valid ? grid_value(M, j, 0, t.cell[tp], ch, noise, nkey) : 0.f);
+  }
+  for (int s = P.w0; s < 8 * P.f0; ++s) put_half(X, row, s, 0.f);
+}
+
+// Scatter-add of `d` (c values) into grid cell rows through four taps,
+// weight w[tp] * gs each.
+__device__ __forceinline__ void scatter_taps(float* g, int c, const Taps& t, const float* d,
+                                             int tap_stride, bool bilinear, float gs) {
+#pragma unroll
+  for (int tp = 0; tp < 4; ++tp) {
+    const float wgt = (bilinear ? t.w[tp] : 1.f) * gs;
+    float* gp = g + (size_t)t.cell[tp] * c;
+    const float* dt = d + tp * tap_stride;
+    if ((c & 3) == 0) {
+#pragma unroll
+      for (int q = 0; q < kMaxGridCh / 4; ++q)
+        if (4 * q < c) {
+          const float4 v = *reinterpret_cast<const float4*>(dt + 4 * q);
+          atomicAdd(reinterpret_cast<float4*>(gp) + q,
+                    make_float4(v.x * wgt, v.y * wgt, v.z * wgt, v.w * wgt));
+        }
+    } else {
+      for (int ch = 0; ch < c; ++ch) atomicAdd(gp + ch, dt[ch] * wgt);
+    }
+  }
+}
+
 __device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t& phase, int bar_id) {
   const bool ok = tc::mbar_wait(bar, phase, kWaitLimit);
   phase ^= 1;
   return !tc::bar_or(bar_id, kRows, !ok);
 }
 
+template <int ACT, bool LEARNED>
 __global__ void __launch_bounds__(kRows* kNWG, 1) train_tc_kernel(const ntc_material M,
                                                                    const BwdArgs A, int* status) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -310,7 +436,7 @@ __global__ void __launch_bounds__(kRows* kNWG, 1) train_tc_kernel(const ntc_mate
   __shared__ uint32_t tmem_base;
   __shared__ int abort_any;
   __shared__ float red[kNWG * 4];
-  const TPlan P(M.c0, M.c1);
+  const TPlan P(M.c0, M.c1, LEARNED);
   uint8_t* sm = smem_raw;
   const int tid = threadIdx.x, warp = tid >> 5;
   const int wg = tid / kRows, row = tid % kRows;
@@ -331,17 +457,18 @@ __global__ void __launch_bounds__(kRows* kNWG, 1) train_tc_kernel(const ntc_mate
   tc::fence_after_sync();
 
   const uint32_t tw = tmem_base + 256u * wg;
+  const uint32_t tD = tw + P.colD;
   const uint32_t lane = (uint32_t)((warp & 3) * 32) << 16;
   uint64_t* bar = &mbar[wg];
   uint8_t* W = sm + P.wg0 + wg * P.wg_bytes;
   const uint32_t sW = tc::smem_u32(W), sbase = tc::smem_u32(sm);
   const MipTabT* tb = reinterpret_cast<const MipTabT*>(sm + P.tab);
   constexpr uint32_t lbo_a = (kRows / 8) * 128, lbo64 = (kHidden / 8) * 128, lbo16 = (kN3 / 8) * 128;
-  const uint32_t lbo_k = (uint32_t)(P.k_int / 8) * 128;
   constexpr uint32_t id64 = tc::idesc(kRows, kHidden), id16 = tc::idesc(kRows, kN3);
-  const uint32_t idk = tc::idesc(kRows, P.k_int);
-  const uint32_t id_w12 = tc::idesc(kRows, P.k_int + 80) | (1u << 15) | (1u << 16);
-  const uint32_t id_w3 = tc::idesc(kRows, kN3) | (1u << 15) | (1u << 16);
+  constexpr uint32_t idb = 1u << 16, ida = 1u << 15;  // B / A read MN-major
+  const uint32_t id_dx = tc::idesc(kRows, P.dx_n) | idb;
+  const uint32_t id_w12 = tc::idesc(kRows, P.k_int + kHidden) | ida | idb;
+  const uint32_t id_w3 = tc::idesc(kRows, kN3) | ida | idb;
 
   const int64_t step = A.step_dev ? *A.step_dev : A.noise_step;
   const uint64_t nkey = rng_key(A.noise_seed, noise_stream(step));
@@ -382,8 +509,9 @@ __global__ void __launch_bounds__(kRows* kNWG, 1) train_tc_kernel(const ntc_mate
       const int j = tb->level[m];
       const int wm = tb->wm[m], hm = tb->hm[m];
       GridSample gs;
+      if (LEARNED) learned_g0(M, P, j, x, y, wm, hm, valid, A.noise != 0, nkey, X, row);
 #pragma unroll
-      for (int k = 0; k < 2; ++k) {
+      for (int k = LEARNED ? 1 : 0; k < 2; ++k) {
         const int ck = k ? M.c1 : M.c0;
         if (!A.noise && (ck & 3) == 0) sample_grid_f32x4(M, j, k, x, y, wm, hm, gs);
         else sample_grid(M, j, k, x, y, wm, hm, A.noise != 0 && valid, nkey, gs);
@@ -421,12 +549,12 @@ __global__ void __launch_bounds__(kRows* kNWG, 1) train_tc_kernel(const ntc_mate
     // ---- layer 1 -----------------------------------------------------------------
     if (row == 0) {
       tc::fence_after_sync();
-      issue_kmajor(tw + kColD, sW + P.X, lbo_a, sbase + P.w1, lbo64, P.k_int / 16, id64, 0);
+      issue_kmajor(tD, sW + P.X, lbo_a, sbase + P.w1, lbo64, P.k_int / 16, id64, 0);
       tc::mma_commit(bar);
     }
     if (!wait_phase(bar, phase, bar_id)) { aborted = true; break; }
     tc::fence_after_sync();
-    row64_to_tile(tw + kColD + lane, W + P.H1, row, [](int, float z) { return fmaxf(z, 0.f); });
+    hidden_forward<ACT>(tD + lane, W + P.H1, W + P.DZ1, row);
     tc::fence_before_sync();
     tc::fence_proxy_async();
     tc::bar_sync(bar_id, kRows);
@@ -434,13 +562,13 @@ __global__ void __launch_bounds__(kRows* kNWG, 1) train_tc_kernel(const ntc_mate
     // ---- layer 2 -----------------------------------------------------------------
     if (row == 0) {
       tc::fence_after_sync();
-      issue_kmajor(tw + kColD, sW + P.H1, lbo_a, sbase + P.w2, lbo64, 4, id64, 0);
-      issue_kmajor(tw + kColD, sW + P.ONE, lbo_a, sbase + P.wb2, lbo64, 1, id64, 1);
+      issue_kmajor(tD, sW + P.H1, lbo_a, sbase + P.w2, lbo64, 4, id64, 0);
+      issue_kmajor(tD, sW + P.ONE, lbo_a, sbase + P.wb2, lbo64, 1, id64, 1);
       tc::mma_commit(bar);
     }
     if (!wait_phase(bar, phase, bar_id)) { aborted = true; break; }
     tc::fence_after_sync();
-    row64_to_tile(tw + kColD + lane, W + P.H2, row, [](int, float z) { return fmaxf(z, 0.f); });
+    hidden_forward<ACT>(tD + lane, W + P.H2, W + P.DZ2, row);
     tc::fence_before_sync();
     tc::fence_proxy_async();
     tc::bar_sync(bar_id, kRows);
@@ -448,15 +576,15 @@ __global__ void __launch_bounds__(kRows* kNWG, 1) train_tc_kernel(const ntc_mate
     // ---- layer 3, loss, dZ3 ----------------------------------------------------
     if (row == 0) {
       tc::fence_after_sync();
-      issue_kmajor(tw + kColD, sW + P.H2, lbo_a, sbase + P.w3, lbo16, 4, id16, 0);
-      issue_kmajor(tw + kColD, sW + P.ONE, lbo_a, sbase + P.wb3, lbo16, 1, id16, 1);
+      issue_kmajor(tD, sW + P.H2, lbo_a, sbase + P.w3, lbo16, 4, id16, 0);
+      issue_kmajor(tD, sW + P.ONE, lbo_a, sbase + P.wb3, lbo16, 1, id16, 1);
       tc::mma_commit(bar);
     }
     if (!wait_phase(bar, phase, bar_id)) { aborted = true; break; }
     tc::fence_after_sync();
     {
       float zv[16];
-      tc::tmem_ld16(tw + kColD + lane, zv);
+      tc::tmem_ld16(tD + lane, zv);
       tc::tmem_ld_wait();
       float d[16];
 #pragma unroll
@@ -483,17 +611,12 @@ __global__ void __launch_bounds__(kRows* kNWG, 1) train_tc_kernel(const ntc_mate
     // ---- dH2 = dZ3 W3 -> dZ2 ------------------------------------------------------
     if (row == 0) {
       tc::fence_after_sync();
-      issue_kmajor(tw + kColD, sW + P.DZ3, lbo_a, sbase + P.w3t, lbo64, 1, id64, 0);
+      issue_kmn(tD, sW + P.DZ3, lbo_a, sbase + P.w3, (kN3 / 8) * 128, 1, id64 | idb);
       tc::mma_commit(bar);
     }
     if (!wait_phase(bar, phase, bar_id)) { aborted = true; break; }
     tc::fence_after_sync();
-    {
-      __half2 h[32];
-      tile_row64(W + P.H2, row, h);
-      row64_to_tile(tw + kColD + lane, W + P.DZ2, row,
-                    [&](int q, float g) { return half_of(h, q) > 0.f ? g : 0.f; });
-    }
+    hidden_backward<ACT>(tD + lane, W + P.H2, W + P.DZ2, row);
     tc::fence_before_sync();
     tc::fence_proxy_async();
     tc::bar_sync(bar_id, kRows);
@@ -501,17 +624,12 @@ __global__ void __launch_bounds__(kRows* kNWG, 1) train_tc_kernel(const ntc_mate
     // ---- dH1 = dZ2 W2 -> dZ1 ------------------------------------------------------
     if (row == 0) {
       tc::fence_after_sync();
-      issue_kmajor(tw + kColD, sW + P.DZ2, lbo_a, sbase + P.w2t, lbo64, 4, id64, 0);
+      issue_kmn(tD, sW + P.DZ2, lbo_a, sbase + P.w2, lbo64, 4, id64 | idb);
       tc::mma_commit(bar);
     }
     if (!wait_phase(bar, phase, bar_id)) { aborted = true; break; }
     tc::fence_after_sync();
-    {
-      __half2 h[32];
-      tile_row64(W + P.H1, row, h);
-      row64_to_tile(tw + kColD + lane, W + P.DZ1, row,
-                    [&](int q, float g) { return half_of(h, q) > 0.f ? g : 0.f; });
-    }
+    hidden_backward<ACT>(tD + lane, W + P.H1, W + P.DZ1, row);
     tc::fence_before_sync();
     tc::fence_proxy_async();
     tc::bar_sync(bar_id, kRows);
@@ -519,21 +637,45 @@ __global__ void __launch_bounds__(kRows* kNWG, 1) train_tc_kernel(const ntc_mate
     // ---- dX = dZ1 W1, and the weight gradients of this tile ---------------------
     if (row == 0) {
       tc::fence_after_sync();
-      issue_kmajor(tw + kColD, sW + P.DZ1, lbo_a, sbase + P.w1t, lbo_k, 4, idk, 0);
-      issue_mnmajor(tw + kColW12, sW + P.Q, sW + P.P, id_w12, acc);
-      issue_mnmajor(tw + kColW3, sW + P.R, sW + P.DZ3, id_w3, acc);
+      issue_kmn(tD, sW + P.DZ1, lbo_a, sbase + P.w1, lbo64, 4, id_dx);
+      issue_mnmajor(tw + P.colW12, sW + P.Q, sW + P.P, id_w12, acc);
+      issue_mnmajor(tw + P.colW3, sW + P.R, sW + P.DZ3, id_w3, acc);
       tc::mma_commit(bar);
     }
     acc = 1;
     if (!wait_phase(bar, phase, bar_id)) { aborted = true; break; }
     tc::fence_after_sync();
-    if (A.grids) {
+    if (A.grids && LEARNED) {
+      // dX row -> this thread's staging row (the operand tiles are free now),
+      // then G0 per tap slot (weight 1) and G1 through the bilinear taps
+      float* dxs = reinterpret_cast<float*>(W) + row * kDxStride;
+      for (int cb = 0; cb < P.dx_n; cb += 16) {
+        float v[16];
+        tc::tmem_ld16(tD + lane + cb, v);
+        tc::tmem_ld_wait();
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          *reinterpret_cast<float4*>(dxs + cb + 4 * q) =
+              make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+      }
+      if (valid) {
+        const int j = tb->level[m];
+        const int wm = tb->wm[m], hm = tb->hm[m];
+        const ntc_level& L = M.lv[j];
+        if (float* g = A.g.grid0[j])
+          scatter_taps(g, M.c0, bilinear_taps(x, y, wm, hm, L.g0_w, L.g0_h), dxs, M.c0, false,
+                       A.grad_scale);
+        if (float* g = A.g.grid1[j])
+          scatter_taps(g, M.c1, bilinear_taps(x, y, wm, hm, L.g1_w, L.g1_h), dxs + 8 * P.f0, 0,
+                       true, A.grad_scale);
+      }
+    } else if (A.grids) {
       // dX slots: G0 at columns 0.., G1 at 8 * f0.. (f0 is 1 or 2)
       float d[32], dg0[16], dg1[16];
       {
         float lo[16], hi[16];
-        tc::tmem_ld16(tw + kColD + lane, lo);
-        tc::tmem_ld16(tw + kColD + lane + 16, hi);
+        tc::tmem_ld16(tD + lane, lo);
+        tc::tmem_ld16(tD + lane + 16, hi);
         tc::tmem_ld_wait();
 #pragma unroll
         for (int e = 0; e < 16; ++e) { d[e] = lo[e]; d[16 + e] = hi[e]; }
@@ -584,35 +726,34 @@ __global__ void __launch_bounds__(kRows* kNWG, 1) train_tc_kernel(const ntc_mate
   tc::fence_after_sync();
   const float gs = A.grad_scale;
   if (!aborted && acc) {
-    // [dW1 db1; dW2 db2]: row r < 64 -> (dW1 row r, db1 r), else (dW2 row r-64, db2 r-64)
+    // [dW1 db1; dW2 db2]: row r < 64 -> dW1 row r (X columns; the head
+    // constant-one slot gives db1 r), else dW2 row r-64 (H1 columns; the
+    // head slot gives db2 r-64)
     const int kin = P.k_int;
 #pragma unroll 1
-    for (int cb = 0; cb < 128; cb += 16) {
+    for (int cb = 0; cb < kin + kHidden; cb += 16) {
       float v[16];
-      tc::tmem_ld16(tw + kColW12 + lane + cb, v);
+      tc::tmem_ld16(tw + P.colW12 + lane + cb, v);
       tc::tmem_ld_wait();
 #pragma unroll
       for (int e = 0; e < 16; ++e) {
         const int col = cb + e;
-        if (row < kHidden) {
-          if (col < kin) {
-            const int uc = slot_column(M, P, col);
+        if (col < kin) {
+          const int uc = slot_column(M, P, col);
+          if (row < kHidden) {
             if (uc >= 0 && A.g.w[0]) atomicAdd(A.g.w[0] + row * M.k_in + uc, v[e] * gs);
-          } else if (col == kin + 64 && A.g.b[0]) {
-            atomicAdd(A.g.b[0] + row, v[e] * gs);
+            else if (uc == -2 && A.g.b[0]) atomicAdd(A.g.b[0] + row, v[e] * gs);
+          } else if (uc == -2 && A.g.b[1]) {
+            atomicAdd(A.g.b[1] + (row - kHidden), v[e] * gs);
           }
-        } else {
-          const int o = row - kHidden;
-          if (col >= kin && col < kin + 64 && A.g.w[1])
-            atomicAdd(A.g.w[1] + o * kHidden + (col - kin), v[e] * gs);
-          else if (col == kin + 64 && A.g.b[1])
-            atomicAdd(A.g.b[1] + o, v[e] * gs);
+        } else if (row >= kHidden && A.g.w[1]) {
+          atomicAdd(A.g.w[1] + (row - kHidden) * kHidden + (col - kin), v[e] * gs);
         }
       }
     }
     // [dW3^T; db3]: row r < 64 -> dW3[:, r]; row 64 -> db3
     float v[16];
-    tc::tmem_ld16(tw + kColW3 + lane, v);
+    tc::tmem_ld16(tw + P.colW3 + lane, v);
     tc::tmem_ld_wait();
 #pragma unroll
     for (int c = 0; c < kN3; ++c) {
@@ -639,24 +780,37 @@ __global__ void __launch_bounds__(kRows* kNWG, 1) train_tc_kernel(const ntc_mate
   }
 }
 
-}  // namespace
-
-cudaError_t launch_train_tc(const ntc_material& m, const BwdArgs& a, cudaStream_t s) {
-  if (a.n == 0) return cudaSuccess;
-  if (m.precision != NTC_PREC_F16 || m.act != NTC_ACT_RELU || m.interp0 != NTC_INTERP_BILINEAR ||
-      !a.train)
-    return cudaErrorNotSupported;
-  const TPlan P(m.c0, m.c1);
+template <int ACT, bool LEARNED>
+cudaError_t launch_t(const ntc_material& m, const BwdArgs& a, const TPlan& P, cudaStream_t s) {
   const size_t smem = P.total;
-  cudaError_t e = cudaFuncSetAttribute(train_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(train_tc_kernel<ACT, LEARNED>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int64_t tiles = (a.n + kRows - 1) / kRows;
   const int64_t ctas = (tiles + kNWG - 1) / kNWG;
   const int64_t cap = sm_count();
   const int grid = (int)(ctas < cap ? ctas : cap);
-  train_tc_kernel<<<grid, kRows * kNWG, smem, s>>>(m, a, status_word());
+  train_tc_kernel<ACT, LEARNED><<<grid, kRows * kNWG, smem, s>>>(m, a, status_word());
   return cudaGetLastError();
+}
+
+}  // namespace
+
+bool train_tc_supported(const ntc_material& m) {
+  const TPlan P(m.c0, m.c1, m.interp0 == NTC_INTERP_LEARNED);
+  return m.precision == NTC_PREC_F16 && (m.act == NTC_ACT_RELU || m.act == NTC_ACT_HARDGELU) &&
+         P.fits();
+}
+
+cudaError_t launch_train_tc(const ntc_material& m, const BwdArgs& a, cudaStream_t s) {
+  if (a.n == 0) return cudaSuccess;
+  if (!train_tc_supported(m) || !a.train) return cudaErrorNotSupported;
+  const bool learned = m.interp0 == NTC_INTERP_LEARNED;
+  const TPlan P(m.c0, m.c1, learned);
+  if (m.act == NTC_ACT_HARDGELU)
+    return learned ? launch_t<NTC_ACT_HARDGELU, true>(m, a, P, s)
+                   : launch_t<NTC_ACT_HARDGELU, false>(m, a, P, s);
+  return learned ? launch_t<NTC_ACT_RELU, true>(m, a, P, s) : launch_t<NTC_ACT_RELU, false>(m, a, P, s);
 }
 
 }  // namespace ntc

@@ -2,7 +2,8 @@
 the MLP input (the paper's decoder input, 4 c0 + c1 + 13 values) with the
 paper's hardGELU and identity output.  Parity with the FP64 oracle of the
 same model: FP32 form (decode and gradients), FP16 tensor-core decode
-(nearest, trilinear, stochastic; warp-specialised and batched launches)."""
+(nearest, trilinear, stochastic; warp-specialised and batched launches) and
+FP16 tensor-core training (gradients of every tensor)."""
 import numpy as np
 import pytest
 import torch
@@ -112,12 +113,73 @@ def test_learned_gradients_fp32_match_oracle():
         assert rel_err(to_np(got), ref) < 1e-2
 
 
-def test_learned_tensor_core_training_is_refused():
-    case = make_case(64, 64, 5, 8, 4, k_in=64, seed=96, interp0=1)
+def _f16_weights(case):
+    w = [np.asarray(a, np.float64) for a in case.weights]
+    for i in (0, 2, 4):
+        w[i] = case.weights[i].astype(np.float16).astype(np.float64)
+    return w
+
+
+@pytest.mark.parametrize("dense_noise", [True, False])
+@pytest.mark.parametrize("shape", PROFILES)
+def test_learned_gradients_f16_tensor_cores_match_oracle(shape, dense_noise):
+    """FP16 tcgen05 fused step of the paper-form decoder (learned G0,
+    hardGELU, identity output) on the four profiles' layouts: loss and the
+    gradient of every tensor against the oracle's reverse mode, noise on
+    (dense noise pass, or noise added per tap)."""
+    case = make_case(**shape, act=1, out_act=1, seed=97, interp0=1)
+    w, h, c = case.width, case.height, case.channels
+    chain = gen.box_mip_chain_u8(gen.synthetic_texture(w, h, c, seed=1097))
+    wt = case.weights
+    tr = ntc.Trainer(w, h, c, case.c0, case.c1, case.bits0, case.bits1, case.q0, case.q1,
+                     case.val0, case.val1, [wt[0], wt[2], wt[4]], [wt[1], wt[3], wt[5]],
+                     case.k_in, ntc.PREC_F16, act=1, out_act=1, total_steps=10,
+                     noisy_scratch=dense_noise, interp0=ntc.INTERP_LEARNED)
+    step = 4
+    tr.step_t.fill_(step)
+    target = ntc.Target(chain)
+    batch, seed = 7 * 128 + 33, 616
+    loss = ntc.ntc_train_step(tr, target, batch, seed, flags=ntc.FLAG_GRAD_ONLY).item()
+    assert ntc.ntc_device_status() == ntc.OK
+    md = case.oracle_model(weights=_f16_weights(case), quantized=False)
+    xym = oracle.sample_batch(seed, step, batch, w, h, md.mips)
+    lref, g = md.loss_grad_xym(xym, oracle.targets_of_xym(chain, xym), noise=(seed, step))
+    assert abs(loss - lref) <= 2e-3 * lref, (loss, lref)
+    refs = g["grid0"] + g["grid1"] + g["w"]
+    for k, (got, ref) in enumerate(zip(tr.grad_views, refs)):
+        err = rel_err(to_np(got), ref.reshape(got.shape))
+        assert err <= 1e-2, (k, err)
+
+
+def test_learned_f16_training_reduces_loss():
+    """A few hundred full FP16 steps of the paper-form decoder lower the loss
+    and export a material whose packed decode follows the trained model."""
+    case = make_case(128, 128, 9, 12, 10, 4, 4, k_in=80, act=1, out_act=1, seed=98, interp0=1)
+    chain = gen.box_mip_chain_u8(gen.synthetic_texture(128, 128, 9, seed=1098))
+    wt = case.weights
+    tr = ntc.Trainer(128, 128, 9, 12, 10, 4, 4, case.q0, case.q1, case.val0, case.val1,
+                     [wt[0], wt[2], wt[4]], [wt[1], wt[3], wt[5]], 80, ntc.PREC_F16, act=1,
+                     out_act=1, total_steps=300, interp0=ntc.INTERP_LEARNED)
+    target = ntc.Target(chain)
+    first = ntc.ntc_train_step(tr, target, 4096, 11).item()
+    for _ in range(298):
+        ntc.ntc_train_step(tr, target, 4096, 11)
+    last = ntc.ntc_train_step(tr, target, 4096, 11).item()
+    assert ntc.ntc_device_status() == ntc.OK
+    assert np.isfinite(last) and last < 0.5 * first, (first, last)
+    m = tr.export(ntc.PREC_F16)
+    assert m.interp0 == ntc.INTERP_LEARNED
+    q = _queries(case.oracle_model(), 2048, 5)
+    out = to_np(ntc.ntc_decode(m, _uvl(q)))
+    assert np.isfinite(out).all()
+
+
+def test_learned_fp32_training_beyond_k64_is_refused():
+    case = make_case(64, 64, 5, 12, 4, k_in=80, seed=96, interp0=1)
     w = case.weights
-    tr = ntc.Trainer(64, 64, 5, 8, 4, 4, 4, case.q0, case.q1, case.val0, case.val1,
-                     [w[0], w[2], w[4]], [w[1], w[3], w[5]], 64, ntc.PREC_F16, total_steps=10)
-    tr.material.interp0 = 1
+    tr = ntc.Trainer(64, 64, 5, 12, 4, 4, 4, case.q0, case.q1, case.val0, case.val1,
+                     [w[0], w[2], w[4]], [w[1], w[3], w[5]], 80, ntc.PREC_F32, total_steps=10,
+                     interp0=ntc.INTERP_LEARNED)
     target = ntc.Target(gen.box_mip_chain_u8(gen.synthetic_texture(64, 64, 5, seed=1096)))
     with pytest.raises(ntc.NTCError):
         ntc.ntc_train_step(tr, target, 256, 1)

@@ -72,6 +72,33 @@ def test_train_gradients_match_oracle(shape, precision):
         assert err <= GRAD_TOL, (k, err)
 
 
+@pytest.mark.parametrize("act,out_act", [(1, 0), (1, 1), (0, 1)])
+@pytest.mark.parametrize("shape", [
+    dict(width=128, height=128, channels=12, c0=16, c1=16, k_in=48),
+    dict(width=64, height=32, channels=5, c0=6, c1=5, k_in=32),
+])
+def test_train_f16_activations_match_oracle(shape, act, out_act):
+    """hardGELU hidden layers (act'(Z) kept in FP16 for the backward) and the
+    identity output on the tensor-core step, against the oracle."""
+    case = make_case(seed=73, act=act, out_act=out_act, **shape)
+    chain = gen.box_mip_chain_u8(gen.synthetic_texture(case.width, case.height, case.channels,
+                                                       seed=1073))
+    tr = _trainer(case, ntc.PREC_F16)
+    target = ntc.Target(chain)
+    batch, seed, step = 3 * 256 + 5, 4343, 1
+    tr.step_t.fill_(step)
+    loss = ntc.ntc_train_step(tr, target, batch, seed, flags=ntc.FLAG_GRAD_ONLY).item()
+    assert ntc.ntc_device_status() == ntc.OK
+    md = case.oracle_model(weights=_oracle_weights(case, ntc.PREC_F16), quantized=False)
+    xym = oracle.sample_batch(seed, step, batch, case.width, case.height, md.mips)
+    lref, gref = md.loss_grad_xym(xym, oracle.targets_of_xym(chain, xym), noise=(seed, step))
+    assert abs(loss - lref) <= 2e-3 * lref, (loss, lref)
+    refs = gref["grid0"] + gref["grid1"] + gref["w"]
+    for k, (v, r) in enumerate(zip(tr.grad_views, refs)):
+        err = rel_err(to_np(v), r.reshape(v.shape))
+        assert err <= GRAD_TOL, (k, err)
+
+
 def test_train_f16_full_step_and_accumulation():
     """GRAD_ONLY twice then a regular step equals the sum of three batches'
     gradients applied once (gradient accumulation); the scratch gradient is
