@@ -38,6 +38,7 @@ import ntc_inputs as gen  # noqa: E402
 METRIC = "decoded texels/s & train samples/s (fwd+bwd), % tensor peak, vs FP32 path"
 DEC_SIDE, DEC_C, DEC_C0, DEC_K = 4096, 16, 12, 48
 TRN_SIDE, TRN_C, TRN_C0, TRN_K = 2048, 12, 16, 48
+CROP_STEPS = 20
 MAX_SM_MHZ = 2070.0
 
 
@@ -62,7 +63,13 @@ def parse():
                     help="skip the 64-material batched decode and training graph")
     ap.add_argument("--render-steps", type=int, default=1000,
                     help="training steps added before the camera-frame decode")
-    return ap.parse_args()
+    ap.add_argument("--no-extras", action="store_true",
+                    help="only the timed step: skip the crop-sampler, paper-form, 64-material, "
+                         "render, FP32, e2e and CPU sections (profiling runs)")
+    a = ap.parse_args()
+    if a.no_extras:
+        a.no_cpu_baseline = a.no_e2e = a.no_fp32_compare = a.no_render = a.no_multi = True
+    return a
 
 
 # ----------------------------------------------------------------------------
@@ -621,7 +628,7 @@ def main():
     q_host = torch.from_numpy(queries).pin_memory()
     q_dev = q_host.to(dev)
     out = torch.empty((args.queries, DEC_C), dtype=torch.float16, device=dev)
-    total = args.warmup + args.steps + 40 + args.render_steps  # + e2e and render passes
+    total = args.warmup + args.steps + 40 + CROP_STEPS + args.render_steps  # + e2e, crops, render
     tr, target, chain, tgrids, tw = make_trainer(train_prec, total)
     seed = 77 + rank
 
@@ -687,7 +694,7 @@ def main():
     # DRAM bytes per launch of decode_ws_kernel from the committed ncu capture
     # (profiles/decode_ws_f16_4096x16.md: 141.3 MB at 2^22 queries, scaled by
     # the query count); null for another precision or query count
-    roof["traffic"] = (141.32e6 * args.queries / (1 << 22)
+    roof["traffic"] = (141.17e6 * args.queries / (1 << 22)
                        if precision == "f16" and tuning and tuning["decode_warpgroups"] == 5 else None)
     roof["traffic_unit"] = "bytes"
     dec_bytes = args.queries * (12 + DEC_C * 2)
@@ -717,6 +724,23 @@ def main():
         e2e = {"value": world * args.queries * e2e_steps / (e2e_ms / 1e3), "unit": "texels/s",
                "h2d_bytes_per_step": int(args.queries * 12),
                "d2h_bytes_per_step": int(args.queries * DEC_C * 2 + 4)}
+
+    # ---- the paper's crop sampler on the same trainer (Sec. 5.1) ----------
+    crops = None
+    if not args.no_extras:
+        try:
+            torch.cuda.synchronize()
+            c0e, c1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            c0e.record(stream)
+            for _ in range(CROP_STEPS):
+                ntc.ntc_train_step(tr, target, args.batch, seed, flags=ntc.FLAG_CROPS)
+            c1e.record(stream)
+            torch.cuda.synchronize()
+            cms = c0e.elapsed_time(c1e) / CROP_STEPS
+            crops = {"sampler": "256x256 crops of one mip per batch (Sec. 5.1)", "train_ms": cms,
+                     "samples_per_s": args.batch / (cms / 1e3), "status": ntc.ntc_device_status()}
+        except Exception as e:  # reported, never fatal to the headline line
+            crops = {"error": f"{type(e).__name__}: {e}"[:300]}
 
     # ---- the plain FP32 CUDA-core form on the same inputs ------------------
     fp32 = None
@@ -768,10 +792,11 @@ def main():
             render = {"error": f"{type(e).__name__}: {e}"[:300]}
 
     paper_form = None
-    try:
-        paper_form = paper_form_eval(ntc, q_dev, args.batch, stream)
-    except Exception as e:  # reported, never fatal to the headline line
-        paper_form = {"error": f"{type(e).__name__}: {e}"[:300]}
+    if not args.no_extras:
+        try:
+            paper_form = paper_form_eval(ntc, q_dev, args.batch, stream)
+        except Exception as e:  # reported, never fatal to the headline line
+            paper_form = {"error": f"{type(e).__name__}: {e}"[:300]}
 
     multi = None
     if not args.no_multi:
@@ -796,7 +821,7 @@ def main():
         "train_samples_per_s": train_rate, "train_loss": loss,
         "decode_ms": statistics.median(dec_ms), "train_ms": statistics.median(trn_ms),
         "roofline": roof, "tuning": tuning, "e2e": e2e, "fp32_path": fp32, "cpu_baseline": cpu,
-        "render": render, "multi_material": multi, "paper_form": paper_form,
+        "render": render, "multi_material": multi, "paper_form": paper_form, "train_crops": crops,
         "gpu_launches": kernels_per_step * args.steps,
         "clocks": clk.summary(), "wall_s": t_wall,
     }

@@ -89,6 +89,9 @@ enum { NTC_INTERP_BILINEAR = 0, NTC_INTERP_LEARNED = 1 };
 #define NTC_FLAG_GRAD_ONLY 0x10   /* train_step: accumulate the batch's gradient into
                                      tr->grad and stop (no Adam update, step counter
                                      unchanged); the next regular step applies the sum */
+#define NTC_FLAG_CROPS 0x20       /* train_step: sample the batch as 256 x 256 texel
+                                     crops of one mip (Sec. 5.1, ntc_sample_crops)
+                                     instead of independent texels (ntc_sample_batch) */
 
 /* One feature level F^j = (G^j_0, G^j_1) (Sec. 4.1, Table 1). */
 typedef struct {
@@ -249,7 +252,8 @@ int ntc_backward(const ntc_material* m, const float* uvl, int64_t n, const float
  * *tr->step += 1.  Sampling and noise are counter-based from (seed, *step),
  * so the call is CUDA-graph capturable and replays identically.
  * flags: NTC_FLAG_FREEZE_GRIDS (no noise, grids neither differentiated nor
- * updated), NTC_FLAG_NO_NOISE, NTC_FLAG_SIMT, NTC_FLAG_GRAD_ONLY.  FP16
+ * updated), NTC_FLAG_NO_NOISE, NTC_FLAG_SIMT, NTC_FLAG_GRAD_ONLY,
+ * NTC_FLAG_CROPS (crop sampler; ignored when uvl_or_null gives the texels).  FP16
  * weights train on the tensor cores (tcgen05; ReLU or hardGELU, sigmoid or
  * identity output, bilinear or learned G0); FP32 weights or NTC_FLAG_SIMT on
  * the FP32 CUDA cores (k_in <= 64). */
@@ -333,8 +337,21 @@ int ntc_unpack(const uint8_t* packed, int64_t cells, int32_t c, int32_t bits, fl
                int32_t* idx_out, float* values_out, void* stream);
 
 /* The training-texel sampler of ntc_train_step (Sec. 5.1), exposed for
- * testing: [batch][3] int32 rows (x, y, m) of step `step`. */
+ * testing: [batch][3] int32 rows (x, y, m) of step `step`, device memory.
+ * Every texel draws its own level of detail (with probability 0.05 a mip
+ * uniform over the chain, else floor(-log4 X), X uniform in (0, 1], clamped
+ * to the last mip) and a uniform texel of that mip. */
 int ntc_sample_batch(uint64_t seed, int64_t step, int64_t batch, int32_t width,
+                     int32_t height, int32_t mips, int32_t* xym_out, void* stream);
+
+/* The crop sampler of ntc_train_step with NTC_FLAG_CROPS (Sec. 5.1), same
+ * output: one level of detail for the whole batch (the rule above), the
+ * batch cut into crops of 256 x 256 texels; crop k = i / 65536 has its
+ * origin (x0, y0) uniform over the mip and texel i of the batch is
+ * ((x0 + i mod 256) mod w_m, (y0 + (i / 256) mod 256) mod h_m), i.e. a crop
+ * wraps around the mip's edges (the material tiles).  A mip smaller than
+ * the crop repeats inside it. */
+int ntc_sample_crops(uint64_t seed, int64_t step, int64_t batch, int32_t width,
                      int32_t height, int32_t mips, int32_t* xym_out, void* stream);
 
 /* The MLP input rows of nearest decodes (Sec. 4.3), exposed for testing:

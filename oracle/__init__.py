@@ -86,6 +86,7 @@ def _declare(L):
         "or_rng": (U64, [U64, U64, U64]),
         "or_noise_value": (D, [U64, I64, I, I, I64, I, I, D]),
         "or_sample_batch": (None, [U64, I64, I64, I, I, I, P]),
+        "or_sample_batch_crops": (None, [U64, I64, I64, I, I, I, P]),
         "or_positional_encoding": (None, [I, I, P]),
         "or_activation": (D, [I, D]),
         "or_activation_grad": (D, [I, D]),
@@ -188,10 +189,13 @@ def noise_value(seed, step, level, grid, cell, ch, c, q) -> float:
     return float(lib().or_noise_value(seed, step, level, grid, cell, ch, c, q))
 
 
-def sample_batch(seed: int, step: int, batch: int, width: int, height: int, n_mips: int):
-    """``[batch, 3]`` int32 rows (x, y, m) of one training batch (Sec. 5.1)."""
+def sample_batch(seed: int, step: int, batch: int, width: int, height: int, n_mips: int,
+                 crops: bool = False):
+    """``[batch, 3]`` int32 rows (x, y, m) of one training batch (Sec. 5.1):
+    independent texels, or 256 x 256 crops of one mip when ``crops``."""
     out = np.empty((batch, 3), np.int32)
-    lib().or_sample_batch(seed, step, batch, width, height, n_mips, _p(out))
+    fn = lib().or_sample_batch_crops if crops else lib().or_sample_batch
+    fn(seed, step, batch, width, height, n_mips, _p(out))
     return out
 
 

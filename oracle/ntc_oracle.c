@@ -144,31 +144,67 @@ double or_noise_value(uint64_t seed, int64_t step, int level, int grid, int64_t 
   return (u - 0.5) * q;
 }
 
-/* Training-batch texels (Sec. 5.1): LOD = floor(-log4 X), X ~ U(0,1], and
- * with probability 0.05 a LOD uniform over the mip chain instead; then a
- * uniform texel of that mip.  Reading: drawn per texel (not per 256^2 crop);
- * X = k / 2^24 with k = (draw >> 40) + 1, so floor(-log4 X) is the largest m
- * with k <= 2^(24-2m), clamped to the last mip.  Output rows (x, y, m). */
+/* Level of detail of one training draw (Sec. 5.1): LOD = floor(-log4 X),
+ * X ~ U(0,1], and with probability 0.05 a LOD uniform over the mip chain
+ * instead.  Reading: X = k / 2^24 with k = (draw >> 40) + 1, so
+ * floor(-log4 X) is the largest m with k <= 2^(24-2m), clamped to the last
+ * mip; counters c_mode (the 5% choice and the uniform mip) and c_exp. */
+static int or_train_lod(uint64_t seed, uint64_t stream, uint64_t c_mode, uint64_t c_exp,
+                        int mips) {
+  uint64_t h0 = or_rng(seed, stream, c_mode);
+  if ((h0 >> 40) < 838861ULL) /* 0.05 * 2^24, rounded up */
+    return (int)(((h0 & 0xFFFFFFFFULL) * (uint64_t)mips) >> 32);
+  uint64_t k = (or_rng(seed, stream, c_exp) >> 40) + 1;
+  int m = 0;
+  while (m + 1 <= 12 && k <= (1ULL << (24 - 2 * (m + 1)))) ++m;
+  return m > mips - 1 ? mips - 1 : m;
+}
+
+/* A uniform integer in [0, n) from 32 random bits (fixed-point product). */
+static uint64_t or_uniform_below(uint64_t bits32, uint64_t n) { return (bits32 * n) >> 32; }
+
+/* Training-batch texels (Sec. 5.1), independent texels: each texel i draws
+ * its LOD (counters 4i, 4i+1) and a uniform texel of that mip (counter
+ * 4i+2).  Output rows (x, y, m). */
 void or_sample_batch(uint64_t seed, int64_t step, int64_t batch, int width, int height,
                      int mips, int32_t* xym) {
   uint64_t stream = ((uint64_t)step << 1);
   for (int64_t i = 0; i < batch; ++i) {
-    uint64_t h0 = or_rng(seed, stream, 4 * (uint64_t)i + 0);
-    int m;
-    if ((h0 >> 40) < 838861ULL) { /* 0.05 * 2^24, rounded up */
-      m = (int)(((h0 & 0xFFFFFFFFULL) * (uint64_t)mips) >> 32);
-    } else {
-      uint64_t h1 = or_rng(seed, stream, 4 * (uint64_t)i + 1);
-      uint64_t k = (h1 >> 40) + 1;
-      m = 0;
-      while (m + 1 <= 12 && k <= (1ULL << (24 - 2 * (m + 1)))) ++m;
-      if (m > mips - 1) m = mips - 1;
-    }
+    int m = or_train_lod(seed, stream, 4 * (uint64_t)i + 0, 4 * (uint64_t)i + 1, mips);
     uint64_t h2 = or_rng(seed, stream, 4 * (uint64_t)i + 2);
     uint64_t wm = (uint64_t)imax(1, width >> m), hm = (uint64_t)imax(1, height >> m);
-    xym[3 * i + 0] = (int32_t)(((h2 & 0xFFFFFFFFULL) * wm) >> 32);
-    xym[3 * i + 1] = (int32_t)(((h2 >> 32) * hm) >> 32);
+    xym[3 * i + 0] = (int32_t)or_uniform_below(h2 & 0xFFFFFFFFULL, wm);
+    xym[3 * i + 1] = (int32_t)or_uniform_below(h2 >> 32, hm);
     xym[3 * i + 2] = m;
+  }
+}
+
+/* Training-batch texels (Sec. 5.1), crops: the batch is a sequence of
+ * square crops of side S = 256 taken from one level of detail, drawn once
+ * for the batch (counters 0, 1).  Crop k starts at a uniform texel (x0, y0)
+ * of that mip (counter 4k+2); reading: a crop that runs past the mip's edge
+ * wraps around (the material tiles), so a mip smaller than S repeats inside
+ * the crop.  The crop is walked row by row: its texel (cx, cy) is batch
+ * entry k S^2 + cy S + cx. */
+void or_sample_batch_crops(uint64_t seed, int64_t step, int64_t batch, int width, int height,
+                           int mips, int32_t* xym) {
+  const int64_t S = 256;
+  uint64_t stream = ((uint64_t)step << 1);
+  int m = or_train_lod(seed, stream, 0, 1, mips);
+  int64_t wm = imax(1, width >> m), hm = imax(1, height >> m);
+  int64_t n_crops = (batch + S * S - 1) / (S * S);
+  for (int64_t k = 0; k < n_crops; ++k) {
+    uint64_t h = or_rng(seed, stream, 4 * (uint64_t)k + 2);
+    int64_t x0 = (int64_t)or_uniform_below(h & 0xFFFFFFFFULL, (uint64_t)wm);
+    int64_t y0 = (int64_t)or_uniform_below(h >> 32, (uint64_t)hm);
+    for (int64_t cy = 0; cy < S; ++cy)
+      for (int64_t cx = 0; cx < S; ++cx) {
+        int64_t i = k * S * S + cy * S + cx;
+        if (i >= batch) return;
+        xym[3 * i + 0] = (int32_t)((x0 + cx) % wm);
+        xym[3 * i + 1] = (int32_t)((y0 + cy) % hm);
+        xym[3 * i + 2] = m;
+      }
   }
 }
 

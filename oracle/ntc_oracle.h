@@ -72,6 +72,8 @@ double or_noise_value(uint64_t seed, int64_t step, int level, int grid, int64_t 
                       int ch, int c, double q);
 void or_sample_batch(uint64_t seed, int64_t step, int64_t batch, int width, int height,
                      int mips, int32_t* xym);
+void or_sample_batch_crops(uint64_t seed, int64_t step, int64_t batch, int width, int height,
+                           int mips, int32_t* xym);
 
 /* --- sampling + decoder (Sec. 4.3, 4.4) --- */
 void or_positional_encoding(int x, int y, double* pe12);

@@ -31,6 +31,7 @@ FILTER_NEAREST, FILTER_TRILINEAR, FILTER_STOCHASTIC = 0, 1, 2
 INTERP_BILINEAR, INTERP_LEARNED = 0, 1
 DTYPE_F32, DTYPE_F16 = 0, 1
 FLAG_NOISE, FLAG_FREEZE_GRIDS, FLAG_NO_NOISE, FLAG_SIMT, FLAG_GRAD_ONLY = 0x1, 0x2, 0x4, 0x8, 0x10
+FLAG_CROPS = 0x20
 
 
 class NTCError(RuntimeError):
@@ -94,6 +95,7 @@ SIGNATURES = {
     "ntc_quantize_pack": (C.c_int, [_P, _I64, _I32, _I32, _F, _P, _P, _P]),
     "ntc_unpack": (C.c_int, [_P, _I64, _I32, _I32, _F, _P, _P, _P]),
     "ntc_sample_batch": (C.c_int, [_U64, _I64, _I64, _I32, _I32, _I32, _P, _P]),
+    "ntc_sample_crops": (C.c_int, [_U64, _I64, _I64, _I32, _I32, _I32, _P, _P]),
     "ntc_sample_features": (C.c_int, [_P, _P, _I64, _P, _I32, _U64, _I64, _P]),
     "ntc_device_status": (C.c_int, [_I32]),
     "ntc_batch_workspace_bytes": (C.c_size_t, []),
@@ -318,9 +320,10 @@ def ntc_unpack(packed: torch.Tensor, c: int, bits: int, q: float, want_idx=True,
 
 
 def ntc_sample_batch(seed: int, step: int, batch: int, width: int, height: int, n_mips: int,
-                     device="cuda", stream=None):
+                     device="cuda", stream=None, crops=False):
     out = torch.empty((batch, 3), dtype=torch.int32, device=device)
-    _call("ntc_sample_batch", seed, step, batch, width, height, n_mips, _ptr(out), _stream(stream))
+    _call("ntc_sample_crops" if crops else "ntc_sample_batch", seed, step, batch, width, height,
+          n_mips, _ptr(out), _stream(stream))
     return out
 
 

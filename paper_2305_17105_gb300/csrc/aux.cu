@@ -187,12 +187,12 @@ __global__ void unpack_kernel(const uint8_t* __restrict__ packed, int64_t cells,
   }
 }
 
-__global__ void sample_batch_kernel(uint64_t skey, int64_t batch, int w, int h, int mips,
+__global__ void sample_batch_kernel(uint64_t skey, int64_t batch, int w, int h, int mips, int crops,
                                     int32_t* __restrict__ xym) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= batch) return;
   int x, y, m;
-  sample_texel(skey, i, w, h, mips, x, y, m);
+  sample_train_texel(crops != 0, skey, i, w, h, mips, x, y, m);
   xym[3 * i] = x;
   xym[3 * i + 1] = y;
   xym[3 * i + 2] = m;
@@ -252,10 +252,10 @@ cudaError_t launch_unpack(const uint8_t* packed, int64_t cells, int c, int bits,
 }
 
 cudaError_t launch_sample_batch(uint64_t seed, int64_t step, int64_t batch, int w, int h, int mips,
-                                int32_t* xym, cudaStream_t s) {
+                                int crops, int32_t* xym, cudaStream_t s) {
   if (batch == 0) return cudaSuccess;
   sample_batch_kernel<<<blocks_for(batch, 256), 256, 0, s>>>(rng_key(seed, sampler_stream(step)),
-                                                             batch, w, h, mips, xym);
+                                                             batch, w, h, mips, crops, xym);
   return cudaGetLastError();
 }
 

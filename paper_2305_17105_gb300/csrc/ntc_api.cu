@@ -366,6 +366,7 @@ int ntc_train_step(const ntc_material* m, const ntc_trainer* tr, const ntc_targe
   b.step_dev = tr->step;
   b.train = 1;
   b.grids = !freeze;
+  b.crops = (flags & NTC_FLAG_CROPS) != 0;
 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaMemsetAsync(loss_out, 0, sizeof(float), s);
@@ -510,15 +511,25 @@ int ntc_unpack(const uint8_t* packed, int64_t cells, int32_t c, int32_t bits, fl
                      "unpack");
 }
 
-int ntc_sample_batch(uint64_t seed, int64_t step, int64_t batch, int32_t width, int32_t height,
-                     int32_t mips, int32_t* xym_out, void* stream) {
+static int sample_batch(uint64_t seed, int64_t step, int64_t batch, int32_t width,
+                        int32_t height, int32_t mips, int crops, int32_t* xym_out, void* stream) {
   if (batch < 0 || step < 0 || !pow2(width) || !pow2(height) || mips < 1 || mips > NTC_MAX_MIPS)
     return fail(NTC_ERR_ARG, "sample_batch args");
   if (batch == 0) return NTC_OK;
   CHECK_PTR(xym_out, "xym_out");
-  return cuda_status(ntc::launch_sample_batch(seed, step, batch, width, height, mips, xym_out,
-                                              static_cast<cudaStream_t>(stream)),
+  return cuda_status(ntc::launch_sample_batch(seed, step, batch, width, height, mips, crops,
+                                              xym_out, static_cast<cudaStream_t>(stream)),
                      "sample_batch");
+}
+
+int ntc_sample_batch(uint64_t seed, int64_t step, int64_t batch, int32_t width, int32_t height,
+                     int32_t mips, int32_t* xym_out, void* stream) {
+  return sample_batch(seed, step, batch, width, height, mips, 0, xym_out, stream);
+}
+
+int ntc_sample_crops(uint64_t seed, int64_t step, int64_t batch, int32_t width, int32_t height,
+                     int32_t mips, int32_t* xym_out, void* stream) {
+  return sample_batch(seed, step, batch, width, height, mips, 1, xym_out, stream);
 }
 
 int ntc_sample_features(const ntc_material* m, const float* uvl, int64_t n, float* rows_out,

@@ -305,30 +305,57 @@ __device__ __forceinline__ void featurize(const ntc_material& M, int x, int y, i
   for (int i = pe + 13; i < M.k_in; ++i) sink(i, 0.f);
 }
 
-// Training texel i of a step (Sec. 5.1): with probability 0.05 a mip uniform
-// over the chain, else LOD = floor(-log4 X), X = k/2^24, k = (draw>>40)+1,
-// i.e. the largest m with k <= 2^(24-2m), clamped to the last mip; then a
-// uniform texel of that mip.  Integer-only, identical on every platform.
+// Level of detail of a training draw (Sec. 5.1) from the hashes of counters
+// c0, c1: with probability 0.05 a mip uniform over the chain, else LOD =
+// floor(-log4 X), X = k/2^24, k = (draw>>40)+1, i.e. the largest m with
+// k <= 2^(24-2m), clamped to the last mip.  Integer-only, identical on every
+// platform.
+__device__ __forceinline__ int sampled_lod(uint64_t skey, uint64_t c0, uint64_t c1, int mips) {
+  const uint64_t h0 = splitmix64(skey ^ c0);
+  if ((h0 >> 40) < 838861ull) return (int)(((h0 & 0xFFFFFFFFull) * (uint64_t)mips) >> 32);
+  const uint64_t kk = (splitmix64(skey ^ c1) >> 40) + 1;
+  int mm = 0;
+#pragma unroll
+  for (int t = 1; t <= 12; ++t)
+    if (kk <= (1ull << (24 - 2 * t))) mm = t;
+  return mm > mips - 1 ? mips - 1 : mm;
+}
+
+// Training texel i of a step, independent texels: its own LOD (counters
+// 4i, 4i+1), then a uniform texel of that mip (counter 4i+2).
 __device__ __forceinline__ void sample_texel(uint64_t skey, int64_t i, int width, int height,
                                              int mips, int& x, int& y, int& m) {
-  const uint64_t h0 = splitmix64(skey ^ (4ull * (uint64_t)i + 0));
-  int mm;
-  if ((h0 >> 40) < 838861ull) {
-    mm = (int)(((h0 & 0xFFFFFFFFull) * (uint64_t)mips) >> 32);
-  } else {
-    const uint64_t h1 = splitmix64(skey ^ (4ull * (uint64_t)i + 1));
-    const uint64_t kk = (h1 >> 40) + 1;
-    mm = 0;
-#pragma unroll
-    for (int t = 1; t <= 12; ++t)
-      if (kk <= (1ull << (24 - 2 * t))) mm = t;
-    if (mm > mips - 1) mm = mips - 1;
-  }
+  const int mm = sampled_lod(skey, 4ull * (uint64_t)i + 0, 4ull * (uint64_t)i + 1, mips);
   const uint64_t h2 = splitmix64(skey ^ (4ull * (uint64_t)i + 2));
   const uint64_t wm = (uint64_t)mip_dim(width, mm), hm = (uint64_t)mip_dim(height, mm);
   x = (int)(((h2 & 0xFFFFFFFFull) * wm) >> 32);
   y = (int)(((h2 >> 32) * hm) >> 32);
   m = mm;
+}
+
+// Training texel i of a step cut into crops (Sec. 5.1): one LOD for the
+// whole batch (counters 0, 1); crop k = i / S^2 (S = kCropSide) has its
+// origin uniform over the mip (counter 4k+2) and wraps around the mip's
+// edges (the material tiles); texel i sits at (i mod S, (i / S) mod S)
+// inside its crop.
+constexpr int kCropSide = 256;
+__device__ __forceinline__ void sample_crop_texel(uint64_t skey, int64_t i, int width, int height,
+                                                  int mips, int& x, int& y, int& m) {
+  const int mm = sampled_lod(skey, 0, 1, mips);
+  const uint64_t k = (uint64_t)i / (uint64_t)(kCropSide * kCropSide);
+  const uint64_t h2 = splitmix64(skey ^ (4ull * k + 2));
+  const uint64_t wm = (uint64_t)mip_dim(width, mm), hm = (uint64_t)mip_dim(height, mm);
+  const uint64_t x0 = ((h2 & 0xFFFFFFFFull) * wm) >> 32, y0 = ((h2 >> 32) * hm) >> 32;
+  x = (int)((x0 + (uint64_t)i % kCropSide) % wm);
+  y = (int)((y0 + (uint64_t)i / kCropSide % kCropSide) % hm);
+  m = mm;
+}
+
+// The sampler of a training step: crops or independent texels.
+__device__ __forceinline__ void sample_train_texel(bool crops, uint64_t skey, int64_t i, int width,
+                                                   int height, int mips, int& x, int& y, int& m) {
+  if (crops) sample_crop_texel(skey, i, width, height, mips, x, y, m);
+  else sample_texel(skey, i, width, height, mips, x, y, m);
 }
 
 // Activations (Sec. 4.4).

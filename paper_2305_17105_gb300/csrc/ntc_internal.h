@@ -29,6 +29,7 @@ struct BwdArgs {
   const int64_t* step_dev; // training mode: device step counter (noise + sampler)
   int train;               // 1: loss mode (dout = 2 (y - t)), 0: dout given
   int grids;               // 0: skip grid gradients (frozen grids)
+  int crops;               // training sampler: 256 x 256 crops of one mip (Sec. 5.1)
 };
 
 cudaError_t launch_decode_simt(const ntc_material& m, const float* uvl, int64_t n, void* out,
@@ -96,7 +97,7 @@ cudaError_t launch_quantize_pack(const float* values, int64_t cells, int c, int 
 cudaError_t launch_unpack(const uint8_t* packed, int64_t cells, int c, int bits, float q,
                           int32_t* idx, float* values, cudaStream_t s);
 cudaError_t launch_sample_batch(uint64_t seed, int64_t step, int64_t batch, int w, int h, int mips,
-                                int32_t* xym, cudaStream_t s);
+                                int crops, int32_t* xym, cudaStream_t s);
 cudaError_t launch_sample_features(const ntc_material& m, const float* uvl, int64_t n, float* rows,
                                    int noise, uint64_t seed, int64_t step, cudaStream_t s);
 

@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(kThreads, 1) backward_simt_kernel(const ntc_ma
     int x = 0, y = 0, m = 0;
     if (valid) {
       if (A.uvl) query_texel(M, A.uvl[3 * i], A.uvl[3 * i + 1], A.uvl[3 * i + 2], x, y, m);
-      else sample_texel(skey, i, M.width, M.height, M.mips, x, y, m);
+      else sample_train_texel(A.crops != 0, skey, i, M.width, M.height, M.mips, x, y, m);
     }
     featurize(M, x, y, m, A.noise != 0, nkey, sink);
     float d1[kHidden];  // h1 during the forward, dZ1 during the backward

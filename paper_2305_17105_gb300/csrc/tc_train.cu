@@ -486,7 +486,7 @@ __global__ void __launch_bounds__(kRows* kNWG, 1) train_tc_kernel(const ntc_mate
     int x = 0, y = 0, m = 0;
     if (valid) {
       if (A.uvl) query_texel(M, A.uvl[3 * i], A.uvl[3 * i + 1], A.uvl[3 * i + 2], x, y, m);
-      else sample_texel(skey, i, M.width, M.height, M.mips, x, y, m);
+      else sample_train_texel(A.crops != 0, skey, i, M.width, M.height, M.mips, x, y, m);
     }
     float tgt[kN3];
     {

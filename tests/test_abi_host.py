@@ -163,3 +163,5 @@ def test_quantize_and_sampler_validation(L):
     assert L.ntc_sample_batch(1, 0, 10, 48, 64, 7, 0x1000, None) == ntc.ERR_ARG
     assert L.ntc_sample_batch(1, 0, 10, 64, 64, 17, 0x1000, None) == ntc.ERR_ARG
     assert L.ntc_sample_batch(1, 0, 0, 64, 64, 7, 0x1000, None) == ntc.OK
+    assert L.ntc_sample_crops(1, 0, 10, 48, 64, 7, 0x1000, None) == ntc.ERR_ARG
+    assert L.ntc_sample_crops(1, 0, 0, 64, 64, 7, 0x1000, None) == ntc.OK

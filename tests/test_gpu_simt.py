@@ -155,6 +155,15 @@ def test_sampler_bit_exact(w, h, step):
     assert np.array_equal(got, oracle.sample_batch(99, step, 5000, w, h, mips))
 
 
+@pytest.mark.parametrize("w,h,step,batch", [(2048, 2048, 0, 5000), (256, 64, 17, 2 * 65536 + 777),
+                                            (4096, 4096, 123456, 4 * 65536), (16, 8, 5, 65536)])
+def test_crop_sampler_bit_exact(w, h, step, batch):
+    mips = oracle.mips(w, h)
+    for s in (step, step + 1, step + 2):
+        got = ntc.ntc_sample_batch(99, s, batch, w, h, mips, crops=True).cpu().numpy()
+        assert np.array_equal(got, oracle.sample_batch(99, s, batch, w, h, mips, crops=True))
+
+
 # -------------------------------------------------------------- backward ---
 def _grad_views(case, dev=DEV):
     g0 = [torch.zeros(v.shape, dtype=torch.float32, device=dev) for v in case.val0]

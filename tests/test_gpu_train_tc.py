@@ -99,6 +99,35 @@ def test_train_f16_activations_match_oracle(shape, act, out_act):
         assert err <= GRAD_TOL, (k, err)
 
 
+@pytest.mark.parametrize("precision", [ntc.PREC_F32, ntc.PREC_F16])
+@pytest.mark.parametrize("step", [2, 9])
+def test_train_crops_gradients_match_oracle(precision, step):
+    """The crop sampler in the fused step (NTC_FLAG_CROPS, Sec. 5.1): one
+    mip, 256 x 256 windows, a ragged last crop; neighbouring texels share
+    grid cells, so many atomics of a warp land on one address."""
+    case = make_case(seed=74, width=512, height=256, channels=8, c0=8, c1=8, k_in=32)
+    chain = gen.box_mip_chain_u8(gen.synthetic_texture(case.width, case.height, case.channels,
+                                                       seed=1074))
+    tr = _trainer(case, precision)
+    target = ntc.Target(chain)
+    batch, seed = 65536 + 4099, 4545
+    tr.step_t.fill_(step)
+    loss = ntc.ntc_train_step(tr, target, batch, seed,
+                              flags=ntc.FLAG_GRAD_ONLY | ntc.FLAG_CROPS).item()
+    assert ntc.ntc_device_status() == ntc.OK
+    md = case.oracle_model(weights=_oracle_weights(case, precision), quantized=False)
+    xym = oracle.sample_batch(seed, step, batch, case.width, case.height, md.mips, crops=True)
+    lref, gref = md.loss_grad_xym(xym, oracle.targets_of_xym(chain, xym), noise=(seed, step))
+    assert abs(loss - lref) <= 2e-3 * lref, (loss, lref)
+    refs = gref["grid0"] + gref["grid1"] + gref["w"]
+    for k, (v, r) in enumerate(zip(tr.grad_views, refs)):
+        if not np.any(r):
+            assert not np.any(to_np(v)), k   # grids of other levels get nothing
+            continue
+        err = rel_err(to_np(v), r.reshape(v.shape))
+        assert err <= GRAD_TOL, (k, err)
+
+
 def test_train_f16_full_step_and_accumulation():
     """GRAD_ONLY twice then a regular step equals the sum of three batches'
     gradients applied once (gradient accumulation); the scratch gradient is

@@ -102,6 +102,65 @@ def test_sampler_lod_law_chi2():
     assert ((hx - e) ** 2 / e).sum() < 45
 
 
+def test_crop_sampler_lod_law_per_batch_chi2():
+    """Crops (Sec. 5.1): one LOD per batch, drawn by the same 95/5 law."""
+    n_mips, steps = 12, 20_000
+    m = np.array([oracle.sample_batch(13, t, 1, 2048, 2048, n_mips, crops=True)[0, 2]
+                  for t in range(steps)])
+    counts = np.bincount(m, minlength=n_mips)
+    exp = oracle.lod_law_probs(n_mips) * steps
+    ok = exp >= 5
+    chi2 = (((counts - exp) ** 2 / exp)[ok]).sum()
+    assert chi2 < 40, (counts, exp)
+
+
+@pytest.mark.parametrize("w,h,step", [(2048, 1024, 3), (64, 64, 8), (512, 512, 21)])
+def test_crop_sampler_structure(w, h, step):
+    """Every texel of a batch from one mip; each 256 x 256 crop is a
+    contiguous window (row by row) that wraps around the mip's edges."""
+    n_mips = int(np.log2(max(w, h))) + 1
+    batch = 3 * 65536 + 1000                     # three whole crops and a ragged one
+    xym = oracle.sample_batch(5, step, batch, w, h, n_mips, crops=True)
+    m = int(xym[0, 2])
+    assert (xym[:, 2] == m).all()
+    wm, hm = max(1, w >> m), max(1, h >> m)
+    i = np.arange(batch)
+    cx, cy, k = i % 256, (i // 256) % 256, i // 65536
+    x0, y0 = xym[k * 65536, 0], xym[k * 65536, 1]
+    assert np.array_equal(xym[:, 0], (x0 + cx) % wm)
+    assert np.array_equal(xym[:, 1], (y0 + cy) % hm)
+    # a ragged batch is the prefix of a longer one (same counters)
+    assert np.array_equal(oracle.sample_batch(5, step, 70000, w, h, n_mips, crops=True), xym[:70000])
+
+
+def test_crop_sampler_small_mip_repeats_evenly():
+    """A mip smaller than the crop tiles it: every texel of an 8 x 4 mip
+    appears (256/8) (256/4) times in a whole crop."""
+    for step in range(40):
+        xym = oracle.sample_batch(17, step, 65536, 32, 16, 6, crops=True)
+        m = int(xym[0, 2])
+        wm, hm = max(1, 32 >> m), max(1, 16 >> m)
+        if wm < 256 and hm < 256:
+            cnt = np.bincount(xym[:, 1] * wm + xym[:, 0], minlength=wm * hm)
+            assert (cnt == (256 // wm) * (256 // hm)).all(), (m, cnt)
+
+
+def test_crop_origins_uniform_and_independent():
+    """Crop origins uniform over the mip, different crops of a batch drawn
+    independently (mip 0 of a 4096^2 texture, 16 crops x 600 steps)."""
+    origins = []
+    for step in range(600):
+        xym = oracle.sample_batch(23, step, 16 * 65536, 4096, 4096, 1, crops=True)
+        origins.append(xym[::65536, :2])
+    o = np.concatenate(origins)
+    hx, _ = np.histogram(o[:, 0], bins=16, range=(0, 4096))
+    hy, _ = np.histogram(o[:, 1], bins=16, range=(0, 4096))
+    e = len(o) / 16
+    assert ((hx - e) ** 2 / e).sum() < 45 and ((hy - e) ** 2 / e).sum() < 45
+    r = np.corrcoef(o[:-1, 0], o[1:, 0])[0, 1]
+    assert abs(r) < 0.05
+
+
 # ----------------------------------------------------------- quantisation ---
 @pytest.mark.parametrize("bits", [1, 2, 4, 8])
 def test_quantizer_levels_and_roundtrip(bits):
