@@ -128,6 +128,10 @@ bool fast_layout_ok(const ntc_material& m);
 // Warp-specialised tensor-core decode (FP16), fast 4-bit layout or generic.
 cudaError_t launch_decode_ws(const ntc_material& m, const float* uvl, int64_t n, void* out,
                              int out_dtype, int filter, uint64_t jkey, cudaStream_t s, bool fast);
+// The same kernel in FP8-E4M3 (kind::f8f6f4): fast 4-bit layout when
+// fast_layout_ok, generic layout otherwise.
+cudaError_t launch_decode_ws_f8(const ntc_material& m, const float* uvl, int64_t n, void* out,
+                                int out_dtype, int filter, uint64_t jkey, cudaStream_t s);
 
 
 int sm_count();

@@ -263,14 +263,16 @@ bool fast_layout_ok(const ntc_material& m) {
 // Launch shape: one CTA per SM with `nwg` warpgroup pipelines (2, 3 or 4),
 // each holding 128 of the SM's 512 TMEM columns, or (5, the default for 0)
 // the warp-specialised form: 4 compute warpgroups plus their MMA issuers
-// (FP16; FP8 runs 4 pipelines).
+// (FP16 and FP8).
 cudaError_t launch_decode_tc(const ntc_material& m, const float* uvl, int64_t n, void* out,
                              int out_dtype, int filter, uint64_t jkey, cudaStream_t s, int nwg) {
   if (n == 0) return cudaSuccess;
   if (nwg == 0) nwg = 5;
   if (nwg < 2 || nwg > 5) return cudaErrorInvalidValue;
-  if (m.precision == NTC_PREC_F8)
-    return launch_shape<true, false>(m, uvl, n, out, out_dtype, filter, jkey, s, nwg == 5 ? 4 : nwg);
+  if (m.precision == NTC_PREC_F8) {
+    if (nwg == 5) return launch_decode_ws_f8(m, uvl, n, out, out_dtype, filter, jkey, s);
+    return launch_shape<true, false>(m, uvl, n, out, out_dtype, filter, jkey, s, nwg);
+  }
   if (m.precision != NTC_PREC_F16) return cudaErrorInvalidValue;
   const Plan P(m, false, fast_layout_ok(m));
   // the warpgroup-pipeline kernel keeps X in 24 TMEM columns (K <= 48)

@@ -72,8 +72,8 @@ struct Plan {
       cb1 = cell_bytes(c1, bits1);
     }
     // the fast layout reads whole 32-bit cell words: 4-bit cells of 4 or 8 bytes
-    fast = taps_ok && !f8 && packed && bits0 == 4 && bits1 == 4 && (cb0 == 4 || cb0 == 8) &&
-           (cb1 == 4 || cb1 == 8);
+    fast = taps_ok && packed && bits0 == 4 && bits1 == 4 && (cb0 == 4 || cb0 == 8) &&
+           (cb1 == 4 || cb1 == 8) && !(f8 && learned);
     eo0 = eo1 = t0 = t1 = 0;
     if (fast) {
       // word 0 holds 5-8 channels; word 1 (8-byte cells) the other c - 8

@@ -1,266 +1,11 @@
 // Warp-specialised tensor-core decode (FP16), instantiated per fast-layout
-// class so that the per-row feature code has no runtime layout branches.
-#include "tc_decode_common.cuh"
+// class so that the per-row feature code has no runtime layout branches, and
+// its many-material form.
+#include "tc_decode_ws.cuh"
 
 namespace ntc {
 
 namespace {
-
-// ---------------------------------------------------------------------------
-// Warp-specialised form (FP16): four compute warpgroups, each running its own
-// stream of tiles, and one issuer warpgroup whose warp w issues every
-// tcgen05.mma chain of compute warpgroup w.  A chain of dependent MMAs holds
-// its issuing thread until it drains, so issuing from the compute warps
-// stalls them; here they only hand over through mbarriers and keep working:
-//   X(i) in shared memory --x--> L1 --d--> epilogue 1 -> H --h--> L2 --d-->
-//   epilogue 2 -> H --h--> L3 (own accumulator D3) --o--> output,
-// and while L2(i) runs the compute warps build X(i+1), while L3(i) runs they
-// gather the cells of tile i+2, while L1(i+1) runs they write tile i.  L1
-// reads its A operand from shared memory, the bias steps a constant-one A
-// block in shared memory; L2 and L3 read H from TMEM.
-// TMEM per compute warpgroup (128 columns): D [0, 64), H [64, 96),
-// D3 [96, 112).
-// ---------------------------------------------------------------------------
-constexpr int kWsCompute = 4;
-constexpr int kWsThreads = kRows * (kWsCompute + 1);
-constexpr int kColD3 = 96;
-
-struct WsPlan {
-  uint32_t cst, x, xbytes, total;
-  __host__ __device__ explicit WsPlan(const Plan& P) {
-    uint32_t o = (P.total + 1023) / 1024 * 1024;
-    cst = o;  o += kRows * 16 * 2;                 // constant-one A block (K = 16)
-    xbytes = kRows * P.k_int * 2;
-    x = o;    o += kWsCompute * xbytes;            // one X tile per compute warpgroup
-    total = o;
-  }
-};
-
-template <int CLS>
-__global__ void __launch_bounds__(kWsThreads, 1) decode_ws_kernel(
-    const ntc_material M, const float* __restrict__ uvl, int64_t n, void* __restrict__ out,
-    int out_dtype, int filter, uint64_t jkey, int* status) {
-  extern __shared__ __align__(1024) uint8_t smem_raw[];
-  __shared__ uint64_t bar_x[kWsCompute], bar_h[kWsCompute], bar_d[kWsCompute],
-      bar_o[kWsCompute], bar_fin[kWsCompute];
-  __shared__ uint32_t tmem_base;
-  __shared__ int wg_abort[kWsCompute];
-  // CLS > 0: compile-time fast class; -1: fast layout with the class read
-  // from the plan (learned interpolation); 0: generic layout
-  constexpr bool FAST = CLS != 0;
-  const Plan P(M, false, FAST);
-  const WsPlan W(P);
-  uint8_t* sm = smem_raw;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int wg = warp >> 2, row = tid & (kRows - 1);
-
-  stage_shared<false>(M, P, sm, tid, blockDim.x);
-  // constant-one A block: every row (1, 1, 0, ..., 0)
-  for (int i = tid; i < kRows * 16 / 2; i += blockDim.x) {
-    const int chunk = i >> 2, e = i & 3;
-    reinterpret_cast<uint32_t*>(sm + W.cst)[i] =
-        (chunk < kRows && e == 0) ? tc::pack_f16x2(1.f, 1.f) : 0u;
-  }
-  if (warp == 0) {
-    tc::tmem_alloc(&tmem_base, 512);
-    tc::tmem_relinquish();
-  }
-  if (tid < kWsCompute) {
-    tc::mbar_init(&bar_x[tid], 4);
-    tc::mbar_init(&bar_h[tid], 4);
-    tc::mbar_init(&bar_d[tid], 1);
-    tc::mbar_init(&bar_o[tid], 1);
-    tc::mbar_init(&bar_fin[tid], 1);
-    wg_abort[tid] = 0;
-  }
-  if (wg < kWsCompute) zero_tail_groups<false>(P, SmemRow{smem_row(sm + W.x + wg * W.xbytes, row)});
-  tc::fence_mbar_init();
-  tc::fence_proxy_async();
-  tc::fence_before_sync();
-  __syncthreads();
-  tc::fence_after_sync();
-
-  const bool tri = filter == NTC_FILTER_TRILINEAR;
-  const int per_tile = tri ? kRows / 8 : kRows;
-  const int64_t ntiles = (n + per_tile - 1) / per_tile;
-  const int64_t stride = (int64_t)gridDim.x * kWsCompute;
-  constexpr uint32_t id64 = tc::idesc(kRows, kHidden), id16 = tc::idesc(kRows, kN3);
-  const int w = wg < kWsCompute ? wg : (warp & 3);  // the compute warpgroup served
-  const int64_t first = (int64_t)blockIdx.x * kWsCompute + w;
-  const uint32_t tw = tmem_base + 128u * w;
-
-  if (wg == kWsCompute) {
-    // ---- issuer warp w ------------------------------------------------------
-    if (lane == 0) {
-      const uint64_t* d = reinterpret_cast<const uint64_t*>(sm + P.desc);
-      const uint32_t xa = tc::smem_u32(sm + W.x + w * W.xbytes);
-      const uint64_t cst = tc::smem_desc(tc::smem_u32(sm + W.cst), 2048, 128);
-      const int k1 = P.k_int / 16;
-      uint32_t px = 0, ph = 0;
-      bool ok = true;
-      for (int64_t tl = first; tl < ntiles; tl += stride) {
-        if (!(ok = tc::mbar_wait(&bar_x[w], px, kWaitLimit))) break;
-        px ^= 1;
-        tc::fence_after_sync();
-        for (int s = 0; s < k1; ++s)
-          tc::mma_f16(tw, tc::smem_desc(xa + s * 4096, 2048, 128), d[s], id64, s > 0);
-        tc::mma_commit(&bar_d[w]);
-        if (!(ok = tc::mbar_wait(&bar_h[w], ph, kWaitLimit))) break;
-        ph ^= 1;
-        tc::fence_after_sync();
-        for (int s = 0; s < kHidden / 16; ++s)
-          tc::mma_f16_ta(tw, tw + kColH + 8 * s, d[kDescW2 + s], id64, s > 0);
-        tc::mma_f16(tw, cst, d[kDescW2 + 4], id64, 1);
-        tc::mma_commit(&bar_d[w]);
-        if (!(ok = tc::mbar_wait(&bar_h[w], ph, kWaitLimit))) break;
-        ph ^= 1;
-        tc::fence_after_sync();
-        for (int s = 0; s < kHidden / 16; ++s)
-          tc::mma_f16_ta(tw + kColD3, tw + kColH + 8 * s, d[kDescW3 + s], id16, s > 0);
-        tc::mma_f16(tw + kColD3, cst, d[kDescW3 + 4], id16, 1);
-        tc::mma_commit(&bar_o[w]);
-      }
-      if (!ok) *reinterpret_cast<volatile int*>(&wg_abort[w]) = 1;
-      // every MMA of this thread completes before TMEM is released
-      tc::mma_commit(&bar_fin[w]);
-      if (!tc::mbar_wait(&bar_fin[w], 0, kWaitLimit)) *reinterpret_cast<volatile int*>(&wg_abort[w]) = 1;
-    }
-  } else {
-    // ---- compute warpgroup w -------------------------------------------------
-    const uint32_t lq = (uint32_t)((warp & 3) * 32) << 16;
-    const uint32_t td = tw + lq, th = tw + kColH + lq, td3 = tw + kColD3 + lq;
-    const SmemRow xs{smem_row(sm + W.x + w * W.xbytes, row)};
-    const MipTab* tb = reinterpret_cast<const MipTab*>(sm + P.tab);
-    const FastK K(M);
-    volatile int* abort_flag = &wg_abort[w];
-    auto qindex = [&](int64_t t) { return tri ? t * per_tile + (row >> 3) : t * per_tile + row; };
-    auto build = [&](const Row& r) {
-      if (CLS > 0) build_fast(FastLayout<(CLS > 0 ? CLS : 1)>(), P, K, sm, r, xs);
-      else if (CLS < 0) build_fast(P, P, K, sm, r, xs);
-      else build_generic<false>(M, P, sm, r, xs, 1.f);
-      tc::fence_proxy_async();
-      __syncwarp();
-      if (lane == 0) tc::mbar_arrive(&bar_x[w]);
-    };
-    const int C = M.channels;
-    uint32_t pd = 0, po = 0;
-    int64_t tl = first;
-    int cur_valid = 0;
-    float cur_wtap = 0.f;
-    Row nxt;
-    Query nq;
-    if (tl < ntiles) {
-      Row r;
-      const int64_t q0 = qindex(tl);
-      locate(M, tb, load_query(uvl, q0, q0 < n), filter, row, r, q0, jkey);
-      if (CLS > 0) gather_fast(FastLayout<(CLS > 0 ? CLS : 1)>(), tb, r);
-      else if (CLS < 0) gather_fast(P, tb, r);
-      build(r);
-      cur_valid = r.valid;
-      cur_wtap = r.wtap;
-      const int64_t q1 = qindex(tl + stride);
-      locate(M, tb, load_query(uvl, q1, tl + stride < ntiles && q1 < n), filter, row, nxt, q1, jkey);
-      if (CLS > 0) gather_fast(FastLayout<(CLS > 0 ? CLS : 1)>(), tb, nxt);
-      else if (CLS < 0) gather_fast(P, tb, nxt);
-      const int64_t q2 = qindex(tl + 2 * stride);
-      nq = load_query(uvl, q2, tl + 2 * stride < ntiles && q2 < n);
-    }
-    for (; tl < ntiles; tl += stride) {
-      const int64_t q = qindex(tl);
-      const bool valid = cur_valid != 0;
-      const float wtap = cur_wtap;
-      // layer 1 -> H1
-      if (!tc::mbar_wait(&bar_d[w], pd, kWaitLimit)) *abort_flag = 1;
-      pd ^= 1;
-      tc::fence_after_sync();
-      hidden_epilogue_q(td, th, M.act);
-      tc::tmem_st_wait();
-      tc::fence_before_sync();
-      __syncwarp();
-      if (lane == 0) tc::mbar_arrive(&bar_h[w]);
-      // the next tile's input rows (layer 1 is done with X)
-      if (tl + stride < ntiles) {
-        build(nxt);
-        cur_valid = nxt.valid;
-        cur_wtap = nxt.wtap;
-      }
-      // layer 2 -> H2
-      if (!tc::mbar_wait(&bar_d[w], pd, kWaitLimit)) *abort_flag = 1;
-      pd ^= 1;
-      tc::fence_after_sync();
-      hidden_epilogue_q(td, th, M.act);
-      tc::tmem_st_wait();
-      tc::fence_before_sync();
-      __syncwarp();
-      if (lane == 0) tc::mbar_arrive(&bar_h[w]);
-      if (*abort_flag) break;
-      // the tile after next: texel and cells; its successor's query
-      locate(M, tb, nq, filter, row, nxt, qindex(tl + 2 * stride), jkey);
-      if (CLS > 0) gather_fast(FastLayout<(CLS > 0 ? CLS : 1)>(), tb, nxt);
-      else if (CLS < 0) gather_fast(P, tb, nxt);
-      {
-        const int64_t t3 = tl + 3 * stride;
-        const int64_t q3 = qindex(t3);
-        nq = load_query(uvl, q3, t3 < ntiles && q3 < n);
-      }
-      // layer 3 -> output
-      if (!tc::mbar_wait(&bar_o[w], po, kWaitLimit)) *abort_flag = 1;
-      po ^= 1;
-      tc::fence_after_sync();
-      float yv[16];
-      tc::tmem_ld16(td3, yv);
-      tc::tmem_ld_wait();
-      tc::fence_before_sync();
-      out_activate(yv, M.out_act);
-      if (tri) {
-#pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          float s = yv[c] * wtap;
-          s += __shfl_xor_sync(0xffffffffu, s, 1);
-          s += __shfl_xor_sync(0xffffffffu, s, 2);
-          s += __shfl_xor_sync(0xffffffffu, s, 4);
-          yv[c] = s;
-        }
-      }
-      if (valid && (!tri || (row & 7) == 0)) store_texel(out, out_dtype, q, C, yv);
-      if (*abort_flag) break;
-    }
-  }
-
-  tc::fence_before_sync();
-  __syncthreads();
-  if (tid == 0) {
-    int any = 0;
-    for (int i = 0; i < kWsCompute; ++i) any |= wg_abort[i];
-    if (any) atomicExch(status, NTC_ERR_TIMEOUT);
-  }
-  if (warp == 0) {
-    tc::fence_after_sync();
-    tc::tmem_dealloc(tmem_base, 512);
-  }
-}
-
-template <int CLS>
-cudaError_t launch_ws(const ntc_material& m, const float* uvl, int64_t n, void* out, int out_dtype,
-                      int filter, uint64_t jkey, cudaStream_t s) {
-  const Plan P(m, false, CLS != 0);
-  const WsPlan W(P);
-  cudaError_t e = cudaFuncSetAttribute(decode_ws_kernel<CLS>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)W.total);
-  if (e != cudaSuccess) return e;
-  const int per_tile = filter == NTC_FILTER_TRILINEAR ? kRows / 8 : kRows;
-  const int64_t tiles = (n + per_tile - 1) / per_tile;
-  const int64_t ctas = (tiles + kWsCompute - 1) / kWsCompute;
-  const int64_t cap = sm_count();
-  const int grid = (int)(ctas < cap ? ctas : cap);
-  decode_ws_kernel<CLS><<<grid, kWsThreads, W.total, s>>>(m, uvl, n, out, out_dtype, filter, jkey,
-                                                          status_word());
-  return cudaGetLastError();
-}
-
-// Compile-time class of a fast-layout grid: 0 (cell of 4 bytes), 1 (9-12
-// channels in 8 bytes), 2 (13-16 channels).
-int grid_class(int c, int cb) { return cb == 4 ? 0 : (c > 12 ? 2 : 1); }
 
 // ---------------------------------------------------------------------------
 // Many materials in one launch, warp-specialised.  The batch descriptor
@@ -591,19 +336,19 @@ cudaError_t launch_decode_ws_batched(const BatchHeader* dev, int64_t total_tiles
 
 cudaError_t launch_decode_ws(const ntc_material& m, const float* uvl, int64_t n, void* out,
                              int out_dtype, int filter, uint64_t jkey, cudaStream_t s, bool fast) {
-  if (!fast) return launch_ws<0>(m, uvl, n, out, out_dtype, filter, jkey, s);
+  if (!fast) return launch_ws<0, false>(m, uvl, n, out, out_dtype, filter, jkey, s);
   const Plan P(m, false, true);
-  if (P.learned) return launch_ws<-1>(m, uvl, n, out, out_dtype, filter, jkey, s);
+  if (P.learned) return launch_ws<-1, false>(m, uvl, n, out, out_dtype, filter, jkey, s);
   switch (1 + 3 * grid_class(m.c0, P.cb0) + grid_class(m.c1, P.cb1)) {
-    case 1: return launch_ws<1>(m, uvl, n, out, out_dtype, filter, jkey, s);
-    case 2: return launch_ws<2>(m, uvl, n, out, out_dtype, filter, jkey, s);
-    case 3: return launch_ws<3>(m, uvl, n, out, out_dtype, filter, jkey, s);
-    case 4: return launch_ws<4>(m, uvl, n, out, out_dtype, filter, jkey, s);
-    case 5: return launch_ws<5>(m, uvl, n, out, out_dtype, filter, jkey, s);
-    case 6: return launch_ws<6>(m, uvl, n, out, out_dtype, filter, jkey, s);
-    case 7: return launch_ws<7>(m, uvl, n, out, out_dtype, filter, jkey, s);
-    case 8: return launch_ws<8>(m, uvl, n, out, out_dtype, filter, jkey, s);
-    default: return launch_ws<9>(m, uvl, n, out, out_dtype, filter, jkey, s);
+    case 1: return launch_ws<1, false>(m, uvl, n, out, out_dtype, filter, jkey, s);
+    case 2: return launch_ws<2, false>(m, uvl, n, out, out_dtype, filter, jkey, s);
+    case 3: return launch_ws<3, false>(m, uvl, n, out, out_dtype, filter, jkey, s);
+    case 4: return launch_ws<4, false>(m, uvl, n, out, out_dtype, filter, jkey, s);
+    case 5: return launch_ws<5, false>(m, uvl, n, out, out_dtype, filter, jkey, s);
+    case 6: return launch_ws<6, false>(m, uvl, n, out, out_dtype, filter, jkey, s);
+    case 7: return launch_ws<7, false>(m, uvl, n, out, out_dtype, filter, jkey, s);
+    case 8: return launch_ws<8, false>(m, uvl, n, out, out_dtype, filter, jkey, s);
+    default: return launch_ws<9, false>(m, uvl, n, out, out_dtype, filter, jkey, s);
   }
 }
 

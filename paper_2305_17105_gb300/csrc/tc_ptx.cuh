@@ -232,6 +232,19 @@ __device__ __forceinline__ uint32_t pack_e4m3x2(float a, float b) {
   return (uint32_t)d;
 }
 
+// Two floats -> packed E4M3x2 of max(a, 0), max(b, 0), saturating.
+__device__ __forceinline__ uint32_t pack_e4m3x2_relu(float a, float b) {
+  uint16_t d;
+  asm("cvt.rn.satfinite.relu.e4m3x2.f32 %0, %1, %2;\n" : "=h"(d) : "f"(b), "f"(a));
+  return (uint32_t)d;
+}
+// Packed half2 -> packed E4M3x2 (byte 0 from the low half), saturating.
+__device__ __forceinline__ uint32_t h2_to_e4m3x2(uint32_t h2) {
+  uint16_t d;
+  asm("cvt.rn.satfinite.e4m3x2.f16x2 %0, %1;\n" : "=h"(d) : "r"(h2));
+  return (uint32_t)d;
+}
+
 // Logistic sigmoid through the hardware tanh approximation:
 // 1/(1+e^-z) = (1 + tanh(z/2)) / 2, one MUFU operation (max relative error of
 // tanh.approx about 2^-11, i.e. < 2.5e-4 absolute on the sigmoid).

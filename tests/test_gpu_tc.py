@@ -168,6 +168,53 @@ def test_decode_f8_close_to_oracle():
     assert oracle.psnr(ref, got) > 35.0
 
 
+@pytest.mark.parametrize("nwg", [4, 5])
+@pytest.mark.parametrize("shape", [
+    dict(width=512, height=512, channels=16, c0=12, c1=12, bits0=4, bits1=4),   # fast 8-byte cells
+    dict(width=256, height=256, channels=9, c0=16, c1=8, bits0=4, bits1=4),     # fast, 16 + 8
+    dict(width=256, height=128, channels=6, c0=8, c1=6, bits0=2, bits1=4),      # generic layout
+])
+def test_decode_f8_forms_close_to_oracle(shape, nwg):
+    """FP8-E4M3 decode (per-layer scales) on the warp-specialised kernel
+    (shape 5: fast 4-bit layout or generic) and the warpgroup-pipeline kernel
+    (shape 4), nearest and trilinear, against the oracle of the stored FP8
+    weights: E4M3 rounding of the layer inputs bounds the error, so the
+    bar is statistical (mean < 1e-2, PSNR > 35 dB)."""
+    case = make_case(k_in=64, seed=59, **shape)
+    mat, md = _f8_material(case)
+    q = gen.random_queries(3 * 4096 + 11, md.mips, seed=4059)
+    ntc.ntc_set_decode_warpgroups(nwg)
+    try:
+        got = _decode(mat, q)
+        tri = _decode(mat, q[:2000], filter=ntc.FILTER_TRILINEAR)
+    finally:
+        ntc.ntc_set_decode_warpgroups(0)
+    assert ntc.ntc_device_status() == ntc.OK
+    for g, r in ((got, md.decode(q)), (tri, md.decode_trilinear(q[:2000]))):
+        assert np.isfinite(g).all()
+        err = np.abs(g - r)
+        assert err.mean() < 1e-2, err.mean()
+        assert oracle.psnr(r, g) > 35.0
+
+
+def test_decode_f8_warp_specialised_matches_pipeline_kernel():
+    """The two FP8 kernels round the same layer inputs to E4M3 (the fast
+    layout through FP16 features): their outputs agree far inside the FP8
+    error."""
+    case = make_case(512, 512, 16, 12, 12, k_in=64, seed=60)
+    mat, md = _f8_material(case)
+    q = gen.random_queries(8192, md.mips, seed=4060)
+    outs = {}
+    for nwg in (4, 5):
+        ntc.ntc_set_decode_warpgroups(nwg)
+        try:
+            outs[nwg] = _decode(mat, q)
+        finally:
+            ntc.ntc_set_decode_warpgroups(0)
+    d = np.abs(outs[4] - outs[5])
+    assert d.mean() < 2e-3 and np.median(d) < 1e-3, (d.mean(), np.median(d))
+
+
 @pytest.mark.parametrize("nwg", [2, 3, 4, 5])
 def test_decode_every_launch_shape(nwg):
     case = make_case(512, 512, 16, 12, 12, k_in=48, seed=57)
