@@ -91,6 +91,7 @@ def _declare(L):
         "or_activation": (D, [I, D]),
         "or_activation_grad": (D, [I, D]),
         "or_features": (None, [P, I, I, I, P, P]),
+        "or_features_uvl": (None, [P, I64, P, P]),
         "or_decode_xym": (None, [P, I64, P, P, P, I]),
         "or_decode_uvl": (None, [P, I64, P, P, P, I]),
         "or_decode_trilinear": (None, [P, I64, P, P, I]),
@@ -199,6 +200,20 @@ def sample_batch(seed: int, step: int, batch: int, width: int, height: int, n_mi
     return out
 
 
+def round_e4m3(x) -> np.ndarray:
+    """Round to the nearest FP8-E4M3 value, ties to even, saturating at
+    +-448: the OCP 8-bit floating-point format with 1 sign bit, 4 exponent
+    bits (bias 7) and 3 mantissa bits, no infinities; binade [2^e, 2^(e+1))
+    holds multiples of 2^(e-3) for e >= -6, below 2^-6 the subnormals are
+    multiples of 2^-9."""
+    x = np.asarray(x, np.float64)
+    a = np.abs(x)
+    _, e = np.frexp(a)                           # a = f 2^e, f in [0.5, 1)
+    quantum = np.ldexp(1.0, np.maximum(e - 1, -6) - 3)
+    r = np.minimum(np.rint(a / quantum) * quantum, 448.0)   # rint: half to even
+    return np.copysign(r, x)
+
+
 def activation(act: int, z: float) -> float:
     return float(lib().or_activation(act, z))
 
@@ -264,6 +279,30 @@ class Model:
         _, nz = self._noise(noise)
         lib().or_features(C.byref(self._s), x, y, m, nz, _p(row))
         return row
+
+    def features_uvl(self, uvl):
+        """``[n, k_in]`` MLP input rows of the nearest texels of ``uvl``."""
+        uvl = np.ascontiguousarray(uvl, np.float32).reshape(-1, 3)
+        rows = np.empty((uvl.shape[0], self.k_in), np.float64)
+        lib().or_features_uvl(C.byref(self._s), uvl.shape[0], _p(uvl), _p(rows))
+        return rows
+
+    def decode_f8(self, uvl, s_w, s_a):
+        """Nearest decode in the FP8-E4M3 precision form: layer l computes
+        (s_w[l] s_a[l]) (W_l / s_w[l]) . e4m3(x_l / s_a[l]) + b_l, i.e. the
+        stored weights are this model's weights (already E4M3 values times
+        s_w[l]) and every layer input is rounded to E4M3 in units of its
+        activation scale; everything else in FP64."""
+        w = self.weights
+        x = self.features_uvl(uvl)
+        for l in range(3):
+            a = round_e4m3(x / s_a[l])
+            x = (s_w[l] * s_a[l]) * (a @ (w[2 * l] / s_w[l]).T) + w[2 * l + 1]
+            if l < 2:
+                x = np.vectorize(lambda v: activation(self.act, v))(x)
+        if self.out_act == 0:
+            x = 1.0 / (1.0 + np.exp(-x))
+        return x
 
     def decode_xym(self, xym, noise=None, threads=None):
         xym = np.ascontiguousarray(xym, np.int32).reshape(-1, 3)

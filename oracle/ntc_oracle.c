@@ -462,6 +462,15 @@ static void decode_uvl_job(job* jb, int64_t lo, int64_t hi) {
   mlp_free(&b);
 }
 
+/* The MLP input rows of the nearest texels of n queries (no noise). */
+void or_features_uvl(const or_model* md, int64_t n, const float* uvl, double* rows) {
+  for (int64_t i = 0; i < n; ++i) {
+    int x, y, m;
+    query_to_xym(md, uvl[3 * i], uvl[3 * i + 1], uvl[3 * i + 2], &x, &y, &m);
+    or_features(md, x, y, m, NULL, rows + i * (int64_t)md->k_in);
+  }
+}
+
 void or_decode_uvl(const or_model* md, int64_t n, const float* uvl, const or_noise* nz,
                    double* out, int nthreads) {
   nthreads = clamp_threads(nthreads, n);

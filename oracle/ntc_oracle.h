@@ -80,6 +80,7 @@ void or_positional_encoding(int x, int y, double* pe12);
 double or_activation(int act, double z);
 double or_activation_grad(int act, double z);
 void or_features(const or_model* md, int x, int y, int m, const or_noise* nz, double* row);
+void or_features_uvl(const or_model* md, int64_t n, const float* uvl, double* rows);
 void or_decode_xym(const or_model* md, int64_t n, const int32_t* xym, const or_noise* nz,
                    double* out, int nthreads);
 void or_decode_uvl(const or_model* md, int64_t n, const float* uvl, const or_noise* nz,

@@ -161,6 +161,49 @@ def test_crop_origins_uniform_and_independent():
     assert abs(r) < 0.05
 
 
+def test_e4m3_rounding_by_hand_and_against_torch():
+    """E4M3 rounding (OCP FP8: bias 7, 3 mantissa bits, max 448): hand values
+    (ties to even, subnormals, saturation), then torch's float8_e4m3fn cast
+    on float32 inputs inside the finite range."""
+    r = oracle.round_e4m3
+    hand = {1.0: 1.0, 1.0625: 1.0, 1.1875: 1.25, 2 ** -9: 2 ** -9, 2 ** -10: 0.0,
+            3 * 2 ** -11: 2 ** -9, 448.0: 448.0, 500.0: 448.0, 1e9: 448.0, 240.0: 240.0,
+            248.0: 256.0, -1.0625: -1.0, 0.0: 0.0, 0.3: 0.3125, 2 ** -6 * 1.0625: 2 ** -6}
+    for x, want in hand.items():
+        assert float(r(x)) == want, (x, float(r(x)), want)
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(7)
+    x = (rng.standard_normal(200_000) * np.exp2(rng.integers(-12, 9, 200_000))).astype(np.float32)
+    x = x[np.abs(x) <= 448.0].astype(np.float64)
+    ref = torch.from_numpy(x.astype(np.float32)).to(torch.float8_e4m3fn).to(torch.float64).numpy()
+    assert np.array_equal(r(x), ref)
+
+
+def test_decode_f8_structure():
+    """The FP8 form of the oracle: with the E4M3 rounding replaced by the
+    identity the scales cancel and it is the plain decode; with the rounding
+    on, each of the three layer inputs (K, 64, 64 values) is rounded once, in
+    units of its activation scale."""
+    from _cases import make_case
+    case = make_case(64, 64, 6, 8, 8, k_in=32, seed=31)
+    md = case.oracle_model()
+    q = np.random.default_rng(3).random((50, 3)).astype(np.float32)
+    q[:, 2] *= md.mips
+    s_w, s_a = [0.01, 0.02, 0.03], [1 / 256, 4 / 256, 4 / 256]
+    real = oracle.round_e4m3
+    calls = []
+    try:
+        oracle.round_e4m3 = lambda a: (calls.append(np.array(a)), np.asarray(a))[1]
+        ident = md.decode_f8(q, s_w, s_a)
+    finally:
+        oracle.round_e4m3 = real
+    assert np.abs(ident - md.decode(q)).max() < 1e-12
+    assert [c.shape[1] for c in calls] == [32, 64, 64]
+    assert np.abs(calls[0] * s_a[0] - md.features_uvl(q)).max() < 1e-12
+    f8 = md.decode_f8(q, s_w, s_a)
+    assert 0 < np.abs(f8 - ident).max() < 0.1
+
+
 # ----------------------------------------------------------- quantisation ---
 @pytest.mark.parametrize("bits", [1, 2, 4, 8])
 def test_quantizer_levels_and_roundtrip(bits):
