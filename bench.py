@@ -316,6 +316,42 @@ def render_eval(ntc, tr, target, chain, batch, seed, extra_steps, stream):
     return res
 
 
+def equal_psnr_eval(ntc, chain, batch, seed, stream, steps=1500):
+    """Training precision at equal steps: the training material compressed
+    twice from the same initialisation and samples, once with the FP16
+    tensor-core step and once with the FP32 CUDA-core step, `steps` steps
+    each; both exports (4-bit grids) decoded in the FP32 form at every texel
+    of mip 0 and compared with the 8-bit reference (PSNR), with the time of
+    each training run."""
+    import torch
+    ys, xs = np.meshgrid(np.arange(TRN_SIDE), np.arange(TRN_SIDE), indexing="ij")
+    t0 = torch.from_numpy(np.stack([(xs + 0.5) / TRN_SIDE, (ys + 0.5) / TRN_SIDE,
+                                    np.zeros_like(xs, float)], -1).reshape(-1, 3)
+                          .astype(np.float32)).cuda()
+    refm = torch.from_numpy(chain[0].reshape(-1, TRN_C).astype(np.float32) / 255.0).cuda()
+    res = {"workload": f"{TRN_SIDE}^2x{TRN_C} material, {steps} steps of {batch} texels from the "
+                       "same initialisation and samples; PSNR of mip 0 of the 4-bit export "
+                       "(decoded in FP32) against the 8-bit reference", "steps": steps}
+    for prec in ("f16", "f32"):
+        tr, target, _, _, _ = make_trainer(prec, steps)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            ntc.ntc_train_step(tr, target, batch, seed)
+        b.record(stream)
+        torch.cuda.synchronize()
+        dec = ntc.ntc_decode(tr.export(ntc.PREC_F32), t0)
+        mse = float(((dec - refm) ** 2).mean())
+        res[f"train_s_{prec}"] = a.elapsed_time(b) / 1e3
+        res[f"psnr_db_{prec}_trained"] = 10 * math.log10(1.0 / mse)
+        res[f"status_{prec}"] = ntc.ntc_device_status()
+        del tr, target
+    res["delta_db"] = res["psnr_db_f16_trained"] - res["psnr_db_f32_trained"]
+    res["speedup_f16_over_f32"] = res["train_s_f32"] / res["train_s_f16"]
+    return res
+
+
 # ----------------------------------------------------------------------------
 # The paper's decoder form: learned interpolation of G0, hardGELU, identity
 # ----------------------------------------------------------------------------
@@ -798,6 +834,13 @@ def main():
         except Exception as e:  # reported, never fatal to the headline line
             paper_form = {"error": f"{type(e).__name__}: {e}"[:300]}
 
+    equal = None
+    if not args.no_extras and not args.no_fp32_compare:
+        try:
+            equal = equal_psnr_eval(ntc, chain, args.batch, seed, stream)
+        except Exception as e:  # reported, never fatal to the headline line
+            equal = {"error": f"{type(e).__name__}: {e}"[:300]}
+
     multi = None
     if not args.no_multi:
         try:
@@ -822,6 +865,7 @@ def main():
         "decode_ms": statistics.median(dec_ms), "train_ms": statistics.median(trn_ms),
         "roofline": roof, "tuning": tuning, "e2e": e2e, "fp32_path": fp32, "cpu_baseline": cpu,
         "render": render, "multi_material": multi, "paper_form": paper_form, "train_crops": crops,
+        "equal_psnr_training": equal,
         "gpu_launches": kernels_per_step * args.steps,
         "clocks": clk.summary(), "wall_s": t_wall,
     }

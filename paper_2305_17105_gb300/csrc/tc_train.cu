@@ -1,33 +1,36 @@
 // Tensor-core (tcgen05) fused forward + L2 loss + backward of the NTC
 // optimisation step (Sec. 4.2, 4.5, 5.1), FP16 operands, FP32 accumulation.
 //
-// One persistent CTA per SM runs two warpgroup pipelines; a warpgroup owns a
-// stream of tiles of 128 training texels (one per thread = one row = one
-// TMEM lane).  Per tile, with every activation kept on chip:
+// One persistent CTA per SM runs NWG warpgroup pipelines (3 when their tiles
+// fit in shared memory, else 2); a warpgroup owns a stream of tiles of 128
+// training texels (one per thread = one row = one TMEM lane).  Per tile, with
+// every activation kept on chip:
 //   forward   X -> Z1 = X W1^T (+b1) -> H1 = act(Z1) -> Z2 (+b2) -> H2 -> Z3 (+b3)
 //             -> y = out(Z3), loss, dZ3 = 2 (y - t) out'(Z3)
-//   backward  dH2 = dZ3 W3, dZ2 = dH2 * act'(Z2), dH1 = dZ2 W2,
-//             dZ1 = dH1 * act'(Z1), dX = dZ1 W1 -> scatter-add into the grid
-//             gradients through the taps (FP32 atomics): bilinear weights for
-//             a bilinear grid, weight 1 per tap slot for learned
-//             interpolation of G0 (Sec. 4.3.1)
-//   weights   [dW1 db1; dW2 db2] += [dZ1^T; dZ2^T] [X | H1] and
-//             [dW3^T; db3] += [H2^T; 1] dZ3, accumulated in TMEM over all of
-//             the CTA's tiles and added to global memory once at the end.
-// X, H1, H2, dZ1, dZ2, dZ3 are FP16 tiles in shared memory, stored one row
-// per texel in the canonical K-major layout (8 x 16-byte core matrices, row
-// group fastest).  The same bytes serve as K-major A operands of the forward
-// and backward layers and, read with the MN-major descriptor mode (K = the
-// 128 texels), as the operands of the weight-gradient MMAs.  The backward
-// layers read the forward weight tiles as MN-major B operands (no transposed
-// copies).  The biases of layer 1 ride in X's two constant-one slots, so the
-// same X columns of the [dW1; dW2] accumulator give db1 and db2.  ReLU's
-// derivative is read back from the sign of H; hardGELU's act'(Z) is written
-// in FP16 into the dZ tile of its layer by the forward epilogue and
-// multiplied in place by the backward one.  dZ3 carries the loss scale B*C
-// (2 (y - t) instead of 2 (y - t) / (B C)) so it stays well inside FP16's
-// range; every gradient is multiplied by 1 / (B C) in FP32 when it leaves the
-// chip.
+//   backward  dH2 = dZ3 W3 and [dW3^T; db3] += [H2^T; 1] dZ3;
+//             dZ2 = dH2 * act'(Z2) (over H2); dH1 = dZ2 W2 and
+//             [dW2 db2] += dZ2^T [H1 | 1]; dZ1 = dH1 * act'(Z1) (over H1);
+//             dX = dZ1 W1 and [dW1 db1] += dZ1^T X; dX -> scatter-add into
+//             the grid gradients through the taps (FP32 atomics): bilinear
+//             weights for a bilinear grid, weight 1 per tap slot for learned
+//             interpolation of G0 (Sec. 4.3.1).
+// The weight-gradient accumulators live in TMEM once per CTA, shared by its
+// pipelines (zeroed at the start; every pipeline's MMAs add into them, the
+// tensor pipe applies them in order) and leave it once at the end.  Each
+// weight gradient is issued as soon as its operands exist, so dZ2 and dZ1
+// overwrite H2 and H1 in place.  X, H1, H2, dZ3 are FP16 tiles in shared
+// memory, one row per texel in the canonical K-major layout (8 x 16-byte core
+// matrices, row group fastest): K-major A operands of the layers and, read
+// with the MN-major descriptor mode (K = the 128 texels), operands of the
+// weight-gradient MMAs; those take M = 128 rows from 16 consecutive groups,
+// of which the first 8 (or 9) are meaningful.  The backward layers read the
+// forward weight tiles as MN-major B operands (no transposed copies).  The
+// biases of layer 1 ride in X's two constant-one slots, so X's columns of
+// the dW1 accumulator give db1.  ReLU's derivative is read back from the sign
+// of H; hardGELU's act'(Z) is written in FP16 into a G tile by the forward
+// epilogue.  dZ3 carries the loss scale B*C (2 (y - t) instead of
+// 2 (y - t) / (B C)) so it stays well inside FP16's range; every gradient is
+// multiplied by 1 / (B C) in FP32 when it leaves the chip.
 #include <cuda_fp16.h>
 
 #include "ntc_device.cuh"
@@ -40,28 +43,35 @@ namespace {
 
 constexpr int kRows = 128;
 constexpr int kN3 = 16;
-constexpr int kNWG = 2;                 // warpgroup pipelines per CTA
-constexpr uint32_t kCols = 512;         // 2 x 256 TMEM columns
+constexpr int kMaxNWG = 3;              // warpgroup pipelines per CTA (at most)
+constexpr uint32_t kCols = 512;         // TMEM columns of the CTA
 constexpr uint32_t kGroup = 2048;       // bytes per 8-unit group of a 128-row tile
 constexpr uint32_t kWaitLimit = 1u << 18;  // suspended tries: ms to seconds
 constexpr int kDxStride = 84;           // floats per row of the dX staging rows
+constexpr uint32_t kSmemMax = 232448u - 2048u;  // dynamic shared memory (static reserve)
 
 // Shared-memory and TMEM plan.  Input slots: G0 groups (c0 values, or the
 // four taps' 4 c0 values with learned interpolation), G1 groups,
 // [PE0..7][PE8..11, LOD, 0, 1, 1], zero groups up to k_int.
 struct TPlan {
-  int w0, f0, f1, gpe, k_int, dx_n;
+  int w0, f0, f1, gpe, k_int, dx_n, nwg;
   uint32_t w1, w2, w3, wb2, wb3, tab, wg0, wg_bytes, total;
-  uint32_t colD, colW12, colW3, cols;  // TMEM columns of one warpgroup
-  // offsets inside one warpgroup's region
-  uint32_t P, X, H1, R, H2, ONE, Q, DZ1, DZ2, DZ3;
-  __host__ __device__ TPlan(int c0, int c1, bool learned) {
+  uint32_t dmax, colW1, colW2, colW3, cols;  // TMEM: D of pipeline p at p dmax, then the
+                                             // shared weight-gradient accumulators
+  // offsets inside one pipeline's region, in this order (the MN-major reads
+  // of 16 groups from H1 or H2 stay inside it): H1 (= dZ1), ONEa (2 groups:
+  // the K = 16 bias steps and the ones column of dW2), H2 (= dZ2), ONEb (1
+  // group: the db3 row of dW3), DZ3, X, and for hardGELU G1, G2 (act'(Z1),
+  // act'(Z2))
+  uint32_t H1, ONEa, H2, ONEb, DZ3, X, G1, G2;
+  __host__ __device__ TPlan(int c0, int c1, bool learned, bool gelu, int n_wg) {
     w0 = learned ? 4 * c0 : c0;
     f0 = (w0 + 7) / 8;
     f1 = (c1 + 7) / 8;
     gpe = f0 + f1;
     k_int = (8 * (gpe + 2) + 15) / 16 * 16;
     dx_n = (8 * gpe + 15) / 16 * 16;     // dX columns: the grid slots
+    nwg = n_wg;
     uint32_t o = 0;
     w1 = o;  o += kHidden * k_int * 2;   // W1 [64][k_int]: B of layer 1, MN-major B of dX
     w2 = o;  o += kHidden * kHidden * 2; // W2: B of layer 2, MN-major B of dH1
@@ -72,28 +82,26 @@ struct TPlan {
     tab = o; o += 16 * 16 * 4;           // per-mip table (MipTabT)
     o = (o + 1023) / 1024 * 1024;
     wg0 = o;
-    // per warpgroup: P = [X | H1], R = [H2 | ONE], Q = [dZ1 | dZ2], DZ3;
-    // R must be followed by Q: the dW3 operand reads 16 groups from R's start
-    P = 0;
-    X = P;
-    H1 = X + (k_int / 8) * kGroup;
-    R = H1 + 8 * kGroup;
-    H2 = R;
-    ONE = H2 + 8 * kGroup;
-    Q = ONE + 2 * kGroup;
-    DZ1 = Q;
-    DZ2 = DZ1 + 8 * kGroup;
-    DZ3 = DZ2 + 8 * kGroup;
-    wg_bytes = DZ3 + 2 * kGroup;
-    total = wg0 + kNWG * wg_bytes;
-    colD = 0;
-    colW12 = dx_n > kHidden ? dx_n : kHidden;
-    colW3 = colW12 + k_int + kHidden;
+    H1 = 0;
+    ONEa = H1 + 8 * kGroup;
+    H2 = ONEa + 2 * kGroup;
+    ONEb = H2 + 8 * kGroup;
+    DZ3 = ONEb + 1 * kGroup;
+    X = DZ3 + 2 * kGroup;
+    G1 = X + (k_int / 8) * kGroup;
+    G2 = G1 + (gelu ? 8 * kGroup : 0);
+    wg_bytes = G2 + (gelu ? 8 * kGroup : 0);
+    if (wg_bytes < H2 + 16 * kGroup) wg_bytes = H2 + 16 * kGroup;
+    total = wg0 + nwg * wg_bytes;
+    dmax = dx_n > kHidden ? dx_n : kHidden;
+    colW1 = nwg * dmax;
+    colW2 = colW1 + k_int;
+    colW3 = colW2 + kHidden + 16;
     cols = colW3 + kN3;
   }
-  // fits one CTA: shared memory, 256 TMEM columns per warpgroup, the dX rows
+  // fits one CTA: shared memory, TMEM, the dX staging rows
   __host__ __device__ bool fits() const {
-    return total + 2048u <= 232448u && cols <= 256u && (uint32_t)kRows * kDxStride * 4 <= wg_bytes &&
+    return total <= kSmemMax && cols <= kCols && (uint32_t)kRows * kDxStride * 4 <= wg_bytes &&
            dx_n <= kDxStride;
   }
 };
@@ -178,13 +186,14 @@ __device__ void stage_train(const ntc_material& M, const TPlan& P, uint8_t* sm) 
     tb->level[m] = level_of_mip(m, M.levels);
     tb->lodn[m] = M.mips > 1 ? (float)m / (float)(M.mips - 1) : 0.f;
   }
-  // constant-one group of every warpgroup (columns 0 and 1 of ONE)
-  for (int i = tid; i < kNWG * kRows * 2; i += nt) {
-    const int w = i / (kRows * 2), r = (i / 2) % kRows, which = i & 1;
-    uint8_t* base = sm + P.wg0 + w * P.wg_bytes + P.ONE;
+  // the constant-one tiles of every pipeline: columns 0 and 1 are one
+  // (ONEa: groups 0 and 1, ONEb: group 0)
+  for (int i = tid; i < P.nwg * 3 * kRows; i += nt) {
+    const int w = i / (3 * kRows), t = (i / kRows) % 3, r = i % kRows;
+    uint8_t* base = sm + P.wg0 + w * P.wg_bytes + (t == 2 ? P.ONEb : P.ONEa);
     const uint4 one = make_uint4(tc::pack_f16x2(1.f, 1.f), 0u, 0u, 0u);
-    *reinterpret_cast<uint4*>(base + tc::canon_chunk(r, which, kRows)) =
-        which ? make_uint4(0, 0, 0, 0) : one;
+    *reinterpret_cast<uint4*>(base + tc::canon_chunk(r, t == 1 ? 1 : 0, kRows)) =
+        t == 1 ? make_uint4(0, 0, 0, 0) : one;
   }
 }
 
@@ -318,7 +327,7 @@ __device__ __forceinline__ void issue_kmn(uint32_t d, uint32_t a, uint32_t a_lbo
 }
 
 // Forward epilogue of a hidden layer: H = act(Z) into `htile`; hardGELU
-// also writes act'(Z) into `gtile` (the layer's dZ tile).
+// also writes act'(Z) into `gtile`.
 template <int ACT>
 __device__ __forceinline__ void hidden_forward(uint32_t taddr, uint8_t* htile, uint8_t* gtile,
                                                int row) {
@@ -344,14 +353,15 @@ __device__ __forceinline__ void hidden_forward(uint32_t taddr, uint8_t* htile, u
   }
 }
 
-// Backward epilogue: dZ = dH * act'(Z) into `dztile` (ReLU: the sign of H;
-// hardGELU: the act'(Z) the forward left in `dztile`, replaced in place).
+// Backward epilogue: dZ = dH * act'(Z) over the layer's H tile (this row is
+// read before it is overwritten): ReLU takes act' from the sign of H,
+// hardGELU from the forward's G tile.
 template <int ACT>
-__device__ __forceinline__ void hidden_backward(uint32_t taddr, const uint8_t* htile,
-                                                uint8_t* dztile, int row) {
+__device__ __forceinline__ void hidden_backward(uint32_t taddr, const uint8_t* gtile,
+                                                uint8_t* htile, int row) {
   __half2 h[32];
-  tile_row64(ACT == NTC_ACT_HARDGELU ? dztile : htile, row, h);
-  row64_to_tile(taddr, dztile, row, [&](int q, float g) {
+  tile_row64(ACT == NTC_ACT_HARDGELU ? gtile : htile, row, h);
+  row64_to_tile(taddr, htile, row, [&](int q, float g) {
     return ACT == NTC_ACT_HARDGELU ? g * half_of(h, q) : (half_of(h, q) > 0.f ? g : 0.f);
   });
 }
@@ -428,37 +438,49 @@ __device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t& phase, int b
   return !tc::bar_or(bar_id, kRows, !ok);
 }
 
-template <int ACT, bool LEARNED>
-__global__ void __launch_bounds__(kRows* kNWG, 1) train_tc_kernel(const ntc_material M,
-                                                                   const BwdArgs A, int* status) {
+template <int ACT, bool LEARNED, int NWG>
+__global__ void __launch_bounds__(kRows* NWG, 1) train_tc_kernel(const ntc_material M,
+                                                                  const BwdArgs A, int* status) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
-  __shared__ uint64_t mbar[kNWG];
+  __shared__ uint64_t mbar[NWG], fin[NWG];
   __shared__ uint32_t tmem_base;
   __shared__ int abort_any;
-  __shared__ float red[kNWG * 4];
-  const TPlan P(M.c0, M.c1, LEARNED);
+  __shared__ float red[NWG * 4];
+  const TPlan P(M.c0, M.c1, LEARNED, ACT == NTC_ACT_HARDGELU, NWG);
   uint8_t* sm = smem_raw;
   const int tid = threadIdx.x, warp = tid >> 5;
   const int wg = tid / kRows, row = tid % kRows;
   const int bar_id = 1 + wg;
   const int C = M.channels;
+  const uint32_t lane = (uint32_t)((warp & 3) * 32) << 16;
 
   stage_train(M, P, sm);
   if (warp == 0) {
     tc::tmem_alloc(&tmem_base, kCols);
     tc::tmem_relinquish();
   }
-  if (tid < kNWG) tc::mbar_init(&mbar[tid], 1);
+  if (tid < NWG) {
+    tc::mbar_init(&mbar[tid], 1);
+    tc::mbar_init(&fin[tid], 1);
+  }
   if (tid == 0) abort_any = 0;
   tc::fence_mbar_init();
   tc::fence_proxy_async();
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
+  // the shared weight-gradient accumulators start at zero (warpgroup 0 holds
+  // every lane; every MMA into them accumulates)
+  if (wg == 0) {
+    const uint32_t z[16] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (uint32_t c = P.colW1; c < P.cols; c += 16) tc::tmem_st16(tmem_base + c + lane, z);
+    tc::tmem_st_wait();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
 
-  const uint32_t tw = tmem_base + 256u * wg;
-  const uint32_t tD = tw + P.colD;
-  const uint32_t lane = (uint32_t)((warp & 3) * 32) << 16;
+  const uint32_t tD = tmem_base + P.dmax * wg;
   uint64_t* bar = &mbar[wg];
   uint8_t* W = sm + P.wg0 + wg * P.wg_bytes;
   const uint32_t sW = tc::smem_u32(W), sbase = tc::smem_u32(sm);
@@ -467,19 +489,20 @@ __global__ void __launch_bounds__(kRows* kNWG, 1) train_tc_kernel(const ntc_mate
   constexpr uint32_t id64 = tc::idesc(kRows, kHidden), id16 = tc::idesc(kRows, kN3);
   constexpr uint32_t idb = 1u << 16, ida = 1u << 15;  // B / A read MN-major
   const uint32_t id_dx = tc::idesc(kRows, P.dx_n) | idb;
-  const uint32_t id_w12 = tc::idesc(kRows, P.k_int + kHidden) | ida | idb;
-  const uint32_t id_w3 = tc::idesc(kRows, kN3) | ida | idb;
+  const uint32_t id_w1 = tc::idesc(kRows, P.k_int) | ida | idb;
+  constexpr uint32_t id_w2 = tc::idesc(kRows, kHidden + 16) | ida | idb;
+  constexpr uint32_t id_w3 = tc::idesc(kRows, kN3) | ida | idb;
+  const uint32_t tW1 = tmem_base + P.colW1, tW2 = tmem_base + P.colW2, tW3 = tmem_base + P.colW3;
 
   const int64_t step = A.step_dev ? *A.step_dev : A.noise_step;
   const uint64_t nkey = rng_key(A.noise_seed, noise_stream(step));
   const uint64_t skey = rng_key(A.sample_seed, sampler_stream(step));
   const int64_t ntiles = (A.n + kRows - 1) / kRows;
   uint32_t phase = 0;
-  uint32_t acc = 0;  // weight-gradient accumulators start empty
   float loss_acc = 0.f;
   bool aborted = false;
 
-  for (int64_t tl = (int64_t)blockIdx.x * kNWG + wg; tl < ntiles; tl += (int64_t)gridDim.x * kNWG) {
+  for (int64_t tl = (int64_t)blockIdx.x * NWG + wg; tl < ntiles; tl += (int64_t)gridDim.x * NWG) {
     const int64_t i = tl * kRows + row;
     const bool valid = i < A.n;
     // ---- texel, target, features -> X -----------------------------------
@@ -554,7 +577,7 @@ __global__ void __launch_bounds__(kRows* kNWG, 1) train_tc_kernel(const ntc_mate
     }
     if (!wait_phase(bar, phase, bar_id)) { aborted = true; break; }
     tc::fence_after_sync();
-    hidden_forward<ACT>(tD + lane, W + P.H1, W + P.DZ1, row);
+    hidden_forward<ACT>(tD + lane, W + P.H1, W + P.G1, row);
     tc::fence_before_sync();
     tc::fence_proxy_async();
     tc::bar_sync(bar_id, kRows);
@@ -563,12 +586,12 @@ __global__ void __launch_bounds__(kRows* kNWG, 1) train_tc_kernel(const ntc_mate
     if (row == 0) {
       tc::fence_after_sync();
       issue_kmajor(tD, sW + P.H1, lbo_a, sbase + P.w2, lbo64, 4, id64, 0);
-      issue_kmajor(tD, sW + P.ONE, lbo_a, sbase + P.wb2, lbo64, 1, id64, 1);
+      issue_kmajor(tD, sW + P.ONEa, lbo_a, sbase + P.wb2, lbo64, 1, id64, 1);
       tc::mma_commit(bar);
     }
     if (!wait_phase(bar, phase, bar_id)) { aborted = true; break; }
     tc::fence_after_sync();
-    hidden_forward<ACT>(tD + lane, W + P.H2, W + P.DZ2, row);
+    hidden_forward<ACT>(tD + lane, W + P.H2, W + P.G2, row);
     tc::fence_before_sync();
     tc::fence_proxy_async();
     tc::bar_sync(bar_id, kRows);
@@ -577,7 +600,7 @@ __global__ void __launch_bounds__(kRows* kNWG, 1) train_tc_kernel(const ntc_mate
     if (row == 0) {
       tc::fence_after_sync();
       issue_kmajor(tD, sW + P.H2, lbo_a, sbase + P.w3, lbo16, 4, id16, 0);
-      issue_kmajor(tD, sW + P.ONE, lbo_a, sbase + P.wb3, lbo16, 1, id16, 1);
+      issue_kmajor(tD, sW + P.ONEa, lbo_a, sbase + P.wb3, lbo16, 1, id16, 1);
       tc::mma_commit(bar);
     }
     if (!wait_phase(bar, phase, bar_id)) { aborted = true; break; }
@@ -608,41 +631,41 @@ __global__ void __launch_bounds__(kRows* kNWG, 1) train_tc_kernel(const ntc_mate
     tc::fence_proxy_async();
     tc::bar_sync(bar_id, kRows);
 
-    // ---- dH2 = dZ3 W3 -> dZ2 ------------------------------------------------------
+    // ---- dH2 = dZ3 W3; [dW3^T; db3] += [H2^T; 1] dZ3; then dZ2 over H2 ---------
     if (row == 0) {
       tc::fence_after_sync();
       issue_kmn(tD, sW + P.DZ3, lbo_a, sbase + P.w3, (kN3 / 8) * 128, 1, id64 | idb);
+      issue_mnmajor(tW3, sW + P.H2, sW + P.DZ3, id_w3, 1);
       tc::mma_commit(bar);
     }
     if (!wait_phase(bar, phase, bar_id)) { aborted = true; break; }
     tc::fence_after_sync();
-    hidden_backward<ACT>(tD + lane, W + P.H2, W + P.DZ2, row);
+    hidden_backward<ACT>(tD + lane, W + P.G2, W + P.H2, row);
     tc::fence_before_sync();
     tc::fence_proxy_async();
     tc::bar_sync(bar_id, kRows);
 
-    // ---- dH1 = dZ2 W2 -> dZ1 ------------------------------------------------------
+    // ---- dH1 = dZ2 W2; [dW2 db2] += dZ2^T [H1 | 1]; then dZ1 over H1 ----------
     if (row == 0) {
       tc::fence_after_sync();
-      issue_kmn(tD, sW + P.DZ2, lbo_a, sbase + P.w2, lbo64, 4, id64 | idb);
+      issue_kmn(tD, sW + P.H2, lbo_a, sbase + P.w2, lbo64, 4, id64 | idb);
+      issue_mnmajor(tW2, sW + P.H2, sW + P.H1, id_w2, 1);
       tc::mma_commit(bar);
     }
     if (!wait_phase(bar, phase, bar_id)) { aborted = true; break; }
     tc::fence_after_sync();
-    hidden_backward<ACT>(tD + lane, W + P.H1, W + P.DZ1, row);
+    hidden_backward<ACT>(tD + lane, W + P.G1, W + P.H1, row);
     tc::fence_before_sync();
     tc::fence_proxy_async();
     tc::bar_sync(bar_id, kRows);
 
-    // ---- dX = dZ1 W1, and the weight gradients of this tile ---------------------
+    // ---- dX = dZ1 W1; [dW1 db1] += dZ1^T X ------------------------------------
     if (row == 0) {
       tc::fence_after_sync();
-      issue_kmn(tD, sW + P.DZ1, lbo_a, sbase + P.w1, lbo64, 4, id_dx);
-      issue_mnmajor(tw + P.colW12, sW + P.Q, sW + P.P, id_w12, acc);
-      issue_mnmajor(tw + P.colW3, sW + P.R, sW + P.DZ3, id_w3, acc);
+      issue_kmn(tD, sW + P.H1, lbo_a, sbase + P.w1, lbo64, 4, id_dx);
+      issue_mnmajor(tW1, sW + P.H1, sW + P.X, id_w1, 1);
       tc::mma_commit(bar);
     }
-    acc = 1;
     if (!wait_phase(bar, phase, bar_id)) { aborted = true; break; }
     tc::fence_after_sync();
     if (A.grids && LEARNED) {
@@ -669,6 +692,13 @@ __global__ void __launch_bounds__(kRows* kNWG, 1) train_tc_kernel(const ntc_mate
           scatter_taps(g, M.c1, bilinear_taps(x, y, wm, hm, L.g1_w, L.g1_h), dxs + 8 * P.f0, 0,
                        true, A.grad_scale);
       }
+      // the staging rows ran over the constant-one tiles: once every row has
+      // been read, each thread writes its row's chunks back
+      tc::bar_sync(bar_id, kRows);
+      const uint4 one = make_uint4(tc::pack_f16x2(1.f, 1.f), 0u, 0u, 0u);
+      *reinterpret_cast<uint4*>(W + P.ONEa + tc::canon_chunk(row, 0, kRows)) = one;
+      *reinterpret_cast<uint4*>(W + P.ONEa + tc::canon_chunk(row, 1, kRows)) = make_uint4(0, 0, 0, 0);
+      *reinterpret_cast<uint4*>(W + P.ONEb + tc::canon_chunk(row, 0, kRows)) = one;
     } else if (A.grids) {
       // dX slots: G0 at columns 0.., G1 at 8 * f0.. (f0 is 1 or 2)
       float d[32], dg0[16], dg1[16];
@@ -718,48 +748,66 @@ __global__ void __launch_bounds__(kRows* kNWG, 1) train_tc_kernel(const ntc_mate
       }
     }
     tc::fence_before_sync();
+    if (LEARNED) tc::fence_proxy_async();  // restored constants, read by the next tile's MMAs
     tc::bar_sync(bar_id, kRows);  // the next tile's features overwrite the operand tiles
   }
 
-  // ---- flush the weight gradients of this warpgroup ----------------------------
-  if (aborted && row == 0) abort_any = 1;
+  // ---- every MMA of this pipeline has completed (bounded) ---------------------
+  if (row == 0) {
+    tc::fence_after_sync();
+    tc::mma_commit(&fin[wg]);
+    if (!tc::mbar_wait(&fin[wg], 0, kWaitLimit)) aborted = true;
+    if (aborted) abort_any = 1;
+  }
+  tc::fence_before_sync();
+  __syncthreads();
   tc::fence_after_sync();
+
+  // ---- flush the CTA's weight gradients ----------------------------------------
   const float gs = A.grad_scale;
-  if (!aborted && acc) {
-    // [dW1 db1; dW2 db2]: row r < 64 -> dW1 row r (X columns; the head
-    // constant-one slot gives db1 r), else dW2 row r-64 (H1 columns; the
-    // head slot gives db2 r-64)
-    const int kin = P.k_int;
+  const int wq = warp & 3;  // lane quarter of this warp: rows 32 wq .. 32 wq + 31
+  const int r = 32 * wq + (tid & 31);
+  if (!abort_any && (int64_t)blockIdx.x * NWG < ntiles) {
+    if (wg == 0 && wq < 2) {
+      // [dW1 db1]: row r, X columns (the head constant-one slot gives db1 r)
 #pragma unroll 1
-    for (int cb = 0; cb < kin + kHidden; cb += 16) {
-      float v[16];
-      tc::tmem_ld16(tw + P.colW12 + lane + cb, v);
-      tc::tmem_ld_wait();
+      for (int cb = 0; cb < P.k_int; cb += 16) {
+        float v[16];
+        tc::tmem_ld16(tW1 + lane + cb, v);
+        tc::tmem_ld_wait();
 #pragma unroll
-      for (int e = 0; e < 16; ++e) {
-        const int col = cb + e;
-        if (col < kin) {
-          const int uc = slot_column(M, P, col);
-          if (row < kHidden) {
-            if (uc >= 0 && A.g.w[0]) atomicAdd(A.g.w[0] + row * M.k_in + uc, v[e] * gs);
-            else if (uc == -2 && A.g.b[0]) atomicAdd(A.g.b[0] + row, v[e] * gs);
-          } else if (uc == -2 && A.g.b[1]) {
-            atomicAdd(A.g.b[1] + (row - kHidden), v[e] * gs);
-          }
-        } else if (row >= kHidden && A.g.w[1]) {
-          atomicAdd(A.g.w[1] + (row - kHidden) * kHidden + (col - kin), v[e] * gs);
+        for (int e = 0; e < 16; ++e) {
+          const int uc = slot_column(M, P, cb + e);
+          if (uc >= 0 && A.g.w[0]) atomicAdd(A.g.w[0] + r * M.k_in + uc, v[e] * gs);
+          else if (uc == -2 && A.g.b[0]) atomicAdd(A.g.b[0] + r, v[e] * gs);
+        }
+      }
+    } else if (wg == 1 && wq < 2) {
+      // [dW2 db2]: row r, H1 columns 0..63, the ones column 64 gives db2 r
+#pragma unroll 1
+      for (int cb = 0; cb < kHidden + 16; cb += 16) {
+        float v[16];
+        tc::tmem_ld16(tW2 + lane + cb, v);
+        tc::tmem_ld_wait();
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          const int col = cb + e;
+          if (col < kHidden && A.g.w[1]) atomicAdd(A.g.w[1] + r * kHidden + col, v[e] * gs);
+          else if (col == kHidden && A.g.b[1]) atomicAdd(A.g.b[1] + r, v[e] * gs);
         }
       }
     }
-    // [dW3^T; db3]: row r < 64 -> dW3[:, r]; row 64 -> db3
-    float v[16];
-    tc::tmem_ld16(tw + P.colW3 + lane, v);
-    tc::tmem_ld_wait();
+    if (wg == NWG - 1 && wq < 3) {
+      // [dW3^T; db3]: row r < 64 -> dW3[:, r]; row 64 -> db3
+      float v[16];
+      tc::tmem_ld16(tW3 + lane, v);
+      tc::tmem_ld_wait();
 #pragma unroll
-    for (int c = 0; c < kN3; ++c) {
-      if (c >= C) continue;
-      if (row < kHidden && A.g.w[2]) atomicAdd(A.g.w[2] + c * kHidden + row, v[c] * gs);
-      if (row == kHidden && A.g.b[2]) atomicAdd(A.g.b[2] + c, v[c] * gs);
+      for (int c = 0; c < kN3; ++c) {
+        if (c >= C) continue;
+        if (r < kHidden && A.g.w[2]) atomicAdd(A.g.w[2] + c * kHidden + r, v[c] * gs);
+        if (r == kHidden && A.g.b[2]) atomicAdd(A.g.b[2] + c, v[c] * gs);
+      }
     }
   }
   // loss
@@ -770,7 +818,7 @@ __global__ void __launch_bounds__(kRows* kNWG, 1) train_tc_kernel(const ntc_mate
   __syncthreads();
   if (tid == 0) {
     float s = 0.f;
-    for (int w = 0; w < kNWG * 4; ++w) s += red[w];
+    for (int w = 0; w < NWG * 4; ++w) s += red[w];
     if (A.loss) atomicAdd(A.loss, s * A.loss_scale);
     if (abort_any) atomicExch(status, NTC_ERR_TIMEOUT);
   }
@@ -780,37 +828,50 @@ __global__ void __launch_bounds__(kRows* kNWG, 1) train_tc_kernel(const ntc_mate
   }
 }
 
-template <int ACT, bool LEARNED>
-cudaError_t launch_t(const ntc_material& m, const BwdArgs& a, const TPlan& P, cudaStream_t s) {
+template <int ACT, bool LEARNED, int NWG>
+cudaError_t launch_t(const ntc_material& m, const BwdArgs& a, cudaStream_t s) {
+  const TPlan P(m.c0, m.c1, LEARNED, ACT == NTC_ACT_HARDGELU, NWG);
   const size_t smem = P.total;
-  cudaError_t e = cudaFuncSetAttribute(train_tc_kernel<ACT, LEARNED>,
+  cudaError_t e = cudaFuncSetAttribute(train_tc_kernel<ACT, LEARNED, NWG>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int64_t tiles = (a.n + kRows - 1) / kRows;
-  const int64_t ctas = (tiles + kNWG - 1) / kNWG;
+  const int64_t ctas = (tiles + NWG - 1) / NWG;
   const int64_t cap = sm_count();
   const int grid = (int)(ctas < cap ? ctas : cap);
-  train_tc_kernel<ACT, LEARNED><<<grid, kRows * kNWG, smem, s>>>(m, a, status_word());
+  train_tc_kernel<ACT, LEARNED, NWG><<<grid, kRows * NWG, smem, s>>>(m, a, status_word());
   return cudaGetLastError();
+}
+
+// Pipelines per CTA: 3 when their tiles fit, else 2 (0: does not fit).
+int train_pipelines(const ntc_material& m) {
+  const bool learned = m.interp0 == NTC_INTERP_LEARNED, gelu = m.act == NTC_ACT_HARDGELU;
+  for (int n = kMaxNWG; n >= 2; --n)
+    if (TPlan(m.c0, m.c1, learned, gelu, n).fits()) return n;
+  return 0;
+}
+
+template <int ACT, bool LEARNED>
+cudaError_t launch_n(const ntc_material& m, const BwdArgs& a, cudaStream_t s) {
+  return train_pipelines(m) == 3 ? launch_t<ACT, LEARNED, 3>(m, a, s)
+                                 : launch_t<ACT, LEARNED, 2>(m, a, s);
 }
 
 }  // namespace
 
 bool train_tc_supported(const ntc_material& m) {
-  const TPlan P(m.c0, m.c1, m.interp0 == NTC_INTERP_LEARNED);
   return m.precision == NTC_PREC_F16 && (m.act == NTC_ACT_RELU || m.act == NTC_ACT_HARDGELU) &&
-         P.fits();
+         train_pipelines(m) > 0;
 }
 
 cudaError_t launch_train_tc(const ntc_material& m, const BwdArgs& a, cudaStream_t s) {
   if (a.n == 0) return cudaSuccess;
   if (!train_tc_supported(m) || !a.train) return cudaErrorNotSupported;
   const bool learned = m.interp0 == NTC_INTERP_LEARNED;
-  const TPlan P(m.c0, m.c1, learned);
   if (m.act == NTC_ACT_HARDGELU)
-    return learned ? launch_t<NTC_ACT_HARDGELU, true>(m, a, P, s)
-                   : launch_t<NTC_ACT_HARDGELU, false>(m, a, P, s);
-  return learned ? launch_t<NTC_ACT_RELU, true>(m, a, P, s) : launch_t<NTC_ACT_RELU, false>(m, a, P, s);
+    return learned ? launch_n<NTC_ACT_HARDGELU, true>(m, a, s)
+                   : launch_n<NTC_ACT_HARDGELU, false>(m, a, s);
+  return learned ? launch_n<NTC_ACT_RELU, true>(m, a, s) : launch_n<NTC_ACT_RELU, false>(m, a, s);
 }
 
 }  // namespace ntc
