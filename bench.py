@@ -355,13 +355,13 @@ def equal_psnr_eval(ntc, chain, batch, seed, stream, steps=1500):
 # ----------------------------------------------------------------------------
 # The paper's decoder form: learned interpolation of G0, hardGELU, identity
 # ----------------------------------------------------------------------------
-def paper_form_eval(ntc, q_dev, batch, stream):
+def paper_form_eval(ntc, q_dev, batch, stream, hidden_layers=2):
     """Decode of the 2^24 queries with the paper's own decoder input (Sec.
     4.3.1, 4.4: the four G0 taps concatenated, 4 c0 + c1 + 13 inputs,
     hardGELU, no output activation) on a 4096^2 x 16 material with the NTC
     2.25 profile's grids (G0 1024^2 x 16 at 4 bits, G1 512^2 x 12 at 4 bits),
-    random weights, FP16 tensor cores; then the training step of the same
-    decoder form (paper_form_train)."""
+    random weights, FP16 tensor cores, `hidden_layers` hidden layers of 64;
+    then the training step of the same decoder form (paper_form_train)."""
     import torch
     g = torch.Generator(device="cuda")
     g.manual_seed(7007)
@@ -372,10 +372,11 @@ def paper_form_eval(ntc, q_dev, batch, stream):
           for (w0, h0), _ in levels]
     g1 = [torch.randint(0, 256, (h1, w1, cb1), dtype=torch.uint8, device="cuda", generator=g)
           for _, (w1, h1) in levels]
-    w = gen.random_mlp(k, 64, DEC_C, seed=7008, n_used=4 * c0 + c1 + 13)
+    w = gen.random_mlp(k, 64, DEC_C, seed=7008, n_used=4 * c0 + c1 + 13,
+                       hidden_layers=hidden_layers)
     mat = ntc.Material(DEC_SIDE, DEC_SIDE, DEC_C, c0, c1, 4, 4, 1 / 16, 1 / 16, g0, g1,
-                       [torch.from_numpy(w[l]).cuda().half() for l in (0, 2, 4)],
-                       [torch.from_numpy(w[l]).cuda() for l in (1, 3, 5)], k, ntc.PREC_F16,
+                       [torch.from_numpy(x).cuda().half() for x in w[0::2]],
+                       [torch.from_numpy(x).cuda() for x in w[1::2]], k, ntc.PREC_F16,
                        act=ntc.ACT_HARDGELU, out_act=ntc.OUT_IDENTITY, interp0=1)
     out = torch.empty((q_dev.shape[0], DEC_C), dtype=torch.float16, device="cuda")
     ntc.ntc_decode(mat, q_dev, out=out)
@@ -387,20 +388,23 @@ def paper_form_eval(ntc, q_dev, batch, stream):
     b.record(stream)
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / 5
-    flop = 2 * (k * 64 + 64 * 64 + 64 * DEC_C)
+    flop = 2 * (k * 64 + (hidden_layers - 1) * 64 * 64 + 64 * DEC_C)
+    mlp = "-".join(["96"] + ["64"] * hidden_layers + ["16"])
     res = {"workload": "4096^2x16, G0 1024^2x16 (learned interpolation: 4 taps concatenated) + "
-                       "G1 512^2x12 at 4 bits, MLP 96-64-64-16 hardGELU/identity, 2^24 random queries",
+                       f"G1 512^2x12 at 4 bits, MLP {mlp} hardGELU/identity, 2^24 random queries",
            "decode_ms": ms, "texels_per_s": q_dev.shape[0] / (ms / 1e3),
            "tflops": flop * q_dev.shape[0] / (ms / 1e3) / 1e12, "status": ntc.ntc_device_status()}
-    res["train"] = paper_form_train(ntc, batch, stream)
+    res["train"] = paper_form_train(ntc, batch, stream, hidden_layers=hidden_layers)
+    if hidden_layers == 2:
+        res["three_hidden_layers"] = paper_form_eval(ntc, q_dev, batch, stream, hidden_layers=3)
     return res
 
 
-def paper_form_train(ntc, batch, stream, steps=20):
+def paper_form_train(ntc, batch, stream, steps=20, hidden_layers=2):
     """Training step of the paper-form decoder (learned G0 interpolation,
     hardGELU, identity output) on a 2048^2 x 12 material with the NTC 2.25
     profile's grids (G0 512^2 x 16, G1 256^2 x 12, FP32 values in the 4-bit
-    range), MLP 96-64-64-12, FP16 tensor-core step with noise, `batch`
+    range), MLP 96-64-64(-64)-12, FP16 tensor-core step with noise, `batch`
     sampled texels per step."""
     import torch
     side, c, c0, c1, k = TRN_SIDE, TRN_C, 16, 12, 96
@@ -413,10 +417,10 @@ def paper_form_train(ntc, batch, stream, steps=20):
     for (w0, h0), (w1, h1) in ntc.pyramid(side, side):
         g0.append(gen.uniform_grid_values((h0, w0, c0), lo, hi, rng))
         g1.append(gen.uniform_grid_values((h1, w1, c1), lo, hi, rng))
-    w = gen.random_mlp(k, 64, c, seed=1104, n_used=4 * c0 + c1 + 13)
-    tr = ntc.Trainer(side, side, c, c0, c1, 4, 4, q, q, g0, g1, [w[0], w[2], w[4]],
-                     [w[1], w[3], w[5]], k, ntc.PREC_F16, act=ntc.ACT_HARDGELU,
-                     out_act=ntc.OUT_IDENTITY, total_steps=steps + 3, interp0=ntc.INTERP_LEARNED)
+    w = gen.random_mlp(k, 64, c, seed=1104, n_used=4 * c0 + c1 + 13, hidden_layers=hidden_layers)
+    tr = ntc.Trainer(side, side, c, c0, c1, 4, 4, q, q, g0, g1, w[0::2], w[1::2], k,
+                     ntc.PREC_F16, act=ntc.ACT_HARDGELU, out_act=ntc.OUT_IDENTITY,
+                     total_steps=steps + 3, interp0=ntc.INTERP_LEARNED)
     target = ntc.Target(chain)
     for _ in range(3):
         ntc.ntc_train_step(tr, target, batch, 5)
@@ -428,8 +432,9 @@ def paper_form_train(ntc, batch, stream, steps=20):
     b.record(stream)
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / steps
+    mlp = "-".join(["96"] + ["64"] * hidden_layers + ["12"])
     return {"workload": f"2048^2x12, G0 512^2x16 (learned interpolation) + G1 256^2x12, "
-                        f"MLP 96-64-64-12 hardGELU/identity, {batch} texels per step",
+                        f"MLP {mlp} hardGELU/identity, {batch} texels per step",
             "train_ms": ms, "samples_per_s": batch / (ms / 1e3), "loss": float(tr.loss.item()),
             "status": ntc.ntc_device_status()}
 
@@ -739,6 +744,25 @@ def main():
     roof["hbm_frac"] = roof["hbm_gbs_algorithmic"] / hbm
     roof["kernel"] = "decode"
 
+    # ---- roofline of the training step (HBM primary, tensor secondary) -----
+    # per sample: 8 taps x 16 channels x 4 B gathered (512 B), the same
+    # scatter-added (512 B), 12 B of 8-bit target; per step the dense Adam
+    # pass: 32 B per parameter (p, m, v, g read; p, m, v written; g cleared)
+    trn_avg_s = statistics.mean(trn_ms) / 1e3
+    n_params = int(tr.params.numel())
+    tbytes = args.batch * (2 * 8 * TRN_C0 * 4 + TRN_C) + n_params * 32
+    tflop = args.batch * 3 * 2 * (TRN_K * 64 + 64 * 64 + 64 * TRN_C)
+    hbm_peak = peaks.get("hbm_gbs", 6773.2)
+    bf16_peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1900.0))
+    train_roof = {"bound": "hbm", "achieved": tbytes / trn_avg_s / 1e9, "peak": hbm_peak,
+                  "unit": "GB/s", "frac": tbytes / trn_avg_s / 1e9 / hbm_peak,
+                  "algorithmic_bytes_per_step": tbytes,
+                  "tensor_tflops": tflop / trn_avg_s / 1e12,
+                  "tensor_frac": tflop / trn_avg_s / 1e12 / bf16_peak,
+                  "tensor_peak_source": "measured bf16 sustained",
+                  "note": "the grids and their gradient largely stay in L2: HBM sees less "
+                          "than the algorithmic bytes"}
+
     # ---- end to end through the public API with host buffers --------------
     e2e = None
     if not args.no_e2e:
@@ -863,7 +887,7 @@ def main():
                    "parallelism": f"replicas x{world}"},
         "train_samples_per_s": train_rate, "train_loss": loss,
         "decode_ms": statistics.median(dec_ms), "train_ms": statistics.median(trn_ms),
-        "roofline": roof, "tuning": tuning, "e2e": e2e, "fp32_path": fp32, "cpu_baseline": cpu,
+        "roofline": roof, "train_roofline": train_roof, "tuning": tuning, "e2e": e2e, "fp32_path": fp32, "cpu_baseline": cpu,
         "render": render, "multi_material": multi, "paper_form": paper_form, "train_crops": crops,
         "equal_psnr_training": equal,
         "gpu_launches": kernels_per_step * args.steps,

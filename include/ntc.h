@@ -127,6 +127,13 @@ typedef struct {
   const float* scale;    /* NTC_PREC_F8 only: 6 device floats, weight scales s_w[3]
                             then input-activation scales s_a[3]; layer l computes
                             (s_w[l]*s_a[l]) * (W8 . q8(x / s_a[l])) + b.  NULL otherwise */
+  int32_t hidden_layers; /* hidden layers with activations (Sec. 4.4): 2 (0 reads as 2),
+                            or 3 -- a third [hidden][hidden] layer w_h3, b_h3 between
+                            W2 and the output layer W3.  Three hidden layers run on
+                            the FP32 decode, the FP16 warp-specialised decode and the
+                            FP16 training step */
+  const void* w_h3;      /* [hidden][hidden], the precision's type (hidden_layers == 3) */
+  const float* b_h3;     /* [hidden] float32 */
 } ntc_material;
 
 /* Gradient outputs of ntc_backward, ACCUMULATED (+=) in float32, same
@@ -136,6 +143,8 @@ typedef struct {
   float* grid1[NTC_MAX_LEVELS];
   float* w[3];
   float* b[3];
+  float* w_h3;           /* third hidden layer (hidden_layers == 3), nullable */
+  float* b_h3;
 } ntc_grads;
 
 /* Optimiser state of ntc_train_step (Sec. 5.1: Adam, two learning rates,
@@ -165,6 +174,9 @@ typedef struct {
   float lr_mlp;         /* 0.005 in the paper */
   float beta1, beta2, eps;
   float* noisy;         /* optional scratch, params' length (see above) */
+  float* w_master_h3;   /* FP32 master of the third hidden layer (hidden_layers == 3),
+                           inside params like w_master[]; its bias is the material's
+                           b_h3, also inside params */
 } ntc_trainer;
 
 /* Reference texture set: the 8-bit mip chain, texel values q/255. */

@@ -130,14 +130,16 @@ def uniform_grid_values(shape, lo: float, hi: float, rng: np.random.Generator) -
 
 
 def random_mlp(k_in: int, hidden: int, c_out: int, seed: int, n_used: int | None = None,
-               gain: float = 1.0):
-    """Three linear layers ``k_in -> hidden -> hidden -> c_out`` initialised
-    U(+-gain/sqrt(fan_in)), weights stored ``[out][in]`` (float32).  Columns of
-    the first layer at or beyond ``n_used`` (the zero padding of the input
-    row) are set to zero.  Returns ``[w1, b1, w2, b2, w3, b3]``."""
+               gain: float = 1.0, hidden_layers: int = 2):
+    """Linear layers ``k_in -> hidden -> hidden [-> hidden] -> c_out`` (two or
+    three hidden layers) initialised U(+-gain/sqrt(fan_in)), weights stored
+    ``[out][in]`` (float32).  Columns of the first layer at or beyond
+    ``n_used`` (the zero padding of the input row) are set to zero.  Returns
+    ``[w1, b1, w2, b2, (wm, bm,) w3, b3]`` in layer order."""
     rng = np.random.default_rng(seed)
     out = []
-    for fi, fo in ((k_in, hidden), (hidden, hidden), (hidden, c_out)):
+    shapes = [(k_in, hidden)] + [(hidden, hidden)] * (hidden_layers - 1) + [(hidden, c_out)]
+    for fi, fo in shapes:
         fan = n_used if (fi == k_in and n_used) else fi
         bound = gain / math.sqrt(fan)
         w = rng.uniform(-bound, bound, size=(fo, fi)).astype(np.float32)

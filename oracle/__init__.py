@@ -58,6 +58,7 @@ class _Model(C.Structure):
         ("k_in", C.c_int), ("hidden", C.c_int), ("act", C.c_int), ("out_act", C.c_int),
         ("w1", C.c_void_p), ("b1", C.c_void_p), ("w2", C.c_void_p), ("b2", C.c_void_p),
         ("w3", C.c_void_p), ("b3", C.c_void_p), ("interp0", C.c_int),
+        ("hidden_layers", C.c_int), ("wm", C.c_void_p), ("bm", C.c_void_p),
     ]
 
 
@@ -68,7 +69,8 @@ class _Noise(C.Structure):
 class _Grads(C.Structure):
     _fields_ = [("grid0", C.c_void_p * MAX_LEVELS), ("grid1", C.c_void_p * MAX_LEVELS),
                 ("w1", C.c_void_p), ("b1", C.c_void_p), ("w2", C.c_void_p),
-                ("b2", C.c_void_p), ("w3", C.c_void_p), ("b3", C.c_void_p)]
+                ("b2", C.c_void_p), ("w3", C.c_void_p), ("b3", C.c_void_p),
+                ("wm", C.c_void_p), ("bm", C.c_void_p)]
 
 
 def _declare(L):
@@ -235,8 +237,9 @@ class Model:
     """One material: latent grids (float64 values) + decoder weights.
 
     ``grids0[j]`` is ``[g0h, g0w, c0]``, ``grids1[j]`` ``[g1h, g1w, c1]``;
-    ``weights`` is ``[w1, b1, w2, b2, w3, b3]`` with ``w`` stored
-    ``[out][in]``.  ``act`` 0 = ReLU, 1 = hardGELU; ``out_act`` 0 = sigmoid,
+    ``weights`` is ``[w1, b1, w2, b2, w3, b3]`` (two hidden layers) or
+    ``[w1, b1, w2, b2, wm, bm, w3, b3]`` (three: the third hidden layer wm
+    before the output layer w3), layer order, ``w`` stored ``[out][in]``.  ``act`` 0 = ReLU, 1 = hardGELU; ``out_act`` 0 = sigmoid,
     1 = identity.
     """
 
@@ -261,9 +264,15 @@ class Model:
         s.k_in, s.hidden, s.act, s.out_act = k_in, hidden, act, out_act
         self.interp0 = s.interp0 = interp0
         w = self.weights
-        s.w1, s.b1, s.w2, s.b2, s.w3, s.b3 = [a.ctypes.data for a in w]
+        assert len(w) in (6, 8)
+        self.hidden_layers = s.hidden_layers = 2 if len(w) == 6 else 3
+        s.w1, s.b1, s.w2, s.b2 = [a.ctypes.data for a in w[:4]]
+        s.w3, s.b3 = w[-2].ctypes.data, w[-1].ctypes.data
+        if len(w) == 8:
+            s.wm, s.bm = w[4].ctypes.data, w[5].ctypes.data
+            assert w[4].shape == (hidden, hidden)
         assert w[0].shape == (hidden, k_in) and w[2].shape == (hidden, hidden)
-        assert w[4].shape == (channels, hidden)
+        assert w[-2].shape == (channels, hidden)
         self._s = s
 
     # -- helpers -----------------------------------------------------------
@@ -293,6 +302,7 @@ class Model:
         stored weights are this model's weights (already E4M3 values times
         s_w[l]) and every layer input is rounded to E4M3 in units of its
         activation scale; everything else in FP64."""
+        assert self.hidden_layers == 2, "the FP8 form has two hidden layers"
         w = self.weights
         x = self.features_uvl(uvl)
         for l in range(3):
@@ -345,7 +355,11 @@ class Model:
         for j in range(self.levels):
             s.grid0[j] = g["grid0"][j].ctypes.data
             s.grid1[j] = g["grid1"][j].ctypes.data
-        s.w1, s.b1, s.w2, s.b2, s.w3, s.b3 = [a.ctypes.data for a in g["w"]]
+        gw = g["w"]
+        s.w1, s.b1, s.w2, s.b2 = [a.ctypes.data for a in gw[:4]]
+        s.w3, s.b3 = gw[-2].ctypes.data, gw[-1].ctypes.data
+        if len(gw) == 8:
+            s.wm, s.bm = gw[4].ctypes.data, gw[5].ctypes.data
         g["_s"] = s
         return g
 

@@ -324,7 +324,7 @@ double or_activation(int act, double z) { return act_f(act, z); }
 double or_activation_grad(int act, double z) { return act_df(act, z); }
 
 typedef struct {
-  double *x, *z1, *h1, *z2, *h2, *z3, *y;
+  double *x, *z1, *h1, *z2, *h2, *zm, *hm, *z3, *y;
 } mlp_buf;
 
 static void mlp_alloc(const or_model* md, mlp_buf* b) {
@@ -333,11 +333,14 @@ static void mlp_alloc(const or_model* md, mlp_buf* b) {
   b->h1 = calloc((size_t)md->hidden, sizeof(double));
   b->z2 = calloc((size_t)md->hidden, sizeof(double));
   b->h2 = calloc((size_t)md->hidden, sizeof(double));
+  b->zm = calloc((size_t)md->hidden, sizeof(double));
+  b->hm = calloc((size_t)md->hidden, sizeof(double));
   b->z3 = calloc((size_t)md->channels, sizeof(double));
   b->y = calloc((size_t)md->channels, sizeof(double));
 }
 static void mlp_free(mlp_buf* b) {
-  free(b->x); free(b->z1); free(b->h1); free(b->z2); free(b->h2); free(b->z3); free(b->y);
+  free(b->x); free(b->z1); free(b->h1); free(b->z2); free(b->h2); free(b->zm); free(b->hm);
+  free(b->z3); free(b->y);
 }
 
 /* z = W v + b for W stored [out][in]. */
@@ -350,14 +353,24 @@ static void linear(const double* w, const double* bias, const double* v, int in,
   }
 }
 
-/* Three linear layers, hidden activations, output activation (Sec. 4.4). */
+/* The last hidden activation: h2, or hm with a third hidden layer. */
+static const double* last_hidden(const or_model* md, const mlp_buf* b) {
+  return md->hidden_layers == 3 ? b->hm : b->h2;
+}
+
+/* Linear layers with hidden activations, then the output layer and its
+ * activation (Sec. 4.4): two hidden layers, or three. */
 static void mlp_forward(const or_model* md, mlp_buf* b) {
   int H = md->hidden, C = md->channels;
   linear(md->w1, md->b1, b->x, md->k_in, H, b->z1);
   for (int i = 0; i < H; ++i) b->h1[i] = act_f(md->act, b->z1[i]);
   linear(md->w2, md->b2, b->h1, H, H, b->z2);
   for (int i = 0; i < H; ++i) b->h2[i] = act_f(md->act, b->z2[i]);
-  linear(md->w3, md->b3, b->h2, H, C, b->z3);
+  if (md->hidden_layers == 3) {
+    linear(md->wm, md->bm, b->h2, H, H, b->zm);
+    for (int i = 0; i < H; ++i) b->hm[i] = act_f(md->act, b->zm[i]);
+  }
+  linear(md->w3, md->b3, last_hidden(md, b), H, C, b->z3);
   for (int i = 0; i < C; ++i)
     b->y[i] = md->out_act == 1 ? b->z3[i] : 1.0 / (1.0 + exp(-b->z3[i]));
 }
@@ -613,20 +626,42 @@ static void backward_one(const or_model* md, int x, int y, int m, const double* 
   int K = md->k_in, H = md->hidden, C = md->channels;
   or_features(md, x, y, m, nz, b->x);
   mlp_forward(md, b);
-  double dz3[64], dh2[256], dz2[256], dh1[256], dz1[256], dx[256];
+  double dz3[64], dh2[256], dz2[256], dh1[256], dz1[256], dx[256], dhm[256], dzm[256];
+  const double* hl = last_hidden(md, b);
   for (int c = 0; c < C; ++c) {
     double d = md->out_act == 1 ? 1.0 : b->y[c] * (1.0 - b->y[c]);
     dz3[c] = dy[c] * d;
   }
   for (int c = 0; c < C; ++c) {
     g->b3[c] += dz3[c];
-    for (int i = 0; i < H; ++i) g->w3[(int64_t)c * H + i] += dz3[c] * b->h2[i];
+    for (int i = 0; i < H; ++i) g->w3[(int64_t)c * H + i] += dz3[c] * hl[i];
   }
-  for (int i = 0; i < H; ++i) {
-    double s = 0.0;
-    for (int c = 0; c < C; ++c) s += md->w3[(int64_t)c * H + i] * dz3[c];
-    dh2[i] = s;
-    dz2[i] = dh2[i] * act_df(md->act, b->z2[i]);
+  if (md->hidden_layers == 3) {
+    /* through the third hidden layer: dhm = W3^T dz3, dzm = dhm act'(zm),
+     * dWm = dzm h2^T, then dh2 = Wm^T dzm */
+    for (int i = 0; i < H; ++i) {
+      double s = 0.0;
+      for (int c = 0; c < C; ++c) s += md->w3[(int64_t)c * H + i] * dz3[c];
+      dhm[i] = s;
+      dzm[i] = dhm[i] * act_df(md->act, b->zm[i]);
+    }
+    for (int o = 0; o < H; ++o) {
+      g->bm[o] += dzm[o];
+      for (int i = 0; i < H; ++i) g->wm[(int64_t)o * H + i] += dzm[o] * b->h2[i];
+    }
+    for (int i = 0; i < H; ++i) {
+      double s = 0.0;
+      for (int o = 0; o < H; ++o) s += md->wm[(int64_t)o * H + i] * dzm[o];
+      dh2[i] = s;
+      dz2[i] = dh2[i] * act_df(md->act, b->z2[i]);
+    }
+  } else {
+    for (int i = 0; i < H; ++i) {
+      double s = 0.0;
+      for (int c = 0; c < C; ++c) s += md->w3[(int64_t)c * H + i] * dz3[c];
+      dh2[i] = s;
+      dz2[i] = dh2[i] * act_df(md->act, b->z2[i]);
+    }
   }
   for (int o = 0; o < H; ++o) {
     g->b2[o] += dz2[o];
@@ -682,10 +717,12 @@ static void grads_alloc(const or_model* md, or_grads* g) {
   g->w1 = calloc((size_t)H * K, sizeof(double)); g->b1 = calloc((size_t)H, sizeof(double));
   g->w2 = calloc((size_t)H * H, sizeof(double)); g->b2 = calloc((size_t)H, sizeof(double));
   g->w3 = calloc((size_t)C * H, sizeof(double)); g->b3 = calloc((size_t)C, sizeof(double));
+  g->wm = calloc((size_t)H * H, sizeof(double)); g->bm = calloc((size_t)H, sizeof(double));
 }
 static void grads_free(const or_model* md, or_grads* g) {
   for (int j = 0; j < md->levels; ++j) { free(g->grid0[j]); free(g->grid1[j]); }
   free(g->w1); free(g->b1); free(g->w2); free(g->b2); free(g->w3); free(g->b3);
+  free(g->wm); free(g->bm);
 }
 static void add_into(double* dst, const double* src, int64_t n) {
   if (!dst) return;
@@ -700,6 +737,7 @@ static void grads_reduce(const or_model* md, const or_grads* dst, const or_grads
   add_into(dst->w1, src->w1, (int64_t)H * K); add_into(dst->b1, src->b1, H);
   add_into(dst->w2, src->w2, (int64_t)H * H); add_into(dst->b2, src->b2, H);
   add_into(dst->w3, src->w3, (int64_t)C * H); add_into(dst->b3, src->b3, C);
+  add_into(dst->wm, src->wm, (int64_t)H * H); add_into(dst->bm, src->bm, H);
 }
 
 static void backward_job(job* jb, int64_t lo, int64_t hi) {

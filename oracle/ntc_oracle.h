@@ -37,6 +37,10 @@ typedef struct {
   const double *w3, *b3;    /* [channels][hidden], [channels] */
   int interp0;              /* G0 resampling (Sec. 4.3.1): 0 bilinear, 1 learned
                                interpolation (the four taps concatenated) */
+  int hidden_layers;        /* hidden layers with activations: 2, or 3 (Sec. 4.4's
+                               "three remaining layers"): a third hidden layer
+                               wm, bm between w2 and the output layer w3 */
+  const double *wm, *bm;    /* [hidden][hidden], [hidden] (hidden_layers == 3) */
 } or_model;
 
 /* Simulated-quantisation noise switch (Sec. 4.2). */
@@ -51,6 +55,7 @@ typedef struct {
   double* grid0[OR_MAX_LEVELS];
   double* grid1[OR_MAX_LEVELS];
   double *w1, *b1, *w2, *b2, *w3, *b3;
+  double *wm, *bm;          /* third hidden layer (hidden_layers == 3) */
 } or_grads;
 
 /* --- pyramid (Sec. 4.1, Table 1) --- */

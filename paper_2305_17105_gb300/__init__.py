@@ -55,12 +55,14 @@ class ntc_material(C.Structure):
                 ("encoding", C.c_int32), ("k_in", C.c_int32), ("hidden", C.c_int32),
                 ("act", C.c_int32), ("out_act", C.c_int32), ("precision", C.c_int32),
                 ("interp0", C.c_int32), ("lv", ntc_level * MAX_LEVELS), ("w", C.c_void_p * 3), ("b", C.c_void_p * 3),
-                ("scale", C.c_void_p)]
+                ("scale", C.c_void_p), ("hidden_layers", C.c_int32), ("w_h3", C.c_void_p),
+                ("b_h3", C.c_void_p)]
 
 
 class ntc_grads(C.Structure):
     _fields_ = [("grid0", C.c_void_p * MAX_LEVELS), ("grid1", C.c_void_p * MAX_LEVELS),
-                ("w", C.c_void_p * 3), ("b", C.c_void_p * 3)]
+                ("w", C.c_void_p * 3), ("b", C.c_void_p * 3), ("w_h3", C.c_void_p),
+                ("b_h3", C.c_void_p)]
 
 
 class ntc_trainer(C.Structure):
@@ -68,7 +70,7 @@ class ntc_trainer(C.Structure):
                 ("grad", C.c_void_p), ("n_params", C.c_int64), ("w_master", C.c_void_p * 3),
                 ("step", C.c_void_p), ("total_steps", C.c_int64), ("lr_grid", C.c_float),
                 ("lr_mlp", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float),
-                ("eps", C.c_float), ("noisy", C.c_void_p)]
+                ("eps", C.c_float), ("noisy", C.c_void_p), ("w_master_h3", C.c_void_p)]
 
 
 class ntc_batch(C.Structure):
@@ -189,14 +191,22 @@ pyramid = ntc_pyramid
 # ----------------------------------------------------------------------------
 # materials
 # ----------------------------------------------------------------------------
+def _layers(seq):
+    """Layer-order list (3 or 4 entries) -> ([first, second, output], third
+    hidden layer or None): the ABI keeps the output layer at index 2."""
+    seq = list(seq)
+    return ([seq[0], seq[1], seq[-1]], seq[2] if len(seq) == 4 else None)
+
+
 class Material:
     """A compressed material on the device, as the C ABI sees it.
 
     ``grids0[j]`` / ``grids1[j]``: uint8 ``[g_h, g_w, cell_bytes]`` (packed) or
     float32 ``[g_h, g_w, c]`` (F32) CUDA tensors.  ``weights``: ``[w1, w2, w3]``
+    (two hidden layers) or ``[w1, w2, w_h3, w3]`` (three), layer order,
     ``[out][in]`` tensors of the precision's dtype (float32, float16, or
-    uint8 holding E4M3 bytes); ``biases`` float32; ``scale`` (F8 only) float32
-    ``[6]``: weight scales then activation scales.
+    uint8 holding E4M3 bytes); ``biases`` float32, same order; ``scale`` (F8
+    only) float32 ``[6]``: weight scales then activation scales.
     """
 
     def __init__(self, width, height, channels, c0, c1, bits0, bits1, q0, q1, grids0, grids1,
@@ -208,6 +218,7 @@ class Material:
         self.q0, self.q1 = float(q0), float(q1)
         self.grids0, self.grids1 = list(grids0), list(grids1)
         self.weights, self.biases = list(weights), list(biases)
+        assert len(self.weights) in (3, 4) and len(self.biases) == len(self.weights)
         self.k_in, self.precision, self.act, self.out_act = k_in, precision, act, out_act
         self.scale = scale
         self.interp0 = interp0
@@ -229,9 +240,13 @@ class Material:
             s.lv[j].g0_h, s.lv[j].g0_w = g0.shape[0], g0.shape[1]
             s.lv[j].g1_h, s.lv[j].g1_w = g1.shape[0], g1.shape[1]
             s.lv[j].grid0, s.lv[j].grid1 = g0.data_ptr(), g1.data_ptr()
+        w, b, wh, bh = _layers(self.weights), _layers(self.biases), None, None
         for l in range(3):
-            s.w[l] = self.weights[l].data_ptr()
-            s.b[l] = self.biases[l].data_ptr()
+            s.w[l] = w[0][l].data_ptr()
+            s.b[l] = b[0][l].data_ptr()
+        s.hidden_layers = len(self.weights) - 1
+        if w[1] is not None:
+            s.w_h3, s.b_h3 = w[1].data_ptr(), b[1].data_ptr()
         s.scale = self.scale.data_ptr() if self.scale is not None else None
         return s
 
@@ -278,13 +293,23 @@ def ntc_autotune_decode(mat: Material, uvl, out, filter=FILTER_NEAREST, stream=N
 
 
 def grads_struct(mat: Material, grid0=None, grid1=None, w=None, b=None) -> ntc_grads:
+    """Gradient destinations; ``w`` / ``b`` in layer order like the
+    material's weights (3 or 4 entries, None entries skipped)."""
     g = ntc_grads()
     for j in range(mat.levels):
         g.grid0[j] = grid0[j].data_ptr() if grid0 is not None and grid0[j] is not None else None
         g.grid1[j] = grid1[j].data_ptr() if grid1 is not None and grid1[j] is not None else None
-    for l in range(3):
-        g.w[l] = w[l].data_ptr() if w is not None and w[l] is not None else None
-        g.b[l] = b[l].data_ptr() if b is not None and b[l] is not None else None
+    ptr = lambda t: t.data_ptr() if t is not None else None
+    if w is not None:
+        (w3, wh) = _layers(w)
+        for l in range(3):
+            g.w[l] = ptr(w3[l])
+        g.w_h3 = ptr(wh)
+    if b is not None:
+        (b3, bh) = _layers(b)
+        for l in range(3):
+            g.b[l] = ptr(b3[l])
+        g.b_h3 = ptr(bh)
     return g
 
 
@@ -408,8 +433,8 @@ class Trainer:
         views = [self.params[o:o + t.size].view(t.shape) for o, t in zip(offs, tensors)]
         L = len(grids0)
         g0, g1, rest = views[:L], views[L:2 * L], views[2 * L:]
-        self.w_master = [rest[0], rest[2], rest[4]]
-        self.b = [rest[1], rest[3], rest[5]]
+        self.w_master = rest[0::2]   # layer order: 3 or 4 layers
+        self.b = rest[1::2]
         self.grad_views = [self.grad[o:o + t.size].view(t.shape) for o, t in zip(offs, tensors)]
         if precision == PREC_F16:
             self.w_compute = [w.half().contiguous() for w in self.w_master]
@@ -449,8 +474,10 @@ class Trainer:
         t.params, t.adam_m = self.params.data_ptr(), self.adam_m.data_ptr()
         t.adam_v, t.grad = self.adam_v.data_ptr(), self.grad.data_ptr()
         t.n_params = self.params.numel()
+        wm, wh = _layers(self.w_master)
         for l in range(3):
-            t.w_master[l] = self.w_master[l].data_ptr()
+            t.w_master[l] = wm[l].data_ptr()
+        t.w_master_h3 = wh.data_ptr() if wh is not None else None
         t.step = self.step_t.data_ptr()
         t.total_steps = self.total_steps
         t.lr_grid, t.lr_mlp = self.lr_grid, self.lr_mlp

@@ -93,6 +93,14 @@ int check_material(const ntc_material* m, bool need_f32_grids) {
     CHECK_PTR(m->b[l], "bias");
   }
   if (m->precision == NTC_PREC_F8) CHECK_PTR(m->scale, "scale");
+  if (m->hidden_layers != 0 && m->hidden_layers != 2 && m->hidden_layers != 3)
+    return fail(NTC_ERR_ARG, "hidden_layers = %d (2 or 3)", m->hidden_layers);
+  if (m->hidden_layers == 3) {
+    CHECK_PTR(m->w_h3, "w_h3");
+    CHECK_PTR(m->b_h3, "b_h3");
+    if (m->precision == NTC_PREC_F8)
+      return fail(NTC_ERR_UNSUPPORTED, "three hidden layers: FP32 or FP16 weights");
+  }
   return NTC_OK;
 }
 
@@ -228,6 +236,9 @@ int ntc_backward(const ntc_material* m, const float* uvl, int64_t n, const float
                  void* stream) {
   int st = check_material(m, true);
   if (st) return st;
+  if (m->hidden_layers == 3)
+    return fail(NTC_ERR_UNSUPPORTED, "ntc_backward: two hidden layers (three train with "
+                                     "ntc_train_step on FP16 weights)");
   if (n < 0) return fail(NTC_ERR_ARG, "n < 0");
   if (!g) return fail(NTC_ERR_ARG, "grads is NULL");
   if (n == 0) return NTC_OK;
@@ -266,6 +277,8 @@ int ntc_train_step(const ntc_material* m, const ntc_trainer* tr, const ntc_targe
   if (m->precision == NTC_PREC_F8) return fail(NTC_ERR_UNSUPPORTED, "FP8 training");
   if (use_simt(m, flags)) {
     if (m->k_in > 64) return fail(NTC_ERR_UNSUPPORTED, "FP32 training supports k_in <= 64");
+    if (m->hidden_layers == 3)
+      return fail(NTC_ERR_UNSUPPORTED, "FP32 training: two hidden layers (three train on FP16)");
   } else if (!ntc::train_tc_supported(*m)) {
     return fail(NTC_ERR_UNSUPPORTED,
                 "tensor-core training: activation or feature layout not supported "
@@ -324,6 +337,16 @@ int ntc_train_step(const ntc_material* m, const ntc_trainer* tr, const ntc_targe
         !add_seg(m->b[l], blen[l], 1, false, 0, 0, nullptr))
       return fail(NTC_ERR_ARG, "MLP tensor %d is not inside params", l);
   }
+  const bool h3 = m->hidden_layers == 3;
+  if (h3) {
+    CHECK_PTR(tr->w_master_h3, "w_master_h3");
+    if (m->precision == NTC_PREC_F32 && m->w_h3 != tr->w_master_h3)
+      return fail(NTC_ERR_ARG, "F32 weights must be the masters");
+    __half* hc = m->precision == NTC_PREC_F16 ? (__half*)m->w_h3 : nullptr;
+    if (!add_seg(tr->w_master_h3, (int64_t)NTC_HIDDEN * NTC_HIDDEN, 1, false, 0, 0, hc) ||
+        !add_seg(m->b_h3, NTC_HIDDEN, 1, false, 0, 0, nullptr))
+      return fail(NTC_ERR_ARG, "third hidden layer is not inside params");
+  }
   const int64_t per_block = ntc::kAdamBlock * ntc::kAdamPerThread;
   a.block_start[0] = 0;
   for (int i = 0; i < a.nseg; ++i)
@@ -356,6 +379,10 @@ int ntc_train_step(const ntc_material* m, const ntc_trainer* tr, const ntc_targe
   for (int l = 0; l < 3; ++l) {
     b.g.w[l] = G + a.seg[2 * m->levels + 2 * l].off;
     b.g.b[l] = G + a.seg[2 * m->levels + 2 * l + 1].off;
+  }
+  if (h3) {
+    b.g.w_h3 = G + a.seg[2 * m->levels + 6].off;
+    b.g.b_h3 = G + a.seg[2 * m->levels + 7].off;
   }
   b.grad_scale = (float)(1.0 / ((double)batch * (double)m->channels));
   b.loss = loss_out;
@@ -440,6 +467,8 @@ int ntc_batch_prepare(const ntc_material* mats, const int64_t* n_queries, int32_
     }
     if (m->precision != NTC_PREC_F16)
       return fail(NTC_ERR_UNSUPPORTED, "batch material %d: batches decode FP16 materials", i);
+    if (m->hidden_layers == 3)
+      return fail(NTC_ERR_UNSUPPORTED, "batch material %d: batches decode two hidden layers", i);
     if (n_queries[i] < 0) return fail(NTC_ERR_ARG, "batch material %d: negative query count", i);
     const int c = ntc::fast_class(*m);
     cls = cls == -2 ? c : (cls == c ? cls : (cls != 0 && c != 0 ? -1 : 0));

@@ -379,6 +379,13 @@ __device__ __forceinline__ float out_fwd(int out_act, float z) {
   return out_act == NTC_OUT_IDENTITY ? z : 1.f / (1.f + __expf(-z));
 }
 
+// Element idx of the third hidden layer's weights (hidden_layers == 3) as
+// float: FP32 or FP16.
+__device__ __forceinline__ float load_weight_h3(const ntc_material& M, int idx) {
+  if (M.precision == NTC_PREC_F16) return __half2float(static_cast<const __half*>(M.w_h3)[idx]);
+  return static_cast<const float*>(M.w_h3)[idx];
+}
+
 // Weight element l (0..2) at [o][i] as float, from the material's precision.
 __device__ __forceinline__ float load_weight(const ntc_material& M, int l, int idx) {
   switch (M.precision) {

@@ -46,7 +46,7 @@ bool train_tc_supported(const ntc_material& m);
 cudaError_t launch_train_tc(const ntc_material& m, const BwdArgs& a, cudaStream_t s);
 
 // Adam over the segments of the trainer's parameter array.
-constexpr int kMaxSegs = 2 * NTC_MAX_LEVELS + 6;
+constexpr int kMaxSegs = 2 * NTC_MAX_LEVELS + 8;
 struct AdamSeg {
   int64_t off, len;   // float offset into params and element count
   float lo, hi;       // clamp range (grids)

@@ -15,17 +15,22 @@ constexpr int kThreads = kTile;  // 128
 
 // Shared-memory weights in float: W1^T [K][64] (input-major, for the
 // forward), W2 [64][64] and W3 [16][64] ([out][in]; W3 rows >= C are zero),
-// b1, b2, b3 (16).  Offsets in floats, all multiples of 4.
+// b1, b2, b3 (16), and with a third hidden layer Wh [64][64], bh.  Offsets in
+// floats, all multiples of 4.
 struct SW {
-  int w1t, w2, w3, b1, b2, b3, size;
-  __host__ __device__ explicit SW(int K) {
+  int w1t, w2, w3, b1, b2, b3, wh, bh, size;
+  bool h3;
+  __host__ __device__ SW(int K, bool third) {
     w1t = 0;
     w2 = w1t + K * kHidden;
     w3 = w2 + kHidden * kHidden;
     b1 = w3 + kMaxC * kHidden;
     b2 = b1 + kHidden;
     b3 = b2 + kHidden;
-    size = b3 + kMaxC;
+    wh = b3 + kMaxC;
+    bh = wh + (third ? kHidden * kHidden : 0);
+    size = bh + (third ? kHidden : 0);
+    h3 = third;
   }
 };
 
@@ -43,6 +48,10 @@ __device__ void stage_weights(const ntc_material& M, const SW& L, float* s) {
     s[L.b2 + i] = M.b[1][i];
   }
   for (int i = threadIdx.x; i < kMaxC; i += blockDim.x) s[L.b3 + i] = i < C ? M.b[2][i] : 0.f;
+  if (L.h3) {
+    for (int i = threadIdx.x; i < kHidden * kHidden; i += blockDim.x) s[L.wh + i] = load_weight_h3(M, i);
+    for (int i = threadIdx.x; i < kHidden; i += blockDim.x) s[L.bh + i] = M.b_h3[i];
+  }
 }
 
 // Layer 1: z = W1 x + b1 with x a K-float row in shared memory (16-byte
@@ -129,6 +138,12 @@ __device__ __forceinline__ void mlp_forward(const float* sw, const SW& L, const 
   dense64<kHidden>(sw + L.w2, sw + L.b2, h1, h2);
 #pragma unroll
   for (int i = 0; i < kHidden; ++i) h2[i] = act_fwd(act, h2[i]);
+  if (L.h3) {
+    // third hidden layer (Sec. 4.4: activations on three layers)
+    dense64<kHidden>(sw + L.wh, sw + L.bh, h2, h1);
+#pragma unroll
+    for (int i = 0; i < kHidden; ++i) h2[i] = act_fwd(act, h1[i]);
+  }
   dense64<kMaxC>(sw + L.w3, sw + L.b3, h2, y);
 #pragma unroll
   for (int c = 0; c < kMaxC; ++c) y[c] = out_fwd(out_act, y[c]);
@@ -148,7 +163,7 @@ __global__ void __launch_bounds__(kThreads) decode_simt_kernel(
     int out_dtype, int filter, int noise, uint64_t nkey, uint64_t jkey) {
   extern __shared__ __align__(16) float smem[];
   const int K = M.k_in, C = M.channels;
-  const SW L(K);
+  const SW L(K, M.hidden_layers == 3);
   float* sw = smem;
   stage_weights(M, L, sw);
   __syncthreads();
@@ -225,7 +240,7 @@ __global__ void __launch_bounds__(kThreads) decode_simt_kernel(
 struct SB {
   SW w;
   int g, x, z1, z2, d3, dx, red, size;
-  __host__ __device__ explicit SB(int K) : w(K) {
+  __host__ __device__ explicit SB(int K) : w(K, false) {
     g = w.size;                                  // gradient accumulators, layout of w
     x = g + w.size;                              // [128][K+4]
     z1 = x + kTile * row_stride(K);              // [128][65]
@@ -486,7 +501,7 @@ cudaError_t launch_decode_simt(const ntc_material& m, const float* uvl, int64_t 
   if (n == 0) return cudaSuccess;
   const uint64_t nkey = rng_key(noise_seed, noise_stream(noise_step));
   const uint64_t jkey = jitter_key(noise_seed, noise_step);
-  const SW L(m.k_in);
+  const SW L(m.k_in, m.hidden_layers == 3);
   const size_t smem = (size_t)(L.size + kThreads * row_stride(m.k_in)) * sizeof(float);
   cudaError_t e = cudaFuncSetAttribute(decode_simt_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

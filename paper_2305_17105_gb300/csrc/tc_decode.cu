@@ -275,8 +275,9 @@ cudaError_t launch_decode_tc(const ntc_material& m, const float* uvl, int64_t n,
   }
   if (m.precision != NTC_PREC_F16) return cudaErrorInvalidValue;
   const Plan P(m, false, fast_layout_ok(m));
-  // the warpgroup-pipeline kernel keeps X in 24 TMEM columns (K <= 48)
-  if (nwg == 5 || P.k_int > 48)
+  // the warpgroup-pipeline kernel keeps X in 24 TMEM columns (K <= 48) and
+  // runs two hidden layers
+  if (nwg == 5 || P.k_int > 48 || m.hidden_layers == 3)
     return launch_decode_ws(m, uvl, n, out, out_dtype, filter, jkey, s, P.fast != 0);
   if (P.fast) return launch_shape<false, true>(m, uvl, n, out, out_dtype, filter, jkey, s, nwg);
   return launch_shape<false, false>(m, uvl, n, out, out_dtype, filter, jkey, s, nwg);

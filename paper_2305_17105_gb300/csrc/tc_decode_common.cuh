@@ -28,8 +28,9 @@ constexpr int kColX = 96;              // FP16: up to 24 columns (48 halves); FP
 constexpr int kColCst = 120;           // FP16: 8 columns
 constexpr uint32_t kWaitLimit = 1u << 18;  // suspended tries: ms to seconds
 // Shared-memory B descriptor table: W1 K-steps [0, 8) (K <= 128), W2 [8, 12),
-// its bias block 12, W3 [13, 17), its bias block 17.
-constexpr int kDescW2 = 8, kDescW3 = 13, kDescs = 18;
+// its bias block 12, W3 [13, 17), its bias block 17, and with a third hidden
+// layer (FP16) Wh [18, 22), its bias block 22.
+constexpr int kDescW2 = 8, kDescW3 = 13, kDescWh = 18, kDescs = 23;
 
 template <bool F8>
 struct Cfg {
@@ -55,8 +56,8 @@ struct MipTab {
 
 // Input-row layout and shared memory plan (byte offsets).
 struct Plan {
-  int fast, learned, eo0, eo1, t0, t1, f0, f1, gpe, k_int, cb0, cb1;
-  uint32_t w1, w2, w3, wb2, wb3, bias, tab, pe, desc, total;
+  int fast, learned, eo0, eo1, t0, t1, f0, f1, gpe, k_int, cb0, cb1, h3;
+  uint32_t w1, w2, w3, wb2, wb3, wh, wbh, bias, tab, pe, desc, total;
   // `taps_ok`: every grid/mip size ratio puts the taps on the 1/16 lattice and
   // the bin widths are powers of two (fast_layout_ok).
   __host__ __device__ Plan(const ntc_material& M, bool f8, bool taps_ok) {
@@ -97,6 +98,9 @@ struct Plan {
     w3 = o;   o += kN3 * kHidden * eb;            // B: W3 (rows >= C zero)
     wb2 = o;  o += f8 ? 0 : kHidden * 16 * 2;     // B: bias block of layer 2 (FP16)
     wb3 = o;  o += f8 ? 0 : kN3 * 16 * 2;         // B: bias block of layer 3 (FP16)
+    h3 = !f8 && M.hidden_layers == 3;             // third hidden layer (FP16 forms)
+    wh = o;   o += h3 ? kHidden * kHidden * 2 : 0;  // B: Wh
+    wbh = o;  o += h3 ? kHidden * 16 * 2 : 0;       // B: its bias block
     bias = o; o += (2 * kHidden + kN3) * 4;       // FP32 biases (FP8 epilogues)
     o = (o + 15) / 16 * 16;
     tab = o;  o += sizeof(MipTab);
@@ -235,6 +239,20 @@ __device__ void stage_shared(const ntc_material& M, const Plan& P, uint8_t* sm, 
     else *reinterpret_cast<__half*>(sm + off) = __float2half_rn(
         live ? h3 * __half2float(static_cast<const __half*>(M.w[2])[i]) : 0.f);
   }
+  if (!F8 && P.h3) {
+    for (int i = tid; i < kHidden * kHidden; i += nt) {
+      const int n = i / kHidden, k = i - n * kHidden;
+      *reinterpret_cast<__half*>(sm + P.wh + tc::canon_offset(n, k, kHidden, 2)) =
+          static_cast<const __half*>(M.w_h3)[i];
+    }
+    for (int i = tid; i < kHidden * 16; i += nt) {
+      const int n = i / 16, k = i - n * 16;
+      __half hd, tl;
+      split_bias(M.b_h3[n], hd, tl);
+      *reinterpret_cast<__half*>(sm + P.wbh + tc::canon_offset(n, k, kHidden, 2)) =
+          k == 0 ? hd : (k == 1 ? tl : __float2half_rn(0.f));
+    }
+  }
   float* bias = reinterpret_cast<float*>(sm + P.bias);
   for (int i = tid; i < kHidden; i += nt) {
     bias[i] = M.b[0][i];
@@ -302,6 +320,10 @@ __device__ void stage_shared(const ntc_material& M, const Plan& P, uint8_t* sm, 
     }
     d[kDescW2 + 4] = tc::smem_desc(sb + P.wb2, lbo, 128);
     d[kDescW3 + 4] = tc::smem_desc(sb + P.wb3, lbo3, 128);
+    if (P.h3) {
+      for (int k = 0; k < kHidden / KS; ++k) d[kDescWh + k] = tc::smem_desc(sb + P.wh + 2 * k * lbo, lbo, 128);
+      d[kDescWh + 4] = tc::smem_desc(sb + P.wbh, lbo, 128);
+    }
   }
 }
 

@@ -336,6 +336,9 @@ cudaError_t launch_decode_ws_batched(const BatchHeader* dev, int64_t total_tiles
 
 cudaError_t launch_decode_ws(const ntc_material& m, const float* uvl, int64_t n, void* out,
                              int out_dtype, int filter, uint64_t jkey, cudaStream_t s, bool fast) {
+  if (m.hidden_layers == 3)  // a third hidden layer: runtime-class fast layout or generic
+    return fast ? launch_ws<-1, false, true>(m, uvl, n, out, out_dtype, filter, jkey, s)
+                : launch_ws<0, false, true>(m, uvl, n, out, out_dtype, filter, jkey, s);
   if (!fast) return launch_ws<0, false>(m, uvl, n, out, out_dtype, filter, jkey, s);
   const Plan P(m, false, true);
   if (P.learned) return launch_ws<-1, false>(m, uvl, n, out, out_dtype, filter, jkey, s);

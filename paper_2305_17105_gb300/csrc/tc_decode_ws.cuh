@@ -81,7 +81,8 @@ __device__ __forceinline__ void hidden_epilogue_q8(uint32_t td, uint32_t ta, int
   }
 }
 
-template <int CLS, bool F8>
+// H3: a third hidden layer (FP16; the runtime-class and generic layouts).
+template <int CLS, bool F8, bool H3>
 __global__ void __launch_bounds__(kWsThreads, 1) decode_ws_kernel(
     const ntc_material M, const float* __restrict__ uvl, int64_t n, void* __restrict__ out,
     int out_dtype, int filter, uint64_t jkey, int* status) {
@@ -173,6 +174,16 @@ __global__ void __launch_bounds__(kWsThreads, 1) decode_ws_kernel(
         }
         if (!F8) tc::mma_f16(tw, cst, d[kDescW2 + 4], id64, 1);
         tc::mma_commit(&bar_d[w]);
+        if (H3) {
+          // third hidden layer: H -> D, like layer 2
+          if (!(ok = tc::mbar_wait(&bar_h[w], ph, kWaitLimit))) break;
+          ph ^= 1;
+          tc::fence_after_sync();
+          for (int s = 0; s < kHidden / 16; ++s)
+            tc::mma_f16_ta(tw, tw + kColH + 8 * s, d[kDescWh + s], id64, s > 0);
+          tc::mma_f16(tw, cst, d[kDescWh + 4], id64, 1);
+          tc::mma_commit(&bar_d[w]);
+        }
         if (!(ok = tc::mbar_wait(&bar_h[w], ph, kWaitLimit))) break;
         ph ^= 1;
         tc::fence_after_sync();
@@ -276,6 +287,17 @@ __global__ void __launch_bounds__(kWsThreads, 1) decode_ws_kernel(
       tc::fence_before_sync();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&bar_h[w]);
+      if (H3) {
+        // third hidden layer -> H
+        if (!tc::mbar_wait(&bar_d[w], pd, kWaitLimit)) *abort_flag = 1;
+        pd ^= 1;
+        tc::fence_after_sync();
+        hidden_epilogue_q(td, th, M.act);
+        tc::tmem_st_wait();
+        tc::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&bar_h[w]);
+      }
       if (*abort_flag) break;
       // the tile after next: texel and cells; its successor's query
       locate(M, tb, nq, filter, row, nxt, qindex(tl + 2 * stride), jkey);
@@ -332,12 +354,14 @@ __global__ void __launch_bounds__(kWsThreads, 1) decode_ws_kernel(
   }
 }
 
-template <int CLS, bool F8>
+template <int CLS, bool F8, bool H3 = false>
 cudaError_t launch_ws(const ntc_material& m, const float* uvl, int64_t n, void* out, int out_dtype,
                       int filter, uint64_t jkey, cudaStream_t s) {
+  static_assert(!(F8 && H3), "three hidden layers run in FP16");
   const Plan P(m, F8, CLS != 0);
+  if (P.h3 != H3) return cudaErrorInvalidValue;
   const WsPlan W(P, F8);
-  cudaError_t e = cudaFuncSetAttribute(decode_ws_kernel<CLS, F8>,
+  cudaError_t e = cudaFuncSetAttribute(decode_ws_kernel<CLS, F8, H3>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)W.total);
   if (e != cudaSuccess) return e;
   const int per_tile = filter == NTC_FILTER_TRILINEAR ? kRows / 8 : kRows;
@@ -345,8 +369,8 @@ cudaError_t launch_ws(const ntc_material& m, const float* uvl, int64_t n, void* 
   const int64_t ctas = (tiles + kWsCompute - 1) / kWsCompute;
   const int64_t cap = sm_count();
   const int grid = (int)(ctas < cap ? ctas : cap);
-  decode_ws_kernel<CLS, F8><<<grid, kWsThreads, W.total, s>>>(m, uvl, n, out, out_dtype, filter,
-                                                              jkey, status_word());
+  decode_ws_kernel<CLS, F8, H3><<<grid, kWsThreads, W.total, s>>>(m, uvl, n, out, out_dtype,
+                                                                  filter, jkey, status_word());
   return cudaGetLastError();
 }
 

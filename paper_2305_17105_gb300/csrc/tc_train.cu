@@ -1,12 +1,15 @@
 // Tensor-core (tcgen05) fused forward + L2 loss + backward of the NTC
 // optimisation step (Sec. 4.2, 4.5, 5.1), FP16 operands, FP32 accumulation.
 //
-// One persistent CTA per SM runs NWG warpgroup pipelines (3 when their tiles
-// fit in shared memory, else 2); a warpgroup owns a stream of tiles of 128
+// One persistent CTA per SM runs NWG warpgroup pipelines (3, 2 or 1: the most
+// whose tiles fit in shared memory); a warpgroup owns a stream of tiles of 128
 // training texels (one per thread = one row = one TMEM lane).  Per tile, with
 // every activation kept on chip:
 //   forward   X -> Z1 = X W1^T (+b1) -> H1 = act(Z1) -> Z2 (+b2) -> H2 -> Z3 (+b3)
-//             -> y = out(Z3), loss, dZ3 = 2 (y - t) out'(Z3)
+//             -> y = out(Z3), loss, dZ3 = 2 (y - t) out'(Z3); with a third
+//             hidden layer H2 -> Zh (+bh) -> H3 feeds the output layer, and
+//             the backward passes through it the same way (dWh += dZh^T
+//             [H2 | 1], dZ2 over H2 from dH2 = dZh Wh)
 //   backward  dH2 = dZ3 W3 and [dW3^T; db3] += [H2^T; 1] dZ3;
 //             dZ2 = dH2 * act'(Z2) (over H2); dH1 = dZ2 W2 and
 //             [dW2 db2] += dZ2^T [H1 | 1]; dZ1 = dH1 * act'(Z1) (over H1);
@@ -54,17 +57,19 @@ constexpr uint32_t kSmemMax = 232448u - 2048u;  // dynamic shared memory (static
 // four taps' 4 c0 values with learned interpolation), G1 groups,
 // [PE0..7][PE8..11, LOD, 0, 1, 1], zero groups up to k_int.
 struct TPlan {
-  int w0, f0, f1, gpe, k_int, dx_n, nwg;
-  uint32_t w1, w2, w3, wb2, wb3, tab, wg0, wg_bytes, total;
-  uint32_t dmax, colW1, colW2, colW3, cols;  // TMEM: D of pipeline p at p dmax, then the
-                                             // shared weight-gradient accumulators
+  int w0, f0, f1, gpe, k_int, dx_n, nwg, h3;
+  uint32_t w1, w2, w3, wb2, wb3, wh, wbh, tab, wg0, wg_bytes, total;
+  uint32_t dmax, colW1, colW2, colWh, colW3, cols;  // TMEM: D of pipeline p at p dmax, then
+                                                    // the shared weight-gradient accumulators
   // offsets inside one pipeline's region, in this order (the MN-major reads
-  // of 16 groups from H1 or H2 stay inside it): H1 (= dZ1), ONEa (2 groups:
-  // the K = 16 bias steps and the ones column of dW2), H2 (= dZ2), ONEb (1
-  // group: the db3 row of dW3), DZ3, X, and for hardGELU G1, G2 (act'(Z1),
-  // act'(Z2))
-  uint32_t H1, ONEa, H2, ONEb, DZ3, X, G1, G2;
-  __host__ __device__ TPlan(int c0, int c1, bool learned, bool gelu, int n_wg) {
+  // of 16 groups from H1, H2 or H3 stay inside it): H1 (= dZ1), ONEa (2
+  // groups: the K = 16 bias steps and the ones column of dW2), H2 (= dZ2),
+  // with a third hidden layer ONEc (2 groups: the ones column of dWh) and H3
+  // (= dZh), then ONEb (1 group: the db3 row of dW3), DZ3, X, and for
+  // hardGELU G1, G2 (, G3): act'(Z) of each hidden layer.  HL is the last
+  // hidden tile (H2 or H3).
+  uint32_t H1, ONEa, H2, ONEc, H3, HL, ONEb, DZ3, X, G1, G2, G3;
+  __host__ __device__ TPlan(int c0, int c1, bool learned, bool gelu, int n_wg, bool third) {
     w0 = learned ? 4 * c0 : c0;
     f0 = (w0 + 7) / 8;
     f1 = (c1 + 7) / 8;
@@ -72,12 +77,15 @@ struct TPlan {
     k_int = (8 * (gpe + 2) + 15) / 16 * 16;
     dx_n = (8 * gpe + 15) / 16 * 16;     // dX columns: the grid slots
     nwg = n_wg;
+    h3 = third;
     uint32_t o = 0;
     w1 = o;  o += kHidden * k_int * 2;   // W1 [64][k_int]: B of layer 1, MN-major B of dX
     w2 = o;  o += kHidden * kHidden * 2; // W2: B of layer 2, MN-major B of dH1
     w3 = o;  o += kN3 * kHidden * 2;     // W3 [16][64]: B of layer 3, MN-major B of dH2
     wb2 = o; o += kHidden * 16 * 2;      // bias blocks (head, tail)
     wb3 = o; o += kN3 * 16 * 2;
+    wh = o;  o += h3 ? kHidden * kHidden * 2 : 0;  // Wh: B of the third layer, MN-major B of dH2
+    wbh = o; o += h3 ? kHidden * 16 * 2 : 0;
     o = (o + 15) / 16 * 16;
     tab = o; o += 16 * 16 * 4;           // per-mip table (MipTabT)
     o = (o + 1023) / 1024 * 1024;
@@ -85,18 +93,23 @@ struct TPlan {
     H1 = 0;
     ONEa = H1 + 8 * kGroup;
     H2 = ONEa + 2 * kGroup;
-    ONEb = H2 + 8 * kGroup;
+    ONEc = H2 + 8 * kGroup;
+    H3 = ONEc + (h3 ? 2 * kGroup : 0);
+    HL = h3 ? H3 : H2;
+    ONEb = HL + 8 * kGroup;
     DZ3 = ONEb + 1 * kGroup;
     X = DZ3 + 2 * kGroup;
     G1 = X + (k_int / 8) * kGroup;
     G2 = G1 + (gelu ? 8 * kGroup : 0);
-    wg_bytes = G2 + (gelu ? 8 * kGroup : 0);
-    if (wg_bytes < H2 + 16 * kGroup) wg_bytes = H2 + 16 * kGroup;
+    G3 = G2 + (gelu ? 8 * kGroup : 0);
+    wg_bytes = G3 + (gelu && h3 ? 8 * kGroup : 0);
+    if (wg_bytes < HL + 16 * kGroup) wg_bytes = HL + 16 * kGroup;
     total = wg0 + nwg * wg_bytes;
     dmax = dx_n > kHidden ? dx_n : kHidden;
     colW1 = nwg * dmax;
     colW2 = colW1 + k_int;
-    colW3 = colW2 + kHidden + 16;
+    colWh = colW2 + kHidden + 16;
+    colW3 = colWh + (h3 ? kHidden + 16 : 0);
     cols = colW3 + kN3;
   }
   // fits one CTA: shared memory, TMEM, the dX staging rows
@@ -179,6 +192,20 @@ __device__ void stage_train(const ntc_material& M, const TPlan& P, uint8_t* sm) 
     *reinterpret_cast<__half*>(sm + P.wb3 + tc::canon_offset(n, k, kN3, 2)) =
         k == 0 ? hd : (k == 1 ? tl : z);
   }
+  if (P.h3) {
+    for (int i = tid; i < kHidden * kHidden; i += nt) {
+      const int o = i / kHidden, k = i - o * kHidden;
+      *reinterpret_cast<__half*>(sm + P.wh + tc::canon_offset(o, k, kHidden, 2)) =
+          static_cast<const __half*>(M.w_h3)[i];
+    }
+    for (int i = tid; i < kHidden * 16; i += nt) {
+      const int n = i / 16, k = i - n * 16;
+      __half hd, tl;
+      split_bias(M.b_h3[n], hd, tl);
+      *reinterpret_cast<__half*>(sm + P.wbh + tc::canon_offset(n, k, kHidden, 2)) =
+          k == 0 ? hd : (k == 1 ? tl : z);
+    }
+  }
   MipTabT* tb = reinterpret_cast<MipTabT*>(sm + P.tab);
   for (int m = tid; m < M.mips; m += nt) {
     tb->wm[m] = mip_dim(M.width, m);
@@ -187,13 +214,15 @@ __device__ void stage_train(const ntc_material& M, const TPlan& P, uint8_t* sm) 
     tb->lodn[m] = M.mips > 1 ? (float)m / (float)(M.mips - 1) : 0.f;
   }
   // the constant-one tiles of every pipeline: columns 0 and 1 are one
-  // (ONEa: groups 0 and 1, ONEb: group 0)
-  for (int i = tid; i < P.nwg * 3 * kRows; i += nt) {
-    const int w = i / (3 * kRows), t = (i / kRows) % 3, r = i % kRows;
-    uint8_t* base = sm + P.wg0 + w * P.wg_bytes + (t == 2 ? P.ONEb : P.ONEa);
+  // (ONEa, ONEc: groups 0 and 1; ONEb: group 0)
+  for (int i = tid; i < P.nwg * 5 * kRows; i += nt) {
+    const int w = i / (5 * kRows), t = (i / kRows) % 5, r = i % kRows;
+    if (t >= 3 && !P.h3) continue;
+    const uint32_t tile = t == 2 ? P.ONEb : (t < 2 ? P.ONEa : P.ONEc);
+    const int g = (t == 1 || t == 4) ? 1 : 0;
     const uint4 one = make_uint4(tc::pack_f16x2(1.f, 1.f), 0u, 0u, 0u);
-    *reinterpret_cast<uint4*>(base + tc::canon_chunk(r, t == 1 ? 1 : 0, kRows)) =
-        t == 1 ? make_uint4(0, 0, 0, 0) : one;
+    *reinterpret_cast<uint4*>(sm + P.wg0 + w * P.wg_bytes + tile + tc::canon_chunk(r, g, kRows)) =
+        g ? make_uint4(0, 0, 0, 0) : one;
   }
 }
 
@@ -446,7 +475,7 @@ __global__ void __launch_bounds__(kRows* NWG, 1) train_tc_kernel(const ntc_mater
   __shared__ uint32_t tmem_base;
   __shared__ int abort_any;
   __shared__ float red[NWG * 4];
-  const TPlan P(M.c0, M.c1, LEARNED, ACT == NTC_ACT_HARDGELU, NWG);
+  const TPlan P(M.c0, M.c1, LEARNED, ACT == NTC_ACT_HARDGELU, NWG, M.hidden_layers == 3);
   uint8_t* sm = smem_raw;
   const int tid = threadIdx.x, warp = tid >> 5;
   const int wg = tid / kRows, row = tid % kRows;
@@ -493,6 +522,7 @@ __global__ void __launch_bounds__(kRows* NWG, 1) train_tc_kernel(const ntc_mater
   constexpr uint32_t id_w2 = tc::idesc(kRows, kHidden + 16) | ida | idb;
   constexpr uint32_t id_w3 = tc::idesc(kRows, kN3) | ida | idb;
   const uint32_t tW1 = tmem_base + P.colW1, tW2 = tmem_base + P.colW2, tW3 = tmem_base + P.colW3;
+  const uint32_t tWh = tmem_base + P.colWh;
 
   const int64_t step = A.step_dev ? *A.step_dev : A.noise_step;
   const uint64_t nkey = rng_key(A.noise_seed, noise_stream(step));
@@ -596,10 +626,26 @@ __global__ void __launch_bounds__(kRows* NWG, 1) train_tc_kernel(const ntc_mater
     tc::fence_proxy_async();
     tc::bar_sync(bar_id, kRows);
 
+    // ---- third hidden layer (Sec. 4.4) -------------------------------------------
+    if (P.h3) {
+      if (row == 0) {
+        tc::fence_after_sync();
+        issue_kmajor(tD, sW + P.H2, lbo_a, sbase + P.wh, lbo64, 4, id64, 0);
+        issue_kmajor(tD, sW + P.ONEa, lbo_a, sbase + P.wbh, lbo64, 1, id64, 1);
+        tc::mma_commit(bar);
+      }
+      if (!wait_phase(bar, phase, bar_id)) { aborted = true; break; }
+      tc::fence_after_sync();
+      hidden_forward<ACT>(tD + lane, W + P.H3, W + P.G3, row);
+      tc::fence_before_sync();
+      tc::fence_proxy_async();
+      tc::bar_sync(bar_id, kRows);
+    }
+
     // ---- layer 3, loss, dZ3 ----------------------------------------------------
     if (row == 0) {
       tc::fence_after_sync();
-      issue_kmajor(tD, sW + P.H2, lbo_a, sbase + P.w3, lbo16, 4, id16, 0);
+      issue_kmajor(tD, sW + P.HL, lbo_a, sbase + P.w3, lbo16, 4, id16, 0);
       issue_kmajor(tD, sW + P.ONEa, lbo_a, sbase + P.wb3, lbo16, 1, id16, 1);
       tc::mma_commit(bar);
     }
@@ -631,19 +677,35 @@ __global__ void __launch_bounds__(kRows* NWG, 1) train_tc_kernel(const ntc_mater
     tc::fence_proxy_async();
     tc::bar_sync(bar_id, kRows);
 
-    // ---- dH2 = dZ3 W3; [dW3^T; db3] += [H2^T; 1] dZ3; then dZ2 over H2 ---------
+    // ---- dHL = dZ3 W3; [dW3^T; db3] += [HL^T; 1] dZ3; then dZL over HL -------
     if (row == 0) {
       tc::fence_after_sync();
       issue_kmn(tD, sW + P.DZ3, lbo_a, sbase + P.w3, (kN3 / 8) * 128, 1, id64 | idb);
-      issue_mnmajor(tW3, sW + P.H2, sW + P.DZ3, id_w3, 1);
+      issue_mnmajor(tW3, sW + P.HL, sW + P.DZ3, id_w3, 1);
       tc::mma_commit(bar);
     }
     if (!wait_phase(bar, phase, bar_id)) { aborted = true; break; }
     tc::fence_after_sync();
-    hidden_backward<ACT>(tD + lane, W + P.G2, W + P.H2, row);
+    hidden_backward<ACT>(tD + lane, W + (P.h3 ? P.G3 : P.G2), W + P.HL, row);
     tc::fence_before_sync();
     tc::fence_proxy_async();
     tc::bar_sync(bar_id, kRows);
+
+    // ---- third layer: dH2 = dZh Wh; [dWh dbh] += dZh^T [H2 | 1]; dZ2 over H2 --
+    if (P.h3) {
+      if (row == 0) {
+        tc::fence_after_sync();
+        issue_kmn(tD, sW + P.H3, lbo_a, sbase + P.wh, lbo64, 4, id64 | idb);
+        issue_mnmajor(tWh, sW + P.H3, sW + P.H2, id_w2, 1);
+        tc::mma_commit(bar);
+      }
+      if (!wait_phase(bar, phase, bar_id)) { aborted = true; break; }
+      tc::fence_after_sync();
+      hidden_backward<ACT>(tD + lane, W + P.G2, W + P.H2, row);
+      tc::fence_before_sync();
+      tc::fence_proxy_async();
+      tc::bar_sync(bar_id, kRows);
+    }
 
     // ---- dH1 = dZ2 W2; [dW2 db2] += dZ2^T [H1 | 1]; then dZ1 over H1 ----------
     if (row == 0) {
@@ -699,6 +761,10 @@ __global__ void __launch_bounds__(kRows* NWG, 1) train_tc_kernel(const ntc_mater
       *reinterpret_cast<uint4*>(W + P.ONEa + tc::canon_chunk(row, 0, kRows)) = one;
       *reinterpret_cast<uint4*>(W + P.ONEa + tc::canon_chunk(row, 1, kRows)) = make_uint4(0, 0, 0, 0);
       *reinterpret_cast<uint4*>(W + P.ONEb + tc::canon_chunk(row, 0, kRows)) = one;
+      if (P.h3) {
+        *reinterpret_cast<uint4*>(W + P.ONEc + tc::canon_chunk(row, 0, kRows)) = one;
+        *reinterpret_cast<uint4*>(W + P.ONEc + tc::canon_chunk(row, 1, kRows)) = make_uint4(0, 0, 0, 0);
+      }
     } else if (A.grids) {
       // dX slots: G0 at columns 0.., G1 at 8 * f0.. (f0 is 1 or 2)
       float d[32], dg0[16], dg1[16];
@@ -768,45 +834,51 @@ __global__ void __launch_bounds__(kRows* NWG, 1) train_tc_kernel(const ntc_mater
   const int wq = warp & 3;  // lane quarter of this warp: rows 32 wq .. 32 wq + 31
   const int r = 32 * wq + (tid & 31);
   if (!abort_any && (int64_t)blockIdx.x * NWG < ntiles) {
-    if (wg == 0 && wq < 2) {
-      // [dW1 db1]: row r, X columns (the head constant-one slot gives db1 r)
+    // flush jobs 0 dW1, 1 dW2, 2 dW3, 3 dWh, one warpgroup each (round robin)
+    for (int job = wg; job < (P.h3 ? 4 : 3); job += NWG) {
+      if (job == 0 && wq < 2) {
+        // [dW1 db1]: row r, X columns (the head constant-one slot gives db1 r)
 #pragma unroll 1
-      for (int cb = 0; cb < P.k_int; cb += 16) {
+        for (int cb = 0; cb < P.k_int; cb += 16) {
+          float v[16];
+          tc::tmem_ld16(tW1 + lane + cb, v);
+          tc::tmem_ld_wait();
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            const int uc = slot_column(M, P, cb + e);
+            if (uc >= 0 && A.g.w[0]) atomicAdd(A.g.w[0] + r * M.k_in + uc, v[e] * gs);
+            else if (uc == -2 && A.g.b[0]) atomicAdd(A.g.b[0] + r, v[e] * gs);
+          }
+        }
+      } else if ((job == 1 || job == 3) && wq < 2) {
+        // [dW2 db2] / [dWh dbh]: row r, input columns 0..63, the ones column
+        // 64 gives the bias
+        const uint32_t ta = job == 1 ? tW2 : tWh;
+        float* gw = job == 1 ? A.g.w[1] : A.g.w_h3;
+        float* gb = job == 1 ? A.g.b[1] : A.g.b_h3;
+#pragma unroll 1
+        for (int cb = 0; cb < kHidden + 16; cb += 16) {
+          float v[16];
+          tc::tmem_ld16(ta + lane + cb, v);
+          tc::tmem_ld_wait();
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            const int col = cb + e;
+            if (col < kHidden && gw) atomicAdd(gw + r * kHidden + col, v[e] * gs);
+            else if (col == kHidden && gb) atomicAdd(gb + r, v[e] * gs);
+          }
+        }
+      } else if (job == 2 && wq < 3) {
+        // [dW3^T; db3]: row r < 64 -> dW3[:, r]; row 64 -> db3
         float v[16];
-        tc::tmem_ld16(tW1 + lane + cb, v);
+        tc::tmem_ld16(tW3 + lane, v);
         tc::tmem_ld_wait();
 #pragma unroll
-        for (int e = 0; e < 16; ++e) {
-          const int uc = slot_column(M, P, cb + e);
-          if (uc >= 0 && A.g.w[0]) atomicAdd(A.g.w[0] + r * M.k_in + uc, v[e] * gs);
-          else if (uc == -2 && A.g.b[0]) atomicAdd(A.g.b[0] + r, v[e] * gs);
+        for (int c = 0; c < kN3; ++c) {
+          if (c >= C) continue;
+          if (r < kHidden && A.g.w[2]) atomicAdd(A.g.w[2] + c * kHidden + r, v[c] * gs);
+          if (r == kHidden && A.g.b[2]) atomicAdd(A.g.b[2] + c, v[c] * gs);
         }
-      }
-    } else if (wg == 1 && wq < 2) {
-      // [dW2 db2]: row r, H1 columns 0..63, the ones column 64 gives db2 r
-#pragma unroll 1
-      for (int cb = 0; cb < kHidden + 16; cb += 16) {
-        float v[16];
-        tc::tmem_ld16(tW2 + lane + cb, v);
-        tc::tmem_ld_wait();
-#pragma unroll
-        for (int e = 0; e < 16; ++e) {
-          const int col = cb + e;
-          if (col < kHidden && A.g.w[1]) atomicAdd(A.g.w[1] + r * kHidden + col, v[e] * gs);
-          else if (col == kHidden && A.g.b[1]) atomicAdd(A.g.b[1] + r, v[e] * gs);
-        }
-      }
-    }
-    if (wg == NWG - 1 && wq < 3) {
-      // [dW3^T; db3]: row r < 64 -> dW3[:, r]; row 64 -> db3
-      float v[16];
-      tc::tmem_ld16(tW3 + lane, v);
-      tc::tmem_ld_wait();
-#pragma unroll
-      for (int c = 0; c < kN3; ++c) {
-        if (c >= C) continue;
-        if (r < kHidden && A.g.w[2]) atomicAdd(A.g.w[2] + c * kHidden + r, v[c] * gs);
-        if (r == kHidden && A.g.b[2]) atomicAdd(A.g.b[2] + c, v[c] * gs);
       }
     }
   }
@@ -830,7 +902,7 @@ __global__ void __launch_bounds__(kRows* NWG, 1) train_tc_kernel(const ntc_mater
 
 template <int ACT, bool LEARNED, int NWG>
 cudaError_t launch_t(const ntc_material& m, const BwdArgs& a, cudaStream_t s) {
-  const TPlan P(m.c0, m.c1, LEARNED, ACT == NTC_ACT_HARDGELU, NWG);
+  const TPlan P(m.c0, m.c1, LEARNED, ACT == NTC_ACT_HARDGELU, NWG, m.hidden_layers == 3);
   const size_t smem = P.total;
   cudaError_t e = cudaFuncSetAttribute(train_tc_kernel<ACT, LEARNED, NWG>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -843,18 +915,21 @@ cudaError_t launch_t(const ntc_material& m, const BwdArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// Pipelines per CTA: 3 when their tiles fit, else 2 (0: does not fit).
+// Pipelines per CTA: the most (3, 2 or 1) whose tiles fit (0: none fits).
 int train_pipelines(const ntc_material& m) {
   const bool learned = m.interp0 == NTC_INTERP_LEARNED, gelu = m.act == NTC_ACT_HARDGELU;
-  for (int n = kMaxNWG; n >= 2; --n)
-    if (TPlan(m.c0, m.c1, learned, gelu, n).fits()) return n;
+  for (int n = kMaxNWG; n >= 1; --n)
+    if (TPlan(m.c0, m.c1, learned, gelu, n, m.hidden_layers == 3).fits()) return n;
   return 0;
 }
 
 template <int ACT, bool LEARNED>
 cudaError_t launch_n(const ntc_material& m, const BwdArgs& a, cudaStream_t s) {
-  return train_pipelines(m) == 3 ? launch_t<ACT, LEARNED, 3>(m, a, s)
-                                 : launch_t<ACT, LEARNED, 2>(m, a, s);
+  switch (train_pipelines(m)) {
+    case 3: return launch_t<ACT, LEARNED, 3>(m, a, s);
+    case 2: return launch_t<ACT, LEARNED, 2>(m, a, s);
+    default: return launch_t<ACT, LEARNED, 1>(m, a, s);
+  }
 }
 
 }  // namespace

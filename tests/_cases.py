@@ -35,8 +35,12 @@ class Case:
     idx1: list
     val0: list              # per level float32 values
     val1: list
-    weights: list           # [w1, b1, w2, b2, w3, b3] float32
+    weights: list           # [w1, b1, w2, b2, (wm, bm,) w3, b3] float32, layer order
     interp0: int = 0        # G0 resampling: 0 bilinear, 1 learned (4 taps concatenated)
+
+    @property
+    def hidden_layers(self):
+        return len(self.weights) // 2 - 1
 
     @property
     def mips(self):
@@ -66,7 +70,8 @@ class Case:
 
 
 def make_case(width=64, height=64, channels=8, c0=8, c1=8, bits0=4, bits1=4, q0=None, q1=None,
-              k_in=None, hidden=64, act=0, out_act=0, seed=0, wgain=1.0, interp0=0):
+              k_in=None, hidden=64, act=0, out_act=0, seed=0, wgain=1.0, interp0=0,
+              hidden_layers=2):
     n0, n1 = 1 << bits0, 1 << bits1
     q0 = 1.0 / n0 if q0 is None else q0
     q1 = 1.0 / n1 if q1 is None else q1
@@ -83,7 +88,8 @@ def make_case(width=64, height=64, channels=8, c0=8, c1=8, bits0=4, bits1=4, q0=
         idx1.append(rng.integers(0, n1, size=(g1h, g1w, c1)).astype(np.int32))
         val0.append(gen.uniform_grid_values((g0h, g0w, c0), lo0, hi0, rng))
         val1.append(gen.uniform_grid_values((g1h, g1w, c1), lo1, hi1, rng))
-    weights = gen.random_mlp(k_in, hidden, channels, 2000 + seed, n_used=used, gain=wgain)
+    weights = gen.random_mlp(k_in, hidden, channels, 2000 + seed, n_used=used, gain=wgain,
+                             hidden_layers=hidden_layers)
     return Case(width, height, channels, c0, c1, bits0, bits1, q0, q1, k_in, hidden, act, out_act,
                 levels, idx0, idx1, val0, val1, weights, interp0)
 

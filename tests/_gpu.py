@@ -21,17 +21,16 @@ def _t(a, dtype=None):
 
 
 def stored_weights(case, precision):
-    """The weights as the library stores them and the exactly converted
-    float64 values the oracle then sees (stored-weight parity)."""
+    """The weights as the library stores them (layer order, 3 or 4 layers)
+    and the exactly converted float64 values the oracle then sees
+    (stored-weight parity)."""
     w = case.weights
-    if precision == ntc.PREC_F16:
-        ws = [w[0].astype(np.float16), w[2].astype(np.float16), w[4].astype(np.float16)]
-        oracle_w = [ws[0].astype(np.float64), w[1], ws[1].astype(np.float64), w[3],
-                    ws[2].astype(np.float64), w[5]]
-        dev = [_t(x) for x in ws]
-    else:
-        oracle_w = list(w)
-        dev = [_t(w[0]), _t(w[2]), _t(w[4])]
+    oracle_w = []
+    dev = []
+    for l in range(len(w) // 2):
+        wl = w[2 * l].astype(np.float16) if precision == ntc.PREC_F16 else w[2 * l]
+        dev.append(_t(wl))
+        oracle_w += [wl.astype(np.float64), w[2 * l + 1]]
     return dev, [np.asarray(x, np.float64) for x in oracle_w]
 
 
@@ -46,7 +45,7 @@ def device_material(case, precision=ntc.PREC_F32, packed=True):
     else:
         g0 = [_t(v) for v in case.val0]
         g1 = [_t(v) for v in case.val1]
-    b = [_t(case.weights[1]), _t(case.weights[3]), _t(case.weights[5])]
+    b = [_t(x) for x in case.weights[1::2]]
     mat = ntc.Material(case.width, case.height, case.channels, case.c0, case.c1, case.bits0,
                        case.bits1, case.q0, case.q1, g0, g1, wdev, b, case.k_in, precision,
                        case.act, case.out_act, interp0=case.interp0)

@@ -106,10 +106,20 @@ def test_valid_material_with_zero_queries_is_a_noop(L):
     (dict(out_act=3), ntc.ERR_ARG),
     (dict(precision=7), ntc.ERR_ARG),
     (dict(encoding=4), ntc.ERR_ARG),
+    (dict(hidden_layers=4), ntc.ERR_ARG),
+    (dict(hidden_layers=1), ntc.ERR_ARG),
+    (dict(hidden_layers=3), ntc.ERR_ARG),                  # w_h3 / b_h3 missing
+    (dict(hidden_layers=3, w_h3=0x20000, b_h3=0x20000, precision=ntc.PREC_F8, k_in=64,
+          scale=0x20000), ntc.ERR_UNSUPPORTED),
 ])
 def test_material_validation(L, kw, code):
     assert _decode_rc(L, _fake_material(**kw), n=5) == code
     assert L.ntc_last_error().decode()
+
+
+def test_three_hidden_layers_valid_material_is_a_noop(L):
+    m = _fake_material(hidden_layers=3, w_h3=0x20000, b_h3=0x20000)
+    assert _decode_rc(L, m, n=0) == ntc.OK
 
 
 def test_pointer_validation(L):

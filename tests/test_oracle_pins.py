@@ -472,11 +472,13 @@ def _flat_params(md):
     return md.grids0 + md.grids1 + md.weights
 
 
-@pytest.mark.parametrize("act", [1, 0])
-def test_gradients_match_central_differences(act):
+@pytest.mark.parametrize("act,hidden_layers", [(1, 2), (0, 2), (1, 3), (0, 3)])
+def test_gradients_match_central_differences(act, hidden_layers):
     """Reverse-mode gradients vs central differences (h = 1e-6) on a tiny
-    material with the simulated-quantisation noise switched on."""
-    case = make_case(16, 16, 3, 2, 2, k_in=32, hidden=8, act=act, seed=10, wgain=2.0)
+    material with the simulated-quantisation noise switched on, two or three
+    hidden layers."""
+    case = make_case(16, 16, 3, 2, 2, k_in=32, hidden=8, act=act, seed=10, wgain=2.0,
+                     hidden_layers=hidden_layers)
     md = case.oracle_model(quantized=False)
     rng = np.random.default_rng(1)
     xym = np.array([[rng.integers(0, 16 >> m), rng.integers(0, 16 >> m), m]
@@ -503,6 +505,28 @@ def test_gradients_match_central_differences(act):
         err = np.linalg.norm(ana - num) / max(np.linalg.norm(num), 1e-30)
         assert err < 1e-6, (p.shape, err)
     assert loss > 0
+
+
+def test_third_hidden_layer_reduces_to_two():
+    """Three hidden layers whose third is the identity (ReLU, W = I, b = 0;
+    h2 >= 0 passes unchanged) decode exactly like the two-layer model, and
+    their gradients agree: the third layer's input gradient is the two-layer
+    model's, and its weight gradient is the outer product dz h2^T."""
+    case = make_case(32, 32, 4, 4, 4, k_in=32, hidden=16, act=0, seed=13)
+    md2 = case.oracle_model(quantized=False)
+    w = [np.asarray(a, np.float64) for a in case.weights]
+    md3 = case.oracle_model(weights=w[:4] + [np.eye(16), np.zeros(16)] + w[4:], quantized=False)
+    assert md3.hidden_layers == 3 and md2.hidden_layers == 2
+    rng = np.random.default_rng(4)
+    xym = np.array([[rng.integers(0, 32 >> m), rng.integers(0, 32 >> m), m]
+                    for m in rng.integers(0, md2.mips, size=40)], np.int32)
+    assert np.array_equal(md3.decode_xym(xym), md2.decode_xym(xym))
+    dout = rng.standard_normal((40, 4))
+    g2, g3 = md2.backward_xym(xym, dout), md3.backward_xym(xym, dout)
+    for a, b in zip(g2["grid0"] + g2["grid1"] + g2["w"][:4] + g2["w"][4:],
+                    g3["grid0"] + g3["grid1"] + g3["w"][:4] + g3["w"][6:]):
+        assert np.allclose(a, b, rtol=1e-12, atol=1e-14)
+    assert np.any(g3["w"][4] != 0) and np.any(g3["w"][5] != 0)
 
 
 def test_backward_is_vector_jacobian_product():
