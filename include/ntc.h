@@ -227,6 +227,26 @@ int ntc_decode(const ntc_material* m, const float* uvl, int64_t n, void* out,
                int32_t out_dtype, int32_t filter, int32_t flags, uint64_t noise_seed,
                int64_t noise_step, void* stream);
 
+/* Decode with HOST query and output buffers (pinned host memory for the
+ * copies to overlap): the queries stream through `workspace` (device,
+ * caller-owned, 16-byte aligned) in chunks; the copy of chunk i+1 to the
+ * device, the decode of chunk i (on `stream`) and the copy of chunk i-1 back
+ * run concurrently on two helper streams that the library creates once per
+ * device.  Outputs equal ntc_decode's.  The call returns once the work is
+ * enqueued: `out_host` is complete when `stream` reaches the call's end
+ * (fork and join through events, so the call can be captured in a CUDA
+ * graph).  The chunk is workspace_bytes / (2 (12 + channels * element bytes))
+ * queries rounded down to a multiple of 128 (NTC_ERR_ARG below 128);
+ * ntc_decode_host_workspace_bytes gives the size for a chosen chunk.
+ * Nearest and trilinear filtering (stochastic filtering hashes the query
+ * index: NTC_ERR_UNSUPPORTED); flags as ntc_decode. */
+int ntc_decode_host(const ntc_material* m, const float* uvl_host, int64_t n, void* out_host,
+                    int32_t out_dtype, int32_t filter, int32_t flags, uint64_t noise_seed,
+                    int64_t noise_step, void* workspace, size_t workspace_bytes, void* stream);
+
+/* Workspace bytes of ntc_decode_host for chunks of `chunk` queries. */
+size_t ntc_decode_host_workspace_bytes(int32_t channels, int32_t out_dtype, int64_t chunk);
+
 /* Launch shape of the tensor-core decode: warpgroup tile pipelines per CTA
  * (one CTA per SM, 128 TMEM columns per pipeline), 2, 3 or 4, or 5 for the
  * warp-specialised form (4 compute warpgroups whose MMA chains a fifth

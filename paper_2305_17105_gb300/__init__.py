@@ -101,6 +101,8 @@ SIGNATURES = {
     "ntc_sample_features": (C.c_int, [_P, _P, _I64, _P, _I32, _U64, _I64, _P]),
     "ntc_device_status": (C.c_int, [_I32]),
     "ntc_batch_workspace_bytes": (C.c_size_t, []),
+    "ntc_decode_host": (C.c_int, [_P, _P, _I64, _P, _I32, _I32, _I32, _U64, _I64, _P, C.c_size_t, _P]),
+    "ntc_decode_host_workspace_bytes": (C.c_size_t, [_I32, _I32, _I64]),
     "ntc_batch_prepare": (C.c_int, [_P, _P, _I32, _I32, _P, C.c_size_t, _P, _P]),
     "ntc_decode_batched": (C.c_int, [_P, _P, _P, _I32, _P]),
     "ntc_set_decode_warpgroups": (C.c_int, [_I32]),
@@ -274,6 +276,31 @@ def ntc_decode(mat: Material, uvl: torch.Tensor, out_dtype=torch.float32,
     _call("ntc_decode", C.byref(s), _ptr(uvl), n, _ptr(out), dt, filter, flags, noise_seed,
           noise_step, _stream(stream))
     return out
+
+
+def ntc_decode_host(mat: Material, uvl_host: torch.Tensor, out_host=None, out_dtype=torch.float32,
+                    filter=FILTER_NEAREST, flags=0, noise_seed=0, noise_step=0, workspace=None,
+                    chunk=1 << 20, stream=None):
+    """Decode HOST (pinned) queries ``[n, 3]`` into a HOST output, copies and
+    decode overlapped chunk by chunk through a device ``workspace`` (uint8
+    CUDA tensor; allocated for ``chunk`` queries when None).  The output is
+    complete once ``stream`` reaches this call's end."""
+    if uvl_host.is_cuda or not uvl_host.is_contiguous() or uvl_host.dtype != torch.float32:
+        raise ValueError("uvl_host must be a contiguous float32 host tensor")
+    n = uvl_host.shape[0]
+    if out_host is None:
+        out_host = torch.empty((n, mat.channels), dtype=out_dtype, pin_memory=True)
+    if out_host.is_cuda or not out_host.is_contiguous():
+        raise ValueError("out_host must be a contiguous host tensor")
+    dt = DTYPE_F16 if out_host.dtype == torch.float16 else DTYPE_F32
+    if workspace is None:
+        nbytes = lib().ntc_decode_host_workspace_bytes(mat.channels, dt, chunk)
+        workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    s = mat.struct
+    _call("ntc_decode_host", C.byref(s), C.c_void_p(uvl_host.data_ptr()), n,
+          C.c_void_p(out_host.data_ptr()), dt, filter, flags, noise_seed, noise_step,
+          _ptr(workspace), workspace.numel(), _stream(stream))
+    return out_host
 
 
 def ntc_set_decode_warpgroups(nwg: int) -> None:

@@ -1,6 +1,7 @@
 // C-ABI entry points of libntc.so (declared in include/ntc.h): argument
 // validation, error reporting and dispatch to the kernels.
 #include <atomic>
+#include <mutex>
 #include <vector>
 #include <stdarg.h>
 #include <stdio.h>
@@ -106,8 +107,54 @@ int check_material(const ntc_material* m, bool need_f32_grids) {
 
 std::atomic<int> g_decode_nwg{0};  // tensor-core decode warpgroups per CTA (0 = default)
 
+// Helper streams and events of ntc_decode_host, created once per device and
+// used under g_pipe_mu (one enqueue sequence at a time).
+struct HostPipe {
+  bool ready = false;
+  cudaStream_t up = nullptr, down = nullptr;
+  cudaEvent_t fork, join_up, join_down, uploaded[2], decoded[2], downloaded[2];
+};
+std::mutex g_pipe_mu;
+HostPipe g_pipes[64];
+
 bool use_simt(const ntc_material* m, int flags) {
   return (flags & NTC_FLAG_SIMT) || m->precision == NTC_PREC_F32;
+}
+
+// The decode of a validated call.
+int decode_impl(const ntc_material* m, const float* uvl, int64_t n, void* out, int32_t out_dtype,
+                int32_t filter, int32_t flags, uint64_t noise_seed, int64_t noise_step,
+                cudaStream_t s) {
+  if (use_simt(m, flags) || (flags & NTC_FLAG_NOISE))
+    return cuda_status(ntc::launch_decode_simt(*m, uvl, n, out, out_dtype, filter,
+                                               (flags & NTC_FLAG_NOISE) != 0, noise_seed,
+                                               noise_step, s),
+                       "decode (FP32 CUDA cores)");
+  return cuda_status(ntc::launch_decode_tc(*m, uvl, n, out, out_dtype, filter,
+                                           ntc::jitter_key(noise_seed, noise_step), s,
+                                           g_decode_nwg.load()),
+                     "decode (tcgen05)");
+}
+
+// This device's helper streams and events (created on first use; caller
+// holds g_pipe_mu).
+int host_pipe(HostPipe** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
+    return cuda_status(cudaErrorInvalidDevice, "decode_host device");
+  HostPipe& P = g_pipes[dev];
+  if (!P.ready) {
+    cudaError_t e = cudaStreamCreateWithFlags(&P.up, cudaStreamNonBlocking);
+    if (!e) e = cudaStreamCreateWithFlags(&P.down, cudaStreamNonBlocking);
+    cudaEvent_t* evs[9] = {&P.fork, &P.join_up, &P.join_down, &P.uploaded[0], &P.uploaded[1],
+                           &P.decoded[0], &P.decoded[1], &P.downloaded[0], &P.downloaded[1]};
+    for (cudaEvent_t* ev : evs)
+      if (!e) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    if (e) return cuda_status(e, "decode_host streams");
+    P.ready = true;
+  }
+  *out = &P;
+  return NTC_OK;
 }
 
 }  // namespace
@@ -174,16 +221,83 @@ int ntc_decode(const ntc_material* m, const float* uvl, int64_t n, void* out, in
   if (n == 0) return NTC_OK;
   CHECK_PTR(uvl, "uvl");
   CHECK_PTR(out, "out");
+  return decode_impl(m, uvl, n, out, out_dtype, filter, flags, noise_seed, noise_step,
+                     static_cast<cudaStream_t>(stream));
+}
+
+size_t ntc_decode_host_workspace_bytes(int32_t channels, int32_t out_dtype, int64_t chunk) {
+  if (channels < 1 || channels > NTC_MAX_CHANNELS || chunk < 0) return 0;
+  const size_t eb = out_dtype == NTC_DTYPE_F16 ? 2 : 4;
+  return 2 * (size_t)chunk * (12 + (size_t)channels * eb);
+}
+
+int ntc_decode_host(const ntc_material* m, const float* uvl_host, int64_t n, void* out_host,
+                    int32_t out_dtype, int32_t filter, int32_t flags, uint64_t noise_seed,
+                    int64_t noise_step, void* workspace, size_t workspace_bytes, void* stream) {
+  int st = check_material(m, (flags & NTC_FLAG_NOISE) != 0);
+  if (st) return st;
+  if (n < 0) return fail(NTC_ERR_ARG, "n < 0");
+  if (out_dtype != NTC_DTYPE_F32 && out_dtype != NTC_DTYPE_F16) return fail(NTC_ERR_ARG, "out_dtype");
+  if (filter == NTC_FILTER_STOCHASTIC)
+    return fail(NTC_ERR_UNSUPPORTED, "decode_host: nearest or trilinear filtering");
+  if (filter != NTC_FILTER_NEAREST && filter != NTC_FILTER_TRILINEAR)
+    return fail(NTC_ERR_ARG, "filter");
+  if ((flags & NTC_FLAG_NOISE) && filter != NTC_FILTER_NEAREST)
+    return fail(NTC_ERR_ARG, "noise needs nearest filtering");
+  if (n == 0) return NTC_OK;
+  if (!uvl_host || !out_host) return fail(NTC_ERR_ARG, "host buffer is NULL");
+  CHECK_PTR(workspace, "workspace");
+  const size_t eb = out_dtype == NTC_DTYPE_F16 ? 2 : 4, C = (size_t)m->channels;
+  const size_t per = 12 + C * eb;
+  const int64_t chunk = (int64_t)(workspace_bytes / (2 * per)) / 128 * 128;
+  if (chunk < 128) return fail(NTC_ERR_ARG, "decode_host: workspace below two 128-query chunks");
+  uint8_t* ws = static_cast<uint8_t*>(workspace);
+  // slots: inputs [2][chunk][3] floats, then outputs [2][chunk][C] (16-byte aligned:
+  // chunk is a multiple of 128)
+  float* in_slot[2] = {reinterpret_cast<float*>(ws), reinterpret_cast<float*>(ws + chunk * 12)};
+  uint8_t* out_slot[2] = {ws + 2 * chunk * 12, ws + 2 * chunk * 12 + chunk * C * eb};
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (use_simt(m, flags) || (flags & NTC_FLAG_NOISE))
-    return cuda_status(ntc::launch_decode_simt(*m, uvl, n, out, out_dtype, filter,
-                                               (flags & NTC_FLAG_NOISE) != 0, noise_seed,
-                                               noise_step, s),
-                       "decode (FP32 CUDA cores)");
-  return cuda_status(ntc::launch_decode_tc(*m, uvl, n, out, out_dtype, filter,
-                                           ntc::jitter_key(noise_seed, noise_step), s,
-                                           g_decode_nwg.load()),
-                     "decode (tcgen05)");
+  std::lock_guard<std::mutex> lock(g_pipe_mu);
+  HostPipe* P = nullptr;
+  if (int e = host_pipe(&P)) return e;
+  // fork: the helper streams start after the work already on `stream`
+  {
+    cudaError_t e = cudaEventRecord(P->fork, s);
+    if (!e) e = cudaStreamWaitEvent(P->up, P->fork, 0);
+    if (!e) e = cudaStreamWaitEvent(P->down, P->fork, 0);
+    if (e) return cuda_status(e, "decode_host fork");
+  }
+  for (int64_t i = 0; i * chunk < n; ++i) {
+    const int sl = (int)(i & 1);
+    const int64_t off = i * chunk, cnt = n - off < chunk ? n - off : chunk;
+    cudaError_t e = cudaSuccess;
+    // chunk i up: its slot is free once the decode of chunk i-2 has read it
+    if (i >= 2) e = cudaStreamWaitEvent(P->up, P->decoded[sl], 0);
+    if (!e) e = cudaMemcpyAsync(in_slot[sl], uvl_host + 3 * off, (size_t)cnt * 12,
+                                cudaMemcpyHostToDevice, P->up);
+    if (!e) e = cudaEventRecord(P->uploaded[sl], P->up);
+    // decode on the caller's stream once the inputs are there and the output
+    // slot has been copied back (chunk i-2)
+    if (!e) e = cudaStreamWaitEvent(s, P->uploaded[sl], 0);
+    if (!e && i >= 2) e = cudaStreamWaitEvent(s, P->downloaded[sl], 0);
+    if (e) return cuda_status(e, "decode_host enqueue");
+    st = decode_impl(m, in_slot[sl], cnt, out_slot[sl], out_dtype, filter, flags, noise_seed,
+                     noise_step, s);
+    if (st) return st;
+    e = cudaEventRecord(P->decoded[sl], s);
+    // chunk i down
+    if (!e) e = cudaStreamWaitEvent(P->down, P->decoded[sl], 0);
+    if (!e) e = cudaMemcpyAsync(static_cast<uint8_t*>(out_host) + (size_t)off * C * eb,
+                                out_slot[sl], (size_t)cnt * C * eb, cudaMemcpyDeviceToHost, P->down);
+    if (!e) e = cudaEventRecord(P->downloaded[sl], P->down);
+    if (e) return cuda_status(e, "decode_host enqueue");
+  }
+  // join: `stream` continues after the last copies of both helpers
+  cudaError_t e = cudaEventRecord(P->join_up, P->up);
+  if (!e) e = cudaEventRecord(P->join_down, P->down);
+  if (!e) e = cudaStreamWaitEvent(s, P->join_up, 0);
+  if (!e) e = cudaStreamWaitEvent(s, P->join_down, 0);
+  return cuda_status(e, "decode_host join");
 }
 
 int ntc_set_decode_warpgroups(int32_t nwg) {

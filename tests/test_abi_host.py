@@ -122,6 +122,32 @@ def test_three_hidden_layers_valid_material_is_a_noop(L):
     assert _decode_rc(L, m, n=0) == ntc.OK
 
 
+def test_decode_host_validation(L):
+    L.ntc_decode_host.restype = C.c_int
+    L.ntc_decode_host.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int32,
+                                  C.c_int32, C.c_int32, C.c_uint64, C.c_int64, C.c_void_p,
+                                  C.c_size_t, C.c_void_p]
+    L.ntc_decode_host_workspace_bytes.restype = C.c_size_t
+    L.ntc_decode_host_workspace_bytes.argtypes = [C.c_int32, C.c_int32, C.c_int64]
+    m = C.byref(_fake_material())
+    host = (C.c_float * 30)()
+    ok = L.ntc_decode_host_workspace_bytes(4, ntc.DTYPE_F16, 128)
+    assert ok == 2 * 128 * (12 + 4 * 2)
+    assert L.ntc_decode_host_workspace_bytes(0, 0, 128) == 0
+    args = lambda **kw: dict(dict(uvl=C.addressof(host), n=10, out=C.addressof(host), dt=0, f=0,
+                                  ws=0x50000, wsb=ok * 2), **kw)
+    def rc(a):
+        return L.ntc_decode_host(m, a["uvl"], a["n"], a["out"], a["dt"], a["f"], 0, 0, 0, a["ws"],
+                                 a["wsb"], None)
+    assert rc(args(n=0)) == ntc.OK
+    assert rc(args(f=ntc.FILTER_STOCHASTIC)) == ntc.ERR_UNSUPPORTED
+    assert rc(args(uvl=None)) == ntc.ERR_ARG
+    assert rc(args(ws=None)) == ntc.ERR_ARG
+    assert rc(args(ws=0x50004)) == ntc.ERR_ALIGN
+    assert rc(args(wsb=ok // 2)) == ntc.ERR_ARG     # below two 128-query chunks
+    assert rc(args(dt=7)) == ntc.ERR_ARG
+
+
 def test_pointer_validation(L):
     assert _decode_rc(L, None, n=5) == ntc.ERR_ARG
     assert _decode_rc(L, _fake_material(), n=5, uvl=0x30004) == ntc.ERR_ALIGN
