@@ -439,6 +439,43 @@ def paper_form_train(ntc, batch, stream, steps=20, hidden_layers=2):
             "status": ntc.ntc_device_status()}
 
 
+def vq_eval(ntc, q_dev, stream):
+    """Decode of the 2^24 queries with a vector-quantised G0 (the paper's
+    VQ-8: two 256-entry codebooks of 8 values, two 8-bit indices per cell,
+    features = the sum of the two entries) on the 4096^2 x 16 material, G0
+    1024^2 (16 bits per cell) + G1 512^2 x 12 at 4 bits, MLP 48-64-64-16,
+    FP16 tensor cores, random indices, codebooks and weights."""
+    import torch
+    g = torch.Generator(device="cuda")
+    g.manual_seed(7107)
+    books, c0, c1, k = 2, 8, 12, 48
+    levels = ntc.ntc_pyramid(DEC_SIDE, DEC_SIDE)
+    g0 = [torch.randint(0, 256, (h0, w0, books), dtype=torch.uint8, device="cuda", generator=g)
+          for (w0, h0), _ in levels]
+    g1 = [torch.randint(0, 256, (h1, w1, ntc.cell_bytes(c1, 4)), dtype=torch.uint8, device="cuda",
+                        generator=g) for _, (w1, h1) in levels]
+    cb = (torch.rand((books, 256, c0), device="cuda", generator=g) - 0.5) * 0.5
+    w = gen.random_mlp(k, 64, DEC_C, seed=7108, n_used=c0 + c1 + 13)
+    mat = ntc.Material(DEC_SIDE, DEC_SIDE, DEC_C, c0, c1, 8, 4, 1 / 16, 1 / 16, g0, g1,
+                       [torch.from_numpy(x).cuda().half() for x in w[0::2]],
+                       [torch.from_numpy(x).cuda() for x in w[1::2]], k, ntc.PREC_F16,
+                       codebook0=cb.contiguous())
+    out = torch.empty((q_dev.shape[0], DEC_C), dtype=torch.float16, device="cuda")
+    ntc.ntc_decode(mat, q_dev, out=out)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(5):
+        ntc.ntc_decode(mat, q_dev, out=out)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / 5
+    return {"workload": "4096^2x16, G0 1024^2 VQ-8 (2 codebooks x 256 x 8, 16 bits per cell) + "
+                        "G1 512^2x12 at 4 bits, MLP 48-64-64-16, 2^24 random queries",
+            "decode_ms": ms, "texels_per_s": q_dev.shape[0] / (ms / 1e3),
+            "status": ntc.ntc_device_status()}
+
+
 # ----------------------------------------------------------------------------
 # Many materials: batched decode launch, graph-captured training of all of them
 # ----------------------------------------------------------------------------
@@ -872,6 +909,13 @@ def main():
         except Exception as e:  # reported, never fatal to the headline line
             paper_form = {"error": f"{type(e).__name__}: {e}"[:300]}
 
+    vq = None
+    if not args.no_extras:
+        try:
+            vq = vq_eval(ntc, q_dev, stream)
+        except Exception as e:  # reported, never fatal to the headline line
+            vq = {"error": f"{type(e).__name__}: {e}"[:300]}
+
     equal = None
     if not args.no_extras and not args.no_fp32_compare:
         try:
@@ -903,7 +947,7 @@ def main():
         "decode_ms": statistics.median(dec_ms), "train_ms": statistics.median(trn_ms),
         "roofline": roof, "train_roofline": train_roof, "tuning": tuning, "e2e": e2e, "fp32_path": fp32, "cpu_baseline": cpu,
         "render": render, "multi_material": multi, "paper_form": paper_form, "train_crops": crops,
-        "equal_psnr_training": equal,
+        "equal_psnr_training": equal, "vq_decode": vq,
         "gpu_launches": kernels_per_step * args.steps,
         "clocks": clk.summary(), "wall_s": t_wall,
     }

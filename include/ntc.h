@@ -134,6 +134,13 @@ typedef struct {
                             FP16 training step */
   const void* w_h3;      /* [hidden][hidden], the precision's type (hidden_layers == 3) */
   const float* b_h3;     /* [hidden] float32 */
+  int32_t vq_books;      /* 0: G0 scalar-quantised like G1.  1..4: vector-quantised G0
+                            (the paper's comparison with vector quantisation): grid0 of
+                            every level holds uint8 [g0_h][g0_w][vq_books] indices, index
+                            b into codebook b of 256 entries of c0 values, and a cell's
+                            features are the sum of its vq_books entries (bits0 is
+                            unused).  Decode only (FP32 and FP16 forms, no noise) */
+  const float* codebook0; /* [vq_books][256][c0] float32, device (vq_books > 0) */
 } ntc_material;
 
 /* Gradient outputs of ntc_backward, ACCUMULATED (+=) in float32, same
@@ -385,6 +392,15 @@ int ntc_sample_batch(uint64_t seed, int64_t step, int64_t batch, int32_t width,
  * the crop repeats inside it. */
 int ntc_sample_crops(uint64_t seed, int64_t step, int64_t batch, int32_t width,
                      int32_t height, int32_t mips, int32_t* xym_out, void* stream);
+
+/* Vector quantisation of `cells` rows of c0 float32 values (device) against
+ * `books` codebooks [books][256][c0] (device float32), greedy residual
+ * search: index b is the entry nearest (squared distance, FP32, channels
+ * summed in order without fused multiply-add, ties to the lowest index) to
+ * what the entries of books 0..b-1 leave of the row.  idx_out [cells][books]
+ * uint8, device.  Produces the indices of a vector-quantised G0. */
+int ntc_vq_assign(const float* values, int64_t cells, int32_t c0, const float* codebooks,
+                  int32_t books, uint8_t* idx_out, void* stream);
 
 /* The MLP input rows of nearest decodes (Sec. 4.3), exposed for testing:
  * float32 [n][k_in]. */

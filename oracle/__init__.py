@@ -216,6 +216,44 @@ def round_e4m3(x) -> np.ndarray:
     return np.copysign(r, x)
 
 
+def vq_reconstruct(idx: np.ndarray, codebooks: np.ndarray) -> np.ndarray:
+    """Vector-quantised grid (the paper's comparison with vector
+    quantisation): every cell of ``idx`` ``[..., books]`` (uint8) maps to the
+    sum over b of entry idx[..., b] of codebook b (``[books, 256, c]``);
+    float64 ``[..., c]``."""
+    idx = np.asarray(idx)
+    cb = np.asarray(codebooks, np.float64)
+    out = np.zeros(idx.shape[:-1] + (cb.shape[2],), np.float64)
+    for b in range(cb.shape[0]):
+        out += cb[b][idx[..., b].astype(np.int64)]
+    return out
+
+
+def vq_assign(values: np.ndarray, codebooks: np.ndarray) -> np.ndarray:
+    """Greedy residual vector quantisation of rows ``values`` ``[n, c]``:
+    index b is the entry of codebook b nearest to what books 0..b-1 leave of
+    the row (squared distance in FP32, channels summed in order, ties to the
+    lowest index), then the entry is subtracted.  uint8 ``[n, books]``."""
+    r = np.array(values, np.float32)
+    cb = np.asarray(codebooks, np.float32)
+    n, c = r.shape
+    idx = np.zeros((n, cb.shape[0]), np.uint8)
+    for b in range(cb.shape[0]):
+        best = np.full(n, np.inf, np.float32)
+        kb = np.zeros(n, np.int64)
+        for k in range(256):
+            d = np.zeros(n, np.float32)
+            for ch in range(c):
+                df = (r[:, ch] - cb[b, k, ch]).astype(np.float32)
+                d = (d + (df * df).astype(np.float32)).astype(np.float32)
+            better = d < best
+            best[better] = d[better]
+            kb[better] = k
+        idx[:, b] = kb
+        r = (r - cb[b][kb]).astype(np.float32)
+    return idx
+
+
 def activation(act: int, z: float) -> float:
     return float(lib().or_activation(act, z))
 

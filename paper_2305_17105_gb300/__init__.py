@@ -56,7 +56,7 @@ class ntc_material(C.Structure):
                 ("act", C.c_int32), ("out_act", C.c_int32), ("precision", C.c_int32),
                 ("interp0", C.c_int32), ("lv", ntc_level * MAX_LEVELS), ("w", C.c_void_p * 3), ("b", C.c_void_p * 3),
                 ("scale", C.c_void_p), ("hidden_layers", C.c_int32), ("w_h3", C.c_void_p),
-                ("b_h3", C.c_void_p)]
+                ("b_h3", C.c_void_p), ("vq_books", C.c_int32), ("codebook0", C.c_void_p)]
 
 
 class ntc_grads(C.Structure):
@@ -103,6 +103,7 @@ SIGNATURES = {
     "ntc_batch_workspace_bytes": (C.c_size_t, []),
     "ntc_decode_host": (C.c_int, [_P, _P, _I64, _P, _I32, _I32, _I32, _U64, _I64, _P, C.c_size_t, _P]),
     "ntc_decode_host_workspace_bytes": (C.c_size_t, [_I32, _I32, _I64]),
+    "ntc_vq_assign": (C.c_int, [_P, _I64, _I32, _P, _I32, _P, _P]),
     "ntc_batch_prepare": (C.c_int, [_P, _P, _I32, _I32, _P, C.c_size_t, _P, _P]),
     "ntc_decode_batched": (C.c_int, [_P, _P, _P, _I32, _P]),
     "ntc_set_decode_warpgroups": (C.c_int, [_I32]),
@@ -209,11 +210,13 @@ class Material:
     ``[out][in]`` tensors of the precision's dtype (float32, float16, or
     uint8 holding E4M3 bytes); ``biases`` float32, same order; ``scale`` (F8
     only) float32 ``[6]``: weight scales then activation scales.
+    ``codebook0`` (vector-quantised G0) float32 ``[books, 256, c0]``: then
+    ``grids0[j]`` are uint8 ``[g0_h, g0_w, books]`` indices.
     """
 
     def __init__(self, width, height, channels, c0, c1, bits0, bits1, q0, q1, grids0, grids1,
                  weights, biases, k_in, precision=PREC_F32, act=ACT_RELU, out_act=OUT_SIGMOID,
-                 scale=None, interp0=0):
+                 scale=None, interp0=0, codebook0=None):
         self.width, self.height, self.channels = width, height, channels
         self.mips = mips_of(width, height)
         self.c0, self.c1, self.bits0, self.bits1 = c0, c1, bits0, bits1
@@ -224,6 +227,7 @@ class Material:
         self.k_in, self.precision, self.act, self.out_act = k_in, precision, act, out_act
         self.scale = scale
         self.interp0 = interp0
+        self.codebook0 = codebook0
         self.encoding = GRID_PACKED if self.grids0[0].dtype == torch.uint8 else GRID_F32
         self.levels = len(self.grids0)
 
@@ -250,6 +254,8 @@ class Material:
         if w[1] is not None:
             s.w_h3, s.b_h3 = w[1].data_ptr(), b[1].data_ptr()
         s.scale = self.scale.data_ptr() if self.scale is not None else None
+        if self.codebook0 is not None:
+            s.vq_books, s.codebook0 = self.codebook0.shape[0], self.codebook0.data_ptr()
         return s
 
     def with_(self, **kw) -> "Material":
@@ -301,6 +307,20 @@ def ntc_decode_host(mat: Material, uvl_host: torch.Tensor, out_host=None, out_dt
           C.c_void_p(out_host.data_ptr()), dt, filter, flags, noise_seed, noise_step,
           _ptr(workspace), workspace.numel(), _stream(stream))
     return out_host
+
+
+def ntc_vq_assign(values: torch.Tensor, codebooks: torch.Tensor, stream=None) -> torch.Tensor:
+    """Greedy residual vector quantisation of ``values`` ``[cells, c0]``
+    against ``codebooks`` ``[books, 256, c0]`` (CUDA float32) -> uint8
+    indices ``[cells, books]``."""
+    _dev(values, "values")
+    _dev(codebooks, "codebooks")
+    cells, c0 = values.shape
+    books = codebooks.shape[0]
+    idx = torch.empty((cells, books), dtype=torch.uint8, device=values.device)
+    _call("ntc_vq_assign", _ptr(values), cells, c0, _ptr(codebooks), books, _ptr(idx),
+          _stream(stream))
+    return idx
 
 
 def ntc_set_decode_warpgroups(nwg: int) -> None:

@@ -251,6 +251,62 @@ cudaError_t launch_unpack(const uint8_t* packed, int64_t cells, int c, int bits,
   return cudaGetLastError();
 }
 
+// Greedy residual vector quantisation of one row per thread against the
+// codebooks staged in shared memory: FP32 squared distances with the channels
+// summed in order and no fused multiply-add, ties to the lowest index.
+__global__ void __launch_bounds__(256) vq_assign_kernel(const float* __restrict__ values,
+                                                        int64_t cells, int c0,
+                                                        const float* __restrict__ books, int nb,
+                                                        uint8_t* __restrict__ idx) {
+  extern __shared__ float cb[];  // [nb][256][c0]
+  for (int i = threadIdx.x; i < nb * 256 * c0; i += blockDim.x) cb[i] = books[i];
+  __syncthreads();
+  for (int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; cell < cells;
+       cell += (int64_t)gridDim.x * blockDim.x) {
+    float r[kMaxGridCh];
+#pragma unroll
+    for (int ch = 0; ch < kMaxGridCh; ++ch) r[ch] = ch < c0 ? values[cell * c0 + ch] : 0.f;
+    for (int b = 0; b < nb; ++b) {
+      float best = __int_as_float(0x7f800000);  // +inf
+      int kb = 0;
+#pragma unroll 1
+      for (int k = 0; k < 256; ++k) {
+        const float* e = cb + (b * 256 + k) * c0;
+        float d = 0.f;
+#pragma unroll
+        for (int ch = 0; ch < kMaxGridCh; ++ch)
+          if (ch < c0) {
+            const float df = __fsub_rn(r[ch], e[ch]);
+            d = __fadd_rn(d, __fmul_rn(df, df));
+          }
+        if (d < best) {
+          best = d;
+          kb = k;
+        }
+      }
+      idx[cell * nb + b] = (uint8_t)kb;
+      const float* e = cb + (b * 256 + kb) * c0;
+#pragma unroll
+      for (int ch = 0; ch < kMaxGridCh; ++ch)
+        if (ch < c0) r[ch] = __fsub_rn(r[ch], e[ch]);
+    }
+  }
+}
+
+cudaError_t launch_vq_assign(const float* values, int64_t cells, int c0, const float* books, int nb,
+                             uint8_t* idx, cudaStream_t s) {
+  if (cells == 0) return cudaSuccess;
+  const size_t smem = (size_t)nb * 256 * c0 * sizeof(float);
+  cudaError_t e = cudaFuncSetAttribute(vq_assign_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  const int64_t blocks = (cells + 255) / 256;
+  const int64_t cap = (int64_t)sm_count() * 4;
+  vq_assign_kernel<<<(int)(blocks < cap ? blocks : cap), 256, smem, s>>>(values, cells, c0, books,
+                                                                       nb, idx);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_sample_batch(uint64_t seed, int64_t step, int64_t batch, int w, int h, int mips,
                                 int crops, int32_t* xym, cudaStream_t s) {
   if (batch == 0) return cudaSuccess;

@@ -102,6 +102,15 @@ int check_material(const ntc_material* m, bool need_f32_grids) {
     if (m->precision == NTC_PREC_F8)
       return fail(NTC_ERR_UNSUPPORTED, "three hidden layers: FP32 or FP16 weights");
   }
+  if (m->vq_books < 0 || m->vq_books > 4)
+    return fail(NTC_ERR_ARG, "vq_books = %d outside 0..4", m->vq_books);
+  if (m->vq_books > 0) {
+    CHECK_PTR(m->codebook0, "codebook0");
+    if (m->precision == NTC_PREC_F8)
+      return fail(NTC_ERR_UNSUPPORTED, "vector-quantised G0: FP32 or FP16 weights");
+    if (need_f32_grids)
+      return fail(NTC_ERR_UNSUPPORTED, "vector-quantised G0: decode only, without noise");
+  }
   return NTC_OK;
 }
 
@@ -583,6 +592,8 @@ int ntc_batch_prepare(const ntc_material* mats, const int64_t* n_queries, int32_
       return fail(NTC_ERR_UNSUPPORTED, "batch material %d: batches decode FP16 materials", i);
     if (m->hidden_layers == 3)
       return fail(NTC_ERR_UNSUPPORTED, "batch material %d: batches decode two hidden layers", i);
+    if (m->vq_books > 0)
+      return fail(NTC_ERR_UNSUPPORTED, "batch material %d: batches decode scalar grids", i);
     if (n_queries[i] < 0) return fail(NTC_ERR_ARG, "batch material %d: negative query count", i);
     const int c = ntc::fast_class(*m);
     cls = cls == -2 ? c : (cls == c ? cls : (cls != 0 && c != 0 ? -1 : 0));
@@ -668,6 +679,19 @@ static int sample_batch(uint64_t seed, int64_t step, int64_t batch, int32_t widt
 int ntc_sample_batch(uint64_t seed, int64_t step, int64_t batch, int32_t width, int32_t height,
                      int32_t mips, int32_t* xym_out, void* stream) {
   return sample_batch(seed, step, batch, width, height, mips, 0, xym_out, stream);
+}
+
+int ntc_vq_assign(const float* values, int64_t cells, int32_t c0, const float* codebooks,
+                  int32_t books, uint8_t* idx_out, void* stream) {
+  if (cells < 0 || c0 < 1 || c0 > ntc::kMaxGridCh || books < 1 || books > 4)
+    return fail(NTC_ERR_ARG, "vq_assign args");
+  if (cells == 0) return NTC_OK;
+  CHECK_PTR(values, "values");
+  CHECK_PTR(codebooks, "codebooks");
+  if (!idx_out) return fail(NTC_ERR_ARG, "idx_out is NULL");
+  return cuda_status(ntc::launch_vq_assign(values, cells, c0, codebooks, books, idx_out,
+                                           static_cast<cudaStream_t>(stream)),
+                     "vq_assign");
 }
 
 int ntc_sample_crops(uint64_t seed, int64_t step, int64_t batch, int32_t width, int32_t height,

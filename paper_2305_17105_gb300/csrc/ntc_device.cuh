@@ -196,6 +196,21 @@ struct GridSample {
   float acc[kMaxGridCh];
 };
 
+// Vector-quantised G0 (vq_books > 0): the c0 features of cell `cell` of
+// level j, the sum of the codebook entries its indices select.
+__device__ __forceinline__ void vq_cell(const ntc_material& M, int j, int cell,
+                                        float (&v)[kMaxGridCh]) {
+  const uint8_t* ib = static_cast<const uint8_t*>(M.lv[j].grid0) + (size_t)cell * M.vq_books;
+#pragma unroll
+  for (int ch = 0; ch < kMaxGridCh; ++ch) v[ch] = 0.f;
+  for (int b = 0; b < M.vq_books; ++b) {
+    const float* e = M.codebook0 + ((size_t)b * 256 + ib[b]) * M.c0;
+#pragma unroll
+    for (int ch = 0; ch < kMaxGridCh; ++ch)
+      if (ch < M.c0) v[ch] += __ldg(e + ch);
+  }
+}
+
 __device__ __forceinline__ void sample_grid(const ntc_material& M, int j, int k, int x, int y,
                                             int wm, int hm, bool noise, uint64_t nkey,
                                             GridSample& gs, Taps* taps_out = nullptr) {
@@ -207,6 +222,17 @@ __device__ __forceinline__ void sample_grid(const ntc_material& M, int j, int k,
   if (taps_out) *taps_out = t;
 #pragma unroll
   for (int ch = 0; ch < kMaxGridCh; ++ch) gs.acc[ch] = 0.f;
+  if (k == 0 && M.vq_books > 0) {
+#pragma unroll
+    for (int tp = 0; tp < 4; ++tp) {
+      float v[kMaxGridCh];
+      vq_cell(M, j, t.cell[tp], v);
+#pragma unroll
+      for (int ch = 0; ch < kMaxGridCh; ++ch)
+        if (ch < c) gs.acc[ch] = fmaf(t.w[tp], v[ch], gs.acc[ch]);
+    }
+    return;
+  }
   if (M.encoding == NTC_GRID_PACKED) {
     const int bits = k ? M.bits1 : M.bits0;
     const int off = (1 << (bits - 1)) - 1;
@@ -258,6 +284,13 @@ __device__ __forceinline__ void sample_grid(const ntc_material& M, int j, int k,
 __device__ __forceinline__ float grid_value(const ntc_material& M, int j, int k, int cell, int ch,
                                             bool noise, uint64_t nkey) {
   const ntc_level& L = M.lv[j];
+  if (k == 0 && M.vq_books > 0) {
+    const uint8_t* ib = static_cast<const uint8_t*>(L.grid0) + (size_t)cell * M.vq_books;
+    float v = 0.f;
+    for (int b = 0; b < M.vq_books; ++b)
+      v += __ldg(M.codebook0 + ((size_t)b * 256 + ib[b]) * M.c0 + ch);
+    return v;
+  }
   const int c = k ? M.c1 : M.c0;
   const float q = k ? M.q1 : M.q0;
   if (M.encoding == NTC_GRID_PACKED) {

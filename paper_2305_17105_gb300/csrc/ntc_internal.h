@@ -96,6 +96,8 @@ cudaError_t launch_quantize_pack(const float* values, int64_t cells, int c, int 
                                  uint8_t* packed, float* snapped, cudaStream_t s);
 cudaError_t launch_unpack(const uint8_t* packed, int64_t cells, int c, int bits, float q,
                           int32_t* idx, float* values, cudaStream_t s);
+cudaError_t launch_vq_assign(const float* values, int64_t cells, int c0, const float* books, int nb,
+                             uint8_t* idx, cudaStream_t s);
 cudaError_t launch_sample_batch(uint64_t seed, int64_t step, int64_t batch, int w, int h, int mips,
                                 int crops, int32_t* xym, cudaStream_t s);
 cudaError_t launch_sample_features(const ntc_material& m, const float* uvl, int64_t n, float* rows,

@@ -74,7 +74,7 @@ struct Plan {
     }
     // the fast layout reads whole 32-bit cell words: 4-bit cells of 4 or 8 bytes
     fast = taps_ok && packed && bits0 == 4 && bits1 == 4 && (cb0 == 4 || cb0 == 8) &&
-           (cb1 == 4 || cb1 == 8) && !(f8 && learned);
+           (cb1 == 4 || cb1 == 8) && !(f8 && learned) && M.vq_books == 0;
     eo0 = eo1 = t0 = t1 = 0;
     if (fast) {
       // word 0 holds 5-8 channels; word 1 (8-byte cells) the other c - 8
@@ -695,7 +695,17 @@ __device__ __forceinline__ void generic_grid(const ntc_material& M, const MipTab
 #pragma unroll 1
     for (int tp = 0; tp < 4; ++tp) {
       float acc[kMaxGridCh];
-      if (M.encoding == NTC_GRID_PACKED) {
+      if (M.vq_books > 0) {
+        const int cell = r.valid ? t.cell[tp] : 0;
+#pragma unroll
+        for (int ch = 0; ch < kMaxGridCh; ++ch) acc[ch] = 0.f;
+        for (int b = 0; b < M.vq_books; ++b) {
+          const float* e = M.codebook0 + ((size_t)b * 256 + base[(size_t)cell * M.vq_books + b]) * c;
+#pragma unroll
+          for (int ch = 0; ch < kMaxGridCh; ++ch)
+            if (ch < c) acc[ch] += __ldg(e + ch);
+        }
+      } else if (M.encoding == NTC_GRID_PACKED) {
         const int off = (1 << (M.bits0 - 1)) - 1;
         const Cell cl = load_cell(base, r.valid ? t.cell[tp] : 0, P.cb0);
 #pragma unroll
@@ -725,7 +735,25 @@ __device__ __forceinline__ void generic_grid(const ntc_material& M, const MipTab
     if (k) taps_of(r.x, r.y, tb->sx1[m], tb->sy1[m], tb->g1w[m], tb->g1h[m], t);
     else taps_of(r.x, r.y, tb->sx0[m], tb->sy0[m], tb->g0w[m], tb->g0h[m], t);
     const uint8_t* base = k ? tb->grid1[m] : tb->grid0[m];
-    if (M.encoding == NTC_GRID_PACKED) {
+    if (k == 0 && M.vq_books > 0) {
+      // vector-quantised G0: each tap's cell is the sum of its codebook entries
+#pragma unroll
+      for (int tp = 0; tp < 4; ++tp) {
+        float v[kMaxGridCh];
+#pragma unroll
+        for (int ch = 0; ch < kMaxGridCh; ++ch) v[ch] = 0.f;
+        for (int b = 0; b < M.vq_books; ++b) {
+          const float* e =
+              M.codebook0 + ((size_t)b * 256 + base[(size_t)t.cell[tp] * M.vq_books + b]) * c;
+#pragma unroll
+          for (int ch = 0; ch < kMaxGridCh; ++ch)
+            if (ch < c) v[ch] += __ldg(e + ch);
+        }
+#pragma unroll
+        for (int ch = 0; ch < kMaxGridCh; ++ch)
+          if (ch < c) acc[ch] = fmaf(t.w[tp], v[ch], acc[ch]);
+      }
+    } else if (M.encoding == NTC_GRID_PACKED) {
       const int bits = k ? M.bits1 : M.bits0;
       const int off = (1 << (bits - 1)) - 1;
       const int cb = k ? P.cb1 : P.cb0;

@@ -111,6 +111,10 @@ def test_valid_material_with_zero_queries_is_a_noop(L):
     (dict(hidden_layers=3), ntc.ERR_ARG),                  # w_h3 / b_h3 missing
     (dict(hidden_layers=3, w_h3=0x20000, b_h3=0x20000, precision=ntc.PREC_F8, k_in=64,
           scale=0x20000), ntc.ERR_UNSUPPORTED),
+    (dict(vq_books=5, codebook0=0x20000), ntc.ERR_ARG),
+    (dict(vq_books=2), ntc.ERR_ARG),                       # codebook missing
+    (dict(vq_books=2, codebook0=0x20000, precision=ntc.PREC_F8, k_in=64, scale=0x20000),
+     ntc.ERR_UNSUPPORTED),
 ])
 def test_material_validation(L, kw, code):
     assert _decode_rc(L, _fake_material(**kw), n=5) == code

@@ -204,6 +204,43 @@ def test_decode_f8_structure():
     assert 0 < np.abs(f8 - ident).max() < 0.1
 
 
+def test_vq_reconstruct_by_hand():
+    """A vector-quantised cell is the sum of the entries its indices select."""
+    cb = np.zeros((2, 256, 2))
+    cb[0, 3] = [1.0, 2.0]
+    cb[1, 7] = [0.25, -0.5]
+    cb[1, 0] = [10.0, 10.0]
+    idx = np.array([[[3, 7], [3, 0]]], np.uint8)
+    got = oracle.vq_reconstruct(idx, cb)
+    assert got.shape == (1, 2, 2)
+    assert np.array_equal(got[0, 0], [1.25, 1.5]) and np.array_equal(got[0, 1], [11.0, 12.0])
+
+
+def test_vq_assign_single_book_is_nearest_entry():
+    """One codebook: the nearest entry (brute force in float64 on points far
+    from any tie)."""
+    rng = np.random.default_rng(5)
+    cb = rng.integers(-20, 20, size=(1, 256, 4)).astype(np.float32) * 4.0
+    cb = np.unique(cb[0], axis=0)[None, :256]
+    if cb.shape[1] < 256:
+        cb = np.concatenate([cb, np.full((1, 256 - cb.shape[1], 4), 1e4, np.float32)], 1)
+    pick = rng.integers(0, 256, 500)
+    vals = cb[0, pick] + rng.uniform(-0.5, 0.5, (500, 4)).astype(np.float32)
+    want = np.argmin(((vals[:, None, :].astype(np.float64) - cb[0][None]) ** 2).sum(-1), 1)
+    assert np.array_equal(oracle.vq_assign(vals, cb)[:, 0], want)
+
+
+def test_vq_assign_residual_and_ties_by_hand():
+    """Two books on a 1-D example: 11.2 -> 10 (book 0) then 1 (book 1);
+    equal entries resolve to the lowest index."""
+    cb = np.full((2, 256, 1), 1e3, np.float32)
+    cb[0, 0], cb[0, 5] = 0.0, 10.0
+    cb[1, 0], cb[1, 1], cb[1, 2] = 0.0, 1.0, -1.0
+    cb[1, 9] = 1.0                         # a duplicate of entry 1
+    idx = oracle.vq_assign(np.array([[11.2], [9.1], [0.2]], np.float32), cb)
+    assert idx.tolist() == [[5, 1], [5, 2], [0, 0]]
+
+
 # ----------------------------------------------------------- quantisation ---
 @pytest.mark.parametrize("bits", [1, 2, 4, 8])
 def test_quantizer_levels_and_roundtrip(bits):
