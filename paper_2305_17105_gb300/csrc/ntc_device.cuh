@@ -205,9 +205,18 @@ __device__ __forceinline__ void vq_cell(const ntc_material& M, int j, int cell,
   for (int ch = 0; ch < kMaxGridCh; ++ch) v[ch] = 0.f;
   for (int b = 0; b < M.vq_books; ++b) {
     const float* e = M.codebook0 + ((size_t)b * 256 + ib[b]) * M.c0;
+    if ((M.c0 & 3) == 0) {  // rows of 4k values: float4 reads
 #pragma unroll
-    for (int ch = 0; ch < kMaxGridCh; ++ch)
-      if (ch < M.c0) v[ch] += __ldg(e + ch);
+      for (int q4 = 0; q4 < kMaxGridCh / 4; ++q4)
+        if (4 * q4 < M.c0) {
+          const float4 f = __ldg(reinterpret_cast<const float4*>(e) + q4);
+          v[4 * q4] += f.x; v[4 * q4 + 1] += f.y; v[4 * q4 + 2] += f.z; v[4 * q4 + 3] += f.w;
+        }
+    } else {
+#pragma unroll
+      for (int ch = 0; ch < kMaxGridCh; ++ch)
+        if (ch < M.c0) v[ch] += __ldg(e + ch);
+    }
   }
 }
 

@@ -736,7 +736,8 @@ __device__ __forceinline__ void generic_grid(const ntc_material& M, const MipTab
     else taps_of(r.x, r.y, tb->sx0[m], tb->sy0[m], tb->g0w[m], tb->g0h[m], t);
     const uint8_t* base = k ? tb->grid1[m] : tb->grid0[m];
     if (k == 0 && M.vq_books > 0) {
-      // vector-quantised G0: each tap's cell is the sum of its codebook entries
+      // vector-quantised G0: each tap's cell is the sum of its codebook
+      // entries (rows of 4k values read as float4)
 #pragma unroll
       for (int tp = 0; tp < 4; ++tp) {
         float v[kMaxGridCh];
@@ -745,9 +746,18 @@ __device__ __forceinline__ void generic_grid(const ntc_material& M, const MipTab
         for (int b = 0; b < M.vq_books; ++b) {
           const float* e =
               M.codebook0 + ((size_t)b * 256 + base[(size_t)t.cell[tp] * M.vq_books + b]) * c;
+          if ((c & 3) == 0) {
 #pragma unroll
-          for (int ch = 0; ch < kMaxGridCh; ++ch)
-            if (ch < c) v[ch] += __ldg(e + ch);
+            for (int q4 = 0; q4 < kMaxGridCh / 4; ++q4)
+              if (4 * q4 < c) {
+                const float4 f = __ldg(reinterpret_cast<const float4*>(e) + q4);
+                v[4 * q4] += f.x; v[4 * q4 + 1] += f.y; v[4 * q4 + 2] += f.z; v[4 * q4 + 3] += f.w;
+              }
+          } else {
+#pragma unroll
+            for (int ch = 0; ch < kMaxGridCh; ++ch)
+              if (ch < c) v[ch] += __ldg(e + ch);
+          }
         }
 #pragma unroll
         for (int ch = 0; ch < kMaxGridCh; ++ch)
