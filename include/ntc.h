@@ -205,6 +205,14 @@ const char* ntc_last_error(void);
  * incomplete.  reset != 0 clears the word.  The only call that synchronises. */
 int ntc_device_status(int32_t reset);
 
+/* Failure-detection self-test (no counterpart in the paper): enqueues a kernel
+ * whose bounded wait cannot complete (an mbarrier nothing arrives at, with
+ * the wait the tensor-core kernels use); after `limit` suspended tries of up
+ * to ~10 us each it records NTC_ERR_TIMEOUT in the device status word --
+ * as a kernel whose MMA completion never arrived would -- and returns, the
+ * context intact.  limit in 1..2^20; read the result with ntc_device_status. */
+int ntc_selftest_wait(int32_t limit, void* stream);
+
 /* Bytes of one packed grid cell for c features of `bits` bits: c*bits bits
  * rounded up to a power-of-two number of bytes.  Channel ch occupies bits
  * [ch*bits, (ch+1)*bits) counting from bit 0 of byte 0.  0 on bad input. */

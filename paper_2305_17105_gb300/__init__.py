@@ -100,6 +100,7 @@ SIGNATURES = {
     "ntc_sample_crops": (C.c_int, [_U64, _I64, _I64, _I32, _I32, _I32, _P, _P]),
     "ntc_sample_features": (C.c_int, [_P, _P, _I64, _P, _I32, _U64, _I64, _P]),
     "ntc_device_status": (C.c_int, [_I32]),
+    "ntc_selftest_wait": (C.c_int, [_I32, _P]),
     "ntc_batch_workspace_bytes": (C.c_size_t, []),
     "ntc_decode_host": (C.c_int, [_P, _P, _I64, _P, _I32, _I32, _I32, _U64, _I64, _P, C.c_size_t, _P]),
     "ntc_decode_host_workspace_bytes": (C.c_size_t, [_I32, _I32, _I64]),
@@ -165,6 +166,12 @@ def ntc_device_status(reset: bool = True) -> int:
     """Synchronise the device and return (and clear) the status word that
     bounded device-side waits set on timeout (OK or ERR_TIMEOUT)."""
     return int(lib().ntc_device_status(1 if reset else 0))
+
+
+def ntc_selftest_wait(limit: int = 1000, stream=None) -> None:
+    """Enqueue the failure-detection self-test: a bounded wait that runs out
+    and records ERR_TIMEOUT in the status word (read by ntc_device_status)."""
+    _call("ntc_selftest_wait", limit, _stream(stream))
 
 
 def version() -> str:

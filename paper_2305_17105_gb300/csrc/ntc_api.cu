@@ -191,6 +191,12 @@ int ntc_device_status(int32_t reset) {
   return v == 0 ? NTC_OK : fail(v, "device status %d", v);
 }
 
+int ntc_selftest_wait(int32_t limit, void* stream) {
+  if (limit < 1 || limit > (1 << 20)) return fail(NTC_ERR_ARG, "limit %d outside 1..2^20", limit);
+  return cuda_status(ntc::launch_selftest_wait((uint32_t)limit, static_cast<cudaStream_t>(stream)),
+                     "selftest_wait");
+}
+
 int32_t ntc_cell_bytes(int32_t c, int32_t bits) {
   if (c < 1 || c > 64 || (bits != 1 && bits != 2 && bits != 4 && bits != 8) || c * bits > 128)
     return 0;

@@ -127,6 +127,7 @@ cudaError_t launch_decode_ws_batched(const BatchHeader* dev, int64_t total_tiles
                                      uint32_t plan_bytes, int cls, const float* uvl, void* out,
                                      int out_dtype, int filter, cudaStream_t s);
 bool fast_layout_ok(const ntc_material& m);
+cudaError_t launch_selftest_wait(uint32_t limit, cudaStream_t s);
 // Warp-specialised tensor-core decode (FP16), fast 4-bit layout or generic.
 cudaError_t launch_decode_ws(const ntc_material& m, const float* uvl, int64_t n, void* out,
                              int out_dtype, int filter, uint64_t jkey, cudaStream_t s, bool fast);

@@ -243,6 +243,23 @@ cudaError_t launch_shape(const ntc_material& m, const float* uvl, int64_t n, voi
 
 }  // namespace
 
+// Failure-detection self-test: one thread waits, with the tensor-core
+// kernels' bounded wait, on an mbarrier that nothing arrives at; when the
+// limit runs out it records NTC_ERR_TIMEOUT in the status word and returns.
+__global__ void selftest_wait_kernel(uint32_t limit, int* status) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&bar, 1);
+    tc::fence_mbar_init();
+    if (!tc::mbar_wait(&bar, 0, limit)) atomicExch(status, NTC_ERR_TIMEOUT);
+  }
+}
+
+cudaError_t launch_selftest_wait(uint32_t limit, cudaStream_t s) {
+  selftest_wait_kernel<<<1, 32, 0, s>>>(limit, status_word());
+  return cudaGetLastError();
+}
+
 // The fast layout's exactness conditions: every grid/mip size ratio of every
 // mip is a multiple of 1/8 (taps on the 1/16 lattice) and the bin widths are
 // powers of two in [2^-6, 2^6] (the half constants of ylerp_of exact).

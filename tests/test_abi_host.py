@@ -152,6 +152,11 @@ def test_decode_host_validation(L):
     assert rc(args(dt=7)) == ntc.ERR_ARG
 
 
+def test_selftest_wait_validation(L):
+    assert L.ntc_selftest_wait(0, None) == ntc.ERR_ARG
+    assert L.ntc_selftest_wait((1 << 20) + 1, None) == ntc.ERR_ARG
+
+
 def test_pointer_validation(L):
     assert _decode_rc(L, None, n=5) == ntc.ERR_ARG
     assert _decode_rc(L, _fake_material(), n=5, uvl=0x30004) == ntc.ERR_ALIGN
