@@ -480,6 +480,57 @@ def vq_eval(ntc, q_dev, stream):
             "status": ntc.ntc_device_status()}
 
 
+def sq_vq_train_eval(ntc, chain, batch, seed, stream, steps=1000):
+    """The appendix comparison of scalar and vector quantisation on the
+    synthetic training material (2048^2 x 12): G0 at 16 bits per cell as
+    SQ-8 (8 channels x 2 bits) or VQ-8 (two 256-entry codebooks of 8 values,
+    VQ-VAE terms, commitment 0.25), G1 256^2 x 12 at 4 bits, MLP with 48
+    inputs, FP16 step, `steps` steps of `batch` texels from the
+    same initialisation; PSNR of mip 0 of the export (decoded in FP16)
+    against the 8-bit reference, and the training time."""
+    import torch
+    side, c, c0, c1, k = TRN_SIDE, TRN_C, 8, 12, 48
+    rng = np.random.default_rng(1203)
+    levels = ntc.pyramid(side, side)
+    ys, xs = np.meshgrid(np.arange(side), np.arange(side), indexing="ij")
+    t0 = torch.from_numpy(np.stack([(xs + 0.5) / side, (ys + 0.5) / side, np.zeros_like(xs, float)],
+                                   -1).reshape(-1, 3).astype(np.float32)).cuda()
+    refm = torch.from_numpy(chain[0].reshape(-1, c).astype(np.float32) / 255.0).cuda()
+    g1 = [gen.uniform_grid_values((h1, w1, c1), -7 / 16, 8 / 16, rng) for _, (w1, h1) in levels]
+    w = gen.random_mlp(k, 64, c, seed=1204, n_used=c0 + c1 + 13)
+    cb = rng.uniform(-0.5, 0.5, (2, 256, c0)).astype(np.float32)
+    cb[1] *= 0.25
+    res = {"workload": f"{side}^2x{c}, G0 at 16 bits per cell (SQ-8: 8 x 2 bits; VQ-8: 2 x 256 x 8 "
+                       f"codebooks) + G1 at 4 bits, MLP 48-64-64-{c}, {steps} steps of {batch} "
+                       "texels, FP16 step", "steps": steps}
+    target = ntc.Target(chain)
+    for name in ("sq", "vq"):
+        if name == "sq":  # 2-bit levels k Q, Q = 1/2: clamp range [-3/4, 1]
+            g0 = [gen.uniform_grid_values((h0, w0, c0), -0.75, 1.0, rng) for (w0, h0), _ in levels]
+            tr = ntc.Trainer(side, side, c, c0, c1, 2, 4, 0.5, 1 / 16, g0, g1, w[0::2], w[1::2], k,
+                             ntc.PREC_F16, total_steps=steps)
+        else:
+            g0 = [gen.uniform_grid_values((h0, w0, c0), -0.5, 0.5, rng) for (w0, h0), _ in levels]
+            tr = ntc.Trainer(side, side, c, c0, c1, 8, 4, 1 / 16, 1 / 16, g0, g1, w[0::2], w[1::2],
+                             k, ntc.PREC_F16, total_steps=steps, codebook0=cb, vq_beta=0.25)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            ntc.ntc_train_step(tr, target, batch, seed)
+        b.record(stream)
+        torch.cuda.synchronize()
+        dec = ntc.ntc_decode(tr.export(ntc.PREC_F16), t0)
+        mse = float(((dec - refm) ** 2).mean())
+        res[f"train_s_{name}"] = a.elapsed_time(b) / 1e3
+        res[f"psnr_db_{name}"] = 10 * math.log10(1.0 / mse)
+        res[f"status_{name}"] = ntc.ntc_device_status()
+        del tr
+    res["psnr_delta_db_vq_minus_sq"] = res["psnr_db_vq"] - res["psnr_db_sq"]
+    res["train_time_ratio_vq_over_sq"] = res["train_s_vq"] / res["train_s_sq"]
+    return res
+
+
 # ----------------------------------------------------------------------------
 # Many materials: batched decode launch, graph-captured training of all of them
 # ----------------------------------------------------------------------------
@@ -923,6 +974,13 @@ def main():
         except Exception as e:  # reported, never fatal to the headline line
             vq = {"error": f"{type(e).__name__}: {e}"[:300]}
 
+    sqvq = None
+    if not args.no_extras:
+        try:
+            sqvq = sq_vq_train_eval(ntc, chain, args.batch, seed, stream)
+        except Exception as e:  # reported, never fatal to the headline line
+            sqvq = {"error": f"{type(e).__name__}: {e}"[:300]}
+
     equal = None
     if not args.no_extras and not args.no_fp32_compare:
         try:
@@ -954,7 +1012,7 @@ def main():
         "decode_ms": statistics.median(dec_ms), "train_ms": statistics.median(trn_ms),
         "roofline": roof, "train_roofline": train_roof, "tuning": tuning, "e2e": e2e, "fp32_path": fp32, "cpu_baseline": cpu,
         "render": render, "multi_material": multi, "paper_form": paper_form, "train_crops": crops,
-        "equal_psnr_training": equal, "vq_decode": vq,
+        "equal_psnr_training": equal, "vq_decode": vq, "sq_vs_vq_training": sqvq,
         "gpu_launches": kernels_per_step * args.steps,
         "clocks": clk.summary(), "wall_s": t_wall,
     }

@@ -139,7 +139,10 @@ typedef struct {
                             every level holds uint8 [g0_h][g0_w][vq_books] indices, index
                             b into codebook b of 256 entries of c0 values, and a cell's
                             features are the sum of its vq_books entries (bits0 is
-                            unused).  Decode only (FP32 and FP16 forms, no noise) */
+                            unused).  Decode: FP32 and FP16 forms, no noise.
+                            Training form (encoding NTC_GRID_F32, ntc_train_step
+                            only): grid0 holds the continuous latents, quantised by
+                            every step (see ntc_train_step) */
   const float* codebook0; /* [vq_books][256][c0] float32, device (vq_books > 0) */
 } ntc_material;
 
@@ -184,6 +187,10 @@ typedef struct {
   float* w_master_h3;   /* FP32 master of the third hidden layer (hidden_layers == 3),
                            inside params like w_master[]; its bias is the material's
                            b_h3, also inside params */
+  uint8_t* vq_idx;      /* vector-quantised G0 (material vq_books > 0): scratch of
+                           sum over levels of g0_w g0_h vq_books bytes (the step's
+                           indices); needs `noisy`.  NULL otherwise */
+  float vq_beta;        /* commitment weight of the vector-quantised G0 */
 } ntc_trainer;
 
 /* Reference texture set: the 8-bit mip chain, texel values q/255. */
@@ -300,7 +307,16 @@ int ntc_backward(const ntc_material* m, const float* uvl, int64_t n, const float
  * so the call is CUDA-graph capturable and replays identically.
  * flags: NTC_FLAG_FREEZE_GRIDS (no noise, grids neither differentiated nor
  * updated), NTC_FLAG_NO_NOISE, NTC_FLAG_SIMT, NTC_FLAG_GRAD_ONLY,
- * NTC_FLAG_CROPS (crop sampler; ignored when uvl_or_null gives the texels).  FP16
+ * NTC_FLAG_CROPS (crop sampler; ignored when uvl_or_null gives the texels).
+ * Vector-quantised G0 (vq_books > 0, training form): each step assigns every
+ * G0 latent row z to codebook entries by greedy residual search (as
+ * ntc_vq_assign), trains the decoder on the quantised rows q (sum of the
+ * entries; G1 keeps its noise), passes q's gradient straight through to z,
+ * and adds the codebook loss (1/N) sum ||sg(r_b) - e_b||^2 and the
+ * commitment loss vq_beta (1/N) sum ||z - sg(q)||^2 (r_b: what books
+ * 0..b-1 leave of z; N: every G0 latent value) to the gradients of the
+ * codebooks (inside params, Adam with lr_grid, unclamped) and of z
+ * (unclamped); loss_out stays the L2 loss.  FP16
  * weights train on the tensor cores (tcgen05; ReLU or hardGELU, sigmoid or
  * identity output, bilinear or learned G0); FP32 weights or NTC_FLAG_SIMT on
  * the FP32 CUDA cores (k_in <= 64). */

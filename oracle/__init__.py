@@ -59,6 +59,7 @@ class _Model(C.Structure):
         ("w1", C.c_void_p), ("b1", C.c_void_p), ("w2", C.c_void_p), ("b2", C.c_void_p),
         ("w3", C.c_void_p), ("b3", C.c_void_p), ("interp0", C.c_int),
         ("hidden_layers", C.c_int), ("wm", C.c_void_p), ("bm", C.c_void_p),
+        ("vq_g0", C.c_int),
     ]
 
 
@@ -254,6 +255,36 @@ def vq_assign(values: np.ndarray, codebooks: np.ndarray) -> np.ndarray:
     return idx
 
 
+def vq_train_terms(z_levels, codebooks, beta: float):
+    """The vector-quantisation terms of one training step of a
+    vector-quantised G0 (VQ-VAE, van den Oord et al. 2017, as the paper's
+    comparison cites): per level, indices of the latent rows z by greedy
+    residual search (``vq_assign``), q = the sum of the selected entries;
+    codebook loss (1/N) sum_cells sum_b ||r_b - e_b||^2 with the residuals
+    r_b held fixed, and commitment loss beta (1/N) sum ||z - q||^2 with q
+    held fixed, N = every G0 latent value.  Returns (indices, q, dL/dz of the
+    commitment term, dL/dcodebooks of the codebook term) per level / total,
+    float64."""
+    cb32 = np.asarray(codebooks, np.float32)
+    cb = cb32.astype(np.float64)
+    n = sum(np.asarray(z).size for z in z_levels)
+    idx_l, q_l, dz_l = [], [], []
+    d_cb = np.zeros_like(cb)
+    for z in z_levels:
+        zf = np.asarray(z, np.float32).reshape(-1, cb.shape[2])
+        idx = vq_assign(zf, cb32)
+        r = zf.astype(np.float64)
+        for b in range(cb.shape[0]):
+            e = cb[b][idx[:, b].astype(np.int64)]
+            np.add.at(d_cb[b], idx[:, b].astype(np.int64), 2.0 / n * (e - r))
+            r = r - e
+        q = vq_reconstruct(idx, cb32)
+        idx_l.append(idx.reshape(np.asarray(z).shape[:-1] + (cb.shape[0],)))
+        q_l.append(q.reshape(np.asarray(z).shape))
+        dz_l.append((2.0 * beta / n * (zf.astype(np.float64) - q)).reshape(np.asarray(z).shape))
+    return idx_l, q_l, dz_l, d_cb
+
+
 def activation(act: int, z: float) -> float:
     return float(lib().or_activation(act, z))
 
@@ -282,7 +313,7 @@ class Model:
     """
 
     def __init__(self, width, height, channels, c0, c1, n0, n1, q0, q1, grids0, grids1,
-                 weights, k_in, hidden=64, act=0, out_act=0, interp0=0):
+                 weights, k_in, hidden=64, act=0, out_act=0, interp0=0, vq_g0=False):
         self.width, self.height, self.channels = width, height, channels
         self.mips = mips(width, height)
         self.levels = len(grids0)
@@ -301,6 +332,7 @@ class Model:
             s.grid1[j] = self.grids1[j].ctypes.data
         s.k_in, s.hidden, s.act, s.out_act = k_in, hidden, act, out_act
         self.interp0 = s.interp0 = interp0
+        self.vq_g0 = s.vq_g0 = int(bool(vq_g0))
         w = self.weights
         assert len(w) in (6, 8)
         self.hidden_layers = s.hidden_layers = 2 if len(w) == 6 else 3

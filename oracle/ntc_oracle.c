@@ -260,7 +260,9 @@ static double grid_value(const or_model* md, int j, int k, int64_t cell, int ch,
   const double* g = k ? md->grid1[j] : md->grid0[j];
   int c = k ? md->c1 : md->c0;
   double v = g[cell * c + ch];
-  if (nz && nz->enabled) v += or_noise_value(nz->seed, nz->step, j, k, cell, ch, c, k ? md->q1 : md->q0);
+  /* a vector-quantised G0 is trained through its quantised values: no noise */
+  if (nz && nz->enabled && !(k == 0 && md->vq_g0))
+    v += or_noise_value(nz->seed, nz->step, j, k, cell, ch, c, k ? md->q1 : md->q0);
   return v;
 }
 

@@ -41,6 +41,8 @@ typedef struct {
                                "three remaining layers"): a third hidden layer
                                wm, bm between w2 and the output layer w3 */
   const double *wm, *bm;    /* [hidden][hidden], [hidden] (hidden_layers == 3) */
+  int vq_g0;                /* G0 holds vector-quantised values: the training noise
+                               applies to G1 only */
 } or_model;
 
 /* Simulated-quantisation noise switch (Sec. 4.2). */

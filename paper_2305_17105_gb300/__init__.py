@@ -70,7 +70,8 @@ class ntc_trainer(C.Structure):
                 ("grad", C.c_void_p), ("n_params", C.c_int64), ("w_master", C.c_void_p * 3),
                 ("step", C.c_void_p), ("total_steps", C.c_int64), ("lr_grid", C.c_float),
                 ("lr_mlp", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float),
-                ("eps", C.c_float), ("noisy", C.c_void_p), ("w_master_h3", C.c_void_p)]
+                ("eps", C.c_float), ("noisy", C.c_void_p), ("w_master_h3", C.c_void_p),
+                ("vq_idx", C.c_void_p), ("vq_beta", C.c_float)]
 
 
 class ntc_batch(C.Structure):
@@ -462,13 +463,17 @@ class Trainer:
     def __init__(self, width, height, channels, c0, c1, bits0, bits1, q0, q1, grids0, grids1,
                  weights, biases, k_in, precision=PREC_F32, act=ACT_RELU, out_act=OUT_SIGMOID,
                  total_steps=1000, lr_grid=0.01, lr_mlp=0.005, betas=(0.9, 0.999), eps=1e-8,
-                 device="cuda", noisy_scratch=True, interp0=INTERP_BILINEAR):
+                 device="cuda", noisy_scratch=True, interp0=INTERP_BILINEAR, codebook0=None,
+                 vq_beta=0.25):
         tensors = [np.asarray(g, np.float32) for g in grids0] + \
                   [np.asarray(g, np.float32) for g in grids1]
         mlp = []
         for w, b in zip(weights, biases):
             mlp += [np.asarray(w, np.float32), np.asarray(b, np.float32)]
         tensors += mlp
+        vq = codebook0 is not None
+        if vq:  # vector-quantised G0: grids0 are the continuous latents, codebooks train too
+            tensors.append(np.asarray(codebook0, np.float32))
         offs, n = [], 0
         for t in tensors:
             offs.append(n)
@@ -486,6 +491,7 @@ class Trainer:
         self.loss = torch.zeros(1, dtype=torch.float32, device=device)
         views = [self.params[o:o + t.size].view(t.shape) for o, t in zip(offs, tensors)]
         L = len(grids0)
+        self.codebook = views.pop() if vq else None
         g0, g1, rest = views[:L], views[L:2 * L], views[2 * L:]
         self.w_master = rest[0::2]   # layer order: 3 or 4 layers
         self.b = rest[1::2]
@@ -498,7 +504,10 @@ class Trainer:
             raise ValueError("training supports FP32 and FP16 weights")
         self.material = Material(width, height, channels, c0, c1, bits0, bits1, q0, q1, g0, g1,
                                  self.w_compute, self.b, k_in, precision, act, out_act,
-                                 interp0=interp0)
+                                 interp0=interp0, codebook0=self.codebook)
+        self.vq_beta = vq_beta
+        self.vq_idx = (torch.empty(sum(g.shape[0] * g.shape[1] for g in grids0) * codebook0.shape[0],
+                                   dtype=torch.uint8, device=device) if vq else None)
         self.total_steps, self.lr_grid, self.lr_mlp = total_steps, lr_grid, lr_mlp
         self.betas, self.eps = betas, eps
 
@@ -508,8 +517,12 @@ class Trainer:
         and packed by ``ntc_quantize_pack``; weights in the requested
         precision (FP16 or FP32) from the FP32 masters; biases copied."""
         m = self.material
-        g0 = [ntc_quantize_pack(g.contiguous(), m.c0, m.bits0, m.q0, stream=stream).view(
-            g.shape[0], g.shape[1], -1) for g in m.grids0]
+        if self.codebook is not None:  # indices of the final latents, the trained codebooks
+            g0 = [ntc_vq_assign(g.reshape(-1, m.c0), self.codebook, stream=stream).view(
+                g.shape[0], g.shape[1], -1) for g in m.grids0]
+        else:
+            g0 = [ntc_quantize_pack(g.contiguous(), m.c0, m.bits0, m.q0, stream=stream).view(
+                g.shape[0], g.shape[1], -1) for g in m.grids0]
         g1 = [ntc_quantize_pack(g.contiguous(), m.c1, m.bits1, m.q1, stream=stream).view(
             g.shape[0], g.shape[1], -1) for g in m.grids1]
         if precision == PREC_F16:
@@ -520,7 +533,8 @@ class Trainer:
             raise ValueError("export writes FP16 or FP32 weights")
         return Material(m.width, m.height, m.channels, m.c0, m.c1, m.bits0, m.bits1, m.q0, m.q1,
                         g0, g1, w, [b.clone() for b in self.b], m.k_in, precision, m.act,
-                        m.out_act, interp0=m.interp0)
+                        m.out_act, interp0=m.interp0,
+                        codebook0=self.codebook.clone() if self.codebook is not None else None)
 
     @property
     def struct(self) -> ntc_trainer:
@@ -538,6 +552,8 @@ class Trainer:
         t.beta1, t.beta2 = self.betas
         t.eps = self.eps
         t.noisy = self.noisy.data_ptr() if self.noisy is not None else None
+        t.vq_idx = self.vq_idx.data_ptr() if self.vq_idx is not None else None
+        t.vq_beta = self.vq_beta
         return t
 
 

@@ -251,6 +251,54 @@ cudaError_t launch_unpack(const uint8_t* packed, int64_t cells, int c, int bits,
   return cudaGetLastError();
 }
 
+// Index of the entry of one codebook (256 x c0 floats in shared memory)
+// nearest to r: squared distance in FP32, the channels summed in order
+// without fused multiply-add, ties to the lowest index.  Rows of 4k values
+// are read as float4 (same arithmetic).
+__device__ __forceinline__ int vq_nearest(const float* book, const float (&r)[kMaxGridCh], int c0) {
+  float best = __int_as_float(0x7f800000);  // +inf
+  int kb = 0;
+  if ((c0 & 3) == 0) {
+#pragma unroll 1
+    for (int k = 0; k < 256; ++k) {
+      const float4* e4 = reinterpret_cast<const float4*>(book + k * c0);
+      float d = 0.f;
+#pragma unroll
+      for (int q4 = 0; q4 < kMaxGridCh / 4; ++q4)
+        if (4 * q4 < c0) {
+          const float4 e = e4[q4];
+          const float ev[4] = {e.x, e.y, e.z, e.w};
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const float df = __fsub_rn(r[4 * q4 + i], ev[i]);
+            d = __fadd_rn(d, __fmul_rn(df, df));
+          }
+        }
+      if (d < best) {
+        best = d;
+        kb = k;
+      }
+    }
+  } else {
+#pragma unroll 1
+    for (int k = 0; k < 256; ++k) {
+      const float* e = book + k * c0;
+      float d = 0.f;
+#pragma unroll
+      for (int ch = 0; ch < kMaxGridCh; ++ch)
+        if (ch < c0) {
+          const float df = __fsub_rn(r[ch], e[ch]);
+          d = __fadd_rn(d, __fmul_rn(df, df));
+        }
+      if (d < best) {
+        best = d;
+        kb = k;
+      }
+    }
+  }
+  return kb;
+}
+
 // Greedy residual vector quantisation of one row per thread against the
 // codebooks staged in shared memory: FP32 squared distances with the channels
 // summed in order and no fused multiply-add, ties to the lowest index.
@@ -267,23 +315,7 @@ __global__ void __launch_bounds__(256) vq_assign_kernel(const float* __restrict_
 #pragma unroll
     for (int ch = 0; ch < kMaxGridCh; ++ch) r[ch] = ch < c0 ? values[cell * c0 + ch] : 0.f;
     for (int b = 0; b < nb; ++b) {
-      float best = __int_as_float(0x7f800000);  // +inf
-      int kb = 0;
-#pragma unroll 1
-      for (int k = 0; k < 256; ++k) {
-        const float* e = cb + (b * 256 + k) * c0;
-        float d = 0.f;
-#pragma unroll
-        for (int ch = 0; ch < kMaxGridCh; ++ch)
-          if (ch < c0) {
-            const float df = __fsub_rn(r[ch], e[ch]);
-            d = __fadd_rn(d, __fmul_rn(df, df));
-          }
-        if (d < best) {
-          best = d;
-          kb = k;
-        }
-      }
+      const int kb = vq_nearest(cb + b * 256 * c0, r, c0);
       idx[cell * nb + b] = (uint8_t)kb;
       const float* e = cb + (b * 256 + kb) * c0;
 #pragma unroll
@@ -293,6 +325,81 @@ __global__ void __launch_bounds__(256) vq_assign_kernel(const float* __restrict_
   }
 }
 
+// One training step's vector quantisation of a G0 level (VQ-VAE terms): per
+// latent row z, greedy residual assignment (as vq_assign_kernel); q, the sum
+// of the selected entries, goes to the scratch grid the fused step reads;
+// the codebook loss (1/N) sum ||sg(r_b) - e_b||^2 gives dE_b[k] += scale
+// (e_b[k] - r_b) and the commitment loss beta (1/N) sum ||z - sg(q)||^2
+// gives dz += scale beta (z - q), scale = 2 / N.  dE is summed per CTA in
+// shared memory and added to global memory once.
+__global__ void __launch_bounds__(256) vq_step_kernel(const float* __restrict__ z, int64_t cells,
+                                                      int c0, const float* __restrict__ books,
+                                                      int nb, uint8_t* __restrict__ idx,
+                                                      float* __restrict__ q_out,
+                                                      float* __restrict__ dz,
+                                                      float* __restrict__ dE, float scale,
+                                                      float beta) {
+  extern __shared__ float sm[];
+  float* cb = sm;                    // [nb][256][c0]
+  float* acc = sm + nb * 256 * c0;   // [nb][256][c0] codebook-gradient partial sums
+  for (int i = threadIdx.x; i < nb * 256 * c0; i += blockDim.x) {
+    cb[i] = books[i];
+    acc[i] = 0.f;
+  }
+  __syncthreads();
+  for (int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; cell < cells;
+       cell += (int64_t)gridDim.x * blockDim.x) {
+    float zr[kMaxGridCh], r[kMaxGridCh], q[kMaxGridCh];
+#pragma unroll
+    for (int ch = 0; ch < kMaxGridCh; ++ch) {
+      zr[ch] = r[ch] = ch < c0 ? z[cell * c0 + ch] : 0.f;
+      q[ch] = 0.f;
+    }
+    for (int b = 0; b < nb; ++b) {
+      const int kb = vq_nearest(cb + b * 256 * c0, r, c0);
+      idx[cell * nb + b] = (uint8_t)kb;
+      const float* e = cb + (b * 256 + kb) * c0;
+      float* a = acc + (b * 256 + kb) * c0;
+#pragma unroll
+      for (int ch = 0; ch < kMaxGridCh; ++ch)
+        if (ch < c0) {
+          if (dE) atomicAdd(a + ch, scale * (e[ch] - r[ch]));
+          r[ch] = __fsub_rn(r[ch], e[ch]);
+          q[ch] += e[ch];
+        }
+    }
+    // the decoder trains on q (the value the exported indices decode to)
+#pragma unroll
+    for (int ch = 0; ch < kMaxGridCh; ++ch)
+      if (ch < c0) {
+        q_out[cell * c0 + ch] = q[ch];
+        if (dz) dz[cell * c0 + ch] += scale * beta * (zr[ch] - q[ch]);
+      }
+  }
+  __syncthreads();
+  if (dE)
+    for (int i = threadIdx.x; i < nb * 256 * c0; i += blockDim.x)
+      if (acc[i] != 0.f) atomicAdd(dE + i, acc[i]);
+}
+
+cudaError_t launch_vq_step(const float* z, int64_t cells, int c0, const float* books, int nb,
+                           uint8_t* idx, float* q_out, float* dz, float* dE, float scale,
+                           float beta, cudaStream_t s) {
+  if (cells == 0) return cudaSuccess;
+  const size_t smem = 2 * (size_t)nb * 256 * c0 * sizeof(float);
+  cudaError_t e = cudaFuncSetAttribute(vq_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, vq_step_kernel, 256, smem);
+  if (e != cudaSuccess) return e;
+  const int64_t blocks = (cells + 255) / 256;
+  const int64_t cap = (int64_t)sm_count() * (per_sm > 0 ? per_sm : 1);
+  vq_step_kernel<<<(int)(blocks < cap ? blocks : cap), 256, smem, s>>>(z, cells, c0, books, nb, idx,
+                                                                     q_out, dz, dE, scale, beta);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_vq_assign(const float* values, int64_t cells, int c0, const float* books, int nb,
                              uint8_t* idx, cudaStream_t s) {
   if (cells == 0) return cudaSuccess;
@@ -300,8 +407,11 @@ cudaError_t launch_vq_assign(const float* values, int64_t cells, int c0, const f
   cudaError_t e = cudaFuncSetAttribute(vq_assign_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, vq_assign_kernel, 256, smem);
+  if (e != cudaSuccess) return e;
   const int64_t blocks = (cells + 255) / 256;
-  const int64_t cap = (int64_t)sm_count() * 4;
+  const int64_t cap = (int64_t)sm_count() * (per_sm > 0 ? per_sm : 1);
   vq_assign_kernel<<<(int)(blocks < cap ? blocks : cap), 256, smem, s>>>(values, cells, c0, books,
                                                                        nb, idx);
   return cudaGetLastError();

@@ -43,7 +43,7 @@ int log2i(int v) {
   } while (0)
 
 // Shape and pointer rules shared by every call that takes a material.
-int check_material(const ntc_material* m, bool need_f32_grids) {
+int check_material(const ntc_material* m, bool need_f32_grids, bool vq_training = false) {
   if (!m) return fail(NTC_ERR_ARG, "material is NULL");
   if (!pow2(m->width) || !pow2(m->height) || m->width > 32768 || m->height > 32768)
     return fail(NTC_ERR_SHAPE, "texture %dx%d: sides must be powers of two <= 32768", m->width,
@@ -108,8 +108,14 @@ int check_material(const ntc_material* m, bool need_f32_grids) {
     CHECK_PTR(m->codebook0, "codebook0");
     if (m->precision == NTC_PREC_F8)
       return fail(NTC_ERR_UNSUPPORTED, "vector-quantised G0: FP32 or FP16 weights");
-    if (need_f32_grids)
-      return fail(NTC_ERR_UNSUPPORTED, "vector-quantised G0: decode only, without noise");
+    if (vq_training) {
+      if (m->encoding != NTC_GRID_F32)
+        return fail(NTC_ERR_ARG, "vector-quantised G0 training: F32 latents");
+    } else if (need_f32_grids || m->encoding != NTC_GRID_PACKED) {
+      return fail(NTC_ERR_UNSUPPORTED,
+                  "vector-quantised G0: decode packed indices without noise (export a trainer's "
+                  "material first)");
+    }
   }
   return NTC_OK;
 }
@@ -399,9 +405,15 @@ int ntc_backward(const ntc_material* m, const float* uvl, int64_t n, const float
 int ntc_train_step(const ntc_material* m, const ntc_trainer* tr, const ntc_target* t,
                    int64_t batch, uint64_t seed, const float* uvl_or_null, float* loss_out,
                    int32_t flags, void* stream) {
-  int st = check_material(m, true);
+  const bool vq = m && m->vq_books > 0;
+  int st = check_material(m, true, vq);
   if (st) return st;
   if (!tr || !t) return fail(NTC_ERR_ARG, "trainer / target is NULL");
+  if (vq) {
+    CHECK_PTR(tr->noisy, "trainer noisy scratch (vector-quantised G0)");
+    if (!tr->vq_idx) return fail(NTC_ERR_ARG, "trainer vq_idx is NULL");
+    if (!(tr->vq_beta >= 0.f)) return fail(NTC_ERR_ARG, "vq_beta must be >= 0");
+  }
   if (batch <= 0) return fail(NTC_ERR_ARG, "batch must be positive");
   if (m->precision == NTC_PREC_F8) return fail(NTC_ERR_UNSUPPORTED, "FP8 training");
   if (use_simt(m, flags)) {
@@ -453,7 +465,7 @@ int ntc_train_step(const ntc_material* m, const ntc_trainer* tr, const ntc_targe
   const float lo1 = -(float)(n1 - 1) / 2.f * m->q1, hi1 = (float)n1 / 2.f * m->q1;
   for (int j = 0; j < m->levels; ++j) {
     const ntc_level& L = m->lv[j];
-    if (!add_seg(L.grid0, (int64_t)L.g0_w * L.g0_h * m->c0, 0, true, lo0, hi0, nullptr) ||
+    if (!add_seg(L.grid0, (int64_t)L.g0_w * L.g0_h * m->c0, 0, !vq, lo0, hi0, nullptr) ||
         !add_seg(L.grid1, (int64_t)L.g1_w * L.g1_h * m->c1, 0, true, lo1, hi1, nullptr))
       return fail(NTC_ERR_ARG, "grid %d is not inside params", j);
   }
@@ -476,6 +488,9 @@ int ntc_train_step(const ntc_material* m, const ntc_trainer* tr, const ntc_targe
         !add_seg(m->b_h3, NTC_HIDDEN, 1, false, 0, 0, nullptr))
       return fail(NTC_ERR_ARG, "third hidden layer is not inside params");
   }
+  const int cb_seg = a.nseg;  // the codebooks of a vector-quantised G0 (lr_grid, unclamped)
+  if (vq && !add_seg(m->codebook0, (int64_t)m->vq_books * 256 * m->c0, 0, false, 0, 0, nullptr))
+    return fail(NTC_ERR_ARG, "codebooks are not inside params");
   const int64_t per_block = ntc::kAdamBlock * ntc::kAdamPerThread;
   a.block_start[0] = 0;
   for (int i = 0; i < a.nseg; ++i)
@@ -540,6 +555,7 @@ int ntc_train_step(const ntc_material* m, const ntc_trainer* tr, const ntc_targe
     na.block_start[0] = 0;
     for (int j = 0; j < m->levels; ++j)
       for (int k = 0; k < 2; ++k) {
+        if (k == 0 && vq) continue;  // a vector-quantised G0 trains through q, noise-free
         const ntc::AdamSeg& sg = a.seg[2 * j + k];
         const int c = k ? m->c1 : m->c0;
         ntc::NoiseSeg& g = na.seg[na.nseg];
@@ -557,6 +573,26 @@ int ntc_train_step(const ntc_material* m, const ntc_trainer* tr, const ntc_targe
     e = ntc::launch_noise_grids(na, s);
     if (e != cudaSuccess) return cuda_status(e, "train_step noise pass");
     b.noise = 0;
+  }
+  if (vq) {
+    // quantise every G0 level into the scratch (the fused step reads q), with
+    // the codebook and commitment gradients of the step
+    int64_t n_lat = 0;
+    for (int j = 0; j < m->levels; ++j) n_lat += a.seg[2 * j].len;
+    const float scale = (float)(2.0 / (double)n_lat);
+    uint8_t* ip = tr->vq_idx;
+    for (int j = 0; j < m->levels; ++j) {
+      const ntc::AdamSeg& sg = a.seg[2 * j];
+      const int64_t cells = sg.len / m->c0;
+      e = ntc::launch_vq_step(tr->params + sg.off, cells, m->c0, m->codebook0, m->vq_books, ip,
+                              tr->noisy + sg.off, freeze ? nullptr : G + sg.off,
+                              freeze ? nullptr : G + a.seg[cb_seg].off, scale, tr->vq_beta, s);
+      if (e != cudaSuccess) return cuda_status(e, "train_step vector quantisation");
+      mt.lv[j].grid0 = tr->noisy + sg.off;
+      ip += cells * m->vq_books;
+    }
+    mt.vq_books = 0;  // the fused step sees q as a plain FP32 grid
+    mt.codebook0 = nullptr;
   }
   e = use_simt(m, flags) ? ntc::launch_backward_simt(mt, b, s) : ntc::launch_train_tc(mt, b, s);
   if (e != cudaSuccess) return cuda_status(e, "train_step forward/backward");

@@ -46,7 +46,8 @@ bool train_tc_supported(const ntc_material& m);
 cudaError_t launch_train_tc(const ntc_material& m, const BwdArgs& a, cudaStream_t s);
 
 // Adam over the segments of the trainer's parameter array.
-constexpr int kMaxSegs = 2 * NTC_MAX_LEVELS + 8;
+// grids (2 per level), W1..W3 and biases (6), the third hidden layer (2), codebooks (1)
+constexpr int kMaxSegs = 2 * NTC_MAX_LEVELS + 9;
 struct AdamSeg {
   int64_t off, len;   // float offset into params and element count
   float lo, hi;       // clamp range (grids)
@@ -96,6 +97,9 @@ cudaError_t launch_quantize_pack(const float* values, int64_t cells, int c, int 
                                  uint8_t* packed, float* snapped, cudaStream_t s);
 cudaError_t launch_unpack(const uint8_t* packed, int64_t cells, int c, int bits, float q,
                           int32_t* idx, float* values, cudaStream_t s);
+cudaError_t launch_vq_step(const float* z, int64_t cells, int c0, const float* books, int nb,
+                           uint8_t* idx, float* q_out, float* dz, float* dE, float scale,
+                           float beta, cudaStream_t s);
 cudaError_t launch_vq_assign(const float* values, int64_t cells, int c0, const float* books, int nb,
                              uint8_t* idx, cudaStream_t s);
 cudaError_t launch_sample_batch(uint64_t seed, int64_t step, int64_t batch, int w, int h, int mips,

@@ -241,6 +241,37 @@ def test_vq_assign_residual_and_ties_by_hand():
     assert idx.tolist() == [[5, 1], [5, 2], [0, 0]]
 
 
+def test_vq_train_terms_by_hand():
+    """VQ-VAE terms on a hand example: one book {0: 0, 1: 1}, latents 0.2 and
+    0.9 (N = 2): indices 0, 1; q = 0, 1; codebook gradient 2/N (e - r) =
+    -0.2, 0.1; commitment gradient 2 beta/N (z - q) = beta (0.2, -0.1)."""
+    cb = np.full((1, 256, 1), 50.0, np.float32)
+    cb[0, 0, 0], cb[0, 1, 0] = 0.0, 1.0
+    idx, q, dz, dcb = oracle.vq_train_terms([np.array([[[0.2], [0.9]]], np.float32)], cb, 0.25)
+    assert idx[0].reshape(-1).tolist() == [0, 1]
+    assert np.allclose(q[0].reshape(-1), [0.0, 1.0])
+    assert np.allclose(dcb[0, :2, 0], [-0.2, 0.1], atol=1e-7) and not np.any(dcb[0, 2:])
+    assert np.allclose(dz[0].reshape(-1), [0.05, -0.025], atol=1e-8)
+
+
+def test_vq_train_terms_residual_books():
+    """Two books: the second book's gradient sees what the first leaves
+    (r_1 = z - e_0); gradients sum over the cells that share an entry."""
+    cb = np.full((2, 256, 1), 50.0, np.float32)
+    cb[0, 3, 0] = 10.0
+    cb[1, 4, 0], cb[1, 5, 0] = 1.0, -1.0
+    z = np.array([[[11.25], [10.75], [9.25]]], np.float32)       # N = 3
+    idx, q, dz, dcb = oracle.vq_train_terms([z], cb, 1.0)
+    assert idx[0].reshape(3, 2).tolist() == [[3, 4], [3, 4], [3, 5]]
+    assert np.allclose(q[0].reshape(-1), [11.0, 11.0, 9.0])
+    # book 0, entry 3: 2/3 * ((10 - 11.25) + (10 - 10.75) + (10 - 9.25))
+    assert np.isclose(dcb[0, 3, 0], 2 / 3 * (-1.25 - 0.75 + 0.75))
+    # book 1: residuals 1.25, 0.75 -> entry 4; -0.75 -> entry 5
+    assert np.isclose(dcb[1, 4, 0], 2 / 3 * ((1 - 1.25) + (1 - 0.75)))
+    assert np.isclose(dcb[1, 5, 0], 2 / 3 * (-1 + 0.75))
+    assert np.allclose(dz[0].reshape(-1), 2 / 3 * np.array([0.25, -0.25, 0.25]))
+
+
 # ----------------------------------------------------------- quantisation ---
 @pytest.mark.parametrize("bits", [1, 2, 4, 8])
 def test_quantizer_levels_and_roundtrip(bits):
