@@ -47,7 +47,7 @@ typedef enum {
   NTC_ERR_ARG = 1,         /* null pointer, negative size, bad enum value */
   NTC_ERR_SHAPE = 2,       /* sizes violate the pyramid / MLP shape rules */
   NTC_ERR_ALIGN = 3,       /* a device pointer is not 16-byte aligned */
-  NTC_ERR_UNSUPPORTED = 4, /* a valid combination this build does not implement */
+  NTC_ERR_UNSUPPORTED = 4, /* a valid combination the library does not implement */
   NTC_ERR_CUDA = 5,        /* a CUDA launch or API call failed */
   NTC_ERR_TIMEOUT = 6      /* a bounded device-side wait gave up (status word) */
 } ntc_status;
