@@ -11,9 +11,11 @@
  * ---------------------------------------
  *  - Every array argument is a DEVICE pointer owned by the caller unless the
  *    parameter says "host".  The library never allocates or frees device
- *    memory and never synchronises the device; all work is enqueued on the
- *    caller's `stream` (a cudaStream_t passed as void*; NULL = legacy default
- *    stream) in launch order.
+ *    memory and never synchronises the device (ntc_device_status and the
+ *    autotuner excepted); all work is enqueued on the caller's `stream` (a
+ *    cudaStream_t passed as void*; NULL = legacy default stream) in launch
+ *    order.  ntc_decode_host also uses two helper streams and a few events
+ *    that it creates once per device, joined back into `stream`.
  *  - Structs (ntc_material, ntc_grads, ntc_trainer, ntc_target) are passed by
  *    HOST pointer; their fields point to device memory.  They are read during
  *    the call only; the call does not keep them.
