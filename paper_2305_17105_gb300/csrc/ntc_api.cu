@@ -450,6 +450,7 @@ int ntc_train_step(const ntc_material* m, const ntc_trainer* tr, const ntc_targe
   };
   auto add_seg = [&](const void* ptr, int64_t len, int group, bool clamp, float lo, float hi,
                      __half* half_copy) -> bool {
+    if (a.nseg >= ntc::kMaxSegs) return false;
     ntc::AdamSeg& sg = a.seg[a.nseg++];
     if (!offset_of(ptr, len, &sg.off)) return false;
     sg.len = len;
