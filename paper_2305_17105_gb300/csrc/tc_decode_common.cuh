@@ -475,12 +475,14 @@ __device__ __forceinline__ void taps16(int x2, int y2, int4 k, int (&cell)[4], i
 // with grid class k = 0 (one 5-8 channel cell word), 1 (a 5-8 channel word
 // and a 1-4 channel tail word) or 2 (two 5-8 channel words).  Kernels that
 // take the class at run time pass the Plan, which has the same fields.
+// Classes 11..19 are the same grid classes with learned interpolation of G0.
 template <int CLS>
 struct FastLayout {
-  static constexpr int k0 = (CLS - 1) / 3, k1 = (CLS - 1) % 3;
+  static constexpr int base = CLS > 10 ? CLS - 10 : CLS;
+  static constexpr int k0 = (base - 1) / 3, k1 = (base - 1) % 3;
   static constexpr int eo0 = k0 == 2 ? 2 : 1, t0 = k0 == 1 ? 1 : 0, cb0 = k0 == 0 ? 4 : 8;
   static constexpr int eo1 = k1 == 2 ? 2 : 1, t1 = k1 == 1 ? 1 : 0, cb1 = k1 == 0 ? 4 : 8;
-  static constexpr int learned = 0;
+  static constexpr int learned = CLS > 10 ? 1 : 0;
 };
 
 // Issue the eight cell loads of a fast-layout row (invalid rows load nothing).

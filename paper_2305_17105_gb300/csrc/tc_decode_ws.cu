@@ -336,12 +336,25 @@ cudaError_t launch_decode_ws_batched(const BatchHeader* dev, int64_t total_tiles
 
 cudaError_t launch_decode_ws(const ntc_material& m, const float* uvl, int64_t n, void* out,
                              int out_dtype, int filter, uint64_t jkey, cudaStream_t s, bool fast) {
-  if (m.hidden_layers == 3)  // a third hidden layer: runtime-class fast layout or generic
-    return fast ? launch_ws<-1, false, true>(m, uvl, n, out, out_dtype, filter, jkey, s)
-                : launch_ws<0, false, true>(m, uvl, n, out, out_dtype, filter, jkey, s);
+  if (m.hidden_layers == 3) {  // a third hidden layer: the paper's profiles, else run time
+    if (!fast) return launch_ws<0, false, true>(m, uvl, n, out, out_dtype, filter, jkey, s);
+    const Plan P(m, false, true);
+    const int cls = (P.learned ? 11 : 1) + 3 * grid_class(m.c0, P.cb0) + grid_class(m.c1, P.cb1);
+    if (cls == 16) return launch_ws<16, false, true>(m, uvl, n, out, out_dtype, filter, jkey, s);
+    if (cls == 18) return launch_ws<18, false, true>(m, uvl, n, out, out_dtype, filter, jkey, s);
+    return launch_ws<-1, false, true>(m, uvl, n, out, out_dtype, filter, jkey, s);
+  }
   if (!fast) return launch_ws<0, false>(m, uvl, n, out, out_dtype, filter, jkey, s);
   const Plan P(m, false, true);
-  if (P.learned) return launch_ws<-1, false>(m, uvl, n, out, out_dtype, filter, jkey, s);
+  if (P.learned) {
+    // the paper's profiles 0.5 and 2.25 (4-bit G0 of 12 / 16 channels, G1 of
+    // 16 / 12) as compile-time classes, other learned layouts at run time
+    switch (11 + 3 * grid_class(m.c0, P.cb0) + grid_class(m.c1, P.cb1)) {
+      case 16: return launch_ws<16, false>(m, uvl, n, out, out_dtype, filter, jkey, s);
+      case 18: return launch_ws<18, false>(m, uvl, n, out, out_dtype, filter, jkey, s);
+      default: return launch_ws<-1, false>(m, uvl, n, out, out_dtype, filter, jkey, s);
+    }
+  }
   switch (1 + 3 * grid_class(m.c0, P.cb0) + grid_class(m.c1, P.cb1)) {
     case 1: return launch_ws<1, false>(m, uvl, n, out, out_dtype, filter, jkey, s);
     case 2: return launch_ws<2, false>(m, uvl, n, out, out_dtype, filter, jkey, s);
