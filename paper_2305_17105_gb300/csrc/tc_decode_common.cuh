@@ -681,7 +681,9 @@ __device__ __forceinline__ void zero_tail_groups(const Plan& P, const S& dst) {
 
 // Generic layout (other bit widths, F32 grids, FP8 operands): float
 // dequantisation and interpolation, channels in order.
-template <bool F8, class S>
+// VQ: the vector-quantised G0 branch is compiled in (kernels that decode
+// such materials).
+template <bool F8, class S, bool VQ = true>
 __device__ __forceinline__ void generic_grid(const ntc_material& M, const MipTab* tb, int k,
                                              const Plan& P, const Row& r, const S& dst, int kg0,
                                              float inv_sa) {
@@ -697,7 +699,7 @@ __device__ __forceinline__ void generic_grid(const ntc_material& M, const MipTab
 #pragma unroll 1
     for (int tp = 0; tp < 4; ++tp) {
       float acc[kMaxGridCh];
-      if (M.vq_books > 0) {
+      if (VQ && M.vq_books > 0) {
         const int cell = r.valid ? t.cell[tp] : 0;
 #pragma unroll
         for (int ch = 0; ch < kMaxGridCh; ++ch) acc[ch] = 0.f;
@@ -737,7 +739,7 @@ __device__ __forceinline__ void generic_grid(const ntc_material& M, const MipTab
     if (k) taps_of(r.x, r.y, tb->sx1[m], tb->sy1[m], tb->g1w[m], tb->g1h[m], t);
     else taps_of(r.x, r.y, tb->sx0[m], tb->sy0[m], tb->g0w[m], tb->g0h[m], t);
     const uint8_t* base = k ? tb->grid1[m] : tb->grid0[m];
-    if (k == 0 && M.vq_books > 0) {
+    if (VQ && k == 0 && M.vq_books > 0) {
       // vector-quantised G0: each tap's cell is the sum of its codebook
       // entries (rows of 4k values read as float4)
 #pragma unroll
@@ -800,13 +802,13 @@ __device__ __forceinline__ void generic_grid(const ntc_material& M, const MipTab
     }
 }
 
-template <bool F8, class S>
+template <bool F8, class S, bool VQ = true>
 __device__ __forceinline__ void build_generic(const ntc_material& M, const Plan& P,
                                               const uint8_t* sm, const Row& r, const S& dst,
                                               float inv_sa) {
   const MipTab* tb = reinterpret_cast<const MipTab*>(sm + P.tab);
-  generic_grid<F8>(M, tb, 0, P, r, dst, 0, inv_sa);
-  generic_grid<F8>(M, tb, 1, P, r, dst, P.f0, inv_sa);
+  generic_grid<F8, S, VQ>(M, tb, 0, P, r, dst, 0, inv_sa);
+  generic_grid<F8, S, VQ>(M, tb, 1, P, r, dst, P.f0, inv_sa);
   if (!F8) {
     pe_groups(P, sm, tb->lodh[r.m], r.x, r.y, dst);
   } else {

@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) decode_ws_batched_kernel(
     auto build = [&](const Row& r) {
       if (CLS > 0) build_fast(Lay(), P, FastK(M), region, r, xs);
       else if (CLS < 0) build_fast(P, P, FastK(M), region, r, xs);
-      else build_generic<false>(M, P, region, r, xs, 1.f);
+      else build_generic<false, SmemRow, false>(M, P, region, r, xs, 1.f);  // batches: no VQ
       tc::fence_proxy_async();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&bar_x[w]);
