@@ -56,8 +56,8 @@ struct MipTab {
 
 // Input-row layout and shared memory plan (byte offsets).
 struct Plan {
-  int fast, learned, eo0, eo1, t0, t1, f0, f1, gpe, k_int, cb0, cb1, h3;
-  uint32_t w1, w2, w3, wb2, wb3, wh, wbh, bias, tab, pe, desc, total;
+  int fast, learned, vq, eo0, eo1, t0, t1, f0, f1, gpe, k_int, cb0, cb1, h3;
+  uint32_t w1, w2, w3, wb2, wb3, wh, wbh, cbk, bias, tab, pe, desc, total;
   // `taps_ok`: every grid/mip size ratio puts the taps on the 1/16 lattice and
   // the bin widths are powers of two (fast_layout_ok).
   __host__ __device__ Plan(const ntc_material& M, bool f8, bool taps_ok) {
@@ -72,15 +72,24 @@ struct Plan {
       cb0 = cell_bytes(c0, bits0);
       cb1 = cell_bytes(c1, bits1);
     }
-    // the fast layout reads whole 32-bit cell words: 4-bit cells of 4 or 8 bytes
-    fast = taps_ok && packed && bits0 == 4 && bits1 == 4 && (cb0 == 4 || cb0 == 8) &&
-           (cb1 == 4 || cb1 == 8) && !(f8 && learned) && M.vq_books == 0;
+    // the fast layout reads whole 32-bit cell words: 4-bit cells of 4 or 8
+    // bytes; a vector-quantised G0 (FP16, bilinear, two books of 8 or 16
+    // values) joins it with 2-byte index cells and the codebooks in shared
+    // memory
+    vq = M.vq_books > 0;
+    const bool g1_ok = packed && bits1 == 4 && (cb1 == 4 || cb1 == 8);
+    if (vq) {
+      fast = taps_ok && g1_ok && !f8 && !learned && M.vq_books == 2 && (c0 == 8 || c0 == 16);
+    } else {
+      fast = taps_ok && g1_ok && bits0 == 4 && (cb0 == 4 || cb0 == 8) && !(f8 && learned);
+    }
     eo0 = eo1 = t0 = t1 = 0;
     if (fast) {
-      // word 0 holds 5-8 channels; word 1 (8-byte cells) the other c - 8
-      eo0 = (cb0 == 8 && c0 > 12) ? 2 : 1;
+      // word 0 holds 5-8 channels; word 1 (8-byte cells) the other c - 8;
+      // vector-quantised G0: c0 / 8 groups of channels in order
+      eo0 = vq ? c0 / 8 : ((cb0 == 8 && c0 > 12) ? 2 : 1);
       eo1 = (cb1 == 8 && c1 > 12) ? 2 : 1;
-      t0 = (cb0 == 8 && c0 <= 12) ? 1 : 0;
+      t0 = (!vq && cb0 == 8 && c0 <= 12) ? 1 : 0;
       t1 = (cb1 == 8 && c1 <= 12) ? 1 : 0;
       f0 = f1 = 0;
       // learned interpolation: each G0 tap's words, the tail halves of taps
@@ -101,6 +110,7 @@ struct Plan {
     h3 = !f8 && M.hidden_layers == 3;             // third hidden layer (FP16 forms)
     wh = o;   o += h3 ? kHidden * kHidden * 2 : 0;  // B: Wh
     wbh = o;  o += h3 ? kHidden * 16 * 2 : 0;       // B: its bias block
+    cbk = o;  o += (vq && !f8) ? M.vq_books * 256 * c0 * 2 : 0;  // FP16 codebooks
     bias = o; o += (2 * kHidden + kN3) * 4;       // FP32 biases (FP8 epilogues)
     o = (o + 15) / 16 * 16;
     tab = o;  o += sizeof(MipTab);
@@ -154,7 +164,10 @@ __device__ __forceinline__ int w1_column(const ntc_material& M, const Plan& P, i
   } else if (P.fast) {
     // 5-8 channel word: half2 (lo E, hi E, lo O, hi O) = channels (0,4) (2,6) (1,5) (3,7)
     const int eo = 2 * (j & 1) + (j >> 1) + 4 * l;
-    if (g < P.eo0) return 8 * g + eo < M.c0 ? 8 * g + eo : -1;
+    if (g < P.eo0) {  // vector-quantised G0: channels in order
+      const int ch = P.vq ? 8 * g + e : 8 * g + eo;
+      return ch < M.c0 ? ch : -1;
+    }
     g -= P.eo0;
     if (g < P.eo1) return 8 * g + eo < M.c1 ? M.c0 + 8 * g + eo : -1;
     g -= P.eo1;
@@ -238,6 +251,10 @@ __device__ void stage_shared(const ntc_material& M, const Plan& P, uint8_t* sm, 
     if (F8) sm[off] = live ? static_cast<const uint8_t*>(M.w[2])[i] : 0;
     else *reinterpret_cast<__half*>(sm + off) = __float2half_rn(
         live ? h3 * __half2float(static_cast<const __half*>(M.w[2])[i]) : 0.f);
+  }
+  if (!F8 && P.vq) {  // FP16 codebooks [books][256][c0]
+    __half* cb = reinterpret_cast<__half*>(sm + P.cbk);
+    for (int i = tid; i < M.vq_books * 256 * M.c0; i += nt) cb[i] = __float2half_rn(M.codebook0[i]);
   }
   if (!F8 && P.h3) {
     for (int i = tid; i < kHidden * kHidden; i += nt) {
@@ -478,6 +495,7 @@ __device__ __forceinline__ void taps16(int x2, int y2, int4 k, int (&cell)[4], i
 // Classes 11..19 are the same grid classes with learned interpolation of G0.
 template <int CLS>
 struct FastLayout {
+  static constexpr int vq = 0;  // vector-quantised G0 runs on the Plan (run-time class)
   static constexpr int base = CLS > 10 ? CLS - 10 : CLS;
   static constexpr int k0 = (base - 1) / 3, k1 = (base - 1) % 3;
   static constexpr int eo0 = k0 == 2 ? 2 : 1, t0 = k0 == 1 ? 1 : 0, cb0 = k0 == 0 ? 4 : 8;
@@ -486,7 +504,8 @@ struct FastLayout {
 };
 
 // Issue the eight cell loads of a fast-layout row (invalid rows load nothing).
-template <class L>
+// VQ: the vector-quantised G0 branch is compiled in.
+template <class L, bool VQ = true>
 __device__ __forceinline__ void gather_fast(const L& lay, const MipTab* tb, Row& r) {
 #pragma unroll
   for (int t = 0; t < 4; ++t) r.c0[t] = r.c1[t] = make_uint2(0, 0);
@@ -502,7 +521,8 @@ __device__ __forceinline__ void gather_fast(const L& lay, const MipTab* tb, Row&
   const uint8_t* g1 = tb->grid1[m];
 #pragma unroll
   for (int t = 0; t < 4; ++t) {
-    if (lay.cb0 == 8) r.c0[t] = __ldg(reinterpret_cast<const uint2*>(g0) + cell0[t]);
+    if (VQ && lay.vq) r.c0[t].x = __ldg(reinterpret_cast<const unsigned short*>(g0) + cell0[t]);
+    else if (lay.cb0 == 8) r.c0[t] = __ldg(reinterpret_cast<const uint2*>(g0) + cell0[t]);
     else r.c0[t].x = __ldg(reinterpret_cast<const uint32_t*>(g0) + cell0[t]);
     if (lay.cb1 == 8) r.c1[t] = __ldg(reinterpret_cast<const uint2*>(g1) + cell1[t]);
     else r.c1[t].x = __ldg(reinterpret_cast<const uint32_t*>(g1) + cell1[t]);
@@ -591,7 +611,7 @@ struct FastK {
 };
 
 // Fast layout: every group of the row from the prefetched cells.
-template <class L, class S>
+template <class L, class S, bool VQ = true>
 __device__ __forceinline__ void build_fast(const L& lay, const Plan& P, const FastK& K,
                                            const uint8_t* sm, const Row& r, const S& dst) {
   const uint32_t fx0 = r.frac & 15, fx1 = (r.frac >> 8) & 15;
@@ -640,13 +660,41 @@ __device__ __forceinline__ void build_fast(const L& lay, const Plan& P, const Fa
     return;
   }
   const YLerp y0 = ylerp_of((r.frac >> 4) & 15, K.s[0], K.s16[0], K.m7q[0]);
+  if (VQ && lay.vq) {
+    // vector-quantised G0: per tap the sum of its two FP16 codebook entries,
+    // blended with the bilinear weights (multiples of 1/256: exact in FP16)
+    const uint32_t fy0 = (r.frac >> 4) & 15;
+    const __half2 wt[4] = {
+        __float2half2_rn((float)((16 - fx0) * (16 - fy0)) * (1.f / 256.f)),
+        __float2half2_rn((float)(fx0 * (16 - fy0)) * (1.f / 256.f)),
+        __float2half2_rn((float)((16 - fx0) * fy0) * (1.f / 256.f)),
+        __float2half2_rn((float)(fx0 * fy0) * (1.f / 256.f))};
+    const int c0 = 8 * lay.eo0;
+    const uint8_t* cbk = sm + P.cbk;
 #pragma unroll
-  for (int f = 0; f < 2; ++f)
-    if (f < lay.eo0) {
-      const uint32_t w[4] = {word_of(r.c0[0], f), word_of(r.c0[1], f), word_of(r.c0[2], f),
-                             word_of(r.c0[3], f)};
-      dst.put4(kg++, eo_group(w, 16 - fx0, fx0, y0));
-    }
+    for (int f = 0; f < 2; ++f)
+      if (f < lay.eo0) {
+        __half2 acc[4] = {u2h(0u), u2h(0u), u2h(0u), u2h(0u)};
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const uint32_t i0 = r.c0[t].x & 0xFFu, i1 = (r.c0[t].x >> 8) & 0xFFu;
+          const uint4 a = *reinterpret_cast<const uint4*>(cbk + ((i0 * c0) + 8 * f) * 2);
+          const uint4 b = *reinterpret_cast<const uint4*>(cbk + (((256 + i1) * c0) + 8 * f) * 2);
+          const uint32_t av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[j] = __hfma2(wt[t], __hadd2(u2h(av[j]), u2h(bv[j])), acc[j]);
+        }
+        dst.put4(kg++, make_uint4(h2u(acc[0]), h2u(acc[1]), h2u(acc[2]), h2u(acc[3])));
+      }
+  } else {
+#pragma unroll
+    for (int f = 0; f < 2; ++f)
+      if (f < lay.eo0) {
+        const uint32_t w[4] = {word_of(r.c0[0], f), word_of(r.c0[1], f), word_of(r.c0[2], f),
+                               word_of(r.c0[3], f)};
+        dst.put4(kg++, eo_group(w, 16 - fx0, fx0, y0));
+      }
+  }
 #pragma unroll
   for (int f = 0; f < 2; ++f)
     if (f < lay.eo1) {

@@ -165,11 +165,11 @@ __global__ void __launch_bounds__(kWsThreads, 1) decode_ws_batched_kernel(
       const bool valid = ql < m_nq;
       locate(M, tb, load_query(uvl, m_q0 + ql, valid), filter, row, r);
       if (CLS > 0) gather_fast(Lay(), tb, r);
-      else if (CLS < 0) gather_fast(P, tb, r);
+      else if (CLS < 0) gather_fast<Plan, false>(P, tb, r);  // batches: no VQ
     };
     auto build = [&](const Row& r) {
       if (CLS > 0) build_fast(Lay(), P, FastK(M), region, r, xs);
-      else if (CLS < 0) build_fast(P, P, FastK(M), region, r, xs);
+      else if (CLS < 0) build_fast<Plan, SmemRow, false>(P, P, FastK(M), region, r, xs);
       else build_generic<false, SmemRow, false>(M, P, region, r, xs, 1.f);  // batches: no VQ
       tc::fence_proxy_async();
       __syncwarp();
@@ -339,13 +339,15 @@ cudaError_t launch_decode_ws(const ntc_material& m, const float* uvl, int64_t n,
   if (m.hidden_layers == 3) {  // a third hidden layer: the paper's profiles, else run time
     if (!fast) return launch_ws<0, false, true>(m, uvl, n, out, out_dtype, filter, jkey, s);
     const Plan P(m, false, true);
-    const int cls = (P.learned ? 11 : 1) + 3 * grid_class(m.c0, P.cb0) + grid_class(m.c1, P.cb1);
+    const int cls = P.vq ? -1 : (P.learned ? 11 : 1) + 3 * grid_class(m.c0, P.cb0) +
+                                    grid_class(m.c1, P.cb1);
     if (cls == 16) return launch_ws<16, false, true>(m, uvl, n, out, out_dtype, filter, jkey, s);
     if (cls == 18) return launch_ws<18, false, true>(m, uvl, n, out, out_dtype, filter, jkey, s);
     return launch_ws<-1, false, true>(m, uvl, n, out, out_dtype, filter, jkey, s);
   }
   if (!fast) return launch_ws<0, false>(m, uvl, n, out, out_dtype, filter, jkey, s);
   const Plan P(m, false, true);
+  if (P.vq) return launch_ws<-1, false>(m, uvl, n, out, out_dtype, filter, jkey, s);
   if (P.learned) {
     // the paper's profiles 0.5 and 2.25 (4-bit G0 of 12 / 16 channels, G1 of
     // 16 / 12) as compile-time classes, other learned layouts at run time

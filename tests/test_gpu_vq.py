@@ -78,6 +78,26 @@ def test_vq_decode_matches_oracle(shape, books, precision):
     assert np.abs(tri - md.decode_trilinear(q[:1500])).max() <= OUT_TOL
 
 
+@pytest.mark.parametrize("nwg", [2, 4, 5])
+def test_vq_fast_layout_every_launch_shape(nwg):
+    """VQ-8 with a 4-bit G1 runs the fast layout (FP16 codebooks in shared
+    memory, exact bilinear weights on the 1/16 lattice) on every launch
+    shape: against the oracle, nearest and trilinear."""
+    case = make_case(seed=86, width=512, height=256, channels=12, c0=8, c1=12, k_in=48)
+    mat, md = _vq_material(case, 2, ntc.PREC_F16, 304)
+    q = gen.random_queries(2 * 4096 + 3, md.mips, seed=4086)
+    ntc.ntc_set_decode_warpgroups(nwg)
+    try:
+        out = to_np(ntc.ntc_decode(mat, torch.from_numpy(q).to(DEV)))
+        tri = to_np(ntc.ntc_decode(mat, torch.from_numpy(q[:1000]).to(DEV),
+                                   filter=ntc.FILTER_TRILINEAR))
+    finally:
+        ntc.ntc_set_decode_warpgroups(0)
+    assert ntc.ntc_device_status() == ntc.OK
+    assert np.abs(out - md.decode(q)).max() <= OUT_TOL
+    assert np.abs(tri - md.decode_trilinear(q[:1000])).max() <= OUT_TOL
+
+
 def test_vq_refusals():
     case = make_case(seed=88, width=256, height=256, channels=8, c0=8, c1=8, k_in=32)
     mat, _ = _vq_material(case, 2, ntc.PREC_F16, 301)
