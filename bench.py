@@ -443,6 +443,38 @@ def paper_form_train(ntc, batch, stream, steps=20, hidden_layers=2):
             "status": ntc.ntc_device_status()}
 
 
+def u8_output_eval(ntc, mat, q_dev, q_host, stream, reps=5):
+    """The same decode with 8-bit UNORM outputs: on the device (inputs
+    resident) and end to end through ntc_decode_host (pinned host buffers,
+    chunks of 2^20 queries)."""
+    import torch
+    n = q_dev.shape[0]
+    out = torch.empty((n, DEC_C), dtype=torch.uint8, device="cuda")
+    out_host = torch.empty((n, DEC_C), dtype=torch.uint8).pin_memory()
+    chunk = min(1 << 20, n)
+    ws = torch.empty(ntc.lib().ntc_decode_host_workspace_bytes(DEC_C, ntc.DTYPE_U8, chunk),
+                     dtype=torch.uint8, device="cuda")
+    res = {}
+    for name, fn in (("device", lambda: ntc.ntc_decode(mat, q_dev, out=out)),
+                     ("e2e", lambda: ntc.ntc_decode_host(mat, q_host, out_host=out_host,
+                                                         workspace=ws))):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / reps
+        res[name + "_ms"] = ms
+        res[name + "_texels_per_s"] = n / (ms / 1e3)
+    res["bytes_per_query"] = 12 + DEC_C
+    res["h2d_bytes_per_step"], res["d2h_bytes_per_step"] = n * 12, n * DEC_C
+    res["status"] = ntc.ntc_device_status()
+    return res
+
+
 def vq_eval(ntc, q_dev, stream):
     """Decode of the 2^24 queries with a vector-quantised G0 (the paper's
     VQ-8: two 256-entry codebooks of 8 values, two 8-bit indices per cell,
@@ -967,6 +999,13 @@ def main():
         except Exception as e:  # reported, never fatal to the headline line
             paper_form = {"error": f"{type(e).__name__}: {e}"[:300]}
 
+    u8 = None
+    if not args.no_extras and precision != "f32":
+        try:
+            u8 = u8_output_eval(ntc, mat, q_dev, q_host, stream)
+        except Exception as e:  # reported, never fatal to the headline line
+            u8 = {"error": f"{type(e).__name__}: {e}"[:300]}
+
     vq = None
     if not args.no_extras:
         try:
@@ -1013,6 +1052,7 @@ def main():
         "roofline": roof, "train_roofline": train_roof, "tuning": tuning, "e2e": e2e, "fp32_path": fp32, "cpu_baseline": cpu,
         "render": render, "multi_material": multi, "paper_form": paper_form, "train_crops": crops,
         "equal_psnr_training": equal, "vq_decode": vq, "sq_vs_vq_training": sqvq,
+        "u8_output": u8,
         "gpu_launches": kernels_per_step * args.steps,
         "clocks": clk.summary(), "wall_s": t_wall,
     }

@@ -74,7 +74,11 @@ enum { NTC_OUT_SIGMOID = 0, NTC_OUT_IDENTITY = 1 }; /* output activation */
  * xi uniform in [0, 1) from a counter hash of (noise_seed, noise_step, query
  * index), which equals trilinear filtering in expectation. */
 enum { NTC_FILTER_NEAREST = 0, NTC_FILTER_TRILINEAR = 1, NTC_FILTER_STOCHASTIC = 2 };
-enum { NTC_DTYPE_F32 = 0, NTC_DTYPE_F16 = 1 };              /* output element type */
+/* Output element type.  U8: 8-bit UNORM, each output y stored as
+ * round-half-to-even(clamp(y, 0, 1) * 255) computed in float32 (NaN -> 0),
+ * the 8-bit encoding of the evaluation textures (appendix "Evaluation
+ * Texture Set Details"). */
+enum { NTC_DTYPE_F32 = 0, NTC_DTYPE_F16 = 1, NTC_DTYPE_U8 = 2 };
 /* Resampling of G0 (Sec. 4.3.1): bilinear like G1, or learned interpolation:
  * the four neighbouring G0 feature vectors of the bilinear footprint (taps
  * (x0,y0), (x1,y0), (x0,y1), (x1,y1)) concatenated in the MLP input, which
@@ -241,7 +245,7 @@ int32_t ntc_pyramid(int32_t width, int32_t height, int32_t* g0_w, int32_t* g0_h,
  *       [0, w_m - 1] (NaN -> 0).  TRILINEAR: lod is continuous; 2x2 texels
  *       around (u, v) on mips floor(lod) and floor(lod)+1 (clamped), texel
  *       taps wrap around, 8 decodes blended.
- *  out  [n][channels] float32 or float16 (out_dtype), row-major.
+ *  out  [n][channels] float32, float16 or 8-bit UNORM (out_dtype), row-major.
  *  flags NTC_FLAG_NOISE (F32 grids only: decode the noisy training grids of
  *       (noise_seed, noise_step)), NTC_FLAG_SIMT.
  * Decodes each query from the level of its mip: bilinear G0 and G1 features,
@@ -268,22 +272,24 @@ int ntc_decode_host(const ntc_material* m, const float* uvl_host, int64_t n, voi
                     int32_t out_dtype, int32_t filter, int32_t flags, uint64_t noise_seed,
                     int64_t noise_step, void* workspace, size_t workspace_bytes, void* stream);
 
-/* Workspace bytes of ntc_decode_host for chunks of `chunk` queries. */
+/* Workspace bytes of ntc_decode_host for chunks of `chunk` queries (0 for
+ * invalid arguments). */
 size_t ntc_decode_host_workspace_bytes(int32_t channels, int32_t out_dtype, int64_t chunk);
 
 /* Launch shape of the tensor-core decode: warpgroup tile pipelines per CTA
  * (one CTA per SM, 128 TMEM columns per pipeline), 2, 3 or 4, or 5 for the
  * warp-specialised form (4 compute warpgroups whose MMA chains a fifth
- * warpgroup issues; FP16, FP8 materials run 4 pipelines); 0 restores the
- * default (5).  Process-wide; takes effect for later ntc_decode calls. */
+ * warpgroup issues; FP16 and FP8); 0 restores the default (5).
+ * Process-wide; takes effect for later ntc_decode calls. */
 int ntc_set_decode_warpgroups(int32_t nwg);
 
 /* Autotuner of the tensor-core decode: times every launch shape (1 warm-up
  * + 3 timed launches each, CUDA events on `stream`) on the caller's queries
  * (writing `out`), selects the fastest as ntc_set_decode_warpgroups would,
  * and returns it in *best (host).  ms_out (host, nullable, 4 floats)
- * receives the mean time per launch of the shapes 2, 3, 4, 5.  Synchronises
- * the stream. */
+ * receives the mean time per launch of the shapes 2, 3, 4, 5.  out_dtype
+ * and filter as ntc_decode (NTC_ERR_ARG otherwise).  Synchronises the
+ * stream. */
 int ntc_autotune_decode(const ntc_material* m, const float* uvl, int64_t n, void* out,
                         int32_t out_dtype, int32_t filter, int32_t* best, float* ms_out,
                         void* stream);

@@ -37,9 +37,10 @@ typedef struct {
   const double *w3, *b3;    /* [channels][hidden], [channels] */
   int interp0;              /* G0 resampling (Sec. 4.3.1): 0 bilinear, 1 learned
                                interpolation (the four taps concatenated) */
-  int hidden_layers;        /* hidden layers with activations: 2, or 3 (Sec. 4.4's
-                               "three remaining layers"): a third hidden layer
-                               wm, bm between w2 and the output layer w3 */
+  int hidden_layers;        /* hidden layers with activations: 2, or 3 (Sec. 4.4
+                               gives activations to three layers after the
+                               first): a third hidden layer wm, bm between w2
+                               and the output layer w3 */
   const double *wm, *bm;    /* [hidden][hidden], [hidden] (hidden_layers == 3) */
   int vq_g0;                /* G0 holds vector-quantised values: the training noise
                                applies to G1 only */

@@ -29,7 +29,8 @@ ACT_RELU, ACT_HARDGELU = 0, 1
 OUT_SIGMOID, OUT_IDENTITY = 0, 1
 FILTER_NEAREST, FILTER_TRILINEAR, FILTER_STOCHASTIC = 0, 1, 2
 INTERP_BILINEAR, INTERP_LEARNED = 0, 1
-DTYPE_F32, DTYPE_F16 = 0, 1
+DTYPE_F32, DTYPE_F16, DTYPE_U8 = 0, 1, 2
+_OUT_DTYPES = {torch.float32: DTYPE_F32, torch.float16: DTYPE_F16, torch.uint8: DTYPE_U8}
 FLAG_NOISE, FLAG_FREEZE_GRIDS, FLAG_NO_NOISE, FLAG_SIMT, FLAG_GRAD_ONLY = 0x1, 0x2, 0x4, 0x8, 0x10
 FLAG_CROPS = 0x20
 
@@ -275,6 +276,13 @@ class Material:
         return m
 
 
+def _out_dtype(t: torch.Tensor) -> int:
+    """Output tensor dtype -> NTC_DTYPE_* (float32, float16, uint8 UNORM)."""
+    if t.dtype not in _OUT_DTYPES:
+        raise TypeError(f"output dtype {t.dtype}: float32, float16 or uint8")
+    return _OUT_DTYPES[t.dtype]
+
+
 # ----------------------------------------------------------------------------
 # entry points (same names as the C ABI)
 # ----------------------------------------------------------------------------
@@ -285,7 +293,7 @@ def ntc_decode(mat: Material, uvl: torch.Tensor, out_dtype=torch.float32,
     n = uvl.shape[0]
     if out is None:
         out = torch.empty((n, mat.channels), dtype=out_dtype, device=uvl.device)
-    dt = DTYPE_F16 if out.dtype == torch.float16 else DTYPE_F32
+    dt = _out_dtype(out)
     s = mat.struct
     _call("ntc_decode", C.byref(s), _ptr(uvl), n, _ptr(out), dt, filter, flags, noise_seed,
           noise_step, _stream(stream))
@@ -306,7 +314,7 @@ def ntc_decode_host(mat: Material, uvl_host: torch.Tensor, out_host=None, out_dt
         out_host = torch.empty((n, mat.channels), dtype=out_dtype, pin_memory=True)
     if out_host.is_cuda or not out_host.is_contiguous():
         raise ValueError("out_host must be a contiguous host tensor")
-    dt = DTYPE_F16 if out_host.dtype == torch.float16 else DTYPE_F32
+    dt = _out_dtype(out_host)
     if workspace is None:
         nbytes = lib().ntc_decode_host_workspace_bytes(mat.channels, dt, chunk)
         workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
@@ -340,7 +348,7 @@ def ntc_autotune_decode(mat: Material, uvl, out, filter=FILTER_NEAREST, stream=N
     (best warpgroups, {shape: ms per launch})."""
     best = C.c_int32(0)
     ms = (C.c_float * 4)()
-    dt = DTYPE_F16 if out.dtype == torch.float16 else DTYPE_F32
+    dt = _out_dtype(out)
     s = mat.struct
     _call("ntc_autotune_decode", C.byref(s), _ptr(uvl), uvl.shape[0], _ptr(out), dt, filter,
           C.byref(best), C.cast(ms, C.c_void_p), _stream(stream))
@@ -443,7 +451,7 @@ def ntc_decode_batched(batch: Batch, uvl, out_dtype=torch.float32, out=None, str
     _dev(uvl, "uvl")
     if out is None:
         out = torch.empty(int(batch.desc.total_outputs), dtype=out_dtype, device=uvl.device)
-    dt = DTYPE_F16 if out.dtype == torch.float16 else DTYPE_F32
+    dt = _out_dtype(out)
     _call("ntc_decode_batched", C.byref(batch.desc), _ptr(uvl), _ptr(out), dt, _stream(stream))
     return out
 

@@ -132,6 +132,11 @@ struct HostPipe {
 std::mutex g_pipe_mu;
 HostPipe g_pipes[64];
 
+bool out_dtype_ok(int32_t d) {
+  return d == NTC_DTYPE_F32 || d == NTC_DTYPE_F16 || d == NTC_DTYPE_U8;
+}
+size_t out_elem_bytes(int32_t d) { return d == NTC_DTYPE_U8 ? 1 : (d == NTC_DTYPE_F16 ? 2 : 4); }
+
 bool use_simt(const ntc_material* m, int flags) {
   return (flags & NTC_FLAG_SIMT) || m->precision == NTC_PREC_F32;
 }
@@ -233,7 +238,7 @@ int ntc_decode(const ntc_material* m, const float* uvl, int64_t n, void* out, in
   int st = check_material(m, (flags & NTC_FLAG_NOISE) != 0);
   if (st) return st;
   if (n < 0) return fail(NTC_ERR_ARG, "n < 0");
-  if (out_dtype != NTC_DTYPE_F32 && out_dtype != NTC_DTYPE_F16) return fail(NTC_ERR_ARG, "out_dtype");
+  if (!out_dtype_ok(out_dtype)) return fail(NTC_ERR_ARG, "out_dtype %d", out_dtype);
   if (filter != NTC_FILTER_NEAREST && filter != NTC_FILTER_TRILINEAR &&
       filter != NTC_FILTER_STOCHASTIC)
     return fail(NTC_ERR_ARG, "filter");
@@ -247,8 +252,8 @@ int ntc_decode(const ntc_material* m, const float* uvl, int64_t n, void* out, in
 }
 
 size_t ntc_decode_host_workspace_bytes(int32_t channels, int32_t out_dtype, int64_t chunk) {
-  if (channels < 1 || channels > NTC_MAX_CHANNELS || chunk < 0) return 0;
-  const size_t eb = out_dtype == NTC_DTYPE_F16 ? 2 : 4;
+  if (channels < 1 || channels > NTC_MAX_CHANNELS || chunk < 0 || !out_dtype_ok(out_dtype)) return 0;
+  const size_t eb = out_elem_bytes(out_dtype);
   return 2 * (size_t)chunk * (12 + (size_t)channels * eb);
 }
 
@@ -258,7 +263,7 @@ int ntc_decode_host(const ntc_material* m, const float* uvl_host, int64_t n, voi
   int st = check_material(m, (flags & NTC_FLAG_NOISE) != 0);
   if (st) return st;
   if (n < 0) return fail(NTC_ERR_ARG, "n < 0");
-  if (out_dtype != NTC_DTYPE_F32 && out_dtype != NTC_DTYPE_F16) return fail(NTC_ERR_ARG, "out_dtype");
+  if (!out_dtype_ok(out_dtype)) return fail(NTC_ERR_ARG, "out_dtype %d", out_dtype);
   if (filter == NTC_FILTER_STOCHASTIC)
     return fail(NTC_ERR_UNSUPPORTED, "decode_host: nearest or trilinear filtering");
   if (filter != NTC_FILTER_NEAREST && filter != NTC_FILTER_TRILINEAR)
@@ -268,7 +273,7 @@ int ntc_decode_host(const ntc_material* m, const float* uvl_host, int64_t n, voi
   if (n == 0) return NTC_OK;
   if (!uvl_host || !out_host) return fail(NTC_ERR_ARG, "host buffer is NULL");
   CHECK_PTR(workspace, "workspace");
-  const size_t eb = out_dtype == NTC_DTYPE_F16 ? 2 : 4, C = (size_t)m->channels;
+  const size_t eb = out_elem_bytes(out_dtype), C = (size_t)m->channels;
   const size_t per = 12 + C * eb;
   const int64_t chunk = (int64_t)(workspace_bytes / (2 * per)) / 128 * 128;
   if (chunk < 128) return fail(NTC_ERR_ARG, "decode_host: workspace below two 128-query chunks");
@@ -335,6 +340,10 @@ int ntc_autotune_decode(const ntc_material* m, const float* uvl, int64_t n, void
   if (st) return st;
   if (m->precision == NTC_PREC_F32) return fail(NTC_ERR_ARG, "the FP32 form has no launch shapes");
   if (n <= 0) return fail(NTC_ERR_ARG, "n must be positive");
+  if (!out_dtype_ok(out_dtype)) return fail(NTC_ERR_ARG, "out_dtype %d", out_dtype);
+  if (filter != NTC_FILTER_NEAREST && filter != NTC_FILTER_TRILINEAR &&
+      filter != NTC_FILTER_STOCHASTIC)
+    return fail(NTC_ERR_ARG, "filter");
   CHECK_PTR(uvl, "uvl");
   CHECK_PTR(out, "out");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -673,7 +682,7 @@ int ntc_batch_prepare(const ntc_material* mats, const int64_t* n_queries, int32_
 int ntc_decode_batched(const ntc_batch* batch, const float* uvl, void* out, int32_t out_dtype,
                        void* stream) {
   if (!batch || !batch->workspace) return fail(NTC_ERR_ARG, "batch is not prepared");
-  if (out_dtype != NTC_DTYPE_F32 && out_dtype != NTC_DTYPE_F16) return fail(NTC_ERR_ARG, "out_dtype");
+  if (!out_dtype_ok(out_dtype)) return fail(NTC_ERR_ARG, "out_dtype %d", out_dtype);
   if (batch->total_queries == 0) return NTC_OK;
   CHECK_PTR(uvl, "uvl");
   CHECK_PTR(out, "out");

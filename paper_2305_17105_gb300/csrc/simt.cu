@@ -215,6 +215,11 @@ __global__ void __launch_bounds__(kThreads) decode_simt_kernel(
 #pragma unroll
       for (int c = 0; c < kMaxC; ++c)
         if (c < C) o[c] = y[c];
+    } else if (out_dtype == NTC_DTYPE_U8) {
+      uint8_t* o = static_cast<uint8_t*>(out) + q * C;
+#pragma unroll
+      for (int c = 0; c < kMaxC; ++c)
+        if (c < C) o[c] = (uint8_t)__float2uint_rn(__saturatef(y[c]) * 255.f);
     } else {
       __half* o = static_cast<__half*>(out) + q * C;
 #pragma unroll

@@ -890,10 +890,33 @@ __device__ __forceinline__ void out_activate(float (&yv)[16], int out_act) {
   }
 }
 
-// One texel's C outputs (FP16 or FP32) at output row q.
+// 8-bit UNORM of four outputs, packed low byte first: rn(sat(y) 255).
+__device__ __forceinline__ uint32_t unorm8x4(float a, float b, float c, float d) {
+  return __float2uint_rn(__saturatef(a) * 255.f) | (__float2uint_rn(__saturatef(b) * 255.f) << 8) |
+         (__float2uint_rn(__saturatef(c) * 255.f) << 16) |
+         (__float2uint_rn(__saturatef(d) * 255.f) << 24);
+}
+
+// One texel's C outputs (FP16, FP32 or 8-bit UNORM) at output row q.
 __device__ __forceinline__ void store_texel(void* out, int out_dtype, int64_t q, int C,
                                             const float (&yv)[16]) {
-  if (out_dtype == NTC_DTYPE_F16) {
+  if (out_dtype == NTC_DTYPE_U8) {
+    uint8_t* o = static_cast<uint8_t*>(out) + q * C;
+    uint32_t w[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) w[j] = unorm8x4(yv[4 * j], yv[4 * j + 1], yv[4 * j + 2], yv[4 * j + 3]);
+    if (C == 16) {
+      *reinterpret_cast<uint4*>(o) = make_uint4(w[0], w[1], w[2], w[3]);
+    } else if ((C & 3) == 0) {
+#pragma unroll
+      for (int c = 0; c < 16; c += 4)
+        if (c < C) *reinterpret_cast<uint32_t*>(o + c) = w[c >> 2];
+    } else {
+#pragma unroll
+      for (int c = 0; c < 16; ++c)
+        if (c < C) o[c] = (uint8_t)(w[c >> 2] >> (8 * (c & 3)));
+    }
+  } else if (out_dtype == NTC_DTYPE_F16) {
     __half* o = static_cast<__half*>(out) + q * C;
     if (C == 16) {
       uint4 a, b;

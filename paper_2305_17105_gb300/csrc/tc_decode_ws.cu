@@ -253,10 +253,15 @@ __global__ void __launch_bounds__(kWsThreads, 1) decode_ws_batched_kernel(
       }
       const int C = M.channels;
       if (valid && (!tri || (row & 7) == 0)) {
-        // vector stores need the material's output block 8-element aligned
-        if ((obase & 7) == 0) {
-          store_texel(static_cast<uint8_t*>(out) + obase * (out_dtype == NTC_DTYPE_F16 ? 2 : 4),
-                      out_dtype, ql, C, yv);
+        // vector stores need the material's output block 16-byte aligned
+        const int eb = out_dtype == NTC_DTYPE_U8 ? 1 : (out_dtype == NTC_DTYPE_F16 ? 2 : 4);
+        if (((obase * eb) & 15) == 0) {
+          store_texel(static_cast<uint8_t*>(out) + obase * eb, out_dtype, ql, C, yv);
+        } else if (out_dtype == NTC_DTYPE_U8) {
+          uint8_t* o = static_cast<uint8_t*>(out) + obase + ql * C;
+#pragma unroll
+          for (int c = 0; c < 16; ++c)
+            if (c < C) o[c] = (uint8_t)__float2uint_rn(__saturatef(yv[c]) * 255.f);
         } else if (out_dtype == NTC_DTYPE_F16) {
           __half* o = static_cast<__half*>(out) + obase + ql * C;
 #pragma unroll

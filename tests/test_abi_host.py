@@ -7,6 +7,7 @@ import os
 import re
 
 import pytest
+import torch
 
 import oracle
 import paper_2305_17105_gb300 as ntc
@@ -138,6 +139,8 @@ def test_decode_host_validation(L):
     ok = L.ntc_decode_host_workspace_bytes(4, ntc.DTYPE_F16, 128)
     assert ok == 2 * 128 * (12 + 4 * 2)
     assert L.ntc_decode_host_workspace_bytes(0, 0, 128) == 0
+    assert L.ntc_decode_host_workspace_bytes(4, ntc.DTYPE_U8, 128) == 2 * 128 * (12 + 4)
+    assert L.ntc_decode_host_workspace_bytes(4, 3, 128) == 0
     args = lambda **kw: dict(dict(uvl=C.addressof(host), n=10, out=C.addressof(host), dt=0, f=0,
                                   ws=0x50000, wsb=ok * 2), **kw)
     def rc(a):
@@ -166,6 +169,7 @@ def test_pointer_validation(L):
     assert _decode_rc(L, m, n=5) == ntc.ERR_ALIGN
     assert _decode_rc(L, _fake_material(), n=-1) == ntc.ERR_ARG
     assert _decode_rc(L, _fake_material(), n=5, out_dtype=9) == ntc.ERR_ARG
+    assert _decode_rc(L, _fake_material(), n=5, out_dtype=3) == ntc.ERR_ARG
     assert _decode_rc(L, _fake_material(), n=5, filt=9) == ntc.ERR_ARG
     # noise needs F32 grids
     assert _decode_rc(L, _fake_material(), n=5, flags=ntc.FLAG_NOISE) == ntc.ERR_ARG
@@ -210,3 +214,23 @@ def test_quantize_and_sampler_validation(L):
     assert L.ntc_sample_batch(1, 0, 0, 64, 64, 7, 0x1000, None) == ntc.OK
     assert L.ntc_sample_crops(1, 0, 10, 48, 64, 7, 0x1000, None) == ntc.ERR_ARG
     assert L.ntc_sample_crops(1, 0, 0, 64, 64, 7, 0x1000, None) == ntc.OK
+
+
+def test_autotune_validation(L):
+    L.ntc_autotune_decode.restype = C.c_int
+    L.ntc_autotune_decode.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int32,
+                                      C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]
+    best = C.c_int32(0)
+    m = C.byref(_fake_material())
+    rc = lambda dt=0, f=0, n=5: L.ntc_autotune_decode(m, 0x30000, n, 0x40000, dt, f,
+                                                       C.byref(best), None, None)
+    assert rc(dt=3) == ntc.ERR_ARG
+    assert rc(f=9) == ntc.ERR_ARG
+    assert rc(n=0) == ntc.ERR_ARG
+
+
+def test_binding_rejects_unknown_output_dtype():
+    for dt in (torch.float64, torch.int32, torch.bfloat16):
+        with pytest.raises(TypeError):
+            ntc._out_dtype(torch.empty(1, dtype=dt))
+    assert ntc._out_dtype(torch.empty(1, dtype=torch.uint8)) == ntc.DTYPE_U8

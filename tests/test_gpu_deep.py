@@ -1,4 +1,4 @@
-"""Three hidden layers (Sec. 4.4: activations on "three remaining layers",
+"""Three hidden layers (Sec. 4.4 gives activations to three layers after the first;
 the network sizes of Table 5): K -> 64 -> 64 -> 64 -> C.  Parity with the
 FP64 oracle of the same model: FP32 and FP16 (warp-specialised) decode with
 every filter, FP16 tensor-core training gradients (bilinear ReLU, and the
