@@ -860,9 +860,9 @@ def main():
                 "peak_source": "measured bf16 burst" + (" x 2 (fp8 nominal ratio)" if precision == "f8" else "")}
     roof["frac"] = roof["achieved"] / roof["peak"]
     # DRAM bytes per launch of decode_ws_kernel from the committed ncu capture
-    # of the FP16 kernel (141.59 MB at 2^22 queries, scaled by the query
+    # of the FP16 kernel (141.50 MB at 2^22 queries, scaled by the query
     # count); null for another precision or launch shape
-    roof["traffic"] = (141.59e6 * args.queries / (1 << 22)
+    roof["traffic"] = (141.50e6 * args.queries / (1 << 22)
                        if precision == "f16" and tuning and tuning["decode_warpgroups"] == 5 else None)
     roof["traffic_unit"] = "bytes"
     dec_bytes = args.queries * (12 + DEC_C * 2)
