@@ -153,9 +153,26 @@ def _stream(stream=None):
     return C.c_void_p(s.cuda_stream)
 
 
-def _dev(t: torch.Tensor, name: str):
-    if not t.is_cuda:
-        raise ValueError(f"{name} must be a CUDA tensor")
+def _queries(t: torch.Tensor, name="uvl", cuda=True) -> int:
+    """Check a ``[n, 3]`` float32 contiguous query tensor; returns n."""
+    if t.dtype != torch.float32 or t.dim() != 2 or t.shape[1] != 3:
+        raise ValueError(f"{name} must be an [n, 3] float32 tensor, got {tuple(t.shape)} {t.dtype}")
+    if t.is_cuda != cuda:
+        raise ValueError(f"{name} must be a {'CUDA' if cuda else 'host'} tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t.shape[0]
+
+
+def _room(t: torch.Tensor, name: str, elems: int, cuda=True, dtype=None):
+    """Check that ``t`` (contiguous, on the right side) holds ``elems``
+    elements (of ``dtype`` when given): the library writes that many."""
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if t.numel() < elems:
+        raise ValueError(f"{name} holds {t.numel()} elements, the call uses {elems}")
+    if t.is_cuda != cuda:
+        raise ValueError(f"{name} must be a {'CUDA' if cuda else 'host'} tensor")
     if not t.is_contiguous():
         raise ValueError(f"{name} must be contiguous")
     return t
@@ -289,11 +306,11 @@ def _out_dtype(t: torch.Tensor) -> int:
 def ntc_decode(mat: Material, uvl: torch.Tensor, out_dtype=torch.float32,
                filter=FILTER_NEAREST, flags=0, noise_seed=0, noise_step=0, out=None, stream=None):
     """Decode ``uvl`` ``[n, 3]`` float32 queries -> ``[n, channels]``."""
-    _dev(uvl, "uvl")
-    n = uvl.shape[0]
+    n = _queries(uvl)
     if out is None:
         out = torch.empty((n, mat.channels), dtype=out_dtype, device=uvl.device)
     dt = _out_dtype(out)
+    _room(out, "out", n * mat.channels)
     s = mat.struct
     _call("ntc_decode", C.byref(s), _ptr(uvl), n, _ptr(out), dt, filter, flags, noise_seed,
           noise_step, _stream(stream))
@@ -307,17 +324,15 @@ def ntc_decode_host(mat: Material, uvl_host: torch.Tensor, out_host=None, out_dt
     decode overlapped chunk by chunk through a device ``workspace`` (uint8
     CUDA tensor; allocated for ``chunk`` queries when None).  The output is
     complete once ``stream`` reaches this call's end."""
-    if uvl_host.is_cuda or not uvl_host.is_contiguous() or uvl_host.dtype != torch.float32:
-        raise ValueError("uvl_host must be a contiguous float32 host tensor")
-    n = uvl_host.shape[0]
+    n = _queries(uvl_host, "uvl_host", cuda=False)
     if out_host is None:
         out_host = torch.empty((n, mat.channels), dtype=out_dtype, pin_memory=True)
-    if out_host.is_cuda or not out_host.is_contiguous():
-        raise ValueError("out_host must be a contiguous host tensor")
     dt = _out_dtype(out_host)
+    _room(out_host, "out_host", n * mat.channels, cuda=False)
     if workspace is None:
         nbytes = lib().ntc_decode_host_workspace_bytes(mat.channels, dt, chunk)
         workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    _room(workspace, "workspace", 0, dtype=torch.uint8)
     s = mat.struct
     _call("ntc_decode_host", C.byref(s), C.c_void_p(uvl_host.data_ptr()), n,
           C.c_void_p(out_host.data_ptr()), dt, filter, flags, noise_seed, noise_step,
@@ -329,10 +344,12 @@ def ntc_vq_assign(values: torch.Tensor, codebooks: torch.Tensor, stream=None) ->
     """Greedy residual vector quantisation of ``values`` ``[cells, c0]``
     against ``codebooks`` ``[books, 256, c0]`` (CUDA float32) -> uint8
     indices ``[cells, books]``."""
-    _dev(values, "values")
-    _dev(codebooks, "codebooks")
+    if values.dim() != 2 or codebooks.dim() != 3 or codebooks.shape[1:] != (256, values.shape[1]):
+        raise ValueError("values [cells, c0] and codebooks [books, 256, c0] expected")
     cells, c0 = values.shape
     books = codebooks.shape[0]
+    _room(values, "values", cells * c0, dtype=torch.float32)
+    _room(codebooks, "codebooks", books * 256 * c0, dtype=torch.float32)
     idx = torch.empty((cells, books), dtype=torch.uint8, device=values.device)
     _call("ntc_vq_assign", _ptr(values), cells, c0, _ptr(codebooks), books, _ptr(idx),
           _stream(stream))
@@ -348,9 +365,11 @@ def ntc_autotune_decode(mat: Material, uvl, out, filter=FILTER_NEAREST, stream=N
     (best warpgroups, {shape: ms per launch})."""
     best = C.c_int32(0)
     ms = (C.c_float * 4)()
+    n = _queries(uvl)
     dt = _out_dtype(out)
+    _room(out, "out", n * mat.channels)
     s = mat.struct
-    _call("ntc_autotune_decode", C.byref(s), _ptr(uvl), uvl.shape[0], _ptr(out), dt, filter,
+    _call("ntc_autotune_decode", C.byref(s), _ptr(uvl), n, _ptr(out), dt, filter,
           C.byref(best), C.cast(ms, C.c_void_p), _stream(stream))
     return best.value, {2: ms[0], 3: ms[1], 4: ms[2], 5: ms[3]}
 
@@ -379,19 +398,23 @@ def grads_struct(mat: Material, grid0=None, grid1=None, w=None, b=None) -> ntc_g
 def ntc_backward(mat: Material, uvl, dout, grads: ntc_grads, flags=0, noise_seed=0, noise_step=0,
                  stream=None):
     """Accumulate d(sum dout*y)/d(grids, weights) into ``grads``."""
-    _dev(uvl, "uvl")
-    _dev(dout, "dout")
+    n = _queries(uvl)
+    _room(dout, "dout", n * mat.channels, dtype=torch.float32)
     s = mat.struct
-    _call("ntc_backward", C.byref(s), _ptr(uvl), uvl.shape[0], _ptr(dout), C.byref(grads), flags,
+    _call("ntc_backward", C.byref(s), _ptr(uvl), n, _ptr(dout), C.byref(grads), flags,
           noise_seed, noise_step, _stream(stream))
 
 
 def ntc_quantize_pack(values: torch.Tensor, c: int, bits: int, q: float, packed=None, snapped=None,
                       want_packed=True, stream=None):
-    _dev(values, "values")
+    _room(values, "values", 0, dtype=torch.float32)
     cells = values.numel() // c
     if packed is None and want_packed:
         packed = torch.empty((cells, cell_bytes(c, bits)), dtype=torch.uint8, device=values.device)
+    if packed is not None:
+        _room(packed, "packed", cells * cell_bytes(c, bits), dtype=torch.uint8)
+    if snapped is not None:
+        _room(snapped, "snapped", cells * c, dtype=torch.float32)
     _call("ntc_quantize_pack", _ptr(values), cells, c, bits, q, _ptr(packed), _ptr(snapped),
           _stream(stream))
     return packed
@@ -399,7 +422,7 @@ def ntc_quantize_pack(values: torch.Tensor, c: int, bits: int, q: float, packed=
 
 def ntc_unpack(packed: torch.Tensor, c: int, bits: int, q: float, want_idx=True, want_values=True,
                stream=None):
-    _dev(packed, "packed")
+    _room(packed, "packed", 0, dtype=torch.uint8)
     cells = packed.numel() // cell_bytes(c, bits)
     idx = torch.empty((cells, c), dtype=torch.int32, device=packed.device) if want_idx else None
     val = torch.empty((cells, c), dtype=torch.float32, device=packed.device) if want_values else None
@@ -416,7 +439,7 @@ def ntc_sample_batch(seed: int, step: int, batch: int, width: int, height: int, 
 
 
 def ntc_sample_features(mat: Material, uvl, flags=0, noise_seed=0, noise_step=0, stream=None):
-    _dev(uvl, "uvl")
+    _queries(uvl)
     rows = torch.empty((uvl.shape[0], mat.k_in), dtype=torch.float32, device=uvl.device)
     s = mat.struct
     _call("ntc_sample_features", C.byref(s), _ptr(uvl), uvl.shape[0], _ptr(rows), flags,
@@ -448,10 +471,11 @@ class Batch:
 
 
 def ntc_decode_batched(batch: Batch, uvl, out_dtype=torch.float32, out=None, stream=None):
-    _dev(uvl, "uvl")
+    _room(uvl, "uvl", 3 * int(batch.desc.total_queries), dtype=torch.float32)
     if out is None:
         out = torch.empty(int(batch.desc.total_outputs), dtype=out_dtype, device=uvl.device)
     dt = _out_dtype(out)
+    _room(out, "out", int(batch.desc.total_outputs))
     _call("ntc_decode_batched", C.byref(batch.desc), _ptr(uvl), _ptr(out), dt, _stream(stream))
     return out
 
@@ -591,6 +615,8 @@ class Target:
 def ntc_train_step(trainer: Trainer, target: Target, batch: int, seed: int, uvl=None, flags=0,
                    stream=None):
     """One fused optimisation step; returns the device loss tensor."""
+    if uvl is not None:
+        _room(uvl, "uvl", 3 * batch, dtype=torch.float32)
     m, t, tg = trainer.material.struct, trainer.struct, target.struct
     _call("ntc_train_step", C.byref(m), C.byref(t), C.byref(tg), batch, seed, _ptr(uvl),
           _ptr(trainer.loss), flags, _stream(stream))
@@ -601,6 +627,8 @@ def ntc_train_step_noalloc(trainer: Trainer, target: Target, batch: int, seed: i
                            flags=0, stream=None):
     """ntc_train_step with the scratch gradient in the library's static
     device array (no caller-provided gradient buffer; see include/ntc.h)."""
+    if uvl is not None:
+        _room(uvl, "uvl", 3 * batch, dtype=torch.float32)
     m, t, tg = trainer.material.struct, trainer.struct, target.struct
     t.grad = None
     _call("ntc_train_step_noalloc", C.byref(m), C.byref(t), C.byref(tg), batch, seed, _ptr(uvl),

@@ -234,3 +234,26 @@ def test_binding_rejects_unknown_output_dtype():
         with pytest.raises(TypeError):
             ntc._out_dtype(torch.empty(1, dtype=dt))
     assert ntc._out_dtype(torch.empty(1, dtype=torch.uint8)) == ntc.DTYPE_U8
+
+
+def test_binding_checks_shapes_before_any_launch():
+    """The binding refuses tensors the library would read or write past
+    their end, before it calls into the library (the host-side cases; the
+    device-buffer cases are GPU tests)."""
+    class M:
+        channels = 4
+        k_in = 32
+    with pytest.raises(ValueError, match=r"\[n, 3\] float32"):
+        ntc.ntc_decode(M, torch.zeros(10, 2))
+    with pytest.raises(ValueError, match=r"\[n, 3\] float32"):
+        ntc.ntc_decode(M, torch.zeros(10, 3, dtype=torch.float64))
+    with pytest.raises(ValueError, match="uvl must be a CUDA tensor"):
+        ntc.ntc_decode(M, torch.zeros(10, 3))
+    with pytest.raises(ValueError, match="uvl must be a CUDA tensor"):
+        ntc.ntc_backward(M, torch.zeros(10, 3), torch.zeros(40), None)
+    with pytest.raises(ValueError, match="the call uses 40"):
+        ntc.ntc_decode_host(M, torch.zeros(10, 3), out_host=torch.zeros(39))
+    with pytest.raises(TypeError):
+        ntc.ntc_decode_host(M, torch.zeros(10, 3), out_host=torch.zeros(40, dtype=torch.int16))
+    with pytest.raises(ValueError, match="codebooks"):
+        ntc.ntc_vq_assign(torch.zeros(5, 8), torch.zeros(2, 255, 8))

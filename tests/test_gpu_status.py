@@ -40,3 +40,33 @@ def test_selftest_limit_validation():
         ntc.ntc_selftest_wait(0)
     with pytest.raises(ntc.NTCError):
         ntc.ntc_selftest_wait((1 << 20) + 1)
+
+
+def test_binding_refuses_short_device_buffers():
+    """Buffers shorter than what the library would write (or read) are
+    refused by the binding before any launch; the outputs stay untouched."""
+    case = make_case(64, 64, 8, 8, 8, k_in=32, seed=95)
+    mat, md = device_material(case, precision=ntc.PREC_F16)
+    q = torch.from_numpy(gen.random_queries(100, md.mips, seed=4095)).to(DEV)
+    short = torch.full((799,), 7.0, device=DEV)
+    with pytest.raises(ValueError, match="the call uses 800"):
+        ntc.ntc_decode(mat, q, out=short)
+    with pytest.raises(ValueError, match="the call uses 800"):
+        ntc.ntc_autotune_decode(mat, q, short)
+    with pytest.raises(ValueError, match="the call uses 800"):
+        ntc.ntc_backward(mat, q, short, ntc.grads_struct(mat))
+    with pytest.raises(ValueError, match=r"\[n, 3\] float32"):
+        ntc.ntc_decode(mat, q[:, :2].contiguous())
+    with pytest.raises(ValueError, match="contiguous"):
+        ntc.ntc_decode(mat, q.t().contiguous().t())
+    with pytest.raises(ValueError, match="the call uses"):
+        ntc.ntc_quantize_pack(torch.zeros(64, device=DEV), 4, 4, 0.25,
+                              packed=torch.zeros(1, dtype=torch.uint8, device=DEV))
+    batch = ntc.Batch([mat], [100])
+    with pytest.raises(ValueError, match="uvl holds"):
+        ntc.ntc_decode_batched(batch, q[:99])
+    with pytest.raises(ValueError, match="the call uses 800"):
+        ntc.ntc_decode_batched(batch, q, out=short)
+    torch.cuda.synchronize()
+    assert bool((short == 7.0).all())
+    assert ntc.ntc_device_status() == ntc.OK
