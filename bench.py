@@ -925,6 +925,25 @@ def main():
                "path": "ntc_decode_host (pinned host buffers, chunks of 2^20 queries, copies "
                        "overlapped with the decode) + ntc_train_step on a second stream + loss "
                        "read back, joined every step"}
+        # this machine's host link (plain pinned copies of the step's output and
+        # inputs), which bounds the end-to-end figure
+        try:
+            link = {}
+            for name, fn, nb in (
+                    ("d2h_gbs", lambda: out_host.copy_(out, non_blocking=True), out.numel() * 2),
+                    ("h2d_gbs", lambda: q_dev.copy_(q_host, non_blocking=True), q_host.numel() * 4)):
+                fn()
+                torch.cuda.synchronize()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                for _ in range(3):
+                    fn()
+                b.record(stream)
+                torch.cuda.synchronize()
+                link[name] = 3 * nb / (a.elapsed_time(b) / 1e3) / 1e9
+            e2e["host_link"] = link
+        except Exception as e:  # reported, never fatal to the headline line
+            e2e["host_link"] = {"error": f"{type(e).__name__}: {e}"[:300]}
 
     # ---- the paper's crop sampler on the same trainer (Sec. 5.1) ----------
     crops = None
