@@ -59,7 +59,7 @@ class _Model(C.Structure):
         ("w1", C.c_void_p), ("b1", C.c_void_p), ("w2", C.c_void_p), ("b2", C.c_void_p),
         ("w3", C.c_void_p), ("b3", C.c_void_p), ("interp0", C.c_int),
         ("hidden_layers", C.c_int), ("wm", C.c_void_p), ("bm", C.c_void_p),
-        ("vq_g0", C.c_int),
+        ("vq_g0", C.c_int), ("f8_sa", C.c_void_p),
     ]
 
 
@@ -71,7 +71,7 @@ class _Grads(C.Structure):
     _fields_ = [("grid0", C.c_void_p * MAX_LEVELS), ("grid1", C.c_void_p * MAX_LEVELS),
                 ("w1", C.c_void_p), ("b1", C.c_void_p), ("w2", C.c_void_p),
                 ("b2", C.c_void_p), ("w3", C.c_void_p), ("b3", C.c_void_p),
-                ("wm", C.c_void_p), ("bm", C.c_void_p)]
+                ("wm", C.c_void_p), ("bm", C.c_void_p), ("rows", C.c_void_p)]
 
 
 def _declare(L):
@@ -100,6 +100,7 @@ def _declare(L):
         "or_decode_trilinear": (None, [P, I64, P, P, I]),
         "or_decode_stochastic": (None, [P, I64, P, C.c_uint64, I64, P, I]),
         "or_backward_xym": (None, [P, I64, P, P, P, P, I]),
+        "or_round_e4m3": (D, [D]),
         "or_loss_grad_xym": (D, [P, I64, P, P, P, P, I]),
         "or_cosine_lr": (D, [D, I64, I64]),
         "or_adam": (None, [P, P, P, P, I64, D, I64, D, D, D, I, D, D]),
@@ -384,6 +385,25 @@ class Model:
             x = 1.0 / (1.0 + np.exp(-x))
         return x
 
+    def f8_form(self, s_w, s_a):
+        """The FP8-E4M3 training and decode form of this model: every weight
+        matrix replaced by s_w[l] e4m3(W_l / s_w[l]) (biases unchanged) and
+        every layer input used as s_a[l] e4m3(v / s_a[l]) inside the C
+        forward.  Its reverse mode is straight-through: each rounding counts
+        as the identity, the weight gradients use the rounded inputs, and the
+        returned weight gradients are those of the quantised weights (which a
+        trainer applies to its master weights).  Two hidden layers."""
+        assert self.hidden_layers == 2, "the FP8 form has two hidden layers"
+        w = list(self.weights)
+        for l in range(3):
+            w[2 * l] = s_w[l] * np.vectorize(lib().or_round_e4m3)(w[2 * l] / s_w[l])
+        f8 = Model(self.width, self.height, self.channels, self.c0, self.c1, self.n0, self.n1,
+                   self.q0, self.q1, self.grids0, self.grids1, w, self.k_in, self.hidden,
+                   self.act, self.out_act, self.interp0, bool(self.vq_g0))
+        f8._sa = np.ascontiguousarray(s_a, np.float64).reshape(3)
+        f8._s.f8_sa = f8._sa.ctypes.data
+        return f8
+
     def decode_xym(self, xym, noise=None, threads=None):
         xym = np.ascontiguousarray(xym, np.int32).reshape(-1, 3)
         out = np.empty((xym.shape[0], self.channels), np.float64)
@@ -417,11 +437,14 @@ class Model:
                                    threads or default_threads())
         return out
 
-    def zero_grads(self):
+    def zero_grads(self, n_rows=None):
         g = {"grid0": [np.zeros_like(a) for a in self.grids0],
              "grid1": [np.zeros_like(a) for a in self.grids1],
              "w": [np.zeros_like(a) for a in self.weights]}
         s = _Grads()
+        if n_rows is not None:
+            g["rows"] = np.zeros((n_rows, self.k_in), np.float64)
+            s.rows = g["rows"].ctypes.data
         for j in range(self.levels):
             s.grid0[j] = g["grid0"][j].ctypes.data
             s.grid1[j] = g["grid1"][j].ctypes.data
@@ -433,22 +456,24 @@ class Model:
         g["_s"] = s
         return g
 
-    def backward_xym(self, xym, dout, noise=None, threads=None):
-        """Gradients of sum(dout * y) (exact reverse mode)."""
+    def backward_xym(self, xym, dout, noise=None, threads=None, rows=False):
+        """Gradients of sum(dout * y) (exact reverse mode; straight-through
+        in the FP8 form); ``rows``: also each texel's input-row gradient
+        (``g["rows"]``, ``[n, k_in]``)."""
         xym = np.ascontiguousarray(xym, np.int32).reshape(-1, 3)
         dout = np.ascontiguousarray(dout, np.float64).reshape(xym.shape[0], self.channels)
-        g = self.zero_grads()
+        g = self.zero_grads(xym.shape[0] if rows else None)
         _, nz = self._noise(noise)
         lib().or_backward_xym(C.byref(self._s), xym.shape[0], _p(xym), _p(dout), nz,
                               C.byref(g["_s"]), threads or default_threads())
         return g
 
-    def loss_grad_xym(self, xym, target, noise=None, threads=None):
+    def loss_grad_xym(self, xym, target, noise=None, threads=None, rows=False):
         """L2 loss (Sec. 4.5) and its gradients for texels ``xym`` with
         ``target`` ``[n, c]`` in [0, 1]."""
         xym = np.ascontiguousarray(xym, np.int32).reshape(-1, 3)
         target = np.ascontiguousarray(target, np.float64).reshape(xym.shape[0], self.channels)
-        g = self.zero_grads()
+        g = self.zero_grads(xym.shape[0] if rows else None)
         _, nz = self._noise(noise)
         loss = lib().or_loss_grad_xym(C.byref(self._s), xym.shape[0], _p(xym), _p(target), nz,
                                       C.byref(g["_s"]), threads or default_threads())

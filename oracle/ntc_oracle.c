@@ -360,14 +360,39 @@ static const double* last_hidden(const or_model* md, const mlp_buf* b) {
   return md->hidden_layers == 3 ? b->hm : b->h2;
 }
 
+/* Nearest FP8-E4M3 value: in the binade [2^e, 2^(e+1)) the values are the
+ * multiples of 2^(e-3) for e >= -6; below 2^-6 the subnormals are multiples
+ * of 2^-9; rint rounds half to even; magnitudes above 448 saturate. */
+double or_round_e4m3(double v) {
+  double a = fabs(v);
+  int e = 0;
+  frexp(a, &e); /* a = f 2^e, f in [0.5, 1) */
+  int ex = e - 1 < -6 ? -6 : e - 1;
+  double quantum = ldexp(1.0, ex - 3);
+  double r = rint(a / quantum) * quantum;
+  if (r > 448.0) r = 448.0;
+  return copysign(r, v);
+}
+
+/* FP8 form: a layer input used in units of its activation scale, rounded. */
+static void round_input(const or_model* md, int layer, double* v, int n) {
+  if (!md->f8_sa) return;
+  double s = md->f8_sa[layer];
+  for (int i = 0; i < n; ++i) v[i] = s * or_round_e4m3(v[i] / s);
+}
+
 /* Linear layers with hidden activations, then the output layer and its
- * activation (Sec. 4.4): two hidden layers, or three. */
+ * activation (Sec. 4.4): two hidden layers, or three.  In the FP8 form the
+ * buffers x, h1, h2 end up holding the rounded layer inputs. */
 static void mlp_forward(const or_model* md, mlp_buf* b) {
   int H = md->hidden, C = md->channels;
+  round_input(md, 0, b->x, md->k_in);
   linear(md->w1, md->b1, b->x, md->k_in, H, b->z1);
   for (int i = 0; i < H; ++i) b->h1[i] = act_f(md->act, b->z1[i]);
+  round_input(md, 1, b->h1, H);
   linear(md->w2, md->b2, b->h1, H, H, b->z2);
   for (int i = 0; i < H; ++i) b->h2[i] = act_f(md->act, b->z2[i]);
+  round_input(md, 2, b->h2, H);
   if (md->hidden_layers == 3) {
     linear(md->wm, md->bm, b->h2, H, H, b->zm);
     for (int i = 0; i < H; ++i) b->hm[i] = act_f(md->act, b->zm[i]);
@@ -406,6 +431,7 @@ typedef struct job_s {
   const or_noise* nz;
   double* out;
   or_grads g;       /* this thread's private accumulators */
+  double* rows;     /* the caller's per-texel input-row gradients, or NULL */
   double loss;
   uint64_t seed;    /* stochastic filtering: seed and frame of the jitter */
   int64_t step;
@@ -624,7 +650,7 @@ void or_decode_stochastic(const or_model* md, int64_t n, const float* uvl, uint6
  * a constant, so it passes gradients unchanged; clamping to the quantisation
  * range happens after the update (Sec. 4.2) and is not differentiated. */
 static void backward_one(const or_model* md, int x, int y, int m, const double* dy,
-                         const or_noise* nz, mlp_buf* b, const or_grads* g) {
+                         const or_noise* nz, mlp_buf* b, const or_grads* g, double* drow) {
   int K = md->k_in, H = md->hidden, C = md->channels;
   or_features(md, x, y, m, nz, b->x);
   mlp_forward(md, b);
@@ -684,6 +710,8 @@ static void backward_one(const or_model* md, int x, int y, int m, const double* 
     for (int o = 0; o < H; ++o) s += md->w1[(int64_t)o * K + i] * dz1[o];
     dx[i] = s;
   }
+  if (drow)
+    for (int i = 0; i < K; ++i) drow[i] = dx[i];
   /* scatter the feature part of dx back through the taps: bilinear weights,
    * or (learned interpolation of G0) each tap's own slots with weight 1 */
   int j = or_level_of_mip(m, md->levels);
@@ -748,7 +776,8 @@ static void backward_job(job* jb, int64_t lo, int64_t hi) {
   int C = jb->md->channels;
   for (int64_t i = lo; i < hi; ++i)
     backward_one(jb->md, jb->xym[3 * i], jb->xym[3 * i + 1], jb->xym[3 * i + 2],
-                 jb->dout + i * C, jb->nz, &b, &jb->g);
+                 jb->dout + i * C, jb->nz, &b, &jb->g,
+                 jb->rows ? jb->rows + i * jb->md->k_in : NULL);
   mlp_free(&b);
 }
 
@@ -758,7 +787,7 @@ void or_backward_xym(const or_model* md, int64_t n, const int32_t* xym, const do
   job* jobs = calloc((size_t)nthreads, sizeof(job));
   for (int t = 0; t < nthreads; ++t) {
     jobs[t].fn = backward_job; jobs[t].md = md; jobs[t].xym = xym; jobs[t].dout = dout;
-    jobs[t].nz = nz;
+    jobs[t].nz = nz; jobs[t].rows = g->rows;
     grads_alloc(md, &jobs[t].g);
   }
   run_jobs(jobs, nthreads, n);

@@ -44,6 +44,14 @@ typedef struct {
   const double *wm, *bm;    /* [hidden][hidden], [hidden] (hidden_layers == 3) */
   int vq_g0;                /* G0 holds vector-quantised values: the training noise
                                applies to G1 only */
+  const double* f8_sa;      /* FP8-E4M3 form (NULL: off): per-layer activation
+                               scales s_a[3]; every layer input v is used as
+                               s_a[l] e4m3(v / s_a[l]) (two hidden layers; the
+                               weights are given already quantised).  Reverse
+                               mode treats each rounding as the identity
+                               (straight-through), so the weight gradients see
+                               the rounded inputs and the input gradients pass
+                               through the roundings unchanged. */
 } or_model;
 
 /* Simulated-quantisation noise switch (Sec. 4.2). */
@@ -59,6 +67,8 @@ typedef struct {
   double* grid1[OR_MAX_LEVELS];
   double *w1, *b1, *w2, *b2, *w3, *b3;
   double *wm, *bm;          /* third hidden layer (hidden_layers == 3) */
+  double* rows;             /* nullable: [n][k_in] gradient of each texel's MLP
+                               input row (written, not accumulated) */
 } or_grads;
 
 /* --- pyramid (Sec. 4.1, Table 1) --- */
@@ -99,6 +109,10 @@ void or_decode_trilinear(const or_model* md, int64_t n, const float* uvl, double
  * jittered texel and mip of frame `step` (see ntc_oracle.c). */
 void or_decode_stochastic(const or_model* md, int64_t n, const float* uvl, uint64_t seed,
                           int64_t step, double* out, int nthreads);
+
+/* --- FP8-E4M3 (OCP 8-bit floating point: bias 7, 3 mantissa bits, ties to
+ * even, saturating at 448, no infinities) --- */
+double or_round_e4m3(double v);
 
 /* --- backward and loss (Sec. 4.5, 5.1) --- */
 void or_backward_xym(const or_model* md, int64_t n, const int32_t* xym, const double* dout,

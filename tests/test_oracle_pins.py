@@ -204,6 +204,149 @@ def test_decode_f8_structure():
     assert 0 < np.abs(f8 - ident).max() < 0.1
 
 
+def test_c_e4m3_rounding_against_torch():
+    """The C oracle's E4M3 rounding (used inside its FP8 forward) against
+    torch's float8_e4m3fn cast, bit for bit, and NaN/zero/sign handling."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(17)
+    x = (rng.standard_normal(50_000) * np.exp2(rng.integers(-14, 10, 50_000))).astype(np.float32)
+    x = x[np.abs(x) <= 448.0].astype(np.float64)
+    got = np.array([oracle.lib().or_round_e4m3(v) for v in x])
+    ref = torch.from_numpy(x.astype(np.float32)).to(torch.float8_e4m3fn).to(torch.float64).numpy()
+    assert np.array_equal(got, ref)
+    assert oracle.lib().or_round_e4m3(1e6) == 448.0 and oracle.lib().or_round_e4m3(-1e6) == -448.0
+    assert math.isnan(oracle.lib().or_round_e4m3(float("nan")))
+    assert math.copysign(1.0, oracle.lib().or_round_e4m3(-1e-9)) == -1.0
+
+
+def _f8_model(act, seed=21):
+    """A small material, its FP64 model and its FP8 form with power-of-two
+    scales: weights max |W| / s_w in (224, 448]; activation scales chosen
+    from the FP64 activations so that each layer meets a different part of
+    the E4M3 range (layer 0 normal values, layer 1 about 10% saturated,
+    layer 2 about half subnormal) -- with power-of-two scales the rounding
+    depends on the scale only at the range's ends."""
+    case = make_case(32, 32, 4, 4, 4, k_in=32, hidden=16, act=act, seed=seed, wgain=2.0)
+    md = case.oracle_model(quantized=False)
+    w = md.weights
+    s_w = [float(2.0 ** np.ceil(np.log2(np.abs(w[2 * l]).max() / 448.0))) for l in range(3)]
+    x = np.stack([md.features(a, b, m) for a, b, m in _texels(md, 200, seed)])
+    f = np.vectorize(lambda z: oracle.activation(act, z))
+    h1 = f(x @ w[0].T + w[1])
+    h2 = f(h1 @ w[2].T + w[3])
+    s_a = [float(2.0 ** np.ceil(np.log2(np.abs(x).max() / 448.0))),
+           float(2.0 ** np.floor(np.log2(np.quantile(np.abs(h1), 0.9) / 448.0))),
+           float(2.0 ** np.ceil(np.log2(np.quantile(np.abs(h2[h2 != 0]), 0.5) / 2.0 ** -6)))]
+    assert len(set(s_a)) == 3
+    return md, md.f8_form(s_w, s_a), s_w, s_a
+
+
+def _texels(md, n, seed):
+    rng = np.random.default_rng(seed)
+    return np.array([[rng.integers(0, md.width >> m), rng.integers(0, md.height >> m), m]
+                     for m in rng.integers(0, md.mips, size=n)], np.int32)
+
+
+def test_f8_form_forward_matches_python_decode_f8():
+    """The C oracle's FP8 forward (rounding inside the MLP) equals the
+    separately pinned Python FP8 decode of the same quantised weights, and
+    its weights are E4M3 multiples of s_w."""
+    md, f8, s_w, s_a = _f8_model(0)
+    q = np.random.default_rng(5).random((300, 3)).astype(np.float32)
+    q[:, 2] *= md.mips
+    a = f8.decode(q)
+    b = f8.decode_f8(q, s_w, s_a)
+    assert np.allclose(a, b, rtol=1e-12, atol=1e-14)
+    assert np.abs(a - md.decode(q)).max() > 1e-4          # the rounding is felt
+    for l in range(3):
+        w = f8.weights[2 * l] / s_w[l]
+        assert np.array_equal(oracle.round_e4m3(w), w) and np.abs(w).max() <= 448
+
+
+@pytest.mark.parametrize("act", [0, 1])
+def test_f8_form_gradients_are_straight_through(act):
+    """Reverse mode of the FP8 form against torch autograd (float64) of the
+    same forward written with the straight-through estimator
+    v + (s e4m3(v / s) - v).detach(): loss, every weight and bias gradient,
+    and each texel's input-row gradient."""
+    torch = pytest.importorskip("torch")
+    md, f8, s_w, s_a = _f8_model(act)
+    xym = _texels(md, 48, 6)
+    target = np.random.default_rng(7).random((48, 4))
+    noise = (99, 4)
+    loss, g = f8.loss_grad_xym(xym, target, noise=noise, rows=True)
+    X = torch.tensor(np.stack([f8.features(x, y, m, noise) for x, y, m in xym]),
+                     requires_grad=True)
+    W = [torch.tensor(w, requires_grad=True) for w in f8.weights]
+
+    def ste(v, s):
+        q = torch.from_numpy(s * oracle.round_e4m3(v.detach().numpy() / s))
+        return v + (q - v).detach()
+
+    def act_t(z):
+        if act == 0:
+            return torch.relu(z)
+        return torch.where(z < -1.5, torch.zeros_like(z),
+                           torch.where(z > 1.5, z, z / 3.0 * (z + 1.5)))
+
+    h = ste(X, s_a[0])
+    h = act_t(h @ W[0].T + W[1])
+    h = act_t(ste(h, s_a[1]) @ W[2].T + W[3])
+    y = torch.sigmoid(ste(h, s_a[2]) @ W[4].T + W[5])
+    lt = ((y - torch.from_numpy(target)) ** 2).mean()
+    lt.backward()
+    assert abs(loss - lt.item()) <= 1e-12 * lt.item()
+    for gw, wt in zip(g["w"], W):
+        assert np.allclose(gw, wt.grad.numpy(), rtol=1e-9, atol=1e-15)
+    assert np.allclose(g["rows"], X.grad.numpy(), rtol=1e-9, atol=1e-15)
+    assert np.abs(g["rows"]).max() > 0
+
+
+def test_f8_form_grid_gradient_is_the_transpose_of_the_features():
+    """The grid gradients are the row gradients pulled back through the
+    (linear) feature map: <dL/dgrid, d> = sum_i <dL/drow_i, rows_i(grid + d)
+    - rows_i(grid)> for a random direction d, noise on."""
+    md, f8, s_w, s_a = _f8_model(1, seed=22)
+    xym = _texels(md, 40, 8)
+    target = np.random.default_rng(9).random((40, 4))
+    noise = (7, 3)
+    _, g = f8.loss_grad_xym(xym, target, noise=noise, rows=True)
+    rng = np.random.default_rng(10)
+    grids = f8.grids0 + f8.grids1
+    d = [rng.standard_normal(a.shape) for a in grids]
+    r0 = np.stack([f8.features(x, y, m, noise) for x, y, m in xym])
+    for a, da in zip(grids, d):
+        a += da
+    r1 = np.stack([f8.features(x, y, m, noise) for x, y, m in xym])
+    for a, da in zip(grids, d):
+        a -= da
+    lhs = sum(np.sum(ga * da) for ga, da in zip(g["grid0"] + g["grid1"], d))
+    rhs = np.sum(g["rows"] * (r1 - r0))
+    assert abs(lhs - rhs) <= 1e-9 * max(abs(rhs), 1e-12)
+    assert abs(rhs) > 0
+
+
+def test_f8_form_output_layer_matches_central_differences():
+    """The output layer's input is rounded before W3 and b3 act, so the loss
+    is smooth in them and central differences must equal the reverse mode
+    (a weight gradient formed with the unrounded input would not)."""
+    md, f8, s_w, s_a = _f8_model(0, seed=23)
+    xym = _texels(md, 32, 11)
+    target = np.random.default_rng(12).random((32, 4))
+    _, g = f8.loss_grad_xym(xym, target)
+    h = 1e-6
+    for li in (4, 5):
+        p, gp = f8.weights[li].reshape(-1), g["w"][li].reshape(-1)
+        for k in np.random.default_rng(li).choice(p.size, size=min(p.size, 24), replace=False):
+            old = p[k]
+            p[k] = old + h
+            lp, _ = f8.loss_grad_xym(xym, target)
+            p[k] = old - h
+            lm, _ = f8.loss_grad_xym(xym, target)
+            p[k] = old
+            assert abs((lp - lm) / (2 * h) - gp[k]) <= 1e-6 * max(abs(gp[k]), 1e-8), (li, k)
+
+
 def test_vq_reconstruct_by_hand():
     """A vector-quantised cell is the sum of the entries its indices select."""
     cb = np.zeros((2, 256, 2))
