@@ -257,3 +257,69 @@ def test_binding_checks_shapes_before_any_launch():
         ntc.ntc_decode_host(M, torch.zeros(10, 3), out_host=torch.zeros(40, dtype=torch.int16))
     with pytest.raises(ValueError, match="codebooks"):
         ntc.ntc_vq_assign(torch.zeros(5, 8), torch.zeros(2, 255, 8))
+
+
+def test_backward_validation(L):
+    g = ntc.ntc_grads()
+    m32 = _fake_material(encoding=ntc.GRID_F32)
+
+    def rc(m, n=5, uvl=0x30000, dout=0x40000, grads=True):
+        return L.ntc_backward(C.byref(m), uvl, n, dout, C.byref(g) if grads else None, 0, 0, 0,
+                              None)
+    assert rc(_fake_material()) == ntc.ERR_ARG          # packed grids are not differentiable
+    assert rc(m32, n=-1) == ntc.ERR_ARG
+    assert rc(m32, grads=False) == ntc.ERR_ARG
+    assert rc(m32, n=0) == ntc.OK
+    assert rc(m32, uvl=0x30004) == ntc.ERR_ALIGN
+    assert rc(m32, dout=None) == ntc.ERR_ARG
+    g.grid0[1] = 0x60008
+    assert rc(m32) == ntc.ERR_ALIGN
+    g.grid0[1] = None
+    assert rc(_fake_material(encoding=ntc.GRID_F32, hidden_layers=3, w_h3=0x20000,
+                             b_h3=0x20000)) == ntc.ERR_UNSUPPORTED
+
+
+def test_batch_validation(L):
+    arr = (ntc.ntc_material * 2)(_fake_material(precision=ntc.PREC_F16),
+                                 _fake_material(precision=ntc.PREC_F16))
+    nq = (C.c_int64 * 2)(10, 20)
+    desc = ntc.ntc_batch()
+    ws_bytes = L.ntc_batch_workspace_bytes()
+
+    def rc(a=arr, q=nq, n=2, f=ntc.FILTER_NEAREST, ws=0x100000, wsb=ws_bytes, d=True):
+        return L.ntc_batch_prepare(C.cast(a, C.c_void_p) if a is not None else None,
+                                   C.cast(q, C.c_void_p) if q is not None else None, n, f, ws, wsb,
+                                   C.byref(desc) if d else None, None)
+    assert rc(a=None) == ntc.ERR_ARG and rc(q=None) == ntc.ERR_ARG and rc(d=False) == ntc.ERR_ARG
+    assert rc(n=0) == ntc.ERR_ARG
+    assert rc(f=ntc.FILTER_STOCHASTIC) == ntc.ERR_ARG
+    assert rc(ws=0x100008) == ntc.ERR_ALIGN
+    assert rc(wsb=ws_bytes - 1) == ntc.ERR_ARG
+    nq[1] = -1
+    assert rc() == ntc.ERR_ARG
+    nq[1] = 20
+    arr[1] = _fake_material()                           # FP32 weights: not batched
+    assert rc() == ntc.ERR_UNSUPPORTED
+    # decode of an unprepared or empty batch
+    assert L.ntc_decode_batched(C.byref(ntc.ntc_batch()), 0x30000, 0x40000, 0, None) == ntc.ERR_ARG
+    empty = ntc.ntc_batch()
+    empty.workspace = 0x100000
+    assert L.ntc_decode_batched(C.byref(empty), 0x30000, 0x40000, 3, None) == ntc.ERR_ARG
+    assert L.ntc_decode_batched(C.byref(empty), 0x30000, 0x40000, ntc.DTYPE_U8, None) == ntc.OK
+
+
+def test_vq_features_and_shape_validation(L):
+    assert L.ntc_vq_assign(0x1000, -1, 8, 0x2000, 2, 0x3000, None) == ntc.ERR_ARG
+    assert L.ntc_vq_assign(0x1000, 10, 0, 0x2000, 2, 0x3000, None) == ntc.ERR_ARG
+    assert L.ntc_vq_assign(0x1000, 10, 8, 0x2000, 5, 0x3000, None) == ntc.ERR_ARG
+    assert L.ntc_vq_assign(0x1000, 0, 8, 0x2000, 2, 0x3000, None) == ntc.OK
+    assert L.ntc_vq_assign(0x1004, 10, 8, 0x2000, 2, 0x3000, None) == ntc.ERR_ALIGN
+    assert L.ntc_vq_assign(0x1000, 10, 8, 0x2000, 2, None, None) == ntc.ERR_ARG
+    m = C.byref(_fake_material())
+    assert L.ntc_sample_features(m, 0x1000, -1, 0x2000, 0, 0, 0, None) == ntc.ERR_ARG
+    assert L.ntc_sample_features(m, 0x1000, 0, 0x2000, 0, 0, 0, None) == ntc.OK
+    assert L.ntc_sample_features(m, 0x1000, 5, 0x2004, 0, 0, 0, None) == ntc.ERR_ALIGN
+    assert L.ntc_sample_features(m, 0x1000, 5, 0x2000, ntc.FLAG_NOISE, 0, 0, None) == ntc.ERR_ARG
+    assert L.ntc_set_decode_warpgroups(1) == ntc.ERR_ARG
+    assert L.ntc_set_decode_warpgroups(6) == ntc.ERR_ARG
+    assert L.ntc_set_decode_warpgroups(5) == ntc.OK and L.ntc_set_decode_warpgroups(0) == ntc.OK
