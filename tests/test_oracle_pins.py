@@ -351,7 +351,7 @@ def test_f8_form_output_layer_matches_central_differences():
 def _train_oracle(f8, steps=300, batch=1024, seed=5):
     """Texture-set PSNR (Eq. 1) before and after `steps` oracle training
     steps (sampler, noise, L2, Adam with cosine rates, clamping) of a tiny
-    32^2 x 4 material, in FP64 or in the FP8 form (R24: weight scales
+    32^2 x 4 material, in FP64 or in the FP8 training form (weight scales
     2^ceil(log2(max |W| / 448)) each step, activation scales 2^-6)."""
     w_, h_, c_ = 32, 32, 4
     case = make_case(w_, h_, c_, 4, 4, k_in=32, hidden=16, act=0, seed=41)
