@@ -386,8 +386,9 @@ class Model:
         return x
 
     def f8_form(self, s_w, s_a):
-        """The FP8-E4M3 training and decode form of this model (no counterpart
-        in the paper, which trains in FP32 and decodes in FP16): every weight
+        """The FP8-E4M3 training and decode form of this model (the paper
+        trains with half-precision tensor cores, Sec. 5.1, and leaves lower
+        precision to future work, Sec. 7): every weight
         matrix replaced by s_w[l] e4m3(W_l / s_w[l]) (biases unchanged) and
         every layer input used as s_a[l] e4m3(v / s_a[l]) inside the C
         forward.  Its reverse mode is straight-through: each rounding counts

@@ -44,9 +44,9 @@ typedef struct {
   const double *wm, *bm;    /* [hidden][hidden], [hidden] (hidden_layers == 3) */
   int vq_g0;                /* G0 holds vector-quantised values: the training noise
                                applies to G1 only */
-  const double* f8_sa;      /* FP8-E4M3 form (NULL: off; no counterpart in the
-                               paper, which works in FP16 and FP32: the form the
-                               FP8 tensor-core kernels compute): per-layer activation
+  const double* f8_sa;      /* FP8-E4M3 form (NULL: off; the paper trains with
+                               half-precision tensor cores, Sec. 5.1, and leaves
+                               lower precision to future work, Sec. 7): per-layer activation
                                scales s_a[3]; every layer input v is used as
                                s_a[l] e4m3(v / s_a[l]) (two hidden layers; the
                                weights are given already quantised).  Reverse
