@@ -220,14 +220,15 @@ def test_c_e4m3_rounding_against_torch():
     assert math.copysign(1.0, oracle.lib().or_round_e4m3(-1e-9)) == -1.0
 
 
-def _f8_model(act, seed=21):
+def _f8_model(act, seed=21, out_act=0, interp0=0):
     """A small material, its FP64 model and its FP8 form with power-of-two
     scales: weights max |W| / s_w in (224, 448]; activation scales chosen
     from the FP64 activations so that each layer meets a different part of
     the E4M3 range (layer 0 normal values, layer 1 about 10% saturated,
     layer 2 about half subnormal) -- with power-of-two scales the rounding
     depends on the scale only at the range's ends."""
-    case = make_case(32, 32, 4, 4, 4, k_in=32, hidden=16, act=act, seed=seed, wgain=2.0)
+    case = make_case(32, 32, 4, 4, 4, k_in=48 if interp0 else 32, hidden=16, act=act, seed=seed,
+                     wgain=2.0, out_act=out_act, interp0=interp0)
     md = case.oracle_model(quantized=False)
     w = md.weights
     s_w = [float(2.0 ** np.ceil(np.log2(np.abs(w[2 * l]).max() / 448.0))) for l in range(3)]
@@ -264,14 +265,15 @@ def test_f8_form_forward_matches_python_decode_f8():
         assert np.array_equal(oracle.round_e4m3(w), w) and np.abs(w).max() <= 448
 
 
-@pytest.mark.parametrize("act", [0, 1])
-def test_f8_form_gradients_are_straight_through(act):
+@pytest.mark.parametrize("act,out_act,interp0", [(0, 0, 0), (1, 0, 0), (1, 1, 1)])
+def test_f8_form_gradients_are_straight_through(act, out_act, interp0):
     """Reverse mode of the FP8 form against torch autograd (float64) of the
     same forward written with the straight-through estimator
     v + (s e4m3(v / s) - v).detach(): loss, every weight and bias gradient,
-    and each texel's input-row gradient."""
+    and each texel's input-row gradient (ReLU or hardGELU, sigmoid or
+    identity output, bilinear or learned G0 rows)."""
     torch = pytest.importorskip("torch")
-    md, f8, s_w, s_a = _f8_model(act)
+    md, f8, s_w, s_a = _f8_model(act, out_act=out_act, interp0=interp0)
     xym = _texels(md, 48, 6)
     target = np.random.default_rng(7).random((48, 4))
     noise = (99, 4)
@@ -293,7 +295,8 @@ def test_f8_form_gradients_are_straight_through(act):
     h = ste(X, s_a[0])
     h = act_t(h @ W[0].T + W[1])
     h = act_t(ste(h, s_a[1]) @ W[2].T + W[3])
-    y = torch.sigmoid(ste(h, s_a[2]) @ W[4].T + W[5])
+    z3 = ste(h, s_a[2]) @ W[4].T + W[5]
+    y = z3 if out_act == 1 else torch.sigmoid(z3)
     lt = ((y - torch.from_numpy(target)) ** 2).mean()
     lt.backward()
     assert abs(loss - lt.item()) <= 1e-12 * lt.item()
