@@ -327,7 +327,7 @@ int ntc_backward(const ntc_material* m, const float* uvl, int64_t n, const float
  * (unclamped); loss_out stays the L2 loss.  FP16
  * weights train on the tensor cores (tcgen05; ReLU or hardGELU, sigmoid or
  * identity output, bilinear or learned G0); FP32 weights or NTC_FLAG_SIMT on
- * the FP32 CUDA cores (k_in <= 64). */
+ * the FP32 CUDA cores (k_in <= 64); FP8 weights: NTC_ERR_UNSUPPORTED. */
 int ntc_train_step(const ntc_material* m, const ntc_trainer* tr, const ntc_target* t,
                    int64_t batch, uint64_t seed, const float* uvl_or_null, float* loss_out,
                    int32_t flags, void* stream);
@@ -366,7 +366,7 @@ int ntc_batch_prepare(const ntc_material* mats, const int64_t* n_queries, int32_
 
 /* Decode every material of a prepared batch in one persistent launch (the
  * multi-material case of Sec. 5.2 / App. A, done by sorting work by material
- * instead of per-SIMD-group loops): uvl [total_queries][3], out (f16 or f32)
+ * instead of per-SIMD-group loops): uvl [total_queries][3], out (f32, f16 or u8)
  * [total_outputs].  Only launches a kernel: capturable in a CUDA graph. */
 int ntc_decode_batched(const ntc_batch* batch, const float* uvl, void* out, int32_t out_dtype,
                        void* stream);

@@ -201,6 +201,9 @@ def test_train_step_validation(L):
     assert rc == ntc.ERR_ARG and "params" in L.ntc_last_error().decode()
     rc = L.ntc_train_step(C.byref(m), C.byref(tr), C.byref(tg), 0, 1, None, loss, 0, None)
     assert rc == ntc.ERR_ARG
+    m8 = _fake_material(encoding=ntc.GRID_F32, precision=ntc.PREC_F8, scale=0x20000)
+    rc = L.ntc_train_step(C.byref(m8), C.byref(tr), C.byref(tg), 16, 1, None, loss, 0, None)
+    assert rc == ntc.ERR_UNSUPPORTED
 
 
 def test_quantize_and_sampler_validation(L):
