@@ -21,6 +21,9 @@ MAX_MIPS = 16
 MAX_CHANNELS = 16
 MAX_K = 128
 HIDDEN = 64
+MAX_FEATURES = 32
+MAX_BATCH = 1024
+NOALLOC_MAX_PARAMS = 1 << 21
 
 OK, ERR_ARG, ERR_SHAPE, ERR_ALIGN, ERR_UNSUPPORTED, ERR_CUDA, ERR_TIMEOUT = range(7)
 GRID_PACKED, GRID_F32 = 0, 1

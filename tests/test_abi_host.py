@@ -326,3 +326,34 @@ def test_vq_features_and_shape_validation(L):
     assert L.ntc_set_decode_warpgroups(1) == ntc.ERR_ARG
     assert L.ntc_set_decode_warpgroups(6) == ntc.ERR_ARG
     assert L.ntc_set_decode_warpgroups(5) == ntc.OK and L.ntc_set_decode_warpgroups(0) == ntc.OK
+
+
+def _header_constants():
+    """NTC_* values from include/ntc.h: enum members (explicit values) and
+    integer #defines (shifts evaluated)."""
+    src = open(os.path.join(ROOT, "include", "ntc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for body in re.findall(r"enum\s*\{(.*?)\}", src, flags=re.S):
+        for name, val in re.findall(r"\b(NTC_[A-Z0-9_]+)\s*=\s*([^,}\n]+)", body):
+            out[name] = int(eval(val.strip(), {}, {}))
+    for name, val in re.findall(r"#define\s+(NTC_[A-Z0-9_]+)\s+\(?([0-9x<> ]+)\)?", src):
+        out[name] = int(eval(val.strip(), {}, {}))
+    return out
+
+
+def test_binding_constants_match_the_header():
+    consts = _header_constants()
+    assert len(consts) > 30
+    alias = {"NTC_MAX_LEVELS": "MAX_LEVELS", "NTC_MAX_MIPS": "MAX_MIPS",
+             "NTC_MAX_CHANNELS": "MAX_CHANNELS", "NTC_MAX_K": "MAX_K", "NTC_HIDDEN": "HIDDEN"}
+    checked = 0
+    for name, val in consts.items():
+        py = alias.get(name, name[len("NTC_"):])
+        if hasattr(ntc, py):
+            assert getattr(ntc, py) == val, (name, getattr(ntc, py), val)
+            checked += 1
+    for must in ("NTC_DTYPE_U8", "NTC_FLAG_CROPS", "NTC_FILTER_STOCHASTIC", "NTC_PREC_F8",
+                 "NTC_ERR_TIMEOUT", "NTC_INTERP_LEARNED", "NTC_GRID_F32"):
+        assert must in consts and hasattr(ntc, must[len("NTC_"):]), must
+    assert checked == len(consts)
