@@ -357,3 +357,40 @@ def test_binding_constants_match_the_header():
                  "NTC_ERR_TIMEOUT", "NTC_INTERP_LEARNED", "NTC_GRID_F32"):
         assert must in consts and hasattr(ntc, must[len("NTC_"):]), must
     assert checked == len(consts)
+
+
+def test_struct_layouts_match_the_header():
+    """sizeof and every field offset of the ABI structs, compiled from
+    include/ntc.h by the host C compiler, equal the binding's ctypes
+    layouts (a drifted field would silently shift every later one)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    structs = [ntc.ntc_level, ntc.ntc_material, ntc.ntc_grads, ntc.ntc_trainer, ntc.ntc_target,
+               ntc.ntc_batch]
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "ntc.h"', "int main(void) {"]
+    for st in structs:
+        nm = st.__name__
+        lines.append(f'  printf("{nm} sizeof %zu\\n", sizeof({nm}));')
+        for f in st._fields_:
+            lines.append(f'  printf("{nm} {f[0]} %zu\\n", offsetof({nm}, {f[0]}));')
+    lines += ["  return 0;", "}"]
+    out_dir = os.path.join(ROOT, "_build")
+    os.makedirs(out_dir, exist_ok=True)
+    src, exe = os.path.join(out_dir, "abi_layout.c"), os.path.join(out_dir, "abi_layout")
+    with open(src, "w") as f:
+        f.write("\n".join(lines) + "\n")
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), src, "-o", exe],
+                   check=True)
+    got = {}
+    for line in subprocess.run([exe], check=True, capture_output=True, text=True).stdout.split("\n"):
+        if line:
+            a, b, v = line.split()
+            got[(a, b)] = int(v)
+    for st in structs:
+        nm = st.__name__
+        assert got[(nm, "sizeof")] == C.sizeof(st), nm
+        for f in st._fields_:
+            assert got[(nm, f[0])] == getattr(st, f[0]).offset, (nm, f[0])

@@ -862,3 +862,38 @@ def test_texture_set_psnr_eq1():
     test = [np.full((4, 4, 1), 0.1), np.full((2, 2, 1), 0.2)]
     # (16 * 0.01 + 4 * 0.04) / 20 = 0.016
     assert abs(oracle.texture_set_psnr(ref, test) - (-10 * math.log10(0.016))) < 1e-12
+
+
+def test_oracle_struct_layouts_match_its_header():
+    """The oracle's ctypes structs against oracle/ntc_oracle.h compiled by the
+    host C compiler: sizeof and every field offset."""
+    import ctypes as C
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    pairs = [(oracle._Model, "or_model"), (oracle._Noise, "or_noise"), (oracle._Grads, "or_grads")]
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "ntc_oracle.h"',
+             "int main(void) {"]
+    for st, nm in pairs:
+        lines.append(f'  printf("{nm} sizeof %zu\\n", sizeof({nm}));')
+        for f in st._fields_:
+            lines.append(f'  printf("{nm} {f[0]} %zu\\n", offsetof({nm}, {f[0]}));')
+    lines += ["  return 0;", "}"]
+    out_dir = os.path.join(root, "_build")
+    os.makedirs(out_dir, exist_ok=True)
+    src, exe = os.path.join(out_dir, "oracle_layout.c"), os.path.join(out_dir, "oracle_layout")
+    with open(src, "w") as f:
+        f.write("\n".join(lines) + "\n")
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(root, "oracle"), src, "-o", exe], check=True)
+    got = {}
+    for line in subprocess.run([exe], check=True, capture_output=True, text=True).stdout.split("\n"):
+        if line:
+            a, b, v = line.split()
+            got[(a, b)] = int(v)
+    for st, nm in pairs:
+        assert got[(nm, "sizeof")] == C.sizeof(st), nm
+        for f in st._fields_:
+            assert got[(nm, f[0])] == getattr(st, f[0]).offset, (nm, f[0])
