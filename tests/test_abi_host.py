@@ -394,3 +394,44 @@ def test_struct_layouts_match_the_header():
         assert got[(nm, "sizeof")] == C.sizeof(st), nm
         for f in st._fields_:
             assert got[(nm, f[0])] == getattr(st, f[0]).offset, (nm, f[0])
+
+
+def _prototypes():
+    """name -> (return type, [parameter types]) of every function in
+    include/ntc.h (comments stripped, parameter names dropped)."""
+    src = open(os.path.join(ROOT, "include", "ntc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"#[^\n]*", "", src)
+    out = {}
+    for ret, name, params in re.findall(r"([A-Za-z_][\w \*]*?)\s*\b(ntc_[a-z_0-9]+)\s*\(([^;{]*?)\)\s*;",
+                                        src, flags=re.S):
+        ps = [p.strip() for p in params.split(",") if p.strip() and p.strip() != "void"]
+        types = [re.sub(r"\s*\b\w+\s*$", "", p) if not p.endswith("*") else p for p in ps]
+        out[name] = (ret.strip().split()[-1] if ret.strip() else ret, types)
+    return out
+
+
+def _ctype_of(ctype: str):
+    t = " ".join(ctype.replace("const ", "").split())
+    if "*" in t:
+        return C.c_char_p if t == "char*" or t == "char *" else C.c_void_p
+    return {"int32_t": C.c_int32, "int64_t": C.c_int64, "uint64_t": C.c_uint64, "float": C.c_float,
+            "size_t": C.c_size_t, "int": C.c_int}[t]
+
+
+def test_binding_signatures_match_the_prototypes():
+    """Every entry point's ctypes argtypes are the header's parameter types
+    in order (a 32-bit argtype for a 64-bit parameter would pass garbage)."""
+    protos = _prototypes()
+    assert set(protos) == set(ntc.SIGNATURES), set(protos) ^ set(ntc.SIGNATURES)
+    for name, (ret, types) in protos.items():
+        rw, rg = _ctype_of(ret), ntc.SIGNATURES[name][0]
+        assert C.sizeof(rg) == C.sizeof(rw) and (rw is C.c_char_p) == (rg is C.c_char_p), name
+        want = [_ctype_of(t) for t in types]
+        got = ntc.SIGNATURES[name][1]
+        assert len(got) == len(want), (name, len(got), len(want))
+        for i, (g, w) in enumerate(zip(got, want)):
+            assert C.sizeof(g) == C.sizeof(w) and (g in (C.c_float,)) == (w in (C.c_float,)), \
+                (name, i, g, w)
+            if w is C.c_void_p:
+                assert g is C.c_void_p, (name, i)
