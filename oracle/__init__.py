@@ -74,38 +74,41 @@ class _Grads(C.Structure):
                 ("wm", C.c_void_p), ("bm", C.c_void_p), ("rows", C.c_void_p)]
 
 
+_P, _I, _I64, _U64, _D = C.c_void_p, C.c_int, C.c_int64, C.c_uint64, C.c_double
+# name -> (restype, argtypes) of every function of ntc_oracle.h
+SIGNATURES = {
+    "or_mips": (_I, [_I, _I]),
+    "or_pyramid": (_I, [_I, _I, _P, _P, _P, _P]),
+    "or_level_of_mip": (_I, [_I, _I]),
+    "or_quantize": (None, [_P, _I64, _I, _D, _P]),
+    "or_dequantize": (None, [_P, _I64, _I, _D, _P]),
+    "or_cell_bytes": (_I, [_I, _I]),
+    "or_pack": (None, [_P, _I64, _I, _I, _P]),
+    "or_unpack": (None, [_P, _I64, _I, _I, _P]),
+    "or_splitmix64": (_U64, [_U64]),
+    "or_rng": (_U64, [_U64, _U64, _U64]),
+    "or_noise_value": (_D, [_U64, _I64, _I, _I, _I64, _I, _I, _D]),
+    "or_sample_batch": (None, [_U64, _I64, _I64, _I, _I, _I, _P]),
+    "or_sample_batch_crops": (None, [_U64, _I64, _I64, _I, _I, _I, _P]),
+    "or_positional_encoding": (None, [_I, _I, _P]),
+    "or_activation": (_D, [_I, _D]),
+    "or_activation_grad": (_D, [_I, _D]),
+    "or_features": (None, [_P, _I, _I, _I, _P, _P]),
+    "or_features_uvl": (None, [_P, _I64, _P, _P]),
+    "or_decode_xym": (None, [_P, _I64, _P, _P, _P, _I]),
+    "or_decode_uvl": (None, [_P, _I64, _P, _P, _P, _I]),
+    "or_decode_trilinear": (None, [_P, _I64, _P, _P, _I]),
+    "or_decode_stochastic": (None, [_P, _I64, _P, C.c_uint64, _I64, _P, _I]),
+    "or_backward_xym": (None, [_P, _I64, _P, _P, _P, _P, _I]),
+    "or_round_e4m3": (_D, [_D]),
+    "or_loss_grad_xym": (_D, [_P, _I64, _P, _P, _P, _P, _I]),
+    "or_cosine_lr": (_D, [_D, _I64, _I64]),
+    "or_adam": (None, [_P, _P, _P, _P, _I64, _D, _I64, _D, _D, _D, _I, _D, _D]),
+}
+
+
 def _declare(L):
-    P, I, I64, U64, D = C.c_void_p, C.c_int, C.c_int64, C.c_uint64, C.c_double
-    sig = {
-        "or_mips": (I, [I, I]),
-        "or_pyramid": (I, [I, I, P, P, P, P]),
-        "or_level_of_mip": (I, [I, I]),
-        "or_quantize": (None, [P, I64, I, D, P]),
-        "or_dequantize": (None, [P, I64, I, D, P]),
-        "or_cell_bytes": (I, [I, I]),
-        "or_pack": (None, [P, I64, I, I, P]),
-        "or_unpack": (None, [P, I64, I, I, P]),
-        "or_splitmix64": (U64, [U64]),
-        "or_rng": (U64, [U64, U64, U64]),
-        "or_noise_value": (D, [U64, I64, I, I, I64, I, I, D]),
-        "or_sample_batch": (None, [U64, I64, I64, I, I, I, P]),
-        "or_sample_batch_crops": (None, [U64, I64, I64, I, I, I, P]),
-        "or_positional_encoding": (None, [I, I, P]),
-        "or_activation": (D, [I, D]),
-        "or_activation_grad": (D, [I, D]),
-        "or_features": (None, [P, I, I, I, P, P]),
-        "or_features_uvl": (None, [P, I64, P, P]),
-        "or_decode_xym": (None, [P, I64, P, P, P, I]),
-        "or_decode_uvl": (None, [P, I64, P, P, P, I]),
-        "or_decode_trilinear": (None, [P, I64, P, P, I]),
-        "or_decode_stochastic": (None, [P, I64, P, C.c_uint64, I64, P, I]),
-        "or_backward_xym": (None, [P, I64, P, P, P, P, I]),
-        "or_round_e4m3": (D, [D]),
-        "or_loss_grad_xym": (D, [P, I64, P, P, P, P, I]),
-        "or_cosine_lr": (D, [D, I64, I64]),
-        "or_adam": (None, [P, P, P, P, I64, D, I64, D, D, D, I, D, D]),
-    }
-    for name, (res, args) in sig.items():
+    for name, (res, args) in SIGNATURES.items():
         f = getattr(L, name)
         f.restype = res
         f.argtypes = args

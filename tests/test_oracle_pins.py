@@ -897,3 +897,30 @@ def test_oracle_struct_layouts_match_its_header():
         assert got[(nm, "sizeof")] == C.sizeof(st), nm
         for f in st._fields_:
             assert got[(nm, f[0])] == getattr(st, f[0]).offset, (nm, f[0])
+
+
+def test_oracle_signatures_match_its_header():
+    """The oracle binding's ctypes argtypes/restypes against the prototypes
+    of oracle/ntc_oracle.h."""
+    import ctypes as C
+    import re
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    src = open(os.path.join(root, "oracle", "ntc_oracle.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"#[^\n]*", "", src)
+    kinds = {"int": C.c_int, "int64_t": C.c_int64, "uint64_t": C.c_uint64, "double": C.c_double,
+             "void": None}
+    protos = re.findall(r"([A-Za-z_][\w ]*?)\s+\b(or_[a-z_0-9]+)\s*\(([^;{]*?)\)\s*;", src,
+                        flags=re.S)
+    assert {p[1] for p in protos} == set(oracle.SIGNATURES)
+    for ret, name, params in protos:
+        res, args = oracle.SIGNATURES[name]
+        assert res is kinds[ret.split()[-1]], name
+        ps = [p.strip() for p in params.split(",") if p.strip() and p.strip() != "void"]
+        assert len(ps) == len(args), name
+        for p, a in zip(ps, args):
+            if "*" in p:
+                assert a is C.c_void_p, (name, p)
+            else:
+                t = re.sub(r"\s*\b\w+$", "", p).replace("const ", "").strip()
+                assert a is kinds[t], (name, p, a)
