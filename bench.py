@@ -762,7 +762,8 @@ def run_reference(args):
             "config": {"workload": "decode 4096^2x16 material, 2^24 random (u,v,lod) queries "
                                    "(bounded prefix per step)", "queries_per_step": ns},
             "cpu_baseline": {"value": value, "unit": "texels/s", "cores": threads, "kind": "oracle",
-                             "sample": f"first {ns} of the 2^24 decode queries per step"},
+                             "sample": f"{ns} of the 2^24 decode queries per step (consecutive "
+                                       f"slices; whole run sized to ~{budget:.0f} s of host time)"},
             "e2e": {"value": value, "unit": "texels/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
