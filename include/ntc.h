@@ -294,12 +294,27 @@ int ntc_autotune_decode(const ntc_material* m, const float* uvl, int64_t n, void
                         int32_t out_dtype, int32_t filter, int32_t* best, float* ms_out,
                         void* stream);
 
+/* Measurement helper (no counterpart in the paper): the FP32 FMA throughput
+ * of the current device in TFLOP/s (*tflops_out, host), the best of five
+ * timed launches of a kernel in which every thread advances 16 independent
+ * fused multiply-add chains -- the ALU roof of the FP32 CUDA-core forms.
+ * Synchronises `stream`. */
+int ntc_probe_fma_tflops(float* tflops_out, void* stream);
+
 /* Gradient of sum_i sum_c dout[i][c] * y[i][c] for nearest decodes y of the
  * queries uvl (Sec. 4.5, reverse mode of ntc_decode), ACCUMULATED into g.
  * Requires NTC_GRID_F32 grids.  With NTC_FLAG_NOISE the forward uses the
  * noisy grids of (noise_seed, noise_step), whose noise passes gradients
  * unchanged.  Activations are recomputed, never stored.  g fields may be
- * NULL to skip that tensor (grid entries: per level). */
+ * NULL to skip that tensor (grid entries: per level).
+ * NTC_PREC_F16 materials run the tensor-core adjoint (the fused kernel of
+ * ntc_train_step fed dout instead of the loss: FP16 operands with the
+ * forward's head + tail inputs, FP32 accumulation; any k_in, two or three
+ * hidden layers, bilinear or learned G0).  dout may have any magnitude: each
+ * CTA scales the rows of its tiles by a power of two that brings their
+ * largest |dout| into [1, 2) before the FP16 products and divides the
+ * gradients by it in FP32.  FP32 and FP8 materials, and NTC_FLAG_SIMT, run
+ * the FP32 CUDA-core adjoint (k_in <= 64, two hidden layers). */
 int ntc_backward(const ntc_material* m, const float* uvl, int64_t n, const float* dout,
                  const ntc_grads* g, int32_t flags, uint64_t noise_seed, int64_t noise_step,
                  void* stream);
@@ -371,6 +386,60 @@ int ntc_batch_prepare(const ntc_material* mats, const int64_t* n_queries, int32_
 int ntc_decode_batched(const ntc_batch* batch, const float* uvl, void* out, int32_t out_dtype,
                        void* stream);
 
+/* A batch of optimisation steps: many materials compressed side by side, one
+ * step of each per call (the paper compresses every material of a scene with
+ * the same fused trainer, Sec. 5.1, and runs many materials in one launch for
+ * decoding, Sec. 5.2 / App. A; here training does the same). */
+typedef struct {
+  void* workspace;         /* device descriptor written by ntc_train_batch_prepare */
+  float* loss_out;         /* device [n_materials]: each step's L2 loss per material */
+  int32_t n_materials;
+  int32_t flags;           /* the NTC_FLAG_* the batch was prepared with */
+  int64_t total_tiles;     /* 128-texel tiles of all materials */
+  int64_t adam_blocks;     /* internal: blocks of the batched Adam pass */
+  int64_t noise_blocks;    /* internal: blocks of the batched noise pass */
+  int32_t act, interp0, hidden_layers;  /* the kernel class every material shares */
+  int32_t k_layout, dx_layout;          /* internal: shared layout of the batch */
+} ntc_train_batch;
+
+#define NTC_MAX_TRAIN_BATCH 256
+
+/* Bytes of the device workspace of a training batch (about 1 MB). */
+size_t ntc_train_batch_workspace_bytes(void);
+
+/* Prepare one optimisation step for each of n_materials materials (HOST
+ * arrays mats, trainers, targets, batches; each entry as for ntc_train_step;
+ * n_materials in 1..NTC_MAX_TRAIN_BATCH).  Every material is NTC_PREC_F16 on
+ * the tensor-core trainer and shares act, interp0 and hidden_layers with the
+ * others; sides, channel counts, c0, c1 and k_in may differ.  batches[i] >= 0
+ * sampled texels of material i per step; 0 leaves material i out (no update,
+ * its step counter unchanged, its loss 0).  Material i samples and draws its
+ * noise with seed + i at its own device step counter, as
+ * ntc_train_step(.., seed + i, ..) would.  flags: NTC_FLAG_FREEZE_GRIDS,
+ * NO_NOISE, CROPS, GRAD_ONLY (NTC_FLAG_SIMT is refused).  loss_out: device
+ * [n_materials] floats.  Validates everything, then copies the descriptor into
+ * `workspace` (device, caller-owned, ntc_train_batch_workspace_bytes()) on
+ * `stream` from pageable memory: call it outside graph capture.  The trainers
+ * must be distinct, and the workspace, trainers and targets must stay alive
+ * and unmoved while steps of the batch run. */
+int ntc_train_batch_prepare(const ntc_material* mats, const ntc_trainer* trainers,
+                            const ntc_target* targets, const int64_t* batches,
+                            int32_t n_materials, uint64_t seed, int32_t flags, float* loss_out,
+                            void* workspace, size_t workspace_bytes, ntc_train_batch* batch_out,
+                            void* stream);
+
+/* One optimisation step of every material of a prepared batch: the dense
+ * noise pass of every material with a noisy scratch (one launch), the fused
+ * forward + loss + backward of all materials' texels in one persistent
+ * launch (tiles ordered by material; a CTA restages the weights and flushes
+ * its weight-gradient accumulators where its share of tiles crosses from one
+ * material to the next), and Adam over every material's parameters (one
+ * launch, whose last block advances the step counters).  Each material's
+ * result equals that of ntc_train_step with the same arguments, up to the
+ * order of floating-point atomic sums.  Only launches kernels and a memset:
+ * capturable in a CUDA graph. */
+int ntc_train_step_batched(const ntc_train_batch* batch, void* stream);
+
 /* ntc_train_step for callers that cannot allocate device memory: code that
  * runs inside an engine's frame loop or a real-time thread (cudaMalloc may
  * synchronise the device and stall it), code that enqueues into a stream that
@@ -378,7 +447,10 @@ int ntc_decode_batched(const ntc_batch* batch, const float* uvl, void* out, int3
  * operation), and plugins that only receive device buffers from their host.
  * The paper has no counterpart: this is a deployment variant of the same step.
  *
- * Identical to ntc_train_step except that tr->grad is ignored (may be NULL):
+ * Identical to ntc_train_step except that tr->grad is ignored (may be NULL)
+ * and NTC_FLAG_GRAD_ONLY is refused with NTC_ERR_ARG (that flag's only
+ * result, the gradient, would stay in the library's private array).  Every
+ * argument check runs before the call puts anything on `stream`.  Otherwise:
  * the scratch gradient is a fixed array of NTC_NOALLOC_MAX_PARAMS floats
  * (8 MiB) compiled into the library, which every GPU that loads the library
  * holds until the process exits.  tr->n_params above NTC_NOALLOC_MAX_PARAMS

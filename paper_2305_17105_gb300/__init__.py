@@ -23,6 +23,7 @@ MAX_K = 128
 HIDDEN = 64
 MAX_FEATURES = 32
 MAX_BATCH = 1024
+MAX_TRAIN_BATCH = 256
 NOALLOC_MAX_PARAMS = 1 << 21
 
 OK, ERR_ARG, ERR_SHAPE, ERR_ALIGN, ERR_UNSUPPORTED, ERR_CUDA, ERR_TIMEOUT = range(7)
@@ -88,6 +89,13 @@ class ntc_target(C.Structure):
     _fields_ = [("texels", C.c_void_p), ("offset", C.c_int64 * MAX_MIPS)]
 
 
+class ntc_train_batch(C.Structure):
+    _fields_ = [("workspace", C.c_void_p), ("loss_out", C.c_void_p), ("n_materials", C.c_int32),
+                ("flags", C.c_int32), ("total_tiles", C.c_int64), ("adam_blocks", C.c_int64),
+                ("noise_blocks", C.c_int64), ("act", C.c_int32), ("interp0", C.c_int32),
+                ("hidden_layers", C.c_int32), ("k_layout", C.c_int32), ("dx_layout", C.c_int32)]
+
+
 # name -> (restype, argtypes); every entry point of include/ntc.h
 _P, _I32, _I64, _U64, _F = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_float
 SIGNATURES = {
@@ -114,6 +122,11 @@ SIGNATURES = {
     "ntc_decode_batched": (C.c_int, [_P, _P, _P, _I32, _P]),
     "ntc_set_decode_warpgroups": (C.c_int, [_I32]),
     "ntc_autotune_decode": (C.c_int, [_P, _P, _I64, _P, _I32, _I32, _P, _P, _P]),
+    "ntc_train_batch_workspace_bytes": (C.c_size_t, []),
+    "ntc_train_batch_prepare": (C.c_int, [_P, _P, _P, _P, _I32, _U64, _I32, _P, _P, C.c_size_t,
+                                          _P, _P]),
+    "ntc_train_step_batched": (C.c_int, [_P, _P]),
+    "ntc_probe_fma_tflops": (C.c_int, [_P, _P]),
 }
 
 _lib = None
@@ -639,39 +652,85 @@ def ntc_train_step_noalloc(trainer: Trainer, target: Target, batch: int, seed: i
     return trainer.loss
 
 
+class TrainBatch:
+    """One optimisation step of many materials per call (ntc_train_step_batched).
+    ``trainers`` and ``targets`` are ``Trainer`` / ``Target`` objects (kept
+    alive here), ``batches`` the texels per step of each material (0 leaves a
+    material out); material i uses seed + i.  ``loss`` holds each material's
+    loss after a step."""
+
+    def __init__(self, trainers, targets, batches, seed, flags=0, device="cuda", stream=None):
+        n = len(trainers)
+        self.trainers, self.targets = list(trainers), list(targets)
+        mats = (ntc_material * n)()
+        trs = (ntc_trainer * n)()
+        tgs = (ntc_target * n)()
+        for i, (tr, tg) in enumerate(zip(trainers, targets)):
+            mats[i], trs[i], tgs[i] = tr.material.struct, tr.struct, tg.struct
+        nb = (C.c_int64 * n)(*[int(x) for x in batches])
+        self.batches = [int(x) for x in batches]
+        self.loss = torch.zeros(n, dtype=torch.float32, device=device)
+        ws_bytes = lib().ntc_train_batch_workspace_bytes()
+        self.workspace = torch.empty(ws_bytes, dtype=torch.uint8, device=device)
+        self.desc = ntc_train_batch()
+        _call("ntc_train_batch_prepare", C.cast(mats, C.c_void_p), C.cast(trs, C.c_void_p),
+              C.cast(tgs, C.c_void_p), C.cast(nb, C.c_void_p), n, seed, flags, _ptr(self.loss),
+              _ptr(self.workspace), ws_bytes, C.byref(self.desc), _stream(stream))
+
+
+def ntc_probe_fma_tflops(stream=None) -> float:
+    """Measured FP32 FMA throughput of the current device (TFLOP/s)."""
+    v = C.c_float(0.0)
+    _call("ntc_probe_fma_tflops", C.byref(v), _stream(stream))
+    return float(v.value)
+
+
+def ntc_train_step_batched(batch: TrainBatch, stream=None):
+    """One step of every material of the batch; returns the device loss
+    tensor [n_materials]."""
+    _call("ntc_train_step_batched", C.byref(batch.desc), _stream(stream))
+    return batch.loss
+
+
 # ----------------------------------------------------------------------------
 # autograd
 # ----------------------------------------------------------------------------
 class NTCDecodeFunction(torch.autograd.Function):
     """Nearest decode with a hand-written adjoint: ``ntc_decode`` forward,
     ``ntc_backward`` backward (recomputes activations; scatter-adds into the
-    latent grids; the simulated-quantisation noise passes gradients)."""
+    latent grids; the simulated-quantisation noise passes gradients).  FP16
+    materials run the tensor-core adjoint, FP32 ones the CUDA-core adjoint.
+    Weights and biases come in layer order, 3 layers (two hidden) or 4
+    (three hidden)."""
 
     @staticmethod
-    def forward(ctx, uvl, mat_proto, noise, *tensors):
+    def forward(ctx, uvl, mat_proto, noise, n_layers, *tensors):
         L = mat_proto.levels
         g0, g1 = list(tensors[:L]), list(tensors[L:2 * L])
-        w, b = list(tensors[2 * L:2 * L + 3]), list(tensors[2 * L + 3:2 * L + 6])
+        w = list(tensors[2 * L:2 * L + n_layers])
+        b = list(tensors[2 * L + n_layers:2 * L + 2 * n_layers])
         wc = [x.half().contiguous() for x in w] if mat_proto.precision == PREC_F16 else w
         mat = mat_proto.with_(grids0=g0, grids1=g1, weights=wc, biases=b)
         flags = FLAG_NOISE if noise is not None else 0
         seed, step = noise if noise is not None else (0, 0)
         y = ntc_decode(mat, uvl, flags=flags, noise_seed=seed, noise_step=step)
         ctx.save_for_backward(uvl, *tensors)
-        ctx.mat, ctx.flags, ctx.seed, ctx.step, ctx.L = mat, flags, seed, step, L
+        ctx.mat, ctx.flags, ctx.seed, ctx.step, ctx.L, ctx.nl = mat, flags, seed, step, L, n_layers
         return y
 
     @staticmethod
     def backward(ctx, dy):
         uvl, *tensors = ctx.saved_tensors
-        L = ctx.L
+        L, nl = ctx.L, ctx.nl
         grads = [torch.zeros_like(t) for t in tensors]
-        gs = grads_struct(ctx.mat, grads[:L], grads[L:2 * L], grads[2 * L:2 * L + 3],
-                          grads[2 * L + 3:2 * L + 6])
+        gs = grads_struct(ctx.mat, grads[:L], grads[L:2 * L], grads[2 * L:2 * L + nl],
+                          grads[2 * L + nl:2 * L + 2 * nl])
         ntc_backward(ctx.mat, uvl, dy.contiguous().float(), gs, flags=ctx.flags,
                      noise_seed=ctx.seed, noise_step=ctx.step)
-        return (None, None, None, *grads)
+        return (None, None, None, None, *grads)
 
 
 def decode_autograd(mat_proto: Material, uvl, grids0, grids1, weights, biases, noise=None):
-    return NTCDecodeFunction.apply(uvl, mat_proto, noise, *grids0, *grids1, *weights, *biases)
+    assert len(weights) == len(biases) and len(weights) in (3, 4)
+    return NTCDecodeFunction.apply(uvl, mat_proto, noise, len(weights), *grids0, *grids1,
+                                   *weights, *biases)

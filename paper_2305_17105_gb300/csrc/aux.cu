@@ -53,9 +53,9 @@ namespace {
 // zeroed for the next step; half-precision weight copies are refreshed.  Each
 // thread owns kAdamPerThread consecutive elements (float4 accesses); the
 // schedule factors are computed once per block in FP32.
-__global__ void __launch_bounds__(kAdamBlock) adam_kernel(const AdamArgs A) {
+// Block b of one material's Adam pass (A: its segments, block prefix sums).
+__device__ __forceinline__ void adam_block(const AdamArgs& A, int64_t b) {
   __shared__ float s_lr, s_ic1, s_ic2;
-  const int64_t b = blockIdx.x;
   int s = 0;
   while (s + 1 < A.nseg && b >= A.block_start[s + 1]) ++s;
   const AdamSeg& S = A.seg[s];
@@ -114,16 +114,54 @@ __global__ void __launch_bounds__(kAdamBlock) adam_kernel(const AdamArgs A) {
   }
 }
 
+__global__ void __launch_bounds__(kAdamBlock) adam_kernel(const AdamArgs A) {
+  adam_block(A, blockIdx.x);
+}
+
+// Index i of the prefix-sum interval start[i] <= b < start[i + 1] (start
+// non-decreasing, start[0] = 0 <= b < start[n]).
+__device__ __forceinline__ int find_interval(const int64_t* start, int n, int64_t b) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (start[mid] <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Adam over every material of a batch: block b belongs to the material
+// whose Adam blocks contain it.  The last block to finish advances the step
+// counter of every material that took part (each block has read its
+// material's counter before it counts itself done) and re-arms the count.
+__global__ void __launch_bounds__(kAdamBlock) adam_batched_kernel(TrainBatchDev* D) {
+  const int64_t b = blockIdx.x;
+  const int i = find_interval(D->adam_start, D->n, b);
+  adam_block(D->adam[i], b - D->adam_start[i]);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const uint32_t done = atomicAdd(&D->adam_done, 1u) + 1u;
+    if (done == gridDim.x) {
+      __threadfence();
+      for (int k = 0; k < D->n; ++k)
+        if (D->adam_start[k + 1] > D->adam_start[k]) *const_cast<int64_t*>(D->adam[k].step) += 1;
+      D->adam_done = 0u;
+      __threadfence();
+    }
+  }
+}
+
 __global__ void advance_step_kernel(int64_t* step) { *step += 1; }
 
 // One thread per channel pair of a grid cell: both channels' noise comes
 // from the same 64-bit draw (noise_of), added in FP32 exactly as the fused
 // step adds it per tap.
-__global__ void __launch_bounds__(kNoiseBlock) noise_grids_kernel(const NoiseArgs a) {
+__device__ __forceinline__ void noise_block(const NoiseArgs& a, int64_t blk) {
   int s = 0;
-  while (s + 1 < a.nseg && (int64_t)blockIdx.x >= a.block_start[s + 1]) ++s;
+  while (s + 1 < a.nseg && blk >= a.block_start[s + 1]) ++s;
   const NoiseSeg& g = a.seg[s];
-  const int64_t p = ((int64_t)blockIdx.x - a.block_start[s]) * kNoiseBlock + threadIdx.x;
+  const int64_t p = (blk - a.block_start[s]) * kNoiseBlock + threadIdx.x;
   if (p >= g.pairs) return;
   const int pc = (g.c + 1) >> 1;
   const int64_t cell = p / pc;
@@ -138,6 +176,17 @@ __global__ void __launch_bounds__(kNoiseBlock) noise_grids_kernel(const NoiseArg
     w += noise_of(key, g.level, g.grid, (int)cell, ch + 1, g.c, g.q);
     a.dst[i + 1] = w;
   }
+}
+
+__global__ void __launch_bounds__(kNoiseBlock) noise_grids_kernel(const NoiseArgs a) {
+  noise_block(a, blockIdx.x);
+}
+
+// The noise pass of every material of a batch in one launch.
+__global__ void __launch_bounds__(kNoiseBlock) noise_batched_kernel(const TrainBatchDev* D) {
+  const int64_t b = blockIdx.x;
+  const int i = find_interval(D->noise_start, D->n, b);
+  noise_block(D->noise[i], b - D->noise_start[i]);
 }
 
 // q = clamp(rint(x / Q) + N/2 - 1, 0, N - 1), ties to even, evaluated in
@@ -228,6 +277,18 @@ cudaError_t launch_noise_grids(const NoiseArgs& a, cudaStream_t s) {
   const int64_t blocks = a.block_start[a.nseg];
   if (blocks == 0) return cudaSuccess;
   noise_grids_kernel<<<(unsigned)blocks, kNoiseBlock, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adam_batched(TrainBatchDev* dev, int64_t blocks, cudaStream_t s) {
+  if (blocks == 0) return cudaSuccess;
+  adam_batched_kernel<<<(unsigned)blocks, kAdamBlock, 0, s>>>(dev);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_noise_batched(const TrainBatchDev* dev, int64_t blocks, cudaStream_t s) {
+  if (blocks == 0) return cudaSuccess;
+  noise_batched_kernel<<<(unsigned)blocks, kNoiseBlock, 0, s>>>(dev);
   return cudaGetLastError();
 }
 

@@ -21,6 +21,12 @@ extern "C" int ntc_train_step_noalloc(const ntc_material* m, const ntc_trainer* 
                                       const float* uvl_or_null, float* loss_out, int32_t flags,
                                       void* stream) {
   if (!tr) return ntc::report_error(NTC_ERR_ARG, "trainer is NULL");
+  // the gradient of a gradient-only step would land in the private array,
+  // where the caller cannot read it and the next call clears it
+  if (flags & NTC_FLAG_GRAD_ONLY)
+    return ntc::report_error(NTC_ERR_ARG,
+                             "NTC_FLAG_GRAD_ONLY: the allocation-free step keeps its gradient "
+                             "private; use ntc_train_step with a caller-owned tr->grad");
   if (tr->n_params <= 0 || tr->n_params > (int64_t)NTC_NOALLOC_MAX_PARAMS)
     return ntc::report_error(NTC_ERR_SHAPE,
                              "n_params = %lld: the allocation-free step holds at most %lld "
@@ -44,11 +50,15 @@ extern "C" int ntc_train_step_noalloc(const ntc_material* m, const ntc_trainer* 
     }
     grad = g_grad_ptr[dev];
   }
+  ntc_trainer with_scratch = *tr;
+  with_scratch.grad = grad;
+  // every argument check of the step runs before anything is put on the
+  // stream, so a refused call leaves the stream untouched
+  const int st = ntc_train_step_check(m, &with_scratch, t, batch, seed, uvl_or_null, loss_out, flags);
+  if (st != NTC_OK) return st;
   // the step needs a zero gradient on entry; the array keeps whatever the
   // previous call (of any material) left in it
   e = cudaMemsetAsync(grad, 0, (size_t)tr->n_params * sizeof(float), static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return ntc::report_error(NTC_ERR_CUDA, "clear scratch: %s", cudaGetErrorString(e));
-  ntc_trainer with_scratch = *tr;
-  with_scratch.grad = grad;
   return ntc_train_step(m, &with_scratch, t, batch, seed, uvl_or_null, loss_out, flags, stream);
 }

@@ -2,6 +2,7 @@
 // validation, error reporting and dispatch to the kernels.
 #include <atomic>
 #include <mutex>
+#include <memory>
 #include <vector>
 #include <stdarg.h>
 #include <stdio.h>
@@ -332,6 +333,12 @@ int ntc_set_decode_warpgroups(int32_t nwg) {
   return NTC_OK;
 }
 
+int ntc_probe_fma_tflops(float* tflops_out, void* stream) {
+  if (!tflops_out) return fail(NTC_ERR_ARG, "tflops_out is NULL");
+  return cuda_status(ntc::probe_fma_tflops(tflops_out, static_cast<cudaStream_t>(stream)),
+                     "FMA probe");
+}
+
 int ntc_autotune_decode(const ntc_material* m, const float* uvl, int64_t n, void* out,
                         int32_t out_dtype, int32_t filter, int32_t* best, float* ms_out,
                         void* stream) {
@@ -380,9 +387,13 @@ int ntc_backward(const ntc_material* m, const float* uvl, int64_t n, const float
                  void* stream) {
   int st = check_material(m, true);
   if (st) return st;
-  if (m->hidden_layers == 3)
-    return fail(NTC_ERR_UNSUPPORTED, "ntc_backward: two hidden layers (three train with "
-                                     "ntc_train_step on FP16 weights)");
+  // FP16 weights: the tensor-core adjoint (the fused training kernel fed dout
+  // instead of the loss); otherwise the FP32 CUDA-core adjoint
+  const bool tc = m->precision == NTC_PREC_F16 && !(flags & NTC_FLAG_SIMT) &&
+                  m->vq_books == 0 && ntc::train_tc_supported(*m);
+  if (!tc && m->hidden_layers == 3)
+    return fail(NTC_ERR_UNSUPPORTED, "ntc_backward: two hidden layers on the FP32 adjoint "
+                                     "(three run on the FP16 tensor-core adjoint)");
   if (n < 0) return fail(NTC_ERR_ARG, "n < 0");
   if (!g) return fail(NTC_ERR_ARG, "grads is NULL");
   if (n == 0) return NTC_OK;
@@ -404,16 +415,33 @@ int ntc_backward(const ntc_material* m, const float* uvl, int64_t n, const float
   a.noise_step = noise_step;
   a.train = 0;
   a.grids = 1;
-  // An arbitrary upstream gradient has no known scale for FP16 operands: the
-  // adjoint always runs in FP32 (FP16 / FP8 weights are widened on load).
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (m->k_in > 64) return fail(NTC_ERR_UNSUPPORTED, "backward supports k_in <= 64");
+  if (tc) return cuda_status(ntc::launch_train_tc(*m, a, s), "backward (FP16 tensor cores)");
+  // FP32 / FP8 weights (widened on load) or NTC_FLAG_SIMT
+  if (m->k_in > 64) return fail(NTC_ERR_UNSUPPORTED, "FP32 backward supports k_in <= 64");
   return cuda_status(ntc::launch_backward_simt(*m, a, s), "backward (FP32 CUDA cores)");
 }
 
-int ntc_train_step(const ntc_material* m, const ntc_trainer* tr, const ntc_target* t,
-                   int64_t batch, uint64_t seed, const float* uvl_or_null, float* loss_out,
-                   int32_t flags, void* stream) {
+// Everything one optimisation step launches, validated and built on the
+// host without any CUDA call.
+struct StepPlan {
+  ntc::AdamArgs a;
+  ntc::BwdArgs b;
+  ntc::NoiseArgs na;
+  ntc_material mt;   // the material as the fused step reads it
+  bool noise_pass;   // dense noise pass into the trainer's noisy scratch
+  bool vq, simt;
+  int cb_seg;        // Adam segment of the codebooks (vector-quantised G0)
+};
+
+static int plan_train_step(const ntc_material* m, const ntc_trainer* tr, const ntc_target* t,
+                           int64_t batch, uint64_t seed, const float* uvl_or_null,
+                           float* loss_out, int32_t flags, StepPlan* plan) {
+  StepPlan& sp = *plan;
+  ntc::AdamArgs& a = sp.a;
+  ntc::BwdArgs& b = sp.b;
+  a = ntc::AdamArgs{};
+  b = ntc::BwdArgs{};
   const bool vq = m && m->vq_books > 0;
   int st = check_material(m, true, vq);
   if (st) return st;
@@ -449,7 +477,6 @@ int ntc_train_step(const ntc_material* m, const ntc_trainer* tr, const ntc_targe
       if (m->w[l] != tr->w_master[l]) return fail(NTC_ERR_ARG, "F32 weights must be the masters");
 
   // Segments of the parameter array: grids (group 0, clamped), MLP (group 1).
-  ntc::AdamArgs a{};
   const float* P = tr->params;
   auto offset_of = [&](const void* ptr, int64_t len, int64_t* off) -> bool {
     const float* f = static_cast<const float*>(ptr);
@@ -520,7 +547,6 @@ int ntc_train_step(const ntc_material* m, const ntc_trainer* tr, const ntc_targe
   a.freeze_grids = freeze;
 
   // Fused forward + loss + backward into tr->grad.
-  ntc::BwdArgs b{};
   b.uvl = uvl_or_null;
   b.target = t->texels;
   for (int i = 0; i < NTC_MAX_MIPS; ++i) b.tgt_off[i] = t->offset[i];
@@ -548,16 +574,18 @@ int ntc_train_step(const ntc_material* m, const ntc_trainer* tr, const ntc_targe
   b.train = 1;
   b.grids = !freeze;
   b.crops = (flags & NTC_FLAG_CROPS) != 0;
-
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  cudaError_t e = cudaMemsetAsync(loss_out, 0, sizeof(float), s);
-  if (e != cudaSuccess) return cuda_status(e, "train_step memset");
+  sp.vq = vq;
+  sp.simt = use_simt(m, flags);
+  sp.cb_seg = cb_seg;
   // With the noisy scratch: one dense noise pass, and the fused step reads
   // the noisy grids at the same offsets of the scratch.
-  ntc_material mt = *m;
+  ntc_material& mt = sp.mt;
+  mt = *m;
+  sp.na = ntc::NoiseArgs{};
+  sp.noise_pass = false;
   if (b.noise && tr->noisy) {
     CHECK_PTR(tr->noisy, "trainer noisy scratch");
-    ntc::NoiseArgs na{};
+    ntc::NoiseArgs& na = sp.na;
     na.src = tr->params;
     na.dst = tr->noisy;
     na.seed = seed;
@@ -580,9 +608,26 @@ int ntc_train_step(const ntc_material* m, const ntc_trainer* tr, const ntc_targe
         ++na.nseg;
         (k ? mt.lv[j].grid1 : mt.lv[j].grid0) = tr->noisy + sg.off;
       }
-    e = ntc::launch_noise_grids(na, s);
-    if (e != cudaSuccess) return cuda_status(e, "train_step noise pass");
+    sp.noise_pass = true;
     b.noise = 0;
+  }
+  return NTC_OK;
+}
+
+// Launches a planned step on `s`.
+static int launch_train_plan(const ntc_material* m, const ntc_trainer* tr, StepPlan& sp,
+                             float* loss_out, int32_t flags, cudaStream_t s) {
+  ntc::AdamArgs& a = sp.a;
+  ntc::BwdArgs& b = sp.b;
+  ntc_material& mt = sp.mt;
+  const bool vq = sp.vq, freeze = (flags & NTC_FLAG_FREEZE_GRIDS) != 0;
+  const int cb_seg = sp.cb_seg;
+  float* G = tr->grad;
+  cudaError_t e = cudaMemsetAsync(loss_out, 0, sizeof(float), s);
+  if (e != cudaSuccess) return cuda_status(e, "train_step memset");
+  if (sp.noise_pass) {
+    e = ntc::launch_noise_grids(sp.na, s);
+    if (e != cudaSuccess) return cuda_status(e, "train_step noise pass");
   }
   if (vq) {
     // quantise every G0 level into the scratch (the fused step reads q), with
@@ -604,12 +649,158 @@ int ntc_train_step(const ntc_material* m, const ntc_trainer* tr, const ntc_targe
     mt.vq_books = 0;  // the fused step sees q as a plain FP32 grid
     mt.codebook0 = nullptr;
   }
-  e = use_simt(m, flags) ? ntc::launch_backward_simt(mt, b, s) : ntc::launch_train_tc(mt, b, s);
+  e = sp.simt ? ntc::launch_backward_simt(mt, b, s) : ntc::launch_train_tc(mt, b, s);
   if (e != cudaSuccess) return cuda_status(e, "train_step forward/backward");
   if (flags & NTC_FLAG_GRAD_ONLY) return NTC_OK;
   e = ntc::launch_adam(a, a.block_start[a.nseg], s);
   if (e != cudaSuccess) return cuda_status(e, "train_step adam");
   return cuda_status(ntc::launch_advance_step(tr->step, s), "train_step step counter");
+}
+
+// The optimisation step.  With `check_only` the call validates its
+// arguments and returns before its first stream operation.
+static int train_step_impl(const ntc_material* m, const ntc_trainer* tr, const ntc_target* t,
+                           int64_t batch, uint64_t seed, const float* uvl_or_null,
+                           float* loss_out, int32_t flags, void* stream, bool check_only) {
+  StepPlan sp;
+  const int st = plan_train_step(m, tr, t, batch, seed, uvl_or_null, loss_out, flags, &sp);
+  if (st != NTC_OK || check_only) return st;
+  return launch_train_plan(m, tr, sp, loss_out, flags, static_cast<cudaStream_t>(stream));
+}
+
+int ntc_train_step(const ntc_material* m, const ntc_trainer* tr, const ntc_target* t,
+                   int64_t batch, uint64_t seed, const float* uvl_or_null, float* loss_out,
+                   int32_t flags, void* stream) {
+  return train_step_impl(m, tr, t, batch, seed, uvl_or_null, loss_out, flags, stream, false);
+}
+
+int ntc_train_step_check(const ntc_material* m, const ntc_trainer* tr, const ntc_target* t,
+                         int64_t batch, uint64_t seed, const float* uvl_or_null, float* loss_out,
+                         int32_t flags) {
+  return train_step_impl(m, tr, t, batch, seed, uvl_or_null, loss_out, flags, nullptr, true);
+}
+
+size_t ntc_train_batch_workspace_bytes(void) { return sizeof(ntc::TrainBatchDev); }
+
+int ntc_train_batch_prepare(const ntc_material* mats, const ntc_trainer* trainers,
+                            const ntc_target* targets, const int64_t* batches,
+                            int32_t n_materials, uint64_t seed, int32_t flags, float* loss_out,
+                            void* workspace, size_t workspace_bytes, ntc_train_batch* out,
+                            void* stream) {
+  if (!mats || !trainers || !targets || !batches || !out)
+    return fail(NTC_ERR_ARG, "train batch: NULL argument");
+  if (n_materials < 1 || n_materials > ntc::kMaxTrainBatch)
+    return fail(NTC_ERR_ARG, "train batch: n_materials = %d outside 1..%d", n_materials,
+                ntc::kMaxTrainBatch);
+  const int32_t allowed =
+      NTC_FLAG_FREEZE_GRIDS | NTC_FLAG_NO_NOISE | NTC_FLAG_CROPS | NTC_FLAG_GRAD_ONLY;
+  if (flags & ~allowed)
+    return fail(NTC_ERR_ARG, "train batch: flags 0x%x (batches train on the tensor cores; "
+                             "FREEZE_GRIDS, NO_NOISE, CROPS, GRAD_ONLY)", (unsigned)flags);
+  CHECK_PTR(workspace, "workspace");
+  CHECK_PTR(loss_out, "loss_out");
+  if (workspace_bytes < sizeof(ntc::TrainBatchDev))
+    return fail(NTC_ERR_ARG, "train batch: workspace of %zu bytes, need %zu", workspace_bytes,
+                sizeof(ntc::TrainBatchDev));
+  std::unique_ptr<ntc::TrainBatchDev> H(new ntc::TrainBatchDev());
+  memset(H.get(), 0, sizeof(ntc::TrainBatchDev));
+  const int hl0 = mats[0].hidden_layers == 0 ? 2 : mats[0].hidden_layers;
+  int k_lay = 0, dx_lay = 0;
+  for (int i = 0; i < n_materials; ++i) {
+    const ntc_material* m = &mats[i];
+    if (batches[i] < 0) return fail(NTC_ERR_ARG, "train batch material %d: negative batch", i);
+    if (m->precision != NTC_PREC_F16)
+      return fail(NTC_ERR_UNSUPPORTED,
+                  "train batch material %d: batches train FP16 materials on the tensor cores", i);
+    if (m->vq_books > 0)
+      return fail(NTC_ERR_UNSUPPORTED, "train batch material %d: scalar-quantised grids only", i);
+    const int hl = m->hidden_layers == 0 ? 2 : m->hidden_layers;
+    if (m->act != mats[0].act || m->interp0 != mats[0].interp0 || hl != hl0)
+      return fail(NTC_ERR_UNSUPPORTED,
+                  "train batch material %d: every material shares act, interp0 and "
+                  "hidden_layers with material 0", i);
+    for (int j = 0; j < i; ++j)
+      if (trainers[j].params == trainers[i].params || trainers[j].step == trainers[i].step)
+        return fail(NTC_ERR_ARG, "train batch: materials %d and %d share a trainer", j, i);
+  }
+  for (int i = 0; i < n_materials; ++i) {
+    const ntc_material* m = &mats[i];
+    StepPlan sp;
+    const int64_t nb = batches[i] > 0 ? batches[i] : 1;
+    // (the loss array was checked as a whole; each material adds into its element)
+    int st = plan_train_step(m, &trainers[i], &targets[i], nb, seed + (uint64_t)i, nullptr,
+                             loss_out, flags, &sp);
+    if (st) {
+      char why[sizeof(g_err)];
+      memcpy(why, g_err, sizeof(why));
+      return fail(st, "train batch material %d: %s", i, why);
+    }
+    if (sp.simt || sp.vq)
+      return fail(NTC_ERR_UNSUPPORTED, "train batch material %d: tensor-core trainer only", i);
+    const bool active = batches[i] > 0;
+    sp.b.loss = loss_out + i;
+    H->mats[i] = sp.mt;
+    H->args[i] = sp.b;
+    H->tile_start[i + 1] = H->tile_start[i] + (active ? (batches[i] + 127) / 128 : 0);
+    const bool adam = active && !(flags & NTC_FLAG_GRAD_ONLY);
+    if (adam) H->adam[i] = sp.a;
+    H->adam_start[i + 1] = H->adam_start[i] + (adam ? sp.a.block_start[sp.a.nseg] : 0);
+    const bool noise = active && sp.noise_pass;
+    if (noise) H->noise[i] = sp.na;
+    H->noise_start[i + 1] = H->noise_start[i] + (noise ? sp.na.block_start[sp.na.nseg] : 0);
+    int k = 0, dx = 0;
+    ntc::train_widths(*m, &k, &dx);
+    k_lay = k > k_lay ? k : k_lay;
+    dx_lay = dx > dx_lay ? dx : dx_lay;
+  }
+  if (ntc::train_pipelines_layout(mats[0], k_lay, dx_lay) == 0)
+    return fail(NTC_ERR_UNSUPPORTED, "train batch: the shared layout does not fit one CTA");
+  H->n = n_materials;
+  H->adam_done = 0;
+  H->total_tiles = H->tile_start[n_materials];
+  H->adam_blocks = H->adam_start[n_materials];
+  H->noise_blocks = H->noise_start[n_materials];
+  if (H->adam_blocks > 0x7fffffff || H->noise_blocks > 0x7fffffff)
+    return fail(NTC_ERR_SHAPE, "train batch: too many parameters for one launch");
+  cudaError_t e = cudaMemcpyAsync(workspace, H.get(), sizeof(ntc::TrainBatchDev),
+                                  cudaMemcpyHostToDevice, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_status(e, "train batch: descriptor upload");
+  out->workspace = workspace;
+  out->loss_out = loss_out;
+  out->n_materials = n_materials;
+  out->flags = flags;
+  out->total_tiles = H->total_tiles;
+  out->adam_blocks = H->adam_blocks;
+  out->noise_blocks = H->noise_blocks;
+  out->act = mats[0].act;
+  out->interp0 = mats[0].interp0;
+  out->hidden_layers = hl0;
+  out->k_layout = k_lay;
+  out->dx_layout = dx_lay;
+  return NTC_OK;
+}
+
+int ntc_train_step_batched(const ntc_train_batch* batch, void* stream) {
+  if (!batch || !batch->workspace || !batch->loss_out)
+    return fail(NTC_ERR_ARG, "train batch is not prepared");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  auto* dev = static_cast<ntc::TrainBatchDev*>(batch->workspace);
+  cudaError_t e = cudaMemsetAsync(batch->loss_out, 0, sizeof(float) * batch->n_materials, s);
+  if (e != cudaSuccess) return cuda_status(e, "train batch: loss reset");
+  e = ntc::launch_noise_batched(dev, batch->noise_blocks, s);
+  if (e != cudaSuccess) return cuda_status(e, "train batch: noise pass");
+  // the kernel class of the batch (its layout comes from k_layout, dx_layout)
+  ntc_material cls{};
+  cls.c0 = cls.c1 = 1;
+  cls.act = batch->act;
+  cls.interp0 = batch->interp0;
+  cls.hidden_layers = batch->hidden_layers;
+  cls.precision = NTC_PREC_F16;
+  e = ntc::launch_train_tc_batched(dev, cls, batch->total_tiles, batch->k_layout,
+                                   batch->dx_layout, s);
+  if (e != cudaSuccess) return cuda_status(e, "train batch: forward/backward");
+  if (batch->flags & NTC_FLAG_GRAD_ONLY) return NTC_OK;
+  return cuda_status(ntc::launch_adam_batched(dev, batch->adam_blocks, s), "train batch: adam");
 }
 
 size_t ntc_batch_workspace_bytes(void) { return sizeof(ntc::BatchHeader); }

@@ -118,6 +118,37 @@ struct BatchHeader {
   int64_t o_off[kMaxBatch + 1];       // output element offsets
   ntc_material mats[kMaxBatch];
 };
+// Device-side descriptor of a batch of optimisation steps
+// (ntc_train_batch_prepare): per material the material as the fused step
+// reads it, the step's arguments, its Adam segments and its noise segments;
+// the 128-texel tiles of all materials in one list ordered by material.
+constexpr int kMaxTrainBatch = 256;
+struct TrainBatchDev {
+  int32_t n;                              // materials
+  uint32_t adam_done;                     // Adam blocks finished in this step (reset by the last)
+  int64_t total_tiles, adam_blocks, noise_blocks;
+  int64_t tile_start[kMaxTrainBatch + 1]; // prefix sums of tiles
+  int64_t adam_start[kMaxTrainBatch + 1]; // prefix sums of Adam blocks (0 for a skipped material)
+  int64_t noise_start[kMaxTrainBatch + 1];
+  ntc_material mats[kMaxTrainBatch];
+  BwdArgs args[kMaxTrainBatch];
+  AdamArgs adam[kMaxTrainBatch];
+  NoiseArgs noise[kMaxTrainBatch];
+};
+// The fused step over a batch: one persistent launch; every material shares
+// act, interp0 and hidden_layers (the kernel class) and the layout of the
+// largest k_int / dX width.
+cudaError_t launch_train_tc_batched(const TrainBatchDev* dev, const ntc_material& first,
+                                    int64_t total_tiles, int k_lay, int dx_lay, cudaStream_t s);
+// Pipelines per CTA of the batched step for that class and layout (0: none fits).
+int train_pipelines_layout(const ntc_material& first, int k_lay, int dx_lay);
+// Internal widths of a material's training rows: k_int and the dX columns.
+void train_widths(const ntc_material& m, int* k_int, int* dx_n);
+// Adam over every material of the batch in one launch; its last block
+// advances the step counter of every material that took part.
+cudaError_t launch_adam_batched(TrainBatchDev* dev, int64_t blocks, cudaStream_t s);
+cudaError_t launch_noise_batched(const TrainBatchDev* dev, int64_t blocks, cudaStream_t s);
+
 // Input-layout class of a material for the warp-specialised kernels: 0
 // generic, 1..9 fast 4-bit layout (1 + 3 k0 + k1 by grid class).
 int fast_class(const ntc_material& m);
@@ -142,6 +173,9 @@ cudaError_t launch_decode_ws_f8(const ntc_material& m, const float* uvl, int64_t
 
 
 int sm_count();
+// FP32 FMA throughput of the current device (TFLOP/s, best of 5 timed
+// launches of an FMA-chain kernel); synchronises `s`.
+cudaError_t probe_fma_tflops(float* tflops, cudaStream_t s);
 
 // Record a thread-local error message (ntc_last_error) and return `code`.
 int report_error(int code, const char* fmt, ...);
@@ -152,3 +186,9 @@ int* status_word();
 int read_status_word(int reset);  // synchronises the device; -1 on CUDA error
 
 }  // namespace ntc
+
+// ntc_train_step's argument checks alone (no stream operation; the same
+// status and message as ntc_train_step would give).  Library-internal.
+extern "C" __attribute__((visibility("hidden"))) int ntc_train_step_check(
+    const ntc_material* m, const ntc_trainer* tr, const ntc_target* t, int64_t batch,
+    uint64_t seed, const float* uvl_or_null, float* loss_out, int32_t flags);

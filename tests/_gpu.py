@@ -63,21 +63,15 @@ def rel_err(got, ref):
     return np.linalg.norm(got - ref) / (den if den > 0 else 1.0)
 
 
-# Gradient bars.  FP32 form: 1e-2 relative (L2) per tensor.  FP16 tensor-core
-# form: 1e-2 relative over the whole grid gradient and over the whole MLP
-# gradient, and 3e-2 per tensor.  The FP16 step rounds dZ1 to FP16 (2^-11
-# relative) before dX = dZ1 W1; a coarse level's cells sum few, cancelling
-# texel contributions, which lifts that rounding to ~1-1.5% of such a
-# tensor's norm at any batch size (measured; the FP32 form meets the oracle
-# to ~1e-6 on the same tensors).
+# Gradient bar: 1e-2 relative error (L2 norm) per tensor, for the FP32 form
+# and for the FP16 tensor-core form.  The FP16 form meets it because its
+# forward feeds each ReLU / hardGELU layer an FP16 head plus an FP16 tail of
+# its input (the activation masks are then those of the exact forward); its
+# backward products stay plain FP16 with FP32 accumulation (~3e-4).
 def check_grads(got_views, refs, n_grids, fp16):
     got = [np.asarray(to_np(v), np.float64).reshape(-1) for v in got_views]
     ref = [np.asarray(r, np.float64).reshape(-1) for r in refs]
-    per = 3e-2 if fp16 else 1e-2
-    for k, (g, r) in enumerate(zip(got, ref)):
-        err = rel_err(g, r)
-        assert err <= per, (k, err)
-    if fp16:
-        for lo, hi in ((0, n_grids), (n_grids, len(ref))):
-            err = rel_err(np.concatenate(got[lo:hi]), np.concatenate(ref[lo:hi]))
-            assert err <= 1e-2, (lo, hi, err)
+    errs = [rel_err(g, r) for g, r in zip(got, ref)]
+    for k, err in enumerate(errs):
+        assert err <= 1e-2, (k, err, errs)
+    return errs

@@ -206,6 +206,64 @@ def test_train_step_validation(L):
     assert rc == ntc.ERR_UNSUPPORTED
 
 
+def test_noalloc_step_refuses_gradient_only(L):
+    """The allocation-free step keeps its gradient in a private array, so a
+    gradient-only call (whose only result is that gradient) is refused
+    before any CUDA call."""
+    m = _fake_material(encoding=ntc.GRID_F32)
+    tr = ntc.ntc_trainer()
+    tr.n_params = 16
+    rc = L.ntc_train_step_noalloc(C.byref(m), C.byref(tr), C.byref(ntc.ntc_target()), 16, 1, None,
+                                  C.c_void_p(0x50000), ntc.FLAG_GRAD_ONLY, None)
+    assert rc == ntc.ERR_ARG and "GRAD_ONLY" in L.ntc_last_error().decode()
+    assert L.ntc_train_step_noalloc(C.byref(m), None, None, 16, 1, None, None, 0, None) == ntc.ERR_ARG
+
+
+def test_train_batch_validation(L):
+    """ntc_train_batch_prepare refuses, before any CUDA call: an empty or
+    oversized batch, flags outside FREEZE_GRIDS / NO_NOISE / CROPS /
+    GRAD_ONLY, FP32 materials, materials of different kernel classes, a
+    trainer used twice, negative batches and a short workspace."""
+    n = 2
+    mats = (ntc.ntc_material * n)(*[_fake_material(encoding=ntc.GRID_F32, precision=ntc.PREC_F16)
+                                    for _ in range(n)])
+    trs = (ntc.ntc_trainer * n)()
+    tgs = (ntc.ntc_target * n)()
+    for i in range(n):
+        trs[i].params = 0x100000 * (i + 1)
+        trs[i].step = 0x900000 + 0x100 * i
+    nb = (C.c_int64 * n)(100, 0)
+    ws_bytes = L.ntc_train_batch_workspace_bytes()
+    assert ws_bytes > 0
+    out = ntc.ntc_train_batch()
+
+    def rc(mats_=mats, trs_=trs, nb_=nb, count=n, flags=0, ws=0x700000, wsb=ws_bytes):
+        return L.ntc_train_batch_prepare(C.cast(mats_, C.c_void_p), C.cast(trs_, C.c_void_p),
+                                         C.cast(tgs, C.c_void_p), C.cast(nb_, C.c_void_p), count,
+                                         1, flags, C.c_void_p(0x800000), ws, wsb, C.byref(out),
+                                         None)
+
+    assert rc(count=0) == ntc.ERR_ARG
+    assert rc(count=ntc.MAX_TRAIN_BATCH + 1) == ntc.ERR_ARG
+    assert rc(flags=ntc.FLAG_SIMT) == ntc.ERR_ARG
+    assert rc(wsb=ws_bytes - 1) == ntc.ERR_ARG
+    mats[1].precision = ntc.PREC_F32
+    assert rc() == ntc.ERR_UNSUPPORTED and "FP16" in L.ntc_last_error().decode()
+    mats[1].precision = ntc.PREC_F16
+    mats[1].act = ntc.ACT_HARDGELU
+    assert rc() == ntc.ERR_UNSUPPORTED and "shares" in L.ntc_last_error().decode()
+    mats[1].act = ntc.ACT_RELU
+    nb[1] = -1
+    assert rc() == ntc.ERR_ARG
+    nb[1] = 0
+    trs[1].params = trs[0].params
+    assert rc() == ntc.ERR_ARG and "share a trainer" in L.ntc_last_error().decode()
+    trs[1].params = 0x200000
+    # the per-material checks of ntc_train_step apply (no Adam state here)
+    assert rc() == ntc.ERR_ARG and "material 0" in L.ntc_last_error().decode()
+    assert L.ntc_train_step_batched(None, None) == ntc.ERR_ARG
+
+
 def test_quantize_and_sampler_validation(L):
     assert L.ntc_quantize_pack(0x1000, 10, 8, 3, 0.0625, 0x2000, None, None) == ntc.ERR_ARG
     assert L.ntc_quantize_pack(0x1000, 10, 8, 4, 0.0, 0x2000, None, None) == ntc.ERR_ARG
