@@ -19,6 +19,7 @@ on a bounded sample of the same workload instead.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -40,6 +41,21 @@ DEC_SIDE, DEC_C, DEC_C0, DEC_K = 4096, 16, 12, 48
 TRN_SIDE, TRN_C, TRN_C0, TRN_K = 2048, 12, 16, 48
 CROP_STEPS = 20
 MAX_SM_MHZ = 2070.0
+# DRAM bytes (read + write) of one FP16 decode_ws_kernel launch of the 2^24
+# query workload, from a single-launch ncu capture at that size (summarised
+# with the other ncu captures); valid only for the kernel sources it was
+# taken on (their hash), null otherwise.
+DECODE_SOURCES = ("tc_decode_ws.cuh", "tc_decode_common.cuh", "tc_decode_ws.cu", "tc_ptx.cuh",
+                  "ntc_device.cuh")
+DECODE_TRAFFIC = ("4ecebe64ededd090", 213.16e6 + 482.97e6)  # (sources sha256[:16], bytes per launch)
+
+
+def decode_sources_sha():
+    h = hashlib.sha256()
+    for f in DECODE_SOURCES:
+        with open(os.path.join(ROOT, "paper_2305_17105_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def parse():
@@ -61,8 +77,11 @@ def parse():
                     help="skip the camera-frame decode of the trained model")
     ap.add_argument("--no-multi", action="store_true",
                     help="skip the 64-material batched decode and training graph")
-    ap.add_argument("--render-steps", type=int, default=1000,
-                    help="training steps added before the camera-frame decode")
+    ap.add_argument("--decode-train-steps", type=int, default=1000,
+                    help="training steps that compress the 4096^2 x 16 decode material "
+                         "(0: random grids and weights, for profiling runs)")
+    ap.add_argument("--render-steps", type=int, default=0,
+                    help="(unused: the camera frame decodes the trained decode material)")
     ap.add_argument("--decode-shape", type=int, default=0, choices=[0, 2, 3, 4, 5],
                     help="tensor-core decode launch shape; 0: chosen by the autotuner "
                          "(profiling runs fix it: the autotuner's timing is not "
@@ -174,7 +193,7 @@ def decode_shapes():
     return ntc.pyramid(DEC_SIDE, DEC_SIDE)
 
 
-def make_decode_material(precision, device="cuda"):
+def make_random_decode_material(precision, device="cuda"):
     """4096^2 x 16 material: random 4-bit grids (packed on the device by the
     library's quantiser) and random MLP weights of the requested precision.
     Returns (Material, host float grid values, host weights)."""
@@ -194,26 +213,76 @@ def make_decode_material(precision, device="cuda"):
             p = ntc.ntc_quantize_pack(t, DEC_C0, 4, q)
             dst.append(p.view(src.shape[0], src.shape[1], -1))
     w = gen.random_mlp(DEC_K, 64, DEC_C, seed=2001, n_used=2 * DEC_C0 + 13)
-    wt = {"f32": torch.float32, "f16": torch.float16}
-    prec = {"f32": ntc.PREC_F32, "f16": ntc.PREC_F16, "f8": ntc.PREC_F8}[precision]
-    scale = None
-    if precision == "f8":
-        ws, dev_w = [], []
-        for l in (0, 2, 4):
-            s = float(np.abs(w[l]).max()) / 448.0
-            ws.append(s)
-            q8 = torch.from_numpy(w[l] / s).to(device).to(torch.float8_e4m3fn)
-            dev_w.append(q8.view(torch.uint8))
-        scale = torch.tensor(ws + [1.0, 1.0, 1.0], dtype=torch.float32, device=device)
-    else:
-        dev_w = [torch.from_numpy(w[l]).to(device).to(wt[precision]) for l in (0, 2, 4)]
+    dev_w = [torch.from_numpy(w[l]).to(device).to(
+        torch.float32 if precision == "f32" else torch.float16) for l in (0, 2, 4)]
     dev_b = [torch.from_numpy(w[l]).to(device) for l in (1, 3, 5)]
-    k_in = DEC_K if precision != "f8" else 64
-    if k_in != DEC_K:
-        dev_w[0] = torch.nn.functional.pad(dev_w[0], (0, k_in - DEC_K))
     mat = ntc.Material(DEC_SIDE, DEC_SIDE, DEC_C, DEC_C0, DEC_C0, 4, 4, q, q, g0, g1, dev_w, dev_b,
-                       k_in, prec, scale=scale)
+                       DEC_K, ntc.PREC_F32 if precision == "f32" else ntc.PREC_F16)
+    if precision == "f8":
+        calib = torch.from_numpy(gen.random_queries(1 << 16, 13, seed=4999)).to(device)
+        mat = ntc.f8_material(mat, [w[0], w[2], w[4]], calib)
     return mat, (g0h, g1h), w
+
+
+def make_decode_material(precision, train_steps, batch, device="cuda"):
+    """The 4096^2 x 16 decode material compressed by the library's own trainer:
+    a synthetic 16-channel texture set (seed 1001), grids G0 1024^2 x 12 and
+    G1 512^2 x 12 (4-bit range) and an MLP 48-64-64-16 trained for
+    `train_steps` FP16 tensor-core steps of `batch` texels (seed 1004), then
+    exported with 4-bit packed grids.  Returns the material in the requested
+    precision (FP8: per-layer scales from ntc_f8_quantize_weights and
+    ntc_f8_activation_scales), the host grid values, the FP32 master
+    weights (layer order, with biases), the 8-bit mip chain and a summary."""
+    import torch
+    import paper_2305_17105_gb300 as ntc
+    if train_steps <= 0:
+        mat, gh, w = make_random_decode_material(precision, device)
+        return mat, gh, w, None, {"trained": False}, None
+    t0 = time.perf_counter()
+    tex = gen.synthetic_texture(DEC_SIDE, DEC_SIDE, DEC_C, seed=1001)
+    chain = gen.box_mip_chain_u8(tex)
+    del tex
+    t_gen = time.perf_counter() - t0
+    rng = np.random.default_rng(1001)
+    n, q = 16, 1.0 / 16
+    lo, hi = -(n - 1) / 2 * q, n / 2 * q
+    g0, g1 = [], []
+    for (w0, h0), (w1, h1) in decode_shapes():
+        g0.append(gen.uniform_grid_values((h0, w0, DEC_C0), lo, hi, rng))
+        g1.append(gen.uniform_grid_values((h1, w1, DEC_C0), lo, hi, rng))
+    w = gen.random_mlp(DEC_K, 64, DEC_C, seed=2001, n_used=2 * DEC_C0 + 13)
+    tr = ntc.Trainer(DEC_SIDE, DEC_SIDE, DEC_C, DEC_C0, DEC_C0, 4, 4, q, q, g0, g1,
+                     [w[0], w[2], w[4]], [w[1], w[3], w[5]], DEC_K, ntc.PREC_F16,
+                     total_steps=train_steps, device=device)
+    target = ntc.Target(chain, device=device)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(train_steps):
+        ntc.ntc_train_step(tr, target, batch, 1004)
+    loss = float(tr.loss.item())
+    t_train = time.perf_counter() - t0
+    m16 = tr.export(ntc.PREC_F16)
+    w32 = [x.detach().cpu().numpy().astype(np.float32) for x in tr.w_master]
+    b32 = [x.detach().cpu().numpy().astype(np.float32) for x in tr.b]
+    w_host = [w32[0], b32[0], w32[1], b32[1], w32[2], b32[2]]
+    grids_host = ([g.cpu().numpy() for g in tr.material.grids0],
+                  [g.cpu().numpy() for g in tr.material.grids1])
+    calib = torch.from_numpy(gen.random_queries(1 << 16, 13, seed=4999)).to(device)
+    forms = {"f16": m16, "f32": tr.export(ntc.PREC_F32), "f8": ntc.f8_material(m16, w32, calib)}
+    mat = forms[precision]
+    # texture quality of the export: every texel of mip 0 against the reference
+    ys, xs = np.meshgrid(np.arange(DEC_SIDE), np.arange(DEC_SIDE), indexing="ij")
+    t0q = np.stack([(xs + 0.5) / DEC_SIDE, (ys + 0.5) / DEC_SIDE, np.zeros_like(xs, float)],
+                   -1).reshape(-1, 3).astype(np.float32)
+    dec = ntc.ntc_decode(m16, torch.from_numpy(t0q).to(device))
+    refm = torch.from_numpy(chain[0].reshape(-1, DEC_C)).to(device).float() / 255.0
+    mse = float(((dec - refm) ** 2).mean())
+    info = {"trained": True, "steps": train_steps, "batch": batch, "final_loss": loss,
+            "train_s": t_train, "texture_gen_s": t_gen,
+            "texture_psnr_mip0_db_f16": 10 * math.log10(1.0 / mse) if mse > 0 else None}
+    del tr, target, dec, refm
+    torch.cuda.empty_cache()
+    return mat, grids_host, w_host, chain, info, forms
 
 
 def make_trainer(precision, total_steps, device="cuda"):
@@ -238,42 +307,24 @@ def make_trainer(precision, total_steps, device="cuda"):
 # ----------------------------------------------------------------------------
 # Render-like decode of a trained model (camera frame, trilinear filtering)
 # ----------------------------------------------------------------------------
-def f8_of(ntc, mat16, w32, device="cuda"):
-    """E4M3 copy of a material: per-layer weight scales max|w|/448 and
-    activation scales that keep each layer's inputs inside the E4M3 range."""
+def render_eval(ntc, forms, grids_host, w_host, stream, stride=127):
+    """The camera workload on the trained 4096^2 x 16 decode material: a
+    3840x2160 frame with trilinear filtering (8 decodes per pixel) in FP16,
+    FP8-E4M3 and FP32.  Reports frame times and, for each precision, the
+    PSNR against the FP64 oracle with the FP32 master weights (every
+    `stride`-th pixel), plus stochastic filtering (one decode per pixel)."""
     import torch
-    ws, q8 = [], []
-    for l in range(3):
-        s = float(np.abs(w32[l]).max()) / 448.0
-        ws.append(s)
-        q8.append(torch.from_numpy(w32[l] / s).to(device).to(torch.float8_e4m3fn).view(torch.uint8))
-    scale = torch.tensor(ws + [1.0 / 256, 16.0 / 256, 16.0 / 256], dtype=torch.float32, device=device)
-    # FP8 operands take K in steps of 32: W1 padded with zero columns
-    k8 = (mat16.k_in + 31) // 32 * 32
-    q8[0] = torch.nn.functional.pad(q8[0], (0, k8 - mat16.k_in))
-    return mat16.with_(weights=q8, precision=ntc.PREC_F8, scale=scale, k_in=k8)
-
-
-def render_eval(ntc, tr, target, chain, batch, seed, extra_steps, stream):
-    """The camera workload: the training material's model after `extra_steps`
-    more steps, exported with 4-bit grids, decoded for a 3840x2160 frame with
-    trilinear filtering (8 decodes per pixel) in FP16, FP8 and FP32.  Reports
-    frame times, the PSNR of each reduced-precision frame against the FP32
-    form's frame, and the texture PSNR of mip 0 against the 8-bit reference."""
-    import torch
-    for _ in range(extra_steps):
-        ntc.ntc_train_step(tr, target, batch, seed)
-    m16 = tr.export(ntc.PREC_F16)
-    m32 = tr.export(ntc.PREC_F32)
-    m8 = f8_of(ntc, m16, [x.cpu().numpy() for x in tr.w_master])
-    q = gen.camera_queries(3840, 2160, TRN_SIDE, ntc.mips_of(TRN_SIDE, TRN_SIDE))
+    import oracle
+    mips = ntc.mips_of(DEC_SIDE, DEC_SIDE)
+    q = gen.camera_queries(3840, 2160, DEC_SIDE, mips)
     uvl = torch.from_numpy(q).cuda()
-    res = {"workload": f"3840x2160 camera frame over the trained {TRN_SIDE}^2x{TRN_C} material "
+    res = {"workload": f"3840x2160 camera frame over the trained {DEC_SIDE}^2x{DEC_C} material "
                        "(plane pitched 60 deg, 90 deg FoV), trilinear: 8 decodes per pixel",
-           "pixels": int(q.shape[0]), "train_steps": int(tr.step_t.item())}
+           "pixels": int(q.shape[0])}
     frames = {}
-    for name, m in (("f16", m16), ("f8", m8), ("f32", m32)):
-        o = torch.empty((q.shape[0], TRN_C), dtype=torch.float32, device="cuda")
+    for name in ("f16", "f8", "f32"):
+        m = forms[name]
+        o = torch.empty((q.shape[0], DEC_C), dtype=torch.float32, device="cuda")
         ntc.ntc_decode(m, uvl, out=o, filter=ntc.FILTER_TRILINEAR)
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -287,18 +338,29 @@ def render_eval(ntc, tr, target, chain, batch, seed, extra_steps, stream):
         res[f"decodes_per_s_{name}"] = 8 * q.shape[0] / (ms / 1e3)
         frames[name] = o
 
-    def psnr(a, b):
-        mse = float(((a - b) ** 2).mean())
+    def psnr(x, y):
+        mse = float(np.mean((np.asarray(x, np.float64) - np.asarray(y, np.float64)) ** 2))
         return float("inf") if mse == 0 else 10 * math.log10(1.0 / mse)
 
-    res["psnr_vs_f32_form_db"] = {k: psnr(frames[k], frames["f32"]) for k in ("f16", "f8")}
+    # the FP64 oracle of the same model (4-bit grids, FP32 master weights) on
+    # a pixel subset: the total precision loss of each form
+    md = oracle_decoder(grids_host, [np.asarray(x, np.float64) for x in w_host])
+    idx = np.arange(0, q.shape[0], stride)
+    t0 = time.perf_counter()
+    ref = md.decode_trilinear(q[idx])
+    res["oracle_pixels"] = int(idx.size)
+    res["oracle_s"] = time.perf_counter() - t0
+    sel = torch.from_numpy(idx).cuda()
+    res["psnr_vs_fp64_oracle_db"] = {k: psnr(frames[k][sel].cpu().numpy(), ref)
+                                     for k in ("f32", "f16", "f8")}
+    res["max_abs_vs_fp64_oracle"] = {
+        k: float(np.abs(frames[k][sel].cpu().numpy() - ref).max()) for k in ("f32", "f16", "f8")}
     # stochastic filtering (Sec. 5.3): one jittered nearest decode per pixel
-    o = torch.empty((q.shape[0], TRN_C), dtype=torch.float32, device="cuda")
-    ms = {"s": 0.0}
+    o = torch.empty((q.shape[0], DEC_C), dtype=torch.float32, device="cuda")
 
     def stoch(frame=[0]):
         frame[0] += 1
-        ntc.ntc_decode(m16, uvl, out=o, filter=ntc.FILTER_STOCHASTIC, noise_seed=9,
+        ntc.ntc_decode(forms["f16"], uvl, out=o, filter=ntc.FILTER_STOCHASTIC, noise_seed=9,
                        noise_step=frame[0])
     stoch()
     torch.cuda.synchronize()
@@ -309,14 +371,8 @@ def render_eval(ntc, tr, target, chain, batch, seed, extra_steps, stream):
     b.record(stream)
     torch.cuda.synchronize()
     res["frame_ms_stochastic_f16"] = a.elapsed_time(b) / 5
-    res["psnr_stochastic_frame_vs_trilinear_db"] = psnr(o, frames["f16"])
-    # texture quality: every texel of mip 0 against the 8-bit reference
-    ys, xs = np.meshgrid(np.arange(TRN_SIDE), np.arange(TRN_SIDE), indexing="ij")
-    t0 = np.stack([(xs + 0.5) / TRN_SIDE, (ys + 0.5) / TRN_SIDE, np.zeros_like(xs, float)],
-                  -1).reshape(-1, 3).astype(np.float32)
-    dec = ntc.ntc_decode(m16, torch.from_numpy(t0).cuda())
-    refm = torch.from_numpy(chain[0].reshape(-1, TRN_C).astype(np.float32) / 255.0).cuda()
-    res["texture_psnr_mip0_db"] = psnr(dec, refm)
+    res["psnr_stochastic_frame_vs_trilinear_db"] = psnr(o.cpu().numpy(),
+                                                        frames["f16"].cpu().numpy())
     return res
 
 
@@ -686,6 +742,51 @@ def multi_material_eval(ntc, n_mat, q_per, train_batch, stream):
 
 
 # ----------------------------------------------------------------------------
+# Measured peaks of the reduced and widened precision forms
+# ----------------------------------------------------------------------------
+def fp8_gemm_tflops(n=8192, reps=10):
+    """Dense FP8-E4M3 GEMM throughput (TFLOP/s, best of `reps`): the library
+    GEMM behind torch._scaled_mm on n^3 operands, scales 1, BF16 output."""
+    import torch
+    g = torch.Generator(device="cuda")
+    g.manual_seed(11)
+    a = (torch.randn(n, n, device="cuda", generator=g) * 0.5).to(torch.float8_e4m3fn)
+    b = (torch.randn(n, n, device="cuda", generator=g) * 0.5).to(torch.float8_e4m3fn)
+    one = torch.ones((), device="cuda", dtype=torch.float32)
+
+    def f():
+        return torch._scaled_mm(a, b.t(), scale_a=one, scale_b=one, out_dtype=torch.bfloat16)
+    for _ in range(3):
+        f()
+    torch.cuda.synchronize()
+    best = float("inf")
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        f()
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    del a, b
+    return 2.0 * n ** 3 / (best / 1e3) / 1e12
+
+
+def measured_peaks(ntc):
+    out = {}
+    try:
+        out["fp32_fma_tflops"] = ntc.ntc_probe_fma_tflops()
+        out["fp32_fma_source"] = "ntc_probe_fma_tflops: 16 independent FMA chains per thread, best of 5"
+    except Exception as e:  # reported, never fatal
+        out["fp32_fma_error"] = f"{type(e).__name__}: {e}"[:200]
+    try:
+        out["fp8_tflops"] = fp8_gemm_tflops()
+        out["fp8_source"] = "torch._scaled_mm E4M3 8192^3, BF16 out, best of 10 (burst)"
+    except Exception as e:  # reported, never fatal
+        out["fp8_error"] = f"{type(e).__name__}: {e}"[:200]
+    return out
+
+
+# ----------------------------------------------------------------------------
 # CPU oracle baseline (bounded samples)
 # ----------------------------------------------------------------------------
 def oracle_decoder(grids_host, weights):
@@ -806,7 +907,8 @@ def main():
     stream = torch.cuda.current_stream()
 
     # ---- inputs resident in HBM -------------------------------------------
-    mat, grids_host, w_host = make_decode_material(precision)
+    mat, grids_host, w_host, dec_chain, dec_info, forms = make_decode_material(
+        precision, args.decode_train_steps, args.batch)
     queries = gen.random_queries(args.queries, 13, seed=4001 + rank)
     q_host = torch.from_numpy(queries).pin_memory()
     q_dev = q_host.to(dev)
@@ -865,23 +967,32 @@ def main():
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except OSError:
         pass
+    mpeaks = measured_peaks(ntc)
     if precision == "f32":
-        sm_mhz = MAX_SM_MHZ
-        peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+        peak = mpeaks.get("fp32_fma_tflops") or 152 * 128 * 2 * MAX_SM_MHZ * 1e6 / 1e12
         roof = {"bound": "alu", "achieved": flop_per_q * args.queries / dec_avg_s / 1e12,
-                "peak": peak, "unit": "TFLOP/s", "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
-    else:
-        bf16 = peaks.get("bf16_tflops", 1900.0)
-        peak = bf16 * (2.0 if precision == "f8" else 1.0)
+                "peak": peak, "unit": "TFLOP/s",
+                "peak_source": ("measured FP32 FMA probe" if "fp32_fma_tflops" in mpeaks
+                                else "fallback: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz")}
+    elif precision == "f8":
+        peak = mpeaks.get("fp8_tflops") or 2.0 * peaks.get("bf16_tflops", 1900.0)
         roof = {"bound": "tensor", "achieved": flop_per_q * args.queries / dec_avg_s / 1e12,
                 "peak": peak, "unit": "TFLOP/s",
-                "peak_source": "measured bf16 burst" + (" x 2 (fp8 nominal ratio)" if precision == "f8" else "")}
+                "peak_source": ("measured FP8-E4M3 GEMM burst" if "fp8_tflops" in mpeaks
+                                else "fallback: measured bf16 burst x 2 (nominal ratio)")}
+    else:
+        peak = peaks.get("bf16_tflops", 1900.0)
+        roof = {"bound": "tensor", "achieved": flop_per_q * args.queries / dec_avg_s / 1e12,
+                "peak": peak, "unit": "TFLOP/s", "peak_source": "measured bf16 burst"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    # DRAM bytes per launch of decode_ws_kernel from the committed ncu capture
-    # of the FP16 kernel (141.50 MB at 2^22 queries, scaled by the query
-    # count); null for another precision or launch shape
-    roof["traffic"] = (141.50e6 * args.queries / (1 << 22)
-                       if precision == "f16" and tuning and tuning["decode_warpgroups"] == 5 else None)
+    # DRAM bytes per launch from the committed full-size ncu capture, when it
+    # was taken on these kernel sources, this precision, shape and size
+    sha = decode_sources_sha()
+    ok = (DECODE_TRAFFIC is not None and DECODE_TRAFFIC[0] == sha and precision == "f16"
+          and args.queries == 1 << 24 and tuning and tuning["decode_warpgroups"] == 5)
+    roof["traffic"] = DECODE_TRAFFIC[1] if ok else None
+    roof["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch "
+                              "at 2^24 queries" if ok else f"no capture for sources {sha}")
     roof["traffic_unit"] = "bytes"
     dec_bytes = args.queries * (12 + DEC_C * 2)
     hbm = peaks.get("hbm_gbs", 6773.2)
@@ -985,7 +1096,8 @@ def main():
     if precision != "f32" and not args.no_fp32_compare:
         fp32 = {}
         if precision == "f16":
-            mat32 = mat.with_(weights=[w.float() for w in mat.weights], precision=ntc.PREC_F32)
+            mat32 = forms["f32"] if forms else mat.with_(
+                weights=[w.float() for w in mat.weights], precision=ntc.PREC_F32)
             for _ in range(2):
                 ntc.ntc_decode(mat32, q_dev, out=out)
             torch.cuda.synchronize()
@@ -997,6 +1109,10 @@ def main():
             torch.cuda.synchronize()
             fp32["decode_texels_per_s"] = 3 * args.queries / (a.elapsed_time(b) / 1e3)
             fp32["decode_speedup"] = value / world / fp32["decode_texels_per_s"]
+            fp32["decode_tflops"] = flop_per_q * fp32["decode_texels_per_s"] / 1e12
+            if mpeaks.get("fp32_fma_tflops"):
+                fp32["decode_alu_frac_of_measured_fma"] = (fp32["decode_tflops"]
+                                                           / mpeaks["fp32_fma_tflops"])
         if train_prec != "f32":
             tr32, _, _, _, _ = make_trainer("f32", 16)
             for _ in range(2):
@@ -1012,6 +1128,28 @@ def main():
             fp32["train_speedup"] = train_rate / world / fp32["train_samples_per_s"]
             del tr32
 
+    # ---- the FP8-E4M3 form of the same decode -------------------------------
+    fp8 = None
+    if precision == "f16" and forms and not args.no_fp32_compare:
+        m8 = forms["f8"]
+        for _ in range(2):
+            ntc.ntc_decode(m8, q_dev, out=out)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(5):
+            ntc.ntc_decode(m8, q_dev, out=out)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms8 = a.elapsed_time(b) / 5
+        fp8 = {"decode_ms": ms8, "decode_texels_per_s": args.queries / (ms8 / 1e3),
+               "decode_tflops": flop_per_q * args.queries / (ms8 / 1e3) / 1e12,
+               "scales": [float(x) for x in m8.scale.cpu().numpy()],
+               "scales_from": "ntc_f8_quantize_weights + ntc_f8_activation_scales (2^16 queries)"}
+        if mpeaks.get("fp8_tflops"):
+            fp8["tensor_frac_of_measured_fp8"] = fp8["decode_tflops"] / mpeaks["fp8_tflops"]
+        fp8["vs_f16_decode_ms"] = statistics.mean(dec_ms)
+
     # ---- CPU oracle baseline (rank 0, N = 1) --------------------------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -1025,7 +1163,9 @@ def main():
     render = None
     if not args.no_render:
         try:
-            render = render_eval(ntc, tr, target, chain, args.batch, seed, args.render_steps, stream)
+            if forms is None:
+                raise RuntimeError("the camera frame needs the trained decode material")
+            render = render_eval(ntc, forms, grids_host, w_host, stream)
         except Exception as e:  # reported, never fatal to the headline line
             render = {"error": f"{type(e).__name__}: {e}"[:300]}
 
@@ -1083,6 +1223,10 @@ def main():
                                "MLP 48-64-64-16), 2^24 random (u,v,lod) queries + one train step "
                                "2048^2x12 (G0 512^2x16, G1 256^2x16 FP32, MLP 48-64-64-12), "
                                "2^18 texels", "queries": args.queries, "train_batch": args.batch,
+                   "decode_model": (f"compressed by the library's FP16 trainer "
+                                    f"({args.decode_train_steps} steps of {args.batch} texels) "
+                                    "from a synthetic 4096^2x16 texture set"
+                                    if dec_info.get("trained") else "random grids and weights"),
                    "decode_precision": precision, "train_precision": train_prec,
                    "l2": "inputs larger than L2 (0.74 GB streamed per decode pass)",
                    "parallelism": f"replicas x{world}"},
@@ -1090,6 +1234,7 @@ def main():
         "decode_ms": statistics.median(dec_ms), "train_ms": statistics.median(trn_ms),
         "roofline": roof, "train_roofline": train_roof, "tuning": tuning, "e2e": e2e, "fp32_path": fp32, "cpu_baseline": cpu,
         "render": render, "multi_material": multi, "paper_form": paper_form, "train_crops": crops,
+        "fp8_path": fp8, "measured_peaks": mpeaks, "decode_material": dec_info,
         "equal_psnr_training": equal, "vq_decode": vq, "sq_vs_vq_training": sqvq,
         "u8_output": u8,
         "gpu_launches": kernels_per_step * args.steps,

@@ -294,6 +294,29 @@ int ntc_autotune_decode(const ntc_material* m, const float* uvl, int64_t n, void
                         int32_t out_dtype, int32_t filter, int32_t* best, float* ms_out,
                         void* stream);
 
+/* FP8-E4M3 form (the precision step below the paper's half-precision
+ * tensor cores, Sec. 5.1, 7): one layer's weights w [rows][cols] (device
+ * float32) quantised to E4M3 bytes w8_out [rows][cols_out] (columns cols ..
+ * cols_out-1 zero; the FP8 form takes k_in in steps of 32) with the layer's
+ * weight scale s_w = max|w| / 448 (448: the largest finite E4M3 value; 1
+ * for an all-zero matrix) written to *scale_out (device float): the layer
+ * computes (s_w s_a) (W8 . e4m3(x / s_a)) + b.  E4M3 rounding to nearest
+ * even, saturating.  rows, cols_out <= NTC_MAX_K.  Only launches a kernel. */
+int ntc_f8_quantize_weights(const float* w, int32_t rows, int32_t cols, int32_t cols_out,
+                            uint8_t* w8_out, float* scale_out, void* stream);
+
+/* Activation scales of the FP8-E4M3 form from calibration queries: decodes
+ * the n queries uvl (nearest texels, FP32 arithmetic) with material m (FP32
+ * or FP16 weights, two hidden layers) and writes to act_scale_out (device,
+ * 3 floats) for each layer l the smallest power of two s_a[l] with
+ * max|x_l| / s_a[l] <= 448 over the queries, x_l the layer's input (the
+ * feature row, act(Z1), act(Z2)); 1 where the input is all zero.  Powers of
+ * two keep the FP8 training form's FP16 operand copies exact.  With
+ * ntc_f8_quantize_weights this fills the 6 scales of an NTC_PREC_F8
+ * material (s_w[0..2], then s_a[0..2]).  Only launches kernels. */
+int ntc_f8_activation_scales(const ntc_material* m, const float* uvl, int64_t n,
+                             float* act_scale_out, void* stream);
+
 /* Measurement helper (no counterpart in the paper): the FP32 FMA throughput
  * of the current device in TFLOP/s (*tflops_out, host), the best of five
  * timed launches of a kernel in which every thread advances 16 independent

@@ -127,6 +127,8 @@ SIGNATURES = {
                                           _P, _P]),
     "ntc_train_step_batched": (C.c_int, [_P, _P]),
     "ntc_probe_fma_tflops": (C.c_int, [_P, _P]),
+    "ntc_f8_quantize_weights": (C.c_int, [_P, _I32, _I32, _I32, _P, _P, _P]),
+    "ntc_f8_activation_scales": (C.c_int, [_P, _P, _I64, _P, _P]),
 }
 
 _lib = None
@@ -676,6 +678,50 @@ class TrainBatch:
         _call("ntc_train_batch_prepare", C.cast(mats, C.c_void_p), C.cast(trs, C.c_void_p),
               C.cast(tgs, C.c_void_p), C.cast(nb, C.c_void_p), n, seed, flags, _ptr(self.loss),
               _ptr(self.workspace), ws_bytes, C.byref(self.desc), _stream(stream))
+
+
+def ntc_f8_quantize_weights(w, cols_out=None, scale_out=None, stream=None):
+    """E4M3 bytes (uint8 [rows, cols_out]) of a float32 weight matrix and its
+    scale max|w| / 448 (written into ``scale_out``, a 1-element device view,
+    or a new tensor)."""
+    assert w.dtype == torch.float32 and w.dim() == 2 and w.is_contiguous()
+    rows, cols = w.shape
+    cols_out = cols if cols_out is None else int(cols_out)
+    w8 = torch.empty((rows, cols_out), dtype=torch.uint8, device=w.device)
+    if scale_out is None:
+        scale_out = torch.empty(1, dtype=torch.float32, device=w.device)
+    _call("ntc_f8_quantize_weights", _ptr(w), rows, cols, cols_out, _ptr(w8), _ptr(scale_out),
+          _stream(stream))
+    return w8, scale_out
+
+
+def ntc_f8_activation_scales(mat: Material, uvl, out=None, stream=None):
+    """Power-of-two activation scales s_a[3] of the FP8 form from the
+    per-layer input maxima of an FP32 decode of the queries ``uvl``."""
+    n = _queries(uvl)
+    if out is None:
+        out = torch.empty(3, dtype=torch.float32, device=uvl.device)
+    s = mat.struct
+    _call("ntc_f8_activation_scales", C.byref(s), _ptr(uvl), n, _ptr(out), _stream(stream))
+    return out
+
+
+def f8_material(mat: Material, w32, calib_uvl, stream=None) -> Material:
+    """The FP8-E4M3 form of a material: E4M3 weights with per-layer scales
+    (ntc_f8_quantize_weights on the FP32 weights ``w32``, layer order) and
+    activation scales calibrated on the queries ``calib_uvl``
+    (ntc_f8_activation_scales); K rounded up to a multiple of 32."""
+    k8 = (mat.k_in + 31) // 32 * 32
+    dev = calib_uvl.device
+    scale = torch.empty(6, dtype=torch.float32, device=dev)
+    w8 = []
+    for l, w in enumerate(w32):
+        wt = torch.as_tensor(w, dtype=torch.float32, device=dev).contiguous()
+        q, _ = ntc_f8_quantize_weights(wt, k8 if l == 0 else wt.shape[1], scale[l:l + 1],
+                                       stream=stream)
+        w8.append(q)
+    ntc_f8_activation_scales(mat, calib_uvl, out=scale[3:6], stream=stream)
+    return mat.with_(weights=w8, precision=PREC_F8, scale=scale, k_in=k8)
 
 
 def ntc_probe_fma_tflops(stream=None) -> float:

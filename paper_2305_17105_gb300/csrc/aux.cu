@@ -6,6 +6,7 @@
 
 #include "ntc_device.cuh"
 #include "ntc_internal.h"
+#include "tc_ptx.cuh"
 
 namespace ntc {
 
@@ -277,6 +278,98 @@ cudaError_t launch_noise_grids(const NoiseArgs& a, cudaStream_t s) {
   const int64_t blocks = a.block_start[a.nseg];
   if (blocks == 0) return cudaSuccess;
   noise_grids_kernel<<<(unsigned)blocks, kNoiseBlock, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+namespace {
+// One weight matrix [rows][cols] (FP32) -> E4M3 with one scale: s = max|W| /
+// 448 (the largest finite E4M3 value; 1 for an all-zero matrix), W8 = rn(W /
+// s) saturating, rows padded with zero bytes to cols_out.  One block.
+__global__ void __launch_bounds__(256) f8_weights_kernel(const float* __restrict__ w, int rows,
+                                                         int cols, int cols_out,
+                                                         uint8_t* __restrict__ w8, float* scale) {
+  __shared__ float red[8];
+  float mx = 0.f;
+  for (int i = threadIdx.x; i < rows * cols; i += blockDim.x) mx = fmaxf(mx, fabsf(w[i]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  float m = 0.f;
+  for (int k = 0; k < 8; ++k) m = fmaxf(m, red[k]);
+  const float sc = m > 0.f ? m / 448.f : 1.f;
+  if (threadIdx.x == 0) *scale = sc;
+  for (int i = threadIdx.x; i < rows * cols_out; i += blockDim.x) {
+    const int r = i / cols_out, c = i - r * cols_out;
+    const float v = c < cols ? w[r * cols + c] / sc : 0.f;
+    w8[i] = (uint8_t)(tc::pack_e4m3x2(v, 0.f) & 0xFFu);
+  }
+}
+}  // namespace
+
+namespace {
+// The smallest power of two p with a / p <= 448 (1 for a = 0 or not finite).
+__device__ __forceinline__ float pow2_scale(float a) {
+  if (!(a > 0.f) || !(a < __int_as_float(0x7f800000))) return 1.f;
+  int e = 0;
+  const float f = frexpf(a / 448.f, &e);  // a / 448 = f 2^e, f in [0.5, 1)
+  if (f == 0.5f) e -= 1;
+  e = e < -126 ? -126 : (e > 127 ? 127 : e);
+  return __int_as_float((127 + e) << 23);
+}
+
+struct F8Prep {
+  const float* w[3];
+  uint8_t* w8[3];
+  int rows[3], cols[3];
+};
+
+// Block l: layer l's weight scale and E4M3 weights; block 0 also turns the
+// recorded layer-input maxima (scale9[6..8], float bits) into the
+// activation scales scale9[3..5] and clears them.
+__global__ void __launch_bounds__(256) f8_train_prep_kernel(const F8Prep a, float* scale9) {
+  __shared__ float red[8];
+  const int l = blockIdx.x;
+  const float* w = a.w[l];
+  const int n = a.rows[l] * a.cols[l];
+  float mx = 0.f;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) mx = fmaxf(mx, fabsf(w[i]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  float m = 0.f;
+  for (int k = 0; k < 8; ++k) m = fmaxf(m, red[k]);
+  const float sw = pow2_scale(m), inv = 1.f / sw;
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    a.w8[l][i] = (uint8_t)(tc::pack_e4m3x2(w[i] * inv, 0.f) & 0xFFu);
+  if (threadIdx.x == 0) scale9[l] = sw;
+  if (l == 0 && threadIdx.x < 3) {
+    uint32_t* amax = reinterpret_cast<uint32_t*>(scale9 + 6);
+    const float v = __uint_as_float(amax[threadIdx.x]);
+    if (v > 0.f) scale9[3 + threadIdx.x] = pow2_scale(v);
+    amax[threadIdx.x] = 0u;
+  }
+}
+}  // namespace
+
+cudaError_t launch_f8_train_prep(const float* const* w_master, uint8_t* const* w8, int k_in,
+                                 int channels, float* scale9, cudaStream_t s) {
+  F8Prep a;
+  for (int l = 0; l < 3; ++l) {
+    a.w[l] = w_master[l];
+    a.w8[l] = w8[l];
+  }
+  a.rows[0] = kHidden; a.cols[0] = k_in;
+  a.rows[1] = kHidden; a.cols[1] = kHidden;
+  a.rows[2] = channels; a.cols[2] = kHidden;
+  f8_train_prep_kernel<<<3, 256, 0, s>>>(a, scale9);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_f8_weights(const float* w, int rows, int cols, int cols_out, uint8_t* w8,
+                              float* scale, cudaStream_t s) {
+  f8_weights_kernel<<<1, 256, 0, s>>>(w, rows, cols, cols_out, w8, scale);
   return cudaGetLastError();
 }
 

@@ -59,6 +59,10 @@ int check_material(const ntc_material* m, bool need_f32_grids, bool vq_training 
     return fail(NTC_ERR_SHAPE, "c0 = %d, c1 = %d outside 1..%d", m->c0, m->c1, ntc::kMaxGridCh);
   for (int b : {m->bits0, m->bits1})
     if (b != 1 && b != 2 && b != 4 && b != 8) return fail(NTC_ERR_ARG, "bits %d not in {1,2,4,8}", b);
+  if (m->encoding == NTC_GRID_PACKED &&
+      (m->c1 * m->bits1 > 128 || (m->vq_books == 0 && m->c0 * m->bits0 > 128)))
+    return fail(NTC_ERR_SHAPE, "packed cells hold at most 128 bits (c0 x bits0 = %d, c1 x bits1 = %d)",
+                m->c0 * m->bits0, m->c1 * m->bits1);
   if (!(m->q0 > 0.f) || !(m->q1 > 0.f)) return fail(NTC_ERR_ARG, "bin widths must be positive");
   if (m->encoding != NTC_GRID_PACKED && m->encoding != NTC_GRID_F32)
     return fail(NTC_ERR_ARG, "encoding %d", m->encoding);
@@ -333,6 +337,36 @@ int ntc_set_decode_warpgroups(int32_t nwg) {
   return NTC_OK;
 }
 
+int ntc_f8_quantize_weights(const float* w, int32_t rows, int32_t cols, int32_t cols_out,
+                            uint8_t* w8_out, float* scale_out, void* stream) {
+  if (rows < 1 || cols < 1 || cols_out < cols || cols_out > NTC_MAX_K || rows > NTC_MAX_K)
+    return fail(NTC_ERR_ARG, "f8 weights: rows %d, cols %d, cols_out %d", rows, cols, cols_out);
+  if (!w || !w8_out || !scale_out) return fail(NTC_ERR_ARG, "f8 weights: NULL pointer");
+  if (((uintptr_t)w & 3u) || ((uintptr_t)scale_out & 3u))
+    return fail(NTC_ERR_ALIGN, "f8 weights: float arrays must be 4-byte aligned");
+  return cuda_status(ntc::launch_f8_weights(w, rows, cols, cols_out, w8_out, scale_out,
+                                            static_cast<cudaStream_t>(stream)),
+                     "f8 weights");
+}
+
+int ntc_f8_activation_scales(const ntc_material* m, const float* uvl, int64_t n,
+                             float* act_scale_out, void* stream) {
+  int st = check_material(m, false);
+  if (st) return st;
+  if (m->precision == NTC_PREC_F8)
+    return fail(NTC_ERR_ARG, "f8 activation scales: calibrate the FP32 or FP16 model");
+  if (m->hidden_layers == 3)
+    return fail(NTC_ERR_UNSUPPORTED, "f8 activation scales: the FP8 form has two hidden layers");
+  if (m->vq_books > 0) return fail(NTC_ERR_UNSUPPORTED, "f8 activation scales: scalar grids");
+  if (n < 0) return fail(NTC_ERR_ARG, "n < 0");
+  if (n > 0) CHECK_PTR(uvl, "uvl");
+  if (!act_scale_out || ((uintptr_t)act_scale_out & 3u))
+    return fail(NTC_ERR_ARG, "act_scale_out is NULL or not 4-byte aligned");
+  return cuda_status(ntc::launch_f8_calibrate(*m, uvl, n, reinterpret_cast<uint32_t*>(act_scale_out),
+                                              act_scale_out, static_cast<cudaStream_t>(stream)),
+                     "f8 activation scales");
+}
+
 int ntc_probe_fma_tflops(float* tflops_out, void* stream) {
   if (!tflops_out) return fail(NTC_ERR_ARG, "tflops_out is NULL");
   return cuda_status(ntc::probe_fma_tflops(tflops_out, static_cast<cudaStream_t>(stream)),
@@ -452,7 +486,11 @@ static int plan_train_step(const ntc_material* m, const ntc_trainer* tr, const n
     if (!(tr->vq_beta >= 0.f)) return fail(NTC_ERR_ARG, "vq_beta must be >= 0");
   }
   if (batch <= 0) return fail(NTC_ERR_ARG, "batch must be positive");
-  if (m->precision == NTC_PREC_F8) return fail(NTC_ERR_UNSUPPORTED, "FP8 training");
+  if (m->precision == NTC_PREC_F8 && use_simt(m, flags))
+    return fail(NTC_ERR_UNSUPPORTED, "FP8 training runs on the tensor cores (no NTC_FLAG_SIMT)");
+  if (m->precision == NTC_PREC_F8 && !ntc::train_tc_supported(*m))
+    return fail(NTC_ERR_UNSUPPORTED, "FP8 training: bilinear G0, two hidden layers, k_in a "
+                                     "multiple of 32, scalar grids");
   if (use_simt(m, flags)) {
     if (m->k_in > 64) return fail(NTC_ERR_UNSUPPORTED, "FP32 training supports k_in <= 64");
     if (m->hidden_layers == 3)
@@ -625,6 +663,15 @@ static int launch_train_plan(const ntc_material* m, const ntc_trainer* tr, StepP
   float* G = tr->grad;
   cudaError_t e = cudaMemsetAsync(loss_out, 0, sizeof(float), s);
   if (e != cudaSuccess) return cuda_status(e, "train_step memset");
+  if (m->precision == NTC_PREC_F8) {
+    // this step's E4M3 weights and scales from the masters and the previous
+    // step's layer-input maxima (R24)
+    const float* wm[3] = {tr->w_master[0], tr->w_master[1], tr->w_master[2]};
+    uint8_t* w8[3];
+    for (int l = 0; l < 3; ++l) w8[l] = static_cast<uint8_t*>(const_cast<void*>(m->w[l]));
+    e = ntc::launch_f8_train_prep(wm, w8, m->k_in, m->channels, const_cast<float*>(m->scale), s);
+    if (e != cudaSuccess) return cuda_status(e, "train_step FP8 weights");
+  }
   if (sp.noise_pass) {
     e = ntc::launch_noise_grids(sp.na, s);
     if (e != cudaSuccess) return cuda_status(e, "train_step noise pass");

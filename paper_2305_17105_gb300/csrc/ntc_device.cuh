@@ -16,7 +16,9 @@ namespace ntc {
 constexpr int kTile = 128;       // queries per CTA tile (one per thread)
 constexpr int kHidden = NTC_HIDDEN;
 constexpr int kMaxC = NTC_MAX_CHANNELS;
-constexpr int kMaxGridCh = 16;   // features per cell of one grid
+constexpr int kMaxGridCh = 20;   // features per cell of one grid (Sec. 6: profile 0.5's G1)
+constexpr int kGridPad = 24;     // kMaxGridCh rounded up to whole groups of 8 features
+constexpr int kFastGridCh = 16;  // widest grid of the 16-byte-vector gather paths
 
 // ---------------------------------------------------------------------------
 // Counter-based random numbers: SplitMix64 (Steele, Lea & Flood, OOPSLA 2014),
@@ -193,7 +195,7 @@ __host__ __device__ __forceinline__ int cell_bytes(int c, int bits) {
 // Features of one grid at texel (x, y) of mip m: acc[ch] = sum_t w_t g_t[ch].
 // ---------------------------------------------------------------------------
 struct GridSample {
-  float acc[kMaxGridCh];
+  float acc[kGridPad];  // channels >= c are zero
 };
 
 // Vector-quantised G0 (vq_books > 0): the c0 features of cell `cell` of
@@ -230,7 +232,7 @@ __device__ __forceinline__ void sample_grid(const ntc_material& M, int j, int k,
   const Taps t = bilinear_taps(x, y, wm, hm, gw, gh);
   if (taps_out) *taps_out = t;
 #pragma unroll
-  for (int ch = 0; ch < kMaxGridCh; ++ch) gs.acc[ch] = 0.f;
+  for (int ch = 0; ch < kGridPad; ++ch) gs.acc[ch] = 0.f;
   if (k == 0 && M.vq_books > 0) {
 #pragma unroll
     for (int tp = 0; tp < 4; ++tp) {

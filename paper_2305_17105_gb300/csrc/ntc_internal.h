@@ -44,6 +44,16 @@ cudaError_t launch_decode_tc(const ntc_material& m, const float* uvl, int64_t n,
 // the operand tiles of two pipelines fit one CTA (k_int <= 96).
 bool train_tc_supported(const ntc_material& m);
 cudaError_t launch_train_tc(const ntc_material& m, const BwdArgs& a, cudaStream_t s);
+// The FP8-E4M3 form of the fused step (R24: E4M3 forward on kind::f8f6f4,
+// FP16 backward on the same values, straight-through); m.w[] hold E4M3
+// bytes and m.scale 9 floats (s_w[3], s_a[3], layer-input maxima[3]).
+cudaError_t launch_train_tc_f8(const ntc_material& m, const BwdArgs& a, cudaStream_t s);
+// The FP8 step's pre-pass: s_w[l] = the smallest power of two with
+// max|W_l| / s_w <= 448 from the FP32 masters, W8_l = e4m3(W_l / s_w[l])
+// into the material's weight bytes, and s_a[l] from the layer-input maxima
+// the previous step recorded (kept where none was recorded), which it clears.
+cudaError_t launch_f8_train_prep(const float* const* w_master, uint8_t* const* w8, int k_in,
+                                 int channels, float* scale9, cudaStream_t s);
 
 // Adam over the segments of the trainer's parameter array.
 // grids (2 per level), W1..W3 and biases (6), the third hidden layer (2), codebooks (1)
@@ -91,6 +101,14 @@ struct NoiseArgs {
 };
 constexpr int kNoiseBlock = 256;
 cudaError_t launch_noise_grids(const NoiseArgs& a, cudaStream_t s);
+// FP8-E4M3 form: one weight matrix quantised with its scale max|W| / 448, and
+// the power-of-two activation scales from the per-layer input maxima of an
+// FP32 decode of calibration queries (amax: 3 words of scratch, may alias sa).
+cudaError_t launch_f8_weights(const float* w, int rows, int cols, int cols_out, uint8_t* w8,
+                              float* scale, cudaStream_t s);
+cudaError_t launch_f8_calibrate(const ntc_material& m, const float* uvl, int64_t n,
+                                uint32_t* amax, float* sa, cudaStream_t s);
+
 cudaError_t launch_advance_step(int64_t* step, cudaStream_t s);
 
 cudaError_t launch_quantize_pack(const float* values, int64_t cells, int c, int bits, float q,

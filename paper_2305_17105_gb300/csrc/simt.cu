@@ -229,6 +229,65 @@ __global__ void __launch_bounds__(kThreads) decode_simt_kernel(
   }
 }
 
+// Calibration of the FP8-E4M3 form: the largest magnitude of each layer's
+// input (the feature row, act(Z1), act(Z2)) over the nearest decodes of the
+// queries, in FP32, reduced per warp and merged into amax[3] (float bits;
+// every value is non-negative, so the unsigned order is the float order).
+__global__ void __launch_bounds__(kThreads) f8_calib_kernel(const ntc_material M,
+                                                            const float* __restrict__ uvl,
+                                                            int64_t n, uint32_t* amax) {
+  extern __shared__ __align__(16) float smem[];
+  const int K = M.k_in;
+  const SW L(K, false);
+  float* sw = smem;
+  stage_weights(M, L, sw);
+  __syncthreads();
+  RowSink sink{smem + L.size + threadIdx.x * row_stride(K)};
+  float mx[3] = {0.f, 0.f, 0.f};
+  for (int64_t q = (int64_t)blockIdx.x * kThreads + threadIdx.x; q < n;
+       q += (int64_t)gridDim.x * kThreads) {
+    int x, yy, m;
+    query_texel(M, uvl[3 * q], uvl[3 * q + 1], uvl[3 * q + 2], x, yy, m);
+    featurize(M, x, yy, m, false, 0, sink);
+    for (int k = 0; k < K; ++k) mx[0] = fmaxf(mx[0], fabsf(sink.row[k]));
+    float h1[kHidden], h2[kHidden];
+    layer1(sw + L.w1t, sw + L.b1, sink.row, K, h1);
+#pragma unroll
+    for (int i = 0; i < kHidden; ++i) {
+      h1[i] = act_fwd(M.act, h1[i]);
+      mx[1] = fmaxf(mx[1], fabsf(h1[i]));
+    }
+    dense64<kHidden>(sw + L.w2, sw + L.b2, h1, h2);
+#pragma unroll
+    for (int i = 0; i < kHidden; ++i) mx[2] = fmaxf(mx[2], fabsf(act_fwd(M.act, h2[i])));
+  }
+#pragma unroll
+  for (int l = 0; l < 3; ++l) {
+    float v = mx[l];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(&amax[l], __float_as_uint(v));
+  }
+}
+
+// amax[3] (float bits) -> the activation scales s_a[l]: the smallest power
+// of two with amax / s_a <= 448 (the largest finite E4M3 value); 1 for an
+// all-zero input.
+__global__ void f8_scales_kernel(const uint32_t* amax, float* sa) {
+  const int l = threadIdx.x;
+  if (l >= 3) return;
+  const float a = __uint_as_float(amax[l]);
+  float s = 1.f;
+  if (a > 0.f && a < __int_as_float(0x7f800000)) {
+    int e = 0;
+    const float f = frexpf(a / 448.f, &e);  // a / 448 = f 2^e, f in [0.5, 1)
+    if (f == 0.5f) e -= 1;                    // an exact power of two needs no headroom
+    e = e < -126 ? -126 : (e > 127 ? 127 : e);
+    s = __int_as_float((127 + e) << 23);
+  }
+  sa[l] = s;
+}
+
 // ---------------------------------------------------------------------------
 // Fused forward + loss + backward (Sec. 5.1): per 128-texel tile,
 //  A) per thread: texel, features (+noise), forward; the pre-activations Z1,
@@ -519,6 +578,25 @@ cudaError_t launch_decode_simt(const ntc_material& m, const float* uvl, int64_t 
   const int grid = (int)(tiles < cap ? tiles : cap);
   decode_simt_kernel<<<grid, kThreads, smem, s>>>(m, uvl, n, out, out_dtype, filter, noise, nkey,
                                                   jkey);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_f8_calibrate(const ntc_material& m, const float* uvl, int64_t n,
+                               uint32_t* amax, float* sa, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(amax, 0, 3 * sizeof(uint32_t), s);
+  if (e != cudaSuccess) return e;
+  if (n > 0) {
+    const SW L(m.k_in, false);
+    const size_t smem = (size_t)(L.size + kThreads * row_stride(m.k_in)) * sizeof(float);
+    e = cudaFuncSetAttribute(f8_calib_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t tiles = (n + kThreads - 1) / kThreads;
+    const int64_t cap = (int64_t)sm_count() * 4;
+    f8_calib_kernel<<<(int)(tiles < cap ? tiles : cap), kThreads, smem, s>>>(m, uvl, n, amax);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  f8_scales_kernel<<<1, 32, 0, s>>>(amax, sa);
   return cudaGetLastError();
 }
 

@@ -746,11 +746,11 @@ __device__ __forceinline__ void generic_grid(const ntc_material& M, const MipTab
     const uint8_t* base = tb->grid0[m];
 #pragma unroll 1
     for (int tp = 0; tp < 4; ++tp) {
-      float acc[kMaxGridCh];
+      float acc[kGridPad];
       if (VQ && M.vq_books > 0) {
         const int cell = r.valid ? t.cell[tp] : 0;
 #pragma unroll
-        for (int ch = 0; ch < kMaxGridCh; ++ch) acc[ch] = 0.f;
+        for (int ch = 0; ch < kGridPad; ++ch) acc[ch] = 0.f;
         for (int b = 0; b < M.vq_books; ++b) {
           const float* e = M.codebook0 + ((size_t)b * 256 + base[(size_t)cell * M.vq_books + b]) * c;
 #pragma unroll
@@ -761,15 +761,15 @@ __device__ __forceinline__ void generic_grid(const ntc_material& M, const MipTab
         const int off = (1 << (M.bits0 - 1)) - 1;
         const Cell cl = load_cell(base, r.valid ? t.cell[tp] : 0, P.cb0);
 #pragma unroll
-        for (int ch = 0; ch < kMaxGridCh; ++ch)
+        for (int ch = 0; ch < kGridPad; ++ch)
           acc[ch] = ch < c ? (float)((int)cell_index(cl, ch, M.bits0) - off) * q : 0.f;
       } else {
         const float* g = reinterpret_cast<const float*>(base) + (size_t)(r.valid ? t.cell[tp] : 0) * c;
 #pragma unroll
-        for (int ch = 0; ch < kMaxGridCh; ++ch) acc[ch] = ch < c ? __ldg(g + ch) : 0.f;
+        for (int ch = 0; ch < kGridPad; ++ch) acc[ch] = ch < c ? __ldg(g + ch) : 0.f;
       }
 #pragma unroll
-      for (int g2 = 0; g2 < 2; ++g2)
+      for (int g2 = 0; g2 < kGridPad / 8; ++g2)
         if (g2 < f0t) {
           float v[8];
 #pragma unroll
@@ -779,9 +779,9 @@ __device__ __forceinline__ void generic_grid(const ntc_material& M, const MipTab
     }
     return;
   }
-  float acc[kMaxGridCh];
+  float acc[kGridPad];
 #pragma unroll
-  for (int ch = 0; ch < kMaxGridCh; ++ch) acc[ch] = 0.f;
+  for (int ch = 0; ch < kGridPad; ++ch) acc[ch] = 0.f;
   if (r.valid) {
     Taps t;
     if (k) taps_of(r.x, r.y, tb->sx1[m], tb->sy1[m], tb->g1w[m], tb->g1h[m], t);
@@ -841,7 +841,7 @@ __device__ __forceinline__ void generic_grid(const ntc_material& M, const MipTab
   }
   const int ng = k ? P.f1 : P.f0;
 #pragma unroll
-  for (int g = 0; g < 2; ++g)
+  for (int g = 0; g < kGridPad / 8; ++g)
     if (g < ng) {
       float v[8];
 #pragma unroll

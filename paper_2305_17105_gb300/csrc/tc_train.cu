@@ -5,8 +5,11 @@
 namespace ntc {
 
 bool train_tc_supported(const ntc_material& m) {
-  return m.precision == NTC_PREC_F16 && (m.act == NTC_ACT_RELU || m.act == NTC_ACT_HARDGELU) &&
-         train_pipelines(m) > 0;
+  if (m.act != NTC_ACT_RELU && m.act != NTC_ACT_HARDGELU) return false;
+  if (m.precision == NTC_PREC_F8)  // FP8 form: bilinear G0, two hidden layers, K in 32s
+    return m.interp0 == NTC_INTERP_BILINEAR && m.hidden_layers != 3 && m.k_in % 32 == 0 &&
+           m.vq_books == 0 && m.scale != nullptr && train_pipelines(m) > 0;
+  return m.precision == NTC_PREC_F16 && train_pipelines(m) > 0;
 }
 
 void train_widths(const ntc_material& m, int* k_int, int* dx_n) {
@@ -23,6 +26,7 @@ int train_pipelines_layout(const ntc_material& first, int k_lay, int dx_lay) {
 cudaError_t launch_train_tc(const ntc_material& m, const BwdArgs& a, cudaStream_t s) {
   if (a.n == 0) return cudaSuccess;
   if (!train_tc_supported(m) || (!a.train && !a.dout)) return cudaErrorNotSupported;
+  if (m.precision == NTC_PREC_F8) return launch_train_tc_f8(m, a, s);
   return launch_class<false>(m, a, nullptr, (a.n + kRows - 1) / kRows, 0, 0, s);
 }
 

@@ -69,8 +69,12 @@ constexpr uint32_t kSmemMax = 232448u - 2048u;  // dynamic shared memory (static
 // four taps' 4 c0 values with learned interpolation), G1 groups,
 // [PE0..7][PE8..11, LOD, 0, 1, 1], zero groups up to k_int.
 struct TPlan {
-  int w0, f0, f1, gpe, k_int, dx_n, nwg, h3;
+  int w0, f0, f1, gpe, k_int, dx_n, nwg, h3, f8, k8;
   uint32_t w1, w2, w3, wb2, wb3, wh, wbh, tab, wg0, wg_bytes, total;
+  // FP8-E4M3 forward (R24): E4M3 weight tiles, FP32 biases, and per
+  // pipeline S8, the E4M3 tile of H2 (X's E4M3 tile lives in the H1 tile
+  // and H1's in the H2 tile until the MMA that reads each has completed)
+  uint32_t w1_8, w2_8, w3_8, bf, S8;
   uint32_t dmax, colW1, colW2, colWh, colW3, cols;  // TMEM: D of pipeline p at p dmax, then
                                                     // the shared weight-gradient accumulators
   // offsets inside one pipeline's region, in this order (the MN-major reads
@@ -85,7 +89,7 @@ struct TPlan {
   // columns follow the larger of them and this material's own, so that
   // every material of a batch shares one layout (0: this material alone).
   __host__ __device__ TPlan(int c0, int c1, bool learned, bool gelu, int n_wg, bool third,
-                            int k_lay = 0, int dx_lay = 0) {
+                            int k_lay = 0, int dx_lay = 0, bool fp8 = false) {
     w0 = learned ? 4 * c0 : c0;
     f0 = (w0 + 7) / 8;
     f1 = (c1 + 7) / 8;
@@ -94,6 +98,8 @@ struct TPlan {
     dx_n = (8 * gpe + 15) / 16 * 16;     // dX columns: the grid slots
     nwg = n_wg;
     h3 = third;
+    f8 = fp8;
+    k8 = (k_int + 31) / 32 * 32;  // E4M3 K-steps take 32 inputs
     const int kl = k_int > k_lay ? k_int : k_lay, dl = dx_n > dx_lay ? dx_n : dx_lay;
     uint32_t o = 0;
     w1 = o;  o += kHidden * kl * 2;      // W1 [64][k_int]: B of layer 1, MN-major B of dX
@@ -105,6 +111,10 @@ struct TPlan {
     wbh = o; o += h3 ? kHidden * 16 * 2 : 0;
     o = (o + 15) / 16 * 16;
     tab = o; o += 16 * 16 * 4;           // per-mip table (MipTabT)
+    w1_8 = o; o += fp8 ? kHidden * k8 : 0;
+    w2_8 = o; o += fp8 ? kHidden * kHidden : 0;
+    w3_8 = o; o += fp8 ? kN3 * kHidden : 0;
+    bf = o;   o += fp8 ? (2 * kHidden + kN3) * 4 : 0;
     o = (o + 1023) / 1024 * 1024;
     wg0 = o;
     H1 = 0;
@@ -121,6 +131,8 @@ struct TPlan {
     G3 = G2 + (gelu ? 8 * kGroup : 0);
     wg_bytes = G3 + (gelu && h3 ? 8 * kGroup : 0);
     if (wg_bytes < HL + 16 * kGroup) wg_bytes = HL + 16 * kGroup;
+    S8 = wg_bytes;
+    if (fp8) wg_bytes += kRows * kHidden;
     total = wg0 + nwg * wg_bytes;
     dmax = dl > kHidden ? dl : kHidden;
     colW1 = nwg * dmax;
@@ -132,7 +144,7 @@ struct TPlan {
   // fits one CTA: shared memory, TMEM, the dX staging rows
   __host__ __device__ bool fits() const {
     return total <= kSmemMax && cols <= kCols && (uint32_t)kRows * kDxStride * 4 <= wg_bytes &&
-           dmax <= kDxStride && colW2 - colW1 <= 2 * kHidden;
+           dmax <= kDxStride && colW2 - colW1 <= 2 * kHidden && (!f8 || (!h3 && k8 <= 2 * kHidden));
   }
 };
 
@@ -170,10 +182,64 @@ __device__ __forceinline__ __half w_at(const ntc_material& M, int l, int idx) {
   return static_cast<const __half*>(M.w[l])[idx];
 }
 
+// Packed E4M3x2 (byte 0 -> low half) -> packed f16x2; exact (every E4M3
+// value is an FP16 value).
+__device__ __forceinline__ uint32_t e4m3x2_to_f16x2(uint32_t b) {
+  uint32_t d;
+  const uint16_t h = (uint16_t)b;
+  asm("cvt.rn.f16x2.e4m3x2 %0, %1;\n" : "=r"(d) : "h"(h));
+  return d;
+}
+
+// E4M3 byte -> FP16 (exact).
+__device__ __forceinline__ __half e4m3_to_half(uint8_t b) {
+  union { uint32_t u; __half2 h; } c;
+  c.u = e4m3x2_to_f16x2(b);
+  return __low2half(c.h);
+}
+
+// FP8 form (R24): the material's weights are E4M3 bytes (the step's pre-pass
+// quantised them from the FP32 masters with power-of-two scales).  The
+// forward reads them as E4M3 tiles; the backward reads FP16 tiles holding
+// the same E4M3 values (unscaled: the scales enter the FP32 epilogues); the
+// biases go to FP32 arrays for the epilogues.
+__device__ void stage_train_f8(const ntc_material& M, const TPlan& P, uint8_t* sm) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const uint8_t* w1 = static_cast<const uint8_t*>(M.w[0]);
+  const uint8_t* w2 = static_cast<const uint8_t*>(M.w[1]);
+  const uint8_t* w3 = static_cast<const uint8_t*>(M.w[2]);
+  for (int i = tid; i < kHidden * P.k8; i += nt) {
+    const int o = i / P.k8, s = i - o * P.k8;
+    const int col = s < P.k_int ? slot_column(M, P, s) : -1;
+    const uint8_t b = col >= 0 ? w1[o * M.k_in + col] : (uint8_t)0;
+    sm[P.w1_8 + tc::canon_offset(o, s, kHidden, 1)] = b;
+    if (s < P.k_int)
+      *reinterpret_cast<__half*>(sm + P.w1 + tc::canon_offset(o, s, kHidden, 2)) = e4m3_to_half(b);
+  }
+  for (int i = tid; i < kHidden * kHidden; i += nt) {
+    const int o = i / kHidden, k = i - o * kHidden;
+    const uint8_t b = w2[i];
+    sm[P.w2_8 + tc::canon_offset(o, k, kHidden, 1)] = b;
+    *reinterpret_cast<__half*>(sm + P.w2 + tc::canon_offset(o, k, kHidden, 2)) = e4m3_to_half(b);
+  }
+  for (int i = tid; i < kN3 * kHidden; i += nt) {
+    const int c = i / kHidden, k = i - c * kHidden;
+    const uint8_t b = c < M.channels ? w3[i] : (uint8_t)0;
+    sm[P.w3_8 + tc::canon_offset(c, k, kN3, 1)] = b;
+    *reinterpret_cast<__half*>(sm + P.w3 + tc::canon_offset(c, k, kN3, 2)) = e4m3_to_half(b);
+  }
+  float* bf = reinterpret_cast<float*>(sm + P.bf);
+  for (int i = tid; i < 2 * kHidden + kN3; i += nt)
+    bf[i] = i < kHidden ? M.b[0][i]
+                        : (i < 2 * kHidden ? M.b[1][i - kHidden]
+                                           : (i - 2 * kHidden < M.channels ? M.b[2][i - 2 * kHidden] : 0.f));
+}
+
 __device__ void stage_train(const ntc_material& M, const TPlan& P, uint8_t* sm) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const __half z = __float2half_rn(0.f);
-  for (int i = tid; i < kHidden * P.k_int; i += nt) {
+  if (P.f8) stage_train_f8(M, P, sm);
+  for (int i = tid; i < kHidden * P.k_int && !P.f8; i += nt) {
     const int o = i / P.k_int, s = i - o * P.k_int;
     const int col = slot_column(M, P, s);
     __half v = z;
@@ -186,11 +252,11 @@ __device__ void stage_train(const ntc_material& M, const TPlan& P, uint8_t* sm) 
     }
     *reinterpret_cast<__half*>(sm + P.w1 + tc::canon_offset(o, s, kHidden, 2)) = v;
   }
-  for (int i = tid; i < kHidden * kHidden; i += nt) {
+  for (int i = tid; i < kHidden * kHidden && !P.f8; i += nt) {
     const int o = i / kHidden, k = i - o * kHidden;
     *reinterpret_cast<__half*>(sm + P.w2 + tc::canon_offset(o, k, kHidden, 2)) = w_at(M, 1, i);
   }
-  for (int i = tid; i < kN3 * kHidden; i += nt) {
+  for (int i = tid; i < kN3 * kHidden && !P.f8; i += nt) {
     const int c = i / kHidden, k = i - c * kHidden;
     *reinterpret_cast<__half*>(sm + P.w3 + tc::canon_offset(c, k, kN3, 2)) =
         c < M.channels ? w_at(M, 2, i) : z;
@@ -343,8 +409,8 @@ __device__ __forceinline__ void ld_nc_v8(const float* p, float4& a, float4& b) {
       : "l"(p));
 }
 
-// Bilinear sample of one FP32 grid of 4k channels with 16-byte loads, all
-// taps' loads issued before the interpolation (same FMA order as
+// Bilinear sample of one FP32 grid of 4k <= 16 channels with 16-byte loads,
+// all taps' loads issued before the interpolation (same FMA order as
 // sample_grid, so the same values).
 __device__ __forceinline__ void sample_grid_f32x4(const ntc_material& M, int j, int k, int x, int y,
                                                   int wm, int hm, GridSample& gs) {
@@ -353,7 +419,7 @@ __device__ __forceinline__ void sample_grid_f32x4(const ntc_material& M, int j, 
   const int c4 = (k ? M.c1 : M.c0) >> 2;
   const Taps t = bilinear_taps(x, y, wm, hm, gw, gh);
   const float4* g = static_cast<const float4*>(k ? L.grid1 : L.grid0);
-  float4 v[4][kMaxGridCh / 4];
+  float4 v[4][kFastGridCh / 4];
   if ((c4 == 2 || c4 == 4) && (reinterpret_cast<uintptr_t>(g) & 31) == 0) {
     // 32-byte loads: one L1 wavefront brings 8 channels
 #pragma unroll
@@ -368,15 +434,15 @@ __device__ __forceinline__ void sample_grid_f32x4(const ntc_material& M, int j, 
 #pragma unroll
     for (int tp = 0; tp < 4; ++tp)
 #pragma unroll
-      for (int q = 0; q < kMaxGridCh / 4; ++q)
+      for (int q = 0; q < kFastGridCh / 4; ++q)
         v[tp][q] = q < c4 ? __ldg(g + (size_t)t.cell[tp] * c4 + q) : make_float4(0.f, 0.f, 0.f, 0.f);
   }
 #pragma unroll
-  for (int ch = 0; ch < kMaxGridCh; ++ch) gs.acc[ch] = 0.f;
+  for (int ch = 0; ch < kGridPad; ++ch) gs.acc[ch] = 0.f;
 #pragma unroll
   for (int tp = 0; tp < 4; ++tp)
 #pragma unroll
-    for (int q = 0; q < kMaxGridCh / 4; ++q) {
+    for (int q = 0; q < kFastGridCh / 4; ++q) {
       gs.acc[4 * q] = fmaf(t.w[tp], v[tp][q].x, gs.acc[4 * q]);
       gs.acc[4 * q + 1] = fmaf(t.w[tp], v[tp][q].y, gs.acc[4 * q + 1]);
       gs.acc[4 * q + 2] = fmaf(t.w[tp], v[tp][q].z, gs.acc[4 * q + 2]);
@@ -424,16 +490,103 @@ __device__ __forceinline__ void hidden_forward(uint32_t taddr, uint8_t* htile, u
   }
 }
 
+// FP8 form: eight features of a row rounded to E4M3 in units of the layer-1
+// activation scale (x_hat = s_a e4m3(x / s_a)): the E4M3 bytes go to the A
+// tile of layer 1 (laid over the H1 tile), the same values in FP16 (unscaled)
+// to X for the weight-gradient MMA.  `ones`: the group holding the two
+// constant-one slots (elements 6, 7), which stay 1 in X and 0 in the E4M3
+// tile (the biases enter the epilogue).  amax: the largest |x| seen.
+__device__ __forceinline__ void put_x8(uint8_t* W, const TPlan& P, int row, int g,
+                                       const float (&v)[8], float inv, bool ones, float& amax) {
+  uint32_t h[4], b[2] = {0u, 0u};
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const bool one = ones && j == 3;
+    if (!one) amax = fmaxf(amax, fmaxf(fabsf(v[2 * j]), fabsf(v[2 * j + 1])));
+    const uint32_t e = one ? 0u : tc::pack_e4m3x2(v[2 * j] * inv, v[2 * j + 1] * inv);
+    h[j] = one ? tc::pack_f16x2(1.f, 1.f) : e4m3x2_to_f16x2(e);
+    b[j >> 1] |= e << (16 * (j & 1));
+  }
+  *reinterpret_cast<uint4*>(W + P.X + (uint32_t)g * kGroup + tc::canon_chunk(row, 0, kRows)) =
+      make_uint4(h[0], h[1], h[2], h[3]);
+  *reinterpret_cast<uint2*>(W + P.H1 + tc::canon_chunk(row, g >> 1, kRows) + (g & 1) * 8) =
+      make_uint2(b[0], b[1]);
+}
+
+// FP8 forward epilogue of a hidden layer: z = s_in acc + b (s_in = s_a s_w of
+// the layer), H = act(z) rounded to E4M3 in units of the next layer's
+// activation scale (inv = 1 / s_a'): bytes into `h8` (the next layer's A
+// tile), the same values in FP16 into `h16` (for the backward); a ReLU unit
+// with z > 0 whose value rounds to zero is stored as -0 so that the backward
+// still reads its mask.  hardGELU writes act'(z) into `gtile`.
+template <int ACT>
+__device__ __forceinline__ void hidden_forward_f8(uint32_t taddr, float s_in, const float* bias,
+                                                  float inv, uint8_t* h16, uint8_t* h8,
+                                                  uint8_t* gtile, int row, float& amax) {
+#pragma unroll
+  for (int half = 0; half < 2; ++half) {
+    float a[16], b[16];
+    tc::tmem_ld16(taddr + 32 * half, a);
+    tc::tmem_ld16(taddr + 32 * half + 16, b);
+    tc::tmem_ld_wait();
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      float z[8], dv[8];
+      uint32_t hw[4], bw[2] = {0u, 0u};
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int i = 8 * g + e;
+        z[e] = fmaf(i < 16 ? a[i] : b[i - 16], s_in, bias[32 * half + i]);
+        dv[e] = act_grad(ACT, z[e]);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float h0 = act_fwd(ACT, z[2 * j]), h1 = act_fwd(ACT, z[2 * j + 1]);
+        amax = fmaxf(amax, fmaxf(fabsf(h0), fabsf(h1)));
+        const uint32_t e = tc::pack_e4m3x2(h0 * inv, h1 * inv);
+        uint32_t f = e4m3x2_to_f16x2(e);
+        if (ACT == NTC_ACT_RELU) {
+          if (z[2 * j] > 0.f && (f & 0xFFFFu) == 0u) f |= 0x8000u;
+          if (z[2 * j + 1] > 0.f && (f >> 16) == 0u) f |= 0x80000000u;
+        }
+        hw[j] = f;
+        bw[j >> 1] |= e << (16 * (j & 1));
+      }
+      const int gg = 4 * half + g;
+      *reinterpret_cast<uint4*>(h16 + tc::canon_chunk(row, gg, kRows)) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+      *reinterpret_cast<uint2*>(h8 + tc::canon_chunk(row, gg >> 1, kRows) + (gg & 1) * 8) =
+          make_uint2(bw[0], bw[1]);
+      if (ACT == NTC_ACT_HARDGELU) put_chunk(gtile, row, gg, dv);
+    }
+  }
+}
+
+__device__ __forceinline__ void issue_kmajor_f8(uint32_t d, uint32_t a, uint32_t a_lbo, uint32_t b,
+                                                uint32_t b_lbo, int ksteps, uint32_t id) {
+  for (int s = 0; s < ksteps; ++s)
+    tc::mma_f8(d, tc::smem_desc(a + 2 * s * a_lbo, a_lbo, 128),
+               tc::smem_desc(b + 2 * s * b_lbo, b_lbo, 128), id, s > 0);
+}
+
 // Backward epilogue: dZ = dH * act'(Z) over the layer's H tile (this row is
 // read before it is overwritten): ReLU takes act' from the sign of H,
 // hardGELU from the forward's G tile.
-template <int ACT>
+// FP8 form: the accumulator is dZ_next W8 (E4M3 weight values), scaled by
+// the layer's weight scale `sc`; a ReLU unit's mask is any nonzero bit
+// pattern of H (its -0 marks a positive Z whose value rounded to zero).
+template <int ACT, bool F8>
 __device__ __forceinline__ void hidden_backward(uint32_t taddr, const uint8_t* gtile,
-                                                uint8_t* htile, int row) {
+                                                uint8_t* htile, int row, float sc = 1.f) {
   __half2 h[32];
   tile_row64(ACT == NTC_ACT_HARDGELU ? gtile : htile, row, h);
   row64_to_tile(taddr, htile, row, [&](int q, float g) {
-    return ACT == NTC_ACT_HARDGELU ? g * half_of(h, q) : (half_of(h, q) > 0.f ? g : 0.f);
+    if (F8) g *= sc;
+    if (ACT == NTC_ACT_HARDGELU) return g * half_of(h, q);
+    if (F8) {
+      const __half hv = (q & 1) ? __high2half(h[q >> 1]) : __low2half(h[q >> 1]);
+      return __half_as_ushort(hv) != 0 ? g : 0.f;
+    }
+    return half_of(h, q) > 0.f ? g : 0.f;
   });
 }
 
@@ -472,20 +625,20 @@ __device__ __forceinline__ void learned_g0(const ntc_material& M, const TPlan& P
   const ntc_level& L = M.lv[j];
   const Taps t = bilinear_taps(x, y, wm, hm, L.g0_w, L.g0_h);
   const int c = M.c0;
-  if ((c & 3) == 0 && !noise) {
+  if ((c & 3) == 0 && c <= kFastGridCh && !noise) {
     const float* g = static_cast<const float*>(L.grid0);
-    float4 v[4][kMaxGridCh / 4];
+    float4 v[4][kFastGridCh / 4];
 #pragma unroll
     for (int tp = 0; tp < 4; ++tp)
 #pragma unroll
-      for (int q = 0; q < kMaxGridCh / 4; ++q)
+      for (int q = 0; q < kFastGridCh / 4; ++q)
         v[tp][q] = (valid && 4 * q < c)
                        ? __ldg(reinterpret_cast<const float4*>(g + (size_t)t.cell[tp] * c) + q)
                        : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
     for (int tp = 0; tp < 4; ++tp)
 #pragma unroll
-      for (int q = 0; q < kMaxGridCh / 4; ++q)
+      for (int q = 0; q < kFastGridCh / 4; ++q)
         if (4 * q < c) put_half4(W, P, row, tp * c + 4 * q, v[tp][q]);
   } else {
 #pragma unroll
@@ -532,7 +685,7 @@ __device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t& phase, int b
 // runs its tiles on the NWG pipelines, waits for their MMAs and flushes the
 // accumulators into that material's gradient.  Otherwise one material (M0,
 // A0) whose tiles the CTAs take in turn, NWG at a time.
-template <int ACT, bool LEARNED, int NWG, bool BATCHED>
+template <int ACT, bool LEARNED, int NWG, bool BATCHED, bool F8>
 __global__ void __launch_bounds__(kRows* NWG, 1) train_tc_kernel(const ntc_material M0,
                                                                   const BwdArgs A0,
                                                                   const TrainBatchDev* hb,
@@ -602,9 +755,18 @@ __global__ void __launch_bounds__(kRows* NWG, 1) train_tc_kernel(const ntc_mater
     t_step = (int64_t)gridDim.x * NWG;
   }
   const TPlan P(M.c0, M.c1, LEARNED, ACT == NTC_ACT_HARDGELU, NWG, M.hidden_layers == 3, k_lay,
-                dx_lay);
+                dx_lay, F8);
   const int C = M.channels;
   stage_train(M, P, sm);
+  // FP8 form: this step's scales (weights s_w, layer inputs s_a; powers of
+  // two written by the step's pre-pass) and the largest |input| of each
+  // layer seen by this thread (delayed scaling of the next step)
+  float sw[3] = {1.f, 1.f, 1.f}, sa[3] = {1.f, 1.f, 1.f}, am[3] = {0.f, 0.f, 0.f};
+  if (F8)
+    for (int l = 0; l < 3; ++l) {
+      sw[l] = M.scale[l];
+      sa[l] = M.scale[3 + l];
+    }
   if (tid == 0) dout_max = 0u;
   tc::fence_proxy_async();
   tc::fence_before_sync();
@@ -707,16 +869,17 @@ __global__ void __launch_bounds__(kRows* NWG, 1) train_tc_kernel(const ntc_mater
 #pragma unroll
       for (int k = LEARNED ? 1 : 0; k < 2; ++k) {
         const int ck = k ? M.c1 : M.c0;
-        if (!A.noise && (ck & 3) == 0) sample_grid_f32x4(M, j, k, x, y, wm, hm, gs);
+        if (!A.noise && (ck & 3) == 0 && ck <= kFastGridCh) sample_grid_f32x4(M, j, k, x, y, wm, hm, gs);
         else sample_grid(M, j, k, x, y, wm, hm, A.noise != 0 && valid, nkey, gs);
         const int g0 = k ? P.f0 : 0, ng = k ? P.f1 : P.f0;
 #pragma unroll
-        for (int g = 0; g < 2; ++g)
+        for (int g = 0; g < kGridPad / 8; ++g)
           if (g < ng) {
             float v[8];
 #pragma unroll
             for (int e = 0; e < 8; ++e) v[e] = valid ? gs.acc[8 * g + e] : 0.f;
-            put_x(W, P, row, g0 + g, v);
+            if (F8) put_x8(W, P, row, g0 + g, v, 1.f / sa[0], false, am[0]);
+            else put_x(W, P, row, g0 + g, v);
           }
       }
       struct Pe {
@@ -727,15 +890,25 @@ __global__ void __launch_bounds__(kRows* NWG, 1) train_tc_kernel(const ntc_mater
       float v[8];
 #pragma unroll
       for (int e = 0; e < 8; ++e) v[e] = pe.v[e];
-      put_x(W, P, row, P.gpe, v);
+      if (F8) put_x8(W, P, row, P.gpe, v, 1.f / sa[0], false, am[0]);
+      else put_x(W, P, row, P.gpe, v);
 #pragma unroll
       for (int e = 0; e < 4; ++e) v[e] = pe.v[8 + e];
       v[4] = tb->lodn[m];
       v[5] = 0.f;
       v[6] = v[7] = 1.f;
-      put_x(W, P, row, P.gpe + 1, v);
+      if (F8) put_x8(W, P, row, P.gpe + 1, v, 1.f / sa[0], true, am[0]);
+      else put_x(W, P, row, P.gpe + 1, v);
       const float zz[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-      for (int g = P.gpe + 2; g < P.k_int / 8; ++g) put_x(W, P, row, g, zz);
+      for (int g = P.gpe + 2; g < P.k_int / 8; ++g) {
+        if (F8) put_x8(W, P, row, g, zz, 1.f, false, am[0]);
+        else put_x(W, P, row, g, zz);
+      }
+      // the E4M3 tile's K padding up to a multiple of 32 inputs
+      if (F8)
+        for (int g = P.k_int / 8; g < P.k8 / 8; ++g)
+          *reinterpret_cast<uint2*>(W + P.H1 + tc::canon_chunk(row, g >> 1, kRows) + (g & 1) * 8) =
+              make_uint2(0u, 0u);
     }
     tc::fence_proxy_async();
     tc::bar_sync(bar_id, kRows);
@@ -743,15 +916,23 @@ __global__ void __launch_bounds__(kRows* NWG, 1) train_tc_kernel(const ntc_mater
     // ---- layer 1 -----------------------------------------------------------------
     if (row == 0) {
       tc::fence_after_sync();
-      issue_kmajor(tD, sW + P.X, lbo_a, sbase + P.w1, lbo64, P.k_int / 16, id64, 0);
-      for (int s = 0; s < P.k_int / 16; ++s)
-        tc::mma_f16(tD, tc::smem_desc(sW + xlo_group(P, 2 * s), lbo_a, 128),
-                    tc::smem_desc(sbase + P.w1 + 2 * s * lbo64, lbo64, 128), id64, 1);
+      if (F8) {
+        issue_kmajor_f8(tD, sW + P.H1, lbo_a, sbase + P.w1_8, lbo64, P.k8 / 32, id64);
+      } else {
+        issue_kmajor(tD, sW + P.X, lbo_a, sbase + P.w1, lbo64, P.k_int / 16, id64, 0);
+        for (int s = 0; s < P.k_int / 16; ++s)
+          tc::mma_f16(tD, tc::smem_desc(sW + xlo_group(P, 2 * s), lbo_a, 128),
+                      tc::smem_desc(sbase + P.w1 + 2 * s * lbo64, lbo64, 128), id64, 1);
+      }
       tc::mma_commit(bar);
     }
     if (!wait_phase(bar, phase, bar_id)) { aborted = true; break; }
     tc::fence_after_sync();
-    hidden_forward<ACT>(tD + lane, W + P.H1, W + P.G1, W + P.H2, row);
+    if (F8)
+      hidden_forward_f8<ACT>(tD + lane, sa[0] * sw[0], reinterpret_cast<const float*>(sm + P.bf),
+                             1.f / sa[1], W + P.H1, W + P.H2, W + P.G1, row, am[1]);
+    else
+      hidden_forward<ACT>(tD + lane, W + P.H1, W + P.G1, W + P.H2, row);
     tc::fence_before_sync();
     tc::fence_proxy_async();
     tc::bar_sync(bar_id, kRows);
@@ -759,14 +940,23 @@ __global__ void __launch_bounds__(kRows* NWG, 1) train_tc_kernel(const ntc_mater
     // ---- layer 2 -----------------------------------------------------------------
     if (row == 0) {
       tc::fence_after_sync();
-      issue_kmajor(tD, sW + P.H1, lbo_a, sbase + P.w2, lbo64, 4, id64, 0);
-      issue_kmajor(tD, sW + P.H2, lbo_a, sbase + P.w2, lbo64, 4, id64, 1);
-      issue_kmajor(tD, sW + P.ONEa, lbo_a, sbase + P.wb2, lbo64, 1, id64, 1);
+      if (F8) {
+        issue_kmajor_f8(tD, sW + P.H2, lbo_a, sbase + P.w2_8, lbo64, 2, id64);
+      } else {
+        issue_kmajor(tD, sW + P.H1, lbo_a, sbase + P.w2, lbo64, 4, id64, 0);
+        issue_kmajor(tD, sW + P.H2, lbo_a, sbase + P.w2, lbo64, 4, id64, 1);
+        issue_kmajor(tD, sW + P.ONEa, lbo_a, sbase + P.wb2, lbo64, 1, id64, 1);
+      }
       tc::mma_commit(bar);
     }
     if (!wait_phase(bar, phase, bar_id)) { aborted = true; break; }
     tc::fence_after_sync();
-    hidden_forward<ACT>(tD + lane, W + P.H2, W + P.G2, P.h3 ? W + P.H3 : nullptr, row);
+    if (F8)
+      hidden_forward_f8<ACT>(tD + lane, sa[1] * sw[1],
+                             reinterpret_cast<const float*>(sm + P.bf) + kHidden, 1.f / sa[2],
+                             W + P.H2, W + P.S8, W + P.G2, row, am[2]);
+    else
+      hidden_forward<ACT>(tD + lane, W + P.H2, W + P.G2, P.h3 ? W + P.H3 : nullptr, row);
     tc::fence_before_sync();
     tc::fence_proxy_async();
     tc::bar_sync(bar_id, kRows);
@@ -791,8 +981,12 @@ __global__ void __launch_bounds__(kRows* NWG, 1) train_tc_kernel(const ntc_mater
     // ---- layer 3, loss, dZ3 ----------------------------------------------------
     if (row == 0) {
       tc::fence_after_sync();
-      issue_kmajor(tD, sW + P.HL, lbo_a, sbase + P.w3, lbo16, 4, id16, 0);
-      issue_kmajor(tD, sW + P.ONEa, lbo_a, sbase + P.wb3, lbo16, 1, id16, 1);
+      if (F8) {
+        issue_kmajor_f8(tD, sW + P.S8, lbo_a, sbase + P.w3_8, lbo16, 2, id16);
+      } else {
+        issue_kmajor(tD, sW + P.HL, lbo_a, sbase + P.w3, lbo16, 4, id16, 0);
+        issue_kmajor(tD, sW + P.ONEa, lbo_a, sbase + P.wb3, lbo16, 1, id16, 1);
+      }
       tc::mma_commit(bar);
     }
     if (!wait_phase(bar, phase, bar_id)) { aborted = true; break; }
@@ -801,6 +995,11 @@ __global__ void __launch_bounds__(kRows* NWG, 1) train_tc_kernel(const ntc_mater
       float zv[16];
       tc::tmem_ld16(tD + lane, zv);
       tc::tmem_ld_wait();
+      if (F8) {
+        const float* b3 = reinterpret_cast<const float*>(sm + P.bf) + 2 * kHidden;
+#pragma unroll
+        for (int c = 0; c < kN3; ++c) zv[c] = fmaf(zv[c], sa[2] * sw[2], b3[c]);
+      }
       float d[16];
 #pragma unroll
       for (int c = 0; c < kN3; ++c) {
@@ -837,7 +1036,7 @@ __global__ void __launch_bounds__(kRows* NWG, 1) train_tc_kernel(const ntc_mater
     }
     if (!wait_phase(bar, phase, bar_id)) { aborted = true; break; }
     tc::fence_after_sync();
-    hidden_backward<ACT>(tD + lane, W + (P.h3 ? P.G3 : P.G2), W + P.HL, row);
+    hidden_backward<ACT, F8>(tD + lane, W + (P.h3 ? P.G3 : P.G2), W + P.HL, row, sw[2]);
     tc::fence_before_sync();
     tc::fence_proxy_async();
     tc::bar_sync(bar_id, kRows);
@@ -852,7 +1051,7 @@ __global__ void __launch_bounds__(kRows* NWG, 1) train_tc_kernel(const ntc_mater
       }
       if (!wait_phase(bar, phase, bar_id)) { aborted = true; break; }
       tc::fence_after_sync();
-      hidden_backward<ACT>(tD + lane, W + P.G2, W + P.H2, row);
+      hidden_backward<ACT, F8>(tD + lane, W + P.G2, W + P.H2, row);
       tc::fence_before_sync();
       tc::fence_proxy_async();
       tc::bar_sync(bar_id, kRows);
@@ -867,7 +1066,7 @@ __global__ void __launch_bounds__(kRows* NWG, 1) train_tc_kernel(const ntc_mater
     }
     if (!wait_phase(bar, phase, bar_id)) { aborted = true; break; }
     tc::fence_after_sync();
-    hidden_backward<ACT>(tD + lane, W + P.G1, W + P.H1, row);
+    hidden_backward<ACT, F8>(tD + lane, W + P.G1, W + P.H1, row, sw[1]);
     tc::fence_before_sync();
     tc::fence_proxy_async();
     tc::bar_sync(bar_id, kRows);
@@ -881,9 +1080,11 @@ __global__ void __launch_bounds__(kRows* NWG, 1) train_tc_kernel(const ntc_mater
     }
     if (!wait_phase(bar, phase, bar_id)) { aborted = true; break; }
     tc::fence_after_sync();
-    if (A.grids && LEARNED) {
+    const bool staged = LEARNED || M.c0 > kFastGridCh || M.c1 > kFastGridCh;
+    if (A.grids && staged) {
       // dX row -> this thread's staging row (the operand tiles are free now),
-      // then G0 per tap slot (weight 1) and G1 through the bilinear taps
+      // then G0 per tap slot (weight 1; learned interpolation) or through
+      // the bilinear taps, and G1 through the bilinear taps
       float* dxs = reinterpret_cast<float*>(W) + row * kDxStride;
       for (int cb = 0; cb < P.dx_n; cb += 16) {
         float v[16];
@@ -899,11 +1100,11 @@ __global__ void __launch_bounds__(kRows* NWG, 1) train_tc_kernel(const ntc_mater
         const int wm = tb->wm[m], hm = tb->hm[m];
         const ntc_level& L = M.lv[j];
         if (float* g = A.g.grid0[j])
-          scatter_taps(g, M.c0, bilinear_taps(x, y, wm, hm, L.g0_w, L.g0_h), dxs, M.c0, false,
-                       gscale);
+          scatter_taps(g, M.c0, bilinear_taps(x, y, wm, hm, L.g0_w, L.g0_h), dxs,
+                       LEARNED ? M.c0 : 0, !LEARNED, F8 ? gscale * sw[0] : gscale);
         if (float* g = A.g.grid1[j])
           scatter_taps(g, M.c1, bilinear_taps(x, y, wm, hm, L.g1_w, L.g1_h), dxs + 8 * P.f0, 0,
-                       true, gscale);
+                       true, F8 ? gscale * sw[0] : gscale);
       }
       // the staging rows ran over the constant-one tiles: once every row has
       // been read, each thread writes its row's chunks back
@@ -944,7 +1145,7 @@ __global__ void __launch_bounds__(kRows* NWG, 1) train_tc_kernel(const ntc_mater
           const Taps t = bilinear_taps(x, y, wm, hm, k ? L.g1_w : L.g0_w, k ? L.g1_h : L.g0_h);
 #pragma unroll
           for (int tp = 0; tp < 4; ++tp) {
-            const float wgt = t.w[tp] * gscale;
+            const float wgt = t.w[tp] * (F8 ? gscale * sw[0] : gscale);
             float* gp = g + (size_t)t.cell[tp] * c;
             if ((c & 3) == 0) {
 #pragma unroll
@@ -957,7 +1158,7 @@ __global__ void __launch_bounds__(kRows* NWG, 1) train_tc_kernel(const ntc_mater
                 }
             } else {
 #pragma unroll
-              for (int ch = 0; ch < kMaxGridCh; ++ch)
+              for (int ch = 0; ch < kFastGridCh; ++ch)
                 if (ch < c) atomicAdd(gp + ch, (k ? dg1[ch] : dg0[ch]) * wgt);
             }
           }
@@ -965,7 +1166,7 @@ __global__ void __launch_bounds__(kRows* NWG, 1) train_tc_kernel(const ntc_mater
       }
     }
     tc::fence_before_sync();
-    if (LEARNED) tc::fence_proxy_async();  // restored constants, read by the next tile's MMAs
+    if (staged) tc::fence_proxy_async();  // restored constants, read by the next tile's MMAs
     tc::bar_sync(bar_id, kRows);  // the next tile's features overwrite the operand tiles
   }
 
@@ -998,7 +1199,7 @@ __global__ void __launch_bounds__(kRows* NWG, 1) train_tc_kernel(const ntc_mater
 #pragma unroll
           for (int e = 0; e < 16; ++e) {
             const int uc = slot_column(M, P, cb + e);
-            if (uc >= 0 && A.g.w[0]) atomicAdd(A.g.w[0] + r * M.k_in + uc, v[e] * gs);
+            if (uc >= 0 && A.g.w[0]) atomicAdd(A.g.w[0] + r * M.k_in + uc, v[e] * gs * sa[0]);
             else if (uc == -2 && A.g.b[0]) atomicAdd(A.g.b[0] + r, v[e] * gs);
           }
         }
@@ -1008,6 +1209,7 @@ __global__ void __launch_bounds__(kRows* NWG, 1) train_tc_kernel(const ntc_mater
         const uint32_t ta = job == 1 ? tW2 : tWh;
         float* gw = job == 1 ? A.g.w[1] : A.g.w_h3;
         float* gb = job == 1 ? A.g.b[1] : A.g.b_h3;
+        const float gsw = gs * (job == 1 ? sa[1] : 1.f);  // FP8: H1 was held in units of s_a1
 #pragma unroll 1
         for (int cb = 0; cb < kHidden + 16; cb += 16) {
           float v[16];
@@ -1016,7 +1218,7 @@ __global__ void __launch_bounds__(kRows* NWG, 1) train_tc_kernel(const ntc_mater
 #pragma unroll
           for (int e = 0; e < 16; ++e) {
             const int col = cb + e;
-            if (col < kHidden && gw) atomicAdd(gw + r * kHidden + col, v[e] * gs);
+            if (col < kHidden && gw) atomicAdd(gw + r * kHidden + col, v[e] * gsw);
             else if (col == kHidden && gb) atomicAdd(gb + r, v[e] * gs);
           }
         }
@@ -1028,10 +1230,22 @@ __global__ void __launch_bounds__(kRows* NWG, 1) train_tc_kernel(const ntc_mater
 #pragma unroll
         for (int c = 0; c < kN3; ++c) {
           if (c >= C) continue;
-          if (r < kHidden && A.g.w[2]) atomicAdd(A.g.w[2] + c * kHidden + r, v[c] * gs);
+          if (r < kHidden && A.g.w[2]) atomicAdd(A.g.w[2] + c * kHidden + r, v[c] * gs * sa[2]);
           if (r == kHidden && A.g.b[2]) atomicAdd(A.g.b[2] + c, v[c] * gs);
         }
       }
+    }
+  }
+  // FP8: the largest |input| of each layer, for the next step's scales
+  if (F8) {
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+      float v = am[l];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+      if ((tid & 31) == 0 && v > 0.f)
+        atomicMax(reinterpret_cast<unsigned int*>(const_cast<float*>(M.scale)) + 6 + l,
+                  __float_as_uint(v));
     }
   }
   // loss
@@ -1060,19 +1274,19 @@ __global__ void __launch_bounds__(kRows* NWG, 1) train_tc_kernel(const ntc_mater
   }
 }
 
-template <int ACT, bool LEARNED, int NWG, bool BATCHED>
+template <int ACT, bool LEARNED, int NWG, bool BATCHED, bool F8>
 cudaError_t launch_t(const ntc_material& m, const BwdArgs& a, const TrainBatchDev* hb,
                      int64_t tiles, int k_lay, int dx_lay, cudaStream_t s) {
   const TPlan P(m.c0, m.c1, LEARNED, ACT == NTC_ACT_HARDGELU, NWG, m.hidden_layers == 3, k_lay,
-                dx_lay);
+                dx_lay, F8);
   const size_t smem = P.total;
-  cudaError_t e = cudaFuncSetAttribute(train_tc_kernel<ACT, LEARNED, NWG, BATCHED>,
+  cudaError_t e = cudaFuncSetAttribute(train_tc_kernel<ACT, LEARNED, NWG, BATCHED, F8>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int64_t ctas = (tiles + NWG - 1) / NWG;
   const int64_t cap = sm_count();
   const int grid = (int)(ctas < cap ? ctas : cap);
-  train_tc_kernel<ACT, LEARNED, NWG, BATCHED>
+  train_tc_kernel<ACT, LEARNED, NWG, BATCHED, F8>
       <<<grid, kRows * NWG, smem, s>>>(m, a, hb, k_lay, dx_lay, status_word());
   return cudaGetLastError();
 }
@@ -1080,19 +1294,21 @@ cudaError_t launch_t(const ntc_material& m, const BwdArgs& a, const TrainBatchDe
 // Pipelines per CTA: the most (3, 2 or 1) whose tiles fit (0: none fits).
 int pipelines_for(const ntc_material& m, int k_lay, int dx_lay) {
   const bool learned = m.interp0 == NTC_INTERP_LEARNED, gelu = m.act == NTC_ACT_HARDGELU;
+  const bool f8 = m.precision == NTC_PREC_F8;
   for (int n = kMaxNWG; n >= 1; --n)
-    if (TPlan(m.c0, m.c1, learned, gelu, n, m.hidden_layers == 3, k_lay, dx_lay).fits()) return n;
+    if (TPlan(m.c0, m.c1, learned, gelu, n, m.hidden_layers == 3, k_lay, dx_lay, f8).fits())
+      return n;
   return 0;
 }
 int train_pipelines(const ntc_material& m) { return pipelines_for(m, 0, 0); }
 
-template <int ACT, bool LEARNED, bool BATCHED>
+template <int ACT, bool LEARNED, bool BATCHED, bool F8>
 cudaError_t launch_n(const ntc_material& m, const BwdArgs& a, const TrainBatchDev* hb,
                      int64_t tiles, int k_lay, int dx_lay, cudaStream_t s) {
   switch (pipelines_for(m, k_lay, dx_lay)) {
-    case 3: return launch_t<ACT, LEARNED, 3, BATCHED>(m, a, hb, tiles, k_lay, dx_lay, s);
-    case 2: return launch_t<ACT, LEARNED, 2, BATCHED>(m, a, hb, tiles, k_lay, dx_lay, s);
-    default: return launch_t<ACT, LEARNED, 1, BATCHED>(m, a, hb, tiles, k_lay, dx_lay, s);
+    case 3: return launch_t<ACT, LEARNED, 3, BATCHED, F8>(m, a, hb, tiles, k_lay, dx_lay, s);
+    case 2: return launch_t<ACT, LEARNED, 2, BATCHED, F8>(m, a, hb, tiles, k_lay, dx_lay, s);
+    default: return launch_t<ACT, LEARNED, 1, BATCHED, F8>(m, a, hb, tiles, k_lay, dx_lay, s);
   }
 }
 
@@ -1101,10 +1317,18 @@ cudaError_t launch_class(const ntc_material& m, const BwdArgs& a, const TrainBat
                          int64_t tiles, int k_lay, int dx_lay, cudaStream_t s) {
   const bool learned = m.interp0 == NTC_INTERP_LEARNED;
   if (m.act == NTC_ACT_HARDGELU)
-    return learned ? launch_n<NTC_ACT_HARDGELU, true, BATCHED>(m, a, hb, tiles, k_lay, dx_lay, s)
-                   : launch_n<NTC_ACT_HARDGELU, false, BATCHED>(m, a, hb, tiles, k_lay, dx_lay, s);
-  return learned ? launch_n<NTC_ACT_RELU, true, BATCHED>(m, a, hb, tiles, k_lay, dx_lay, s)
-                 : launch_n<NTC_ACT_RELU, false, BATCHED>(m, a, hb, tiles, k_lay, dx_lay, s);
+    return learned ? launch_n<NTC_ACT_HARDGELU, true, BATCHED, false>(m, a, hb, tiles, k_lay, dx_lay, s)
+                   : launch_n<NTC_ACT_HARDGELU, false, BATCHED, false>(m, a, hb, tiles, k_lay, dx_lay, s);
+  return learned ? launch_n<NTC_ACT_RELU, true, BATCHED, false>(m, a, hb, tiles, k_lay, dx_lay, s)
+                 : launch_n<NTC_ACT_RELU, false, BATCHED, false>(m, a, hb, tiles, k_lay, dx_lay, s);
+}
+
+// The FP8-E4M3 form (single material, bilinear G0).
+inline cudaError_t launch_class_f8(const ntc_material& m, const BwdArgs& a, int64_t tiles,
+                                   cudaStream_t s) {
+  if (m.act == NTC_ACT_HARDGELU)
+    return launch_n<NTC_ACT_HARDGELU, false, false, true>(m, a, nullptr, tiles, 0, 0, s);
+  return launch_n<NTC_ACT_RELU, false, false, true>(m, a, nullptr, tiles, 0, 0, s);
 }
 
 }  // namespace

@@ -201,9 +201,26 @@ def test_train_step_validation(L):
     assert rc == ntc.ERR_ARG and "params" in L.ntc_last_error().decode()
     rc = L.ntc_train_step(C.byref(m), C.byref(tr), C.byref(tg), 0, 1, None, loss, 0, None)
     assert rc == ntc.ERR_ARG
+    # the FP8 form trains on the tensor cores only, bilinear G0, K in 32s
     m8 = _fake_material(encoding=ntc.GRID_F32, precision=ntc.PREC_F8, scale=0x20000)
-    rc = L.ntc_train_step(C.byref(m8), C.byref(tr), C.byref(tg), 16, 1, None, loss, 0, None)
+    rc = L.ntc_train_step(C.byref(m8), C.byref(tr), C.byref(tg), 16, 1, None, loss,
+                          ntc.FLAG_SIMT, None)
     assert rc == ntc.ERR_UNSUPPORTED
+    m8l = _fake_material(encoding=ntc.GRID_F32, precision=ntc.PREC_F8, scale=0x20000, k_in=64,
+                         act=ntc.ACT_HARDGELU)
+    rc = L.ntc_train_step(C.byref(m8l), C.byref(tr), C.byref(tg), 16, 1, None, loss, 0, None)
+    assert rc == ntc.ERR_ARG and "params" in L.ntc_last_error().decode()  # passes the FP8 checks
+
+
+def test_grid_width_rules(L):
+    """Grids hold 1..20 features per cell (profile 0.5's G1 has 20), packed
+    cells at most 128 bits."""
+    assert _decode_rc(L, _fake_material(c0=12, c1=20, k_in=48), n=0) == ntc.OK
+    assert _decode_rc(L, _fake_material(c0=21, c1=8, k_in=48), n=0) == ntc.ERR_SHAPE
+    assert _decode_rc(L, _fake_material(c0=20, c1=8, bits0=8, k_in=48), n=0) == ntc.ERR_SHAPE
+    assert _decode_rc(L, _fake_material(c0=16, c1=8, bits0=8, k_in=48), n=0) == ntc.OK
+    f32 = _fake_material(c0=20, c1=8, bits0=8, k_in=48, encoding=ntc.GRID_F32)
+    assert _decode_rc(L, f32, n=0) == ntc.OK
 
 
 def test_noalloc_step_refuses_gradient_only(L):

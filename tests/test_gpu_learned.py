@@ -17,11 +17,11 @@ from _gpu import DEV, check_grads, device_material, rel_err, to_np
 pytestmark = pytest.mark.gpu
 OUT_TOL = 2e-3
 
-# (c0 x b0, c1 x b1) of the paper's four profiles (Sec. 6), at small sides;
-# grids hold at most 16 channels here, so profile 0.5's 20-channel G1 runs with 16
+# (c0 x b0, c1 x b1) of the paper's four profiles (the NTC profiles table,
+# Sec. 6), at small sides
 PROFILES = [
     dict(width=256, height=256, channels=9, c0=8, c1=12, bits0=2, bits1=4, k_in=64),   # 0.2
-    dict(width=256, height=128, channels=9, c0=12, c1=16, bits0=4, bits1=4, k_in=80),  # 0.5 (G1 16 of 20)
+    dict(width=256, height=128, channels=9, c0=12, c1=20, bits0=4, bits1=4, k_in=96),  # 0.5
     dict(width=128, height=128, channels=9, c0=12, c1=10, bits0=2, bits1=4, k_in=80),  # 1.0
     dict(width=256, height=256, channels=9, c0=16, c1=12, bits0=4, bits1=4, k_in=96),  # 2.25
 ]
@@ -75,7 +75,10 @@ def test_learned_decode_f16_matches_oracle(shape):
 
 
 def test_learned_and_bilinear_in_one_batch():
-    a = make_case(seed=93, act=1, out_act=1, interp0=1, **PROFILES[1])
+    # profile 2.25's fast layout (profile 0.5's 20-channel G1 decodes on the
+    # generic layout, whose K = 96 plan does not fit the batched kernel's
+    # four per-warpgroup material regions: refused, see below)
+    a = make_case(seed=93, act=1, out_act=1, interp0=1, **PROFILES[3])
     b = make_case(128, 128, 8, 12, 12, k_in=48, seed=94)
     mats = [device_material(a, precision=ntc.PREC_F16), device_material(b, precision=ntc.PREC_F16)]
     qs = [_queries(mats[0][1], 777, 4093), _queries(mats[1][1], 555, 4094)]
@@ -203,3 +206,11 @@ def test_learned_fp32_training_beyond_k64_is_refused():
     target = ntc.Target(gen.box_mip_chain_u8(gen.synthetic_texture(64, 64, 5, seed=1096)))
     with pytest.raises(ntc.NTCError):
         ntc.ntc_train_step(tr, target, 256, 1)
+
+
+def test_batch_refuses_a_plan_too_large_for_its_regions():
+    a = make_case(seed=93, act=1, out_act=1, interp0=1, **PROFILES[1])
+    m, _ = device_material(a, precision=ntc.PREC_F16)
+    with pytest.raises(ntc.NTCError) as ei:
+        ntc.Batch([m], [128])
+    assert ei.value.code == ntc.ERR_UNSUPPORTED
