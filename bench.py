@@ -285,7 +285,7 @@ def make_decode_material(precision, train_steps, batch, device="cuda"):
     return mat, grids_host, w_host, chain, info, forms
 
 
-def make_trainer(precision, total_steps, device="cuda"):
+def make_trainer(precision, total_steps, device="cuda", k_in=TRN_K):
     import paper_2305_17105_gb300 as ntc
     tex = gen.synthetic_texture(TRN_SIDE, TRN_SIDE, TRN_C, seed=1002)
     chain = gen.box_mip_chain_u8(tex)
@@ -296,11 +296,12 @@ def make_trainer(precision, total_steps, device="cuda"):
     for (w0, h0), (w1, h1) in ntc.pyramid(TRN_SIDE, TRN_SIDE):
         g0.append(gen.uniform_grid_values((h0, w0, TRN_C0), lo, hi, rng))
         g1.append(gen.uniform_grid_values((h1, w1, TRN_C0), lo, hi, rng))
-    w = gen.random_mlp(TRN_K, 64, TRN_C, seed=2002, n_used=2 * TRN_C0 + 13)
-    prec = {"f32": ntc.PREC_F32, "f16": ntc.PREC_F16}[precision]
+    w = gen.random_mlp(k_in, 64, TRN_C, seed=2002, n_used=2 * TRN_C0 + 13)
+    prec = {"f32": ntc.PREC_F32, "f16": ntc.PREC_F16, "f8": ntc.PREC_F8}[precision]
     tr = ntc.Trainer(TRN_SIDE, TRN_SIDE, TRN_C, TRN_C0, TRN_C0, 4, 4, q, q, g0, g1,
-                     [w[0], w[2], w[4]], [w[1], w[3], w[5]], TRN_K, prec,
-                     total_steps=total_steps, device=device)
+                     [w[0], w[2], w[4]], [w[1], w[3], w[5]], k_in, prec,
+                     total_steps=total_steps, device=device,
+                     f8_act_scales=[1.0 / 256, 1.0 / 64, 1.0 / 64] if precision == "f8" else None)
     return tr, ntc.Target(chain, device=device), chain, (g0, g1), w
 
 
@@ -392,8 +393,11 @@ def equal_psnr_eval(ntc, chain, batch, seed, stream, steps=1500):
     res = {"workload": f"{TRN_SIDE}^2x{TRN_C} material, {steps} steps of {batch} texels from the "
                        "same initialisation and samples; PSNR of mip 0 of the 4-bit export "
                        "(decoded in FP32) against the 8-bit reference", "steps": steps}
-    for prec in ("f16", "f32"):
-        tr, target, _, _, _ = make_trainer(prec, steps)
+    # f16 / f32: K = 48; f8 needs K in steps of 32, so it runs against its own
+    # FP16 twin at K = 64 (zero columns; the same initialisation for both)
+    for prec, arm, k in (("f16", "f16", TRN_K), ("f32", "f32", TRN_K), ("f16", "f16_k64", 64),
+                         ("f8", "f8", 64)):
+        tr, target, _, _, _ = make_trainer(prec, steps, k_in=k)
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
@@ -403,12 +407,16 @@ def equal_psnr_eval(ntc, chain, batch, seed, stream, steps=1500):
         torch.cuda.synchronize()
         dec = ntc.ntc_decode(tr.export(ntc.PREC_F32), t0)
         mse = float(((dec - refm) ** 2).mean())
-        res[f"train_s_{prec}"] = a.elapsed_time(b) / 1e3
-        res[f"psnr_db_{prec}_trained"] = 10 * math.log10(1.0 / mse)
-        res[f"status_{prec}"] = ntc.ntc_device_status()
+        res[f"train_s_{arm}"] = a.elapsed_time(b) / 1e3
+        res[f"psnr_db_{arm}_trained"] = 10 * math.log10(1.0 / mse)
+        res[f"status_{arm}"] = ntc.ntc_device_status()
         del tr, target
     res["delta_db"] = res["psnr_db_f16_trained"] - res["psnr_db_f32_trained"]
     res["speedup_f16_over_f32"] = res["train_s_f32"] / res["train_s_f16"]
+    res["delta_db_f8_minus_f16_k64"] = res["psnr_db_f8_trained"] - res["psnr_db_f16_k64_trained"]
+    res["speedup_f8_over_f16_k64"] = res["train_s_f16_k64"] / res["train_s_f8"]
+    res["f8_samples_per_s"] = steps * batch / res["train_s_f8"]
+    res["f16_k64_samples_per_s"] = steps * batch / res["train_s_f16_k64"]
     return res
 
 

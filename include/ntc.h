@@ -197,6 +197,11 @@ typedef struct {
                            sum over levels of g0_w g0_h vq_books bytes (the step's
                            indices); needs `noisy`.  NULL otherwise */
   float vq_beta;        /* commitment weight of the vector-quantised G0 */
+  int64_t* noisy_tag;   /* nullable, device int64[2] (initialise to {-1, -1}): with `noisy`,
+                           each step's Adam also writes the next step's noisy grids and
+                           tags them {seed, step}; the next step's noise pass skips when
+                           the tag matches its own seed and step.  Reset it to {-1, -1}
+                           after changing params outside the library */
 } ntc_trainer;
 
 /* Reference texture set: the 8-bit mip chain, texel values q/255. */
@@ -285,11 +290,14 @@ int ntc_set_decode_warpgroups(int32_t nwg);
 
 /* Autotuner of the tensor-core decode: times every launch shape (1 warm-up
  * + 3 timed launches each, CUDA events on `stream`) on the caller's queries
- * (writing `out`), selects the fastest as ntc_set_decode_warpgroups would,
- * and returns it in *best (host).  ms_out (host, nullable, 4 floats)
- * receives the mean time per launch of the shapes 2, 3, 4, 5.  out_dtype
- * and filter as ntc_decode (NTC_ERR_ARG otherwise).  Synchronises the
- * stream. */
+ * (writing `out`) and records the fastest in the library's tuning cache
+ * under this call's key -- the material's shape, channel counts, bit widths,
+ * K, activations, precision and layout, the filter, the output type, the
+ * device's SM count and the query count's power-of-two bucket -- and in
+ * *best (host).  Later decodes with the same key use it unless
+ * ntc_set_decode_warpgroups chose a shape.  ms_out (host, nullable, 4 floats)
+ * receives the mean time per launch of the shapes 2, 3, 4, 5.  out_dtype and
+ * filter as ntc_decode (NTC_ERR_ARG otherwise).  Synchronises the stream. */
 int ntc_autotune_decode(const ntc_material* m, const float* uvl, int64_t n, void* out,
                         int32_t out_dtype, int32_t filter, int32_t* best, float* ms_out,
                         void* stream);
@@ -323,6 +331,32 @@ int ntc_f8_activation_scales(const ntc_material* m, const float* uvl, int64_t n,
  * fused multiply-add chains -- the ALU roof of the FP32 CUDA-core forms.
  * Synchronises `stream`. */
 int ntc_probe_fma_tflops(float* tflops_out, void* stream);
+
+/* Autotuner of the tensor-core training step: times the fused
+ * forward+backward with 1, 2 and 3 warpgroup pipelines per CTA (those whose
+ * tiles fit; 1 warm-up + 3 timed gradient-only steps each, CUDA events on
+ * `stream`) on the arguments of ntc_train_step (no NTC_FLAG_SIMT or
+ * GRAD_ONLY), records the fastest in the tuning cache (key: the material's
+ * shape and precision, crops or not, the SM count and the batch's
+ * power-of-two bucket) and in *best (host); ntc_train_step and
+ * ntc_train_step_noalloc with that key use it.  ms_out (host, nullable, 3
+ * floats): mean time per step for 1, 2, 3 pipelines (0 where they do not
+ * fit).  Leaves params, Adam state, the step counter and (FP8 form) the
+ * scales as they were and tr->grad zeroed; *loss_out is scratch.
+ * Synchronises the stream. */
+int ntc_autotune_train(const ntc_material* m, const ntc_trainer* tr, const ntc_target* t,
+                       int64_t batch, uint64_t seed, int32_t flags, float* loss_out,
+                       int32_t* best, float* ms_out, void* stream);
+
+/* The tuning cache as text, one "<key> <value>" line per entry, for a caller
+ * to keep between processes: ntc_tuning_export writes it NUL-terminated
+ * into buf (host; NULL: only the size) and its size including the NUL into
+ * *len_out (host, nullable); NTC_ERR_ARG if cap is too small.
+ * ntc_tuning_import adds the entries of such text (values 1..5) to the
+ * cache, replacing equal keys; ntc_tuning_clear empties it.  Host only. */
+int ntc_tuning_export(char* buf, size_t cap, size_t* len_out);
+int ntc_tuning_import(const char* text);
+int ntc_tuning_clear(void);
 
 /* Gradient of sum_i sum_c dout[i][c] * y[i][c] for nearest decodes y of the
  * queries uvl (Sec. 4.5, reverse mode of ntc_decode), ACCUMULATED into g.

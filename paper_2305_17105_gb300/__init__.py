@@ -76,7 +76,7 @@ class ntc_trainer(C.Structure):
                 ("step", C.c_void_p), ("total_steps", C.c_int64), ("lr_grid", C.c_float),
                 ("lr_mlp", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float),
                 ("eps", C.c_float), ("noisy", C.c_void_p), ("w_master_h3", C.c_void_p),
-                ("vq_idx", C.c_void_p), ("vq_beta", C.c_float)]
+                ("vq_idx", C.c_void_p), ("vq_beta", C.c_float), ("noisy_tag", C.c_void_p)]
 
 
 class ntc_batch(C.Structure):
@@ -129,6 +129,10 @@ SIGNATURES = {
     "ntc_probe_fma_tflops": (C.c_int, [_P, _P]),
     "ntc_f8_quantize_weights": (C.c_int, [_P, _I32, _I32, _I32, _P, _P, _P]),
     "ntc_f8_activation_scales": (C.c_int, [_P, _P, _I64, _P, _P]),
+    "ntc_autotune_train": (C.c_int, [_P, _P, _P, _I64, _U64, _I32, _P, _P, _P, _P]),
+    "ntc_tuning_export": (C.c_int, [C.c_char_p, C.c_size_t, _P]),
+    "ntc_tuning_import": (C.c_int, [C.c_char_p]),
+    "ntc_tuning_clear": (C.c_int, []),
 }
 
 _lib = None
@@ -514,7 +518,7 @@ class Trainer:
                  weights, biases, k_in, precision=PREC_F32, act=ACT_RELU, out_act=OUT_SIGMOID,
                  total_steps=1000, lr_grid=0.01, lr_mlp=0.005, betas=(0.9, 0.999), eps=1e-8,
                  device="cuda", noisy_scratch=True, interp0=INTERP_BILINEAR, codebook0=None,
-                 vq_beta=0.25):
+                 vq_beta=0.25, f8_act_scales=None):
         tensors = [np.asarray(g, np.float32) for g in grids0] + \
                   [np.asarray(g, np.float32) for g in grids1]
         mlp = []
@@ -537,6 +541,9 @@ class Trainer:
         self.grad = torch.zeros_like(self.params)
         # scratch for the dense noise pass of each step (None: noise per tap)
         self.noisy = torch.empty_like(self.params) if noisy_scratch else None
+        # {seed, step} of the noisy copy the last step's Adam wrote
+        self.noisy_tag = torch.full((2,), -1, dtype=torch.int64, device=device) \
+            if noisy_scratch else None
         self.step_t = torch.zeros(1, dtype=torch.int64, device=device)
         self.loss = torch.zeros(1, dtype=torch.float32, device=device)
         views = [self.params[o:o + t.size].view(t.shape) for o, t in zip(offs, tensors)]
@@ -546,15 +553,25 @@ class Trainer:
         self.w_master = rest[0::2]   # layer order: 3 or 4 layers
         self.b = rest[1::2]
         self.grad_views = [self.grad[o:o + t.size].view(t.shape) for o, t in zip(offs, tensors)]
+        self.f8_scale = None
         if precision == PREC_F16:
             self.w_compute = [w.half().contiguous() for w in self.w_master]
         elif precision == PREC_F32:
             self.w_compute = self.w_master
+        elif precision == PREC_F8:
+            # FP8-E4M3 form (R24): E4M3 weights the step's pre-pass writes from
+            # the masters; scale = s_w[3], s_a[3], layer-input maxima[3]
+            self.w_compute = [torch.zeros(w.shape, dtype=torch.uint8, device=device)
+                              for w in self.w_master]
+            sa = [1.0, 1.0, 1.0] if f8_act_scales is None else [float(x) for x in f8_act_scales]
+            self.f8_scale = torch.tensor([1.0, 1.0, 1.0] + sa + [0.0, 0.0, 0.0],
+                                         dtype=torch.float32, device=device)
         else:
-            raise ValueError("training supports FP32 and FP16 weights")
+            raise ValueError("precision")
         self.material = Material(width, height, channels, c0, c1, bits0, bits1, q0, q1, g0, g1,
                                  self.w_compute, self.b, k_in, precision, act, out_act,
-                                 interp0=interp0, codebook0=self.codebook)
+                                 interp0=interp0, codebook0=self.codebook,
+                                 scale=self.f8_scale)
         self.vq_beta = vq_beta
         self.vq_idx = (torch.empty(sum(g.shape[0] * g.shape[1] for g in grids0) * codebook0.shape[0],
                                    dtype=torch.uint8, device=device) if vq else None)
@@ -575,16 +592,27 @@ class Trainer:
                 g.shape[0], g.shape[1], -1) for g in m.grids0]
         g1 = [ntc_quantize_pack(g.contiguous(), m.c1, m.bits1, m.q1, stream=stream).view(
             g.shape[0], g.shape[1], -1) for g in m.grids1]
+        scale = None
         if precision == PREC_F16:
             w = [x.half().contiguous() for x in self.w_master]
         elif precision == PREC_F32:
             w = [x.clone() for x in self.w_master]
+        elif precision == PREC_F8:
+            # E4M3 weights with scales max|W| / 448 (ntc_f8_quantize_weights);
+            # activation scales: the FP8 trainer's current ones
+            if self.f8_scale is None:
+                raise ValueError("FP8 export of a trainer that is not in the FP8 form")
+            scale = torch.empty(6, dtype=torch.float32, device=self.params.device)
+            w = [ntc_f8_quantize_weights(x.contiguous(), scale_out=scale[l:l + 1],
+                                         stream=stream)[0] for l, x in enumerate(self.w_master)]
+            scale[3:6] = self.f8_scale[3:6]
         else:
-            raise ValueError("export writes FP16 or FP32 weights")
+            raise ValueError("export writes FP8, FP16 or FP32 weights")
         return Material(m.width, m.height, m.channels, m.c0, m.c1, m.bits0, m.bits1, m.q0, m.q1,
                         g0, g1, w, [b.clone() for b in self.b], m.k_in, precision, m.act,
                         m.out_act, interp0=m.interp0,
-                        codebook0=self.codebook.clone() if self.codebook is not None else None)
+                        codebook0=self.codebook.clone() if self.codebook is not None else None,
+                        scale=scale)
 
     @property
     def struct(self) -> ntc_trainer:
@@ -604,7 +632,13 @@ class Trainer:
         t.noisy = self.noisy.data_ptr() if self.noisy is not None else None
         t.vq_idx = self.vq_idx.data_ptr() if self.vq_idx is not None else None
         t.vq_beta = self.vq_beta
+        t.noisy_tag = self.noisy_tag.data_ptr() if self.noisy_tag is not None else None
         return t
+
+    def invalidate_noisy(self):
+        """Mark the noisy copy stale (after changing params outside the library)."""
+        if self.noisy_tag is not None:
+            self.noisy_tag.fill_(-1)
 
 
 class Target:
@@ -722,6 +756,45 @@ def f8_material(mat: Material, w32, calib_uvl, stream=None) -> Material:
         w8.append(q)
     ntc_f8_activation_scales(mat, calib_uvl, out=scale[3:6], stream=stream)
     return mat.with_(weights=w8, precision=PREC_F8, scale=scale, k_in=k8)
+
+
+def ntc_autotune_train(trainer: Trainer, target: Target, batch: int, seed: int, flags=0,
+                       stream=None):
+    """Time the fused step with 1-3 pipelines per CTA and record the fastest
+    in the tuning cache; returns (best, [ms for 1, 2, 3])."""
+    m, t, tg = trainer.material.struct, trainer.struct, target.struct
+    best = C.c_int32(0)
+    ms = (C.c_float * 3)()
+    _call("ntc_autotune_train", C.byref(m), C.byref(t), C.byref(tg), batch, seed, flags,
+          _ptr(trainer.loss), C.byref(best), ms, _stream(stream))
+    return int(best.value), [float(x) for x in ms]
+
+
+def tuning_export() -> str:
+    """The tuning cache as text (one "<key> <value>" line per entry)."""
+    n = C.c_size_t(0)
+    _call("ntc_tuning_export", None, 0, C.byref(n))
+    buf = C.create_string_buffer(int(n.value))
+    _call("ntc_tuning_export", buf, int(n.value), C.byref(n))
+    return buf.value.decode()
+
+
+def tuning_import(text: str) -> None:
+    _call("ntc_tuning_import", text.encode())
+
+
+def tuning_clear() -> None:
+    _call("ntc_tuning_clear")
+
+
+def tuning_save(path: str) -> None:
+    with open(path, "w") as f:
+        f.write(tuning_export())
+
+
+def tuning_load(path: str) -> None:
+    with open(path) as f:
+        tuning_import(f.read())
 
 
 def ntc_probe_fma_tflops(stream=None) -> float:

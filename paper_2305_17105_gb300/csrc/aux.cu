@@ -48,6 +48,19 @@ int read_status_word(int reset) {
 
 namespace {
 
+// The noise of channels ch and ch + 1 (ch even) of a cell: both come from
+// the same 64-bit draw (the values noise_of gives for each).
+__device__ __forceinline__ float2 noise_pair_of(uint64_t key, int level, int grid, int cell,
+                                                int ch, int c, float q) {
+  const uint64_t pairs = (uint64_t)((c + 1) >> 1);
+  const uint64_t counter = ((uint64_t)(2 * level + grid) << 40) |
+                           ((uint64_t)cell * pairs + (uint64_t)(ch >> 1));
+  const uint64_t h = splitmix64(key ^ counter);
+  const uint32_t e = (uint32_t)(h >> 40), o = (uint32_t)((h >> 16) & 0xFFFFFFu);
+  return make_float2(((float)e * (1.0f / 16777216.0f) - 0.5f) * q,
+                     ((float)o * (1.0f / 16777216.0f) - 0.5f) * q);
+}
+
 // One Adam step (Kingma & Ba, bias-corrected) at the device step counter t,
 // learning rate lr0 (1 + cos(pi t / T)) / 2 per group, then the grid clamp
 // to [-(N-1)/2 Q, N/2 Q] (Sec. 4.2: clamp after the update).  The gradient is
@@ -57,11 +70,13 @@ namespace {
 // Block b of one material's Adam pass (A: its segments, block prefix sums).
 __device__ __forceinline__ void adam_block(const AdamArgs& A, int64_t b) {
   __shared__ float s_lr, s_ic1, s_ic2;
+  __shared__ uint64_t s_key;
   int s = 0;
   while (s + 1 < A.nseg && b >= A.block_start[s + 1]) ++s;
   const AdamSeg& S = A.seg[s];
   if (threadIdx.x == 0) {
     const int64_t t = *A.step;
+    s_key = rng_key(A.noise_seed, noise_stream(t + 1));
     const float x = (float)((double)t / (double)A.total);
     s_lr = A.lr[S.group] * 0.5f * (1.f + cospif(x));
     s_ic1 = 1.f / (1.f - powf(A.beta1, (float)(t + 1)));
@@ -81,6 +96,16 @@ __device__ __forceinline__ void adam_block(const AdamArgs& A, int64_t b) {
     po = p - lr * (mo * inv_c1) / (sqrtf(vo * inv_c2) + eps);
     if (S.clamp) po = fminf(fmaxf(po, S.lo), S.hi);
   };
+  // the next step's noisy value of segment element k (the same FP32 sum as
+  // the dense noise pass)
+  const bool fold = A.fold && S.noise_c > 0;
+  const uint64_t nkey = s_key;
+  auto noisy = [&](int64_t k, float po) {
+    const int c = S.noise_c;
+    const int64_t cell = k / c;
+    const int ch = (int)(k - cell * c);
+    return po + noise_of(nkey, S.noise_level, S.noise_grid, (int)cell, ch, c, S.noise_q);
+  };
   if (first + kAdamPerThread <= S.len) {
     // segments start 16-byte aligned: whole float4 groups
     const float4 p = *reinterpret_cast<const float4*>(A.p + e0);
@@ -96,6 +121,24 @@ __device__ __forceinline__ void adam_block(const AdamArgs& A, int64_t b) {
     *reinterpret_cast<float4*>(A.m + e0) = mo;
     *reinterpret_cast<float4*>(A.v + e0) = vo;
     *reinterpret_cast<float4*>(A.g + e0) = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (fold) {
+      float4 nv;
+      const int c = S.noise_c;
+      if ((c & 1) == 0) {
+        // even channel counts: elements (first, first+1) and (first+2,
+        // first+3) are channel pairs of one cell, one draw each
+        const int64_t cell0 = first / c, cell1 = (first + 2) / c;
+        const float2 n0 = noise_pair_of(nkey, S.noise_level, S.noise_grid, (int)cell0,
+                                        (int)(first - cell0 * c), c, S.noise_q);
+        const float2 n1 = noise_pair_of(nkey, S.noise_level, S.noise_grid, (int)cell1,
+                                        (int)(first + 2 - cell1 * c), c, S.noise_q);
+        nv = make_float4(po.x + n0.x, po.y + n0.y, po.z + n1.x, po.w + n1.y);
+      } else {
+        nv = make_float4(noisy(first, po.x), noisy(first + 1, po.y), noisy(first + 2, po.z),
+                         noisy(first + 3, po.w));
+      }
+      *reinterpret_cast<float4*>(A.noisy + e0) = nv;
+    }
     if (S.half_copy) {
       __half2* h = reinterpret_cast<__half2*>(S.half_copy + first);
       h[0] = __floats2half2_rn(po.x, po.y);
@@ -110,6 +153,7 @@ __device__ __forceinline__ void adam_block(const AdamArgs& A, int64_t b) {
       A.m[e] = mo;
       A.v[e] = vo;
       A.g[e] = 0.f;
+      if (fold) A.noisy[e] = noisy(k, po);
       if (S.half_copy) S.half_copy[k] = __float2half_rn(po);
     }
   }
@@ -146,18 +190,36 @@ __global__ void __launch_bounds__(kAdamBlock) adam_batched_kernel(TrainBatchDev*
     if (done == gridDim.x) {
       __threadfence();
       for (int k = 0; k < D->n; ++k)
-        if (D->adam_start[k + 1] > D->adam_start[k]) *const_cast<int64_t*>(D->adam[k].step) += 1;
+        if (D->adam_start[k + 1] > D->adam_start[k]) {
+          int64_t* st = const_cast<int64_t*>(D->adam[k].step);
+          *st += 1;
+          if (D->adam[k].fold && D->adam[k].noisy_tag) {
+            D->adam[k].noisy_tag[0] = (int64_t)D->adam[k].noise_seed;
+            D->adam[k].noisy_tag[1] = *st;
+          }
+        }
       D->adam_done = 0u;
       __threadfence();
     }
   }
 }
 
-__global__ void advance_step_kernel(int64_t* step) { *step += 1; }
+__global__ void advance_step_kernel(int64_t* step, int64_t* tag, uint64_t seed) {
+  *step += 1;
+  if (tag) {
+    tag[0] = (int64_t)seed;
+    tag[1] = *step;
+  }
+}
 
 // One thread per channel pair of a grid cell: both channels' noise comes
 // from the same 64-bit draw (noise_of), added in FP32 exactly as the fused
 // step adds it per tap.
+// The previous step's Adam already wrote this step's noisy grids.
+__device__ __forceinline__ bool noisy_current(const NoiseArgs& a) {
+  return a.tag && a.tag[0] == (int64_t)a.seed && a.tag[1] == *a.step;
+}
+
 __device__ __forceinline__ void noise_block(const NoiseArgs& a, int64_t blk) {
   int s = 0;
   while (s + 1 < a.nseg && blk >= a.block_start[s + 1]) ++s;
@@ -179,15 +241,20 @@ __device__ __forceinline__ void noise_block(const NoiseArgs& a, int64_t blk) {
   }
 }
 
+// A few CTAs per SM walk the blocks of the pass, so that a pass whose copy
+// is already current costs one check per CTA.
 __global__ void __launch_bounds__(kNoiseBlock) noise_grids_kernel(const NoiseArgs a) {
-  noise_block(a, blockIdx.x);
+  if (noisy_current(a)) return;
+  const int64_t blocks = a.block_start[a.nseg];
+  for (int64_t b = blockIdx.x; b < blocks; b += gridDim.x) noise_block(a, b);
 }
 
 // The noise pass of every material of a batch in one launch.
 __global__ void __launch_bounds__(kNoiseBlock) noise_batched_kernel(const TrainBatchDev* D) {
-  const int64_t b = blockIdx.x;
-  const int i = find_interval(D->noise_start, D->n, b);
-  noise_block(D->noise[i], b - D->noise_start[i]);
+  for (int64_t b = blockIdx.x; b < D->noise_blocks; b += gridDim.x) {
+    const int i = find_interval(D->noise_start, D->n, b);
+    if (!noisy_current(D->noise[i])) noise_block(D->noise[i], b - D->noise_start[i]);
+  }
 }
 
 // q = clamp(rint(x / Q) + N/2 - 1, 0, N - 1), ties to even, evaluated in
@@ -277,7 +344,8 @@ cudaError_t launch_adam(const AdamArgs& a, int64_t blocks, cudaStream_t s) {
 cudaError_t launch_noise_grids(const NoiseArgs& a, cudaStream_t s) {
   const int64_t blocks = a.block_start[a.nseg];
   if (blocks == 0) return cudaSuccess;
-  noise_grids_kernel<<<(unsigned)blocks, kNoiseBlock, 0, s>>>(a);
+  const int64_t cap = (int64_t)sm_count() * 8;
+  noise_grids_kernel<<<(unsigned)(blocks < cap ? blocks : cap), kNoiseBlock, 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -381,12 +449,13 @@ cudaError_t launch_adam_batched(TrainBatchDev* dev, int64_t blocks, cudaStream_t
 
 cudaError_t launch_noise_batched(const TrainBatchDev* dev, int64_t blocks, cudaStream_t s) {
   if (blocks == 0) return cudaSuccess;
-  noise_batched_kernel<<<(unsigned)blocks, kNoiseBlock, 0, s>>>(dev);
+  const int64_t cap = (int64_t)sm_count() * 8;
+  noise_batched_kernel<<<(unsigned)(blocks < cap ? blocks : cap), kNoiseBlock, 0, s>>>(dev);
   return cudaGetLastError();
 }
 
-cudaError_t launch_advance_step(int64_t* step, cudaStream_t s) {
-  advance_step_kernel<<<1, 1, 0, s>>>(step);
+cudaError_t launch_advance_step(int64_t* step, cudaStream_t s, int64_t* tag, uint64_t seed) {
+  advance_step_kernel<<<1, 1, 0, s>>>(step, tag, seed);
   return cudaGetLastError();
 }
 

@@ -1,10 +1,13 @@
 // C-ABI entry points of libntc.so (declared in include/ntc.h): argument
 // validation, error reporting and dispatch to the kernels.
 #include <atomic>
+#include <map>
 #include <mutex>
+#include <string>
 #include <memory>
 #include <vector>
 #include <stdarg.h>
+#include <stdlib.h>
 #include <stdio.h>
 #include <string.h>
 
@@ -127,6 +130,42 @@ int check_material(const ntc_material* m, bool need_f32_grids, bool vq_training 
 
 std::atomic<int> g_decode_nwg{0};  // tensor-core decode warpgroups per CTA (0 = default)
 
+// Tuning cache: the autotuners' choices keyed by what decides them -- the
+// kind of launch, the material's shape and precision, the filter, the SM
+// count and the size of the call (log2 bucket).  One line of text per
+// entry, "<key> <value>", for export and import.
+std::mutex g_tune_mu;
+std::map<std::string, int> g_tune;
+
+int log2_bucket(int64_t n) {
+  int b = 0;
+  while (b < 62 && ((int64_t)1 << (b + 1)) <= n) ++b;
+  return b;
+}
+
+std::string tune_key(const char* kind, const ntc_material& m, int filter, int out_dtype,
+                     int64_t n) {
+  char buf[320];
+  snprintf(buf, sizeof(buf),
+           "%s:prec=%d:c=%d:c0=%d:c1=%d:b0=%d:b1=%d:k=%d:act=%d:out=%d:interp=%d:hl=%d:vq=%d:"
+           "taps=%d:filter=%d:dtype=%d:sms=%d:n=2^%d",
+           kind, m.precision, m.channels, m.c0, m.c1, m.bits0, m.bits1, m.k_in, m.act, m.out_act,
+           m.interp0, m.hidden_layers == 3 ? 3 : 2, m.vq_books, ntc::fast_layout_ok(m) ? 1 : 0,
+           filter, out_dtype, ntc::sm_count(), log2_bucket(n));
+  return std::string(buf);
+}
+
+int tune_lookup(const std::string& key) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  auto it = g_tune.find(key);
+  return it == g_tune.end() ? 0 : it->second;
+}
+
+void tune_store(const std::string& key, int value) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune[key] = value;
+}
+
 // Helper streams and events of ntc_decode_host, created once per device and
 // used under g_pipe_mu (one enqueue sequence at a time).
 struct HostPipe {
@@ -155,9 +194,10 @@ int decode_impl(const ntc_material* m, const float* uvl, int64_t n, void* out, i
                                                (flags & NTC_FLAG_NOISE) != 0, noise_seed,
                                                noise_step, s),
                        "decode (FP32 CUDA cores)");
+  int nwg = g_decode_nwg.load();  // ntc_set_decode_warpgroups, else the autotuner's choice
+  if (nwg == 0) nwg = tune_lookup(tune_key("decode", *m, filter, out_dtype, n));
   return cuda_status(ntc::launch_decode_tc(*m, uvl, n, out, out_dtype, filter,
-                                           ntc::jitter_key(noise_seed, noise_step), s,
-                                           g_decode_nwg.load()),
+                                           ntc::jitter_key(noise_seed, noise_step), s, nwg),
                      "decode (tcgen05)");
 }
 
@@ -411,10 +451,12 @@ int ntc_autotune_decode(const ntc_material* m, const float* uvl, int64_t n, void
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc != NTC_OK) return rc;
-  g_decode_nwg.store(best_nwg);
+  tune_store(tune_key("decode", *m, filter, out_dtype, n), best_nwg);
   *best = best_nwg;
   return NTC_OK;
 }
+
+
 
 int ntc_backward(const ntc_material* m, const float* uvl, int64_t n, const float* dout,
                  const ntc_grads* g, int32_t flags, uint64_t noise_seed, int64_t noise_step,
@@ -614,6 +656,7 @@ static int plan_train_step(const ntc_material* m, const ntc_trainer* tr, const n
   b.crops = (flags & NTC_FLAG_CROPS) != 0;
   sp.vq = vq;
   sp.simt = use_simt(m, flags);
+  b.pipelines = sp.simt ? 0 : tune_lookup(tune_key("train", *m, b.crops ? 1 : 0, 0, batch));
   sp.cb_seg = cb_seg;
   // With the noisy scratch: one dense noise pass, and the fused step reads
   // the noisy grids at the same offsets of the scratch.
@@ -648,6 +691,24 @@ static int plan_train_step(const ntc_material* m, const ntc_trainer* tr, const n
       }
     sp.noise_pass = true;
     b.noise = 0;
+    // fold the next step's noise into this step's Adam (no VQ: its G0
+    // scratch holds the quantised rows)
+    if (tr->noisy_tag && !vq) {
+      if (((uintptr_t)tr->noisy_tag & 7u) != 0) return fail(NTC_ERR_ALIGN, "noisy_tag");
+      na.tag = tr->noisy_tag;
+      a.fold = 1;
+      a.noisy = tr->noisy;
+      a.noise_seed = seed;
+      a.noisy_tag = tr->noisy_tag;
+      for (int j = 0; j < m->levels; ++j)
+        for (int k = 0; k < 2; ++k) {
+          ntc::AdamSeg& sg = a.seg[2 * j + k];
+          sg.noise_c = k ? m->c1 : m->c0;
+          sg.noise_level = j;
+          sg.noise_grid = k;
+          sg.noise_q = k ? m->q1 : m->q0;
+        }
+    }
   }
   return NTC_OK;
 }
@@ -701,7 +762,108 @@ static int launch_train_plan(const ntc_material* m, const ntc_trainer* tr, StepP
   if (flags & NTC_FLAG_GRAD_ONLY) return NTC_OK;
   e = ntc::launch_adam(a, a.block_start[a.nseg], s);
   if (e != cudaSuccess) return cuda_status(e, "train_step adam");
-  return cuda_status(ntc::launch_advance_step(tr->step, s), "train_step step counter");
+  return cuda_status(ntc::launch_advance_step(tr->step, s, a.fold ? a.noisy_tag : nullptr,
+                                              a.noise_seed),
+                     "train_step step counter");
+}
+
+int ntc_autotune_train(const ntc_material* m, const ntc_trainer* tr, const ntc_target* t,
+                       int64_t batch, uint64_t seed, int32_t flags, float* loss_out,
+                       int32_t* best, float* ms_out, void* stream) {
+  if (!best) return fail(NTC_ERR_ARG, "best is NULL");
+  if (flags & (NTC_FLAG_SIMT | NTC_FLAG_GRAD_ONLY))
+    return fail(NTC_ERR_ARG, "the autotuner times the tensor-core step (no SIMT or GRAD_ONLY flag)");
+  const int32_t f = flags | NTC_FLAG_GRAD_ONLY;  // timed steps leave params and step unchanged
+  StepPlan sp;
+  int st = plan_train_step(m, tr, t, batch, seed, nullptr, loss_out, f, &sp);
+  if (st) return st;
+  if (sp.simt) return fail(NTC_ERR_ARG, "the FP32 form has no pipeline choice");
+  if (m->vq_books > 0) return fail(NTC_ERR_UNSUPPORTED, "autotune: scalar-quantised grids");
+  const int np_max = ntc::train_pipelines_layout(*m, 0, 0);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // the FP8 form's scales (and recorded maxima) are restored afterwards
+  float saved[9];
+  const bool f8 = m->precision == NTC_PREC_F8;
+  if (f8) {
+    cudaError_t e = cudaMemcpyAsync(saved, m->scale, sizeof(saved), cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    if (e) return cuda_status(e, "autotune: save FP8 scales");
+  }
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return cuda_status(cudaGetLastError(), "autotune events");
+  float best_ms = 1e30f;
+  int best_np = 0, rc = NTC_OK;
+  for (int np = 1; np <= np_max && rc == NTC_OK; ++np) {
+    sp.b.pipelines = np;
+    rc = launch_train_plan(m, tr, sp, loss_out, f, s);  // warm-up
+    cudaError_t e = rc == NTC_OK ? cudaEventRecord(e0, s) : cudaErrorUnknown;
+    for (int r = 0; r < 3 && rc == NTC_OK && e == cudaSuccess; ++r)
+      rc = launch_train_plan(m, tr, sp, loss_out, f, s);
+    if (rc != NTC_OK) break;
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) rc = cuda_status(e, "autotune");
+    if (ms_out) ms_out[np - 1] = ms / 3.f;
+    if (ms < best_ms) { best_ms = ms; best_np = np; }
+  }
+  for (int np = np_max + 1; np <= 3 && ms_out; ++np) ms_out[np - 1] = 0.f;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  // the timed gradient-only steps accumulated into the scratch gradient
+  cudaError_t e = cudaMemsetAsync(tr->grad, 0, (size_t)tr->n_params * sizeof(float), s);
+  if (!e && f8) e = cudaMemcpyAsync(const_cast<float*>(m->scale), saved, sizeof(saved),
+                                    cudaMemcpyHostToDevice, s);
+  if (!e) e = cudaStreamSynchronize(s);
+  if (rc == NTC_OK && e) rc = cuda_status(e, "autotune: restore");
+  if (rc != NTC_OK) return rc;
+  tune_store(tune_key("train", *m, (flags & NTC_FLAG_CROPS) ? 1 : 0, 0, batch), best_np);
+  *best = best_np;
+  return NTC_OK;
+}
+
+int ntc_tuning_export(char* buf, size_t cap, size_t* len_out) {
+  std::string text;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    for (const auto& kv : g_tune) text += kv.first + " " + std::to_string(kv.second) + "\n";
+  }
+  if (len_out) *len_out = text.size() + 1;
+  if (!buf) return NTC_OK;
+  if (cap < text.size() + 1) return fail(NTC_ERR_ARG, "tuning export: %zu bytes needed", text.size() + 1);
+  memcpy(buf, text.c_str(), text.size() + 1);
+  return NTC_OK;
+}
+
+int ntc_tuning_import(const char* text) {
+  if (!text) return fail(NTC_ERR_ARG, "text is NULL");
+  std::map<std::string, int> add;
+  const char* p = text;
+  while (*p) {
+    const char* e = strchr(p, '\n');
+    const std::string line = e ? std::string(p, e) : std::string(p);
+    p = e ? e + 1 : p + line.size();
+    if (line.empty()) continue;
+    const size_t sp = line.rfind(' ');
+    if (sp == std::string::npos || sp == 0)
+      return fail(NTC_ERR_ARG, "tuning import: malformed line '%.60s'", line.c_str());
+    char* end = nullptr;
+    const long v = strtol(line.c_str() + sp + 1, &end, 10);
+    if (*end != '\0' || v < 1 || v > 5)
+      return fail(NTC_ERR_ARG, "tuning import: bad value in '%.60s'", line.c_str());
+    add[line.substr(0, sp)] = (int)v;
+  }
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  for (const auto& kv : add) g_tune[kv.first] = kv.second;
+  return NTC_OK;
+}
+
+int ntc_tuning_clear(void) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune.clear();
+  return NTC_OK;
 }
 
 // The optimisation step.  With `check_only` the call validates its

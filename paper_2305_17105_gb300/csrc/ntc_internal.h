@@ -30,6 +30,7 @@ struct BwdArgs {
   int train;               // 1: loss mode (dout = 2 (y - t)), 0: dout given
   int grids;               // 0: skip grid gradients (frozen grids)
   int crops;               // training sampler: 256 x 256 crops of one mip (Sec. 5.1)
+  int pipelines;           // tensor-core step: warpgroup pipelines per CTA (0: the most that fit)
 };
 
 cudaError_t launch_decode_simt(const ntc_material& m, const float* uvl, int64_t n, void* out,
@@ -64,6 +65,9 @@ struct AdamSeg {
   int group;          // 0 grids, 1 MLP
   int clamp;
   __half* half_copy;  // refresh target (F16 weights) or nullptr
+  // grid segments: the next step's noisy copy (AdamArgs::fold); c = 0: none
+  int noise_c, noise_level, noise_grid;
+  float noise_q;
 };
 struct AdamArgs {
   AdamSeg seg[kMaxSegs];
@@ -78,6 +82,14 @@ struct AdamArgs {
   float lr[2];
   float beta1, beta2, eps;
   int freeze_grids;
+  // With fold, the update also writes the next step's noisy grids
+  // (params + the noise of (noise_seed, step + 1)) into `noisy`, and the
+  // step counter's advance tags them (noisy_tag = {seed, step + 1}), so that
+  // the next step's dense noise pass finds them current and skips.
+  int fold;
+  float* noisy;
+  uint64_t noise_seed;
+  int64_t* noisy_tag;
 };
 constexpr int kAdamBlock = 256;
 constexpr int kAdamPerThread = 4;  // one float4 per thread
@@ -93,6 +105,7 @@ struct NoiseSeg {
 struct NoiseArgs {
   const float* src;
   float* dst;
+  const int64_t* tag;  // nullable: skip when {seed, *step} (the copy is current)
   NoiseSeg seg[2 * NTC_MAX_LEVELS];
   int64_t block_start[2 * NTC_MAX_LEVELS + 1];
   int nseg;
@@ -109,7 +122,9 @@ cudaError_t launch_f8_weights(const float* w, int rows, int cols, int cols_out, 
 cudaError_t launch_f8_calibrate(const ntc_material& m, const float* uvl, int64_t n,
                                 uint32_t* amax, float* sa, cudaStream_t s);
 
-cudaError_t launch_advance_step(int64_t* step, cudaStream_t s);
+// *step += 1; with tag (nullable): tag = {seed, new step}.
+cudaError_t launch_advance_step(int64_t* step, cudaStream_t s, int64_t* tag = nullptr,
+                                uint64_t seed = 0);
 
 cudaError_t launch_quantize_pack(const float* values, int64_t cells, int c, int bits, float q,
                                  uint8_t* packed, float* snapped, cudaStream_t s);

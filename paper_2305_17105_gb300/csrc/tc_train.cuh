@@ -1305,7 +1305,9 @@ int train_pipelines(const ntc_material& m) { return pipelines_for(m, 0, 0); }
 template <int ACT, bool LEARNED, bool BATCHED, bool F8>
 cudaError_t launch_n(const ntc_material& m, const BwdArgs& a, const TrainBatchDev* hb,
                      int64_t tiles, int k_lay, int dx_lay, cudaStream_t s) {
-  switch (pipelines_for(m, k_lay, dx_lay)) {
+  int np = pipelines_for(m, k_lay, dx_lay);
+  if (a.pipelines > 0 && a.pipelines < np) np = a.pipelines;  // the autotuner's choice
+  switch (np) {
     case 3: return launch_t<ACT, LEARNED, 3, BATCHED, F8>(m, a, hb, tiles, k_lay, dx_lay, s);
     case 2: return launch_t<ACT, LEARNED, 2, BATCHED, F8>(m, a, hb, tiles, k_lay, dx_lay, s);
     default: return launch_t<ACT, LEARNED, 1, BATCHED, F8>(m, a, hb, tiles, k_lay, dx_lay, s);

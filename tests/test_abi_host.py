@@ -212,6 +212,21 @@ def test_train_step_validation(L):
     assert rc == ntc.ERR_ARG and "params" in L.ntc_last_error().decode()  # passes the FP8 checks
 
 
+def test_tuning_cache_text(L):
+    """The tuning cache's text form: import, export and clear are host-only;
+    malformed lines and values outside 1..5 are refused."""
+    ntc.tuning_clear()
+    ntc.tuning_import("train:k=1 2\ndecode:k=2 5\n\n")
+    text = ntc.tuning_export()
+    assert text == "decode:k=2 5\ntrain:k=1 2\n"
+    for bad in ("novalue\n", "train:k=1 9\n", "train:k=1 x\n"):
+        with pytest.raises(ntc.NTCError):
+            ntc.tuning_import(bad)
+    assert ntc.tuning_export() == text  # a refused import adds nothing
+    ntc.tuning_clear()
+    assert ntc.tuning_export() == ""
+
+
 def test_grid_width_rules(L):
     """Grids hold 1..20 features per cell (profile 0.5's G1 has 20), packed
     cells at most 128 bits."""

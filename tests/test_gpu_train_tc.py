@@ -199,3 +199,52 @@ def test_dense_noise_pass_equals_noise_per_tap(precision):
         losses.append(tr.loss.item())
     assert abs(losses[0] - losses[1]) <= 1e-6 * abs(losses[1])
     assert rel_err(grads[0], grads[1]) < 1e-5
+
+
+def _expected_noisy(tr, case, seed, step):
+    """params + the oracle's noise of (seed, step) for every grid value, summed
+    in FP32 (the dense noise pass's arithmetic), per grid view."""
+    out = []
+    for k, views in ((0, tr.material.grids0), (1, tr.material.grids1)):
+        c, q = (case.c1, case.q1) if k else (case.c0, case.q0)
+        for j, v in enumerate(views):
+            p = v.detach().cpu().numpy().reshape(-1, c).astype(np.float32)
+            noise = np.array([[oracle.noise_value(seed, step, j, k, cell, ch, c, q)
+                               for ch in range(c)] for cell in range(p.shape[0])], np.float32)
+            out.append((p + noise).reshape(-1))
+    return out
+
+
+def _noisy_views(tr):
+    base = tr.params.data_ptr()
+    res = []
+    for views in (tr.material.grids0, tr.material.grids1):
+        for v in views:
+            off = (v.data_ptr() - base) // 4
+            res.append(tr.noisy[off:off + v.numel()].cpu().numpy())
+    return res
+
+
+def test_noise_folded_into_adam_matches_the_noise_pass():
+    """With noisy_tag each step's Adam writes the next step's noisy grids and
+    the next noise pass skips.  The copy Adam writes equals params + the
+    oracle's noise of (seed, next step) bit for bit; with changing seeds and
+    a NO_NOISE step in between, every step's loss equals that of a trainer
+    that runs the dense noise pass every step."""
+    case = make_case(128, 64, 12, 12, 12, k_in=48, seed=76)
+    chain = gen.box_mip_chain_u8(gen.synthetic_texture(128, 64, 12, seed=1076))
+    target = ntc.Target(chain)
+    a, b = _trainer(case, ntc.PREC_F16, total=40), _trainer(case, ntc.PREC_F16, total=40)
+    b.noisy_tag = None  # the noise pass every step
+    plan = [(5, 0), (5, 0), (6, 0), (6, ntc.FLAG_NO_NOISE), (6, 0), (6, 0)]
+    for i, (seed, flags) in enumerate(plan):
+        la = ntc.ntc_train_step(a, target, 2048 + 17, seed, flags=flags).item()
+        lb = ntc.ntc_train_step(b, target, 2048 + 17, seed, flags=flags).item()
+        assert abs(la - lb) <= 1e-5 * lb, (seed, flags, la, lb)
+        if not flags:
+            torch.cuda.synchronize()
+            for got, want in zip(_noisy_views(a), _expected_noisy(a, case, seed, i + 1)):
+                assert np.array_equal(got, want), i
+    assert ntc.ntc_device_status() == ntc.OK
+    assert a.noisy_tag.cpu().tolist() == [6, len(plan)]
+    assert rel_err(to_np(a.params), to_np(b.params)) <= 1e-3
