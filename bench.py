@@ -89,7 +89,11 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="only the timed step: skip the crop-sampler, paper-form, 64-material, "
                          "render, FP32, e2e and CPU sections (profiling runs)")
+    ap.add_argument("--multi-only", action="store_true",
+                    help="the timed step and the 64-material section only (profiling runs)")
     a = ap.parse_args()
+    if a.multi_only:
+        a.no_cpu_baseline = a.no_e2e = a.no_fp32_compare = a.no_render = True
     if a.no_extras:
         a.no_cpu_baseline = a.no_e2e = a.no_fp32_compare = a.no_render = a.no_multi = True
     return a
@@ -734,6 +738,17 @@ def multi_material_eval(ntc, n_mat, q_per, train_batch, stream):
     algo = n_mat * train_batch * 1036 + n_params * 32
     res["train_batched_graph_step_ms"] = ms_t
     res["train_samples_per_s"] = n_mat * train_batch / (ms_t / 1e3)
+    # the whole compression schedule of the workload: 1,000 steps of every
+    # material, one graph replay each
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(1000):
+        g_b.replay()
+    b.record(stream)
+    torch.cuda.synchronize()
+    res["train_1000_steps_s"] = a.elapsed_time(b) / 1e3
+    res["train_1000_steps_samples_per_s"] = 1000 * n_mat * train_batch / res["train_1000_steps_s"]
+    res["train_final_loss_mean"] = float(tb.loss.mean().item())
     res["train_kernels_per_step"] = 3
     res["train_params"] = n_params
     res["train_algorithmic_bytes_per_step"] = algo
@@ -1084,7 +1099,7 @@ def main():
 
     # ---- the paper's crop sampler on the same trainer (Sec. 5.1) ----------
     crops = None
-    if not args.no_extras:
+    if not args.no_extras and not args.multi_only:
         try:
             torch.cuda.synchronize()
             c0e, c1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -1178,35 +1193,35 @@ def main():
             render = {"error": f"{type(e).__name__}: {e}"[:300]}
 
     paper_form = None
-    if not args.no_extras:
+    if not args.no_extras and not args.multi_only:
         try:
             paper_form = paper_form_eval(ntc, q_dev, args.batch, stream)
         except Exception as e:  # reported, never fatal to the headline line
             paper_form = {"error": f"{type(e).__name__}: {e}"[:300]}
 
     u8 = None
-    if not args.no_extras and precision != "f32":
+    if not args.no_extras and not args.multi_only and precision != "f32":
         try:
             u8 = u8_output_eval(ntc, mat, q_dev, q_host, stream)
         except Exception as e:  # reported, never fatal to the headline line
             u8 = {"error": f"{type(e).__name__}: {e}"[:300]}
 
     vq = None
-    if not args.no_extras:
+    if not args.no_extras and not args.multi_only:
         try:
             vq = vq_eval(ntc, q_dev, stream)
         except Exception as e:  # reported, never fatal to the headline line
             vq = {"error": f"{type(e).__name__}: {e}"[:300]}
 
     sqvq = None
-    if not args.no_extras:
+    if not args.no_extras and not args.multi_only:
         try:
             sqvq = sq_vq_train_eval(ntc, chain, args.batch, seed, stream)
         except Exception as e:  # reported, never fatal to the headline line
             sqvq = {"error": f"{type(e).__name__}: {e}"[:300]}
 
     equal = None
-    if not args.no_extras and not args.no_fp32_compare:
+    if not args.no_extras and not args.multi_only and not args.no_fp32_compare:
         try:
             equal = equal_psnr_eval(ntc, chain, args.batch, seed, stream)
         except Exception as e:  # reported, never fatal to the headline line

@@ -68,26 +68,31 @@ __device__ __forceinline__ float2 noise_pair_of(uint64_t key, int level, int gri
 // thread owns kAdamPerThread consecutive elements (float4 accesses); the
 // schedule factors are computed once per block in FP32.
 // Block b of one material's Adam pass (A: its segments, block prefix sums).
-__device__ __forceinline__ void adam_block(const AdamArgs& A, int64_t b) {
-  __shared__ float s_lr, s_ic1, s_ic2;
-  __shared__ uint64_t s_key;
-  int s = 0;
-  while (s + 1 < A.nseg && b >= A.block_start[s + 1]) ++s;
-  const AdamSeg& S = A.seg[s];
-  if (threadIdx.x == 0) {
-    const int64_t t = *A.step;
-    s_key = rng_key(A.noise_seed, noise_stream(t + 1));
-    const float x = (float)((double)t / (double)A.total);
-    s_lr = A.lr[S.group] * 0.5f * (1.f + cospif(x));
-    s_ic1 = 1.f / (1.f - powf(A.beta1, (float)(t + 1)));
-    s_ic2 = 1.f / (1.f - powf(A.beta2, (float)(t + 1)));
-  }
-  __syncthreads();
-  if (A.freeze_grids && S.group == 0) return;
-  const float lr = s_lr, inv_c1 = s_ic1, inv_c2 = s_ic2;
+// The step's schedule factors (cosine-annealed learning rate of both groups,
+// bias corrections) and the next step's noise key, from the device counter.
+struct AdamSched {
+  float lr[2], ic1, ic2;
+  uint64_t key;
+};
+__device__ __forceinline__ AdamSched adam_sched(const AdamArgs& A) {
+  AdamSched c;
+  const int64_t t = *A.step;
+  c.key = rng_key(A.noise_seed, noise_stream(t + 1));
+  const float x = (float)((double)t / (double)A.total);
+  const float cosf_ = 0.5f * (1.f + cospif(x));
+  c.lr[0] = A.lr[0] * cosf_;
+  c.lr[1] = A.lr[1] * cosf_;
+  c.ic1 = 1.f / (1.f - powf(A.beta1, (float)(t + 1)));
+  c.ic2 = 1.f / (1.f - powf(A.beta2, (float)(t + 1)));
+  return c;
+}
+
+// The elements of block `lb` of segment S (no barrier inside).
+__device__ __forceinline__ void adam_seg_block(const AdamArgs& A, const AdamSeg& S, int64_t lb,
+                                               const AdamSched& sc) {
+  const float lr = sc.lr[S.group], inv_c1 = sc.ic1, inv_c2 = sc.ic2;
   const float b1 = A.beta1, b2 = A.beta2, eps = A.eps;
-  const int64_t first =
-      ((b - A.block_start[s]) * (int64_t)kAdamBlock + threadIdx.x) * kAdamPerThread;
+  const int64_t first = (lb * (int64_t)kAdamBlock + threadIdx.x) * kAdamPerThread;
   if (first >= S.len) return;
   const int64_t e0 = S.off + first;
   auto upd = [&](float p, float m, float v, float g, float& po, float& mo, float& vo) {
@@ -99,7 +104,7 @@ __device__ __forceinline__ void adam_block(const AdamArgs& A, int64_t b) {
   // the next step's noisy value of segment element k (the same FP32 sum as
   // the dense noise pass)
   const bool fold = A.fold && S.noise_c > 0;
-  const uint64_t nkey = s_key;
+  const uint64_t nkey = sc.key;
   auto noisy = [&](int64_t k, float po) {
     const int c = S.noise_c;
     const int64_t cell = k / c;
@@ -159,6 +164,18 @@ __device__ __forceinline__ void adam_block(const AdamArgs& A, int64_t b) {
   }
 }
 
+// Block b of one material's Adam pass (A: its segments, block prefix sums).
+__device__ __forceinline__ void adam_block(const AdamArgs& A, int64_t b) {
+  __shared__ AdamSched s_sc;
+  int s = 0;
+  while (s + 1 < A.nseg && b >= A.block_start[s + 1]) ++s;
+  const AdamSeg& S = A.seg[s];
+  if (threadIdx.x == 0) s_sc = adam_sched(A);
+  __syncthreads();
+  if (A.freeze_grids && S.group == 0) return;
+  adam_seg_block(A, S, b - A.block_start[s], s_sc);
+}
+
 __global__ void __launch_bounds__(kAdamBlock) adam_kernel(const AdamArgs A) {
   adam_block(A, blockIdx.x);
 }
@@ -175,14 +192,34 @@ __device__ __forceinline__ int find_interval(const int64_t* start, int n, int64_
   return lo;
 }
 
-// Adam over every material of a batch: block b belongs to the material
-// whose Adam blocks contain it.  The last block to finish advances the step
-// counter of every material that took part (each block has read its
-// material's counter before it counts itself done) and re-arms the count.
+// Adam over every material of a batch.  Persistent: CTA j walks the
+// contiguous range [T j / G, T (j+1) / G) of the batch's blocks, looking its
+// material and segment up once and advancing them as its range crosses into
+// the next (the descriptors live in global memory; a lookup per block would
+// put chains of dependent loads before every block's work).  The last CTA
+// to finish advances the step counter of every material that took part
+// (each CTA has read its materials' counters before it counts itself done)
+// and tags their folded noisy copies.
 __global__ void __launch_bounds__(kAdamBlock) adam_batched_kernel(TrainBatchDev* D) {
-  const int64_t b = blockIdx.x;
-  const int i = find_interval(D->adam_start, D->n, b);
-  adam_block(D->adam[i], b - D->adam_start[i]);
+  __shared__ AdamSched sc;
+  const int64_t total = D->adam_blocks;
+  const int64_t b0 = total * blockIdx.x / gridDim.x, b1 = total * (blockIdx.x + 1) / gridDim.x;
+  int i = -1, s = 0;
+  for (int64_t b = b0; b < b1; ++b) {
+    if (i < 0 || b >= D->adam_start[i + 1]) {
+      i = i < 0 ? find_interval(D->adam_start, D->n, b) : i + 1;
+      while (b >= D->adam_start[i + 1]) ++i;  // materials without blocks
+      s = 0;
+      __syncthreads();  // every thread is done with the previous schedule
+      if (threadIdx.x == 0) sc = adam_sched(D->adam[i]);
+      __syncthreads();
+    }
+    const AdamArgs& A = D->adam[i];
+    const int64_t lb = b - D->adam_start[i];
+    while (s + 1 < A.nseg && lb >= A.block_start[s + 1]) ++s;
+    const AdamSeg& S = A.seg[s];
+    if (!(A.freeze_grids && S.group == 0)) adam_seg_block(A, S, lb - A.block_start[s], sc);
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
@@ -250,10 +287,23 @@ __global__ void __launch_bounds__(kNoiseBlock) noise_grids_kernel(const NoiseArg
 }
 
 // The noise pass of every material of a batch in one launch.
+// Persistent like adam_batched_kernel: a contiguous range of blocks per CTA,
+// one lookup and one currency check per material it reaches; a material
+// whose noisy copy is current is jumped over.
 __global__ void __launch_bounds__(kNoiseBlock) noise_batched_kernel(const TrainBatchDev* D) {
-  for (int64_t b = blockIdx.x; b < D->noise_blocks; b += gridDim.x) {
-    const int i = find_interval(D->noise_start, D->n, b);
-    if (!noisy_current(D->noise[i])) noise_block(D->noise[i], b - D->noise_start[i]);
+  const int64_t total = D->noise_blocks;
+  const int64_t b0 = total * blockIdx.x / gridDim.x, b1 = total * (blockIdx.x + 1) / gridDim.x;
+  int i = -1;
+  for (int64_t b = b0; b < b1; ++b) {
+    if (i < 0 || b >= D->noise_start[i + 1]) {
+      i = i < 0 ? find_interval(D->noise_start, D->n, b) : i + 1;
+      while (b >= D->noise_start[i + 1]) ++i;
+      if (noisy_current(D->noise[i])) {
+        b = D->noise_start[i + 1] - 1;  // the whole material
+        continue;
+      }
+    }
+    noise_block(D->noise[i], b - D->noise_start[i]);
   }
 }
 
@@ -443,7 +493,8 @@ cudaError_t launch_f8_weights(const float* w, int rows, int cols, int cols_out, 
 
 cudaError_t launch_adam_batched(TrainBatchDev* dev, int64_t blocks, cudaStream_t s) {
   if (blocks == 0) return cudaSuccess;
-  adam_batched_kernel<<<(unsigned)blocks, kAdamBlock, 0, s>>>(dev);
+  const int64_t cap = (int64_t)sm_count() * 8;
+  adam_batched_kernel<<<(unsigned)(blocks < cap ? blocks : cap), kAdamBlock, 0, s>>>(dev);
   return cudaGetLastError();
 }
 
