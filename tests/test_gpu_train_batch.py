@@ -137,3 +137,53 @@ def test_batched_full_steps_equal_single_steps_and_replay_in_a_graph():
         assert int(a[k][2].step_t.item()) == int(b[k][2].step_t.item())
         if BATCHES[k]:
             assert rel_err(to_np(a[k][2].params), to_np(b[k][2].params)) <= 1e-4, k
+
+
+@pytest.mark.parametrize("variant", ["learned", "three_hidden", "crops"])
+def test_batched_variants_equal_single_steps(variant):
+    """The paper's decoder form (learned G0, hardGELU, identity), three hidden
+    layers and crop batches in the batched step: each material's loss and
+    gradient equal its single-material step's (same arithmetic, atomic order
+    aside); the learned form also against the oracle."""
+    flags = ntc.FLAG_GRAD_ONLY | (ntc.FLAG_CROPS if variant == "crops" else 0)
+    shapes = [dict(width=128, height=128, channels=9, c0=12, c1=10, k_in=80),
+              dict(width=256, height=128, channels=6, c0=8, c1=12, k_in=64),
+              dict(width=64, height=64, channels=12, c0=16, c1=12, k_in=96)]
+    kw = dict(act=1, out_act=1, interp0=1) if variant == "learned" else {}
+    if variant == "three_hidden":
+        kw = dict(hidden_layers=3)
+    if variant == "crops":
+        shapes = [dict(width=512, height=256, channels=8, c0=8, c1=8, k_in=32),
+                  dict(width=256, height=256, channels=12, c0=12, c1=12, k_in=48)]
+    batches = [3000, 70000, 1] if variant != "crops" else [65536 + 4099, 70000]
+    sets = []
+    for k, shape in enumerate(shapes):
+        case = make_case(seed=160 + k, **kw, **shape)
+        chain = gen.box_mip_chain_u8(gen.synthetic_texture(case.width, case.height,
+                                                           case.channels, seed=1160 + k))
+        w = case.weights
+        tr = ntc.Trainer(case.width, case.height, case.channels, case.c0, case.c1, case.bits0,
+                         case.bits1, case.q0, case.q1, case.val0, case.val1, w[0::2], w[1::2],
+                         case.k_in, ntc.PREC_F16, case.act, case.out_act, total_steps=20,
+                         interp0=case.interp0)
+        tr.step_t.fill_(k + 1)
+        sets.append((case, chain, tr, ntc.Target(chain)))
+    tb = ntc.TrainBatch([s[2] for s in sets], [s[3] for s in sets], batches, SEED, flags=flags)
+    loss = ntc.ntc_train_step_batched(tb).cpu().numpy()
+    assert ntc.ntc_device_status() == ntc.OK
+    for k, (case, chain, tr, target) in enumerate(sets):
+        g_batched = to_np(tr.grad)
+        tr.grad.zero_()
+        l1 = ntc.ntc_train_step(tr, target, batches[k], SEED + k, flags=flags).item()
+        assert abs(l1 - loss[k]) <= 1e-5 * max(l1, 1e-12), (variant, k, l1, loss[k])
+        assert rel_err(g_batched, to_np(tr.grad)) <= 1e-5, (variant, k)
+        if variant == "learned" and batches[k] > 1:
+            w16 = [np.asarray(a, np.float64) for a in case.weights]
+            for i in range(0, len(w16), 2):
+                w16[i] = case.weights[i].astype(np.float16).astype(np.float64)
+            md = case.oracle_model(weights=w16, quantized=False)
+            xym = oracle.sample_batch(SEED + k, k + 1, batches[k], case.width, case.height, md.mips)
+            lref, g = md.loss_grad_xym(xym, oracle.targets_of_xym(chain, xym),
+                                       noise=(SEED + k, k + 1))
+            assert abs(l1 - lref) <= 2e-3 * lref
+            check_grads(tr.grad_views, g["grid0"] + g["grid1"] + g["w"], 2 * len(case.val0), True)

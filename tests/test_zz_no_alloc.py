@@ -4,7 +4,7 @@ ntc_train_step_noalloc serves callers that must not allocate device memory
 (frame loops, streams under graph capture, plugins handed their buffers by a
 host): its scratch gradient is a static array inside the library.  Both
 trainers run through it: the FP32 CUDA-core step and the default FP16
-tensor-core step.  This file is collected last so that a run stopping at its
+tensor-core step (and its FP8-E4M3 form).  This file is collected last so that a run stopping at its
 first failure has already run every other test.
 """
 import ctypes as C
@@ -50,7 +50,7 @@ def _step_both(ref, cand, target, batch, seed, call):
     assert rel_err(d_cand, d_ref) <= GRAD_TOL, call
 
 
-@pytest.mark.parametrize("precision", [ntc.PREC_F32, ntc.PREC_F16])
+@pytest.mark.parametrize("precision", [ntc.PREC_F32, ntc.PREC_F16, ntc.PREC_F8])
 def test_noalloc_step_matches_regular_step_twice(precision):
     case = make_case(128, 128, 6, 8, 8, k_in=32, seed=61)
     chain = gen.box_mip_chain_u8(gen.synthetic_texture(128, 128, 6, seed=1061))
