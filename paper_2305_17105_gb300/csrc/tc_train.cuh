@@ -235,58 +235,108 @@ __device__ void stage_train_f8(const ntc_material& M, const TPlan& P, uint8_t* s
                                            : (i - 2 * kHidden < M.channels ? M.b[2][i - 2 * kHidden] : 0.f));
 }
 
+// Eight consecutive FP16 values of row `row` of a [rows][ld] weight matrix,
+// columns k0 .. k0 + 7 (one 16-byte chunk of the canonical K-major layout).
+__device__ __forceinline__ uint4 w_chunk(const __half* w, int ld, int row, int k0) {
+  const __half* p = w + (size_t)row * ld + k0;
+  if ((reinterpret_cast<uintptr_t>(p) & 15) == 0) return __ldg(reinterpret_cast<const uint4*>(p));
+  uint32_t h[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) h[e] = __ldg(reinterpret_cast<const unsigned short*>(p) + e);
+  return make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16), h[6] | (h[7] << 16));
+}
+
+// A bias block chunk: (head, tail, 0, ..., 0) of an FP32 bias in group 0,
+// zeros in group 1.
+__device__ __forceinline__ uint4 bias_chunk(float b, int g) {
+  if (g) return make_uint4(0u, 0u, 0u, 0u);
+  __half hd, tl;
+  split_bias(b, hd, tl);
+  return make_uint4((uint32_t)__half_as_ushort(hd) | ((uint32_t)__half_as_ushort(tl) << 16), 0u, 0u, 0u);
+}
+
+// One staging job of the FP16 weight tiles: a 16-byte chunk (8 consecutive
+// K values of one output row) of W1 (internal slot order, the bias head and
+// tail in the constant-one slots), W2, W3 (rows >= C zero), the bias blocks
+// of layers 2 and 3, and with a third hidden layer Wh and its bias block.
+// Returns the chunk's byte offset in shared memory.
+__device__ __forceinline__ uint32_t stage_job(const ntc_material& M, const TPlan& P, int j, uint4& v) {
+  const int n1 = kHidden * (P.k_int / 8);
+  if (j < n1) {
+    const int o = j / (P.k_int / 8), g = j - o * (P.k_int / 8);
+    uint32_t h[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int col = slot_column(M, P, 8 * g + e);
+      __half x = __float2half_rn(0.f);
+      if (col >= 0) {
+        x = __ldg(static_cast<const __half*>(M.w[0]) + o * M.k_in + col);
+      } else if (col < -1) {
+        __half hd, tl;
+        split_bias(__ldg(M.b[0] + o), hd, tl);
+        x = col == -2 ? hd : tl;
+      }
+      h[e] = __half_as_ushort(x);
+    }
+    v = make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16), h[6] | (h[7] << 16));
+    return P.w1 + tc::canon_chunk(o, g, kHidden);
+  }
+  j -= n1;
+  if (j < kHidden * 8) {  // W2 [64][64]
+    const int o = j >> 3, g = j & 7;
+    v = w_chunk(static_cast<const __half*>(M.w[1]), kHidden, o, 8 * g);
+    return P.w2 + tc::canon_chunk(o, g, kHidden);
+  }
+  j -= kHidden * 8;
+  if (j < kN3 * 8) {  // W3 [C][64], rows >= C zero
+    const int c = j >> 3, g = j & 7;
+    v = c < M.channels ? w_chunk(static_cast<const __half*>(M.w[2]), kHidden, c, 8 * g)
+                       : make_uint4(0u, 0u, 0u, 0u);
+    return P.w3 + tc::canon_chunk(c, g, kN3);
+  }
+  j -= kN3 * 8;
+  if (j < kHidden * 2) {  // bias block of layer 2
+    const int o = j >> 1, g = j & 1;
+    v = bias_chunk(g ? 0.f : __ldg(M.b[1] + o), g);
+    return P.wb2 + tc::canon_chunk(o, g, kHidden);
+  }
+  j -= kHidden * 2;
+  if (j < kN3 * 2) {  // bias block of layer 3, rows >= C zero
+    const int c = j >> 1, g = j & 1;
+    v = c < M.channels ? bias_chunk(g ? 0.f : __ldg(M.b[2] + c), g) : make_uint4(0u, 0u, 0u, 0u);
+    return P.wb3 + tc::canon_chunk(c, g, kN3);
+  }
+  j -= kN3 * 2;
+  if (j < kHidden * 8) {  // Wh [64][64] (third hidden layer)
+    const int o = j >> 3, g = j & 7;
+    v = w_chunk(static_cast<const __half*>(M.w_h3), kHidden, o, 8 * g);
+    return P.wh + tc::canon_chunk(o, g, kHidden);
+  }
+  j -= kHidden * 8;
+  const int o = j >> 1, g = j & 1;  // its bias block
+  v = bias_chunk(g ? 0.f : __ldg(M.b_h3 + o), g);
+  return P.wbh + tc::canon_chunk(o, g, kHidden);
+}
+
 __device__ void stage_train(const ntc_material& M, const TPlan& P, uint8_t* sm) {
   const int tid = threadIdx.x, nt = blockDim.x;
-  const __half z = __float2half_rn(0.f);
-  if (P.f8) stage_train_f8(M, P, sm);
-  for (int i = tid; i < kHidden * P.k_int && !P.f8; i += nt) {
-    const int o = i / P.k_int, s = i - o * P.k_int;
-    const int col = slot_column(M, P, s);
-    __half v = z;
-    if (col >= 0) {
-      v = w_at(M, 0, o * M.k_in + col);
-    } else if (col < -1) {
-      __half hd, tl;
-      split_bias(M.b[0][o], hd, tl);
-      v = col == -2 ? hd : tl;
-    }
-    *reinterpret_cast<__half*>(sm + P.w1 + tc::canon_offset(o, s, kHidden, 2)) = v;
-  }
-  for (int i = tid; i < kHidden * kHidden && !P.f8; i += nt) {
-    const int o = i / kHidden, k = i - o * kHidden;
-    *reinterpret_cast<__half*>(sm + P.w2 + tc::canon_offset(o, k, kHidden, 2)) = w_at(M, 1, i);
-  }
-  for (int i = tid; i < kN3 * kHidden && !P.f8; i += nt) {
-    const int c = i / kHidden, k = i - c * kHidden;
-    *reinterpret_cast<__half*>(sm + P.w3 + tc::canon_offset(c, k, kN3, 2)) =
-        c < M.channels ? w_at(M, 2, i) : z;
-  }
-  for (int i = tid; i < kHidden * 16; i += nt) {
-    const int n = i / 16, k = i - n * 16;
-    __half hd, tl;
-    split_bias(M.b[1][n], hd, tl);
-    *reinterpret_cast<__half*>(sm + P.wb2 + tc::canon_offset(n, k, kHidden, 2)) =
-        k == 0 ? hd : (k == 1 ? tl : z);
-  }
-  for (int i = tid; i < kN3 * 16; i += nt) {
-    const int n = i / 16, k = i - n * 16;
-    __half hd = z, tl = z;
-    if (n < M.channels) split_bias(M.b[2][n], hd, tl);
-    *reinterpret_cast<__half*>(sm + P.wb3 + tc::canon_offset(n, k, kN3, 2)) =
-        k == 0 ? hd : (k == 1 ? tl : z);
-  }
-  if (P.h3) {
-    for (int i = tid; i < kHidden * kHidden; i += nt) {
-      const int o = i / kHidden, k = i - o * kHidden;
-      *reinterpret_cast<__half*>(sm + P.wh + tc::canon_offset(o, k, kHidden, 2)) =
-          static_cast<const __half*>(M.w_h3)[i];
-    }
-    for (int i = tid; i < kHidden * 16; i += nt) {
-      const int n = i / 16, k = i - n * 16;
-      __half hd, tl;
-      split_bias(M.b_h3[n], hd, tl);
-      *reinterpret_cast<__half*>(sm + P.wbh + tc::canon_offset(n, k, kHidden, 2)) =
-          k == 0 ? hd : (k == 1 ? tl : z);
+  if (P.f8) {
+    stage_train_f8(M, P, sm);
+  } else {
+    // every thread issues the loads of up to four chunks before it stores
+    // any of them, so the staging costs about one global round trip per
+    // four chunks instead of one per element
+    const int jobs = kHidden * (P.k_int / 8) + kHidden * 8 + kN3 * 8 + kHidden * 2 + kN3 * 2 +
+                     (P.h3 ? kHidden * 8 + kHidden * 2 : 0);
+    for (int j0 = tid; j0 < jobs; j0 += 4 * nt) {
+      uint4 v[4];
+      uint32_t off[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (j0 + u * nt < jobs) off[u] = stage_job(M, P, j0 + u * nt, v[u]);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (j0 + u * nt < jobs) *reinterpret_cast<uint4*>(sm + off[u]) = v[u];
     }
   }
   MipTabT* tb = reinterpret_cast<MipTabT*>(sm + P.tab);
@@ -1190,36 +1240,62 @@ __global__ void __launch_bounds__(kRows* NWG, 1) train_tc_kernel(const ntc_mater
     // flush jobs 0 dW1, 1 dW2, 2 dW3, 3 dWh, one warpgroup each (round robin)
     for (int job = wg; job < (P.h3 ? 4 : 3); job += NWG) {
       if (job == 0 && wq < 2) {
-        // [dW1 db1]: row r, X columns (the head constant-one slot gives db1 r)
+        // [dW1 db1]: row r, X columns (the head constant-one slot gives db1
+        // r); four slots that map to four consecutive, 16-byte aligned user
+        // columns leave as one vector reduction
+        float* gw = A.g.w[0];
 #pragma unroll 1
         for (int cb = 0; cb < P.k_int; cb += 16) {
           float v[16];
           tc::tmem_ld16(tW1 + lane + cb, v);
           tc::tmem_ld_wait();
 #pragma unroll
-          for (int e = 0; e < 16; ++e) {
-            const int uc = slot_column(M, P, cb + e);
-            if (uc >= 0 && A.g.w[0]) atomicAdd(A.g.w[0] + r * M.k_in + uc, v[e] * gs * sa[0]);
-            else if (uc == -2 && A.g.b[0]) atomicAdd(A.g.b[0] + r, v[e] * gs);
+          for (int q = 0; q < 4; ++q) {
+            int uc[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) uc[e] = slot_column(M, P, cb + 4 * q + e);
+            const int64_t o = (int64_t)r * M.k_in + uc[0];
+            if (gw && uc[0] >= 0 && uc[1] == uc[0] + 1 && uc[2] == uc[0] + 2 && uc[3] == uc[0] + 3 &&
+                (reinterpret_cast<uintptr_t>(gw + o) & 15) == 0) {
+              const float f = gs * sa[0];
+              atomicAdd(reinterpret_cast<float4*>(gw + o),
+                        make_float4(v[4 * q] * f, v[4 * q + 1] * f, v[4 * q + 2] * f, v[4 * q + 3] * f));
+            } else {
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                if (uc[e] >= 0 && gw) atomicAdd(gw + r * M.k_in + uc[e], v[4 * q + e] * gs * sa[0]);
+                else if (uc[e] == -2 && A.g.b[0]) atomicAdd(A.g.b[0] + r, v[4 * q + e] * gs);
+              }
+            }
           }
         }
       } else if ((job == 1 || job == 3) && wq < 2) {
-        // [dW2 db2] / [dWh dbh]: row r, input columns 0..63, the ones column
-        // 64 gives the bias
+        // [dW2 db2] / [dWh dbh]: row r, input columns 0..63 (vector
+        // reductions where the row is 16-byte aligned), the ones column 64
+        // gives the bias
         const uint32_t ta = job == 1 ? tW2 : tWh;
         float* gw = job == 1 ? A.g.w[1] : A.g.w_h3;
         float* gb = job == 1 ? A.g.b[1] : A.g.b_h3;
         const float gsw = gs * (job == 1 ? sa[1] : 1.f);  // FP8: H1 was held in units of s_a1
+        const bool vec = gw && (reinterpret_cast<uintptr_t>(gw + r * kHidden) & 15) == 0;
 #pragma unroll 1
         for (int cb = 0; cb < kHidden + 16; cb += 16) {
           float v[16];
           tc::tmem_ld16(ta + lane + cb, v);
           tc::tmem_ld_wait();
+          if (cb < kHidden && vec) {
 #pragma unroll
-          for (int e = 0; e < 16; ++e) {
-            const int col = cb + e;
-            if (col < kHidden && gw) atomicAdd(gw + r * kHidden + col, v[e] * gsw);
-            else if (col == kHidden && gb) atomicAdd(gb + r, v[e] * gs);
+            for (int q = 0; q < 4; ++q)
+              atomicAdd(reinterpret_cast<float4*>(gw + r * kHidden + cb) + q,
+                        make_float4(v[4 * q] * gsw, v[4 * q + 1] * gsw, v[4 * q + 2] * gsw,
+                                    v[4 * q + 3] * gsw));
+          } else {
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+              const int col = cb + e;
+              if (col < kHidden && gw) atomicAdd(gw + r * kHidden + col, v[e] * gsw);
+              else if (col == kHidden && gb) atomicAdd(gb + r, v[e] * gs);
+            }
           }
         }
       } else if (job == 2 && wq < 3) {
