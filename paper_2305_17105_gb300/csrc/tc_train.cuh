@@ -63,6 +63,10 @@ constexpr uint32_t kCols = 512;         // TMEM columns of the CTA
 constexpr uint32_t kGroup = 2048;       // bytes per 8-unit group of a 128-row tile
 constexpr uint32_t kWaitLimit = 1u << 18;  // suspended tries: ms to seconds
 constexpr int kDxStride = 84;           // floats per row of the dX staging rows
+// Coalesced grid scatter: per warp, 32 dX rows of 36 floats (conflict-free
+// 16-byte stores) and 32 rows of 112 bytes holding the 8 (grid, tap) cell
+// addresses and weights of a texel; 8 KB per warp, 32 KB per pipeline.
+constexpr int kScatDx = 36, kScatMeta = 112, kScatWarp = 32 * kScatDx * 4 + 32 * kScatMeta;
 constexpr uint32_t kSmemMax = 232448u - 2048u;  // dynamic shared memory (static reserve)
 
 // Shared-memory and TMEM plan.  Input slots: G0 groups (c0 values, or the
@@ -1131,6 +1135,7 @@ __global__ void __launch_bounds__(kRows* NWG, 1) train_tc_kernel(const ntc_mater
     if (!wait_phase(bar, phase, bar_id)) { aborted = true; break; }
     tc::fence_after_sync();
     const bool staged = LEARNED || M.c0 > kFastGridCh || M.c1 > kFastGridCh;
+    const bool vec_scatter = A.grids && !staged && (M.c0 & 3) == 0 && (M.c1 & 3) == 0;
     if (A.grids && staged) {
       // dX row -> this thread's staging row (the operand tiles are free now),
       // then G0 per tap slot (weight 1; learned interpolation) or through
@@ -1167,6 +1172,83 @@ __global__ void __launch_bounds__(kRows* NWG, 1) train_tc_kernel(const ntc_mater
         *reinterpret_cast<uint4*>(W + P.ONEc + tc::canon_chunk(row, 0, kRows)) = one;
         *reinterpret_cast<uint4*>(W + P.ONEc + tc::canon_chunk(row, 1, kRows)) = make_uint4(0, 0, 0, 0);
       }
+    } else if (vec_scatter) {
+      // Coalesced scatter (grids of 4k <= 16 channels): each warp stages
+      // its 32 texels' dX rows, cell addresses and tap weights in its 8 KB
+      // of the freed operand tiles, then adds them texel by texel with lane
+      // j taking grid j / 16, tap (j / 4) % 4 and channels 4 (j % 4) .. +3.
+      // The four lanes of a tap write 16 consecutive channels of one cell,
+      // so one warp instruction touches 8 cell rows instead of 32.
+      const int ln = tid & 31;
+      uint8_t* ws = W + (warp & 3) * kScatWarp;
+      float* dxr = reinterpret_cast<float*>(ws) + ln * kScatDx;
+      uint8_t* mr = ws + 32 * kScatDx * 4 + ln * kScatMeta;
+#pragma unroll
+      for (int cb = 0; cb < 32; cb += 16) {
+        float v[16];
+        tc::tmem_ld16(tD + lane + cb, v);
+        tc::tmem_ld_wait();
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          *reinterpret_cast<float4*>(dxr + cb + 4 * q) =
+              make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+      }
+      {
+        float* ga[8];
+        float wt[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) { ga[e] = nullptr; wt[e] = 0.f; }
+        if (valid) {
+          const int j = tb->level[m];
+          const int wm = tb->wm[m], hm = tb->hm[m];
+          const ntc_level& L = M.lv[j];
+          const float gsc = F8 ? gscale * sw[0] : gscale;
+#pragma unroll
+          for (int k = 0; k < 2; ++k) {
+            float* g = k ? A.g.grid1[j] : A.g.grid0[j];
+            if (!g) continue;
+            const int c = k ? M.c1 : M.c0;
+            const Taps t = bilinear_taps(x, y, wm, hm, k ? L.g1_w : L.g0_w, k ? L.g1_h : L.g0_h);
+#pragma unroll
+            for (int tp = 0; tp < 4; ++tp) {
+              ga[4 * k + tp] = g + (size_t)t.cell[tp] * c;
+              wt[4 * k + tp] = t.w[tp] * gsc;
+            }
+          }
+        }
+        uint4* mq = reinterpret_cast<uint4*>(mr);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const uint64_t a0 = reinterpret_cast<uint64_t>(ga[2 * e]), a1 = reinterpret_cast<uint64_t>(ga[2 * e + 1]);
+          mq[e] = make_uint4((uint32_t)a0, (uint32_t)(a0 >> 32), (uint32_t)a1, (uint32_t)(a1 >> 32));
+        }
+        mq[4] = make_uint4(__float_as_uint(wt[0]), __float_as_uint(wt[1]), __float_as_uint(wt[2]), __float_as_uint(wt[3]));
+        mq[5] = make_uint4(__float_as_uint(wt[4]), __float_as_uint(wt[5]), __float_as_uint(wt[6]), __float_as_uint(wt[7]));
+      }
+      __syncwarp();
+      {
+        const int k = ln >> 4, slot = ln >> 2, q = ln & 3;
+        const int col = (k ? 8 * P.f0 : 0) + 4 * q;
+        if (4 * q < (k ? M.c1 : M.c0)) {
+          const float* dx0 = reinterpret_cast<const float*>(ws) + col;
+          const uint8_t* m0 = ws + 32 * kScatDx * 4;
+#pragma unroll 4
+          for (int t = 0; t < 32; ++t) {
+            float* const ga = *reinterpret_cast<float* const*>(m0 + t * kScatMeta + 8 * slot);
+            if (ga) {
+              const float w = *reinterpret_cast<const float*>(m0 + t * kScatMeta + 64 + 4 * slot);
+              const float4 d = *reinterpret_cast<const float4*>(dx0 + t * kScatDx);
+              atomicAdd(reinterpret_cast<float4*>(ga) + q, make_float4(d.x * w, d.y * w, d.z * w, d.w * w));
+            }
+          }
+        }
+      }
+      // the staging ran over ONEa: once every warp of the pipeline is done
+      // with its rows, each thread writes its row's chunks back
+      tc::bar_sync(bar_id, kRows);
+      const uint4 one = make_uint4(tc::pack_f16x2(1.f, 1.f), 0u, 0u, 0u);
+      *reinterpret_cast<uint4*>(W + P.ONEa + tc::canon_chunk(row, 0, kRows)) = one;
+      *reinterpret_cast<uint4*>(W + P.ONEa + tc::canon_chunk(row, 1, kRows)) = make_uint4(0, 0, 0, 0);
     } else if (A.grids) {
       // dX slots: G0 at columns 0.., G1 at 8 * f0.. (f0 is 1 or 2)
       float d[32], dg0[16], dg1[16];
@@ -1216,7 +1298,7 @@ __global__ void __launch_bounds__(kRows* NWG, 1) train_tc_kernel(const ntc_mater
       }
     }
     tc::fence_before_sync();
-    if (staged) tc::fence_proxy_async();  // restored constants, read by the next tile's MMAs
+    if (staged || vec_scatter) tc::fence_proxy_async();  // restored constants, read by the next tile's MMAs
     tc::bar_sync(bar_id, kRows);  // the next tile's features overwrite the operand tiles
   }
 
