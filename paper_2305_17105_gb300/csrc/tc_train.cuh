@@ -896,23 +896,21 @@ __global__ void __launch_bounds__(kRows* NWG, 1) train_tc_kernel(const ntc_mater
       if (A.uvl) query_texel(M, A.uvl[3 * i], A.uvl[3 * i + 1], A.uvl[3 * i + 2], x, y, m);
       else sample_train_texel(A.crops != 0, skey, i, M.width, M.height, M.mips, x, y, m);
     }
-    float tgt[kN3];  // loss mode: the target texel; dout mode: the upstream gradient row
-    if (!A.target) {
-#pragma unroll
-      for (int c = 0; c < kN3; ++c) tgt[c] = (valid && c < C) ? A.dout[i * C + c] : 0.f;
-    } else {
+    // loss mode: the texel's C <= 16 target bytes, loaded here and parked in
+    // the (free) DZ3 tile once the features are built, so their latency
+    // hides behind the gathers; the loss reads them back
+    uint32_t tw[4] = {0u, 0u, 0u, 0u};
+    if (A.target && valid) {
       const uint8_t* trow = A.target + A.tgt_off[m] + ((int64_t)y * tb->wm[m] + x) * C;
       if ((C & 3) == 0) {
         // whole 4-byte words of the u8 row (row offsets are multiples of 4)
 #pragma unroll
-        for (int c4 = 0; c4 < kN3 / 4; ++c4) {
-          const uint32_t wv = (valid && 4 * c4 < C) ? __ldg(reinterpret_cast<const uint32_t*>(trow) + c4) : 0u;
-#pragma unroll
-          for (int b = 0; b < 4; ++b) tgt[4 * c4 + b] = (float)((wv >> (8 * b)) & 0xFFu) * (1.f / 255.f);
-        }
+        for (int c4 = 0; c4 < kN3 / 4; ++c4)
+          if (4 * c4 < C) tw[c4] = __ldg(reinterpret_cast<const uint32_t*>(trow) + c4);
       } else {
 #pragma unroll
-        for (int c = 0; c < kN3; ++c) tgt[c] = (valid && c < C) ? (float)trow[c] * (1.f / 255.f) : 0.f;
+        for (int c = 0; c < kN3; ++c)
+          if (c < C) tw[c >> 2] |= (uint32_t)trow[c] << (8 * (c & 3));
       }
     }
     {
@@ -964,6 +962,9 @@ __global__ void __launch_bounds__(kRows* NWG, 1) train_tc_kernel(const ntc_mater
           *reinterpret_cast<uint2*>(W + P.H1 + tc::canon_chunk(row, g >> 1, kRows) + (g & 1) * 8) =
               make_uint2(0u, 0u);
     }
+    if (A.target)
+      *reinterpret_cast<uint4*>(W + P.DZ3 + tc::canon_chunk(row, 1, kRows)) =
+          make_uint4(tw[0], tw[1], tw[2], tw[3]);
     tc::fence_proxy_async();
     tc::bar_sync(bar_id, kRows);
 
@@ -1054,12 +1055,24 @@ __global__ void __launch_bounds__(kRows* NWG, 1) train_tc_kernel(const ntc_mater
 #pragma unroll
         for (int c = 0; c < kN3; ++c) zv[c] = fmaf(zv[c], sa[2] * sw[2], b3[c]);
       }
+      // the target texel (loss mode) or the upstream gradient row (dout mode)
+      float tgt[kN3];
+      if (A.target) {
+        const uint4 t4 = *reinterpret_cast<const uint4*>(W + P.DZ3 + tc::canon_chunk(row, 1, kRows));
+        const uint32_t tv[4] = {t4.x, t4.y, t4.z, t4.w};
+#pragma unroll
+        for (int c = 0; c < kN3; ++c) tgt[c] = (float)((tv[c >> 2] >> (8 * (c & 3))) & 0xFFu) * (1.f / 255.f);
+      } else {
+#pragma unroll
+        for (int c = 0; c < kN3; ++c) tgt[c] = (valid && c < C) ? A.dout[i * C + c] : 0.f;
+      }
       float d[16];
 #pragma unroll
       for (int c = 0; c < kN3; ++c) {
         float g = 0.f;
         if (valid && c < C) {
-          const float yc = M.out_act == NTC_OUT_IDENTITY ? zv[c] : 1.f / (1.f + __expf(-zv[c]));
+          // sigmoid; the fast division is within 2 ulp
+          const float yc = M.out_act == NTC_OUT_IDENTITY ? zv[c] : __fdividef(1.f, 1.f + __expf(-zv[c]));
           if (A.target) {
             const float e = yc - tgt[c];
             loss_acc = fmaf(e, e, loss_acc);
