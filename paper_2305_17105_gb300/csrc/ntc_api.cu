@@ -713,6 +713,22 @@ static int plan_train_step(const ntc_material* m, const ntc_trainer* tr, const n
   return NTC_OK;
 }
 
+// Seed of the last step that folded the next step's noise into its Adam,
+// per noisy tag (host-side guess of whether the copy will be current).
+static std::mutex g_fold_mu;
+static std::map<const int64_t*, uint64_t> g_fold_seed;
+static bool fold_expected(const int64_t* tag, uint64_t seed) {
+  std::lock_guard<std::mutex> lock(g_fold_mu);
+  const auto it = g_fold_seed.find(tag);
+  return it != g_fold_seed.end() && it->second == seed;
+}
+static void note_fold(const int64_t* tag, bool folded, uint64_t seed) {
+  if (!tag) return;
+  std::lock_guard<std::mutex> lock(g_fold_mu);
+  if (folded) g_fold_seed[tag] = seed;
+  else g_fold_seed.erase(tag);
+}
+
 // Launches a planned step on `s`.
 static int launch_train_plan(const ntc_material* m, const ntc_trainer* tr, StepPlan& sp,
                              float* loss_out, int32_t flags, cudaStream_t s) {
@@ -733,7 +749,30 @@ static int launch_train_plan(const ntc_material* m, const ntc_trainer* tr, StepP
     e = ntc::launch_f8_train_prep(wm, w8, m->k_in, m->channels, const_cast<float*>(m->scale), s);
     if (e != cudaSuccess) return cuda_status(e, "train_step FP8 weights");
   }
-  if (sp.noise_pass) {
+  // With the noise folded into the previous step's Adam, the fused
+  // tensor-core step checks the noisy copy's tag itself (bilinear G0, grids
+  // of 4k <= 16 channels): no launch for the usual case of a current copy,
+  // the noise per tap otherwise.
+  // The check only pays when the copy is expected to be current: the
+  // previous step on this trainer folded with the same seed (a process-wide
+  // note per tag; the kernel still checks the tag, so a wrong guess costs
+  // time, not correctness).  Otherwise the dense pass runs.
+  const bool kernel_fold = sp.noise_pass && sp.na.tag && !sp.simt && !vq &&
+                           m->interp0 == NTC_INTERP_BILINEAR && (m->c0 & 3) == 0 &&
+                           m->c0 <= 16 && (m->c1 & 3) == 0 && m->c1 <= 16 &&
+                           fold_expected(sp.na.tag, sp.na.seed);
+  ntc::BwdArgs bk = sp.b;
+  ntc_material mk = sp.mt;
+  if (kernel_fold) {
+    bk.noise = 1;
+    bk.noisy_tag = sp.na.tag;
+    for (int j = 0; j < m->levels; ++j) {
+      bk.noisy0[j] = static_cast<const float*>(sp.mt.lv[j].grid0);
+      bk.noisy1[j] = static_cast<const float*>(sp.mt.lv[j].grid1);
+      mk.lv[j].grid0 = m->lv[j].grid0;
+      mk.lv[j].grid1 = m->lv[j].grid1;
+    }
+  } else if (sp.noise_pass) {
     e = ntc::launch_noise_grids(sp.na, s);
     if (e != cudaSuccess) return cuda_status(e, "train_step noise pass");
   }
@@ -757,11 +796,13 @@ static int launch_train_plan(const ntc_material* m, const ntc_trainer* tr, StepP
     mt.vq_books = 0;  // the fused step sees q as a plain FP32 grid
     mt.codebook0 = nullptr;
   }
-  e = sp.simt ? ntc::launch_backward_simt(mt, b, s) : ntc::launch_train_tc(mt, b, s);
+  e = sp.simt ? ntc::launch_backward_simt(mt, b, s)
+              : (kernel_fold ? ntc::launch_train_tc(mk, bk, s) : ntc::launch_train_tc(mt, b, s));
   if (e != cudaSuccess) return cuda_status(e, "train_step forward/backward");
   if (flags & NTC_FLAG_GRAD_ONLY) return NTC_OK;
   e = ntc::launch_adam(a, a.block_start[a.nseg], s);
   if (e != cudaSuccess) return cuda_status(e, "train_step adam");
+  note_fold(tr->noisy_tag, a.fold != 0, a.noise_seed);
   return cuda_status(ntc::launch_advance_step(tr->step, s, a.fold ? a.noisy_tag : nullptr,
                                               a.noise_seed),
                      "train_step step counter");

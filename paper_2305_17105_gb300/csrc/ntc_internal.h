@@ -31,6 +31,14 @@ struct BwdArgs {
   int grids;               // 0: skip grid gradients (frozen grids)
   int crops;               // training sampler: 256 x 256 crops of one mip (Sec. 5.1)
   int pipelines;           // tensor-core step: warpgroup pipelines per CTA (0: the most that fit)
+  // Noise check folded into the tensor-core step (single material, bilinear
+  // G0, grids of 4k <= 16 channels): with noisy_tag set, a CTA that finds it
+  // current ({noise_seed, step}) gathers from the trainer's noisy copy
+  // (noisy0/1, level pointers) without noise; otherwise from the material's
+  // grids with the noise added per tap (the same values).
+  const int64_t* noisy_tag;
+  const float* noisy0[NTC_MAX_LEVELS];
+  const float* noisy1[NTC_MAX_LEVELS];
 };
 
 cudaError_t launch_decode_simt(const ntc_material& m, const float* uvl, int64_t n, void* out,

@@ -466,13 +466,16 @@ __device__ __forceinline__ void ld_nc_v8(const float* p, float4& a, float4& b) {
 // Bilinear sample of one FP32 grid of 4k <= 16 channels with 16-byte loads,
 // all taps' loads issued before the interpolation (same FMA order as
 // sample_grid, so the same values).
+// `base` (nullable) replaces the level's grid pointer (the trainer's noisy
+// copy of the same layout).
 __device__ __forceinline__ void sample_grid_f32x4(const ntc_material& M, int j, int k, int x, int y,
-                                                  int wm, int hm, GridSample& gs) {
+                                                  int wm, int hm, GridSample& gs,
+                                                  const float* base = nullptr) {
   const ntc_level& L = M.lv[j];
   const int gw = k ? L.g1_w : L.g0_w, gh = k ? L.g1_h : L.g0_h;
   const int c4 = (k ? M.c1 : M.c0) >> 2;
   const Taps t = bilinear_taps(x, y, wm, hm, gw, gh);
-  const float4* g = static_cast<const float4*>(k ? L.grid1 : L.grid0);
+  const float4* g = static_cast<const float4*>(base ? static_cast<const void*>(base) : (k ? L.grid1 : L.grid0));
   float4 v[4][kFastGridCh / 4];
   if ((c4 == 2 || c4 == 4) && (reinterpret_cast<uintptr_t>(g) & 31) == 0) {
     // 32-byte loads: one L1 wavefront brings 8 channels
@@ -883,6 +886,9 @@ __global__ void __launch_bounds__(kRows* NWG, 1) train_tc_kernel(const ntc_mater
 
   const int64_t step = A.step_dev ? *A.step_dev : A.noise_step;
   const uint64_t nkey = rng_key(A.noise_seed, noise_stream(step));
+  // folded noise check: the noisy copy is current when its tag is {seed, step}
+  const bool use_copy = A.noisy_tag && A.noisy_tag[0] == (int64_t)A.noise_seed && A.noisy_tag[1] == step;
+  const bool noise_on = A.noise != 0 && !use_copy;
   const uint64_t skey = rng_key(A.sample_seed, sampler_stream(step));
   float loss_acc = 0.f;
   bool aborted = false;
@@ -917,12 +923,14 @@ __global__ void __launch_bounds__(kRows* NWG, 1) train_tc_kernel(const ntc_mater
       const int j = tb->level[m];
       const int wm = tb->wm[m], hm = tb->hm[m];
       GridSample gs;
-      if (LEARNED) learned_g0(M, P, j, x, y, wm, hm, valid, A.noise != 0, nkey, W, row);
+      if (LEARNED) learned_g0(M, P, j, x, y, wm, hm, valid, noise_on, nkey, W, row);
 #pragma unroll
       for (int k = LEARNED ? 1 : 0; k < 2; ++k) {
         const int ck = k ? M.c1 : M.c0;
-        if (!A.noise && (ck & 3) == 0 && ck <= kFastGridCh) sample_grid_f32x4(M, j, k, x, y, wm, hm, gs);
-        else sample_grid(M, j, k, x, y, wm, hm, A.noise != 0 && valid, nkey, gs);
+        if (!noise_on && (ck & 3) == 0 && ck <= kFastGridCh)
+          sample_grid_f32x4(M, j, k, x, y, wm, hm, gs, use_copy ? (k ? A.noisy1[j] : A.noisy0[j]) : nullptr);
+        else
+          sample_grid(M, j, k, x, y, wm, hm, noise_on && valid, nkey, gs);
         const int g0 = k ? P.f0 : 0, ng = k ? P.f1 : P.f0;
 #pragma unroll
         for (int g = 0; g < kGridPad / 8; ++g)
