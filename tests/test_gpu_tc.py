@@ -138,6 +138,54 @@ def test_full_size_decode_sampled():
     assert torch.isfinite(out.float()).all()
 
 
+
+def test_full_size_decode_sampled_trained():
+    """The same full-size check on a material compressed by the library's own
+    trainer (400 FP16 steps of 2^17 texels on a synthetic 4096^2 x 16 texture
+    set, exported with 4-bit grids), so that the activations have a trained
+    model's ranges; the oracle decodes the export with its stored FP16
+    weights and FP32 biases."""
+    side, c, c0, k, q = 4096, 16, 12, 48, 1.0 / 16
+    chain = gen.box_mip_chain_u8(gen.synthetic_texture(side, side, c, seed=1001))
+    rng = np.random.default_rng(1001)
+    lo, hi = oracle.quant_range(16, q)
+    g0, g1 = [], []
+    for (w0, h0), (w1, h1) in oracle.pyramid(side, side):
+        g0.append(gen.uniform_grid_values((h0, w0, c0), lo, hi, rng))
+        g1.append(gen.uniform_grid_values((h1, w1, c0), lo, hi, rng))
+    w = gen.random_mlp(k, 64, c, seed=2001, n_used=2 * c0 + 13)
+    steps = 400
+    tr = ntc.Trainer(side, side, c, c0, c0, 4, 4, q, q, g0, g1, [w[0], w[2], w[4]],
+                     [w[1], w[3], w[5]], k, ntc.PREC_F16, total_steps=steps)
+    target = ntc.Target(chain)
+    first = ntc.ntc_train_step(tr, target, 1 << 17, 1004).item()
+    for _ in range(steps - 1):
+        ntc.ntc_train_step(tr, target, 1 << 17, 1004)
+    assert ntc.ntc_device_status() == ntc.OK
+    assert tr.loss.item() < 0.5 * first
+    m16 = tr.export(ntc.PREC_F16)
+    n = 1 << 24
+    qs = gen.random_queries(n, oracle.mips(side, side), seed=4002)
+    out = ntc.ntc_decode(m16, _uvl(qs), out_dtype=torch.float16)
+    assert ntc.ntc_device_status() == ntc.OK
+    assert torch.isfinite(out.float()).all()
+    idx = np.arange(0, n, 4099)
+    got = out[torch.from_numpy(idx).to(DEV)].float().cpu().numpy()
+
+    def grids(gs):
+        res = []
+        for g in gs:
+            h, w_, cb = g.shape
+            ind = oracle.unpack(g.cpu().numpy().reshape(-1, cb), c0, 4)
+            res.append(oracle.dequantize(ind, 16, q).reshape(h, w_, c0))
+        return res
+    w16 = [x.float().cpu().numpy() for x in m16.weights]
+    b32 = [x.cpu().numpy() for x in tr.b]
+    md = oracle.Model(side, side, c, c0, c0, 16, 16, q, q, grids(m16.grids0), grids(m16.grids1),
+                      [np.asarray(a, np.float64) for a in (w16[0], b32[0], w16[1], b32[1], w16[2], b32[2])],
+                      k, 64, 0, 0)
+    assert np.abs(got - md.decode(qs[idx])).max() <= OUT_TOL
+
 def _f8_material(case):
     """E4M3 weights with per-layer scales (max |w| -> 448) and activation
     scales that map the largest input of each layer near 256."""
