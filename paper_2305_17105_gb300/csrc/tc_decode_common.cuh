@@ -431,7 +431,13 @@ __device__ __forceinline__ Query load_query(const float* __restrict__ uvl, int64
 // Query -> texel of this row (nearest and stochastic: one per query;
 // trilinear: tap `row & 7` of query `row / 8`).  q: the query's index (the
 // stochastic filter's counter), jkey: jitter_key of the frame.
-__device__ __forceinline__ void locate(const ntc_material& M, const MipTab* tb, const Query& qu,
+// MM: anything with the material's `mips` (ntc_material, or MipCount for a
+// kernel that keeps it in a register).
+struct MipCount {
+  int mips;
+};
+template <class MM>
+__device__ __forceinline__ void locate(const MM& M, const MipTab* tb, const Query& qu,
                                        int filter, int row, Row& r, int64_t q = 0,
                                        uint64_t jkey = 0) {
   r.valid = qu.valid;

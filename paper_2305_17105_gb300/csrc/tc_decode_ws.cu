@@ -132,6 +132,10 @@ __global__ void __launch_bounds__(kWsThreads, 1) decode_ws_batched_kernel(
     int mid = 0;
     Plan P(mat_s[w], false, false);
     int64_t m_t0 = 0, m_t1 = 0, m_q0 = 0, m_nq = 0, m_o0 = 0;
+    // the fields the tile loop reads, held in registers (the fences and
+    // waits of the loop clobber memory, so fields read from mat_s would be
+    // loaded again every tile)
+    int m_mips = 1, m_act = 0, m_oact = 0, m_C = 0;
     // stage material `mid` (no MMA of this warpgroup in flight, no thread
     // still reading the region)
     auto stage = [&](int id) {
@@ -140,6 +144,10 @@ __global__ void __launch_bounds__(kWsThreads, 1) decode_ws_batched_kernel(
       if (row == 0) mat_s[w] = B->mats[id];
       tc::bar_sync(bar_id, kRows);
       P = Plan(M, false, FAST);
+      m_mips = M.mips;
+      m_act = M.act;
+      m_oact = M.out_act;
+      m_C = M.channels;
       stage_shared<false>(M, P, region, row, kRows);
       zero_tail_groups<false>(P, xs);
       if (row == 0) {
@@ -160,10 +168,13 @@ __global__ void __launch_bounds__(kWsThreads, 1) decode_ws_batched_kernel(
       return m;
     };
     const MipTab* tb = nullptr;
-    auto locate_tile = [&](int64_t t, Row& r) {
+    // tile t's query of this row (tile t of the current material)
+    auto query_of = [&](int64_t t) {
       const int64_t ql = tri ? (t - m_t0) * per_tile + (row >> 3) : (t - m_t0) * per_tile + row;
-      const bool valid = ql < m_nq;
-      locate(M, tb, load_query(uvl, m_q0 + ql, valid), filter, row, r);
+      return load_query(uvl, m_q0 + ql, ql < m_nq);
+    };
+    auto locate_from = [&](const Query& qu, Row& r) {
+      locate(MipCount{m_mips}, tb, qu, filter, row, r);
       if (CLS > 0) gather_fast(Lay(), tb, r);
       else if (CLS < 0) gather_fast<Plan, false>(P, tb, r);  // batches: no VQ
     };
@@ -180,16 +191,20 @@ __global__ void __launch_bounds__(kWsThreads, 1) decode_ws_batched_kernel(
     float cur_wtap = 0.f;
     Row nxt;
     bool have_nxt = false;  // nxt holds tile tl+1, of the current material, gathered
+    Query nq;               // with have_nq: the query of tile tl+2, loaded a tile ahead
+    bool have_nq = false;
     // first tile of a material run (after staging): build it, gather its successor
     auto begin_run = [&](int64_t t) {
       tb = reinterpret_cast<const MipTab*>(region + P.tab);
       Row r;
-      locate_tile(t, r);
+      locate_from(query_of(t), r);
       build(r);
       cur_valid = r.valid;
       cur_wtap = r.wtap;
       have_nxt = t + 1 < t_end && t + 1 < m_t1;
-      if (have_nxt) locate_tile(t + 1, nxt);
+      if (have_nxt) locate_from(query_of(t + 1), nxt);
+      have_nq = t + 2 < t_end && t + 2 < m_t1;
+      if (have_nq) nq = query_of(t + 2);
     };
     if (t_begin < t_end) {
       stage(next_material(t_begin));
@@ -204,7 +219,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) decode_ws_batched_kernel(
       if (!tc::mbar_wait(&bar_d[w], pd, kWaitLimit)) *abort_flag = 1;
       pd ^= 1;
       tc::fence_after_sync();
-      hidden_epilogue_q(td, th, M.act);
+      hidden_epilogue_q(td, th, m_act);
       tc::tmem_st_wait();
       tc::fence_before_sync();
       __syncwarp();
@@ -221,16 +236,19 @@ __global__ void __launch_bounds__(kWsThreads, 1) decode_ws_batched_kernel(
       if (!tc::mbar_wait(&bar_d[w], pd, kWaitLimit)) *abort_flag = 1;
       pd ^= 1;
       tc::fence_after_sync();
-      hidden_epilogue_q(td, th, M.act);
+      hidden_epilogue_q(td, th, m_act);
       tc::tmem_st_wait();
       tc::fence_before_sync();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&bar_h[w]);
       if (*abort_flag) break;
-      // the tile after next, when it is of the current material
-      if (next_same && tl + 2 < t_end && tl + 2 < m_t1) {
-        locate_tile(tl + 2, nxt);
+      // the tile after next, when it is of the current material (its query
+      // was loaded a tile ago), then the query of its successor
+      if (next_same && have_nq) {
+        locate_from(nq, nxt);
         have_nxt = true;
+        have_nq = tl + 3 < t_end && tl + 3 < m_t1;
+        if (have_nq) nq = query_of(tl + 3);
       }
       // layer 3 -> output
       if (!tc::mbar_wait(&bar_o[w], po, kWaitLimit)) *abort_flag = 1;
@@ -240,7 +258,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) decode_ws_batched_kernel(
       tc::tmem_ld16(td3, yv);
       tc::tmem_ld_wait();
       tc::fence_before_sync();
-      out_activate(yv, M.out_act);
+      out_activate(yv, m_oact);
       if (tri) {
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
@@ -251,7 +269,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) decode_ws_batched_kernel(
           yv[c] = s;
         }
       }
-      const int C = M.channels;
+      const int C = m_C;
       if (valid && (!tri || (row & 7) == 0)) {
         // vector stores need the material's output block 16-byte aligned
         const int eb = out_dtype == NTC_DTYPE_U8 ? 1 : (out_dtype == NTC_DTYPE_F16 ? 2 : 4);
