@@ -431,7 +431,10 @@ size_t ntc_batch_workspace_bytes(void);
  * array), splits them into tiles ordered by material and copies the
  * descriptor into `workspace` (device, caller-owned) on `stream` with a
  * host-to-device copy from pageable memory: call it outside graph capture.
- * The workspace must stay untouched while batch decodes that use it run. */
+ * The workspace must stay untouched while batch decodes that use it run.
+ * A material takes at most 2^31 - 1 queries and a batch at most 2^31 - 1
+ * tiles (128 queries each, 16 with trilinear filtering): NTC_ERR_SHAPE
+ * beyond. */
 int ntc_batch_prepare(const ntc_material* mats, const int64_t* n_queries, int32_t n_materials,
                       int32_t filter, void* workspace, size_t workspace_bytes, ntc_batch* batch_out,
                       void* stream);

@@ -1088,6 +1088,8 @@ int ntc_batch_prepare(const ntc_material* mats, const int64_t* n_queries, int32_
     if (m->vq_books > 0)
       return fail(NTC_ERR_UNSUPPORTED, "batch material %d: batches decode scalar grids", i);
     if (n_queries[i] < 0) return fail(NTC_ERR_ARG, "batch material %d: negative query count", i);
+    if (n_queries[i] > INT32_MAX)
+      return fail(NTC_ERR_SHAPE, "batch material %d: more than 2^31 - 1 queries", i);
     const int c = ntc::fast_class(*m);
     cls = cls == -2 ? c : (cls == c ? cls : (cls != 0 && c != 0 ? -1 : 0));
     B.mats[i] = *m;
@@ -1095,6 +1097,8 @@ int ntc_batch_prepare(const ntc_material* mats, const int64_t* n_queries, int32_
     B.q_off[i + 1] = B.q_off[i] + n_queries[i];
     B.o_off[i + 1] = B.o_off[i] + n_queries[i] * m->channels;
   }
+  if (B.tile_start[n_materials] > INT32_MAX)
+    return fail(NTC_ERR_SHAPE, "batch: more than 2^31 - 1 tiles");
   uint32_t kmax = 0;
   for (int i = 0; i < n_materials; ++i) {
     const uint32_t need = ntc::ws_plan_bytes(mats[i], cls != 0);

@@ -78,7 +78,8 @@ __global__ void __launch_bounds__(kWsThreads, 1) decode_ws_batched_kernel(
   const int64_t total = B->total_tiles;
   const int w = wg < kWsCompute ? wg : (warp & 3);
   const int64_t nwgs = (int64_t)gridDim.x * kWsCompute, gw = (int64_t)blockIdx.x * kWsCompute + w;
-  const int64_t t_begin = total * gw / nwgs, t_end = total * (gw + 1) / nwgs;
+  // tile indices fit 32 bits (ntc_batch_prepare refuses larger batches)
+  const int t_begin = (int)(total * gw / nwgs), t_end = (int)(total * (gw + 1) / nwgs);
   constexpr uint32_t id64 = tc::idesc(kRows, kHidden), id16 = tc::idesc(kRows, kN3);
   const uint32_t tw = tmem_base + 128u * w;
   uint8_t* region = smem_raw + (size_t)w * S.region;
@@ -91,7 +92,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) decode_ws_batched_kernel(
       const uint64_t cst = tc::smem_desc(tc::smem_u32(smem_raw + S.cst), 2048, 128);
       uint32_t px = 0, ph = 0;
       bool ok = true;
-      for (int64_t tl = t_begin; tl < t_end; ++tl) {
+      for (int tl = t_begin; tl < t_end; ++tl) {
         if (!(ok = tc::mbar_wait(&bar_x[w], px, kWaitLimit))) break;
         px ^= 1;
         tc::fence_after_sync();
@@ -131,7 +132,10 @@ __global__ void __launch_bounds__(kWsThreads, 1) decode_ws_batched_kernel(
     // the current material: its plan, its tile range and query/output bases
     int mid = 0;
     Plan P(mat_s[w], false, false);
-    int64_t m_t0 = 0, m_t1 = 0, m_q0 = 0, m_nq = 0, m_o0 = 0;
+    // the current material's tiles [m_t0, m_t1), its first query and output
+    // element in the batch, its query count (< 2^31)
+    int m_t0 = 0, m_t1 = 0, m_nq = 0;
+    int64_t m_q0 = 0, m_o0 = 0;
     // the fields the tile loop reads, held in registers (the fences and
     // waits of the loop clobber memory, so fields read from mat_s would be
     // loaded again every tile)
@@ -154,23 +158,23 @@ __global__ void __launch_bounds__(kWsThreads, 1) decode_ws_batched_kernel(
         kint_s[w] = P.k_int;
         desc_s[w] = P.desc;
       }
-      m_t0 = B->tile_start[id];
-      m_t1 = B->tile_start[id + 1];
+      m_t0 = (int)B->tile_start[id];
+      m_t1 = (int)B->tile_start[id + 1];
       m_q0 = B->q_off[id];
-      m_nq = B->q_off[id + 1] - m_q0;
+      m_nq = (int)(B->q_off[id + 1] - m_q0);
       m_o0 = B->o_off[id];
       tc::fence_proxy_async();
       tc::bar_sync(bar_id, kRows);
     };
-    auto next_material = [&](int64_t t) {
+    auto next_material = [&](int t) {
       int m = mid;
       while (m + 1 < nm && t >= B->tile_start[m + 1]) ++m;
       return m;
     };
     const MipTab* tb = nullptr;
     // tile t's query of this row (tile t of the current material)
-    auto query_of = [&](int64_t t) {
-      const int64_t ql = tri ? (t - m_t0) * per_tile + (row >> 3) : (t - m_t0) * per_tile + row;
+    auto query_of = [&](int t) {
+      const int ql = tri ? (t - m_t0) * per_tile + (row >> 3) : (t - m_t0) * per_tile + row;
       return load_query(uvl, m_q0 + ql, ql < m_nq);
     };
     auto locate_from = [&](const Query& qu, Row& r) {
@@ -194,7 +198,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) decode_ws_batched_kernel(
     Query nq;               // with have_nq: the query of tile tl+2, loaded a tile ahead
     bool have_nq = false;
     // first tile of a material run (after staging): build it, gather its successor
-    auto begin_run = [&](int64_t t) {
+    auto begin_run = [&](int t) {
       tb = reinterpret_cast<const MipTab*>(region + P.tab);
       Row r;
       locate_from(query_of(t), r);
@@ -210,8 +214,8 @@ __global__ void __launch_bounds__(kWsThreads, 1) decode_ws_batched_kernel(
       stage(next_material(t_begin));
       begin_run(t_begin);
     }
-    for (int64_t tl = t_begin; tl < t_end; ++tl) {
-      const int64_t ql = tri ? (tl - m_t0) * per_tile + (row >> 3) : (tl - m_t0) * per_tile + row;
+    for (int tl = t_begin; tl < t_end; ++tl) {
+      const int ql = tri ? (tl - m_t0) * per_tile + (row >> 3) : (tl - m_t0) * per_tile + row;
       const bool valid = cur_valid != 0;
       const float wtap = cur_wtap;
       const int64_t obase = m_o0;
@@ -276,17 +280,17 @@ __global__ void __launch_bounds__(kWsThreads, 1) decode_ws_batched_kernel(
         if (((obase * eb) & 15) == 0) {
           store_texel(static_cast<uint8_t*>(out) + obase * eb, out_dtype, ql, C, yv);
         } else if (out_dtype == NTC_DTYPE_U8) {
-          uint8_t* o = static_cast<uint8_t*>(out) + obase + ql * C;
+          uint8_t* o = static_cast<uint8_t*>(out) + obase + (int64_t)ql * C;
 #pragma unroll
           for (int c = 0; c < 16; ++c)
             if (c < C) o[c] = (uint8_t)__float2uint_rn(__saturatef(yv[c]) * 255.f);
         } else if (out_dtype == NTC_DTYPE_F16) {
-          __half* o = static_cast<__half*>(out) + obase + ql * C;
+          __half* o = static_cast<__half*>(out) + obase + (int64_t)ql * C;
 #pragma unroll
           for (int c = 0; c < 16; ++c)
             if (c < C) o[c] = __float2half_rn(yv[c]);
         } else {
-          float* o = static_cast<float*>(out) + obase + ql * C;
+          float* o = static_cast<float*>(out) + obase + (int64_t)ql * C;
 #pragma unroll
           for (int c = 0; c < 16; ++c)
             if (c < C) o[c] = yv[c];

@@ -390,7 +390,14 @@ def test_batch_validation(L):
     assert rc(wsb=ws_bytes - 1) == ntc.ERR_ARG
     nq[1] = -1
     assert rc() == ntc.ERR_ARG
+    nq[1] = 1 << 31                                     # a material's queries must fit 31 bits
+    assert rc() == ntc.ERR_SHAPE
     nq[1] = 20
+    # and a batch's tiles: 200 materials of 2^31 - 1 queries
+    many = (ntc.ntc_material * 200)(*[_fake_material(precision=ntc.PREC_F16)] * 200)
+    big = (C.c_int64 * 200)(*[(1 << 31) - 1] * 200)
+    assert rc(a=many, q=big, n=200) == ntc.ERR_SHAPE
+    assert "tiles" in L.ntc_last_error().decode()
     arr[1] = _fake_material()                           # FP32 weights: not batched
     assert rc() == ntc.ERR_UNSUPPORTED
     # decode of an unprepared or empty batch
