@@ -1199,7 +1199,8 @@ __global__ void __launch_bounds__(kRows* NWG, 1) train_tc_kernel(const ntc_mater
       // of the freed operand tiles, then adds them texel by texel with lane
       // j taking grid j / 16, tap (j / 4) % 4 and channels 4 (j % 4) .. +3.
       // The four lanes of a tap write 16 consecutive channels of one cell,
-      // so one warp instruction touches 8 cell rows instead of 32.
+      // so one warp instruction touches 8 cell rows instead of 32, and a
+      // lane whose consecutive texels share the cell reduces once per run.
       const int ln = tid & 31;
       uint8_t* ws = W + (warp & 3) * kScatWarp;
       float* dxr = reinterpret_cast<float*>(ws) + ln * kScatDx;
@@ -1251,17 +1252,31 @@ __global__ void __launch_bounds__(kRows* NWG, 1) train_tc_kernel(const ntc_mater
         const int k = ln >> 4, slot = ln >> 2, q = ln & 3;
         const int col = (k ? 8 * P.f0 : 0) + 4 * q;
         if (4 * q < (k ? M.c1 : M.c0)) {
+          // consecutive texels whose tap falls in the same cell (neighbours
+          // in a crop batch, Sec. 5.1) are summed in registers first: one
+          // reduction per run of equal cells
           const float* dx0 = reinterpret_cast<const float*>(ws) + col;
           const uint8_t* m0 = ws + 32 * kScatDx * 4;
+          float* run = nullptr;
+          float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll 4
           for (int t = 0; t < 32; ++t) {
             float* const ga = *reinterpret_cast<float* const*>(m0 + t * kScatMeta + 8 * slot);
+            if (ga != run) {
+              if (run) atomicAdd(reinterpret_cast<float4*>(run) + q, acc);
+              run = ga;
+              acc = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
             if (ga) {
               const float w = *reinterpret_cast<const float*>(m0 + t * kScatMeta + 64 + 4 * slot);
               const float4 d = *reinterpret_cast<const float4*>(dx0 + t * kScatDx);
-              atomicAdd(reinterpret_cast<float4*>(ga) + q, make_float4(d.x * w, d.y * w, d.z * w, d.w * w));
+              acc.x = fmaf(d.x, w, acc.x);
+              acc.y = fmaf(d.y, w, acc.y);
+              acc.z = fmaf(d.z, w, acc.z);
+              acc.w = fmaf(d.w, w, acc.w);
             }
           }
+          if (run) atomicAdd(reinterpret_cast<float4*>(run) + q, acc);
         }
       }
       // the staging ran over ONEa: once every warp of the pipeline is done
