@@ -1157,6 +1157,11 @@ __global__ void __launch_bounds__(kRows* NWG, 1) train_tc_kernel(const ntc_mater
     tc::fence_after_sync();
     const bool staged = LEARNED || M.c0 > kFastGridCh || M.c1 > kFastGridCh;
     const bool vec_scatter = A.grids && !staged && (M.c0 & 3) == 0 && (M.c1 & 3) == 0;
+    // the staged form of the coalesced scatter: grids of 4k <= 16 channels
+    // (learned G0) and room for the per-warp tap tables past the 128 rows
+    const bool vec_staged = A.grids && staged && (M.c0 & 3) == 0 && M.c0 <= kFastGridCh &&
+                            (M.c1 & 3) == 0 && M.c1 <= kFastGridCh &&
+                            P.wg_bytes >= (uint32_t)(kRows * kDxStride * 4 + 4 * 32 * kScatMeta);
     if (A.grids && staged) {
       // dX row -> this thread's staging row (the operand tiles are free now),
       // then G0 per tap slot (weight 1; learned interpolation) or through
@@ -1171,7 +1176,72 @@ __global__ void __launch_bounds__(kRows* NWG, 1) train_tc_kernel(const ntc_mater
           *reinterpret_cast<float4*>(dxs + cb + 4 * q) =
               make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
       }
-      if (valid) {
+      if (vec_staged) {
+        // the coalesced scatter below over the staging rows: each warp puts
+        // its texels' 8 (grid, tap) cell addresses and weights past the
+        // 128 rows, lane j then adds grid j / 16, tap (j / 4) % 4, channels
+        // 4 (j % 4) .. +3 texel by texel, once per run of equal cells
+        const int ln = tid & 31, wq = warp & 3;
+        uint8_t* mbase = W + kRows * kDxStride * 4 + wq * 32 * kScatMeta;
+        {
+          float* ga[8];
+          float wt[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) { ga[e] = nullptr; wt[e] = 0.f; }
+          if (valid) {
+            const int j = tb->level[m];
+            const int wm = tb->wm[m], hm = tb->hm[m];
+            const ntc_level& L = M.lv[j];
+            const float gsc = F8 ? gscale * sw[0] : gscale;
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+              float* g = k ? A.g.grid1[j] : A.g.grid0[j];
+              if (!g) continue;
+              const int c = k ? M.c1 : M.c0;
+              const Taps t = bilinear_taps(x, y, wm, hm, k ? L.g1_w : L.g0_w, k ? L.g1_h : L.g0_h);
+#pragma unroll
+              for (int tp = 0; tp < 4; ++tp) {
+                ga[4 * k + tp] = g + (size_t)t.cell[tp] * c;
+                wt[4 * k + tp] = (LEARNED && k == 0 ? 1.f : t.w[tp]) * gsc;
+              }
+            }
+          }
+          uint4* mq = reinterpret_cast<uint4*>(mbase + ln * kScatMeta);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const uint64_t a0 = reinterpret_cast<uint64_t>(ga[2 * e]), a1 = reinterpret_cast<uint64_t>(ga[2 * e + 1]);
+            mq[e] = make_uint4((uint32_t)a0, (uint32_t)(a0 >> 32), (uint32_t)a1, (uint32_t)(a1 >> 32));
+          }
+          mq[4] = make_uint4(__float_as_uint(wt[0]), __float_as_uint(wt[1]), __float_as_uint(wt[2]), __float_as_uint(wt[3]));
+          mq[5] = make_uint4(__float_as_uint(wt[4]), __float_as_uint(wt[5]), __float_as_uint(wt[6]), __float_as_uint(wt[7]));
+        }
+        __syncwarp();
+        const int k = ln >> 4, slot = ln >> 2, q = ln & 3;
+        if (4 * q < (k ? M.c1 : M.c0)) {
+          const int col = (k ? 8 * P.f0 : (LEARNED ? ((ln >> 2) & 3) * M.c0 : 0)) + 4 * q;
+          const float* dx0 = reinterpret_cast<const float*>(W) + (32 * wq) * kDxStride + col;
+          float* run = nullptr;
+          float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 4
+          for (int t = 0; t < 32; ++t) {
+            float* const ga = *reinterpret_cast<float* const*>(mbase + t * kScatMeta + 8 * slot);
+            if (ga != run) {
+              if (run) atomicAdd(reinterpret_cast<float4*>(run) + q, acc);
+              run = ga;
+              acc = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            if (ga) {
+              const float w = *reinterpret_cast<const float*>(mbase + t * kScatMeta + 64 + 4 * slot);
+              const float4 d = *reinterpret_cast<const float4*>(dx0 + t * kDxStride);
+              acc.x = fmaf(d.x, w, acc.x);
+              acc.y = fmaf(d.y, w, acc.y);
+              acc.z = fmaf(d.z, w, acc.z);
+              acc.w = fmaf(d.w, w, acc.w);
+            }
+          }
+          if (run) atomicAdd(reinterpret_cast<float4*>(run) + q, acc);
+        }
+      } else if (valid) {
         const int j = tb->level[m];
         const int wm = tb->wm[m], hm = tb->hm[m];
         const ntc_level& L = M.lv[j];
