@@ -200,8 +200,13 @@ typedef struct {
   int64_t* noisy_tag;   /* nullable, device int64[2] (initialise to {-1, -1}): with `noisy`,
                            each step's Adam also writes the next step's noisy grids and
                            tags them {seed, step}; the next step's noise pass skips when
-                           the tag matches its own seed and step.  Reset it to {-1, -1}
-                           after changing params outside the library */
+                           the tag matches its own seed and step.  When the previous
+                           step on this trainer folded with the same seed (bilinear G0,
+                           grids of 4k <= 16 channels, tensor-core step) the fused step
+                           checks the tag itself and launches no noise pass; a stale
+                           tag then makes it add the noise per tap (the same values).
+                           Reset it to {-1, -1} after changing params outside the
+                           library */
 } ntc_trainer;
 
 /* Reference texture set: the 8-bit mip chain, texel values q/255. */
