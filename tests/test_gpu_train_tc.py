@@ -201,6 +201,39 @@ def test_dense_noise_pass_equals_noise_per_tap(precision):
     assert rel_err(grads[0], grads[1]) < 1e-5
 
 
+
+def test_fused_step_checks_a_stale_tag_itself():
+    """After a regular step with seed s the library expects the next step
+    with s to find the noisy copy current, and lets the fused kernel check
+    the tag instead of launching the noise pass.  Moving the step counter by
+    hand makes the tag stale: the fused step must then add the noise per tap,
+    so its loss and gradient equal those of a trainer without the noisy
+    scratch in the same state."""
+    case = make_case(128, 64, 12, 12, 12, k_in=48, seed=77)
+    chain = gen.box_mip_chain_u8(gen.synthetic_texture(128, 64, 12, seed=1077))
+    target = ntc.Target(chain)
+    w = case.weights
+    a = _trainer(case, ntc.PREC_F16, total=40)
+    b = ntc.Trainer(case.width, case.height, case.channels, case.c0, case.c1, case.bits0,
+                    case.bits1, case.q0, case.q1, case.val0, case.val1, [w[0], w[2], w[4]],
+                    [w[1], w[3], w[5]], case.k_in, ntc.PREC_F16, case.act, case.out_act,
+                    total_steps=40, noisy_scratch=False)
+    for tr in (a, b):
+        ntc.ntc_train_step(tr, target, 2048 + 17, 9)   # a: Adam writes the copy of step 1
+    torch.cuda.synchronize()
+    assert a.noisy_tag.cpu().tolist() == [9, 1]
+    losses, grads = [], []
+    for tr in (a, b):
+        tr.step_t.fill_(5)                             # a's tag {9, 1} is now stale
+        ntc.ntc_train_step(tr, target, 2048 + 17, 9, flags=ntc.FLAG_GRAD_ONLY)
+        torch.cuda.synchronize()
+        assert ntc.ntc_device_status() == ntc.OK
+        losses.append(tr.loss.item())
+        grads.append(to_np(tr.grad))
+    # the first step's parameters differ by the order of its atomic sums
+    assert abs(losses[0] - losses[1]) <= 1e-5 * abs(losses[1])
+    assert rel_err(grads[0], grads[1]) < 1e-4
+
 def _expected_noisy(tr, case, seed, step):
     """params + the oracle's noise of (seed, step) for every grid value, summed
     in FP32 (the dense noise pass's arithmetic), per grid view."""
