@@ -730,6 +730,43 @@ __device__ __forceinline__ void scatter_taps(float* g, int c, const Taps& t, con
   }
 }
 
+// One lane's part of the coalesced grid scatter: slot `slot` (grid, tap) and
+// channels 4q .. 4q+3 of each of the warp's 32 texels, whose cell addresses
+// and weights sit at meta + t * kScatMeta and whose dX values at
+// dx + t * dx_stride.  MERGE: consecutive texels that share the cell are
+// summed in registers and reduced once per run (coherent texels: crops or
+// given queries); otherwise one reduction per texel.
+template <bool MERGE>
+__device__ __forceinline__ void scatter_lane(const uint8_t* meta, const float* dx, int dx_stride,
+                                             int slot, int q) {
+  float* run = nullptr;
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 4
+  for (int t = 0; t < 32; ++t) {
+    float* const ga = *reinterpret_cast<float* const*>(meta + t * kScatMeta + 8 * slot);
+    if (MERGE) {
+      if (ga != run) {
+        if (run) atomicAdd(reinterpret_cast<float4*>(run) + q, acc);
+        run = ga;
+        acc = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+    if (ga) {
+      const float w = *reinterpret_cast<const float*>(meta + t * kScatMeta + 64 + 4 * slot);
+      const float4 d = *reinterpret_cast<const float4*>(dx + t * dx_stride);
+      if (MERGE) {
+        acc.x = fmaf(d.x, w, acc.x);
+        acc.y = fmaf(d.y, w, acc.y);
+        acc.z = fmaf(d.z, w, acc.z);
+        acc.w = fmaf(d.w, w, acc.w);
+      } else {
+        atomicAdd(reinterpret_cast<float4*>(ga) + q, make_float4(d.x * w, d.y * w, d.z * w, d.w * w));
+      }
+    }
+  }
+  if (MERGE && run) atomicAdd(reinterpret_cast<float4*>(run) + q, acc);
+}
+
 __device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t& phase, int bar_id) {
   const bool ok = tc::mbar_wait(bar, phase, kWaitLimit);
   phase ^= 1;
@@ -1157,6 +1194,8 @@ __global__ void __launch_bounds__(kRows* NWG, 1) train_tc_kernel(const ntc_mater
     tc::fence_after_sync();
     const bool staged = LEARNED || M.c0 > kFastGridCh || M.c1 > kFastGridCh;
     const bool vec_scatter = A.grids && !staged && (M.c0 & 3) == 0 && (M.c1 & 3) == 0;
+    // coherent texels (crop batches, given queries): merge runs of equal cells
+    const bool merge = A.crops || A.uvl;
     // the staged form of the coalesced scatter: grids of 4k <= 16 channels
     // (learned G0) and room for the per-warp tap tables past the 128 rows
     const bool vec_staged = A.grids && staged && (M.c0 & 3) == 0 && M.c0 <= kFastGridCh &&
@@ -1220,26 +1259,8 @@ __global__ void __launch_bounds__(kRows* NWG, 1) train_tc_kernel(const ntc_mater
         if (4 * q < (k ? M.c1 : M.c0)) {
           const int col = (k ? 8 * P.f0 : (LEARNED ? ((ln >> 2) & 3) * M.c0 : 0)) + 4 * q;
           const float* dx0 = reinterpret_cast<const float*>(W) + (32 * wq) * kDxStride + col;
-          float* run = nullptr;
-          float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll 4
-          for (int t = 0; t < 32; ++t) {
-            float* const ga = *reinterpret_cast<float* const*>(mbase + t * kScatMeta + 8 * slot);
-            if (ga != run) {
-              if (run) atomicAdd(reinterpret_cast<float4*>(run) + q, acc);
-              run = ga;
-              acc = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-            if (ga) {
-              const float w = *reinterpret_cast<const float*>(mbase + t * kScatMeta + 64 + 4 * slot);
-              const float4 d = *reinterpret_cast<const float4*>(dx0 + t * kDxStride);
-              acc.x = fmaf(d.x, w, acc.x);
-              acc.y = fmaf(d.y, w, acc.y);
-              acc.z = fmaf(d.z, w, acc.z);
-              acc.w = fmaf(d.w, w, acc.w);
-            }
-          }
-          if (run) atomicAdd(reinterpret_cast<float4*>(run) + q, acc);
+          if (merge) scatter_lane<true>(mbase, dx0, kDxStride, slot, q);
+          else scatter_lane<false>(mbase, dx0, kDxStride, slot, q);
         }
       } else if (valid) {
         const int j = tb->level[m];
@@ -1322,31 +1343,10 @@ __global__ void __launch_bounds__(kRows* NWG, 1) train_tc_kernel(const ntc_mater
         const int k = ln >> 4, slot = ln >> 2, q = ln & 3;
         const int col = (k ? 8 * P.f0 : 0) + 4 * q;
         if (4 * q < (k ? M.c1 : M.c0)) {
-          // consecutive texels whose tap falls in the same cell (neighbours
-          // in a crop batch, Sec. 5.1) are summed in registers first: one
-          // reduction per run of equal cells
           const float* dx0 = reinterpret_cast<const float*>(ws) + col;
           const uint8_t* m0 = ws + 32 * kScatDx * 4;
-          float* run = nullptr;
-          float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll 4
-          for (int t = 0; t < 32; ++t) {
-            float* const ga = *reinterpret_cast<float* const*>(m0 + t * kScatMeta + 8 * slot);
-            if (ga != run) {
-              if (run) atomicAdd(reinterpret_cast<float4*>(run) + q, acc);
-              run = ga;
-              acc = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-            if (ga) {
-              const float w = *reinterpret_cast<const float*>(m0 + t * kScatMeta + 64 + 4 * slot);
-              const float4 d = *reinterpret_cast<const float4*>(dx0 + t * kScatDx);
-              acc.x = fmaf(d.x, w, acc.x);
-              acc.y = fmaf(d.y, w, acc.y);
-              acc.z = fmaf(d.z, w, acc.z);
-              acc.w = fmaf(d.w, w, acc.w);
-            }
-          }
-          if (run) atomicAdd(reinterpret_cast<float4*>(run) + q, acc);
+          if (merge) scatter_lane<true>(m0, dx0, kScatDx, slot, q);
+          else scatter_lane<false>(m0, dx0, kScatDx, slot, q);
         }
       }
       // the staging ran over ONEa: once every warp of the pipeline is done
